@@ -1,0 +1,159 @@
+/*
+ * nuht.h -- C ABI of the GB300 (sm_103a) nonuniform fast Hankel transform.
+ *
+ * The transform (the discrete Hankel transform, Sec. 1, eq. DHT; matrix
+ * form A(k, j) = J_nu(omega_k r_j) of Sec. 2):
+ *
+ *     g_k = sum_{j=0}^{n-1} c_j J_nu(omega_k r_j),   k = 0..m-1,
+ *
+ * from n nonuniform points r_j >= 0 to m nonuniform frequencies omega_k >= 0,
+ * to a requested precision eps, by the paper's method (Algorithm 2): the
+ * matrix is subdivided along omega r = z (Algorithm 1); blocks with
+ * omega r <= z use the Wimp expansion (Sec. 3.1), blocks with omega r > z use
+ * Hankel's expansion through 2M type-3 NUFFTs (Sec. 3.2), and small
+ * mixed blocks are summed directly.  The orders L, M and the crossover z come
+ * from the error bounds of Lemma 3.1 and Sec. 3.2 (eq. asy-error), as
+ * described in Sec. 3.3.
+ *
+ * Index convention: points are indexed by j (length n), frequencies by k
+ * (length m).  The paper uses the opposite letters.
+ *
+ * Accuracy contract (per coefficient vector):
+ *     max_k |g_k - g_k^exact| <= 10 eps ||c||_1.
+ *
+ * Memory: unless stated otherwise every array argument is a DEVICE pointer
+ * (cudaMalloc'd or managed memory of the current device).  All FP64 arrays are
+ * contiguous.  The caller owns every array it passes.  Calls are ordered on
+ * the given CUDA stream (a cudaStream_t passed as void*; NULL = the legacy
+ * default stream) and may return before the GPU work finishes, except
+ * nuht_plan, which synchronises the stream once (the subdivision runs on the
+ * host), and the *_host entry points, which synchronise before returning.
+ *
+ * Errors: every int-returning call returns NUHT_OK (0) or one of the
+ * NUHT_ERR_* codes below; nuht_strerror() gives a message.  On error no
+ * output array is written (plan: *out is set to NULL).
+ */
+#ifndef NUHT_H
+#define NUHT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define NUHT_OK              0
+#define NUHT_ERR_INVALID_ARG 1   /* n or m < 0, eps outside [1e-15, 1e-1], nvec < 1, NULL plan ... */
+#define NUHT_ERR_DOMAIN      2   /* some r_j or omega_k is negative, NaN or infinite */
+#define NUHT_ERR_NOMEM       3   /* a device or host allocation failed */
+#define NUHT_ERR_CUDA        4   /* a CUDA runtime call failed (see nuht_last_cuda_error) */
+#define NUHT_ERR_TIMEOUT     5   /* a bounded device wait gave up (reserved) */
+#define NUHT_ERR_UNSUPPORTED 6   /* option combination not built (e.g. order |nu| > 100) */
+
+/* --------------------------------------------------------------- options */
+#define NUHT_PREC_FP64  0   /* every stage in FP64 (or FP64-accurate arithmetic) */
+#define NUHT_PREC_MIXED 1   /* FP32 spreading / FFT / interpolation, FP64 phases and moments */
+
+/* Block classes (Sec. 4.1). */
+#define NUHT_BLOCK_LOCAL  0
+#define NUHT_BLOCK_ASY    1
+#define NUHT_BLOCK_DIRECT 2
+
+typedef struct {
+    int precision;     /* NUHT_PREC_FP64 (default) or NUHT_PREC_MIXED */
+    int min_size;      /* largest area (rows*cols) of a mixed block summed directly;
+                          default 1024 (Sec. 4.1) */
+    int n_split_cand;  /* candidate rows tried by SplitIndices (Sec. 4.1); default 16 */
+    int m_terms;       /* asymptotic terms M; 0 = the heuristic of Sec. 3.3 */
+    int class_mask;    /* bit c set = apply blocks of class c (testing aid); default 7 */
+    int reserved[7];   /* must be zero */
+} nuht_opts;
+
+typedef struct {
+    int     nu;            /* order */
+    int     M;             /* Hankel terms (pairs), Sec. 3.3 */
+    int     L;             /* Wimp order (terms l = 0..L), Lemma 3.1 */
+    int     nufft_width;   /* ES kernel width w of the type-3 NUFFTs */
+    double  z;             /* crossover point, B^asy_{nu,M}(z) = eps */
+    double  eps;
+    int64_t n, m;
+    int64_t n_local, n_asy, n_direct;     /* block counts per class */
+    int64_t direct_entries;               /* sum of direct block areas */
+    int64_t local_rows_cols;              /* sum over local blocks of rows + cols */
+    int64_t asy_rows_cols;                /* sum over asymptotic blocks of rows + cols */
+    int64_t fft_points;                   /* sum over asymptotic blocks of FFT sizes */
+    int64_t device_bytes;                 /* device memory held by the plan */
+} nuht_plan_info;
+
+typedef struct nuht_plan_s *nuht_plan_t;
+
+/* Fill *opt with the defaults listed above. */
+void nuht_default_opts(nuht_opts *opt);
+
+/* Host-only: the expansion orders and crossover of Sec. 3.3 for (nu, eps).
+ * m_terms = 0 uses the heuristic of Sec. 3.3 (eq. num-asy-terms) for M.  Outputs: *M, *z (root of
+ * B^asy_{nu,M}(z) = eps, Sec. 3.2 eq. asy-error) and *L (smallest L with
+ * B^loc_{nu,L}(z) < eps, Lemma 3.1).  No GPU needed. */
+int nuht_choose_params(int nu, double eps, int m_terms, int *M, double *z, int *L);
+
+/* Build a plan for order nu, points r[0..n), frequencies omega[0..m) (device
+ * FP64, any order, values >= 0), tolerance eps in [1e-15, 1e-1].  Sorts r and
+ * omega on the device, subdivides the matrix on the host (Algorithm 1) and
+ * uploads the block work lists.  The plan copies what it needs; r and omega
+ * may be freed after return.  opt may be NULL (defaults).  Negative nu is
+ * mapped through J_{-nu} = (-1)^nu J_nu.  n = 0 or m = 0 is allowed. */
+int nuht_plan(nuht_plan_t *out, int nu, const double *r, int64_t n,
+              const double *omega, int64_t m, double eps, const nuht_opts *opt,
+              void *stream);
+
+/* Forward transform g = A c.  c: n x nvec (row-major, c[j*nvec + v]) FP64,
+ * or n x nvec complex (interleaved re,im: c[2*(j*nvec+v)+{0,1}]) when
+ * is_complex != 0.  g: m x nvec of the same kind, OVERWRITTEN, in the
+ * caller's original omega order.  The operator is real, so a complex c is
+ * transformed as its real and imaginary parts. */
+int nuht_execute(nuht_plan_t p, const double *c, double *g, int nvec, int is_complex,
+                 void *stream);
+
+/* Adjoint (transposed) transform c = A^T g with the same conventions (g has
+ * m rows, c has n rows, c is overwritten, in the caller's original r order).
+ * A is real, so the adjoint is the transpose. */
+int nuht_adjoint(nuht_plan_t p, const double *g, double *c, int nvec, int is_complex,
+                 void *stream);
+
+/* Whole transform from HOST arrays: copies r, omega, c to the device, plans,
+ * executes, copies g (m x nvec real) back to the host array g, and frees the
+ * plan.  r, omega, c, g are host pointers (pinned memory is fastest).
+ * Synchronises the stream before returning. */
+int nuht_transform_host(int nu, const double *r, int64_t n, const double *omega,
+                        int64_t m, double eps, const double *c, double *g, int nvec,
+                        const nuht_opts *opt, void *stream);
+
+/* Plan summary (orders, block counts, work sizes). */
+int nuht_info(nuht_plan_t p, nuht_plan_info *out);
+
+/* Copy the blocks of class cls (NUHT_BLOCK_*) into ranges, 4 int64 per block
+ * (k0, k1, j0, j1; inclusive; indices into the SORTED omega / r), host
+ * memory, at most cap blocks.  *count receives the number of blocks of that
+ * class (call with cap = 0 to size the buffer). */
+int nuht_get_blocks(nuht_plan_t p, int cls, int64_t *ranges, int64_t cap, int64_t *count);
+
+/* Copy the sorting permutations to HOST arrays: perm_r[i] = user index of
+ * the i-th smallest r (n entries), perm_omega likewise (m entries).  Either
+ * pointer may be NULL. */
+int nuht_get_permutations(nuht_plan_t p, int32_t *perm_r, int32_t *perm_omega);
+
+/* Release a plan (NULL is ignored).  Waits for the plan's stream. */
+void nuht_destroy(nuht_plan_t p);
+
+/* Static message for a status code. */
+const char *nuht_strerror(int code);
+
+/* Message of the last CUDA error seen by this library in this thread. */
+const char *nuht_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUHT_H */

@@ -139,6 +139,6 @@ def direct_rows(nu, r, omega, c, rows, nthreads=0):
 
 
 def direct(nu, r, omega, c, nthreads=0):
-    """Full O(nm) direct sum g_k = sum_j c_j J_nu(omega_k r_j), Eq. (1.5)."""
+    """Full O(nm) direct sum g_k = sum_j c_j J_nu(omega_k r_j) (Sec. 1, eq. DHT)."""
     return direct_rows(nu, r, omega, c, np.arange(np.asarray(omega).size),
                        nthreads)

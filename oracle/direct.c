@@ -1,8 +1,8 @@
 /*
  * Oracle (test infrastructure only; never part of the product path).
  *
- * Plain FP64 CPU evaluation of the discrete Hankel transform, Eq. (1.5)
- * (the DHT definition in the introduction):
+ * Plain FP64 CPU evaluation of the discrete Hankel transform (Sec. 1,
+ * eq. DHT):
  *
  *     g_k = sum_j c_j J_nu(omega_k r_j)
  *

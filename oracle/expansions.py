@@ -1,16 +1,17 @@
 """Oracle: pointwise local (Wimp) and asymptotic (Hankel) sums.
 
 Test infrastructure only.  These evaluate, term by term with the oracle's own
-J_n, the two truncated expansions whose errors Lemma 3.1 and Eq. (3.5) bound:
+J_n, the two truncated expansions whose errors Lemma 3.1 and the remainder bound of Sec. 3.2 (eq. asy-error) bound:
 
-* Wimp expansion (Sec. 3.1, Eq. 3.1).  The printed coefficient
+* Wimp expansion (Sec. 3.1).  The printed coefficient
   C_l(x) = delta_l J_{nu/2+l}(x) J_{nu/2-l}(x) contradicts the proof of
   Lemma 3.1, which evaluates the factors at x/2; the reading used is
       even nu:  J_nu(x y) = sum_l delta_l J_{nu/2+l}(x/2) J_{nu/2-l}(x/2) T_{2l}(y),
       odd nu:   J_nu(x y) = sum_l 2 J_{(nu+1)/2+l}(x/2) J_{(nu-1)/2-l}(x/2) T_{2l+1}(y),
   delta_0 = 1, delta_l = 2 otherwise, |y| <= 1 (the odd form follows from
   Graf's addition theorem, DLMF 10.23.7, with both arguments x/2).
-* Hankel expansion (Sec. 3.2, Eq. 3.4 / the bracket of Eq. 3.5), M pairs of
+* Hankel expansion (Sec. 3.2, eq. asymptotic-expansion / the bracket of
+  eq. asy-error), M pairs of
   terms, phi = -(2nu+1)pi/4.
 """
 import math
@@ -52,7 +53,7 @@ def wimp_sum(nu, L, x, y):
 
 def hankel_sum(nu, M, x):
     """sqrt(2/pi) sum_{l<M} [(-1)^l a_2l x^(-2l-1/2) cos(x+phi)
-                             - (-1)^l a_2l+1 x^(-2l-3/2) sin(x+phi)], Eq. (3.5)."""
+                             - (-1)^l a_2l+1 x^(-2l-3/2) sin(x+phi)], Sec. 3.2."""
     phi = -(2.0 * nu + 1.0) * math.pi / 4.0
     # cos/sin(x + phi) by angle addition, so that x + phi is never rounded
     cx, sx, cp, sp = math.cos(x), math.sin(x), math.cos(phi), math.sin(phi)

@@ -1,7 +1,6 @@
 """Oracle: direct type-3 nonuniform DFT (test infrastructure only).
 
-F(omega_k) = sum_j x_j exp(+i omega_k r_j), the operator F of Sec. 3.2
-(Eq. 3.6) evaluated by its definition, O(nm), in FP64.
+F(omega_k) = sum_j x_j exp(+i omega_k r_j), the matrix F of Sec. 3.2 evaluated by its definition, O(nm), in FP64.
 """
 import numpy as np
 

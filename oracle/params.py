@@ -14,10 +14,10 @@ Plain-Python restatement of Sec. 3.1-3.3 of the paper:
   The gamma case of the even bound is taken with strict inequality
   L+1 > nu/2 (equality would divide by zero).  Arguments outside Siegel's
   range (p >= 1) or beta+gamma >= 0 give an infinite bound.
-* B^asy_{nu,M}(z): Eq. (3.5), the first-neglected-terms remainder of the
+* B^asy_{nu,M}(z): Sec. 3.2, eq. asy-error, the first-neglected-terms remainder of the
   M-term Hankel expansion, with a_k(nu) = prod_{i=1..k}(4nu^2-(2i-1)^2)/(k! 8^k)
   (DLMF 10.17.1; the printed product is garbled).
-* M: the heuristic of Eq. (3.7).
+* M: the heuristic of Sec. 3.3 (eq. num-asy-terms).
 * z: the root of B^asy(z) = eps (Sec. 3.3; any accurate root finder gives the
   same value, Newton with a bisection safeguard is used here).
 * L: the smallest L with B^loc(z) < eps (Sec. 3.3).
@@ -72,14 +72,14 @@ def b_loc(nu, L, x):
 
 
 def b_asy(nu, M, z):
-    """Eq. (3.5): sqrt(2/pi) (|a_2M|/z^(2M+1/2) + |a_2M+1|/z^(2M+3/2))."""
+    """Sec. 3.2, eq. asy-error: sqrt(2/pi) (|a_2M|/z^(2M+1/2) + |a_2M+1|/z^(2M+3/2))."""
     return math.sqrt(2.0 / math.pi) * (
         abs(hankel_a(2 * M, nu)) / z ** (2 * M + 0.5)
         + abs(hankel_a(2 * M + 1, nu)) / z ** (2 * M + 1.5))
 
 
 def choose_m(nu, eps):
-    """Eq. (3.7): M = min(floor(1 + nu/5 - log10(eps)/4), 20)."""
+    """Sec. 3.3, eq. num-asy-terms: M = min(floor(1 + nu/5 - log10(eps)/4), 20)."""
     return min(int(math.floor(1.0 + abs(nu) / 5.0 - math.log10(eps) / 4.0)), 20)
 
 

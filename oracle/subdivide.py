@@ -1,6 +1,6 @@
 """Oracle: block subdivision of the Hankel matrix (test infrastructure only).
 
-Plain restatement of Sec. 4.1: SplitIndices (Eq. 4.1, with the quasi-optimal
+Plain restatement of Sec. 4.1: SplitIndices (eq. subdiv-optim, with the quasi-optimal
 candidate search the paper recommends) and Algorithm 1 (Subdivide).
 
 Indexing: rows are frequencies omega (sorted ascending, 0-based k), columns
@@ -9,7 +9,7 @@ inclusive.  An entry is local when omega_k * r_j <= z (products in FP64),
 asymptotic otherwise.
 
 Readings of the printed algorithm (see the design notes):
-* Eq. (4.1) writes argmax of the mixed area; the text says the chosen pair
+* eq. subdiv-optim writes argmax of the mixed area; the text says the chosen pair
   minimises it, which is what makes the fast blocks large.  The mixed area
   (k-k0+1)(j1-j) + (k1-k)(j-j0+1) is minimised.
 * For a candidate row k the column is j(k) = max{ j in [j0, j1] :
@@ -37,7 +37,7 @@ def _last_local_col(r, w, z, j0, j1):
 
 
 def split_indices(r, omega, z, blk, n_cand=16):
-    """Quasi-optimal (k, j) for a mixed block, Eq. (4.1)."""
+    """Quasi-optimal (k, j) for a mixed block (Sec. 4.1, eq. subdiv-optim)."""
     k0, k1, j0, j1 = blk
     nrows = k1 - k0 + 1
     if nrows <= n_cand:

@@ -1,0 +1,247 @@
+// Plan-time device kernels: input domain check, LSD radix sort of FP64 keys
+// with their original indices, and the execute-time gather / scatter between
+// user order and sorted order.
+//
+// The subdivision of Algorithm 1 and the complexity theorem of Sec. 4.2 take
+// the points and frequencies sorted ascending; the inputs are unsorted, so the
+// plan sorts them once and keeps the permutations.
+//
+// Keys are non-negative doubles (checked first), whose IEEE bit patterns
+// compare like unsigned integers, so an 8-pass, 8-bit LSD radix sort on the
+// raw 64-bit patterns sorts them.  Each pass: per-tile digit histogram,
+// one exclusive scan over (digit, tile), then a stable scatter in which each
+// CTA ranks its tile's elements round by round (warp match + per-warp
+// prefix counts), so equal keys keep their input order.
+#include <cstdint>
+
+#include "nuht_internal.h"
+
+namespace nuht {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                       // elements per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems; // 4096
+constexpr int kRadix = 256;
+
+__global__ void k_check_domain(const double* __restrict__ x, int64_t n, int* flag)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = x[i];
+        // rejects negatives, NaN and +-inf; -0.0 is accepted
+        if (!(v >= 0.0) || !(v <= 1.7976931348623157e308)) bad = 1;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// keys: bit patterns (with -0.0 folded onto +0.0), values: 0..n-1
+__global__ void k_sort_init(const double* __restrict__ in, int64_t n, uint64_t* __restrict__ keys,
+                            int32_t* __restrict__ vals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = in[i];
+        if (v == 0.0) v = 0.0;  // -0.0 -> +0.0
+        keys[i] = (uint64_t)__double_as_longlong(v);
+        vals[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int ntiles,
+                            uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int it = 0; it < kSortItems; ++it) {
+        int64_t i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    // digit-major layout: hist[d * ntiles + tile]
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// Single-CTA exclusive scan of len entries (in place): warp-shuffle scans
+// within each 1024-entry chunk, a carry between chunks.
+__global__ void k_sort_scan(uint32_t* __restrict__ a, int64_t len)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < len; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        uint32_t v = (i < len) ? a[i] : 0u;
+        uint32_t x = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += t;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t y = wsum[lane];
+            for (int off = 1; off < 32; off <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, y, off);
+                if (lane >= off) y += t;
+            }
+            wsum[lane] = y;   // inclusive prefix of warp totals
+        }
+        __syncthreads();
+        uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u);
+        if (i < len) a[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                               int64_t n, int shift, int ntiles,
+                               const uint32_t* __restrict__ offs, uint64_t* __restrict__ kout,
+                               int32_t* __restrict__ vout)
+{
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t base[kRadix];            // running position of each digit in this tile
+    __shared__ uint32_t wcnt[kWarps][kRadix];    // per-warp counts, then per-warp prefixes
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        base[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    for (int it = 0; it < kSortItems; ++it) {
+        int64_t i = tbase + it * kSortThreads + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        int32_t val = valid ? vin[i] : 0;
+        unsigned d = valid ? (unsigned)((key >> shift) & 0xFF) : 0x100u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned wrank = __popc(peers & lt);
+        bool leader = (peers & lt) == 0;
+        if (valid && leader) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // exclusive prefix over warps for each digit, advance the tile base
+        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) {
+            uint32_t run = base[dd];
+            for (int w = 0; w < kWarps; ++w) {
+                uint32_t t = wcnt[w][dd];
+                wcnt[w][dd] = run;
+                run += t;
+            }
+            base[dd] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wcnt[warp][d] + wrank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kWarps * kRadix; k += blockDim.x) (&wcnt[0][0])[k] = 0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_sort_finish(const uint64_t* __restrict__ keys, int64_t n, double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __longlong_as_double((long long)keys[i]);
+}
+
+__global__ void k_gather(const double* __restrict__ c, const int32_t* __restrict__ perm, int64_t n,
+                         int stride, int comp, double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = c[(int64_t)perm[i] * stride + comp];
+}
+
+__global__ void k_scatter(const double* __restrict__ gs, const int32_t* __restrict__ perm, int64_t m,
+                          int stride, int comp, double* __restrict__ g)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        g[(int64_t)perm[i] * stride + comp] = gs[i];
+}
+
+inline int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return b < 1 ? 1 : (int)b;
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+cudaError_t launch_check_domain(const double* x, int64_t n, int* flag, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_check_domain<<<grid_for(n, 256), 256, 0, s>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+size_t radix_sort_scratch_bytes(int64_t n)
+{
+    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    return 2 * align256(sizeof(uint64_t) * (size_t)n) + align256(sizeof(int32_t) * (size_t)n) +
+           align256(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ntiles > 0 ? ntiles : 1));
+}
+
+// Sorts in[0..n) ascending into out, perm[i] = input index of out[i].
+cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* perm, void* scratch,
+                           size_t scratch_bytes, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (scratch_bytes < radix_sort_scratch_bytes(n)) return cudaErrorInvalidValue;
+    int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    char* p = (char*)scratch;
+    uint64_t* k0 = (uint64_t*)p; p += align256(sizeof(uint64_t) * (size_t)n);
+    uint64_t* k1 = (uint64_t*)p; p += align256(sizeof(uint64_t) * (size_t)n);
+    int32_t* v1 = (int32_t*)p; p += align256(sizeof(int32_t) * (size_t)n);
+    uint32_t* hist = (uint32_t*)p;
+    int32_t* v0 = perm;   // ping-pong between perm and v1; 8 passes end in perm
+    k_sort_init<<<grid_for(n, 256), 256, 0, s>>>(in, n, k0, v0);
+    uint64_t* ka = k0; uint64_t* kb = k1;
+    int32_t* va = v0; int32_t* vb = v1;
+    for (int pass = 0; pass < 8; ++pass) {
+        int shift = 8 * pass;
+        k_sort_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist);
+        k_sort_scan<<<1, 1024, 0, s>>>(hist, (int64_t)kRadix * ntiles);
+        k_sort_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, n, shift, ntiles, hist, kb, vb);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        int32_t* tv = va; va = vb; vb = tv;
+    }
+    // after an even number of passes the data is back in (k0, perm)
+    k_sort_finish<<<grid_for(n, 256), 256, 0, s>>>(ka, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
+                          double* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
+                           double* g, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_scatter<<<grid_for(m, 256), 256, 0, s>>>(gs, perm, m, stride, comp, g);
+    return cudaGetLastError();
+}
+
+}  // namespace nuht

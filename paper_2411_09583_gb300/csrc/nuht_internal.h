@@ -1,0 +1,127 @@
+// Internal types of the GB300 NUHT library (host + device).
+//
+// A plan holds one or more problems (a batch).  Every block of the
+// subdivision (Algorithm 1) carries the index of its problem, so the same
+// kernels serve a single transform and a batch of uneven ones.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nuht.h"
+
+namespace nuht {
+
+constexpr int kMaxM = 20;           // Hankel term pairs (Sec. 3.3 caps M at 20)
+constexpr int kMaxQ = 2 * kMaxM;    // weight powers q = 0..2M-1
+constexpr int kMaxW = 16;           // ES kernel width
+constexpr int kMaxDeg = 20;         // degree of the kernel piece polynomials
+constexpr int kMaxNtop = 256;       // largest Bessel index kept by the local evaluation
+constexpr int kFftSmemMax = 4096;   // largest FFT done by one CTA in shared memory
+constexpr int kFftMaxLog2 = 24;     // largest FFT (two passes of <= 4096)
+
+// Per-problem constants.
+struct ProbParams {
+    int nu;        // |nu|
+    int sgn;       // (-1)^nu when the user order was negative, else +1
+    int M, L, Q;   // Q = 2M
+    int ntop;      // largest Bessel index used by the local evaluation
+    double z;      // crossover
+    double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
+    double a[kMaxQ];             // Hankel coefficients a_q(nu), q < Q
+    int64_t r_off, w_off;        // offsets of this problem in the sorted arrays
+    int64_t n, m;
+    int64_t c_off, g_off;        // offsets of this problem's c and g (batched)
+};
+
+// Local block: rows k0..k1 (omega), columns j0..j1 (r), absolute indices into
+// the concatenated sorted arrays.  R = largest r of the block.
+struct LocalBlock {
+    int32_t prob, k0, k1, j0, j1, pad;
+    double R;
+    int64_t mom_off;   // offset of the block's L+1 moments
+};
+
+// Asymptotic block: type-3 NUFFT geometry (centres, grid spacings, sizes).
+struct AsyBlock {
+    int32_t prob, k0, k1, j0, j1;
+    int32_t N1;        // spread grid cells l = -N1..N1
+    int32_t nf2;       // FFT size (power of two)
+    int32_t log2nf2;
+    int64_t b_off;     // complex offset of the spread grid  [2 N1 + 1][Q]
+    int64_t q_off;     // complex offset of the FFT output   [nf2][Q]
+    double rc, wc;     // centres of the r and omega ranges
+    double h;          // spread grid spacing in r: h = pi / (sigma S)
+    double inv_h;
+    double rho;        // smallest r of the block (weights are (r/rho)^(-q-1/2))
+    double alpha;      // w h / 2: outer deconvolution argument scale
+    double alpha2;     // w Delta / 2 with Delta = 2 pi / nf2
+    double inv_delta;  // nf2 / (2 pi)
+};
+
+struct DirectBlock {
+    int32_t prob, k0, k1, j0, j1, pad;
+};
+
+// A contiguous run of points (or frequencies) of one block.
+struct Tile {
+    int32_t blk;
+    int32_t count;
+    int64_t start;     // absolute index into the sorted array
+};
+
+// One line of a (batched) FFT: block, weight power q, line index (two-pass only).
+struct FftItem {
+    int32_t blk, q, line, pad;
+};
+
+// Kernel tables shared by every asymptotic block of a plan.
+struct Tables {
+    const double* es;      // [w][deg + 1] monomial coefficients in v = 2 z0 - 1
+    int w, deg;
+    double half_w;         // w / 2
+    const double* ph;      // psi-hat pieces [ph_pieces][ph_deg + 1] in v in [-1, 1]
+    int ph_pieces, ph_deg;
+    double ph_scale;       // pieces per unit of xi
+    double ph_xmax;        // table covers xi in [0, ph_xmax]
+    const double2* tw;     // e^{2 pi i k / 2^tw_log2}, k < 2^(tw_log2 - 1)
+    int tw_log2;
+};
+
+// ------------------------------------------------------------ device launches
+// (each returns cudaGetLastError() of its launch)
+cudaError_t launch_check_domain(const double* x, int64_t n, int* flag, cudaStream_t s);
+cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* perm,
+                           void* scratch, size_t scratch_bytes, cudaStream_t s);
+size_t radix_sort_scratch_bytes(int64_t n);
+
+cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
+                          double* out, cudaStream_t s);
+cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
+                           double* g, cudaStream_t s);
+
+cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                 int ntiles, int lmax, const double* r_s, const double* c_s,
+                                 double* mom, cudaStream_t s);
+int local_eval_threads(int ntop_max);
+cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                              int ntiles, int ntop_max, int threads, const double* w_s,
+                              const double* mom, double* g_s, cudaStream_t s);
+cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
+                          const double* r_s, const double* w_s, const double* c_s, double* g_s,
+                          cudaStream_t s);
+cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                              int ntiles, int qmax, Tables tab, const double* r_s,
+                              const double* c_s, double2* grid_b, cudaStream_t s);
+cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const FftItem* items,
+                                 int nitems, int max_nf2, Tables tab, const double2* grid_b,
+                                 double2* grid_q, cudaStream_t s);
+cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const FftItem* items_a,
+                                 int nitems_a, const FftItem* items_b, int nitems_b, Tables tab,
+                                 const double2* grid_b, double2* tmp, double2* grid_q,
+                                 cudaStream_t s);
+cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                              int ntiles, Tables tab, const double* w_s, const double2* grid_q,
+                              double* g_s, cudaStream_t s);
+
+}  // namespace nuht

@@ -1,0 +1,536 @@
+// C ABI of the NUHT library: plan (sort + subdivision + work lists), execute
+// (Algorithm 2 on the device), info and helpers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nuht_host.h"
+
+using namespace nuht;
+
+namespace {
+
+thread_local std::string g_cuda_msg = "no CUDA error";
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+#define NUHT_CK(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            g_cuda_msg = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+            return e_ == cudaErrorMemoryAllocation ? NUHT_ERR_NOMEM : NUHT_ERR_CUDA;    \
+        }                                                                               \
+    } while (0)
+
+// One device allocation carved into aligned pieces.
+struct Arena {
+    size_t size = 0;
+    template <class T>
+    size_t reserve(size_t count)
+    {
+        size_t off = size;
+        size += align256(sizeof(T) * (count > 0 ? count : 1));
+        return off;
+    }
+};
+
+}  // namespace
+
+struct nuht_plan_s {
+    int nu_user = 0;
+    double eps = 0.0;
+    nuht_opts opt{};
+    int64_t n = 0, m = 0;
+    cudaStream_t stream = nullptr;
+    ProbParams prob{};
+    int w = 0;
+
+    // device memory
+    char* dmem = nullptr;
+    size_t dbytes = 0;
+    ProbParams* d_prob = nullptr;
+    double *d_r = nullptr, *d_w = nullptr;
+    int32_t *d_pr = nullptr, *d_pw = nullptr;
+    LocalBlock* d_loc = nullptr;
+    Tile *d_tmom = nullptr, *d_teval = nullptr;
+    AsyBlock* d_asy = nullptr;
+    Tile *d_tspread = nullptr, *d_tinterp = nullptr;
+    FftItem *d_fsmall = nullptr, *d_fa = nullptr, *d_fb = nullptr;
+    DirectBlock* d_dir = nullptr;
+    double* d_mom = nullptr;
+    double2 *d_gb = nullptr, *d_gq = nullptr, *d_gtmp = nullptr;
+    double *d_cs = nullptr, *d_gs = nullptr;
+    double *d_es = nullptr, *d_ph = nullptr;
+    double2* d_tw = nullptr;
+
+    int n_loc = 0, n_tmom = 0, n_teval = 0;
+    int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
+    int n_dir = 0;
+    int64_t mom_len = 0, gb_len = 0, gq_len = 0;
+    int max_nf2_small = 0, max_dir_rows = 0, ntop_max = 0, eval_threads = 0;
+    bool has_large_fft = false;
+    Tables tab{};
+    std::vector<HBlock> hb[3];
+    int64_t direct_entries = 0, local_rc = 0, asy_rc = 0, fft_points = 0;
+};
+
+extern "C" {
+
+void nuht_default_opts(nuht_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = NUHT_PREC_FP64;
+    o->min_size = 1024;
+    o->n_split_cand = 16;
+    o->m_terms = 0;
+    o->class_mask = 7;
+}
+
+const char* nuht_strerror(int code)
+{
+    switch (code) {
+        case NUHT_OK: return "ok";
+        case NUHT_ERR_INVALID_ARG: return "invalid argument";
+        case NUHT_ERR_DOMAIN: return "r and omega must be finite and non-negative";
+        case NUHT_ERR_NOMEM: return "out of memory";
+        case NUHT_ERR_CUDA: return "CUDA error";
+        case NUHT_ERR_TIMEOUT: return "device wait timed out";
+        case NUHT_ERR_UNSUPPORTED: return "unsupported parameters";
+        default: return "unknown status";
+    }
+}
+
+const char* nuht_last_cuda_error(void) { return g_cuda_msg.c_str(); }
+
+int nuht_choose_params(int nu, double eps, int m_terms, int* M, double* z, int* L)
+{
+    if (!M || !z || !L) return NUHT_ERR_INVALID_ARG;
+    if (!(eps >= 1e-15 && eps <= 1e-1)) return NUHT_ERR_INVALID_ARG;
+    if (m_terms < 0 || m_terms > kMaxM) return NUHT_ERR_INVALID_ARG;
+    if (nu > 100 || nu < -100) return NUHT_ERR_UNSUPPORTED;
+    return choose_params(nu, eps, m_terms, M, z, L);
+}
+
+void nuht_destroy(nuht_plan_t p)
+{
+    if (!p) return;
+    if (p->dmem) {
+        cudaFreeAsync(p->dmem, p->stream);
+        cudaStreamSynchronize(p->stream);
+    }
+    delete p;
+}
+
+static int build_plan(nuht_plan_t P, const double* r, const double* omega)
+{
+    cudaStream_t s = P->stream;
+    const int64_t n = P->n, m = P->m;
+    ProbParams& pp = P->prob;
+
+    // ---- sort (device) -------------------------------------------------
+    Arena sa;
+    size_t o_r = sa.reserve<double>(n), o_w = sa.reserve<double>(m);
+    size_t o_pr = sa.reserve<int32_t>(n), o_pw = sa.reserve<int32_t>(m);
+    size_t o_flag = sa.reserve<int>(2);
+    size_t o_scr = sa.size;
+    size_t scr = radix_sort_scratch_bytes(n > m ? n : m);
+    sa.size += align256(scr);
+    char* sort_mem = nullptr;
+    NUHT_CK(cudaMallocAsync((void**)&sort_mem, sa.size, s));
+    struct Free {
+        char* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } free_sort{sort_mem, s};
+    int* d_flag = (int*)(sort_mem + o_flag);
+    NUHT_CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * 2, s));
+    NUHT_CK(launch_check_domain(r, n, d_flag, s));
+    NUHT_CK(launch_check_domain(omega, m, d_flag + 1, s));
+    double* r_s = (double*)(sort_mem + o_r);
+    double* w_s = (double*)(sort_mem + o_w);
+    int32_t* pr = (int32_t*)(sort_mem + o_pr);
+    int32_t* pw = (int32_t*)(sort_mem + o_pw);
+    NUHT_CK(radix_sort_f64(r, n, r_s, pr, sort_mem + o_scr, scr, s));
+    NUHT_CK(radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr, scr, s));
+    std::vector<double> hr((size_t)n), hw((size_t)m);
+    int hflag[2] = {0, 0};
+    NUHT_CK(cudaMemcpyAsync(hflag, d_flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+    if (n) NUHT_CK(cudaMemcpyAsync(hr.data(), r_s, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (m) NUHT_CK(cudaMemcpyAsync(hw.data(), w_s, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    NUHT_CK(cudaStreamSynchronize(s));
+    if (hflag[0] || hflag[1]) return NUHT_ERR_DOMAIN;
+
+    // ---- subdivision (host, Algorithm 1) --------------------------------
+    subdivide(hr.data(), n, hw.data(), m, pp.z, P->opt.min_size, P->opt.n_split_cand, P->hb[0],
+              P->hb[1], P->hb[2]);
+    const auto& LB = P->hb[0];
+    const auto& AB = P->hb[1];
+    const auto& DB = P->hb[2];
+
+    // ---- per-block work lists --------------------------------------------
+    const HostTables& T = kernel_tables(P->w);
+    std::vector<LocalBlock> vloc;
+    std::vector<Tile> vtmom, vteval;
+    std::vector<AsyBlock> vasy;
+    std::vector<Tile> vtspread, vtinterp;
+    std::vector<FftItem> vfs, vfa, vfb;
+    std::vector<DirectBlock> vdir;
+    const int Q = pp.Q;
+    P->ntop_max = pp.ntop;
+    P->eval_threads = local_eval_threads(P->ntop_max);
+    int64_t mom_off = 0;
+    for (size_t b = 0; b < LB.size(); ++b) {
+        const HBlock& h = LB[b];
+        LocalBlock lb{};
+        lb.prob = 0;
+        lb.k0 = (int32_t)h.k0; lb.k1 = (int32_t)h.k1; lb.j0 = (int32_t)h.j0; lb.j1 = (int32_t)h.j1;
+        lb.R = hr[(size_t)h.j1];
+        lb.mom_off = mom_off;
+        mom_off += pp.L + 1;
+        vloc.push_back(lb);
+        for (int64_t j = h.j0; j <= h.j1; j += kMomentTile) {
+            int64_t c = h.j1 - j + 1;
+            vtmom.push_back(Tile{(int32_t)b, (int32_t)(c < kMomentTile ? c : kMomentTile), j});
+        }
+        for (int64_t k = h.k0; k <= h.k1; k += P->eval_threads) {
+            int64_t c = h.k1 - k + 1;
+            vteval.push_back(Tile{(int32_t)b, (int32_t)(c < P->eval_threads ? c : P->eval_threads), k});
+        }
+        P->local_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
+    }
+    P->mom_len = mom_off;
+    const int sp_tile = spread_tile_points(Q);
+    int64_t gb_off = 0, gq_off = 0;
+    for (size_t b = 0; b < AB.size(); ++b) {
+        const HBlock& h = AB[b];
+        AsyBlock ab{};
+        ab.prob = 0;
+        ab.k0 = (int32_t)h.k0; ab.k1 = (int32_t)h.k1; ab.j0 = (int32_t)h.j0; ab.j1 = (int32_t)h.j1;
+        const double rlo = hr[(size_t)h.j0], rhi = hr[(size_t)h.j1];
+        const double wlo = hw[(size_t)h.k0], whi = hw[(size_t)h.k1];
+        ab.rc = 0.5 * (rlo + rhi);
+        const double X = 0.5 * (rhi - rlo);
+        ab.wc = 0.5 * (wlo + whi);
+        const double S = 0.5 * (whi - wlo);
+        const double Seff = S > 0.0 ? S : 1.0;
+        ab.h = M_PI / (2.0 * Seff);
+        ab.inv_h = 1.0 / ab.h;
+        const double n1f = std::ceil(X / ab.h + 0.5 * P->w) + 1.0;   // one cell of rounding margin
+        if (n1f > (double)(1 << 22)) return NUHT_ERR_UNSUPPORTED;
+        ab.N1 = (int32_t)n1f;
+        const int64_t nf1 = 2 * (int64_t)ab.N1 + 1;
+        int lg = 5;
+        while (((int64_t)1 << lg) < 2 * nf1) ++lg;
+        if (lg > kFftMaxLog2) return NUHT_ERR_UNSUPPORTED;
+        ab.log2nf2 = lg;
+        ab.nf2 = 1 << lg;
+        ab.rho = rlo;
+        ab.alpha = 0.5 * P->w * ab.h;
+        ab.alpha2 = P->w * M_PI / ab.nf2;
+        ab.inv_delta = ab.nf2 / (2.0 * M_PI);
+        ab.b_off = gb_off;
+        gb_off += nf1 * Q;
+        ab.q_off = gq_off;
+        gq_off += (int64_t)ab.nf2 * Q;
+        vasy.push_back(ab);
+        for (int64_t j = h.j0; j <= h.j1; j += sp_tile) {
+            int64_t c = h.j1 - j + 1;
+            vtspread.push_back(Tile{(int32_t)b, (int32_t)(c < sp_tile ? c : sp_tile), j});
+        }
+        for (int64_t k = h.k0; k <= h.k1; k += kInterpTile) {
+            int64_t c = h.k1 - k + 1;
+            vtinterp.push_back(Tile{(int32_t)b, (int32_t)(c < kInterpTile ? c : kInterpTile), k});
+        }
+        if (ab.nf2 <= kFftSmemMax) {
+            if (ab.nf2 > P->max_nf2_small) P->max_nf2_small = ab.nf2;
+            for (int q = 0; q < Q; ++q) vfs.push_back(FftItem{(int32_t)b, q, 0, 0});
+        } else {
+            P->has_large_fft = true;
+            const int n1 = ab.nf2 / kFftSmemMax;
+            for (int q = 0; q < Q; ++q) {
+                for (int l = 0; l < n1; ++l) vfa.push_back(FftItem{(int32_t)b, q, l, 0});
+                for (int l = 0; l < kFftSmemMax; ++l) vfb.push_back(FftItem{(int32_t)b, q, l, 0});
+            }
+        }
+        P->asy_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
+        P->fft_points += ab.nf2;
+    }
+    P->gb_len = gb_off;
+    P->gq_len = gq_off;
+    for (size_t b = 0; b < DB.size(); ++b) {
+        const HBlock& h = DB[b];
+        DirectBlock db{0, (int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, 0};
+        vdir.push_back(db);
+        const int rows = (int)(h.k1 - h.k0 + 1);
+        if (rows > P->max_dir_rows) P->max_dir_rows = rows;
+        P->direct_entries += (h.k1 - h.k0 + 1) * (h.j1 - h.j0 + 1);
+    }
+    P->n_loc = (int)vloc.size(); P->n_tmom = (int)vtmom.size(); P->n_teval = (int)vteval.size();
+    P->n_asy = (int)vasy.size(); P->n_tspread = (int)vtspread.size(); P->n_tinterp = (int)vtinterp.size();
+    P->n_fsmall = (int)vfs.size(); P->n_fa = (int)vfa.size(); P->n_fb = (int)vfb.size();
+    P->n_dir = (int)vdir.size();
+
+    // ---- one device arena for everything the plan keeps -------------------
+    Arena A;
+    size_t a_prob = A.reserve<ProbParams>(1);
+    size_t a_r = A.reserve<double>(n), a_w = A.reserve<double>(m);
+    size_t a_pr = A.reserve<int32_t>(n), a_pw = A.reserve<int32_t>(m);
+    size_t a_loc = A.reserve<LocalBlock>(vloc.size());
+    size_t a_tmom = A.reserve<Tile>(vtmom.size()), a_teval = A.reserve<Tile>(vteval.size());
+    size_t a_asy = A.reserve<AsyBlock>(vasy.size());
+    size_t a_tsp = A.reserve<Tile>(vtspread.size()), a_tin = A.reserve<Tile>(vtinterp.size());
+    size_t a_fs = A.reserve<FftItem>(vfs.size()), a_fa = A.reserve<FftItem>(vfa.size());
+    size_t a_fb = A.reserve<FftItem>(vfb.size());
+    size_t a_dir = A.reserve<DirectBlock>(vdir.size());
+    size_t a_es = A.reserve<double>(T.es.size()), a_ph = A.reserve<double>(T.ph.size());
+    size_t a_tw = A.reserve<double2>(T.tw.size());
+    size_t host_part = A.size;   // everything above is uploaded from one staging buffer
+    size_t a_mom = A.reserve<double>((size_t)P->mom_len);
+    size_t a_gb = A.reserve<double2>((size_t)P->gb_len);
+    size_t a_gq = A.reserve<double2>((size_t)P->gq_len);
+    size_t a_gt = A.reserve<double2>(P->has_large_fft ? (size_t)P->gq_len : 1);
+    size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
+    NUHT_CK(cudaMallocAsync((void**)&P->dmem, A.size, s));
+    P->dbytes = A.size;
+    char* D = P->dmem;
+    std::vector<char> stage(host_part, 0);
+    auto put = [&](size_t off, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(stage.data() + off, src, bytes);
+    };
+    put(a_prob, &pp, sizeof(pp));
+    put(a_loc, vloc.data(), sizeof(LocalBlock) * vloc.size());
+    put(a_tmom, vtmom.data(), sizeof(Tile) * vtmom.size());
+    put(a_teval, vteval.data(), sizeof(Tile) * vteval.size());
+    put(a_asy, vasy.data(), sizeof(AsyBlock) * vasy.size());
+    put(a_tsp, vtspread.data(), sizeof(Tile) * vtspread.size());
+    put(a_tin, vtinterp.data(), sizeof(Tile) * vtinterp.size());
+    put(a_fs, vfs.data(), sizeof(FftItem) * vfs.size());
+    put(a_fa, vfa.data(), sizeof(FftItem) * vfa.size());
+    put(a_fb, vfb.data(), sizeof(FftItem) * vfb.size());
+    put(a_dir, vdir.data(), sizeof(DirectBlock) * vdir.size());
+    put(a_es, T.es.data(), sizeof(double) * T.es.size());
+    put(a_ph, T.ph.data(), sizeof(double) * T.ph.size());
+    put(a_tw, T.tw.data(), sizeof(double2) * T.tw.size());
+    NUHT_CK(cudaMemcpyAsync(D, stage.data(), host_part, cudaMemcpyHostToDevice, s));
+    // sorted arrays and permutations stay on the device
+    P->d_r = (double*)(D + a_r); P->d_w = (double*)(D + a_w);
+    P->d_pr = (int32_t*)(D + a_pr); P->d_pw = (int32_t*)(D + a_pw);
+    if (n) {
+        NUHT_CK(cudaMemcpyAsync(P->d_r, r_s, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        NUHT_CK(cudaMemcpyAsync(P->d_pr, pr, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    if (m) {
+        NUHT_CK(cudaMemcpyAsync(P->d_w, w_s, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        NUHT_CK(cudaMemcpyAsync(P->d_pw, pw, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+    }
+    P->d_prob = (ProbParams*)(D + a_prob);
+    P->d_loc = (LocalBlock*)(D + a_loc);
+    P->d_tmom = (Tile*)(D + a_tmom); P->d_teval = (Tile*)(D + a_teval);
+    P->d_asy = (AsyBlock*)(D + a_asy);
+    P->d_tspread = (Tile*)(D + a_tsp); P->d_tinterp = (Tile*)(D + a_tin);
+    P->d_fsmall = (FftItem*)(D + a_fs); P->d_fa = (FftItem*)(D + a_fa); P->d_fb = (FftItem*)(D + a_fb);
+    P->d_dir = (DirectBlock*)(D + a_dir);
+    P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
+    P->d_mom = (double*)(D + a_mom);
+    P->d_gb = (double2*)(D + a_gb); P->d_gq = (double2*)(D + a_gq); P->d_gtmp = (double2*)(D + a_gt);
+    P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
+    Tables& tb = P->tab;
+    tb.es = P->d_es; tb.w = T.w; tb.deg = T.deg; tb.half_w = 0.5 * T.w;
+    tb.ph = P->d_ph; tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
+    tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
+    tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
+    // the staging buffer must outlive the copy
+    NUHT_CK(cudaStreamSynchronize(s));
+    return NUHT_OK;
+}
+
+int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double* omega, int64_t m,
+              double eps, const nuht_opts* opt, void* stream)
+{
+    if (!out) return NUHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || m < 0 || n > 0x7fffffffLL || m > 0x7fffffffLL) return NUHT_ERR_INVALID_ARG;
+    if (!(eps >= 1e-15 && eps <= 1e-1)) return NUHT_ERR_INVALID_ARG;
+    if ((n > 0 && !r) || (m > 0 && !omega)) return NUHT_ERR_INVALID_ARG;
+    if (nu > 100 || nu < -100) return NUHT_ERR_UNSUPPORTED;
+    nuht_opts o;
+    nuht_default_opts(&o);
+    if (opt) o = *opt;
+    if (o.min_size < 1 || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
+        (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
+        return NUHT_ERR_INVALID_ARG;
+    for (int i = 0; i < 7; ++i)
+        if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
+    nuht_plan_t P = new (std::nothrow) nuht_plan_s();
+    if (!P) return NUHT_ERR_NOMEM;
+    P->nu_user = nu;
+    P->eps = eps;
+    P->opt = o;
+    P->n = n;
+    P->m = m;
+    P->stream = (cudaStream_t)stream;
+    const int anu = nu < 0 ? -nu : nu;
+    ProbParams& pp = P->prob;
+    pp.nu = anu;
+    pp.sgn = (nu < 0 && (anu & 1)) ? -1 : 1;
+    int rc = choose_params(anu, eps, o.m_terms, &pp.M, &pp.z, &pp.L);
+    if (rc != NUHT_OK) { delete P; return rc; }
+    pp.Q = 2 * pp.M;
+    const int hp = (anu & 1) ? (anu + 1) / 2 : anu / 2;
+    pp.ntop = hp + pp.L;
+    if (pp.ntop >= kMaxNtop) { delete P; return NUHT_ERR_UNSUPPORTED; }
+    const double phi = -(2.0 * anu + 1.0) * M_PI / 4.0;
+    pp.cphi = std::cos(phi);
+    pp.sphi = std::sin(phi);
+    for (int q = 0; q < kMaxQ; ++q) pp.a[q] = q < pp.Q ? hankel_coeff(q, anu) : 0.0;
+    pp.r_off = 0; pp.w_off = 0; pp.n = n; pp.m = m; pp.c_off = 0; pp.g_off = 0;
+    P->w = nufft_width(eps);
+    rc = build_plan(P, r, omega);
+    if (rc != NUHT_OK) { nuht_destroy(P); return rc; }
+    *out = P;
+    return NUHT_OK;
+}
+
+static int apply_forward(nuht_plan_t P, cudaStream_t s)
+{
+    const int mask = P->opt.class_mask;
+    NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * (P->m > 0 ? P->m : 1), s));
+    if ((mask & 1) && P->n_loc) {
+        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
+        NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->prob.L, P->d_r,
+                                     P->d_cs, P->d_mom, s));
+    }
+    if ((mask & 2) && P->n_asy) {
+        NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
+        NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->prob.Q, P->tab,
+                                  P->d_r, P->d_cs, P->d_gb, s));
+        NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small,
+                                     P->tab, P->d_gb, P->d_gq, s));
+        if (P->has_large_fft)
+            NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
+                                         P->d_gb, P->d_gtmp, P->d_gq, s));
+        NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->tab, P->d_w,
+                                  P->d_gq, P->d_gs, s));
+    }
+    if ((mask & 1) && P->n_loc)
+        NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
+                                  P->eval_threads, P->d_w, P->d_mom, P->d_gs, s));
+    if ((mask & 4) && P->n_dir)
+        NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->d_r, P->d_w, P->d_cs,
+                              P->d_gs, s));
+    return NUHT_OK;
+}
+
+int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_complex, void* stream)
+{
+    if (!P || nvec < 1) return NUHT_ERR_INVALID_ARG;
+    if ((P->n > 0 && !c) || (P->m > 0 && !g)) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int comps = nvec * (is_complex ? 2 : 1);
+    if (P->m == 0) return NUHT_OK;
+    if (P->n == 0) {
+        NUHT_CK(cudaMemsetAsync(g, 0, sizeof(double) * P->m * comps, s));
+        return NUHT_OK;
+    }
+    for (int comp = 0; comp < comps; ++comp) {
+        NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, s));
+        int rc = apply_forward(P, s);
+        if (rc != NUHT_OK) return rc;
+        NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, g, s));
+    }
+    return NUHT_OK;
+}
+
+int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_complex, void* stream)
+{
+    (void)P; (void)g; (void)c; (void)nvec; (void)is_complex; (void)stream;
+    return NUHT_ERR_UNSUPPORTED;
+}
+
+int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega, int64_t m, double eps,
+                        const double* c, double* g, int nvec, const nuht_opts* opt, void* stream)
+{
+    if (n < 0 || m < 0 || nvec < 1) return NUHT_ERR_INVALID_ARG;
+    if ((n > 0 && (!r || !c)) || (m > 0 && (!omega || !g))) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Arena A;
+    size_t o_r = A.reserve<double>(n), o_w = A.reserve<double>(m);
+    size_t o_c = A.reserve<double>((size_t)n * nvec), o_g = A.reserve<double>((size_t)m * nvec);
+    char* D = nullptr;
+    NUHT_CK(cudaMallocAsync((void**)&D, A.size, s));
+    int rc = NUHT_OK;
+    nuht_plan_t P = nullptr;
+    do {
+        cudaError_t e = cudaSuccess;
+        if (n) e = cudaMemcpyAsync(D + o_r, r, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && m) e = cudaMemcpyAsync(D + o_w, omega, sizeof(double) * m, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(D + o_c, c, sizeof(double) * n * nvec, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { g_cuda_msg = cudaGetErrorString(e); rc = NUHT_ERR_CUDA; break; }
+        rc = nuht_plan(&P, nu, (const double*)(D + o_r), n, (const double*)(D + o_w), m, eps, opt, stream);
+        if (rc != NUHT_OK) break;
+        rc = nuht_execute(P, (const double*)(D + o_c), (double*)(D + o_g), nvec, 0, stream);
+        if (rc != NUHT_OK) break;
+        if (m) e = cudaMemcpyAsync(g, D + o_g, sizeof(double) * m * nvec, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { g_cuda_msg = cudaGetErrorString(e); rc = NUHT_ERR_CUDA; break; }
+    } while (0);
+    nuht_destroy(P);
+    cudaFreeAsync(D, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+int nuht_info(nuht_plan_t P, nuht_plan_info* out)
+{
+    if (!P || !out) return NUHT_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->nu = P->nu_user;
+    out->M = P->prob.M;
+    out->L = P->prob.L;
+    out->nufft_width = P->w;
+    out->z = P->prob.z;
+    out->eps = P->eps;
+    out->n = P->n;
+    out->m = P->m;
+    out->n_local = (int64_t)P->hb[0].size();
+    out->n_asy = (int64_t)P->hb[1].size();
+    out->n_direct = (int64_t)P->hb[2].size();
+    out->direct_entries = P->direct_entries;
+    out->local_rows_cols = P->local_rc;
+    out->asy_rows_cols = P->asy_rc;
+    out->fft_points = P->fft_points;
+    out->device_bytes = (int64_t)P->dbytes;
+    return NUHT_OK;
+}
+
+int nuht_get_blocks(nuht_plan_t P, int cls, int64_t* ranges, int64_t cap, int64_t* count)
+{
+    if (!P || cls < 0 || cls > 2 || !count || cap < 0 || (cap > 0 && !ranges)) return NUHT_ERR_INVALID_ARG;
+    const auto& v = P->hb[cls];
+    *count = (int64_t)v.size();
+    const int64_t nc = cap < *count ? cap : *count;
+    for (int64_t i = 0; i < nc; ++i) {
+        ranges[4 * i + 0] = v[(size_t)i].k0;
+        ranges[4 * i + 1] = v[(size_t)i].k1;
+        ranges[4 * i + 2] = v[(size_t)i].j0;
+        ranges[4 * i + 3] = v[(size_t)i].j1;
+    }
+    return NUHT_OK;
+}
+
+int nuht_get_permutations(nuht_plan_t P, int32_t* perm_r, int32_t* perm_omega)
+{
+    if (!P) return NUHT_ERR_INVALID_ARG;
+    if (perm_r && P->n)
+        NUHT_CK(cudaMemcpyAsync(perm_r, P->d_pr, sizeof(int32_t) * P->n, cudaMemcpyDeviceToHost, P->stream));
+    if (perm_omega && P->m)
+        NUHT_CK(cudaMemcpyAsync(perm_omega, P->d_pw, sizeof(int32_t) * P->m, cudaMemcpyDeviceToHost, P->stream));
+    NUHT_CK(cudaStreamSynchronize(P->stream));
+    return NUHT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// Algorithm 1 (Subdivide) with the quasi-optimal SplitIndices of Sec. 4.1.
+//
+// Rows are the sorted frequencies omega (index k), columns the sorted points r
+// (index j).  An entry is local when omega_k * r_j <= z (FP64 product).
+// Readings of the printed algorithm:
+//  * the split minimises the mixed (off-diagonal) area (k-k0+1)(j1-j) +
+//    (k1-k)(j-j0+1) over the candidate rows (the display writes argmax, the
+//    text minimises); for a row k the column is the last local one,
+//    j(k) = max{j : omega_k r_j <= z} (j0-1 if none), which makes the
+//    lower-right block purely asymptotic;
+//  * candidates: every row if the block has at most n_cand rows, else
+//    k0 + floor(c (k1-k0)/(n_cand-1)), c = 0..n_cand-1; ties keep the first;
+//  * the off-diagonal blocks' areas are (rows) x (cols) of each block (the
+//    printed size tests swap index names); a mixed block with area <=
+//    min_size is summed directly;
+//  * blocks that are entirely local (or asymptotic) go to the local (or
+//    asymptotic) list whatever their size; empty blocks are dropped;
+//  * the work list is first-in first-out.
+#include <deque>
+
+#include "nuht_host.h"
+
+namespace nuht {
+
+namespace {
+
+int64_t last_local_col(const double* r, double w, double z, int64_t j0, int64_t j1)
+{
+    int64_t lo = j0, hi = j1 + 1;   // first j with w r_j > z
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (w * r[mid] <= z) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+}  // namespace
+
+void subdivide(const double* r, int64_t n, const double* w, int64_t m, double z, int64_t min_size,
+               int n_cand, std::vector<HBlock>& loc, std::vector<HBlock>& asy,
+               std::vector<HBlock>& dir)
+{
+    loc.clear();
+    asy.clear();
+    dir.clear();
+    if (n <= 0 || m <= 0) return;
+    std::deque<HBlock> work;
+    auto place = [&](int64_t k0, int64_t k1, int64_t j0, int64_t j1) {
+        if (k1 < k0 || j1 < j0) return;
+        const HBlock b{k0, k1, j0, j1};
+        if (w[k1] * r[j1] <= z) { loc.push_back(b); return; }
+        if (w[k0] * r[j0] > z) { asy.push_back(b); return; }
+        if ((k1 - k0 + 1) * (j1 - j0 + 1) <= min_size) { dir.push_back(b); return; }
+        work.push_back(b);
+    };
+    place(0, m - 1, 0, n - 1);
+    while (!work.empty()) {
+        const HBlock b = work.front();
+        work.pop_front();
+        const int64_t rows = b.k1 - b.k0 + 1;
+        int64_t best_area = -1, bk = b.k0, bj = b.j0 - 1;
+        const int64_t ncand = rows <= n_cand ? rows : n_cand;
+        for (int64_t c = 0; c < ncand; ++c) {
+            const int64_t k = rows <= n_cand ? b.k0 + c : b.k0 + (c * (b.k1 - b.k0)) / (n_cand - 1);
+            const int64_t j = last_local_col(r, w[k], z, b.j0, b.j1);
+            const int64_t area = (k - b.k0 + 1) * (b.j1 - j) + (b.k1 - k) * (j - b.j0 + 1);
+            if (best_area < 0 || area < best_area) {
+                best_area = area;
+                bk = k;
+                bj = j;
+            }
+        }
+        place(b.k0, bk, b.j0, bj);             // upper left: local
+        place(bk + 1, b.k1, bj + 1, b.j1);     // lower right: asymptotic
+        place(b.k0, bk, bj + 1, b.j1);         // upper right: mixed
+        place(bk + 1, b.k1, b.j0, bj);         // lower left: mixed
+    }
+}
+
+}  // namespace nuht

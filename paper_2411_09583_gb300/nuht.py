@@ -1,0 +1,159 @@
+"""Python binding of the GB300 NUHT library (argument marshalling only).
+
+    g_k = sum_j c_j J_nu(omega_k r_j)      (the discrete Hankel transform, Sec. 1)
+
+Every step of the transform runs in libnuht.so (CUDA, sm_103a); this module
+only checks tensors, passes device pointers and the current CUDA stream, and
+wraps status codes.  PyTorch provides device memory and streams.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(x, name):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not x.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if x.dtype not in (torch.float64, torch.complex128):
+        raise TypeError("%s must be float64 or complex128, got %s" % (name, x.dtype))
+    return x.contiguous()
+
+
+def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class_mask=7):
+    o = N.NuhtOpts()
+    N.lib().nuht_default_opts(ctypes.byref(o))
+    o.precision = {"fp64": N.PREC_FP64, "mixed": N.PREC_MIXED}[precision]
+    o.min_size = int(min_size)
+    o.n_split_cand = int(n_split_cand)
+    o.m_terms = int(m_terms)
+    o.class_mask = int(class_mask)
+    return o
+
+
+def choose_params(nu, eps, m_terms=0):
+    """(M, z, L) of Sec. 3.3 as chosen by the library (host computation)."""
+    M, z, L = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    N.check(N.lib().nuht_choose_params(int(nu), float(eps), int(m_terms), ctypes.byref(M),
+                                       ctypes.byref(z), ctypes.byref(L)), "nuht_choose_params")
+    return M.value, z.value, L.value
+
+
+class Plan:
+    """A plan for order nu, points r (n,) and frequencies omega (m,), tolerance eps.
+
+    r and omega are float64 CUDA tensors (any order, values >= 0).
+    """
+
+    def __init__(self, nu, r, omega, eps, stream=None, **opts):
+        r = _dev_f64(r, "r")
+        omega = _dev_f64(omega, "omega")
+        if r.dtype != torch.float64 or omega.dtype != torch.float64:
+            raise TypeError("r and omega must be float64")
+        self.n, self.m = r.numel(), omega.numel()
+        self.device = r.device
+        self._opts = make_opts(**opts)
+        self._h = ctypes.c_void_p()
+        self._stream = stream
+        with torch.cuda.device(self.device):
+            N.check(N.lib().nuht_plan(ctypes.byref(self._h), int(nu), ctypes.c_void_p(r.data_ptr()),
+                                      self.n, ctypes.c_void_p(omega.data_ptr()), self.m,
+                                      float(eps), ctypes.byref(self._opts),
+                                      _stream_ptr(stream)), "nuht_plan")
+
+    def _apply(self, fn, x, rows_in, rows_out, out, what):
+        x = _dev_f64(x, "input")
+        if x.shape[0] != rows_in:
+            raise ValueError("%s: input must have %d rows, got %d" % (what, rows_in, x.shape[0]))
+        is_c = x.dtype == torch.complex128
+        nvec = 1 if x.dim() == 1 else int(np.prod(x.shape[1:]))
+        shape = (rows_out,) + tuple(x.shape[1:])
+        if out is None:
+            out = torch.empty(shape, dtype=x.dtype, device=x.device)
+        elif out.shape != shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise ValueError("%s: bad output tensor" % what)
+        xin = torch.view_as_real(x) if is_c else x
+        xo = torch.view_as_real(out) if is_c else out
+        with torch.cuda.device(self.device):
+            N.check(fn(self._h, ctypes.c_void_p(xin.data_ptr()), ctypes.c_void_p(xo.data_ptr()),
+                       nvec, 1 if is_c else 0, _stream_ptr(self._stream)), what)
+        return out
+
+    def execute(self, c, out=None):
+        """g = A c; c has n rows (float64 or complex128), g has m rows."""
+        return self._apply(N.lib().nuht_execute, c, self.n, self.m, out, "nuht_execute")
+
+    def adjoint(self, g, out=None):
+        """c = A^T g; g has m rows, c has n rows."""
+        return self._apply(N.lib().nuht_adjoint, g, self.m, self.n, out, "nuht_adjoint")
+
+    def info(self):
+        inf = N.NuhtPlanInfo()
+        N.check(N.lib().nuht_info(self._h, ctypes.byref(inf)), "nuht_info")
+        return {f: getattr(inf, f) for f, _ in N.NuhtPlanInfo._fields_}
+
+    def blocks(self, cls):
+        """(count, 4) int64 array of (k0, k1, j0, j1) for block class cls (0 local, 1 asy, 2 direct)."""
+        cnt = ctypes.c_int64()
+        N.check(N.lib().nuht_get_blocks(self._h, int(cls), None, 0, ctypes.byref(cnt)), "nuht_get_blocks")
+        out = np.zeros((cnt.value, 4), dtype=np.int64)
+        if cnt.value:
+            N.check(N.lib().nuht_get_blocks(self._h, int(cls), out.ctypes.data_as(ctypes.c_void_p),
+                                            cnt.value, ctypes.byref(cnt)), "nuht_get_blocks")
+        return out
+
+    def permutations(self):
+        pr = np.zeros(self.n, dtype=np.int32)
+        pw = np.zeros(self.m, dtype=np.int32)
+        N.check(N.lib().nuht_get_permutations(self._h, pr.ctypes.data_as(ctypes.c_void_p),
+                                              pw.ctypes.data_as(ctypes.c_void_p)),
+                "nuht_get_permutations")
+        return pr, pw
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            N.lib().nuht_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def nuht(nu, r, omega, c, eps, **opts):
+    """One-shot transform on device tensors: plan, execute, release."""
+    with Plan(nu, r, omega, eps, **opts) as p:
+        return p.execute(c)
+
+
+def transform_host(nu, r, omega, c, eps, stream=None, **opts):
+    """Whole transform from host arrays through nuht_transform_host (real c)."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    nvec = 1 if c.ndim == 1 else int(np.prod(c.shape[1:]))
+    g = np.empty((omega.size,) + c.shape[1:], dtype=np.float64)
+    o = make_opts(**opts)
+    N.check(N.lib().nuht_transform_host(int(nu), r.ctypes.data_as(ctypes.c_void_p), r.size,
+                                        omega.ctypes.data_as(ctypes.c_void_p), omega.size,
+                                        float(eps), c.ctypes.data_as(ctypes.c_void_p),
+                                        g.ctypes.data_as(ctypes.c_void_p), nvec, ctypes.byref(o),
+                                        _stream_ptr(stream)), "nuht_transform_host")
+    return g

@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA NUHT against the oracle's direct sum.
+
+Bar: max_k |g_k - g_k^oracle| <= 10 eps ||c||_1 (the accuracy contract), on
+seeded synthetic inputs shaped like the paper's experiments.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import subdivide as OS
+from paper_2411_09583_gb300.workloads import (exponential_grid, loguniform_problem, sample_rows,
+                                              uniform_problem)
+
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import class_reference, dev, run_forward, to_dev, tol  # noqa: E402
+
+
+def _check(nu, r, omega, c, eps, **opts):
+    g, info, blocks = run_forward(nu, r, omega, c, eps, **opts)
+    ref = oracle.direct(nu, r, omega, c)
+    err = np.max(np.abs(g - ref), axis=0) if g.size else 0.0
+    assert np.all(err <= tol(eps, c)), (err, tol(eps, c), info)
+    return g, info, blocks, err
+
+
+def test_small_uniform_config():
+    # n = m = 2000, nu = 0, eps = 1e-8, r ~ U[0,1], omega ~ U[0,2000] (seed 1)
+    r, omega, c = uniform_problem(2000, 2000, omega_max=2000.0, seed=1)
+    g, info, blocks, err = _check(0, r, omega, c, 1e-8)
+    assert info["n_local"] > 0 and info["n_asy"] > 0 and info["n_direct"] > 0
+    # far inside the contract in practice
+    assert err <= 1e-2 * tol(1e-8, c)
+
+
+@pytest.mark.parametrize("cls", [0, 1, 2])
+def test_each_block_class_alone(cls):
+    r, omega, c = uniform_problem(1500, 1700, omega_max=3000.0, seed=21)
+    eps = 1e-10
+    g, info, blocks = run_forward(0, r, omega, c, eps, class_mask=1 << cls)
+    ref = class_reference(0, r, omega, c, blocks[cls])
+    assert np.max(np.abs(g - ref)) <= tol(eps, c)
+
+
+@pytest.mark.parametrize("nu", [0, 1, 2, 3, 4, 7, 10, 15, 20])
+def test_orders(nu):
+    r, omega, c = uniform_problem(1300, 1100, omega_max=1500.0 + 40 * nu, seed=100 + nu)
+    _check(nu, r, omega, c, 1e-10)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9, 1e-12, 1e-14])
+def test_tolerances(eps):
+    r, omega, c = uniform_problem(1200, 1250, omega_max=2500.0, seed=7)
+    for nu in (0, 5):
+        _check(nu, r, omega, c, eps)
+
+
+def test_negative_order():
+    r, omega, c = uniform_problem(700, 600, omega_max=900.0, seed=8)
+    g3, _, _ = run_forward(3, r, omega, c, 1e-10)
+    gm3, _, _ = run_forward(-3, r, omega, c, 1e-10)
+    assert np.max(np.abs(gm3 + g3)) <= 1e-13 * np.abs(c).sum()
+
+
+def test_clustered_and_exponential_points():
+    r, omega, c = loguniform_problem(1500, 1400, omega_max=4e4, seed=4, complex_c=False)
+    _check(1, r, omega, c, 1e-10)
+    v, _ = exponential_grid(1500)
+    c = np.random.default_rng(3).standard_normal(1500)
+    _check(0, v, v * 40.0, c, 1e-8)
+
+
+def test_block_lists_match_oracle_subdivision():
+    r, omega, c = uniform_problem(2500, 2300, omega_max=3000.0, seed=11)
+    g, info, blocks = run_forward(2, r, omega, c, 1e-9)
+    rs, ws = np.sort(r), np.sort(omega)
+    Lb, Ab, Db = OS.subdivide(list(rs), list(ws), info["z"], 1024, 16)
+    for mine, ref in zip(blocks, (Lb, Ab, Db)):
+        assert [tuple(b) for b in mine.tolist()] == [tuple(b) for b in ref]
+
+
+def test_permutations_are_stable_sorts():
+    from paper_2411_09583_gb300 import Plan
+    rng = np.random.default_rng(12)
+    r = np.round(rng.uniform(0, 1, 3000), 2)          # many ties
+    omega = rng.uniform(0, 500, 2000)
+    omega[::7] = 0.0
+    with Plan(0, to_dev(r), to_dev(omega), 1e-8) as p:
+        pr, pw = p.permutations()
+    assert np.array_equal(pr, np.argsort(r, kind="stable"))
+    assert np.array_equal(pw, np.argsort(omega, kind="stable"))
+
+
+def test_complex_and_multiple_vectors():
+    r, omega, c = uniform_problem(900, 800, omega_max=1200.0, seed=13, nvec=3)
+    g, info, _ = run_forward(1, r, omega, c, 1e-9)
+    ref = oracle.direct(1, r, omega, c)
+    assert np.all(np.max(np.abs(g - ref), axis=0) <= tol(1e-9, c))
+    cz = c[:, 0] + 1j * c[:, 1]
+    gz, _, _ = run_forward(1, r, omega, cz, 1e-9)
+    refz = oracle.direct(1, r, omega, cz)
+    assert np.max(np.abs(gz - refz)) <= 10 * 1e-9 * np.abs(cz).sum()
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(14)
+    # empty sides
+    g, _, _ = run_forward(0, np.zeros(0), rng.uniform(0, 10, 5), np.zeros(0), 1e-8)
+    assert g.shape == (5,) and np.all(g == 0)
+    g, _, _ = run_forward(0, rng.uniform(0, 1, 5), np.zeros(0), rng.standard_normal(5), 1e-8)
+    assert g.shape == (0,)
+    # single point / frequency, zeros, duplicates
+    for (n, m) in [(1, 1), (1, 300), (300, 1), (33, 47)]:
+        r = rng.uniform(0, 1, n)
+        omega = rng.uniform(0, 3000, m)
+        c = rng.standard_normal(n)
+        _check(2, r, omega, c, 1e-9)
+    r = np.zeros(50)
+    c = rng.standard_normal(50)
+    g, _, _ = run_forward(0, r, rng.uniform(0, 100, 40), c, 1e-10)
+    assert np.max(np.abs(g - c.sum())) <= 1e-12 * np.abs(c).sum()
+    g, _, _ = run_forward(4, r, rng.uniform(0, 100, 40), c, 1e-10)
+    assert np.max(np.abs(g)) <= 1e-12 * np.abs(c).sum()
+    r = np.repeat(rng.uniform(0, 1, 20), 30)
+    omega = np.concatenate([np.zeros(10), np.repeat(rng.uniform(0, 5000, 25), 20)])
+    c = rng.standard_normal(r.size)
+    _check(1, r, omega, c, 1e-9)
+
+
+def test_invalid_inputs_rejected():
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300._native import NUHT_ERR_DOMAIN, NuhtError
+    r = np.array([0.1, -0.2, 0.3])
+    with pytest.raises(NuhtError) as e:
+        Plan(0, to_dev(r), to_dev(np.ones(3)), 1e-8)
+    assert e.value.code == NUHT_ERR_DOMAIN
+    with pytest.raises(NuhtError):
+        Plan(0, to_dev(np.ones(3)), to_dev(np.array([1.0, np.nan])), 1e-8)
+    with pytest.raises(NuhtError):
+        Plan(0, to_dev(np.ones(3)), to_dev(np.array([1.0, np.inf])), 1e-8)
+
+
+@pytest.mark.parametrize("nu", [0, 2, 5])
+def test_gaussian_pair_end_to_end(nu):
+    # int_0^inf exp(-r^2/2) J_nu(w r) r^(nu+1) dr = w^nu exp(-w^2/2), Gauss-Legendre on [0, 12]
+    x, wq = np.polynomial.legendre.leggauss(400)
+    r = 6.0 * (x + 1.0)
+    c = 6.0 * wq * r ** (nu + 1) * np.exp(-0.5 * r * r)
+    omega = np.linspace(0.0, 6.0, 301)
+    g, _, _ = run_forward(nu, r, omega, c, 1e-12)
+    assert np.max(np.abs(g - omega ** nu * np.exp(-0.5 * omega ** 2))) < 1e-11
+
+
+def test_unit_disk_end_to_end():
+    # Sec. 5.2: int_0^1 J_0(w r) r dr = J_1(w)/w
+    x, wq = np.polynomial.legendre.leggauss(2000)
+    r = 0.5 * (x + 1.0)
+    c = 0.5 * wq * r
+    omega = np.linspace(1.0, 1500.0, 700)
+    g, _, _ = run_forward(0, r, omega, c, 1e-12)
+    ref = oracle.jn(1, omega) / omega
+    assert np.max(np.abs(g - ref)) < 1e-11
+
+
+def test_linearity_and_input_permutation():
+    r, omega, c = uniform_problem(1000, 900, omega_max=2000.0, seed=15)
+    d = np.random.default_rng(16).standard_normal(1000)
+    g1, _, _ = run_forward(0, r, omega, c, 1e-10)
+    g2, _, _ = run_forward(0, r, omega, d, 1e-10)
+    g3, _, _ = run_forward(0, r, omega, 2 * c - 3 * d, 1e-10)
+    assert np.max(np.abs(g3 - (2 * g1 - 3 * g2))) <= 1e-12 * np.abs(c).sum() * 5
+    p = np.random.default_rng(17).permutation(1000)
+    g4, _, _ = run_forward(0, r[p], omega, c[p], 1e-10)
+    assert np.max(np.abs(g4 - g1)) <= 1e-12 * np.abs(c).sum()
+
+
+@pytest.mark.parametrize("nu", [0, 10])
+def test_full_size_sampled_rows(nu):
+    # n = m = 1e6, r ~ U[0,1], omega ~ U[0,1e5], eps = 1e-12: sampled outputs vs the oracle
+    eps = 1e-12
+    r, omega, c = uniform_problem(1_000_000, 1_000_000, omega_max=1e5, seed=2 if nu == 0 else 3)
+    g, info, _ = run_forward(nu, r, omega, c, eps)
+    rows = sample_rows(omega.size, 200, seed=99)
+    ref = oracle.direct_rows(nu, r, omega, c, rows)
+    err = np.max(np.abs(g[rows] - ref))
+    assert err <= tol(eps, c), (err, tol(eps, c))

@@ -30,7 +30,7 @@ def test_fig1_worked_example(nu, eps, M, L):
 
 
 def test_m_heuristic_by_hand():
-    # Eq. (3.7) evaluated by hand
+    # Sec. 3.3, eq. num-asy-terms, evaluated by hand
     assert P.choose_m(0, 1e-8) == 3      # floor(1 + 0 + 2)
     assert P.choose_m(10, 1e-12) == 6    # floor(1 + 2 + 3)
     assert P.choose_m(1, 1e-5) == 2      # floor(1 + 0.2 + 1.25)
@@ -63,7 +63,7 @@ def test_crossover_root_and_local_order_minimal(nu, eps):
 
 @pytest.mark.parametrize("nu,eps", CASES)
 def test_hankel_truncation_within_bound(nu, eps):
-    # Eq. (3.5): |J - Hankel_M| <= B^asy(x) <= eps for x >= z, and the bound is tight
+    # Sec. 3.2, eq. asy-error: |J - Hankel_M| <= B^asy(x) <= eps for x >= z, and the bound is tight
     M, z, L = P.choose_params(nu, eps)
     xs = np.concatenate([np.linspace(z, 1.05 * z, 120), np.linspace(z, 30 * z, 600)])
     errs = np.array([abs(E.hankel_sum(nu, M, x) - oracle.jn(nu, x)) for x in xs])
