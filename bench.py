@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 NUHT: one JSON line on stdout (rank 0).
+
+Workload (one step = the whole transform from unsorted device inputs):
+    n = m = 1e6 points / frequencies, nu = 0, eps = 1e-12,
+    r ~ U[0, 1], omega ~ U[0, 1e5], c ~ N(0, 1), FP64, seed 2 (+ rank),
+    plan (domain check, device sort, subdivision, work lists) + execute
+    (gather, local moments, type-3 spread / FFT / interpolation, local
+    evaluation, direct blocks, scatter).
+value = (n + m) * ranks / seconds per step (max over ranks), with the L2
+flushed between timed steps.  `execute_only` repeats the measurement with the
+plan reused.  `e2e` times nuht_transform_host: pinned host inputs -> device,
+plan, execute, g back to the host.
+
+--impl reference times the oracle (plain FP64 direct sum on the host cores)
+on a bounded sample of output rows of the same workload, extrapolated to the
+whole transform.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NUHT (n+m)/s at ε=1e-8 fp64 vs fp32-mixed; batched; % HBM roofline"
+UNIT = "(n+m)/s"
+# FP64 FMA pipe of GB300: 2 FMA (4 FLOP) per clock per SM, 152 SMs, 2070 MHz max clock.
+FP64_PEAK_TFLOPS = 4 * 152 * 2070e6 / 1e12
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--m", type=int, default=1_000_000)
+    ap.add_argument("--nu", type=int, default=0)
+    ap.add_argument("--eps", type=float, default=1e-12)
+    ap.add_argument("--omega-max", type=float, default=1e5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target duration of the oracle sample")
+    return ap.parse_args(argv)
+
+
+def workload_config(a):
+    return {"workload": "nuht_fp64_uniform_n%d_m%d_nu%d_eps%g" % (a.n, a.m, a.nu, a.eps),
+            "n": a.n, "m": a.m, "nu": a.nu, "eps": a.eps,
+            "r": "U[0,1]", "omega": "U[0,%g]" % a.omega_max, "c": "N(0,1) real",
+            "seed": 2, "step": "plan+execute from unsorted device inputs",
+            "l2": "flushed between timed steps (%d MiB write)" % (L2_FLUSH_BYTES >> 20)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, ws, device=None):
+    """Largest value over all ranks (identity for a single process)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_sample(a, r, omega, c, target_s):
+    """Time the oracle on sampled output rows; returns (extrapolated (n+m)/s, rows, seconds)."""
+    import numpy as np
+
+    import oracle
+    from paper_2411_09583_gb300.workloads import sample_rows
+    oracle.build()
+    probe = sample_rows(omega.size, 32, seed=1234)
+    t0 = time.perf_counter()
+    oracle.direct_rows(a.nu, r, omega, c, probe)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    nrows = int(min(max(32, 32 * target_s / dt), omega.size, 20000))
+    rows = sample_rows(omega.size, nrows, seed=4321)
+    t0 = time.perf_counter()
+    oracle.direct_rows(a.nu, r, omega, c, rows)
+    dt = time.perf_counter() - t0
+    full = dt * omega.size / nrows
+    return (r.size + omega.size) / full, nrows, dt
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a):
+    import numpy as np
+
+    from paper_2411_09583_gb300.workloads import uniform_problem
+    r, omega, c = uniform_problem(a.n, a.m, omega_max=a.omega_max, seed=2)
+    per_step = max(2.0, min(a.cpu_seconds, 120.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        oracle_sample(a, r, omega, c, per_step * 0.3)
+    vals, rows_used, secs = [], 0, 0.0
+    for _ in range(a.steps):
+        v, nrows, dt = oracle_sample(a, r, omega, c, per_step)
+        vals.append(v)
+        rows_used, secs = nrows, secs + dt
+    value = statistics.median(vals)
+    cores = os.cpu_count()
+    sample = ("oracle direct sum over all n points for %d random output rows per step, "
+              "extrapolated to m rows" % rows_used)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * (a.n + a.m) / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- our arm
+def _dominant_flops(stage, info, blocks, tab):
+    """Algorithmic FP64 FLOPs of one launch of the stage (see the design notes)."""
+    w, d, Q, L = tab["w"], tab["deg"], 2 * info["M"], info["L"]
+    asy = blocks[1]
+    loc = blocks[0]
+    if stage == "asy_spread":
+        units = float((asy[:, 3] - asy[:, 2] + 1).sum())
+        return units * (2 * w * d + 4 * w * Q), units
+    if stage == "asy_interp":
+        units = float((asy[:, 1] - asy[:, 0] + 1).sum())
+        return units * (2 * w * d + 4 * w * Q), units
+    if stage == "local_moments":
+        units = float((loc[:, 3] - loc[:, 2] + 1).sum())
+        return units * 4 * (L + 1), units
+    return None, None
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2411_09583_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        db = json.load(open(path))
+        ent = db.get(kernel)
+        if not ent or ent.get("workload") != workload:
+            return None
+        if ent.get("source_hash") != source_hash(*ent.get("sources", [])):
+            return None
+        return ent.get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2411_09583_gb300 import build_native
+    build_native.build()
+    from paper_2411_09583_gb300 import Plan, nuht as nuht_mod
+    from paper_2411_09583_gb300.nuht import kernel_launch_count, transform_host
+    from paper_2411_09583_gb300.workloads import uniform_problem
+
+    seed = 2 + rank
+    r, omega, c = uniform_problem(a.n, a.m, omega_max=a.omega_max, seed=seed)
+    dr, dw, dc = (torch.tensor(x, device=dev) for x in (r, omega, c))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(timing=False):
+        p = Plan(a.nu, dr, dw, a.eps, timing=timing)
+        g = p.execute(dc)
+        return p, g
+
+    # warm-up
+    for _ in range(max(a.warmup, 0)):
+        p, g = step()
+        p.close()
+    torch.cuda.synchronize(dev)
+
+    # timed: K whole transforms (plan + execute), L2 flushed between steps
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    stage_ms = {}
+    launches0 = kernel_launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    info = blocks = None
+    for i in range(a.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        p, g = step(timing=True)
+        ev[i][1].record(stream)
+        st = p.stage_times()
+        for k, v in st.items():
+            stage_ms.setdefault(k, []).append(v)
+        if info is None:
+            info = p.info()
+            blocks = [p.blocks(k) for k in range(3)]
+        p.close()
+    torch.cuda.synchronize(dev)
+    launches = kernel_launch_count() - launches0
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, ws, dev)
+    value = ws * a.steps * (a.n + a.m) / total_s
+
+    # execute only (plan reused)
+    p = Plan(a.nu, dr, dw, a.eps)
+    for _ in range(2):
+        p.execute(dc)
+    exe_ms = []
+    for i in range(a.steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        p.execute(dc)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        exe_ms.append(s0.elapsed_time(s1))
+    p.close()
+    exe_s = max_over_ranks(sum(exe_ms) / 1e3, ws, dev)
+
+    # end to end through the host-buffer entry point (pinned memory)
+    hr = torch.from_numpy(r).pin_memory().numpy()
+    hw = torch.from_numpy(omega).pin_memory().numpy()
+    hc = torch.from_numpy(c).pin_memory().numpy()
+    transform_host(a.nu, hr, hw, hc, a.eps)
+    e2e_ms = []
+    for i in range(max(3, a.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        gh = transform_host(a.nu, hr, hw, hc, a.eps)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(s0.elapsed_time(s1))
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, ws, dev)
+    e2e_value = ws * len(e2e_ms) * (a.n + a.m) / e2e_s
+
+    # dominant kernel and its roofline (FP64 ALU bound)
+    mean_stage = {k: sum(v) / len(v) for k, v in stage_ms.items()}
+    dom = max(mean_stage, key=mean_stage.get)
+    tab = {"w": info["nufft_width"], "deg": info["nufft_degree"]}
+    flops, units = _dominant_flops(dom, info, blocks, tab)
+    kernel_of = {"asy_spread": "k_asy_spread", "asy_interp": "k_asy_interp",
+                 "local_moments": "k_local_moments", "local_eval": "k_local_eval",
+                 "direct": "k_direct", "asy_fft": "k_asy_fft_small"}
+    roof = None
+    if flops is not None:
+        ach = flops / (mean_stage[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": kernel_of.get(dom, dom), "stage": dom,
+                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 FMA pipe: 4 FLOP/clk/SM x 152 SMs x 2070 MHz "
+                               "(derived from unit counts and max clock; measured 1.19 TF/s)",
+                "algorithmic_flops_per_launch": flops, "units_per_launch": units,
+                "launch_ms": mean_stage[dom],
+                "traffic": stored_traffic(kernel_of.get(dom, dom),
+                                          workload_config(a)["workload"])}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not a.no_cpu_baseline:
+            v, nrows, dt = oracle_sample(a, r, omega, c, a.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "oracle direct sum over all n points for %d random output rows "
+                             "(%.1f s), extrapolated to m rows" % (nrows, dt)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded uniform r, omega; Gaussian c)",
+                "config": dict(workload_config(a), parallelism="replicas" if ws > 1 else "1 GPU"),
+                "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": 8 * (a.n + a.m + a.n),
+                        "d2h_bytes_per_step": 8 * a.m},
+                "gpu_launches": launches,
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "execute_only": {"value": ws * a.steps * (a.n + a.m) / exe_s, "unit": UNIT,
+                                 "ms_per_step": 1e3 * exe_s / a.steps},
+                "stage_ms": mean_stage,
+                "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
+                         "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
+                         "direct_entries": info["direct_entries"],
+                         "asy_rows_cols": info["asy_rows_cols"],
+                         "local_rows_cols": info["local_rows_cols"]}}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    ws, rank, _ = dist_env()
+    if a.impl == "reference":
+        if rank != 0:
+            return 0
+        run_reference(a)
+        return 0
+    run_ours(a)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -67,14 +67,29 @@ typedef struct {
     int n_split_cand;  /* candidate rows tried by SplitIndices (Sec. 4.1); default 16 */
     int m_terms;       /* asymptotic terms M; 0 = the heuristic of Sec. 3.3 */
     int class_mask;    /* bit c set = apply blocks of class c (testing aid); default 7 */
-    int reserved[7];   /* must be zero */
+    int timing;        /* nonzero: execute records a CUDA event pair around each stage
+                          (see nuht_stage_times); default 0 */
+    int reserved[6];   /* must be zero */
 } nuht_opts;
+
+/* Execute stages, in launch order (nuht_stage_times / nuht_stage_name). */
+#define NUHT_STAGE_GATHER        0   /* c to sorted order */
+#define NUHT_STAGE_LOCAL_MOMENTS 1   /* Wimp moments of the local blocks */
+#define NUHT_STAGE_ASY_SPREAD    2   /* type-3 spreading of the asymptotic blocks */
+#define NUHT_STAGE_ASY_FFT       3   /* deconvolution + FFT of the spread grids */
+#define NUHT_STAGE_ASY_INTERP    4   /* interpolation + Hankel combination */
+#define NUHT_STAGE_LOCAL_EVAL    5   /* Wimp evaluation of the local blocks */
+#define NUHT_STAGE_DIRECT        6   /* direct blocks */
+#define NUHT_STAGE_SCATTER       7   /* g back to user order */
+#define NUHT_NUM_STAGES          8
 
 typedef struct {
     int     nu;            /* order */
     int     M;             /* Hankel terms (pairs), Sec. 3.3 */
     int     L;             /* Wimp order (terms l = 0..L), Lemma 3.1 */
     int     nufft_width;   /* ES kernel width w of the type-3 NUFFTs */
+    int     nufft_degree;  /* degree of the kernel's piecewise polynomials */
+    int     pad_;
     double  z;             /* crossover point, B^asy_{nu,M}(z) = eps */
     double  eps;
     int64_t n, m;
@@ -142,6 +157,20 @@ int nuht_get_blocks(nuht_plan_t p, int cls, int64_t *ranges, int64_t cap, int64_
  * the i-th smallest r (n entries), perm_omega likewise (m entries).  Either
  * pointer may be NULL. */
 int nuht_get_permutations(nuht_plan_t p, int32_t *perm_r, int32_t *perm_omega);
+
+/* Device time (milliseconds) of each stage of the most recent nuht_execute
+ * of a plan built with opts.timing != 0, summed over the vectors of that call;
+ * ms has room for cap doubles (NUHT_NUM_STAGES suffices); stages that did not
+ * run report 0.  Waits for the events of that call.  NUHT_ERR_INVALID_ARG if
+ * timing is off or nothing ran yet. */
+int nuht_stage_times(nuht_plan_t p, double *ms, int cap);
+
+/* Static name of stage i ("gather", "local_moments", ...), or NULL. */
+const char *nuht_stage_name(int i);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a diagnostic counter). */
+int64_t nuht_kernel_launch_count(void);
 
 /* Release a plan (NULL is ignored).  Waits for the plan's stream. */
 void nuht_destroy(nuht_plan_t p);

@@ -28,18 +28,22 @@ BLOCK_LOCAL, BLOCK_ASY, BLOCK_DIRECT = 0, 1, 2
 EXPORTED = ["nuht_default_opts", "nuht_choose_params", "nuht_plan", "nuht_execute",
             "nuht_adjoint", "nuht_transform_host", "nuht_info", "nuht_get_blocks",
             "nuht_get_permutations", "nuht_destroy", "nuht_strerror",
-            "nuht_last_cuda_error"]
+            "nuht_last_cuda_error", "nuht_stage_times", "nuht_stage_name",
+            "nuht_kernel_launch_count"]
+NUM_STAGES = 8
 
 
 class NuhtOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("min_size", ctypes.c_int),
                 ("n_split_cand", ctypes.c_int), ("m_terms", ctypes.c_int),
-                ("class_mask", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("class_mask", ctypes.c_int), ("timing", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class NuhtPlanInfo(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_int), ("M", ctypes.c_int), ("L", ctypes.c_int),
-                ("nufft_width", ctypes.c_int), ("z", ctypes.c_double), ("eps", ctypes.c_double),
+                ("nufft_width", ctypes.c_int), ("nufft_degree", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("z", ctypes.c_double), ("eps", ctypes.c_double),
                 ("n", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("n_local", ctypes.c_int64), ("n_asy", ctypes.c_int64),
                 ("n_direct", ctypes.c_int64), ("direct_entries", ctypes.c_int64),
@@ -104,5 +108,11 @@ def lib():
         L.nuht_strerror.restype = ctypes.c_char_p
         L.nuht_last_cuda_error.argtypes = []
         L.nuht_last_cuda_error.restype = ctypes.c_char_p
+        L.nuht_stage_times.argtypes = [p, p, i]
+        L.nuht_stage_times.restype = i
+        L.nuht_stage_name.argtypes = [i]
+        L.nuht_stage_name.restype = ctypes.c_char_p
+        L.nuht_kernel_launch_count.argtypes = []
+        L.nuht_kernel_launch_count.restype = i64
         _lib = L
         return _lib

@@ -310,6 +310,7 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -325,6 +326,7 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;
     k_asy_fft_small<<<nitems, nt, smem, s>>>(probs, blks, items, tab, grid_b, grid_q);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -343,6 +345,7 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_asy_fft_pass_b<<<nitems_b, 256, smem, s>>>(probs, blks, items_b, tab, tmp, grid_q);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -353,6 +356,7 @@ cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, con
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(double) * (size_t)tab.w * (tab.deg + 1);
     k_asy_interp<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -171,6 +171,7 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_local_moments<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r_s, c_s, mom);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -194,6 +195,7 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_local_eval<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w_s, mom, g_s);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -206,6 +208,7 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, c_s, g_s);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -189,6 +189,7 @@ cudaError_t launch_check_domain(const double* x, int64_t n, int* flag, cudaStrea
 {
     if (n <= 0) return cudaSuccess;
     k_check_domain<<<grid_for(n, 256), 256, 0, s>>>(x, n, flag);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -225,6 +226,7 @@ cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* pe
     }
     // after an even number of passes the data is back in (k0, perm)
     k_sort_finish<<<grid_for(n, 256), 256, 0, s>>>(ka, n, out);
+    count_launches(2 + 8 * 3);
     return cudaGetLastError();
 }
 
@@ -233,6 +235,7 @@ cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int s
 {
     if (n <= 0) return cudaSuccess;
     k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -241,6 +244,7 @@ cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int
 {
     if (m <= 0) return cudaSuccess;
     k_scatter<<<grid_for(m, 256), 256, 0, s>>>(gs, perm, m, stride, comp, g);
+    count_launches(1);
     return cudaGetLastError();
 }
 

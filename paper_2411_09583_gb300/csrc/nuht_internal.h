@@ -89,7 +89,9 @@ struct Tables {
 };
 
 // ------------------------------------------------------------ device launches
-// (each returns cudaGetLastError() of its launch)
+// (each returns cudaGetLastError() of its launch and adds the number of
+// kernels it launched to the library's launch counter)
+void count_launches(int k);
 cudaError_t launch_check_domain(const double* x, int64_t n, int* flag, cudaStream_t s);
 cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* perm,
                            void* scratch, size_t scratch_bytes, cudaStream_t s);

@@ -1,5 +1,6 @@
 // C ABI of the NUHT library: plan (sort + subdivision + work lists), execute
 // (Algorithm 2 on the device), info and helpers.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,10 @@ using namespace nuht;
 namespace {
 
 thread_local std::string g_cuda_msg = "no CUDA error";
+std::atomic<int64_t> g_launches{0};
+
+const char* const kStageNames[NUHT_NUM_STAGES] = {
+    "gather", "local_moments", "asy_spread", "asy_fft", "asy_interp", "local_eval", "direct", "scatter"};
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -76,7 +81,56 @@ struct nuht_plan_s {
     Tables tab{};
     std::vector<HBlock> hb[3];
     int64_t direct_entries = 0, local_rc = 0, asy_rc = 0, fft_points = 0;
+
+    // stage timing (opts.timing): event pairs per (vector component, stage)
+    std::vector<cudaEvent_t> ev;
+    std::vector<char> ev_used;
+    int ev_comps = 0;
 };
+
+namespace nuht {
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}
+
+namespace {
+
+// Records the start / end event of a stage when the plan times its stages.
+struct StageTimer {
+    nuht_plan_t P;
+    int comp;
+    cudaStream_t s;
+    int begin(int stage)
+    {
+        if (!P->opt.timing) return NUHT_OK;
+        size_t i = ((size_t)comp * NUHT_NUM_STAGES + stage) * 2;
+        P->ev_used[i / 2] = 1;
+        NUHT_CK(cudaEventRecord(P->ev[i], s));
+        return NUHT_OK;
+    }
+    int end(int stage)
+    {
+        if (!P->opt.timing) return NUHT_OK;
+        size_t i = ((size_t)comp * NUHT_NUM_STAGES + stage) * 2;
+        NUHT_CK(cudaEventRecord(P->ev[i + 1], s));
+        return NUHT_OK;
+    }
+};
+
+int ensure_events(nuht_plan_t P, int comps)
+{
+    if (!P->opt.timing) return NUHT_OK;
+    size_t need = (size_t)comps * NUHT_NUM_STAGES * 2;
+    while (P->ev.size() < need) {
+        cudaEvent_t e;
+        NUHT_CK(cudaEventCreate(&e));
+        P->ev.push_back(e);
+    }
+    P->ev_used.assign(P->ev.size() / 2, 0);
+    P->ev_comps = comps;
+    return NUHT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -123,7 +177,29 @@ void nuht_destroy(nuht_plan_t p)
         cudaFreeAsync(p->dmem, p->stream);
         cudaStreamSynchronize(p->stream);
     }
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     delete p;
+}
+
+int64_t nuht_kernel_launch_count(void) { return g_launches.load(); }
+
+const char* nuht_stage_name(int i) { return (i >= 0 && i < NUHT_NUM_STAGES) ? kStageNames[i] : nullptr; }
+
+int nuht_stage_times(nuht_plan_t P, double* ms, int cap)
+{
+    if (!P || !ms || cap < 0 || !P->opt.timing || P->ev_comps == 0) return NUHT_ERR_INVALID_ARG;
+    for (int st = 0; st < cap; ++st) ms[st] = 0.0;
+    for (int comp = 0; comp < P->ev_comps; ++comp) {
+        for (int st = 0; st < NUHT_NUM_STAGES && st < cap; ++st) {
+            size_t i = (size_t)comp * NUHT_NUM_STAGES + st;
+            if (!P->ev_used[i]) continue;
+            NUHT_CK(cudaEventSynchronize(P->ev[2 * i + 1]));
+            float t = 0.f;
+            NUHT_CK(cudaEventElapsedTime(&t, P->ev[2 * i], P->ev[2 * i + 1]));
+            ms[st] += t;
+        }
+    }
+    return NUHT_OK;
 }
 
 static int build_plan(nuht_plan_t P, const double* r, const double* omega)
@@ -363,7 +439,7 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
     if (o.min_size < 1 || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
     nuht_plan_t P = new (std::nothrow) nuht_plan_s();
     if (!P) return NUHT_ERR_NOMEM;
@@ -395,33 +471,55 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
     return NUHT_OK;
 }
 
-static int apply_forward(nuht_plan_t P, cudaStream_t s)
+#define NUHT_TRY(x)                   \
+    do {                              \
+        int rc_ = (x);                \
+        if (rc_ != NUHT_OK) return rc_; \
+    } while (0)
+
+// Algorithm 2 on the device for one vector component: local moments, the
+// asymptotic type-3 pipeline, local evaluation and direct blocks, all
+// accumulating into g in sorted order.
+static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
-    NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * (P->m > 0 ? P->m : 1), s));
     if ((mask & 1) && P->n_loc) {
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->prob.L, P->d_r,
                                      P->d_cs, P->d_mom, s));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS));
     }
     if ((mask & 2) && P->n_asy) {
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
         NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->prob.Q, P->tab,
                                   P->d_r, P->d_cs, P->d_gb, s));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small,
                                      P->tab, P->d_gb, P->d_gq, s));
         if (P->has_large_fft)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
                                          P->d_gb, P->d_gtmp, P->d_gq, s));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP));
         NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->tab, P->d_w,
                                   P->d_gq, P->d_gs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP));
     }
-    if ((mask & 1) && P->n_loc)
+    if ((mask & 1) && P->n_loc) {
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL));
         NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
                                   P->eval_threads, P->d_w, P->d_mom, P->d_gs, s));
-    if ((mask & 4) && P->n_dir)
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL));
+    }
+    if ((mask & 4) && P->n_dir) {
+        NUHT_TRY(T.begin(NUHT_STAGE_DIRECT));
         NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->d_r, P->d_w, P->d_cs,
                               P->d_gs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_DIRECT));
+    }
     return NUHT_OK;
 }
 
@@ -436,11 +534,17 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         NUHT_CK(cudaMemsetAsync(g, 0, sizeof(double) * P->m * comps, s));
         return NUHT_OK;
     }
+    NUHT_TRY(ensure_events(P, comps));
     for (int comp = 0; comp < comps; ++comp) {
+        StageTimer T{P, comp, s};
+        NUHT_TRY(T.begin(NUHT_STAGE_GATHER));
+        NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * P->m, s));
         NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, s));
-        int rc = apply_forward(P, s);
-        if (rc != NUHT_OK) return rc;
+        NUHT_TRY(T.end(NUHT_STAGE_GATHER));
+        NUHT_TRY(apply_forward(P, T, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_SCATTER));
         NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, g, s));
+        NUHT_TRY(T.end(NUHT_STAGE_SCATTER));
     }
     return NUHT_OK;
 }
@@ -492,6 +596,7 @@ int nuht_info(nuht_plan_t P, nuht_plan_info* out)
     out->M = P->prob.M;
     out->L = P->prob.L;
     out->nufft_width = P->w;
+    out->nufft_degree = P->tab.deg;
     out->z = P->prob.z;
     out->eps = P->eps;
     out->n = P->n;

@@ -29,7 +29,8 @@ def _dev_f64(x, name):
     return x.contiguous()
 
 
-def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class_mask=7):
+def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class_mask=7,
+              timing=False):
     o = N.NuhtOpts()
     N.lib().nuht_default_opts(ctypes.byref(o))
     o.precision = {"fp64": N.PREC_FP64, "mixed": N.PREC_MIXED}[precision]
@@ -37,7 +38,17 @@ def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class
     o.n_split_cand = int(n_split_cand)
     o.m_terms = int(m_terms)
     o.class_mask = int(class_mask)
+    o.timing = 1 if timing else 0
     return o
+
+
+def kernel_launch_count():
+    """Kernels launched by libnuht.so in this process so far."""
+    return int(N.lib().nuht_kernel_launch_count())
+
+
+def stage_names():
+    return [N.lib().nuht_stage_name(i).decode() for i in range(N.NUM_STAGES)]
 
 
 def choose_params(nu, eps, m_terms=0):
@@ -110,6 +121,12 @@ class Plan:
             N.check(N.lib().nuht_get_blocks(self._h, int(cls), out.ctypes.data_as(ctypes.c_void_p),
                                             cnt.value, ctypes.byref(cnt)), "nuht_get_blocks")
         return out
+
+    def stage_times(self):
+        """{stage: device ms} of the most recent execute (plan built with timing=True)."""
+        ms = (ctypes.c_double * N.NUM_STAGES)()
+        N.check(N.lib().nuht_stage_times(self._h, ms, N.NUM_STAGES), "nuht_stage_times")
+        return dict(zip(stage_names(), list(ms)))
 
     def permutations(self):
         pr = np.zeros(self.n, dtype=np.int32)
