@@ -50,6 +50,7 @@ extern "C" {
 #define NUHT_ERR_CUDA        4   /* a CUDA runtime call failed (see nuht_last_cuda_error) */
 #define NUHT_ERR_TIMEOUT     5   /* a bounded device wait gave up (reserved) */
 #define NUHT_ERR_UNSUPPORTED 6   /* option combination not built (e.g. order |nu| > 100) */
+#define NUHT_ERR_SCRATCH     7   /* request exceeds the fixed scratch of nuht_local_apply_noalloc */
 
 /* --------------------------------------------------------------- options */
 #define NUHT_PREC_FP64  0   /* every stage in FP64 (or FP64-accurate arithmetic) */
@@ -171,6 +172,38 @@ const char *nuht_stage_name(int i);
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter). */
 int64_t nuht_kernel_launch_count(void);
+
+/* ------------------------------------------------- no-allocation entry point
+ * The paper has no counterpart to this call; it is a service for callers that
+ * cannot let a library call cudaMalloc -- frameworks that reserve nearly all
+ * device memory for their own pool up front, and latency-critical loops in
+ * which cudaMalloc / cudaFree would stall on an implicit device
+ * synchronisation.
+ *
+ * nuht_local_apply_noalloc computes g = A c (same definition and accuracy
+ * contract as nuht_execute) for a transform whose whole matrix is local:
+ * the caller gives bounds r_max >= every r_j and omega_max >= every omega_k
+ * with omega_max * r_max <= z(nu, eps) (z from nuht_choose_params), and the
+ * Wimp expansion of Sec. 3.1 is applied to the whole matrix as one block.
+ * r (n), omega (m), c (n x nvec, c[j*nvec+v]) and g (m x nvec, overwritten)
+ * are device FP64 arrays in any order.  Values outside the stated bounds give
+ * unspecified (but memory-safe) results.
+ *
+ * It allocates nothing.  Its scratch (the nvec x (L+1) Wimp moments) is a
+ * fixed device array of NUHT_NOALLOC_MAX_MOMENTS doubles (256 KiB) that every
+ * GPU which loads the library holds until the process exits; requests with
+ * nvec * (L + 1) > NUHT_NOALLOC_MAX_MOMENTS return NUHT_ERR_SCRATCH.  All calls
+ * on a device share that array (each call clears what it uses), so calls that
+ * overlap on the GPU -- e.g. on two streams -- race.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  Errors: NUHT_ERR_INVALID_ARG (sizes, pointers, eps),
+ * NUHT_ERR_DOMAIN (omega_max * r_max > z, or a bound negative / not finite),
+ * NUHT_ERR_UNSUPPORTED (|nu| > 100), NUHT_ERR_SCRATCH, NUHT_ERR_CUDA. */
+#define NUHT_NOALLOC_MAX_MOMENTS 32768
+int nuht_local_apply_noalloc(int nu, double eps, const double *r, int64_t n, double r_max,
+                             const double *omega, int64_t m, double omega_max,
+                             const double *c, double *g, int nvec, void *stream);
 
 /* Release a plan (NULL is ignored).  Waits for the plan's stream. */
 void nuht_destroy(nuht_plan_t p);

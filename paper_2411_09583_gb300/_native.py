@@ -19,6 +19,8 @@ NUHT_ERR_NOMEM = 3
 NUHT_ERR_CUDA = 4
 NUHT_ERR_TIMEOUT = 5
 NUHT_ERR_UNSUPPORTED = 6
+NUHT_ERR_SCRATCH = 7
+NOALLOC_MAX_MOMENTS = 32768
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -29,7 +31,7 @@ EXPORTED = ["nuht_default_opts", "nuht_choose_params", "nuht_plan", "nuht_execut
             "nuht_adjoint", "nuht_transform_host", "nuht_info", "nuht_get_blocks",
             "nuht_get_permutations", "nuht_destroy", "nuht_strerror",
             "nuht_last_cuda_error", "nuht_stage_times", "nuht_stage_name",
-            "nuht_kernel_launch_count"]
+            "nuht_kernel_launch_count", "nuht_local_apply_noalloc"]
 NUM_STAGES = 8
 
 
@@ -114,5 +116,7 @@ def lib():
         L.nuht_stage_name.restype = ctypes.c_char_p
         L.nuht_kernel_launch_count.argtypes = []
         L.nuht_kernel_launch_count.restype = i64
+        L.nuht_local_apply_noalloc.argtypes = [i, d, p, i64, d, p, i64, d, p, p, i, p]
+        L.nuht_local_apply_noalloc.restype = i
         _lib = L
         return _lib

@@ -155,6 +155,7 @@ const char* nuht_strerror(int code)
         case NUHT_ERR_CUDA: return "CUDA error";
         case NUHT_ERR_TIMEOUT: return "device wait timed out";
         case NUHT_ERR_UNSUPPORTED: return "unsupported parameters";
+        case NUHT_ERR_SCRATCH: return "request exceeds the no-allocation scratch (nvec * (L + 1) > NUHT_NOALLOC_MAX_MOMENTS)";
         default: return "unknown status";
     }
 }

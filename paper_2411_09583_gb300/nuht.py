@@ -154,6 +154,29 @@ class Plan:
         self.close()
 
 
+def local_apply_noalloc(nu, r, omega, c, eps, r_max, omega_max, out=None, stream=None):
+    """g = A c through nuht_local_apply_noalloc (no device allocation inside the call).
+
+    For transforms whose whole matrix is local: r_max >= every r_j, omega_max >=
+    every omega_k and omega_max * r_max <= z(nu, eps).  c: (n,) or (n, nvec) float64
+    CUDA tensor; returns g with m rows.  `out` may pass a preallocated output.
+    """
+    r = _dev_f64(r, "r")
+    omega = _dev_f64(omega, "omega")
+    c = _dev_f64(c, "c")
+    nvec = 1 if c.dim() == 1 else int(np.prod(c.shape[1:]))
+    shape = (omega.numel(),) + tuple(c.shape[1:])
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=c.device)
+    with torch.cuda.device(c.device):
+        N.check(N.lib().nuht_local_apply_noalloc(
+            int(nu), float(eps), ctypes.c_void_p(r.data_ptr()), r.numel(), float(r_max),
+            ctypes.c_void_p(omega.data_ptr()), omega.numel(), float(omega_max),
+            ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(out.data_ptr()), nvec,
+            _stream_ptr(stream)), "nuht_local_apply_noalloc")
+    return out
+
+
 def nuht(nu, r, omega, c, eps, **opts):
     """One-shot transform on device tensors: plan, execute, release."""
     with Plan(nu, r, omega, eps, **opts) as p:
