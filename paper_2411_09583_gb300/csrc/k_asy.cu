@@ -20,9 +20,16 @@
 // where psi^(xi) = int psi(t) cos(xi t) dt.  The two 1/psi^ factors undo the
 // smoothing of the two spreading steps (Poisson summation); 4 / w^2 collects
 // the grid spacings h and 2 pi / nf2 against alpha and alpha2.
+//
+// Arithmetic: per-point set-up (coordinates, phases, weights' base) in FP64;
+// kernel taps, weighted values and all tap sums in double-float (df64.cuh,
+// ~48 bits, on the FP32 pipes); grids and the FFT in FP64.  The FFT output is
+// stored split into (hi, lo) floats so that the interpolation reads it as
+// double-float without FP64 work.
 #include <cstdint>
 
 #include "device_math.cuh"
+#include "df64.cuh"
 #include "nuht_internal.h"
 
 namespace nuht {
@@ -58,18 +65,17 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
                              const double* __restrict__ r_s, const double* __restrict__ c_s,
                              double2* __restrict__ grid_b)
 {
-    extern __shared__ double smem[];
+    extern __shared__ float4 smem4[];
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
-    double* coef = smem;                          // [w][deg+1]
-    double* taps = coef + ncoef;                  // [nt][w]
-    // double2 needs 16-byte alignment: round the double offset up to even
-    double2* aval = (double2*)(smem + ((ncoef + nt * w + 1) & ~1));   // [nt][Q]
-    int* l0s = (int*)(aval + nt * Q);             // [nt]
-    for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es[i];
+    float4* aval = smem4;                                   // [nt][Q]: (re.h, re.l, im.h, im.l)
+    float2* coef = (float2*)(aval + nt * Q);                // [w][deg+1]
+    float2* taps = coef + ncoef;                            // [nt][w]
+    int* l0s = (int*)(taps + nt * w);                       // [nt]
+    for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
     __syncthreads();
     const int cnt = t.count;
     if (tid < cnt) {
@@ -81,15 +87,22 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
         double z0 = lf - a;
         z0 = fmin(fmax(z0, 0.0), 1.0);
         const double v = 2.0 * z0 - 1.0;
-        for (int i = 0; i < w; ++i) taps[tid * w + i] = horner(coef + i * (deg + 1), deg, v);
+        const float vh = (float)v, vl = (float)(v - (double)vh);
+        for (int i = 0; i < w; ++i) {
+            const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl);
+            taps[tid * w + i] = make_float2(tp.h, tp.l);
+        }
         l0s[tid] = (int)lf;
         double sn, cs;
         sincos_prod(B.wc, x, &sn, &cs);
         const double ratio = B.rho / rj;              // (r/rho)^(-1)
-        double wq = c_s[j] * sqrt(ratio);             // c_j (r/rho)^(-1/2)
+        const double w0 = c_s[j] * sqrt(ratio);       // c_j (r/rho)^(-1/2)
+        const df rat = df_from(ratio);
+        df wr = df_from(w0 * cs), wi = df_from(w0 * sn);
         for (int q = 0; q < Q; ++q) {
-            aval[tid * Q + q] = make_double2(wq * cs, wq * sn);
-            wq *= ratio;
+            aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
+            wr = df_mul(wr, rat);
+            wi = df_mul(wi, rat);
         }
     }
     __syncthreads();
@@ -104,21 +117,22 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
         int lo = 0, hi = cnt;
         const int key = cell - w + 1;
         while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
-        int p_lo = lo;
+        const int p_lo = lo;
         hi = cnt;
         while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] <= cell) lo = mid + 1; else hi = mid; }
         const int p_hi = lo;
-        double sr = 0.0, si = 0.0;
+        acc2 ar{0.f, 0.f}, ai{0.f, 0.f};
         for (int p = p_lo; p < p_hi; ++p) {
-            const double k = taps[p * w + (cell - l0s[p])];
-            const double2 av = aval[p * Q + q];
-            sr = fma(k, av.x, sr);
-            si = fma(k, av.y, si);
+            const float2 k2 = taps[p * w + (cell - l0s[p])];
+            const float4 av = aval[p * Q + q];
+            const df k{k2.x, k2.y};
+            acc_fma(ar, k, df{av.x, av.y});
+            acc_fma(ai, k, df{av.z, av.w});
         }
         const int idx = cell + B.N1;
         if (p_hi > p_lo && idx >= 0 && idx < nf1) {
-            atomicAdd(&gb[(int64_t)idx * Q + q].x, sr);
-            atomicAdd(&gb[(int64_t)idx * Q + q].y, si);
+            atomicAdd(&gb[(int64_t)idx * Q + q].x, acc_value(ar));
+            atomicAdd(&gb[(int64_t)idx * Q + q].y, acc_value(ai));
         }
     }
 }
@@ -159,9 +173,16 @@ __device__ __forceinline__ double2 corrected_mode(const AsyBlock& B, const Table
     return make_double2(v.x * s, v.y * s);
 }
 
+// Complex FP64 value stored as double-float parts (re.h, re.l, im.h, im.l).
+__device__ __forceinline__ float4 split4(double2 v)
+{
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const FftItem* __restrict__ items, Tables tab,
-                                const double2* __restrict__ grid_b, double2* __restrict__ grid_q)
+                                const double2* __restrict__ grid_b, float4* __restrict__ grid_q)
 {
     extern __shared__ double2 X[];
     const FftItem it = items[blockIdx.x];
@@ -173,8 +194,8 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
         X[__brev(tt) >> (32 - logN)] = corrected_mode(B, tab, gb, Q, it.q, tt);
     __syncthreads();
     smem_fft(X, logN, tab.tw, tab.tw_log2);
-    double2* gq = grid_q + B.q_off;
-    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) gq[(int64_t)tt * Q + it.q] = X[tt];
+    float4* gq = grid_q + B.q_off;
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) gq[(int64_t)tt * Q + it.q] = split4(X[tt]);
 }
 
 // Four-step FFT for nf2 = N1 * N2 > kFftSmemMax, N2 = kFftSmemMax.
@@ -211,7 +232,7 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
 
 __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const FftItem* __restrict__ items, Tables tab,
-                                 const double2* __restrict__ tmp, double2* __restrict__ grid_q)
+                                 const double2* __restrict__ tmp, float4* __restrict__ grid_q)
 {
     extern __shared__ double2 X[];
     const FftItem it = items[blockIdx.x];
@@ -226,9 +247,9 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
         X[logN1 > 0 ? (__brev(n1) >> (32 - logN1)) : 0] = tq[(int64_t)(n1 + N1 * k2) * Q + it.q];
     __syncthreads();
     smem_fft(X, logN1, tab.tw, tab.tw_log2);
-    double2* gq = grid_q + B.q_off;
+    float4* gq = grid_q + B.q_off;
     for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x)
-        gq[(int64_t)(k2 + N2 * k1) * Q + it.q] = X[k1];
+        gq[(int64_t)(k2 + N2 * k1) * Q + it.q] = split4(X[k1]);
     (void)N;
 }
 
@@ -237,15 +258,15 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
 // deconvolve, post-phase, and combine the Hankel terms into g.
 __global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, Tables tab,
-                             const double* __restrict__ w_s, const double2* __restrict__ grid_q,
+                             const double* __restrict__ w_s, const float4* __restrict__ grid_q,
                              double* __restrict__ g_s)
 {
-    extern __shared__ double coef[];
+    extern __shared__ float2 coef2[];
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
     const int w = tab.w, deg = tab.deg;
-    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef[i] = tab.es[i];
+    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
     __syncthreads();
     if ((int)threadIdx.x >= t.count) return;
     const int64_t k = t.start + threadIdx.x;
@@ -256,35 +277,49 @@ __global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBloc
     double z0 = tf - a;
     z0 = fmin(fmax(z0, 0.0), 1.0);
     const double v = 2.0 * z0 - 1.0;
-    double taps[kMaxW];
+    const float vh = (float)v, vl = (float)(v - (double)vh);
+    float th[kMaxW], tl[kMaxW];
 #pragma unroll
-    for (int i = 0; i < kMaxW; ++i) taps[i] = (i < w) ? horner(coef + i * (deg + 1), deg, v) : 0.0;
+    for (int i = 0; i < kMaxW; ++i) {
+        if (i < w) {
+            const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl);
+            th[i] = tp.h;
+            tl[i] = tp.l;
+        } else {
+            th[i] = 0.f;
+            tl[i] = 0.f;
+        }
+    }
     const int t0 = (int)tf;
     const int mask = B.nf2 - 1;
     const int Q = P.Q;
-    const double2* gq = grid_q + B.q_off;
+    const float4* gq = grid_q + B.q_off;
     const double m1 = 1.0 / (wk * B.rho);     // 1/(omega rho) < 1/z
-    double tr = 0.0, ti = 0.0;                // sum_q a_q i^q (omega rho)^(-q) P_q
-    double mq = 1.0;
+    const df m1d = df_from(m1);
+    // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
+    acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
+    df mq{1.f, 0.f};
     for (int q = 0; q < Q; ++q) {
-        double pr = 0.0, pi = 0.0;
+        acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < kMaxW; ++i) {
             if (i < w) {
-                const double2 gv = gq[(int64_t)((t0 + i) & mask) * Q + q];
-                pr = fma(taps[i], gv.x, pr);
-                pi = fma(taps[i], gv.y, pi);
+                const float4 gv = gq[(int64_t)((t0 + i) & mask) * Q + q];
+                const df tp{th[i], tl[i]};
+                acc_fma(pr, tp, df{gv.x, gv.y});
+                acc_fma(pi, tp, df{gv.z, gv.w});
             }
         }
-        const double cq = P.a[q] * mq;
-        // multiply by i^q
+        const df prd = fast_two_sum(pr.s, pr.c), pid = fast_two_sum(pi.s, pi.c);
+        const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
+        // multiply by i^q: (pr + i pi) i^q
         switch (q & 3) {
-            case 0: tr = fma(cq, pr, tr); ti = fma(cq, pi, ti); break;
-            case 1: tr = fma(-cq, pi, tr); ti = fma(cq, pr, ti); break;
-            case 2: tr = fma(-cq, pr, tr); ti = fma(-cq, pi, ti); break;
-            default: tr = fma(cq, pi, tr); ti = fma(-cq, pr, ti); break;
+            case 0: acc_fma(tr, cq, prd); acc_fma(ti, cq, pid); break;
+            case 1: acc_fma(tr, df{-cq.h, -cq.l}, pid); acc_fma(ti, cq, prd); break;
+            case 2: acc_fma(tr, df{-cq.h, -cq.l}, prd); acc_fma(ti, df{-cq.h, -cq.l}, pid); break;
+            default: acc_fma(tr, cq, pid); acc_fma(ti, df{-cq.h, -cq.l}, prd); break;
         }
-        mq *= m1;
+        mq = df_mul(mq, m1d);
     }
     double sn, cs;
     sincos_prod(wk, B.rc, &sn, &cs);
@@ -293,7 +328,7 @@ __global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBloc
     const double ei = sn * P.cphi + cs * P.sphi;
     const double scale = 0.7978845608028654 * sqrt(m1) * (4.0 / ((double)w * (double)w)) /
                          psihat(tab, B.alpha * s);
-    const double val = scale * (er * tr - ei * ti);
+    const double val = scale * (er * acc_value(tr) - ei * acc_value(ti));
     atomicAdd(&g_s[k], (double)P.sgn * val);
 }
 
@@ -305,8 +340,8 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
 {
     if (ntiles <= 0) return cudaSuccess;
     const int nt = (qmax > 16) ? 128 : 256;
-    const size_t ndbl = ((size_t)tab.w * (tab.deg + 1) + (size_t)nt * tab.w + 1) & ~(size_t)1;
-    size_t smem = sizeof(double) * ndbl + sizeof(double2) * (size_t)nt * qmax + sizeof(int) * (size_t)nt;
+    size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
+                  sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
@@ -316,7 +351,7 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
 
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const FftItem* items,
                                  int nitems, int max_nf2, Tables tab, const double2* grid_b,
-                                 double2* grid_q, cudaStream_t s)
+                                 float4* grid_q, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
     size_t smem = sizeof(double2) * (size_t)max_nf2;
@@ -332,7 +367,7 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
 
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const FftItem* items_a,
                                  int nitems_a, const FftItem* items_b, int nitems_b, Tables tab,
-                                 const double2* grid_b, double2* tmp, double2* grid_q,
+                                 const double2* grid_b, double2* tmp, float4* grid_q,
                                  cudaStream_t s)
 {
     if (nitems_a <= 0) return cudaSuccess;
@@ -350,11 +385,11 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
 }
 
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, Tables tab, const double* w_s, const double2* grid_q,
+                              int ntiles, Tables tab, const double* w_s, const float4* grid_q,
                               double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)tab.w * (tab.deg + 1);
+    size_t smem = sizeof(float2) * (size_t)tab.w * (tab.deg + 1);
     k_asy_interp<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();

@@ -24,6 +24,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                       // elements per thread per tile
 constexpr int kSortTile = kSortThreads * kSortItems; // 4096
 constexpr int kRadix = 256;
+static_assert(kSortThreads == kRadix, "the scatter kernel scans one digit total per thread");
 
 __global__ void k_check_domain(const double* __restrict__ x, int64_t n, int* flag)
 {
@@ -67,21 +68,22 @@ __global__ void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int sh
         hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-// Single-CTA exclusive scan of len entries (in place): warp-shuffle scans
-// within each 1024-entry chunk, a carry between chunks.
-__global__ void k_sort_scan(uint32_t* __restrict__ a, int64_t len)
+// One CTA per digit: exclusive scan of that digit's per-tile counts (in place,
+// hist[d * ntiles + tile]) and the digit's total in tot[d].
+__global__ void k_sort_rowscan(uint32_t* __restrict__ hist, int ntiles, uint32_t* __restrict__ tot)
 {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* a = hist + (int64_t)blockIdx.x * ntiles;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < len; base += 1024) {
-        int64_t i = base + threadIdx.x;
-        uint32_t v = (i < len) ? a[i] : 0u;
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = (i < ntiles) ? a[i] : 0u;
         uint32_t x = v;
         for (int off = 1; off < 32; off <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
             if (lane >= off) x += t;
         }
         if (lane == 31) wsum[warp] = x;
@@ -89,31 +91,45 @@ __global__ void k_sort_scan(uint32_t* __restrict__ a, int64_t len)
         if (warp == 0) {
             uint32_t y = wsum[lane];
             for (int off = 1; off < 32; off <<= 1) {
-                uint32_t t = __shfl_up_sync(0xffffffffu, y, off);
+                const uint32_t t = __shfl_up_sync(0xffffffffu, y, off);
                 if (lane >= off) y += t;
             }
-            wsum[lane] = y;   // inclusive prefix of warp totals
+            wsum[lane] = y;
         }
         __syncthreads();
-        uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u);
-        if (i < len) a[i] = carry + incl - v;
+        const uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u);
+        if (i < ntiles) a[i] = carry + incl - v;
         __syncthreads();
         if (threadIdx.x == 1023) carry += incl;
         __syncthreads();
     }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
 __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                                int64_t n, int shift, int ntiles,
-                               const uint32_t* __restrict__ offs, uint64_t* __restrict__ kout,
-                               int32_t* __restrict__ vout)
+                               const uint32_t* __restrict__ offs, const uint32_t* __restrict__ tot,
+                               uint64_t* __restrict__ kout, int32_t* __restrict__ vout)
 {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t base[kRadix];            // running position of each digit in this tile
     __shared__ uint32_t wcnt[kWarps][kRadix];    // per-warp counts, then per-warp prefixes
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-        base[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    // start of each digit's bucket: exclusive scan of the 256 digit totals
+    {
+        const uint32_t v = tot[threadIdx.x];     // blockDim.x == kRadix
+        uint32_t x = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += t;
+        }
+        if (lane == 31) wcnt[0][warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += wcnt[0][w];
+        base[threadIdx.x] = pre + x - v + offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
@@ -174,6 +190,23 @@ __global__ void k_scatter(const double* __restrict__ gs, const int32_t* __restri
         g[(int64_t)perm[i] * stride + comp] = gs[i];
 }
 
+// s[k] = max{j : omega_k * r_j <= z} (or -1): the boundary of the local region
+// in row k of the sorted matrix (non-increasing in k).  Binary search per row.
+__global__ void k_staircase(const double* __restrict__ r, int64_t n, const double* __restrict__ w,
+                            int64_t m, double z, int32_t* __restrict__ s)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double wk = w[k];
+        int64_t lo = 0, hi = n;   // first j with wk * r_j > z
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (wk * r[mid] <= z) lo = mid + 1; else hi = mid;
+        }
+        s[k] = (int32_t)(lo - 1);
+    }
+}
+
 inline int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -197,7 +230,8 @@ size_t radix_sort_scratch_bytes(int64_t n)
 {
     int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     return 2 * align256(sizeof(uint64_t) * (size_t)n) + align256(sizeof(int32_t) * (size_t)n) +
-           align256(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ntiles > 0 ? ntiles : 1));
+           align256(sizeof(uint32_t) * (size_t)kRadix * (size_t)(ntiles > 0 ? ntiles : 1)) +
+           align256(sizeof(uint32_t) * (size_t)kRadix);
 }
 
 // Sorts in[0..n) ascending into out, perm[i] = input index of out[i].
@@ -211,7 +245,8 @@ cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* pe
     uint64_t* k0 = (uint64_t*)p; p += align256(sizeof(uint64_t) * (size_t)n);
     uint64_t* k1 = (uint64_t*)p; p += align256(sizeof(uint64_t) * (size_t)n);
     int32_t* v1 = (int32_t*)p; p += align256(sizeof(int32_t) * (size_t)n);
-    uint32_t* hist = (uint32_t*)p;
+    uint32_t* hist = (uint32_t*)p; p += align256(sizeof(uint32_t) * (size_t)kRadix * (size_t)ntiles);
+    uint32_t* tot = (uint32_t*)p;
     int32_t* v0 = perm;   // ping-pong between perm and v1; 8 passes end in perm
     k_sort_init<<<grid_for(n, 256), 256, 0, s>>>(in, n, k0, v0);
     uint64_t* ka = k0; uint64_t* kb = k1;
@@ -219,14 +254,23 @@ cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* pe
     for (int pass = 0; pass < 8; ++pass) {
         int shift = 8 * pass;
         k_sort_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist);
-        k_sort_scan<<<1, 1024, 0, s>>>(hist, (int64_t)kRadix * ntiles);
-        k_sort_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, n, shift, ntiles, hist, kb, vb);
+        k_sort_rowscan<<<kRadix, 1024, 0, s>>>(hist, ntiles, tot);
+        k_sort_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, n, shift, ntiles, hist, tot, kb, vb);
         uint64_t* tk = ka; ka = kb; kb = tk;
         int32_t* tv = va; va = vb; vb = tv;
     }
     // after an even number of passes the data is back in (k0, perm)
     k_sort_finish<<<grid_for(n, 256), 256, 0, s>>>(ka, n, out);
     count_launches(2 + 8 * 3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_t m, double z,
+                             int32_t* s_out, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_staircase<<<grid_for(m, 256), 256, 0, s>>>(r, n, w, m, z, s_out);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ struct HostTables {
     int w = 0, deg = 0;
     double beta = 0.0;
     std::vector<double> es;     // [w][deg + 1]
+    std::vector<float2> es2;    // the same split into (hi, lo) floats
     int ph_pieces = 0, ph_deg = 0;
     double ph_scale = 0.0, ph_xmax = 0.0;
     std::vector<double> ph;     // [ph_pieces][ph_deg + 1]
@@ -35,10 +36,15 @@ struct HBlock {
     int64_t k0, k1, j0, j1;
 };
 
-// Algorithm 1 with SplitIndices; r, w sorted ascending (local indices).
-void subdivide(const double* r, int64_t n, const double* w, int64_t m, double z, int64_t min_size,
-               int n_cand, std::vector<HBlock>& loc, std::vector<HBlock>& asy,
-               std::vector<HBlock>& dir);
+// Algorithm 1 with SplitIndices on the sorted matrix, from the staircase
+// stair[k] = max{j : omega_k r_j <= z} (or -1) of every row.
+void subdivide(const int32_t* stair, int64_t n, int64_t m, int64_t min_size, int n_cand,
+               std::vector<HBlock>& loc, std::vector<HBlock>& asy, std::vector<HBlock>& dir);
+
+// Device memory from the library's pool (kept reserved between plans) and
+// pinned host staging buffers (grow-only, used under stage_lock()).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
 
 inline int spread_tile_points(int qmax) { return qmax > 16 ? 128 : 256; }
 constexpr int kInterpTile = 128;

@@ -29,6 +29,7 @@ struct ProbParams {
     double z;      // crossover
     double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
     double a[kMaxQ];             // Hankel coefficients a_q(nu), q < Q
+    float2 a2[kMaxQ];            // the same as double-float (hi, lo)
     int64_t r_off, w_off;        // offsets of this problem in the sorted arrays
     int64_t n, m;
     int64_t c_off, g_off;        // offsets of this problem's c and g (batched)
@@ -78,6 +79,7 @@ struct FftItem {
 // Kernel tables shared by every asymptotic block of a plan.
 struct Tables {
     const double* es;      // [w][deg + 1] monomial coefficients in v = 2 z0 - 1
+    const float2* es2;     // the same as double-float (hi, lo)
     int w, deg;
     double half_w;         // w / 2
     const double* ph;      // psi-hat pieces [ph_pieces][ph_deg + 1] in v in [-1, 1]
@@ -97,6 +99,8 @@ cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* pe
                            void* scratch, size_t scratch_bytes, cudaStream_t s);
 size_t radix_sort_scratch_bytes(int64_t n);
 
+cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_t m, double z,
+                             int32_t* s_out, cudaStream_t s);
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
                           double* out, cudaStream_t s);
 cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
@@ -117,13 +121,13 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
                               const double* c_s, double2* grid_b, cudaStream_t s);
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const FftItem* items,
                                  int nitems, int max_nf2, Tables tab, const double2* grid_b,
-                                 double2* grid_q, cudaStream_t s);
+                                 float4* grid_q, cudaStream_t s);
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const FftItem* items_a,
                                  int nitems_a, const FftItem* items_b, int nitems_b, Tables tab,
-                                 const double2* grid_b, double2* tmp, double2* grid_q,
+                                 const double2* grid_b, double2* tmp, float4* grid_q,
                                  cudaStream_t s);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, Tables tab, const double* w_s, const double2* grid_q,
+                              int ntiles, Tables tab, const double* w_s, const float4* grid_q,
                               double* g_s, cudaStream_t s);
 
 }  // namespace nuht

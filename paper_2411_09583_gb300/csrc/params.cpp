@@ -197,6 +197,11 @@ const HostTables& kernel_tables(int w)
         auto f = [&](double v) { return es_kernel(-1.0 + ((v + 1.0) * 0.5 + i) * 2.0 / w, T.beta); };
         cheb_monomial(f, T.deg, &T.es[(size_t)i * (T.deg + 1)]);
     }
+    T.es2.resize(T.es.size());
+    for (size_t i = 0; i < T.es.size(); ++i) {
+        const float hi = (float)T.es[i];
+        T.es2[i] = make_float2(hi, (float)(T.es[i] - (double)hi));
+    }
     // psi^ on [0, xmax], xmax slightly above w pi / 4 (the largest argument used)
     std::vector<double> gx, gw;
     gauss_legendre(160, gx, gw);

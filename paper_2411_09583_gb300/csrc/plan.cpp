@@ -2,6 +2,7 @@
 // (Algorithm 2 on the device), info and helpers.
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -67,7 +68,8 @@ struct nuht_plan_s {
     FftItem *d_fsmall = nullptr, *d_fa = nullptr, *d_fb = nullptr;
     DirectBlock* d_dir = nullptr;
     double* d_mom = nullptr;
-    double2 *d_gb = nullptr, *d_gq = nullptr, *d_gtmp = nullptr;
+    double2 *d_gb = nullptr, *d_gtmp = nullptr;
+    float4* d_gq = nullptr;   // FFT output, complex values as double-float parts
     double *d_cs = nullptr, *d_gs = nullptr;
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
@@ -89,8 +91,71 @@ struct nuht_plan_s {
 };
 
 namespace nuht {
+
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+constexpr int kMaxDev = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDev] = {};
+}  // namespace
+
+// One memory pool per device, owned by the library, whose release threshold
+// keeps freed plan memory reserved for the next plan (no re-mapping per plan).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pool[dev], &props);
+            if (e != cudaSuccess) { g_pool[dev] = nullptr; return e; }
+            uint64_t thr = ~(uint64_t)0;
+            e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+            if (e != cudaSuccess) return e;
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
+
+void pool_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+}  // namespace nuht
+
+namespace {
+
+// Pinned host staging buffers (grow-only), used by one plan build at a time.
+struct Staging {
+    char* p = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes + bytes / 2 + (1 << 20);
+        cudaError_t e = cudaMallocHost((void**)&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+};
+std::mutex g_stage_mu;
+Staging g_stage_in, g_stage_out;
+
+}  // namespace
 
 namespace {
 
@@ -175,7 +240,7 @@ void nuht_destroy(nuht_plan_t p)
 {
     if (!p) return;
     if (p->dmem) {
-        cudaFreeAsync(p->dmem, p->stream);
+        pool_free(p->dmem, p->stream);
         cudaStreamSynchronize(p->stream);
     }
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
@@ -213,15 +278,16 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     Arena sa;
     size_t o_r = sa.reserve<double>(n), o_w = sa.reserve<double>(m);
     size_t o_pr = sa.reserve<int32_t>(n), o_pw = sa.reserve<int32_t>(m);
+    size_t o_st = sa.reserve<int32_t>(m);
     size_t o_flag = sa.reserve<int>(2);
     size_t o_scr = sa.size;
     size_t scr = radix_sort_scratch_bytes(n > m ? n : m);
     sa.size += align256(scr);
     char* sort_mem = nullptr;
-    NUHT_CK(cudaMallocAsync((void**)&sort_mem, sa.size, s));
+    NUHT_CK(pool_alloc((void**)&sort_mem, sa.size, s));
     struct Free {
         char* p; cudaStream_t s;
-        ~Free() { if (p) cudaFreeAsync(p, s); }
+        ~Free() { pool_free(p, s); }
     } free_sort{sort_mem, s};
     int* d_flag = (int*)(sort_mem + o_flag);
     NUHT_CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * 2, s));
@@ -231,19 +297,30 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     double* w_s = (double*)(sort_mem + o_w);
     int32_t* pr = (int32_t*)(sort_mem + o_pr);
     int32_t* pw = (int32_t*)(sort_mem + o_pw);
+    int32_t* stair = (int32_t*)(sort_mem + o_st);
     NUHT_CK(radix_sort_f64(r, n, r_s, pr, sort_mem + o_scr, scr, s));
     NUHT_CK(radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr, scr, s));
-    std::vector<double> hr((size_t)n), hw((size_t)m);
-    int hflag[2] = {0, 0};
-    NUHT_CK(cudaMemcpyAsync(hflag, d_flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
-    if (n) NUHT_CK(cudaMemcpyAsync(hr.data(), r_s, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (m) NUHT_CK(cudaMemcpyAsync(hw.data(), w_s, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    NUHT_CK(launch_staircase(r_s, n, w_s, m, pp.z, stair, s));
+    // sorted values (block geometry) and the staircase (subdivision) to pinned host memory
+    std::lock_guard<std::mutex> stage_lock(g_stage_mu);
+    const size_t in_bytes = align256(8) + align256(sizeof(double) * n) + align256(sizeof(double) * m) +
+                            align256(sizeof(int32_t) * m);
+    NUHT_CK(g_stage_in.reserve(in_bytes));
+    int* hflag = (int*)g_stage_in.p;
+    double* hr_p = (double*)(g_stage_in.p + align256(8));
+    double* hw_p = (double*)((char*)hr_p + align256(sizeof(double) * n));
+    int32_t* hst = (int32_t*)((char*)hw_p + align256(sizeof(double) * m));
+    NUHT_CK(cudaMemcpyAsync(hflag, d_flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    if (n) NUHT_CK(cudaMemcpyAsync(hr_p, r_s, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (m) NUHT_CK(cudaMemcpyAsync(hw_p, w_s, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    if (m) NUHT_CK(cudaMemcpyAsync(hst, stair, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
     NUHT_CK(cudaStreamSynchronize(s));
     if (hflag[0] || hflag[1]) return NUHT_ERR_DOMAIN;
+    const double* hr = hr_p;
+    const double* hw = hw_p;
 
     // ---- subdivision (host, Algorithm 1) --------------------------------
-    subdivide(hr.data(), n, hw.data(), m, pp.z, P->opt.min_size, P->opt.n_split_cand, P->hb[0],
-              P->hb[1], P->hb[2]);
+    subdivide(hst, n, m, P->opt.min_size, P->opt.n_split_cand, P->hb[0], P->hb[1], P->hb[2]);
     const auto& LB = P->hb[0];
     const auto& AB = P->hb[1];
     const auto& DB = P->hb[2];
@@ -265,7 +342,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         LocalBlock lb{};
         lb.prob = 0;
         lb.k0 = (int32_t)h.k0; lb.k1 = (int32_t)h.k1; lb.j0 = (int32_t)h.j0; lb.j1 = (int32_t)h.j1;
-        lb.R = hr[(size_t)h.j1];
+        lb.R = hr[h.j1];
         lb.mom_off = mom_off;
         mom_off += pp.L + 1;
         vloc.push_back(lb);
@@ -287,8 +364,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         AsyBlock ab{};
         ab.prob = 0;
         ab.k0 = (int32_t)h.k0; ab.k1 = (int32_t)h.k1; ab.j0 = (int32_t)h.j0; ab.j1 = (int32_t)h.j1;
-        const double rlo = hr[(size_t)h.j0], rhi = hr[(size_t)h.j1];
-        const double wlo = hw[(size_t)h.k0], whi = hw[(size_t)h.k1];
+        const double rlo = hr[h.j0], rhi = hr[h.j1];
+        const double wlo = hw[h.k0], whi = hw[h.k1];
         ab.rc = 0.5 * (rlo + rhi);
         const double X = 0.5 * (rhi - rlo);
         ab.wc = 0.5 * (wlo + whi);
@@ -364,6 +441,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_fb = A.reserve<FftItem>(vfb.size());
     size_t a_dir = A.reserve<DirectBlock>(vdir.size());
     size_t a_es = A.reserve<double>(T.es.size()), a_ph = A.reserve<double>(T.ph.size());
+    size_t a_es2 = A.reserve<float2>(T.es2.size());
     size_t a_tw = A.reserve<double2>(T.tw.size());
     size_t host_part = A.size;   // everything above is uploaded from one staging buffer
     size_t a_mom = A.reserve<double>((size_t)P->mom_len);
@@ -371,12 +449,13 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_gq = A.reserve<double2>((size_t)P->gq_len);
     size_t a_gt = A.reserve<double2>(P->has_large_fft ? (size_t)P->gq_len : 1);
     size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
-    NUHT_CK(cudaMallocAsync((void**)&P->dmem, A.size, s));
+    NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
-    std::vector<char> stage(host_part, 0);
+    NUHT_CK(g_stage_out.reserve(host_part));
+    char* stage = g_stage_out.p;
     auto put = [&](size_t off, const void* src, size_t bytes) {
-        if (bytes) std::memcpy(stage.data() + off, src, bytes);
+        if (bytes) std::memcpy(stage + off, src, bytes);
     };
     put(a_prob, &pp, sizeof(pp));
     put(a_loc, vloc.data(), sizeof(LocalBlock) * vloc.size());
@@ -390,9 +469,10 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     put(a_fb, vfb.data(), sizeof(FftItem) * vfb.size());
     put(a_dir, vdir.data(), sizeof(DirectBlock) * vdir.size());
     put(a_es, T.es.data(), sizeof(double) * T.es.size());
+    put(a_es2, T.es2.data(), sizeof(float2) * T.es2.size());
     put(a_ph, T.ph.data(), sizeof(double) * T.ph.size());
     put(a_tw, T.tw.data(), sizeof(double2) * T.tw.size());
-    NUHT_CK(cudaMemcpyAsync(D, stage.data(), host_part, cudaMemcpyHostToDevice, s));
+    NUHT_CK(cudaMemcpyAsync(D, stage, host_part, cudaMemcpyHostToDevice, s));
     // sorted arrays and permutations stay on the device
     P->d_r = (double*)(D + a_r); P->d_w = (double*)(D + a_w);
     P->d_pr = (int32_t*)(D + a_pr); P->d_pw = (int32_t*)(D + a_pw);
@@ -413,10 +493,11 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_dir = (DirectBlock*)(D + a_dir);
     P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
     P->d_mom = (double*)(D + a_mom);
-    P->d_gb = (double2*)(D + a_gb); P->d_gq = (double2*)(D + a_gq); P->d_gtmp = (double2*)(D + a_gt);
+    P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (double2*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
     Tables& tb = P->tab;
-    tb.es = P->d_es; tb.w = T.w; tb.deg = T.deg; tb.half_w = 0.5 * T.w;
+    tb.es = P->d_es; tb.es2 = (const float2*)(D + a_es2);
+    tb.w = T.w; tb.deg = T.deg; tb.half_w = 0.5 * T.w;
     tb.ph = P->d_ph; tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
     tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
     tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
@@ -463,7 +544,11 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
     const double phi = -(2.0 * anu + 1.0) * M_PI / 4.0;
     pp.cphi = std::cos(phi);
     pp.sphi = std::sin(phi);
-    for (int q = 0; q < kMaxQ; ++q) pp.a[q] = q < pp.Q ? hankel_coeff(q, anu) : 0.0;
+    for (int q = 0; q < kMaxQ; ++q) {
+        pp.a[q] = q < pp.Q ? hankel_coeff(q, anu) : 0.0;
+        const float hi = (float)pp.a[q];
+        pp.a2[q] = make_float2(hi, (float)(pp.a[q] - (double)hi));
+    }
     pp.r_off = 0; pp.w_off = 0; pp.n = n; pp.m = m; pp.c_off = 0; pp.g_off = 0;
     P->w = nufft_width(eps);
     rc = build_plan(P, r, omega);
@@ -566,7 +651,7 @@ int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega,
     size_t o_r = A.reserve<double>(n), o_w = A.reserve<double>(m);
     size_t o_c = A.reserve<double>((size_t)n * nvec), o_g = A.reserve<double>((size_t)m * nvec);
     char* D = nullptr;
-    NUHT_CK(cudaMallocAsync((void**)&D, A.size, s));
+    NUHT_CK(pool_alloc((void**)&D, A.size, s));
     int rc = NUHT_OK;
     nuht_plan_t P = nullptr;
     do {
@@ -584,7 +669,7 @@ int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega,
         if (e != cudaSuccess) { g_cuda_msg = cudaGetErrorString(e); rc = NUHT_ERR_CUDA; break; }
     } while (0);
     nuht_destroy(P);
-    cudaFreeAsync(D, s);
+    pool_free(D, s);
     cudaStreamSynchronize(s);
     return rc;
 }

@@ -22,24 +22,13 @@
 
 namespace nuht {
 
-namespace {
-
-int64_t last_local_col(const double* r, double w, double z, int64_t j0, int64_t j1)
+void subdivide(const int32_t* stair, int64_t n, int64_t m, int64_t min_size, int n_cand,
+               std::vector<HBlock>& loc, std::vector<HBlock>& asy, std::vector<HBlock>& dir)
 {
-    int64_t lo = j0, hi = j1 + 1;   // first j with w r_j > z
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if (w * r[mid] <= z) lo = mid + 1; else hi = mid;
-    }
-    return lo - 1;
-}
-
-}  // namespace
-
-void subdivide(const double* r, int64_t n, const double* w, int64_t m, double z, int64_t min_size,
-               int n_cand, std::vector<HBlock>& loc, std::vector<HBlock>& asy,
-               std::vector<HBlock>& dir)
-{
+    // stair[k] = max{j : omega_k r_j <= z} over the whole sorted r (or -1), so
+    // within columns j0..j1: last local column = min(stair[k], j1), or j0 - 1
+    // when stair[k] < j0; a block is all local iff stair[k1] >= j1 and all
+    // asymptotic iff stair[k0] < j0 (stair is non-increasing in k).
     loc.clear();
     asy.clear();
     dir.clear();
@@ -48,8 +37,8 @@ void subdivide(const double* r, int64_t n, const double* w, int64_t m, double z,
     auto place = [&](int64_t k0, int64_t k1, int64_t j0, int64_t j1) {
         if (k1 < k0 || j1 < j0) return;
         const HBlock b{k0, k1, j0, j1};
-        if (w[k1] * r[j1] <= z) { loc.push_back(b); return; }
-        if (w[k0] * r[j0] > z) { asy.push_back(b); return; }
+        if (stair[k1] >= j1) { loc.push_back(b); return; }
+        if (stair[k0] < j0) { asy.push_back(b); return; }
         if ((k1 - k0 + 1) * (j1 - j0 + 1) <= min_size) { dir.push_back(b); return; }
         work.push_back(b);
     };
@@ -62,7 +51,9 @@ void subdivide(const double* r, int64_t n, const double* w, int64_t m, double z,
         const int64_t ncand = rows <= n_cand ? rows : n_cand;
         for (int64_t c = 0; c < ncand; ++c) {
             const int64_t k = rows <= n_cand ? b.k0 + c : b.k0 + (c * (b.k1 - b.k0)) / (n_cand - 1);
-            const int64_t j = last_local_col(r, w[k], z, b.j0, b.j1);
+            int64_t j = stair[k];
+            if (j > b.j1) j = b.j1;
+            if (j < b.j0) j = b.j0 - 1;
             const int64_t area = (k - b.k0 + 1) * (b.j1 - j) + (b.k1 - k) * (j - b.j0 + 1);
             if (best_area < 0 || area < best_area) {
                 best_area = area;
