@@ -7,7 +7,11 @@
 // C_l(x) = delta_l J_{nu/2+l}(x/2) J_{nu/2-l}(x/2) for even nu and
 // 2 J_{(nu+1)/2+l}(x/2) J_{(nu-1)/2-l}(x/2) with T_{2l+1} for odd nu (the
 // argument x/2 follows the proof of Lemma 3.1; the odd form is Graf's addition
-// theorem with both arguments x/2).  All in FP64.
+// theorem with both arguments x/2).
+//
+// Arithmetic: the Chebyshev recurrences, the Miller recurrence and the sums
+// run in double-float (df64.cuh, ~48 bits on the FP32 pipes); coordinates,
+// normalisation and the rare small-argument rows in FP64.
 //
 // Direct blocks are small mixed blocks summed entry by entry with a device
 // J_nu: Miller recurrence (or the power series) where omega r <= z, and the
@@ -16,6 +20,7 @@
 #include <cstdint>
 
 #include "device_math.cuh"
+#include "df64.cuh"
 #include "nuht_internal.h"
 
 namespace nuht {
@@ -24,35 +29,51 @@ namespace {
 
 constexpr int kMomThreads = 128;
 
+__device__ __forceinline__ df df_neg(df a) { return df{-a.h, -a.l}; }
+__device__ __forceinline__ df df_scale(df a, float p2) { return df{a.h * p2, a.l * p2}; }
+
+// |v| > 2^60: the double-float Miller recurrence rescales by 2^-60 (exact)
+__device__ __forceinline__ bool df_big(df v) { return fabsf(v.h) > 1.152921504606847e18f; }
+
+// (double)i * inv2y as double-float, with inv2y = (ih, il)
+__device__ __forceinline__ df df_imul(float fi, float ih, float il)
+{
+    const float p = fi * ih;
+    float e = fmaf(fi, ih, -p);
+    e = fmaf(fi, il, e);
+    return fast_two_sum(p, e);
+}
+
 // One CTA per tile of columns of one local block.  Each thread keeps its own
-// column of partial moments in shared memory (acc[l * blockDim + tid]); the
-// columns are summed at the end and added to the block's moments.
+// column of partial moments (compensated double-float accumulators) in shared
+// memory, acc[l * blockDim + tid]; the columns are summed in FP64 at the end
+// and added to the block's moments.
 __global__ void __launch_bounds__(kMomThreads)
 k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
                 const Tile* __restrict__ tiles, const double* __restrict__ r_s,
                 const double* __restrict__ c_s, double* __restrict__ mom)
 {
-    extern __shared__ double acc[];
+    extern __shared__ acc2 acc[];
     const Tile t = tiles[blockIdx.x];
     const LocalBlock B = blks[t.blk];
     const int L = probs[B.prob].L;
     const int odd = probs[B.prob].nu & 1;
     const int nt = blockDim.x, tid = threadIdx.x;
-    for (int l = 0; l <= L; ++l) acc[l * nt + tid] = 0.0;
+    for (int l = 0; l <= L; ++l) acc[l * nt + tid] = acc2{0.f, 0.f};
     const double invR = B.R > 0.0 ? 1.0 / B.R : 0.0;
     for (int64_t j = t.start + tid; j < t.start + t.count; j += nt) {
         const double y = r_s[j] * invR;
-        const double cj = c_s[j];
+        const df cj = df_from(c_s[j]);
         const double u = fma(2.0 * y, y, -1.0);   // T_2(y)
-        const double u2 = 2.0 * u;
+        const df u2 = df_from(2.0 * u);
         // even: T_{2l}(y) = T_l(u); odd: T_{2l+1}(y) with T_1 = y, T_3 = y (2u - 1)
-        double t0 = odd ? y : 1.0;
-        double t1 = odd ? y * (u2 - 1.0) : u;
-        acc[tid] += cj * t0;
-        if (L >= 1) acc[nt + tid] += cj * t1;
+        df t0 = odd ? df_from(y) : df{1.f, 0.f};
+        df t1 = odd ? df_from(y * (2.0 * u - 1.0)) : df_from(u);
+        acc_fma(acc[tid], cj, t0);
+        if (L >= 1) acc_fma(acc[nt + tid], cj, t1);
         for (int l = 2; l <= L; ++l) {
-            double t2 = fma(u2, t1, -t0);
-            acc[l * nt + tid] = fma(cj, t2, acc[l * nt + tid]);
+            const df t2 = df_add(df_mul(u2, t1), df_neg(t0));
+            acc_fma(acc[l * nt + tid], cj, t2);
             t0 = t1;
             t1 = t2;
         }
@@ -61,11 +82,61 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     for (int l = warp; l <= L; l += nw) {
         double s = 0.0;
-        for (int k = lane; k < nt; k += 32) s += acc[l * nt + k];
+        for (int k = lane; k < nt; k += 32) s += acc_value(acc[l * nt + k]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if (lane == 0) atomicAdd(&mom[B.mom_off + l], s);
     }
+}
+
+// J_0..J_ntop(y), unnormalised, into this thread's column jb[n * nt + tid]
+// (double-float); returns the normalisation S = J_0 + 2 sum_k J_2k of the same
+// scale.  Miller's backward recurrence from ns (even), rescaled by 2^-60
+// whenever a value passes 2^60.  Needs y >= 1 (growth per step <= 2 ns / y).
+__device__ __forceinline__ df miller_store_df(double y, int ntop, int ns, float2* jb, int nt, int tid)
+{
+    const double inv2y = 2.0 / y;
+    const float ih = (float)inv2y, il = (float)(inv2y - (double)ih);
+    df jp1{0.f, 0.f}, jc{1.f, 0.f}, S{2.f, 0.f};
+    if (ns <= ntop) jb[ns * nt + tid] = make_float2(jc.h, jc.l);
+    for (int i = ns; i >= 2; i -= 2) {
+        const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
+        const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
+        if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = make_float2(jm.h, jm.l);
+        if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = make_float2(jmm.h, jmm.l);
+        S = df_add(S, df{2.f * jmm.h, 2.f * jmm.l});
+        jp1 = jm;
+        jc = jmm;
+        if (df_big(jc)) {
+            const float sc = 8.673617379884035e-19f;   // 2^-60
+            jc = df_scale(jc, sc); jp1 = df_scale(jp1, sc); S = df_scale(S, sc);
+            const int top = ntop < ns ? ntop : ns;
+            for (int q = i - 2; q <= top; ++q) {
+                const float2 v = jb[q * nt + tid];
+                jb[q * nt + tid] = make_float2(v.x * sc, v.y * sc);
+            }
+        }
+    }
+    return df_add(S, df_neg(jc));   // J_0 was added with weight 2; it counts once
+}
+
+// Small arguments (y < 1): J_0..J_ntop(y) directly from the power series
+// (DLMF 10.2.2) in FP64, stored as double-float; already normalised (returns 1).
+__device__ __forceinline__ double series_store_fp64(double y, int ntop, float2* jb, int nt, int tid)
+{
+    const double h = 0.5 * y, q = -h * h;
+    double lead = 1.0;   // (y/2)^n / n!
+    for (int n = 0; n <= ntop; ++n) {
+        if (n > 0) lead *= h / (double)n;
+        double term = lead, sum = lead;
+        for (int k = 1; k <= 12; ++k) {
+            term *= q / ((double)k * (double)(n + k));
+            sum += term;
+        }
+        const float fh = (float)sum;
+        jb[n * nt + tid] = make_float2(fh, (float)(sum - (double)fh));
+    }
+    return 1.0;
 }
 
 // One thread per row of a local block.  J_0..J_ntop(x/2) by Miller's backward
@@ -75,63 +146,80 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
                              const Tile* __restrict__ tiles, const double* __restrict__ w_s,
                              const double* __restrict__ mom, double* __restrict__ g_s)
 {
-    extern __shared__ double jb[];
+    extern __shared__ float2 sm2[];
     const Tile t = tiles[blockIdx.x];
     const LocalBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
     const int nt = blockDim.x, tid = threadIdx.x;
+    const int nu = P.nu, L = P.L;
+    float2* mu = sm2;                 // [L + 1] moments of this block, double-float
+    float2* jb = sm2 + (P.ntop + 1);  // [ntop + 1][nt]
+    for (int l = tid; l <= L; l += nt) {
+        const double v = mom[B.mom_off + l];
+        const float h = (float)v;
+        mu[l] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
     if (tid >= t.count) return;
     const int64_t k = t.start + tid;
-    const int nu = P.nu, L = P.L;
-    const double* mu = mom + B.mom_off;
     const double x = w_s[k] * B.R;
     const double y = 0.5 * x;
     double val;
     if (y < 1e-100) {
         // J_n(y) = delta_n0 to far below rounding: only C_0 survives, and only for nu = 0
-        val = (nu == 0) ? mu[0] : 0.0;
+        val = (nu == 0) ? (double)mu[0].x + (double)mu[0].y : 0.0;
     } else {
         const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
         const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
         const int ntop = hp + L;
         const int ns = miller_start(ntop, y);
-        const double inv2y = 2.0 / y;
-        double jp1 = 0.0, jc = 1.0, S = 2.0;
-        if (ns <= ntop) jb[ns * nt + tid] = jc;
-        for (int i = ns; i >= 2; i -= 2) {
-            double jm = fma((double)i * inv2y, jc, -jp1);
-            double jmm = fma((double)(i - 1) * inv2y, jm, -jc);
-            if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = jm;
-            if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = jmm;
-            S = fma(2.0, jmm, S);
-            jp1 = jm;
-            jc = jmm;
-            if (too_big(jc)) {
-                const double sc = 1e-150;
-                jc *= sc; jp1 *= sc; S *= sc;
-                int top = ntop < ns ? ntop : ns;
-                for (int q = i - 2; q <= top; ++q) jb[q * nt + tid] *= sc;
-            }
+        df S;
+        if (y >= 1.0) {
+            S = miller_store_df(y, ntop, ns, jb, nt, tid);
+        } else {
+            S = df_from(series_store_fp64(y, ntop, jb, nt, tid));
         }
-        S -= jc;
-        double sum = 0.0;
+        // scale by a power of two near 1/S so that products of two values stay in FP32 range
+        const float p2 = exp2f(-(float)ilogbf(S.h));
+        S = df_scale(S, p2);
+        acc2 sum{0.f, 0.f};
         for (int l = 0; l <= L; ++l) {
-            int a = hp + l;
-            int b = hm - l;
-            double jbv;
-            if (b >= 0) {
-                jbv = jb[b * nt + tid];
-            } else {
-                jbv = jb[(-b) * nt + tid];
-                if ((-b) & 1) jbv = -jbv;
-            }
-            double cl = jb[a * nt + tid] * jbv;
-            if (l > 0 || (nu & 1)) cl *= 2.0;
-            sum = fma(cl, mu[l], sum);
+            const int b = hm - l;
+            const float2 va = jb[(hp + l) * nt + tid];
+            float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
+            float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
+            if (l > 0 || (nu & 1)) sgn *= 2.f;
+            const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
+            acc_fma(sum, cl, df{mu[l].x, mu[l].y});
         }
-        val = sum / (S * S);
+        const double Sd = df_to(S);
+        val = acc_value(sum) / (Sd * Sd);
     }
     atomicAdd(&g_s[k], (double)P.sgn * val);
+}
+
+// J_n(x) for 1 <= x by Miller's recurrence in double-float (no storage).
+__device__ __forceinline__ double jn_miller_df(int n, double x)
+{
+    const int ns = miller_start(n, x);
+    const double inv2x = 2.0 / x;
+    const float ih = (float)inv2x, il = (float)(inv2x - (double)ih);
+    df jp1{0.f, 0.f}, jc{1.f, 0.f}, S{2.f, 0.f}, res{0.f, 0.f};
+    for (int i = ns; i >= 2; i -= 2) {
+        const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
+        const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
+        if (i - 1 == n) res = jm;
+        if (i - 2 == n) res = jmm;
+        S = df_add(S, df{2.f * jmm.h, 2.f * jmm.l});
+        jp1 = jm;
+        jc = jmm;
+        if (df_big(jc)) {
+            const float sc = 8.673617379884035e-19f;   // 2^-60
+            jc = df_scale(jc, sc); jp1 = df_scale(jp1, sc); S = df_scale(S, sc); res = df_scale(res, sc);
+        }
+    }
+    S = df_add(S, df_neg(jc));
+    return df_to(res) / df_to(S);
 }
 
 // One CTA per direct block (area <= min_size): entries in parallel, row sums
@@ -151,7 +239,10 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         const int rr = e / cols, cc = e - rr * cols;
         const double w = w_s[B.k0 + rr], r = r_s[B.j0 + cc];
         const double x = w * r;
-        const double v = (x <= P.z) ? jn_small_arg(P.nu, x) : jn_hankel(P, w, r);
+        double v;
+        if (x > P.z) v = jn_hankel(P, w, r);
+        else if (x < 1.0) v = jn_series(P.nu, x);
+        else v = jn_miller_df(P.nu, x);
         atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
     }
     __syncthreads();
@@ -166,7 +257,7 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
                                  double* mom, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)(lmax + 1) * kMomThreads;
+    size_t smem = sizeof(acc2) * (size_t)(lmax + 1) * kMomThreads;
     cudaError_t e = cudaFuncSetAttribute(k_local_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -190,7 +281,7 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
                                    const double* mom, double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)(ntop_max + 1) * threads;
+    size_t smem = sizeof(float2) * ((size_t)(ntop_max + 1) * threads + (size_t)(ntop_max + 1));
     cudaError_t e = cudaFuncSetAttribute(k_local_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

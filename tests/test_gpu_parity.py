@@ -184,3 +184,17 @@ def test_full_size_sampled_rows(nu):
     ref = oracle.direct_rows(nu, r, omega, c, rows)
     err = np.max(np.abs(g[rows] - ref))
     assert err <= tol(eps, c), (err, tol(eps, c))
+
+
+@pytest.mark.parametrize("nu", [0, 3])
+def test_relative_l2_error_tracks_eps(nu):
+    # Sec. 5.1.3 measures the relative 2-norm error against eps; it follows eps
+    # down to 1e-12 here.  The double-float (~48-bit) loops put a floor near
+    # 1e-13 under it, so at eps = 1e-14 the bound is that floor (the accuracy
+    # contract 10 eps ||c||_1 still holds there, see test_tolerances).
+    r, omega, c = uniform_problem(1000, 1000, omega_max=3000.0, seed=31 + nu)
+    ref = oracle.direct(nu, r, omega, c)
+    for eps in (1e-6, 1e-9, 1e-12, 1e-14):
+        g, _, _ = run_forward(nu, r, omega, c, eps)
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert rel <= max(10 * eps, 3e-13), (eps, rel)
