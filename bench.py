@@ -203,6 +203,11 @@ def _dominant_flops(stage, info, blocks, tab):
     if stage == "local_moments":
         units = float((loc[:, 3] - loc[:, 2] + 1).sum())
         return units * 4 * (L + 1), units
+    if stage == "local_eval":
+        # per row: 2 multiply-adds per Miller step (ns ~ max(L + 8, y + 20 + 4 sqrt y))
+        # and 2 per Wimp term
+        units = float((loc[:, 1] - loc[:, 0] + 1).sum())
+        return units * (4 * (L + 28) + 4 * (L + 1)), units
     return None, None
 
 

@@ -100,6 +100,9 @@ typedef struct {
     int64_t asy_rows_cols;                /* sum over asymptotic blocks of rows + cols */
     int64_t fft_points;                   /* sum over asymptotic blocks of FFT sizes */
     int64_t device_bytes;                 /* device memory held by the plan */
+    double  plan_ms[4];                   /* host wall time of the plan phases: [0] checks, sort
+                                             and copies back, [1] subdivision, [2] work lists,
+                                             [3] upload */
 } nuht_plan_info;
 
 typedef struct nuht_plan_s *nuht_plan_t;

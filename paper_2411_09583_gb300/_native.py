@@ -50,7 +50,8 @@ class NuhtPlanInfo(ctypes.Structure):
                 ("n_local", ctypes.c_int64), ("n_asy", ctypes.c_int64),
                 ("n_direct", ctypes.c_int64), ("direct_entries", ctypes.c_int64),
                 ("local_rows_cols", ctypes.c_int64), ("asy_rows_cols", ctypes.c_int64),
-                ("fft_points", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("fft_points", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("plan_ms", ctypes.c_double * 4)]
 
 
 class NuhtError(RuntimeError):

@@ -60,10 +60,20 @@ __device__ __forceinline__ df df_add(df a, df b)
 // sum runs in FP32 with its rounding errors (TwoProduct, TwoSum) and the low
 // coefficient parts gathered in a correction polynomial; the low part of the
 // argument enters through the first-order term vl p'(vh).
-__device__ __forceinline__ df horner_comp(const float2* __restrict__ c, int deg, float vh, float vl)
+//
+// Degrees above kc (whose coefficients are so small that FP32 rounding of
+// their partial sum stays far below the target accuracy) are summed first in
+// plain FP32; kc >= deg makes every step compensated.
+__device__ __forceinline__ df horner_comp(const float2* __restrict__ c, int deg, float vh, float vl,
+                                          int kc = 1 << 30)
 {
-    float s = c[deg].x, r = c[deg].y, dp = 0.0f;
-    for (int k = deg - 1; k >= 0; --k) {
+    float s = c[deg].x, r = kc >= deg ? c[deg].y : 0.0f, dp = 0.0f;
+    int k = deg - 1;
+    for (; k > kc; --k) {
+        dp = fmaf(dp, vh, s);
+        s = fmaf(s, vh, c[k].x);
+    }
+    for (; k >= 0; --k) {
         dp = fmaf(dp, vh, s);                    // derivative by Horner, FP32 is enough
         const float p = s * vh;
         const float pi = fmaf(s, vh, -p);
@@ -94,5 +104,78 @@ __device__ __forceinline__ void acc_fma(acc2& A, df a, df b)
 }
 
 __device__ __forceinline__ double acc_value(acc2 A) { return (double)A.s + (double)A.c; }
+
+}  // namespace nuht
+
+namespace nuht {
+
+__device__ __forceinline__ df df_negate(df a) { return df{-a.h, -a.l}; }
+
+// 1/a by one Newton step from the FP32 reciprocal (error ~ 2^-47).
+__device__ __forceinline__ df df_recip(df a)
+{
+    const float y0 = 1.0f / a.h;
+    const df p = df_mul(a, df{y0, 0.0f});
+    const float e = (1.0f - p.h) - p.l;
+    return fast_two_sum(y0, y0 * e);
+}
+
+// sqrt(a), a > 0, by one Newton step from the FP32 square root.
+__device__ __forceinline__ df df_sqrt(df a)
+{
+    const float y0 = sqrtf(a.h);
+    const float ph = y0 * y0;
+    const float pl = fmaf(y0, y0, -ph);
+    const float r = ((a.h - ph) - pl) + a.l;
+    return fast_two_sum(y0, r * (0.5f / y0));
+}
+
+// sin and cos of the exact product a*b (a, b doubles, |a*b| up to ~1e12).
+// The product is split exactly (FMA two-product) and reduced modulo pi/2 in
+// FP64 against a two-term pi/2; the remainder |t| <= pi/4 goes to the Taylor
+// series sin t = t sum_k (-t^2)^k/(2k+1)!, cos t = sum_k (-t^2)^k/(2k)!, summed
+// in double-float (truncation below 5e-17), then the quadrant is applied.
+__device__ __forceinline__ void df_sincos_prod(double a, double b, df* sn, df* cs)
+{
+    // 1/n! split into float hi + lo parts (odd n for sin, even n for cos)
+    const float2 ks[8] = {{1.0f, 0.0f}, {-0.1666666716337204f, 4.967053879312289e-09f},
+                          {0.008333333767950535f, -4.34617203337595e-10f},
+                          {-0.00019841270113829523f, 2.725596874933456e-12f},
+                          {2.7557318844628753e-06f, 3.793571224297229e-14f},
+                          {-2.5052107943679403e-08f, -4.4176230446483665e-16f},
+                          {1.6059044372074283e-10f, -5.352526511562726e-18f},
+                          {-7.647163609812713e-13f, -1.2200710471178288e-20f}};
+    const float2 kc[9] = {{1.0f, 0.0f}, {-0.5f, 0.0f}, {0.0416666679084301f, -1.2417634698280722e-09f},
+                          {-0.0013888889225199819f, 3.3631094437103215e-11f},
+                          {2.4801587642286904e-05f, -3.40699609366682e-13f},
+                          {-2.755731998149713e-07f, 7.575112209051195e-15f},
+                          {2.0876755879584152e-09f, 1.1082839147459852e-16f},
+                          {-1.147074536050896e-11f, -2.372207689231238e-19f},
+                          {4.7794772561329454e-14f, 7.62544404448643e-22f}};
+    const double kPio2Hi = 1.5707963267948966;       // nearest double to pi/2
+    const double kPio2Lo = 6.123233995736766e-17;    // pi/2 - kPio2Hi
+    const double k2OverPi = 0.6366197723675814;
+    const double p = a * b;
+    const double e = fma(a, b, -p);
+    const double k = rint(p * k2OverPi);
+    double t = fma(-k, kPio2Hi, p);
+    t = fma(-k, kPio2Lo, t) + e;
+    const df x = df_from(t);
+    const df y = df_mul(x, x);
+    df ps{ks[7].x, ks[7].y};
+#pragma unroll
+    for (int i = 6; i >= 0; --i) ps = df_add(df_mul(ps, y), df{ks[i].x, ks[i].y});
+    df pc{kc[8].x, kc[8].y};
+#pragma unroll
+    for (int i = 7; i >= 0; --i) pc = df_add(df_mul(pc, y), df{kc[i].x, kc[i].y});
+    const df s0 = df_mul(x, ps);
+    const int q = (int)((long long)k & 3);
+    switch (q) {
+        case 0: *sn = s0; *cs = pc; break;
+        case 1: *sn = pc; *cs = df_negate(s0); break;
+        case 2: *sn = df_negate(s0); *cs = df_negate(pc); break;
+        default: *sn = df_negate(pc); *cs = s0; break;
+    }
+}
 
 }  // namespace nuht

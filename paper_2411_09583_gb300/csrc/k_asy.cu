@@ -36,6 +36,8 @@ namespace nuht {
 
 namespace {
 
+constexpr int kWinCells = 64;   // grid cells an interpolation tile stages in shared memory
+
 __device__ __forceinline__ double horner(const double* c, int deg, double v)
 {
     double acc = c[deg];
@@ -52,6 +54,18 @@ __device__ __forceinline__ double psihat(const Tables& T, double xi)
     if (piece > T.ph_pieces - 1) piece = T.ph_pieces - 1;
     double v = 2.0 * (t - (double)piece) - 1.0;
     return horner(T.ph + piece * (T.ph_deg + 1), T.ph_deg, v);
+}
+
+// psi^(xi) in double-float from the split table (compensated Horner); xi >= 0.
+__device__ __forceinline__ df psihat_df(const Tables& T, double xi)
+{
+    xi = fabs(xi);
+    const double t = xi * T.ph_scale;
+    int piece = (int)t;
+    if (piece > T.ph_pieces - 1) piece = T.ph_pieces - 1;
+    const double v = 2.0 * (t - (double)piece) - 1.0;
+    const float vh = (float)v, vl = (float)(v - (double)vh);
+    return horner_comp(T.ph2 + piece * (T.ph_deg + 1), T.ph_deg, vh, vl);
 }
 
 // ------------------------------------------------------------------ spread
@@ -89,16 +103,15 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
         const double v = 2.0 * z0 - 1.0;
         const float vh = (float)v, vl = (float)(v - (double)vh);
         for (int i = 0; i < w; ++i) {
-            const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl);
+            const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
         l0s[tid] = (int)lf;
-        double sn, cs;
-        sincos_prod(B.wc, x, &sn, &cs);
-        const double ratio = B.rho / rj;              // (r/rho)^(-1)
-        const double w0 = c_s[j] * sqrt(ratio);       // c_j (r/rho)^(-1/2)
-        const df rat = df_from(ratio);
-        df wr = df_from(w0 * cs), wi = df_from(w0 * sn);
+        df sn, cs;
+        df_sincos_prod(B.wc, x, &sn, &cs);
+        const df rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1)
+        const df w0 = df_mul(df_from(c_s[j]), df_sqrt(rat));            // c_j (r/rho)^(-1/2)
+        df wr = df_mul(w0, cs), wi = df_mul(w0, sn);
         for (int q = 0; q < Q; ++q) {
             aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
             wr = df_mul(wr, rat);
@@ -110,29 +123,60 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     const int span = l0s[cnt - 1] - lfirst + w;
     const int nf1 = 2 * B.N1 + 1;
     double2* gb = grid_b + B.b_off;
-    for (int item = tid; item < span * Q; item += nt) {
-        const int c = item / Q, q = item - c * Q;
+    // Outputs (cell, q), q fastest.  For a dense tile (span of cells close to
+    // the kernel width) every thread walks all the tile's points in lockstep,
+    // so each step reads one row of taps / values (broadcast or contiguous,
+    // no bank conflicts) and skips points whose taps miss its cell.  A sparse
+    // tile (points spread over many cells) instead binary-searches the few
+    // points that reach each cell.  Each output is split between kSub lanes
+    // (halves of the point range) combined by a shuffle, so that more threads
+    // than outputs can work.
+    constexpr int kSub = 2;
+    const bool dense = span <= 2 * w;
+    const int nout = span * Q;
+    const int lane = tid & 31;
+    const int sub = lane & (kSub - 1);
+    const unsigned gmask = 0x3u << (lane & ~(kSub - 1));
+    const int half = (cnt + 1) >> 1;
+    for (int base = tid - sub; base < nout * kSub; base += nt) {
+        const int item = (base + sub) / kSub;   // same item for both lanes of a pair
+        const bool live = item < nout;
+        const int c = live ? item / Q : 0, q = live ? item - c * Q : 0;
         const int cell = lfirst + c;
-        // points with l0 in [cell - w + 1, cell]: l0s is non-decreasing
-        int lo = 0, hi = cnt;
-        const int key = cell - w + 1;
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
-        const int p_lo = lo;
-        hi = cnt;
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] <= cell) lo = mid + 1; else hi = mid; }
-        const int p_hi = lo;
+        int p_lo, p_hi;
+        if (dense) {
+            p_lo = sub * half;
+            p_hi = sub ? cnt : half;
+        } else {
+            int lo = 0, hi = cnt;
+            const int key = cell - w + 1;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
+            const int plo = lo;
+            hi = cnt;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] <= cell) lo = mid + 1; else hi = mid; }
+            const int mid2 = (plo + lo + 1) >> 1;
+            p_lo = sub ? mid2 : plo;
+            p_hi = sub ? lo : mid2;
+        }
+        if (!live) p_hi = p_lo;
         acc2 ar{0.f, 0.f}, ai{0.f, 0.f};
         for (int p = p_lo; p < p_hi; ++p) {
-            const float2 k2 = taps[p * w + (cell - l0s[p])];
-            const float4 av = aval[p * Q + q];
-            const df k{k2.x, k2.y};
-            acc_fma(ar, k, df{av.x, av.y});
-            acc_fma(ai, k, df{av.z, av.w});
+            const int i = cell - l0s[p];
+            if (i >= 0 && i < w) {
+                const float2 k2 = taps[p * w + i];
+                const float4 av = aval[p * Q + q];
+                const df k{k2.x, k2.y};
+                acc_fma(ar, k, df{av.x, av.y});
+                acc_fma(ai, k, df{av.z, av.w});
+            }
         }
+        double vr = acc_value(ar), vi = acc_value(ai);
+        vr += __shfl_down_sync(gmask, vr, 1, kSub);
+        vi += __shfl_down_sync(gmask, vi, 1, kSub);
         const int idx = cell + B.N1;
-        if (p_hi > p_lo && idx >= 0 && idx < nf1) {
-            atomicAdd(&gb[(int64_t)idx * Q + q].x, acc_value(ar));
-            atomicAdd(&gb[(int64_t)idx * Q + q].y, acc_value(ai));
+        if (live && sub == 0 && idx >= 0 && idx < nf1 && (vr != 0.0 || vi != 0.0)) {
+            atomicAdd(&gb[(int64_t)idx * Q + q].x, vr);
+            atomicAdd(&gb[(int64_t)idx * Q + q].y, vi);
         }
     }
 }
@@ -181,21 +225,74 @@ __device__ __forceinline__ float4 split4(double2 v)
 }
 
 __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                                const FftItem* __restrict__ items, Tables tab,
+                                const Tile* __restrict__ items, Tables tab,
                                 const double2* __restrict__ grid_b, float4* __restrict__ grid_q)
 {
     extern __shared__ double2 X[];
-    const FftItem it = items[blockIdx.x];
+    const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
+    const int q = (int)it.start;
     const int N = B.nf2, logN = B.log2nf2;
     const double2* gb = grid_b + B.b_off;
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x)
-        X[__brev(tt) >> (32 - logN)] = corrected_mode(B, tab, gb, Q, it.q, tt);
+        X[__brev(tt) >> (32 - logN)] = corrected_mode(B, tab, gb, Q, q, tt);
     __syncthreads();
     smem_fft(X, logN, tab.tw, tab.tw_log2);
     float4* gq = grid_q + B.q_off;
-    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) gq[(int64_t)tt * Q + it.q] = split4(X[tt]);
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) gq[(int64_t)tt * Q + q] = split4(X[tt]);
+}
+
+// All Q grids of one small block (nf2 * Q <= kFftSmemMax) in one CTA: the
+// deconvolution factor of each mode is computed once and used for every q;
+// the Q transforms share every butterfly stage.
+__global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+                                const Tile* __restrict__ items, Tables tab,
+                                const double2* __restrict__ grid_b, float4* __restrict__ grid_q)
+{
+    extern __shared__ double2 X[];   // [Q][N], each grid bit-reversed
+    const Tile it = items[blockIdx.x];
+    const AsyBlock B = blks[it.blk];
+    const int Q = probs[B.prob].Q;
+    const int N = B.nf2, logN = B.log2nf2, half = N >> 1;
+    const double2* gb = grid_b + B.b_off;
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) {
+        const int l = (tt < half) ? tt : tt - N;
+        const int dst = __brev(tt) >> (32 - logN);
+        if (l < -B.N1 || l > B.N1) {
+            for (int q = 0; q < Q; ++q) X[q * N + dst] = make_double2(0.0, 0.0);
+        } else {
+            const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
+            const double2* src = gb + (int64_t)(l + B.N1) * Q;
+            for (int q = 0; q < Q; ++q) {
+                const double2 v = src[q];
+                X[q * N + dst] = make_double2(v.x * sc, v.y * sc);
+            }
+        }
+    }
+    __syncthreads();
+    for (int st = 0; st < logN; ++st) {
+        const int len = 1 << st;
+        const int tw_shift = tab.tw_log2 - (st + 1);
+        for (int b = threadIdx.x; b < Q * half; b += blockDim.x) {
+            const int q = b >> (logN - 1);
+            const int bb = b & (half - 1);
+            const int pos = bb & (len - 1);
+            const int i0 = q * N + ((bb >> st) << (st + 1)) + pos;
+            const int i1 = i0 + len;
+            const double2 wv = tab.tw[pos << tw_shift];
+            const double2 u = X[i0], v = X[i1];
+            const double2 vw = make_double2(v.x * wv.x - v.y * wv.y, v.x * wv.y + v.y * wv.x);
+            X[i0] = make_double2(u.x + vw.x, u.y + vw.y);
+            X[i1] = make_double2(u.x - vw.x, u.y - vw.y);
+        }
+        __syncthreads();
+    }
+    float4* gq = grid_q + B.q_off;
+    for (int idx = threadIdx.x; idx < N * Q; idx += blockDim.x) {
+        const int tt = idx / Q, q = idx - tt * Q;
+        gq[idx] = split4(X[q * N + tt]);
+    }
 }
 
 // Four-step FFT for nf2 = N1 * N2 > kFftSmemMax, N2 = kFftSmemMax.
@@ -203,20 +300,21 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
 // stored at tmp[n1 + N1 k2].  Pass B (line = k2): FFT over n1 of
 // tmp[n1 + N1 k2], stored at X[k2 + N2 k1].
 __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                                 const FftItem* __restrict__ items, Tables tab,
+                                 const Tile* __restrict__ items, Tables tab,
                                  const double2* __restrict__ grid_b, double2* __restrict__ tmp)
 {
     extern __shared__ double2 X[];
-    const FftItem it = items[blockIdx.x];
+    const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
     const int N = B.nf2;
     const int logN2 = 12, N2 = 1 << logN2;
     const int N1 = N >> logN2;
-    const int n1 = it.line;
+    const int iq = (int)(it.start / N1);
+    const int n1 = (int)(it.start - (int64_t)iq * N1);
     const double2* gb = grid_b + B.b_off;
     for (int n2 = threadIdx.x; n2 < N2; n2 += blockDim.x)
-        X[__brev(n2) >> (32 - logN2)] = corrected_mode(B, tab, gb, Q, it.q, n1 + N1 * n2);
+        X[__brev(n2) >> (32 - logN2)] = corrected_mode(B, tab, gb, Q, iq, n1 + N1 * n2);
     __syncthreads();
     smem_fft(X, logN2, tab.tw, tab.tw_log2);
     double2* tq = tmp + B.q_off;
@@ -226,50 +324,53 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
         const long long num = (2LL * n1 * k2) % (2LL * N);
         sincospi((double)num / (double)N, &s, &c);
         const double2 v = X[k2];
-        tq[(int64_t)(n1 + N1 * k2) * Q + it.q] = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+        tq[(int64_t)(n1 + N1 * k2) * Q + iq] = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
     }
 }
 
 __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                                 const FftItem* __restrict__ items, Tables tab,
+                                 const Tile* __restrict__ items, Tables tab,
                                  const double2* __restrict__ tmp, float4* __restrict__ grid_q)
 {
     extern __shared__ double2 X[];
-    const FftItem it = items[blockIdx.x];
+    const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
     const int N = B.nf2;
     const int logN2 = 12, N2 = 1 << logN2;
     const int logN1 = B.log2nf2 - logN2, N1 = 1 << logN1;
-    const int k2 = it.line;
+    const int iq = (int)(it.start >> logN2);
+    const int k2 = (int)(it.start & (N2 - 1));
     const double2* tq = tmp + B.q_off;
     for (int n1 = threadIdx.x; n1 < N1; n1 += blockDim.x)
-        X[logN1 > 0 ? (__brev(n1) >> (32 - logN1)) : 0] = tq[(int64_t)(n1 + N1 * k2) * Q + it.q];
+        X[logN1 > 0 ? (__brev(n1) >> (32 - logN1)) : 0] = tq[(int64_t)(n1 + N1 * k2) * Q + iq];
     __syncthreads();
     smem_fft(X, logN1, tab.tw, tab.tw_log2);
     float4* gq = grid_q + B.q_off;
     for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x)
-        gq[(int64_t)(k2 + N2 * k1) * Q + it.q] = split4(X[k1]);
+        gq[(int64_t)(k2 + N2 * k1) * Q + iq] = split4(X[k1]);
     (void)N;
 }
 
 // ------------------------------------------------------------ interpolate
 // One thread per frequency: interpolate the 2M FFT grids at theta = s h,
 // deconvolve, post-phase, and combine the Hankel terms into g.
-__global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+__global__ void __launch_bounds__(128, 4) k_asy_interp(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, Tables tab,
                              const double* __restrict__ w_s, const float4* __restrict__ grid_q,
                              double* __restrict__ g_s)
 {
-    extern __shared__ float2 coef2[];
+    extern __shared__ float4 win[];          // [kWinCells][Q] grid cells of this tile
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
     const int w = tab.w, deg = tab.deg;
+    const int Q = P.Q;
+    float2* coef2 = (float2*)(win + kWinCells * Q);
+    int* t0s = (int*)(coef2 + w * (deg + 1));
     for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
-    __syncthreads();
-    if ((int)threadIdx.x >= t.count) return;
-    const int64_t k = t.start + threadIdx.x;
+    const bool valid = (int)threadIdx.x < t.count;
+    const int64_t k = t.start + (valid ? threadIdx.x : 0);
     const double wk = w_s[k];
     const double s = wk - B.wc;
     const double a = s * B.h * B.inv_delta - tab.half_w;
@@ -278,11 +379,28 @@ __global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBloc
     z0 = fmin(fmax(z0, 0.0), 1.0);
     const double v = 2.0 * z0 - 1.0;
     const float vh = (float)v, vl = (float)(v - (double)vh);
+    // the tile's targets are sorted, so their cells form one window
+    const int t0 = (int)tf;
+    if (valid) t0s[threadIdx.x] = t0;
+    __syncthreads();
+    const int wstart = t0s[0];
+    const int wlen = t0s[t.count - 1] - wstart + w;
+    const int mask = B.nf2 - 1;
+    const float4* gq = grid_q + B.q_off;
+    const bool staged = wlen <= kWinCells;
+    if (staged) {
+        for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
+            const int cc = idx / Q;
+            win[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
     float th[kMaxW], tl[kMaxW];
 #pragma unroll
     for (int i = 0; i < kMaxW; ++i) {
         if (i < w) {
-            const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl);
+            const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             th[i] = tp.h;
             tl[i] = tp.l;
         } else {
@@ -290,27 +408,42 @@ __global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBloc
             tl[i] = 0.f;
         }
     }
-    const int t0 = (int)tf;
-    const int mask = B.nf2 - 1;
-    const int Q = P.Q;
-    const float4* gq = grid_q + B.q_off;
-    const double m1 = 1.0 / (wk * B.rho);     // 1/(omega rho) < 1/z
-    const df m1d = df_from(m1);
+    const df m1d = df_recip(df_from(wk * B.rho));   // 1/(omega rho) < 1/z
     // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
     acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
     df mq{1.f, 0.f};
+    const int qs = P.qs;
     for (int q = 0; q < Q; ++q) {
-        acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
+        df prd, pid;
+        if (q < qs) {
+            acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < kMaxW; ++i) {
-            if (i < w) {
-                const float4 gv = gq[(int64_t)((t0 + i) & mask) * Q + q];
-                const df tp{th[i], tl[i]};
-                acc_fma(pr, tp, df{gv.x, gv.y});
-                acc_fma(pi, tp, df{gv.z, gv.w});
+            for (int i = 0; i < kMaxW; ++i) {
+                if (i < w) {
+                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q]
+                                             : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                    const df tp{th[i], tl[i]};
+                    acc_fma(pr, tp, df{gv.x, gv.y});
+                    acc_fma(pi, tp, df{gv.z, gv.w});
+                }
             }
+            prd = fast_two_sum(pr.s, pr.c);
+            pid = fast_two_sum(pi.s, pi.c);
+        } else {
+            // small Hankel term: FP32 interpolation is accurate enough
+            float pr = 0.f, pi = 0.f;
+#pragma unroll
+            for (int i = 0; i < kMaxW; ++i) {
+                if (i < w) {
+                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q]
+                                             : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                    pr = fmaf(th[i], gv.x, pr);
+                    pi = fmaf(th[i], gv.z, pi);
+                }
+            }
+            prd = df{pr, 0.f};
+            pid = df{pi, 0.f};
         }
-        const df prd = fast_two_sum(pr.s, pr.c), pid = fast_two_sum(pi.s, pi.c);
         const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
         // multiply by i^q: (pr + i pi) i^q
         switch (q & 3) {
@@ -321,14 +454,17 @@ __global__ void k_asy_interp(const ProbParams* __restrict__ probs, const AsyBloc
         }
         mq = df_mul(mq, m1d);
     }
-    double sn, cs;
-    sincos_prod(wk, B.rc, &sn, &cs);
-    // e^{i (omega r_c + phi)}
-    const double er = cs * P.cphi - sn * P.sphi;
-    const double ei = sn * P.cphi + cs * P.sphi;
-    const double scale = 0.7978845608028654 * sqrt(m1) * (4.0 / ((double)w * (double)w)) /
-                         psihat(tab, B.alpha * s);
-    const double val = scale * (er * acc_value(tr) - ei * acc_value(ti));
+    df sn, cs;
+    df_sincos_prod(wk, B.rc, &sn, &cs);
+    // Re(e^{i (omega r_c + phi)} T) = Re(e^{i omega r_c} (e^{i phi} T))
+    const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
+    const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
+    const df ur = df_add(df_mul(cph, tre), df_negate(df_mul(sph, tim)));
+    const df ui = df_add(df_mul(sph, tre), df_mul(cph, tim));
+    const df re = df_add(df_mul(cs, ur), df_negate(df_mul(sn, ui)));
+    // sqrt(2/pi) (omega rho)^(-1/2) (4 / w^2) / psi^(alpha s)
+    const df scale = df_mul(df_sqrt(m1d), df_recip(psihat_df(tab, B.alpha * s)));
+    const double val = tab.interp_const * df_to(df_mul(scale, re));
     atomicAdd(&g_s[k], (double)P.sgn * val);
 }
 
@@ -349,7 +485,7 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const FftItem* items,
+cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* grid_b,
                                  float4* grid_q, cudaStream_t s)
 {
@@ -365,8 +501,21 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const FftItem* items_a,
-                                 int nitems_a, const FftItem* items_b, int nitems_b, Tables tab,
+cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
+                                 int nitems, Tables tab, const double2* grid_b, float4* grid_q,
+                                 cudaStream_t s)
+{
+    if (nitems <= 0) return cudaSuccess;
+    size_t smem = sizeof(double2) * (size_t)kFftSmemMax;
+    cudaError_t e = cudaFuncSetAttribute(k_asy_fft_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_asy_fft_block<<<nitems, 256, smem, s>>>(probs, blks, items, tab, grid_b, grid_q);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
+                                 int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
                                  const double2* grid_b, double2* tmp, float4* grid_q,
                                  cudaStream_t s)
 {
@@ -385,11 +534,14 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
 }
 
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, Tables tab, const double* w_s, const float4* grid_q,
+                              int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
                               double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float2) * (size_t)tab.w * (tab.deg + 1);
+    size_t smem = sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
+                  sizeof(int) * 128;
+    cudaError_t e = cudaFuncSetAttribute(k_asy_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_asy_interp<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();

@@ -207,6 +207,24 @@ __global__ void k_staircase(const double* __restrict__ r, int64_t n, const doubl
     }
 }
 
+// Tile i of a list: segment b with prefix[b] <= i < prefix[b + 1] (binary
+// search), then its start and count inside the segment's index range.
+__global__ void k_expand_tiles(const Seg* __restrict__ segs, const int32_t* __restrict__ prefix, int nseg,
+                               int total, Tile* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = nseg;   // last b with prefix[b] <= i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= i) lo = mid; else hi = mid;
+        }
+        const Seg sg = segs[lo];
+        const int64_t start = sg.first + (int64_t)(i - prefix[lo]) * sg.len;
+        const int64_t rem = sg.last - start + 1;
+        out[i] = Tile{sg.blk, (int32_t)(rem < sg.len ? rem : sg.len), start};
+    }
+}
+
 inline int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -270,6 +288,15 @@ cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_
 {
     if (m <= 0) return cudaSuccess;
     k_staircase<<<grid_for(m, 256), 256, 0, s>>>(r, n, w, m, z, s_out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg, int total, Tile* out,
+                                cudaStream_t s)
+{
+    if (total <= 0 || nseg <= 0) return cudaSuccess;
+    k_expand_tiles<<<grid_for(total, 256), 256, 0, s>>>(segs, prefix, nseg, total, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ struct HostTables {
     int ph_pieces = 0, ph_deg = 0;
     double ph_scale = 0.0, ph_xmax = 0.0;
     std::vector<double> ph;     // [ph_pieces][ph_deg + 1]
+    std::vector<float2> ph2;    // the same split into (hi, lo) floats
     int tw_log2 = 0;
     std::vector<double2> tw;
 };

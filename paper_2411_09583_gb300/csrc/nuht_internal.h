@@ -25,9 +25,11 @@ struct ProbParams {
     int nu;        // |nu|
     int sgn;       // (-1)^nu when the user order was negative, else +1
     int M, L, Q;   // Q = 2M
+    int qs;        // terms q >= qs are small enough to be summed in FP32
     int ntop;      // largest Bessel index used by the local evaluation
     double z;      // crossover
     double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
+    float2 cphi2, sphi2;         // the same as double-float
     double a[kMaxQ];             // Hankel coefficients a_q(nu), q < Q
     float2 a2[kMaxQ];            // the same as double-float (hi, lo)
     int64_t r_off, w_off;        // offsets of this problem in the sorted arrays
@@ -71,9 +73,13 @@ struct Tile {
     int64_t start;     // absolute index into the sorted array
 };
 
-// One line of a (batched) FFT: block, weight power q, line index (two-pass only).
-struct FftItem {
-    int32_t blk, q, line, pad;
+// A run of tiles: indices first..last of block blk cut into tiles of len.
+// Tile lists are expanded from these on the device (k_expand_tiles).  FFT work
+// items are tiles of length one whose start is the item's ordinal in its
+// block (q for single-pass FFTs, q * lines + line for the two-pass passes).
+struct Seg {
+    int32_t blk, len;
+    int64_t first, last;
 };
 
 // Kernel tables shared by every asymptotic block of a plan.
@@ -81,8 +87,11 @@ struct Tables {
     const double* es;      // [w][deg + 1] monomial coefficients in v = 2 z0 - 1
     const float2* es2;     // the same as double-float (hi, lo)
     int w, deg;
+    int deg_comp;          // degrees above this one are evaluated in plain FP32
     double half_w;         // w / 2
     const double* ph;      // psi-hat pieces [ph_pieces][ph_deg + 1] in v in [-1, 1]
+    const float2* ph2;     // the same as double-float
+    double interp_const;   // sqrt(2/pi) * 4 / w^2
     int ph_pieces, ph_deg;
     double ph_scale;       // pieces per unit of xi
     double ph_xmax;        // table covers xi in [0, ph_xmax]
@@ -103,6 +112,8 @@ cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_
                              int32_t* s_out, cudaStream_t s);
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
                           double* out, cudaStream_t s);
+cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg, int total, Tile* out,
+                                cudaStream_t s);
 cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
                            double* g, cudaStream_t s);
 
@@ -119,15 +130,18 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* r_s,
                               const double* c_s, double2* grid_b, cudaStream_t s);
-cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const FftItem* items,
+cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* grid_b,
                                  float4* grid_q, cudaStream_t s);
-cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const FftItem* items_a,
-                                 int nitems_a, const FftItem* items_b, int nitems_b, Tables tab,
+cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
+                                 int nitems, Tables tab, const double2* grid_b, float4* grid_q,
+                                 cudaStream_t s);
+cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
+                                 int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
                                  const double2* grid_b, double2* tmp, float4* grid_q,
                                  cudaStream_t s);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, Tables tab, const double* w_s, const float4* grid_q,
+                              int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
                               double* g_s, cudaStream_t s);
 
 }  // namespace nuht

@@ -215,6 +215,11 @@ const HostTables& kernel_tables(int w)
         auto f = [&](double v) { return es_fourier((p + (v + 1.0) * 0.5) * width, T.beta, gx, gw); };
         cheb_monomial(f, T.ph_deg, &T.ph[(size_t)p * (T.ph_deg + 1)]);
     }
+    T.ph2.resize(T.ph.size());
+    for (size_t i = 0; i < T.ph.size(); ++i) {
+        const float hi = (float)T.ph[i];
+        T.ph2[i] = make_float2(hi, (float)(T.ph[i] - (double)hi));
+    }
     // twiddles e^{2 pi i k / 4096}, k < 2048
     T.tw_log2 = 12;
     T.tw.assign((size_t)1 << (T.tw_log2 - 1), make_double2(0.0, 0.0));

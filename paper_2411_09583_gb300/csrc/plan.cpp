@@ -1,6 +1,7 @@
 // C ABI of the NUHT library: plan (sort + subdivision + work lists), execute
 // (Algorithm 2 on the device), info and helpers.
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <mutex>
 #include <cstdio>
@@ -44,6 +45,21 @@ struct Arena {
     }
 };
 
+// Segments of a tile list plus their exclusive prefix of tile counts; the
+// tiles themselves are expanded on the device.
+struct SegList {
+    std::vector<Seg> segs;
+    std::vector<int32_t> prefix{0};
+    void add(int32_t blk, int64_t first, int64_t last, int len)
+    {
+        const int64_t cnt = (last - first + len) / len;
+        segs.push_back(Seg{blk, len, first, last});
+        prefix.push_back(prefix.back() + (int32_t)cnt);
+    }
+    int nseg() const { return (int)segs.size(); }
+    int total() const { return prefix.back(); }
+};
+
 }  // namespace
 
 struct nuht_plan_s {
@@ -65,7 +81,7 @@ struct nuht_plan_s {
     Tile *d_tmom = nullptr, *d_teval = nullptr;
     AsyBlock* d_asy = nullptr;
     Tile *d_tspread = nullptr, *d_tinterp = nullptr;
-    FftItem *d_fsmall = nullptr, *d_fa = nullptr, *d_fb = nullptr;
+    Tile *d_fblock = nullptr, *d_fsmall = nullptr, *d_fa = nullptr, *d_fb = nullptr;
     DirectBlock* d_dir = nullptr;
     double* d_mom = nullptr;
     double2 *d_gb = nullptr, *d_gtmp = nullptr;
@@ -75,7 +91,7 @@ struct nuht_plan_s {
     double2* d_tw = nullptr;
 
     int n_loc = 0, n_tmom = 0, n_teval = 0;
-    int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
+    int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fblock = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
     int n_dir = 0;
     int64_t mom_len = 0, gb_len = 0, gq_len = 0;
     int max_nf2_small = 0, max_dir_rows = 0, ntop_max = 0, eval_threads = 0;
@@ -83,6 +99,7 @@ struct nuht_plan_s {
     Tables tab{};
     std::vector<HBlock> hb[3];
     int64_t direct_entries = 0, local_rc = 0, asy_rc = 0, fft_points = 0;
+    double plan_ms[4] = {0, 0, 0, 0};
 
     // stage timing (opts.timing): event pairs per (vector component, stage)
     std::vector<cudaEvent_t> ev;
@@ -163,8 +180,7 @@ namespace {
 struct StageTimer {
     nuht_plan_t P;
     int comp;
-    cudaStream_t s;
-    int begin(int stage)
+    int begin(int stage, cudaStream_t s)
     {
         if (!P->opt.timing) return NUHT_OK;
         size_t i = ((size_t)comp * NUHT_NUM_STAGES + stage) * 2;
@@ -172,7 +188,7 @@ struct StageTimer {
         NUHT_CK(cudaEventRecord(P->ev[i], s));
         return NUHT_OK;
     }
-    int end(int stage)
+    int end(int stage, cudaStream_t s)
     {
         if (!P->opt.timing) return NUHT_OK;
         size_t i = ((size_t)comp * NUHT_NUM_STAGES + stage) * 2;
@@ -268,8 +284,17 @@ int nuht_stage_times(nuht_plan_t P, double* ms, int cap)
     return NUHT_OK;
 }
 
+static double ms_since(std::chrono::steady_clock::time_point& t)
+{
+    auto now = std::chrono::steady_clock::now();
+    double ms = std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+    return ms;
+}
+
 static int build_plan(nuht_plan_t P, const double* r, const double* omega)
 {
+    auto clk = std::chrono::steady_clock::now();
     cudaStream_t s = P->stream;
     const int64_t n = P->n, m = P->m;
     ProbParams& pp = P->prob;
@@ -316,6 +341,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     if (m) NUHT_CK(cudaMemcpyAsync(hst, stair, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
     NUHT_CK(cudaStreamSynchronize(s));
     if (hflag[0] || hflag[1]) return NUHT_ERR_DOMAIN;
+    P->plan_ms[0] = ms_since(clk);
     const double* hr = hr_p;
     const double* hw = hw_p;
 
@@ -324,15 +350,17 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     const auto& LB = P->hb[0];
     const auto& AB = P->hb[1];
     const auto& DB = P->hb[2];
+    P->plan_ms[1] = ms_since(clk);
 
     // ---- per-block work lists --------------------------------------------
     const HostTables& T = kernel_tables(P->w);
     std::vector<LocalBlock> vloc;
-    std::vector<Tile> vtmom, vteval;
     std::vector<AsyBlock> vasy;
-    std::vector<Tile> vtspread, vtinterp;
-    std::vector<FftItem> vfs, vfa, vfb;
     std::vector<DirectBlock> vdir;
+    SegList smom, seval, sspread, sinterp, sfs, sfa, sfb, sfk;
+    vloc.reserve(LB.size());
+    vasy.reserve(AB.size());
+    vdir.reserve(DB.size());
     const int Q = pp.Q;
     P->ntop_max = pp.ntop;
     P->eval_threads = local_eval_threads(P->ntop_max);
@@ -346,14 +374,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         lb.mom_off = mom_off;
         mom_off += pp.L + 1;
         vloc.push_back(lb);
-        for (int64_t j = h.j0; j <= h.j1; j += kMomentTile) {
-            int64_t c = h.j1 - j + 1;
-            vtmom.push_back(Tile{(int32_t)b, (int32_t)(c < kMomentTile ? c : kMomentTile), j});
-        }
-        for (int64_t k = h.k0; k <= h.k1; k += P->eval_threads) {
-            int64_t c = h.k1 - k + 1;
-            vteval.push_back(Tile{(int32_t)b, (int32_t)(c < P->eval_threads ? c : P->eval_threads), k});
-        }
+        smom.add((int32_t)b, h.j0, h.j1, kMomentTile);
+        seval.add((int32_t)b, h.k0, h.k1, P->eval_threads);
         P->local_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
     }
     P->mom_len = mom_off;
@@ -391,24 +413,17 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         ab.q_off = gq_off;
         gq_off += (int64_t)ab.nf2 * Q;
         vasy.push_back(ab);
-        for (int64_t j = h.j0; j <= h.j1; j += sp_tile) {
-            int64_t c = h.j1 - j + 1;
-            vtspread.push_back(Tile{(int32_t)b, (int32_t)(c < sp_tile ? c : sp_tile), j});
-        }
-        for (int64_t k = h.k0; k <= h.k1; k += kInterpTile) {
-            int64_t c = h.k1 - k + 1;
-            vtinterp.push_back(Tile{(int32_t)b, (int32_t)(c < kInterpTile ? c : kInterpTile), k});
-        }
-        if (ab.nf2 <= kFftSmemMax) {
+        sspread.add((int32_t)b, h.j0, h.j1, sp_tile);
+        sinterp.add((int32_t)b, h.k0, h.k1, kInterpTile);
+        if ((int64_t)ab.nf2 * Q <= kFftSmemMax) {
+            sfk.add((int32_t)b, 0, 0, 1);                // all Q grids in one CTA
+        } else if (ab.nf2 <= kFftSmemMax) {
             if (ab.nf2 > P->max_nf2_small) P->max_nf2_small = ab.nf2;
-            for (int q = 0; q < Q; ++q) vfs.push_back(FftItem{(int32_t)b, q, 0, 0});
+            sfs.add((int32_t)b, 0, Q - 1, 1);
         } else {
             P->has_large_fft = true;
-            const int n1 = ab.nf2 / kFftSmemMax;
-            for (int q = 0; q < Q; ++q) {
-                for (int l = 0; l < n1; ++l) vfa.push_back(FftItem{(int32_t)b, q, l, 0});
-                for (int l = 0; l < kFftSmemMax; ++l) vfb.push_back(FftItem{(int32_t)b, q, l, 0});
-            }
+            sfa.add((int32_t)b, 0, (int64_t)Q * (ab.nf2 / kFftSmemMax) - 1, 1);
+            sfb.add((int32_t)b, 0, (int64_t)Q * kFftSmemMax - 1, 1);
         }
         P->asy_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
         P->fft_points += ab.nf2;
@@ -423,30 +438,35 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         if (rows > P->max_dir_rows) P->max_dir_rows = rows;
         P->direct_entries += (h.k1 - h.k0 + 1) * (h.j1 - h.j0 + 1);
     }
-    P->n_loc = (int)vloc.size(); P->n_tmom = (int)vtmom.size(); P->n_teval = (int)vteval.size();
-    P->n_asy = (int)vasy.size(); P->n_tspread = (int)vtspread.size(); P->n_tinterp = (int)vtinterp.size();
-    P->n_fsmall = (int)vfs.size(); P->n_fa = (int)vfa.size(); P->n_fb = (int)vfb.size();
+    P->n_loc = (int)vloc.size(); P->n_tmom = smom.total(); P->n_teval = seval.total();
+    P->n_asy = (int)vasy.size(); P->n_tspread = sspread.total(); P->n_tinterp = sinterp.total();
+    P->n_fblock = sfk.total(); P->n_fsmall = sfs.total(); P->n_fa = sfa.total(); P->n_fb = sfb.total();
     P->n_dir = (int)vdir.size();
 
     // ---- one device arena for everything the plan keeps -------------------
     Arena A;
     size_t a_prob = A.reserve<ProbParams>(1);
-    size_t a_r = A.reserve<double>(n), a_w = A.reserve<double>(m);
-    size_t a_pr = A.reserve<int32_t>(n), a_pw = A.reserve<int32_t>(m);
     size_t a_loc = A.reserve<LocalBlock>(vloc.size());
-    size_t a_tmom = A.reserve<Tile>(vtmom.size()), a_teval = A.reserve<Tile>(vteval.size());
     size_t a_asy = A.reserve<AsyBlock>(vasy.size());
-    size_t a_tsp = A.reserve<Tile>(vtspread.size()), a_tin = A.reserve<Tile>(vtinterp.size());
-    size_t a_fs = A.reserve<FftItem>(vfs.size()), a_fa = A.reserve<FftItem>(vfa.size());
-    size_t a_fb = A.reserve<FftItem>(vfb.size());
     size_t a_dir = A.reserve<DirectBlock>(vdir.size());
     size_t a_es = A.reserve<double>(T.es.size()), a_ph = A.reserve<double>(T.ph.size());
-    size_t a_es2 = A.reserve<float2>(T.es2.size());
+    size_t a_es2 = A.reserve<float2>(T.es2.size()), a_ph2 = A.reserve<float2>(T.ph2.size());
     size_t a_tw = A.reserve<double2>(T.tw.size());
+    constexpr int kLists = 8;
+    SegList* lists[kLists] = {&smom, &seval, &sspread, &sinterp, &sfs, &sfa, &sfb, &sfk};
+    size_t a_seg[kLists], a_pre[kLists];
+    for (int i = 0; i < kLists; ++i) {
+        a_seg[i] = A.reserve<Seg>(lists[i]->segs.size());
+        a_pre[i] = A.reserve<int32_t>(lists[i]->prefix.size());
+    }
     size_t host_part = A.size;   // everything above is uploaded from one staging buffer
+    size_t a_tile[kLists];
+    for (int i = 0; i < kLists; ++i) a_tile[i] = A.reserve<Tile>((size_t)lists[i]->total());
+    size_t a_r = A.reserve<double>(n), a_w = A.reserve<double>(m);
+    size_t a_pr = A.reserve<int32_t>(n), a_pw = A.reserve<int32_t>(m);
     size_t a_mom = A.reserve<double>((size_t)P->mom_len);
     size_t a_gb = A.reserve<double2>((size_t)P->gb_len);
-    size_t a_gq = A.reserve<double2>((size_t)P->gq_len);
+    size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
     size_t a_gt = A.reserve<double2>(P->has_large_fft ? (size_t)P->gq_len : 1);
     size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
@@ -459,20 +479,27 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     };
     put(a_prob, &pp, sizeof(pp));
     put(a_loc, vloc.data(), sizeof(LocalBlock) * vloc.size());
-    put(a_tmom, vtmom.data(), sizeof(Tile) * vtmom.size());
-    put(a_teval, vteval.data(), sizeof(Tile) * vteval.size());
     put(a_asy, vasy.data(), sizeof(AsyBlock) * vasy.size());
-    put(a_tsp, vtspread.data(), sizeof(Tile) * vtspread.size());
-    put(a_tin, vtinterp.data(), sizeof(Tile) * vtinterp.size());
-    put(a_fs, vfs.data(), sizeof(FftItem) * vfs.size());
-    put(a_fa, vfa.data(), sizeof(FftItem) * vfa.size());
-    put(a_fb, vfb.data(), sizeof(FftItem) * vfb.size());
     put(a_dir, vdir.data(), sizeof(DirectBlock) * vdir.size());
     put(a_es, T.es.data(), sizeof(double) * T.es.size());
     put(a_es2, T.es2.data(), sizeof(float2) * T.es2.size());
     put(a_ph, T.ph.data(), sizeof(double) * T.ph.size());
+    put(a_ph2, T.ph2.data(), sizeof(float2) * T.ph2.size());
     put(a_tw, T.tw.data(), sizeof(double2) * T.tw.size());
+    for (int i = 0; i < kLists; ++i) {
+        put(a_seg[i], lists[i]->segs.data(), sizeof(Seg) * lists[i]->segs.size());
+        put(a_pre[i], lists[i]->prefix.data(), sizeof(int32_t) * lists[i]->prefix.size());
+    }
+    P->plan_ms[2] = ms_since(clk);
     NUHT_CK(cudaMemcpyAsync(D, stage, host_part, cudaMemcpyHostToDevice, s));
+    Tile* tiles[kLists];
+    for (int i = 0; i < kLists; ++i) {
+        tiles[i] = (Tile*)(D + a_tile[i]);
+        NUHT_CK(launch_expand_tiles((const Seg*)(D + a_seg[i]), (const int32_t*)(D + a_pre[i]),
+                                    lists[i]->nseg(), lists[i]->total(), tiles[i], s));
+    }
+    P->d_tmom = tiles[0]; P->d_teval = tiles[1]; P->d_tspread = tiles[2]; P->d_tinterp = tiles[3];
+    P->d_fsmall = tiles[4]; P->d_fa = tiles[5]; P->d_fb = tiles[6]; P->d_fblock = tiles[7];
     // sorted arrays and permutations stay on the device
     P->d_r = (double*)(D + a_r); P->d_w = (double*)(D + a_w);
     P->d_pr = (int32_t*)(D + a_pr); P->d_pw = (int32_t*)(D + a_pw);
@@ -486,10 +513,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     }
     P->d_prob = (ProbParams*)(D + a_prob);
     P->d_loc = (LocalBlock*)(D + a_loc);
-    P->d_tmom = (Tile*)(D + a_tmom); P->d_teval = (Tile*)(D + a_teval);
     P->d_asy = (AsyBlock*)(D + a_asy);
-    P->d_tspread = (Tile*)(D + a_tsp); P->d_tinterp = (Tile*)(D + a_tin);
-    P->d_fsmall = (FftItem*)(D + a_fs); P->d_fa = (FftItem*)(D + a_fa); P->d_fb = (FftItem*)(D + a_fb);
     P->d_dir = (DirectBlock*)(D + a_dir);
     P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
     P->d_mom = (double*)(D + a_mom);
@@ -498,11 +522,26 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     Tables& tb = P->tab;
     tb.es = P->d_es; tb.es2 = (const float2*)(D + a_es2);
     tb.w = T.w; tb.deg = T.deg; tb.half_w = 0.5 * T.w;
-    tb.ph = P->d_ph; tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
+    // plain FP32 for the degrees whose coefficient tail T_k = max_taps sum_{k' > k} |c_k'|
+    // keeps the FP32 rounding (2^-23 T_k) below 1e-2 eps
+    tb.deg_comp = T.deg;
+    for (int k = T.deg - 1; k >= 0; --k) {
+        double tail = 0.0;
+        for (int i = 0; i < T.w; ++i) {
+            double sum = 0.0;
+            for (int kk = k + 1; kk <= T.deg; ++kk) sum += std::fabs(T.es[(size_t)i * (T.deg + 1) + kk]);
+            tail = sum > tail ? sum : tail;
+        }
+        if (tail * 1.1920928955078125e-07 <= 1e-2 * P->eps) tb.deg_comp = k; else break;
+    }
+    tb.ph = P->d_ph; tb.ph2 = (const float2*)(D + a_ph2);
+    tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
+    tb.interp_const = std::sqrt(2.0 / M_PI) * 4.0 / ((double)T.w * (double)T.w);
     tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
     tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
     // the staging buffer must outlive the copy
     NUHT_CK(cudaStreamSynchronize(s));
+    P->plan_ms[3] = ms_since(clk);
     return NUHT_OK;
 }
 
@@ -544,6 +583,20 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
     const double phi = -(2.0 * anu + 1.0) * M_PI / 4.0;
     pp.cphi = std::cos(phi);
     pp.sphi = std::sin(phi);
+    {
+        const float ch = (float)pp.cphi, sh = (float)pp.sphi;
+        pp.cphi2 = make_float2(ch, (float)(pp.cphi - (double)ch));
+        pp.sphi2 = make_float2(sh, (float)(pp.sphi - (double)sh));
+    }
+    // Term q of the Hankel sum is at most |a_q| z^-q times the leading one on an
+    // asymptotic block (omega r > z).  Summing it in FP32 (relative error well
+    // below 1e-6 of the sum of magnitudes) costs at most |a_q| z^-q 1e-6 of
+    // ||c||_1; terms from qs on keep that below 1e-2 eps each.
+    pp.qs = pp.Q;
+    for (int q = pp.Q - 1; q >= 1; --q) {
+        if (std::fabs(hankel_coeff(q, anu)) * std::pow(pp.z, -q) * 1e-6 <= 1e-2 * eps) pp.qs = q;
+        else break;
+    }
     for (int q = 0; q < kMaxQ; ++q) {
         pp.a[q] = q < pp.Q ? hankel_coeff(q, anu) : 0.0;
         const float hi = (float)pp.a[q];
@@ -563,48 +616,51 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
         if (rc_ != NUHT_OK) return rc_; \
     } while (0)
 
-// Algorithm 2 on the device for one vector component: local moments, the
-// asymptotic type-3 pipeline, local evaluation and direct blocks, all
-// accumulating into g in sorted order.
+// Algorithm 2 on the device for one vector component: local moments and
+// evaluation, direct blocks, and the asymptotic type-3 pipeline, all
+// accumulating into g in sorted order (FP64 atomics).  They run one after the
+// other on the caller's stream: each kernel fills the GPU, and running them
+// concurrently only makes them compete for shared memory.
 static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
+    cudaStream_t ls = s;
     if ((mask & 1) && P->n_loc) {
-        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS));
-        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->prob.L, P->d_r,
-                                     P->d_cs, P->d_mom, s));
-        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS));
+                                     P->d_cs, P->d_mom, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
+        NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
+                                  P->eval_threads, P->d_w, P->d_mom, P->d_gs, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
+    }
+    if ((mask & 4) && P->n_dir) {
+        NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
+        NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->d_r, P->d_w, P->d_cs,
+                              P->d_gs, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if ((mask & 2) && P->n_asy) {
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
         NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->prob.Q, P->tab,
                                   P->d_r, P->d_cs, P->d_gb, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
+        NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_gb,
+                                     P->d_gq, s));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small,
                                      P->tab, P->d_gb, P->d_gq, s));
         if (P->has_large_fft)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
                                          P->d_gb, P->d_gtmp, P->d_gq, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP));
-        NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->tab, P->d_w,
-                                  P->d_gq, P->d_gs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP));
-    }
-    if ((mask & 1) && P->n_loc) {
-        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL));
-        NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                  P->eval_threads, P->d_w, P->d_mom, P->d_gs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL));
-    }
-    if ((mask & 4) && P->n_dir) {
-        NUHT_TRY(T.begin(NUHT_STAGE_DIRECT));
-        NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->d_r, P->d_w, P->d_cs,
-                              P->d_gs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_DIRECT));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
+        NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->prob.Q, P->tab,
+                                  P->d_w, P->d_gq, P->d_gs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
     }
     return NUHT_OK;
 }
@@ -622,15 +678,15 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
     }
     NUHT_TRY(ensure_events(P, comps));
     for (int comp = 0; comp < comps; ++comp) {
-        StageTimer T{P, comp, s};
-        NUHT_TRY(T.begin(NUHT_STAGE_GATHER));
+        StageTimer T{P, comp};
+        NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
         NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * P->m, s));
         NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_GATHER));
+        NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_forward(P, T, s));
-        NUHT_TRY(T.begin(NUHT_STAGE_SCATTER));
+        NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
         NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, g, s));
-        NUHT_TRY(T.end(NUHT_STAGE_SCATTER));
+        NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
     }
     return NUHT_OK;
 }
@@ -695,6 +751,7 @@ int nuht_info(nuht_plan_t P, nuht_plan_info* out)
     out->asy_rows_cols = P->asy_rc;
     out->fft_points = P->fft_points;
     out->device_bytes = (int64_t)P->dbytes;
+    for (int i = 0; i < 4; ++i) out->plan_ms[i] = P->plan_ms[i];
     return NUHT_OK;
 }
 

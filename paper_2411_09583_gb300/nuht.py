@@ -110,7 +110,9 @@ class Plan:
     def info(self):
         inf = N.NuhtPlanInfo()
         N.check(N.lib().nuht_info(self._h, ctypes.byref(inf)), "nuht_info")
-        return {f: getattr(inf, f) for f, _ in N.NuhtPlanInfo._fields_}
+        d = {f: getattr(inf, f) for f, _ in N.NuhtPlanInfo._fields_}
+        d["plan_ms"] = list(d["plan_ms"])
+        return d
 
     def blocks(self, cls):
         """(count, 4) int64 array of (k0, k1, j0, j1) for block class cls (0 local, 1 asy, 2 direct)."""
