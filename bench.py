@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--omega-max", type=float, default=1e5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched / mixed-precision side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the oracle sample")
     return ap.parse_args(argv)
@@ -236,6 +238,69 @@ def stored_traffic(kernel, workload):
         return None
 
 
+def run_batched(dev, steps):
+    """256 uneven problems (n, m log-uniform in [1e3, 1e5], nu in 0..20, omega ~ U[0, m],
+    eps = 1e-8) in one plan; execute replayed as one captured CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import batch_problems
+    probs = batch_problems(count=256, lo=1e3, hi=1e5, nu_max=20, seed=5)
+    nus = [p[0] for p in probs]
+    n = [p[1].size for p in probs]
+    m = [p[2].size for p in probs]
+    dr = torch.tensor(np.concatenate([p[1] for p in probs]), device=dev)
+    dw = torch.tensor(np.concatenate([p[2] for p in probs]), device=dev)
+    dc = torch.tensor(np.concatenate([p[3] for p in probs]), device=dev)
+    units = int(sum(n) + sum(m))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        Plan.many(nus, dr, n, dw, m, 1e-8).close()
+    plan_ms = []
+    for _ in range(max(3, steps // 4)):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        bp = Plan.many(nus, dr, n, dw, m, 1e-8)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        plan_ms.append(s0.elapsed_time(s1))
+        bp.close()
+    bp = Plan.many(nus, dr, n, dw, m, 1e-8)
+    g = torch.empty(sum(m), dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            bp.execute(dc, out=g)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bp.execute(dc, out=g)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    ex_ms = []
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        graph.replay()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        ex_ms.append(s0.elapsed_time(s1))
+    info = bp.info()
+    bp.close()
+    exe = statistics.median(ex_ms)
+    pl = statistics.median(plan_ms)
+    return {"workload": "256 problems, n, m ~ 10^U[3,5], nu ~ U{0..20}, omega ~ U[0, m], eps 1e-8",
+            "units_n_plus_m": units, "execute_graph_ms": exe, "plan_ms": pl,
+            "value_execute": units / (exe * 1e-3), "value_plan_execute": units / ((exe + pl) * 1e-3),
+            "unit": UNIT, "execute": "one CUDA graph replay (one launch per stage over all problems)",
+            "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]]}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -359,6 +424,10 @@ def run_ours(a):
                 "traffic": stored_traffic(kernel_of.get(dom, dom),
                                           workload_config(a)["workload"])}
 
+    extra_batched = None
+    if not a.no_extra and ws == 1:
+        extra_batched = run_batched(dev, a.steps)
+
     line = None
     if rank == 0:
         cpu = None
@@ -382,6 +451,7 @@ def run_ours(a):
                 "execute_only": {"value": ws * a.steps * (a.n + a.m) / exe_s, "unit": UNIT,
                                  "ms_per_step": 1e3 * exe_s / a.steps},
                 "stage_ms": mean_stage,
+                "batched": extra_batched,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],

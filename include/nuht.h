@@ -126,6 +126,19 @@ int nuht_plan(nuht_plan_t *out, int nu, const double *r, int64_t n,
               const double *omega, int64_t m, double eps, const nuht_opts *opt,
               void *stream);
 
+/* A batch of nprob independent problems in one plan (the same eps): problem
+ * i has order nu[i] (host array), n[i] points and m[i] frequencies (host
+ * arrays); the points of all problems are concatenated in r (device, sum n[i]
+ * entries, problem 0 first) and the frequencies in omega (device, sum m[i]).
+ * One execute then applies every problem's transform with one launch per
+ * stage over the whole batch: c and g are the concatenations of the
+ * problems' vectors in the same order (c: sum n[i] rows, g: sum m[i] rows).
+ * nprob <= 65536.  nuht_get_blocks reports indices into the concatenated
+ * sorted arrays; nuht_info reports the first problem's orders. */
+int nuht_plan_many(nuht_plan_t *out, int nprob, const int *nu, const double *r, const int64_t *n,
+                   const double *omega, const int64_t *m, double eps, const nuht_opts *opt,
+                   void *stream);
+
 /* Forward transform g = A c.  c: n x nvec (row-major, c[j*nvec + v]) FP64,
  * or n x nvec complex (interleaved re,im: c[2*(j*nvec+v)+{0,1}]) when
  * is_complex != 0.  g: m x nvec of the same kind, OVERWRITTEN, in the

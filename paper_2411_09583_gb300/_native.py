@@ -31,7 +31,7 @@ EXPORTED = ["nuht_default_opts", "nuht_choose_params", "nuht_plan", "nuht_execut
             "nuht_adjoint", "nuht_transform_host", "nuht_info", "nuht_get_blocks",
             "nuht_get_permutations", "nuht_destroy", "nuht_strerror",
             "nuht_last_cuda_error", "nuht_stage_times", "nuht_stage_name",
-            "nuht_kernel_launch_count", "nuht_local_apply_noalloc"]
+            "nuht_kernel_launch_count", "nuht_local_apply_noalloc", "nuht_plan_many"]
 NUM_STAGES = 8
 
 
@@ -119,5 +119,8 @@ def lib():
         L.nuht_kernel_launch_count.restype = i64
         L.nuht_local_apply_noalloc.argtypes = [i, d, p, i64, d, p, i64, d, p, p, i, p]
         L.nuht_local_apply_noalloc.restype = i
+        L.nuht_plan_many.argtypes = [ctypes.POINTER(p), i, p, p, p, p, p, d,
+                                     ctypes.POINTER(NuhtOpts), p]
+        L.nuht_plan_many.restype = i
         _lib = L
         return _lib

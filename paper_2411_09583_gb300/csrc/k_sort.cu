@@ -252,9 +252,39 @@ size_t radix_sort_scratch_bytes(int64_t n)
            align256(sizeof(uint32_t) * (size_t)kRadix);
 }
 
-// Sorts in[0..n) ascending into out, perm[i] = input index of out[i].
+// seg[i] = segment of the element at input index perm[i] (offsets off[0..nseg]),
+// as a radix key.
+__global__ void k_seg_keys(const int32_t* __restrict__ perm, int64_t n, const int64_t* __restrict__ off,
+                           int nseg, uint64_t* __restrict__ keys)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = perm[i];
+        int lo = 0, hi = nseg;   // last segment with off[seg] <= x
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= x) lo = mid; else hi = mid;
+        }
+        keys[i] = (uint64_t)lo;
+    }
+}
+
+__global__ void k_gather_keys(const double* __restrict__ in, const int32_t* __restrict__ perm, int64_t n,
+                              double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = in[perm[i]];
+        out[i] = (v == 0.0) ? 0.0 : v;
+    }
+}
+
+// Sorts in[0..n) ascending into out, perm[i] = input index of out[i].  With
+// nseg > 1 segments (device offsets off[0..nseg], nseg <= 65536) each segment
+// is sorted on its own: the value passes are followed by two stable passes on
+// the segment number, so the output keeps the segments in order.
 cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* perm, void* scratch,
-                           size_t scratch_bytes, cudaStream_t s)
+                           size_t scratch_bytes, cudaStream_t s, const int64_t* off, int nseg)
 {
     if (n <= 0) return cudaSuccess;
     if (scratch_bytes < radix_sort_scratch_bytes(n)) return cudaErrorInvalidValue;
@@ -278,9 +308,48 @@ cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* pe
         int32_t* tv = va; va = vb; vb = tv;
     }
     // after an even number of passes the data is back in (k0, perm)
-    k_sort_finish<<<grid_for(n, 256), 256, 0, s>>>(ka, n, out);
-    count_launches(2 + 8 * 3);
+    if (nseg <= 1) {
+        k_sort_finish<<<grid_for(n, 256), 256, 0, s>>>(ka, n, out);
+        count_launches(2 + 8 * 3);
+        return cudaGetLastError();
+    }
+    k_seg_keys<<<grid_for(n, 256), 256, 0, s>>>(perm, n, off, nseg, ka);
+    for (int pass = 0; pass < 2; ++pass) {
+        const int shift = 8 * pass;
+        k_sort_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist);
+        k_sort_rowscan<<<kRadix, 1024, 0, s>>>(hist, ntiles, tot);
+        k_sort_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, n, shift, ntiles, hist, tot, kb, vb);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        int32_t* tv = va; va = vb; vb = tv;
+    }
+    k_gather_keys<<<grid_for(n, 256), 256, 0, s>>>(in, perm, n, out);
+    count_launches(1 + 10 * 3 + 2);
     return cudaGetLastError();
+}
+
+// Staircase of every row of a batch: row k belongs to the problem p with
+// w_off <= k < w_off + m (binary search); the search runs over that problem's
+// points and the result is a column index local to the problem.
+__global__ void k_staircase_many(const double* __restrict__ r, const double* __restrict__ w, int64_t m,
+                                 const ProbParams* __restrict__ probs, int nprob, int32_t* __restrict__ s)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nprob;   // last problem with w_off <= k
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (probs[mid].w_off <= k) lo = mid; else hi = mid;
+        }
+        const ProbParams& P = probs[lo];
+        const double wk = w[k];
+        const double* rp = r + P.r_off;
+        int64_t a = 0, b = P.n;
+        while (a < b) {
+            const int64_t mid = a + ((b - a) >> 1);
+            if (wk * rp[mid] <= P.z) a = mid + 1; else b = mid;
+        }
+        s[k] = (int32_t)(a - 1);
+    }
 }
 
 cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_t m, double z,
@@ -288,6 +357,15 @@ cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_
 {
     if (m <= 0) return cudaSuccess;
     k_staircase<<<grid_for(m, 256), 256, 0, s>>>(r, n, w, m, z, s_out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
+                                  int nprob, int32_t* s_out, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_staircase_many<<<grid_for(m, 256), 256, 0, s>>>(r, w, m, probs, nprob, s_out);
     count_launches(1);
     return cudaGetLastError();
 }

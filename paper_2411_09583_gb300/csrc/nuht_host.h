@@ -35,6 +35,7 @@ const HostTables& kernel_tables(int w);
 // Block of the subdivision: rows k0..k1 (sorted omega), columns j0..j1 (sorted r).
 struct HBlock {
     int64_t k0, k1, j0, j1;
+    int32_t prob = 0;   // problem of a batch
 };
 
 // Algorithm 1 with SplitIndices on the sorted matrix, from the staircase

@@ -105,11 +105,14 @@ struct Tables {
 void count_launches(int k);
 cudaError_t launch_check_domain(const double* x, int64_t n, int* flag, cudaStream_t s);
 cudaError_t radix_sort_f64(const double* in, int64_t n, double* out, int32_t* perm,
-                           void* scratch, size_t scratch_bytes, cudaStream_t s);
+                           void* scratch, size_t scratch_bytes, cudaStream_t s,
+                           const int64_t* seg_off = nullptr, int nseg = 1);
 size_t radix_sort_scratch_bytes(int64_t n);
 
 cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_t m, double z,
                              int32_t* s_out, cudaStream_t s);
+cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
+                                  int nprob, int32_t* s_out, cudaStream_t s);
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
                           double* out, cudaStream_t s);
 cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg, int total, Tile* out,

@@ -68,7 +68,8 @@ struct nuht_plan_s {
     nuht_opts opt{};
     int64_t n = 0, m = 0;
     cudaStream_t stream = nullptr;
-    ProbParams prob{};
+    std::vector<ProbParams> probs;   // one per problem of the batch (one for nuht_plan)
+    int lmax = 0, qmax = 0;          // largest L and Q = 2M over the problems
     int w = 0;
 
     // device memory
@@ -297,7 +298,16 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     auto clk = std::chrono::steady_clock::now();
     cudaStream_t s = P->stream;
     const int64_t n = P->n, m = P->m;
-    ProbParams& pp = P->prob;
+    const int nprob = (int)P->probs.size();
+    std::vector<ProbParams>& probs = P->probs;
+    P->lmax = 0;
+    P->qmax = 0;
+    P->ntop_max = 0;
+    for (const ProbParams& q : probs) {
+        P->lmax = q.L > P->lmax ? q.L : P->lmax;
+        P->qmax = q.Q > P->qmax ? q.Q : P->qmax;
+        P->ntop_max = q.ntop > P->ntop_max ? q.ntop : P->ntop_max;
+    }
 
     // ---- sort (device) -------------------------------------------------
     Arena sa;
@@ -305,6 +315,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t o_pr = sa.reserve<int32_t>(n), o_pw = sa.reserve<int32_t>(m);
     size_t o_st = sa.reserve<int32_t>(m);
     size_t o_flag = sa.reserve<int>(2);
+    size_t o_prb = sa.reserve<ProbParams>(probs.size());
+    size_t o_roff = sa.reserve<int64_t>(probs.size() + 1), o_woff = sa.reserve<int64_t>(probs.size() + 1);
     size_t o_scr = sa.size;
     size_t scr = radix_sort_scratch_bytes(n > m ? n : m);
     sa.size += align256(scr);
@@ -316,6 +328,24 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     } free_sort{sort_mem, s};
     int* d_flag = (int*)(sort_mem + o_flag);
     NUHT_CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * 2, s));
+    std::lock_guard<std::mutex> stage_lock(g_stage_mu);
+    // problems and segment offsets (needed by the segmented sort and the staircase)
+    ProbParams* d_prb = (ProbParams*)(sort_mem + o_prb);
+    int64_t* d_roff = (int64_t*)(sort_mem + o_roff);
+    int64_t* d_woff = (int64_t*)(sort_mem + o_woff);
+    {
+        const size_t pb = sizeof(ProbParams) * probs.size(), ob = sizeof(int64_t) * (probs.size() + 1);
+        NUHT_CK(g_stage_out.reserve(pb + 2 * ob));
+        std::memcpy(g_stage_out.p, probs.data(), pb);
+        int64_t* ro = (int64_t*)(g_stage_out.p + pb);
+        int64_t* wo = ro + probs.size() + 1;
+        for (int i = 0; i < nprob; ++i) { ro[i] = probs[i].r_off; wo[i] = probs[i].w_off; }
+        ro[nprob] = n;
+        wo[nprob] = m;
+        NUHT_CK(cudaMemcpyAsync(d_prb, g_stage_out.p, pb, cudaMemcpyHostToDevice, s));
+        NUHT_CK(cudaMemcpyAsync(d_roff, ro, ob, cudaMemcpyHostToDevice, s));
+        NUHT_CK(cudaMemcpyAsync(d_woff, wo, ob, cudaMemcpyHostToDevice, s));
+    }
     NUHT_CK(launch_check_domain(r, n, d_flag, s));
     NUHT_CK(launch_check_domain(omega, m, d_flag + 1, s));
     double* r_s = (double*)(sort_mem + o_r);
@@ -323,11 +353,11 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     int32_t* pr = (int32_t*)(sort_mem + o_pr);
     int32_t* pw = (int32_t*)(sort_mem + o_pw);
     int32_t* stair = (int32_t*)(sort_mem + o_st);
-    NUHT_CK(radix_sort_f64(r, n, r_s, pr, sort_mem + o_scr, scr, s));
-    NUHT_CK(radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr, scr, s));
-    NUHT_CK(launch_staircase(r_s, n, w_s, m, pp.z, stair, s));
+    NUHT_CK(radix_sort_f64(r, n, r_s, pr, sort_mem + o_scr, scr, s, d_roff, nprob));
+    NUHT_CK(radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr, scr, s, d_woff, nprob));
+    if (nprob == 1) NUHT_CK(launch_staircase(r_s, n, w_s, m, probs[0].z, stair, s));
+    else NUHT_CK(launch_staircase_many(r_s, w_s, m, d_prb, nprob, stair, s));
     // sorted values (block geometry) and the staircase (subdivision) to pinned host memory
-    std::lock_guard<std::mutex> stage_lock(g_stage_mu);
     const size_t in_bytes = align256(8) + align256(sizeof(double) * n) + align256(sizeof(double) * m) +
                             align256(sizeof(int32_t) * m);
     NUHT_CK(g_stage_in.reserve(in_bytes));
@@ -345,8 +375,22 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     const double* hr = hr_p;
     const double* hw = hw_p;
 
-    // ---- subdivision (host, Algorithm 1) --------------------------------
-    subdivide(hst, n, m, P->opt.min_size, P->opt.n_split_cand, P->hb[0], P->hb[1], P->hb[2]);
+    // ---- subdivision (host, Algorithm 1), problem by problem ------------
+    for (int c = 0; c < 3; ++c) P->hb[c].clear();
+    {
+        std::vector<HBlock> lb, ab, db;
+        for (int ip = 0; ip < nprob; ++ip) {
+            const ProbParams& q = probs[ip];
+            subdivide(hst + q.w_off, q.n, q.m, P->opt.min_size, P->opt.n_split_cand, lb, ab, db);
+            std::vector<HBlock>* src[3] = {&lb, &ab, &db};
+            for (int c = 0; c < 3; ++c)
+                for (HBlock h : *src[c]) {
+                    h.k0 += q.w_off; h.k1 += q.w_off; h.j0 += q.r_off; h.j1 += q.r_off;
+                    h.prob = ip;
+                    P->hb[c].push_back(h);
+                }
+        }
+    }
     const auto& LB = P->hb[0];
     const auto& AB = P->hb[1];
     const auto& DB = P->hb[2];
@@ -361,14 +405,13 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     vloc.reserve(LB.size());
     vasy.reserve(AB.size());
     vdir.reserve(DB.size());
-    const int Q = pp.Q;
-    P->ntop_max = pp.ntop;
     P->eval_threads = local_eval_threads(P->ntop_max);
     int64_t mom_off = 0;
     for (size_t b = 0; b < LB.size(); ++b) {
         const HBlock& h = LB[b];
+        const ProbParams& pp = probs[h.prob];
         LocalBlock lb{};
-        lb.prob = 0;
+        lb.prob = h.prob;
         lb.k0 = (int32_t)h.k0; lb.k1 = (int32_t)h.k1; lb.j0 = (int32_t)h.j0; lb.j1 = (int32_t)h.j1;
         lb.R = hr[h.j1];
         lb.mom_off = mom_off;
@@ -379,12 +422,13 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         P->local_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
     }
     P->mom_len = mom_off;
-    const int sp_tile = spread_tile_points(Q);
+    const int sp_tile = spread_tile_points(P->qmax);
     int64_t gb_off = 0, gq_off = 0;
     for (size_t b = 0; b < AB.size(); ++b) {
         const HBlock& h = AB[b];
+        const int Q = probs[h.prob].Q;
         AsyBlock ab{};
-        ab.prob = 0;
+        ab.prob = h.prob;
         ab.k0 = (int32_t)h.k0; ab.k1 = (int32_t)h.k1; ab.j0 = (int32_t)h.j0; ab.j1 = (int32_t)h.j1;
         const double rlo = hr[h.j0], rhi = hr[h.j1];
         const double wlo = hw[h.k0], whi = hw[h.k1];
@@ -432,7 +476,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->gq_len = gq_off;
     for (size_t b = 0; b < DB.size(); ++b) {
         const HBlock& h = DB[b];
-        DirectBlock db{0, (int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, 0};
+        DirectBlock db{h.prob, (int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, 0};
         vdir.push_back(db);
         const int rows = (int)(h.k1 - h.k0 + 1);
         if (rows > P->max_dir_rows) P->max_dir_rows = rows;
@@ -445,7 +489,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
 
     // ---- one device arena for everything the plan keeps -------------------
     Arena A;
-    size_t a_prob = A.reserve<ProbParams>(1);
+    size_t a_prob = A.reserve<ProbParams>(probs.size());
     size_t a_loc = A.reserve<LocalBlock>(vloc.size());
     size_t a_asy = A.reserve<AsyBlock>(vasy.size());
     size_t a_dir = A.reserve<DirectBlock>(vdir.size());
@@ -477,7 +521,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     auto put = [&](size_t off, const void* src, size_t bytes) {
         if (bytes) std::memcpy(stage + off, src, bytes);
     };
-    put(a_prob, &pp, sizeof(pp));
+    put(a_prob, probs.data(), sizeof(ProbParams) * probs.size());
     put(a_loc, vloc.data(), sizeof(LocalBlock) * vloc.size());
     put(a_asy, vasy.data(), sizeof(AsyBlock) * vasy.size());
     put(a_dir, vdir.data(), sizeof(DirectBlock) * vdir.size());
@@ -545,41 +589,21 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     return NUHT_OK;
 }
 
-int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double* omega, int64_t m,
-              double eps, const nuht_opts* opt, void* stream)
+// Orders, crossover, Hankel coefficients and precision split of one problem.
+static int init_problem(ProbParams& pp, int nu, double eps, int m_terms, int64_t n, int64_t m,
+                        int64_t r_off, int64_t w_off)
 {
-    if (!out) return NUHT_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (n < 0 || m < 0 || n > 0x7fffffffLL || m > 0x7fffffffLL) return NUHT_ERR_INVALID_ARG;
-    if (!(eps >= 1e-15 && eps <= 1e-1)) return NUHT_ERR_INVALID_ARG;
-    if ((n > 0 && !r) || (m > 0 && !omega)) return NUHT_ERR_INVALID_ARG;
     if (nu > 100 || nu < -100) return NUHT_ERR_UNSUPPORTED;
-    nuht_opts o;
-    nuht_default_opts(&o);
-    if (opt) o = *opt;
-    if (o.min_size < 1 || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
-        (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
-        return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
-        if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
-    nuht_plan_t P = new (std::nothrow) nuht_plan_s();
-    if (!P) return NUHT_ERR_NOMEM;
-    P->nu_user = nu;
-    P->eps = eps;
-    P->opt = o;
-    P->n = n;
-    P->m = m;
-    P->stream = (cudaStream_t)stream;
     const int anu = nu < 0 ? -nu : nu;
-    ProbParams& pp = P->prob;
+    pp = ProbParams{};
     pp.nu = anu;
     pp.sgn = (nu < 0 && (anu & 1)) ? -1 : 1;
-    int rc = choose_params(anu, eps, o.m_terms, &pp.M, &pp.z, &pp.L);
-    if (rc != NUHT_OK) { delete P; return rc; }
+    int rc = choose_params(anu, eps, m_terms, &pp.M, &pp.z, &pp.L);
+    if (rc != NUHT_OK) return rc;
     pp.Q = 2 * pp.M;
     const int hp = (anu & 1) ? (anu + 1) / 2 : anu / 2;
     pp.ntop = hp + pp.L;
-    if (pp.ntop >= kMaxNtop) { delete P; return NUHT_ERR_UNSUPPORTED; }
+    if (pp.ntop >= kMaxNtop) return NUHT_ERR_UNSUPPORTED;
     const double phi = -(2.0 * anu + 1.0) * M_PI / 4.0;
     pp.cphi = std::cos(phi);
     pp.sphi = std::sin(phi);
@@ -602,7 +626,87 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
         const float hi = (float)pp.a[q];
         pp.a2[q] = make_float2(hi, (float)(pp.a[q] - (double)hi));
     }
-    pp.r_off = 0; pp.w_off = 0; pp.n = n; pp.m = m; pp.c_off = 0; pp.g_off = 0;
+    pp.r_off = r_off; pp.w_off = w_off; pp.n = n; pp.m = m; pp.c_off = r_off; pp.g_off = w_off;
+    return NUHT_OK;
+}
+
+static int check_opts(const nuht_opts* opt, nuht_opts& o)
+{
+    nuht_default_opts(&o);
+    if (opt) o = *opt;
+    if (o.min_size < 1 || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
+        (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
+        return NUHT_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
+    return NUHT_OK;
+}
+
+int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double* omega, int64_t m,
+              double eps, const nuht_opts* opt, void* stream)
+{
+    if (!out) return NUHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || m < 0 || n > 0x7fffffffLL || m > 0x7fffffffLL) return NUHT_ERR_INVALID_ARG;
+    if (!(eps >= 1e-15 && eps <= 1e-1)) return NUHT_ERR_INVALID_ARG;
+    if ((n > 0 && !r) || (m > 0 && !omega)) return NUHT_ERR_INVALID_ARG;
+    if (nu > 100 || nu < -100) return NUHT_ERR_UNSUPPORTED;
+    nuht_opts o;
+    int rc = check_opts(opt, o);
+    if (rc != NUHT_OK) return rc;
+    nuht_plan_t P = new (std::nothrow) nuht_plan_s();
+    if (!P) return NUHT_ERR_NOMEM;
+    P->nu_user = nu;
+    P->eps = eps;
+    P->opt = o;
+    P->n = n;
+    P->m = m;
+    P->stream = (cudaStream_t)stream;
+    P->probs.resize(1);
+    rc = init_problem(P->probs[0], nu, eps, o.m_terms, n, m, 0, 0);
+    if (rc != NUHT_OK) { delete P; return rc; }
+    P->w = nufft_width(eps);
+    rc = build_plan(P, r, omega);
+    if (rc != NUHT_OK) { nuht_destroy(P); return rc; }
+    *out = P;
+    return NUHT_OK;
+}
+
+int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, const int64_t* n,
+                   const double* omega, const int64_t* m, double eps, const nuht_opts* opt, void* stream)
+{
+    if (!out) return NUHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nprob < 1 || nprob > 65536 || !nu || !n || !m) return NUHT_ERR_INVALID_ARG;
+    if (!(eps >= 1e-15 && eps <= 1e-1)) return NUHT_ERR_INVALID_ARG;
+    int64_t nt = 0, mt = 0;
+    for (int i = 0; i < nprob; ++i) {
+        if (n[i] < 0 || m[i] < 0) return NUHT_ERR_INVALID_ARG;
+        if (nu[i] > 100 || nu[i] < -100) return NUHT_ERR_UNSUPPORTED;
+        nt += n[i];
+        mt += m[i];
+    }
+    if (nt > 0x7fffffffLL || mt > 0x7fffffffLL) return NUHT_ERR_INVALID_ARG;
+    if ((nt > 0 && !r) || (mt > 0 && !omega)) return NUHT_ERR_INVALID_ARG;
+    nuht_opts o;
+    int rc = check_opts(opt, o);
+    if (rc != NUHT_OK) return rc;
+    nuht_plan_t P = new (std::nothrow) nuht_plan_s();
+    if (!P) return NUHT_ERR_NOMEM;
+    P->nu_user = nu[0];
+    P->eps = eps;
+    P->opt = o;
+    P->n = nt;
+    P->m = mt;
+    P->stream = (cudaStream_t)stream;
+    P->probs.resize(nprob);
+    int64_t ro = 0, wo = 0;
+    for (int i = 0; i < nprob; ++i) {
+        rc = init_problem(P->probs[i], nu[i], eps, o.m_terms, n[i], m[i], ro, wo);
+        if (rc != NUHT_OK) { delete P; return rc; }
+        ro += n[i];
+        wo += m[i];
+    }
     P->w = nufft_width(eps);
     rc = build_plan(P, r, omega);
     if (rc != NUHT_OK) { nuht_destroy(P); return rc; }
@@ -628,7 +732,7 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if ((mask & 1) && P->n_loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
-        NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->prob.L, P->d_r,
+        NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r,
                                      P->d_cs, P->d_mom, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
@@ -645,7 +749,7 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if ((mask & 2) && P->n_asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
-        NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->prob.Q, P->tab,
+        NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab,
                                   P->d_r, P->d_cs, P->d_gb, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
@@ -658,7 +762,7 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                          P->d_gb, P->d_gtmp, P->d_gq, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
-        NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->prob.Q, P->tab,
+        NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
                                   P->d_w, P->d_gq, P->d_gs, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
     }
@@ -735,11 +839,11 @@ int nuht_info(nuht_plan_t P, nuht_plan_info* out)
     if (!P || !out) return NUHT_ERR_INVALID_ARG;
     std::memset(out, 0, sizeof(*out));
     out->nu = P->nu_user;
-    out->M = P->prob.M;
-    out->L = P->prob.L;
+    out->M = P->probs[0].M;
+    out->L = P->probs[0].L;
     out->nufft_width = P->w;
     out->nufft_degree = P->tab.deg;
-    out->z = P->prob.z;
+    out->z = P->probs[0].z;
     out->eps = P->eps;
     out->n = P->n;
     out->m = P->m;

@@ -81,6 +81,33 @@ class Plan:
                                       float(eps), ctypes.byref(self._opts),
                                       _stream_ptr(stream)), "nuht_plan")
 
+    @classmethod
+    def many(cls, nus, r, n, omega, m, eps, stream=None, **opts):
+        """A batch plan: problem i has order nus[i], n[i] points and m[i]
+        frequencies; r and omega are the concatenations (float64 CUDA tensors).
+        execute / adjoint then take and return concatenated vectors."""
+        r = _dev_f64(r, "r")
+        omega = _dev_f64(omega, "omega")
+        nus = np.ascontiguousarray(nus, dtype=np.int32)
+        n = np.ascontiguousarray(n, dtype=np.int64)
+        m = np.ascontiguousarray(m, dtype=np.int64)
+        if not (nus.size == n.size == m.size) or n.sum() != r.numel() or m.sum() != omega.numel():
+            raise ValueError("sizes of the batch do not match r / omega")
+        self = cls.__new__(cls)
+        self.n, self.m = r.numel(), omega.numel()
+        self.device = r.device
+        self._opts = make_opts(**opts)
+        self._h = ctypes.c_void_p()
+        self._stream = stream
+        self.sizes = (n.copy(), m.copy())
+        with torch.cuda.device(self.device):
+            N.check(N.lib().nuht_plan_many(
+                ctypes.byref(self._h), int(nus.size), nus.ctypes.data_as(ctypes.c_void_p),
+                ctypes.c_void_p(r.data_ptr()), n.ctypes.data_as(ctypes.c_void_p),
+                ctypes.c_void_p(omega.data_ptr()), m.ctypes.data_as(ctypes.c_void_p), float(eps),
+                ctypes.byref(self._opts), _stream_ptr(stream)), "nuht_plan_many")
+        return self
+
     def _apply(self, fn, x, rows_in, rows_out, out, what):
         x = _dev_f64(x, "input")
         if x.shape[0] != rows_in:

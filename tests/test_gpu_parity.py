@@ -198,3 +198,54 @@ def test_relative_l2_error_tracks_eps(nu):
         g, _, _ = run_forward(nu, r, omega, c, eps)
         rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
         assert rel <= max(10 * eps, 3e-13), (eps, rel)
+
+
+def _batch(count, lo, hi, nu_max, seed):
+    from paper_2411_09583_gb300.workloads import batch_problems
+    return batch_problems(count=count, lo=lo, hi=hi, nu_max=nu_max, seed=seed)
+
+
+def test_batched_plan_matches_oracle_and_single_plans():
+    # uneven problems (sizes log-uniform, orders 0..20) in one plan, one launch per stage
+    from paper_2411_09583_gb300 import Plan
+    eps = 1e-8
+    probs = _batch(24, 50, 3000, 20, 41)
+    nus = [p[0] for p in probs]
+    r = np.concatenate([p[1] for p in probs])
+    omega = np.concatenate([p[2] for p in probs])
+    c = np.concatenate([p[3] for p in probs])
+    n = [p[1].size for p in probs]
+    m = [p[2].size for p in probs]
+    with Plan.many(nus, to_dev(r), n, to_dev(omega), m, eps) as bp:
+        g = bp.execute(to_dev(c)).cpu().numpy()
+        nblk = sum(len(bp.blocks(k)) for k in range(3))
+    ro = np.concatenate([[0], np.cumsum(n)])
+    wo = np.concatenate([[0], np.cumsum(m)])
+    total_blocks = 0
+    for i, (nu, rr, ww, cc) in enumerate(probs):
+        gi = g[wo[i]:wo[i + 1]]
+        ref = oracle.direct(nu, rr, ww, cc)
+        assert np.max(np.abs(gi - ref)) <= tol(eps, cc), i
+        gs, info, blocks = run_forward(nu, rr, ww, cc, eps)
+        assert np.max(np.abs(gi - gs)) <= 1e-3 * tol(eps, cc)
+        total_blocks += sum(len(b) for b in blocks)
+    assert nblk == total_blocks
+
+
+def test_batched_edge_problems():
+    from paper_2411_09583_gb300 import Plan
+    rng = np.random.default_rng(43)
+    sizes = [(0, 5), (7, 0), (1, 1), (300, 200), (0, 0), (50, 60)]
+    nus = [0, 3, 1, 2, 0, 20]
+    rs = [rng.uniform(0, 1, a) for a, _ in sizes]
+    ws = [rng.uniform(0, 500, b) for _, b in sizes]
+    cs = [rng.standard_normal(a) for a, _ in sizes]
+    with Plan.many(nus, to_dev(np.concatenate(rs)), [a for a, _ in sizes],
+                   to_dev(np.concatenate(ws)), [b for _, b in sizes], 1e-9) as bp:
+        g = bp.execute(to_dev(np.concatenate(cs))).cpu().numpy()
+    off = 0
+    for nu, rr, ww, cc in zip(nus, rs, ws, cs):
+        gi = g[off:off + ww.size]
+        off += ww.size
+        ref = oracle.direct(nu, rr, ww, cc) if rr.size else np.zeros(ww.size)
+        assert np.max(np.abs(gi - ref), initial=0.0) <= 10 * 1e-9 * max(np.abs(cc).sum(), 1e-300)
