@@ -301,6 +301,39 @@ def run_batched(dev, steps):
             "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]]}
 
 
+def run_mixed(dev, steps):
+    """n = m = 4e6, nu = 1, r = 10^U[-3,0], omega ~ U[0, 4e4], complex c, eps = 1e-5:
+    the FP32 mixed path and the FP64 path on the same problem (plan + execute)."""
+    import torch
+
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import loguniform_problem
+    r, omega, c = loguniform_problem(4_000_000, 4_000_000, omega_max=4e4, seed=4, complex_c=True)
+    dr, dw, dc = (torch.tensor(x, device=dev) for x in (r, omega, c))
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "n = m = 4e6, nu = 1, r = 10^U[-3,0], omega ~ U[0,4e4], complex c, eps 1e-5",
+           "unit": UNIT}
+    for prec in ("mixed", "fp64"):
+        for _ in range(2):
+            with Plan(1, dr, dw, 1e-5, precision=prec) as p:
+                p.execute(dc)
+        ms = []
+        for _ in range(max(3, steps // 4)):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            p = Plan(1, dr, dw, 1e-5, precision=prec)
+            p.execute(dc)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(s0.elapsed_time(s1))
+            p.close()
+        t = statistics.median(ms)
+        out[prec] = {"ms_per_step": t, "value": 8e6 / (t * 1e-3)}
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -424,9 +457,10 @@ def run_ours(a):
                 "traffic": stored_traffic(kernel_of.get(dom, dom),
                                           workload_config(a)["workload"])}
 
-    extra_batched = None
+    extra_batched = extra_mixed = None
     if not a.no_extra and ws == 1:
         extra_batched = run_batched(dev, a.steps)
+        extra_mixed = run_mixed(dev, a.steps)
 
     line = None
     if rank == 0:
@@ -452,6 +486,7 @@ def run_ours(a):
                                  "ms_per_step": 1e3 * exe_s / a.steps},
                 "stage_ms": mean_stage,
                 "batched": extra_batched,
+                "mixed_precision": extra_mixed,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],

@@ -468,7 +468,218 @@ __global__ void __launch_bounds__(128, 4) k_asy_interp(const ProbParams* __restr
     atomicAdd(&g_s[k], (double)P.sgn * val);
 }
 
+// ------------------------------------------------------ mixed precision (FP32)
+// sin, cos of the exact product a*b: FP64 reduction modulo pi/2 (as in
+// df_sincos_prod), FP32 sine and cosine of the remainder |t| <= pi/4.
+__device__ __forceinline__ void f32_sincos_prod(double a, double b, float* sn, float* cs)
+{
+    const double kPio2Hi = 1.5707963267948966;
+    const double kPio2Lo = 6.123233995736766e-17;
+    const double p = a * b;
+    const double e = fma(a, b, -p);
+    const double k = rint(p * 0.6366197723675814);
+    double t = fma(-k, kPio2Hi, p);
+    t = fma(-k, kPio2Lo, t) + e;
+    float s0, c0;
+    sincosf((float)t, &s0, &c0);
+    switch ((int)((long long)k & 3)) {
+        case 0: *sn = s0; *cs = c0; break;
+        case 1: *sn = c0; *cs = -s0; break;
+        case 2: *sn = -s0; *cs = -c0; break;
+        default: *sn = -c0; *cs = s0; break;
+    }
+}
+
+__device__ __forceinline__ float horner_f32(const float2* __restrict__ c, int deg, float v)
+{
+    float acc = c[deg].x;
+    for (int k = deg - 1; k >= 0; --k) acc = fmaf(acc, v, c[k].x);
+    return acc;
+}
+
+// FP32 spreading (same structure as k_asy_spread; coordinates in FP64).
+__global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+                                 const Tile* __restrict__ tiles, Tables tab,
+                                 const double* __restrict__ r_s, const double* __restrict__ c_s,
+                                 double2* __restrict__ grid_b)
+{
+    extern __shared__ float2 smf[];
+    const Tile t = tiles[blockIdx.x];
+    const AsyBlock B = blks[t.blk];
+    const int Q = probs[B.prob].Q;
+    const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
+    const int ncoef = w * (deg + 1);
+    float2* aval = smf;                              // [nt][Q]
+    float2* coef = aval + nt * Q;                    // [w][deg+1]
+    float* taps = (float*)(coef + ncoef);            // [nt][w]
+    int* l0s = (int*)(taps + nt * w);                // [nt]
+    for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
+    __syncthreads();
+    const int cnt = t.count;
+    if (tid < cnt) {
+        const int64_t j = t.start + tid;
+        const double rj = r_s[j];
+        const double x = rj - B.rc;
+        const double a = x * B.inv_h - tab.half_w;
+        const double lf = ceil(a);
+        const float z0 = fminf(fmaxf((float)(lf - a), 0.f), 1.f);
+        const float v = 2.f * z0 - 1.f;
+        for (int i = 0; i < w; ++i) taps[tid * w + i] = horner_f32(coef + i * (deg + 1), deg, v);
+        l0s[tid] = (int)lf;
+        float sn, cs;
+        f32_sincos_prod(B.wc, x, &sn, &cs);
+        const float ratio = (float)(B.rho / rj);
+        const float w0 = (float)c_s[j] * sqrtf(ratio);
+        float wr = w0 * cs, wi = w0 * sn;
+        for (int q = 0; q < Q; ++q) {
+            aval[tid * Q + q] = make_float2(wr, wi);
+            wr *= ratio;
+            wi *= ratio;
+        }
+    }
+    __syncthreads();
+    const int lfirst = l0s[0];
+    const int span = l0s[cnt - 1] - lfirst + w;
+    const int nf1 = 2 * B.N1 + 1;
+    double2* gb = grid_b + B.b_off;
+    const bool dense = span <= 2 * w;
+    for (int item = tid; item < span * Q; item += nt) {
+        const int c = item / Q, q = item - c * Q;
+        const int cell = lfirst + c;
+        int p_lo = 0, p_hi = cnt;
+        if (!dense) {
+            int lo = 0, hi = cnt;
+            const int key = cell - w + 1;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
+            p_lo = lo;
+            hi = cnt;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (l0s[mid] <= cell) lo = mid + 1; else hi = mid; }
+            p_hi = lo;
+        }
+        float sr = 0.f, si = 0.f;
+        for (int p = p_lo; p < p_hi; ++p) {
+            const int i = cell - l0s[p];
+            if (i >= 0 && i < w) {
+                const float k = taps[p * w + i];
+                const float2 av = aval[p * Q + q];
+                sr = fmaf(k, av.x, sr);
+                si = fmaf(k, av.y, si);
+            }
+        }
+        const int idx = cell + B.N1;
+        if (idx >= 0 && idx < nf1 && (sr != 0.f || si != 0.f)) {
+            atomicAdd(&gb[(int64_t)idx * Q + q].x, (double)sr);
+            atomicAdd(&gb[(int64_t)idx * Q + q].y, (double)si);
+        }
+    }
+}
+
+// FP32 interpolation and Hankel combination (coordinates and phase reduction in FP64).
+__global__ void __launch_bounds__(128) k_asy_interp_f32(
+    const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
+    Tables tab, const double* __restrict__ w_s, const float4* __restrict__ grid_q, double* __restrict__ g_s)
+{
+    extern __shared__ float4 winf[];
+    const Tile t = tiles[blockIdx.x];
+    const AsyBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int w = tab.w, deg = tab.deg;
+    const int Q = P.Q;
+    float2* coef2 = (float2*)(winf + kWinCells * Q);
+    int* t0s = (int*)(coef2 + w * (deg + 1));
+    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    const bool valid = (int)threadIdx.x < t.count;
+    const int64_t k = t.start + (valid ? threadIdx.x : 0);
+    const double wk = w_s[k];
+    const double s = wk - B.wc;
+    const double a = s * B.h * B.inv_delta - tab.half_w;
+    const double tf = ceil(a);
+    const float v = 2.f * fminf(fmaxf((float)(tf - a), 0.f), 1.f) - 1.f;
+    const int t0 = (int)tf;
+    if (valid) t0s[threadIdx.x] = t0;
+    __syncthreads();
+    const int wstart = t0s[0];
+    const int wlen = t0s[t.count - 1] - wstart + w;
+    const int mask = B.nf2 - 1;
+    const float4* gq = grid_q + B.q_off;
+    const bool staged = wlen <= kWinCells;
+    if (staged)
+        for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
+            const int cc = idx / Q;
+            winf[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
+        }
+    __syncthreads();
+    if (!valid) return;
+    float tp[kMaxW];
+#pragma unroll
+    for (int i = 0; i < kMaxW; ++i) tp[i] = (i < w) ? horner_f32(coef2 + i * (deg + 1), deg, v) : 0.f;
+    const float m1 = (float)(1.0 / (wk * B.rho));
+    float tr = 0.f, ti = 0.f, mq = 1.f;
+    for (int q = 0; q < Q; ++q) {
+        float pr = 0.f, pi = 0.f;
+#pragma unroll
+        for (int i = 0; i < kMaxW; ++i) {
+            if (i < w) {
+                const float4 gv = staged ? winf[(t0 + i - wstart) * Q + q]
+                                         : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                pr = fmaf(tp[i], gv.x, pr);
+                pi = fmaf(tp[i], gv.z, pi);
+            }
+        }
+        const float cq = P.a2[q].x * mq;
+        switch (q & 3) {
+            case 0: tr = fmaf(cq, pr, tr); ti = fmaf(cq, pi, ti); break;
+            case 1: tr = fmaf(-cq, pi, tr); ti = fmaf(cq, pr, ti); break;
+            case 2: tr = fmaf(-cq, pr, tr); ti = fmaf(-cq, pi, ti); break;
+            default: tr = fmaf(cq, pi, tr); ti = fmaf(-cq, pr, ti); break;
+        }
+        mq *= m1;
+    }
+    float sn, cs;
+    f32_sincos_prod(wk, B.rc, &sn, &cs);
+    const float cph = (float)P.cphi, sph = (float)P.sphi;
+    const float ur = cph * tr - sph * ti, ui = sph * tr + cph * ti;
+    const float re = cs * ur - sn * ui;
+    // psi^(alpha s) in FP32 from the table's high parts
+    const double xi = fabs(B.alpha * s) * tab.ph_scale;
+    int piece = (int)xi;
+    if (piece > tab.ph_pieces - 1) piece = tab.ph_pieces - 1;
+    const float ph = horner_f32(tab.ph2 + piece * (tab.ph_deg + 1), tab.ph_deg,
+                                (float)(2.0 * (xi - (double)piece) - 1.0));
+    const float val = (float)tab.interp_const * sqrtf(m1) / ph * re;
+    atomicAdd(&g_s[k], (double)P.sgn * (double)val);
+}
+
 }  // namespace
+
+cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* r_s,
+                                  const double* c_s, double2* grid_b, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    const int nt = (qmax > 16) ? 128 : 256;
+    size_t smem = sizeof(float2) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
+                  sizeof(float) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
+    cudaError_t e = cudaFuncSetAttribute(k_asy_spread_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
+                                  double* g_s, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    size_t smem = sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
+                  sizeof(int) * 128;
+    cudaError_t e = cudaFuncSetAttribute(k_asy_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_asy_interp_f32<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* r_s,

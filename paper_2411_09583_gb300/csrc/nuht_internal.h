@@ -133,6 +133,12 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* r_s,
                               const double* c_s, double2* grid_b, cudaStream_t s);
+cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* r_s,
+                                  const double* c_s, double2* grid_b, cudaStream_t s);
+cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
+                                  double* g_s, cudaStream_t s);
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* grid_b,
                                  float4* grid_q, cudaStream_t s);

@@ -654,6 +654,7 @@ int nuht_plan(nuht_plan_t* out, int nu, const double* r, int64_t n, const double
     nuht_opts o;
     int rc = check_opts(opt, o);
     if (rc != NUHT_OK) return rc;
+    if (o.precision == NUHT_PREC_MIXED && eps < 1e-6) return NUHT_ERR_UNSUPPORTED;
     nuht_plan_t P = new (std::nothrow) nuht_plan_s();
     if (!P) return NUHT_ERR_NOMEM;
     P->nu_user = nu;
@@ -691,6 +692,7 @@ int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, 
     nuht_opts o;
     int rc = check_opts(opt, o);
     if (rc != NUHT_OK) return rc;
+    if (o.precision == NUHT_PREC_MIXED && eps < 1e-6) return NUHT_ERR_UNSUPPORTED;
     nuht_plan_t P = new (std::nothrow) nuht_plan_s();
     if (!P) return NUHT_ERR_NOMEM;
     P->nu_user = nu[0];
@@ -749,8 +751,12 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if ((mask & 2) && P->n_asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
-        NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab,
-                                  P->d_r, P->d_cs, P->d_gb, s));
+        if (P->opt.precision == NUHT_PREC_MIXED)
+            NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab,
+                                          P->d_r, P->d_cs, P->d_gb, s));
+        else
+            NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab,
+                                      P->d_r, P->d_cs, P->d_gb, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_gb,
@@ -762,8 +768,12 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                          P->d_gb, P->d_gtmp, P->d_gq, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
-        NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                  P->d_w, P->d_gq, P->d_gs, s));
+        if (P->opt.precision == NUHT_PREC_MIXED)
+            NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
+                                          P->d_w, P->d_gq, P->d_gs, s));
+        else
+            NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
+                                      P->d_w, P->d_gq, P->d_gs, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
     }
     return NUHT_OK;

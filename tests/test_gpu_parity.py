@@ -249,3 +249,35 @@ def test_batched_edge_problems():
         off += ww.size
         ref = oracle.direct(nu, rr, ww, cc) if rr.size else np.zeros(ww.size)
         assert np.max(np.abs(gi - ref), initial=0.0) <= 10 * 1e-9 * max(np.abs(cc).sum(), 1e-300)
+
+
+@pytest.mark.parametrize("nu", [0, 1, 4])
+def test_mixed_precision_small(nu):
+    # FP32 spreading / interpolation at eps = 1e-5 (and 1e-6) against the FP64 oracle
+    r, omega, c = loguniform_problem(3000, 2500, omega_max=4e4, seed=50 + nu, complex_c=True)
+    ref = oracle.direct(nu, r, omega, c)
+    for eps in (1e-5, 1e-6):
+        g, info, _ = run_forward(nu, r, omega, c, eps, precision="mixed")
+        err = np.max(np.abs(g - ref))
+        assert err <= 10 * eps * np.abs(c).sum(), (eps, err)
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert rel <= 10 * eps, (eps, rel)
+
+
+def test_mixed_precision_rejects_tight_eps():
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300._native import NUHT_ERR_UNSUPPORTED, NuhtError
+    with pytest.raises(NuhtError) as e:
+        Plan(0, to_dev(np.ones(4)), to_dev(np.ones(4)), 1e-9, precision="mixed")
+    assert e.value.code == NUHT_ERR_UNSUPPORTED
+
+
+def test_mixed_precision_full_size_sampled():
+    # n = m = 4e6, nu = 1, r log-uniform on [1e-3, 1], omega ~ U[0, 4e4], complex c, eps = 1e-5
+    eps = 1e-5
+    r, omega, c = loguniform_problem(4_000_000, 4_000_000, omega_max=4e4, seed=4, complex_c=True)
+    g, info, _ = run_forward(1, r, omega, c, eps, precision="mixed")
+    rows = sample_rows(omega.size, 100, seed=98)
+    ref = oracle.direct_rows(1, r, omega, c, rows)
+    err = np.max(np.abs(g[rows] - ref))
+    assert err <= 10 * eps * np.abs(c).sum(), err
