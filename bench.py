@@ -334,6 +334,48 @@ def run_mixed(dev, steps):
     return out
 
 
+def run_grad(dev, steps):
+    """n = m = 1e6, nu = 0, r ~ U[0,1], omega ~ U[0,1e5], eps = 1e-10: one step of
+    L = 1/2 ||A c - g*||^2 with dL/dc (adjoint) and dL/dr (adjoints of orders nu +- 1),
+    plans included."""
+    import numpy as np
+    import torch
+
+    from paper_2411_09583_gb300 import Plan, nuht_autograd
+    from paper_2411_09583_gb300.workloads import uniform_problem
+    r, omega, c = uniform_problem(1_000_000, 1_000_000, omega_max=1e5, seed=6)
+    dr, dw, dc = (torch.tensor(x, device=dev) for x in (r, omega, c))
+    delta = torch.tensor(np.random.default_rng(7).standard_normal(c.size), device=dev)
+    with Plan(0, dr, dw, 1e-10) as p:
+        gstar = p.execute(dc + 0.01 * delta)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one():
+        tc = dc.clone().requires_grad_(True)
+        tr = dr.clone().requires_grad_(True)
+        g = nuht_autograd(tc, tr, dw, 0, 1e-10)
+        loss = 0.5 * ((g - gstar) ** 2).sum()
+        loss.backward()
+        return tc.grad, tr.grad
+
+    for _ in range(2):
+        one()
+    ms = []
+    for _ in range(max(3, steps // 4)):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        one()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(s0.elapsed_time(s1))
+    t = statistics.median(ms)
+    return {"workload": "n = m = 1e6, nu = 0, eps 1e-10, loss 1/2||A c - g*||^2, grads c and r",
+            "ms_per_step": t, "value": 2e6 / (t * 1e-3), "unit": UNIT,
+            "step": "plan + forward + adjoint (dL/dc) + plans and adjoints of orders nu-1, nu+1 (dL/dr)"}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -457,10 +499,11 @@ def run_ours(a):
                 "traffic": stored_traffic(kernel_of.get(dom, dom),
                                           workload_config(a)["workload"])}
 
-    extra_batched = extra_mixed = None
+    extra_batched = extra_mixed = extra_grad = None
     if not a.no_extra and ws == 1:
         extra_batched = run_batched(dev, a.steps)
         extra_mixed = run_mixed(dev, a.steps)
+        extra_grad = run_grad(dev, a.steps)
 
     line = None
     if rank == 0:
@@ -487,6 +530,7 @@ def run_ours(a):
                 "stage_ms": mean_stage,
                 "batched": extra_batched,
                 "mixed_precision": extra_mixed,
+                "differentiation": extra_grad,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],

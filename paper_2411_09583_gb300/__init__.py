@@ -6,3 +6,4 @@ Compute runs in libnuht.so (hand-written CUDA for sm_103a, C ABI in
 include/nuht.h); ``nuht.py`` is the Python binding.
 """
 from .nuht import Plan, choose_params, nuht, transform_host  # noqa: F401
+from .autograd import nuht_autograd  # noqa: F401,E402

@@ -37,6 +37,7 @@ namespace nuht {
 namespace {
 
 constexpr int kWinCells = 64;   // grid cells an interpolation tile stages in shared memory
+constexpr int kInterpTileThreads = 128;   // frequencies per interpolation tile (host: kInterpTile)
 
 __device__ __forceinline__ double horner(const double* c, int deg, double v)
 {
@@ -224,9 +225,39 @@ __device__ __forceinline__ float4 split4(double2 v)
     return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
 }
 
+// FFT input / output of the forward (ADJ = false) and the transposed
+// (ADJ = true) type-3 pipelines.  Forward: modes l (|l| <= N1) of the spread
+// grid src (at b_off), corrected by 1/psi^(alpha2 l), transformed to every t
+// and stored split at dst + q_off.  Transposed: the target grid src (at q_off,
+// every t) is transformed (the DFT matrix e^{2 pi i l t / nf2} is symmetric),
+// and only the modes |l| <= N1 are kept, corrected, and stored split at
+// dst + b_off.
+template <bool ADJ>
+__device__ __forceinline__ double2 fft_in(const AsyBlock& B, const Tables& tab, const double2* __restrict__ src,
+                                          int Q, int q, int tt)
+{
+    if (ADJ) return src[B.q_off + (int64_t)tt * Q + q];
+    return corrected_mode(B, tab, src + B.b_off, Q, q, tt);
+}
+
+template <bool ADJ>
+__device__ __forceinline__ void fft_out(const AsyBlock& B, const Tables& tab, float4* __restrict__ dst, int Q,
+                                        int q, int tt, double2 v)
+{
+    if (!ADJ) {
+        dst[B.q_off + (int64_t)tt * Q + q] = split4(v);
+        return;
+    }
+    const int l = (tt < (B.nf2 >> 1)) ? tt : tt - B.nf2;
+    if (l < -B.N1 || l > B.N1) return;
+    const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
+    dst[B.b_off + (int64_t)(l + B.N1) * Q + q] = split4(make_double2(v.x * sc, v.y * sc));
+}
+
+template <bool ADJ>
 __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
-                                const double2* __restrict__ grid_b, float4* __restrict__ grid_q)
+                                const double2* __restrict__ src, float4* __restrict__ dst)
 {
     extern __shared__ double2 X[];
     const Tile it = items[blockIdx.x];
@@ -234,39 +265,40 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
     const int Q = probs[B.prob].Q;
     const int q = (int)it.start;
     const int N = B.nf2, logN = B.log2nf2;
-    const double2* gb = grid_b + B.b_off;
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x)
-        X[__brev(tt) >> (32 - logN)] = corrected_mode(B, tab, gb, Q, q, tt);
+        X[__brev(tt) >> (32 - logN)] = fft_in<ADJ>(B, tab, src, Q, q, tt);
     __syncthreads();
     smem_fft(X, logN, tab.tw, tab.tw_log2);
-    float4* gq = grid_q + B.q_off;
-    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) gq[(int64_t)tt * Q + q] = split4(X[tt]);
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, q, tt, X[tt]);
 }
 
 // All Q grids of one small block (nf2 * Q <= kFftSmemMax) in one CTA: the
 // deconvolution factor of each mode is computed once and used for every q;
 // the Q transforms share every butterfly stage.
+template <bool ADJ>
 __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
-                                const double2* __restrict__ grid_b, float4* __restrict__ grid_q)
+                                const double2* __restrict__ src, float4* __restrict__ dst)
 {
     extern __shared__ double2 X[];   // [Q][N], each grid bit-reversed
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
     const int N = B.nf2, logN = B.log2nf2, half = N >> 1;
-    const double2* gb = grid_b + B.b_off;
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x) {
         const int l = (tt < half) ? tt : tt - N;
-        const int dst = __brev(tt) >> (32 - logN);
-        if (l < -B.N1 || l > B.N1) {
-            for (int q = 0; q < Q; ++q) X[q * N + dst] = make_double2(0.0, 0.0);
+        const int dst_i = __brev(tt) >> (32 - logN);
+        if (ADJ) {
+            const double2* row = src + B.q_off + (int64_t)tt * Q;
+            for (int q = 0; q < Q; ++q) X[q * N + dst_i] = row[q];
+        } else if (l < -B.N1 || l > B.N1) {
+            for (int q = 0; q < Q; ++q) X[q * N + dst_i] = make_double2(0.0, 0.0);
         } else {
             const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
-            const double2* src = gb + (int64_t)(l + B.N1) * Q;
+            const double2* row = src + B.b_off + (int64_t)(l + B.N1) * Q;
             for (int q = 0; q < Q; ++q) {
-                const double2 v = src[q];
-                X[q * N + dst] = make_double2(v.x * sc, v.y * sc);
+                const double2 v = row[q];
+                X[q * N + dst_i] = make_double2(v.x * sc, v.y * sc);
             }
         }
     }
@@ -288,10 +320,22 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
         }
         __syncthreads();
     }
-    float4* gq = grid_q + B.q_off;
-    for (int idx = threadIdx.x; idx < N * Q; idx += blockDim.x) {
-        const int tt = idx / Q, q = idx - tt * Q;
-        gq[idx] = split4(X[q * N + tt]);
+    if (!ADJ) {
+        float4* gq = dst + B.q_off;
+        for (int idx = threadIdx.x; idx < N * Q; idx += blockDim.x) {
+            const int tt = idx / Q, q = idx - tt * Q;
+            gq[idx] = split4(X[q * N + tt]);
+        }
+    } else {
+        const int nf1 = 2 * B.N1 + 1;
+        float4* gb = dst + B.b_off;
+        for (int idx = threadIdx.x; idx < nf1 * Q; idx += blockDim.x) {
+            const int li = idx / Q, q = idx - li * Q;
+            const int l = li - B.N1;
+            const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
+            const double2 v = X[q * N + (l & (N - 1))];
+            gb[idx] = split4(make_double2(v.x * sc, v.y * sc));
+        }
     }
 }
 
@@ -299,9 +343,10 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
 // Pass A (line = n1): FFT over n2 of x[n1 + N1 n2], times e^{2 pi i n1 k2 / N},
 // stored at tmp[n1 + N1 k2].  Pass B (line = k2): FFT over n1 of
 // tmp[n1 + N1 k2], stored at X[k2 + N2 k1].
+template <bool ADJ>
 __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
-                                 const double2* __restrict__ grid_b, double2* __restrict__ tmp)
+                                 const double2* __restrict__ src, double2* __restrict__ tmp)
 {
     extern __shared__ double2 X[];
     const Tile it = items[blockIdx.x];
@@ -312,9 +357,8 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
     const int N1 = N >> logN2;
     const int iq = (int)(it.start / N1);
     const int n1 = (int)(it.start - (int64_t)iq * N1);
-    const double2* gb = grid_b + B.b_off;
     for (int n2 = threadIdx.x; n2 < N2; n2 += blockDim.x)
-        X[__brev(n2) >> (32 - logN2)] = corrected_mode(B, tab, gb, Q, iq, n1 + N1 * n2);
+        X[__brev(n2) >> (32 - logN2)] = fft_in<ADJ>(B, tab, src, Q, iq, n1 + N1 * n2);
     __syncthreads();
     smem_fft(X, logN2, tab.tw, tab.tw_log2);
     double2* tq = tmp + B.q_off;
@@ -328,15 +372,15 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
     }
 }
 
+template <bool ADJ>
 __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
-                                 const double2* __restrict__ tmp, float4* __restrict__ grid_q)
+                                 const double2* __restrict__ tmp, float4* __restrict__ dst)
 {
     extern __shared__ double2 X[];
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
-    const int N = B.nf2;
     const int logN2 = 12, N2 = 1 << logN2;
     const int logN1 = B.log2nf2 - logN2, N1 = 1 << logN1;
     const int iq = (int)(it.start >> logN2);
@@ -346,10 +390,7 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
         X[logN1 > 0 ? (__brev(n1) >> (32 - logN1)) : 0] = tq[(int64_t)(n1 + N1 * k2) * Q + iq];
     __syncthreads();
     smem_fft(X, logN1, tab.tw, tab.tw_log2);
-    float4* gq = grid_q + B.q_off;
-    for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x)
-        gq[(int64_t)(k2 + N2 * k1) * Q + iq] = split4(X[k1]);
-    (void)N;
+    for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, iq, k2 + N2 * k1, X[k1]);
 }
 
 // ------------------------------------------------------------ interpolate
@@ -466,6 +507,206 @@ __global__ void __launch_bounds__(128, 4) k_asy_interp(const ProbParams* __restr
     const df scale = df_mul(df_sqrt(m1d), df_recip(psihat_df(tab, B.alpha * s)));
     const double val = tab.interp_const * df_to(df_mul(scale, re));
     atomicAdd(&g_s[k], (double)P.sgn * val);
+}
+
+// ------------------------------------------------------------------ adjoint
+// Transposed asymptotic block.  The forward map is
+//   g = Re( D_out I W C S D_in c ),
+// D_in = e^{i w_c x_j} (r_j/rho)^(-q-1/2) (per q), S = spreading, C =
+// 1/psi^(alpha2 l), W = the DFT e^{2 pi i l t / nf2}, I = interpolation at
+// theta_k, D_out = sqrt(2/pi) (4/w^2) / psi^(alpha s_k) (omega_k rho)^(-1/2)
+// e^{i (omega_k r_c + phi)} a_q i^q (omega_k rho)^(-q).  Its transpose on real
+// vectors is c = Re( D_in S^T C W I^T D_out g ) (every diagonal factor is
+// symmetric, W is symmetric, S and I are real): the frequencies spread
+// g_k D_out onto the FFT grid (I^T), the same FFT and correction follow, and
+// the points interpolate the corrected modes (S^T) with D_in.
+
+// Frequencies of a tile -> FFT grid (periodic, atomics into tgrid).
+__global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+                                 const Tile* __restrict__ tiles, Tables tab,
+                                 const double* __restrict__ w_s, const double* __restrict__ g_s,
+                                 double2* __restrict__ tgrid)
+{
+    extern __shared__ float4 sma[];
+    const Tile t = tiles[blockIdx.x];
+    const AsyBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int Q = P.Q;
+    const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
+    const int ncoef = w * (deg + 1);
+    float4* uval = sma;                                 // [nt][Q]
+    float2* coef = (float2*)(uval + nt * Q);            // [w][deg+1]
+    float2* taps = coef + ncoef;                        // [nt][w]
+    int* t0s = (int*)(taps + nt * w);                   // [nt]
+    for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
+    __syncthreads();
+    const int cnt = t.count;
+    if (tid < cnt) {
+        const int64_t k = t.start + tid;
+        const double wk = w_s[k];
+        const double s = wk - B.wc;
+        const double a = s * B.h * B.inv_delta - tab.half_w;
+        const double tf = ceil(a);
+        double z0 = fmin(fmax(tf - a, 0.0), 1.0);
+        const double v = 2.0 * z0 - 1.0;
+        const float vh = (float)v, vl = (float)(v - (double)vh);
+        for (int i = 0; i < w; ++i) {
+            const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
+            taps[tid * w + i] = make_float2(tp.h, tp.l);
+        }
+        t0s[tid] = (int)tf;
+        // g_k sqrt(2/pi) (4/w^2) / psi^(alpha s) (omega rho)^(-1/2) e^{i (omega r_c + phi)}
+        const df m1d = df_recip(df_from(wk * B.rho));
+        df sn, cs;
+        df_sincos_prod(wk, B.rc, &sn, &cs);
+        const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
+        const df er = df_add(df_mul(cs, cph), df_negate(df_mul(sn, sph)));
+        const df ei = df_add(df_mul(sn, cph), df_mul(cs, sph));
+        const df amp = df_mul(df_mul(df_from((double)P.sgn * g_s[k] * tab.interp_const), df_sqrt(m1d)),
+                              df_recip(psihat_df(tab, B.alpha * s)));
+        df fr = df_mul(amp, er), fi = df_mul(amp, ei);
+        df mq{1.f, 0.f};
+        for (int q = 0; q < Q; ++q) {
+            const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
+            // (fr + i fi) i^q cq
+            df ur, ui;
+            switch (q & 3) {
+                case 0: ur = fr; ui = fi; break;
+                case 1: ur = df_negate(fi); ui = fr; break;
+                case 2: ur = df_negate(fr); ui = df_negate(fi); break;
+                default: ur = fi; ui = df_negate(fr); break;
+            }
+            ur = df_mul(ur, cq);
+            ui = df_mul(ui, cq);
+            uval[tid * Q + q] = make_float4(ur.h, ur.l, ui.h, ui.l);
+            mq = df_mul(mq, m1d);
+        }
+    }
+    __syncthreads();
+    const int tfirst = t0s[0];
+    const int span = t0s[cnt - 1] - tfirst + w;
+    const int mask = B.nf2 - 1;
+    double2* tg = tgrid + B.q_off;
+    const bool dense = span <= 2 * w;
+    for (int item = tid; item < span * Q; item += nt) {
+        const int c = item / Q, q = item - c * Q;
+        const int cell = tfirst + c;
+        int p_lo = 0, p_hi = cnt;
+        if (!dense) {
+            int lo = 0, hi = cnt;
+            const int key = cell - w + 1;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (t0s[mid] < key) lo = mid + 1; else hi = mid; }
+            p_lo = lo;
+            hi = cnt;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (t0s[mid] <= cell) lo = mid + 1; else hi = mid; }
+            p_hi = lo;
+        }
+        acc2 ar{0.f, 0.f}, ai{0.f, 0.f};
+        bool any = false;
+        for (int p = p_lo; p < p_hi; ++p) {
+            const int i = cell - t0s[p];
+            if (i >= 0 && i < w) {
+                const float2 k2 = taps[p * w + i];
+                const float4 uv = uval[p * Q + q];
+                const df kk{k2.x, k2.y};
+                acc_fma(ar, kk, df{uv.x, uv.y});
+                acc_fma(ai, kk, df{uv.z, uv.w});
+                any = true;
+            }
+        }
+        if (any) {
+            const int64_t o = (int64_t)(cell & mask) * Q + q;
+            atomicAdd(&tg[o].x, acc_value(ar));
+            atomicAdd(&tg[o].y, acc_value(ai));
+        }
+    }
+}
+
+// Points of a tile: interpolate the corrected modes b' (split, at b_off) with
+// the spreading kernel, apply D_in and sum the Hankel terms into c.
+__global__ void __launch_bounds__(128, 4) k_asy_adj_interp(
+    const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
+    Tables tab, const double* __restrict__ r_s, const float4* __restrict__ bgrid, double* __restrict__ c_s)
+{
+    extern __shared__ float4 winb[];
+    const Tile t = tiles[blockIdx.x];
+    const AsyBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int w = tab.w, deg = tab.deg;
+    const int Q = P.Q;
+    float2* coef2 = (float2*)(winb + kWinCells * Q);
+    int* l0s = (int*)(coef2 + w * (deg + 1));
+    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    const float4* gb = bgrid + B.b_off;
+    const int nf1 = 2 * B.N1 + 1;
+    for (int base = 0; base < t.count; base += blockDim.x) {
+        const bool valid = base + (int)threadIdx.x < t.count;
+        const int64_t j = t.start + base + (valid ? threadIdx.x : 0);
+        const double rj = r_s[j];
+        const double x = rj - B.rc;
+        const double a = x * B.inv_h - tab.half_w;
+        const double lf = ceil(a);
+        const double z0 = fmin(fmax(lf - a, 0.0), 1.0);
+        const double v = 2.0 * z0 - 1.0;
+        const int l0 = (int)lf;
+        __syncthreads();
+        if (valid) l0s[threadIdx.x] = l0;
+        __syncthreads();
+        const int last = (t.count - base < (int)blockDim.x ? t.count - base : (int)blockDim.x) - 1;
+        const int wstart = l0s[0];
+        const int wlen = l0s[last] - wstart + w;
+        const bool staged = wlen <= kWinCells;
+        if (staged)
+            for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
+                const int cc = idx / Q;
+                const int li = wstart + cc + B.N1;
+                winb[idx] = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + (idx - cc * Q)]
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        __syncthreads();
+        if (!valid) continue;
+        const float vh = (float)v, vl = (float)(v - (double)vh);
+        float th[kMaxW], tl[kMaxW];
+#pragma unroll
+        for (int i = 0; i < kMaxW; ++i) {
+            if (i < w) {
+                const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
+                th[i] = tp.h;
+                tl[i] = tp.l;
+            } else {
+                th[i] = 0.f;
+                tl[i] = 0.f;
+            }
+        }
+        // T = sum_q (r/rho)^(-q) y_q, y_q = sum_i tap_i b'_{l0 + i, q}
+        const df rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1)
+        acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
+        df mq{1.f, 0.f};
+        for (int q = 0; q < Q; ++q) {
+            acc2 yr{0.f, 0.f}, yi{0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < kMaxW; ++i) {
+                if (i < w) {
+                    const int li = l0 + i + B.N1;
+                    float4 gv;
+                    if (staged) gv = winb[(l0 + i - wstart) * Q + q];
+                    else gv = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const df tp{th[i], tl[i]};
+                    acc_fma(yr, tp, df{gv.x, gv.y});
+                    acc_fma(yi, tp, df{gv.z, gv.w});
+                }
+            }
+            acc_fma(tr, mq, fast_two_sum(yr.s, yr.c));
+            acc_fma(ti, mq, fast_two_sum(yi.s, yi.c));
+            mq = df_mul(mq, rat);
+        }
+        // c_j += Re( e^{i w_c x} (r/rho)^(-1/2) T )
+        df sn, cs;
+        df_sincos_prod(B.wc, x, &sn, &cs);
+        const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
+        const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
+        atomicAdd(&c_s[j], df_to(df_mul(df_sqrt(rat), re)));
+    }
 }
 
 // ------------------------------------------------------ mixed precision (FP32)
@@ -652,6 +893,35 @@ __global__ void __launch_bounds__(128) k_asy_interp_f32(
 
 }  // namespace
 
+cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
+                                  double2* tgrid, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    const int nt = kInterpTileThreads;
+    size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
+                  sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
+    cudaError_t e = cudaFuncSetAttribute(k_asy_adj_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_asy_adj_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, g_s, tgrid);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
+                                  double* c_s, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    size_t smem = sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
+                  sizeof(int) * 128;
+    cudaError_t e = cudaFuncSetAttribute(k_asy_adj_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_asy_adj_interp<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, c_s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* r_s,
                                   const double* c_s, double2* grid_b, cudaStream_t s)
@@ -697,49 +967,53 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
 }
 
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
-                                 int nitems, int max_nf2, Tables tab, const double2* grid_b,
-                                 float4* grid_q, cudaStream_t s)
+                                 int nitems, int max_nf2, Tables tab, const double2* src,
+                                 float4* dst, cudaStream_t s, bool adj)
 {
     if (nitems <= 0) return cudaSuccess;
     size_t smem = sizeof(double2) * (size_t)max_nf2;
-    cudaError_t e = cudaFuncSetAttribute(k_asy_fft_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = adj ? k_asy_fft_small<true> : k_asy_fft_small<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nt = max_nf2 / 2;
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;
-    k_asy_fft_small<<<nitems, nt, smem, s>>>(probs, blks, items, tab, grid_b, grid_q);
+    kern<<<nitems, nt, smem, s>>>(probs, blks, items, tab, src, dst);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
-                                 int nitems, Tables tab, const double2* grid_b, float4* grid_q,
-                                 cudaStream_t s)
+                                 int nitems, Tables tab, const double2* src, float4* dst,
+                                 cudaStream_t s, bool adj)
 {
     if (nitems <= 0) return cudaSuccess;
     size_t smem = sizeof(double2) * (size_t)kFftSmemMax;
-    cudaError_t e = cudaFuncSetAttribute(k_asy_fft_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = adj ? k_asy_fft_block<true> : k_asy_fft_block<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_fft_block<<<nitems, 256, smem, s>>>(probs, blks, items, tab, grid_b, grid_q);
+    kern<<<nitems, 256, smem, s>>>(probs, blks, items, tab, src, dst);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
-                                 const double2* grid_b, double2* tmp, float4* grid_q,
-                                 cudaStream_t s)
+                                 const double2* src, double2* tmp, float4* dst,
+                                 cudaStream_t s, bool adj)
 {
     if (nitems_a <= 0) return cudaSuccess;
     size_t smem = sizeof(double2) * (size_t)kFftSmemMax;
-    cudaError_t e = cudaFuncSetAttribute(k_asy_fft_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto ka = adj ? k_asy_fft_pass_a<true> : k_asy_fft_pass_a<false>;
+    auto kb = adj ? k_asy_fft_pass_b<true> : k_asy_fft_pass_b<false>;
+    cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_asy_fft_pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_fft_pass_a<<<nitems_a, 256, smem, s>>>(probs, blks, items_a, tab, grid_b, tmp);
+    ka<<<nitems_a, 256, smem, s>>>(probs, blks, items_a, tab, src, tmp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_asy_fft_pass_b<<<nitems_b, 256, smem, s>>>(probs, blks, items_b, tab, tmp, grid_q);
+    kb<<<nitems_b, 256, smem, s>>>(probs, blks, items_b, tab, tmp, dst);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -250,7 +250,176 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         atomicAdd(&g_s[B.k0 + i], (double)P.sgn * rowacc[i]);
 }
 
+// ------------------------------------------------------------------ adjoint
+// Transposed local block A_blk^T = T C^T: adjoint moments
+//   nu_l = sum_{k in block} g_k C_l(omega_k R)          (rows, Miller per row)
+// then c_j += sum_l T_{2l(+1)}(r_j / R) nu_l              (columns).
+__global__ void k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                                    const Tile* __restrict__ tiles, const double* __restrict__ w_s,
+                                    const double* __restrict__ g_s, double* __restrict__ mom)
+{
+    extern __shared__ float2 sm2[];
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int nu = P.nu, L = P.L;
+    float2* jb = sm2;                                   // [ntop + 1][nt]
+    acc2* acc = (acc2*)(sm2 + (P.ntop + 1) * nt);      // [L + 1][nt]
+    for (int l = 0; l <= L; ++l) acc[l * nt + tid] = acc2{0.f, 0.f};
+    // the tile's rows in passes of blockDim (the tile may be longer)
+    for (int row = tid; row < t.count; row += nt) {
+        const int64_t k = t.start + row;
+        const double gk = (double)P.sgn * g_s[k];
+        const double y = 0.5 * w_s[k] * B.R;
+        if (y < 1e-100) {
+            if (nu == 0) acc[tid] = acc2{(float)gk, (float)(gk - (double)(float)gk)};
+        } else {
+            const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;
+            const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;
+            const int ntop = hp + L;
+            const int ns = miller_start(ntop, y);
+            df S = (y >= 1.0) ? miller_store_df(y, ntop, ns, jb, nt, tid)
+                              : df_from(series_store_fp64(y, ntop, jb, nt, tid));
+            const float p2 = exp2f(-(float)ilogbf(S.h));
+            S = df_scale(S, p2);
+            // g_k / S^2 (the normalisation of both Bessel factors)
+            const double Sd = df_to(S);
+            const df gs = df_from(gk / (Sd * Sd));
+            for (int l = 0; l <= L; ++l) {
+                const int b = hm - l;
+                const float2 va = jb[(hp + l) * nt + tid];
+                const float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
+                float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
+                if (l > 0 || (nu & 1)) sgn *= 2.f;
+                const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
+                acc_fma(acc[l * nt + tid], cl, gs);
+            }
+        }
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int l = warp; l <= L; l += nw) {
+        double s = 0.0;
+        for (int k = lane; k < nt; k += 32) s += acc_value(acc[l * nt + k]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) atomicAdd(&mom[B.mom_off + l], s);
+    }
+}
+
+__global__ void __launch_bounds__(kMomThreads)
+k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                 const Tile* __restrict__ tiles, const double* __restrict__ r_s,
+                 const double* __restrict__ mom, double* __restrict__ c_s)
+{
+    extern __shared__ float2 mu2[];
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const int L = probs[B.prob].L;
+    const int odd = probs[B.prob].nu & 1;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    for (int l = tid; l <= L; l += nt) {
+        const double v = mom[B.mom_off + l];
+        const float h = (float)v;
+        mu2[l] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+    const double invR = B.R > 0.0 ? 1.0 / B.R : 0.0;
+    for (int64_t j = t.start + tid; j < t.start + t.count; j += nt) {
+        const double y = r_s[j] * invR;
+        const double u = fma(2.0 * y, y, -1.0);
+        const df u2 = df_from(2.0 * u);
+        df t0 = odd ? df_from(y) : df{1.f, 0.f};
+        df t1 = odd ? df_from(y * (2.0 * u - 1.0)) : df_from(u);
+        acc2 sum{0.f, 0.f};
+        acc_fma(sum, t0, df{mu2[0].x, mu2[0].y});
+        if (L >= 1) acc_fma(sum, t1, df{mu2[1].x, mu2[1].y});
+        for (int l = 2; l <= L; ++l) {
+            const df t2 = df_add(df_mul(u2, t1), df_neg(t0));
+            acc_fma(sum, t2, df{mu2[l].x, mu2[l].y});
+            t0 = t1;
+            t1 = t2;
+        }
+        atomicAdd(&c_s[j], acc_value(sum));
+    }
+}
+
+// Transposed direct block: column sums, one atomic add per column.
+__global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
+                             const double* __restrict__ r_s, const double* __restrict__ w_s,
+                             const double* __restrict__ g_s, double* __restrict__ c_s)
+{
+    extern __shared__ double colacc[];
+    const DirectBlock B = blks[blockIdx.x];
+    const ProbParams& P = probs[B.prob];
+    const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
+    const int area = rows * cols;
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) colacc[i] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < area; e += blockDim.x) {
+        const int rr = e / cols, cc = e - rr * cols;
+        const double w = w_s[B.k0 + rr], r = r_s[B.j0 + cc];
+        const double x = w * r;
+        double v;
+        if (x > P.z) v = jn_hankel(P, w, r);
+        else if (x < 1.0) v = jn_series(P.nu, x);
+        else v = jn_miller_df(P.nu, x);
+        atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cols; i += blockDim.x)
+        atomicAdd(&c_s[B.j0 + i], (double)P.sgn * colacc[i]);
+}
+
 }  // namespace
+
+int local_adj_threads(int ntop_max, int lmax)
+{
+    int t = (int)(200 * 1024 / (8 * (ntop_max + 1 + lmax + 1)));
+    t = (t / 32) * 32;
+    if (t > 128) t = 128;
+    if (t < 32) t = 32;
+    return t;
+}
+
+cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                     int ntiles, int ntop_max, int lmax, int threads, const double* w_s,
+                                     const double* g_s, double* mom, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    size_t smem = sizeof(float2) * (size_t)(ntop_max + 1 + lmax + 1) * threads;
+    cudaError_t e = cudaFuncSetAttribute(k_local_adj_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_adj_moments<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w_s, g_s, mom);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                  int ntiles, int lmax, const double* r_s, const double* mom, double* c_s,
+                                  cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    size_t smem = sizeof(float2) * (size_t)(lmax + 1);
+    k_local_adj_eval<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r_s, mom, c_s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
+                              const double* r_s, const double* w_s, const double* g_s, double* c_s,
+                              cudaStream_t s)
+{
+    if (nblk <= 0) return cudaSuccess;
+    size_t smem = sizeof(double) * (size_t)(max_cols > 0 ? max_cols : 1);
+    cudaError_t e = cudaFuncSetAttribute(k_direct_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, g_s, c_s);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                  int ntiles, int lmax, const double* r_s, const double* c_s,

@@ -130,9 +130,25 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           const double* r_s, const double* w_s, const double* c_s, double* g_s,
                           cudaStream_t s);
+int local_adj_threads(int ntop_max, int lmax);
+cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                     int ntiles, int ntop_max, int lmax, int threads, const double* w_s,
+                                     const double* g_s, double* mom, cudaStream_t s);
+cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                  int ntiles, int lmax, const double* r_s, const double* mom, double* c_s,
+                                  cudaStream_t s);
+cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
+                              const double* r_s, const double* w_s, const double* g_s, double* c_s,
+                              cudaStream_t s);
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* r_s,
                               const double* c_s, double2* grid_b, cudaStream_t s);
+cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
+                                  double2* tgrid, cudaStream_t s);
+cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
+                                  int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
+                                  double* c_s, cudaStream_t s);
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* r_s,
                                   const double* c_s, double2* grid_b, cudaStream_t s);
@@ -140,15 +156,15 @@ cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
                                   double* g_s, cudaStream_t s);
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
-                                 int nitems, int max_nf2, Tables tab, const double2* grid_b,
-                                 float4* grid_q, cudaStream_t s);
+                                 int nitems, int max_nf2, Tables tab, const double2* src,
+                                 float4* dst, cudaStream_t s, bool adj = false);
 cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
-                                 int nitems, Tables tab, const double2* grid_b, float4* grid_q,
-                                 cudaStream_t s);
+                                 int nitems, Tables tab, const double2* src, float4* dst,
+                                 cudaStream_t s, bool adj = false);
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
-                                 const double2* grid_b, double2* tmp, float4* grid_q,
-                                 cudaStream_t s);
+                                 const double2* src, double2* tmp, float4* dst,
+                                 cudaStream_t s, bool adj = false);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
                               double* g_s, cudaStream_t s);

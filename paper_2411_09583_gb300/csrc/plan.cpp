@@ -87,6 +87,8 @@ struct nuht_plan_s {
     double* d_mom = nullptr;
     double2 *d_gb = nullptr, *d_gtmp = nullptr;
     float4* d_gq = nullptr;   // FFT output, complex values as double-float parts
+    double2* d_tg = nullptr;  // adjoint: frequencies spread onto the FFT grid
+    float4* d_bq = nullptr;   // adjoint: corrected modes, double-float parts
     double *d_cs = nullptr, *d_gs = nullptr;
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
@@ -95,7 +97,7 @@ struct nuht_plan_s {
     int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fblock = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
     int n_dir = 0;
     int64_t mom_len = 0, gb_len = 0, gq_len = 0;
-    int max_nf2_small = 0, max_dir_rows = 0, ntop_max = 0, eval_threads = 0;
+    int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, ntop_max = 0, eval_threads = 0;
     bool has_large_fft = false;
     Tables tab{};
     std::vector<HBlock> hb[3];
@@ -478,8 +480,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         const HBlock& h = DB[b];
         DirectBlock db{h.prob, (int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, 0};
         vdir.push_back(db);
-        const int rows = (int)(h.k1 - h.k0 + 1);
+        const int rows = (int)(h.k1 - h.k0 + 1), cols = (int)(h.j1 - h.j0 + 1);
         if (rows > P->max_dir_rows) P->max_dir_rows = rows;
+        if (cols > P->max_dir_cols) P->max_dir_cols = cols;
         P->direct_entries += (h.k1 - h.k0 + 1) * (h.j1 - h.j0 + 1);
     }
     P->n_loc = (int)vloc.size(); P->n_tmom = smom.total(); P->n_teval = seval.total();
@@ -513,6 +516,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
     size_t a_gt = A.reserve<double2>(P->has_large_fft ? (size_t)P->gq_len : 1);
     size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
+    size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
@@ -563,6 +567,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_mom = (double*)(D + a_mom);
     P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (double2*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
+    P->d_tg = (double2*)(D + a_tg); P->d_bq = (float4*)(D + a_bq);
     Tables& tb = P->tab;
     tb.es = P->d_es; tb.es2 = (const float2*)(D + a_es2);
     tb.w = T.w; tb.deg = T.deg; tb.half_w = 0.5 * T.w;
@@ -805,10 +810,77 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
     return NUHT_OK;
 }
 
+// Transpose of apply_forward: g (sorted, d_gs) -> c (sorted, d_cs).  Each
+// block class runs its transposed pipeline; column contributions of blocks at
+// different levels meet in c with FP64 atomics.
+static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
+{
+    const int mask = P->opt.class_mask;
+    if ((mask & 1) && P->n_loc) {
+        const int thr = local_adj_threads(P->ntop_max, P->lmax);
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, s));
+        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
+        NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, P->lmax,
+                                         thr, P->d_w, P->d_gs, P->d_mom, s));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, s));
+        NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r, P->d_mom,
+                                      P->d_cs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, s));
+    }
+    if ((mask & 4) && P->n_dir) {
+        NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, s));
+        NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->d_r, P->d_w, P->d_gs,
+                                  P->d_cs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_DIRECT, s));
+    }
+    if ((mask & 2) && P->n_asy) {
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
+        NUHT_CK(cudaMemsetAsync(P->d_tg, 0, sizeof(double2) * P->gq_len, s));
+        NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab, P->d_w,
+                                      P->d_gs, P->d_tg, s));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
+        NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_tg, P->d_bq,
+                                     s, true));
+        NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small, P->tab,
+                                     P->d_tg, P->d_bq, s, true));
+        if (P->has_large_fft)
+            NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
+                                         P->d_tg, P->d_gtmp, P->d_bq, s, true));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
+        NUHT_CK(launch_asy_adj_interp(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab, P->d_r,
+                                      P->d_bq, P->d_cs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
+    }
+    return NUHT_OK;
+}
+
 int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_complex, void* stream)
 {
-    (void)P; (void)g; (void)c; (void)nvec; (void)is_complex; (void)stream;
-    return NUHT_ERR_UNSUPPORTED;
+    if (!P || nvec < 1) return NUHT_ERR_INVALID_ARG;
+    if ((P->m > 0 && !g) || (P->n > 0 && !c)) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int comps = nvec * (is_complex ? 2 : 1);
+    if (P->n == 0) return NUHT_OK;
+    if (P->m == 0) {
+        NUHT_CK(cudaMemsetAsync(c, 0, sizeof(double) * P->n * comps, s));
+        return NUHT_OK;
+    }
+    NUHT_TRY(ensure_events(P, comps));
+    for (int comp = 0; comp < comps; ++comp) {
+        StageTimer T{P, comp};
+        NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
+        NUHT_CK(cudaMemsetAsync(P->d_cs, 0, sizeof(double) * P->n, s));
+        NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_gs, s));
+        NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
+        NUHT_TRY(apply_adjoint(P, T, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
+        NUHT_CK(launch_scatter(P->d_cs, P->d_pr, P->n, comps, comp, c, s));
+        NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
+    }
+    return NUHT_OK;
 }
 
 int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega, int64_t m, double eps,

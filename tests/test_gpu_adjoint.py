@@ -1,0 +1,152 @@
+"""GPU parity of the adjoint (transposed) NUHT and of the differentiable transform."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gradient as OG
+from paper_2411_09583_gb300.workloads import loguniform_problem, sample_rows, uniform_problem
+
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import class_reference, dev, to_dev, tol  # noqa: E402
+
+torch = pytest.importorskip("torch")
+
+
+def _adjoint(nu, r, omega, e, eps, **opts):
+    from paper_2411_09583_gb300 import Plan
+    with Plan(nu, to_dev(r), to_dev(omega), eps, **opts) as p:
+        return p.adjoint(to_dev(e)).cpu().numpy(), [p.blocks(k) for k in range(3)]
+
+
+@pytest.mark.parametrize("nu", [0, 1, 5, 12])
+def test_adjoint_matches_oracle_transpose(nu):
+    r, omega, _ = uniform_problem(1500, 1300, omega_max=2500.0, seed=60 + nu)
+    e = np.random.default_rng(61 + nu).standard_normal(omega.size)
+    eps = 1e-10
+    ca, _ = _adjoint(nu, r, omega, e, eps)
+    ref = oracle.direct(nu, omega, r, e)       # (A^T e)_j = sum_k e_k J(omega_k r_j)
+    assert np.max(np.abs(ca - ref)) <= tol(eps, e)
+
+
+@pytest.mark.parametrize("nu", [0, 3])
+def test_dot_product_identity(nu):
+    # <A c, e> = <c, A^T e> for the approximate operator itself (exact transpose)
+    from paper_2411_09583_gb300 import Plan
+    r, omega, c = uniform_problem(3000, 2800, omega_max=4000.0, seed=70 + nu)
+    e = np.random.default_rng(71).standard_normal(omega.size)
+    with Plan(nu, to_dev(r), to_dev(omega), 1e-8) as p:
+        g = p.execute(to_dev(c)).cpu().numpy()
+        ca = p.adjoint(to_dev(e)).cpu().numpy()
+    lhs, rhs = float(np.dot(g, e)), float(np.dot(c, ca))
+    scale = float(np.abs(g).dot(np.abs(e)) + np.abs(c).dot(np.abs(ca)))
+    assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs)
+
+
+@pytest.mark.parametrize("cls", [0, 1, 2])
+def test_adjoint_each_block_class(cls):
+    r, omega, _ = uniform_problem(1400, 1600, omega_max=3000.0, seed=72)
+    e = np.random.default_rng(73).standard_normal(omega.size)
+    eps = 1e-10
+    ca, blocks = _adjoint(0, r, omega, e, eps, class_mask=1 << cls)
+    # transposed blocks: swap the roles of rows and columns
+    swapped = [(j0, j1, k0, k1) for k0, k1, j0, j1 in blocks[cls]]
+    ref = class_reference(0, omega, r, e, swapped)
+    assert np.max(np.abs(ca - ref)) <= tol(eps, e)
+
+
+def test_adjoint_complex_multi_and_clustered():
+    r, omega, _ = loguniform_problem(1200, 1000, omega_max=4e4, seed=74, complex_c=False)
+    rng = np.random.default_rng(75)
+    e = rng.standard_normal((omega.size, 2))
+    ca, _ = _adjoint(1, r, omega, e, 1e-9)
+    ref = oracle.direct(1, omega, r, e)
+    assert np.all(np.max(np.abs(ca - ref), axis=0) <= tol(1e-9, e))
+    ez = e[:, 0] + 1j * e[:, 1]
+    cz, _ = _adjoint(1, r, omega, ez, 1e-9)
+    assert np.max(np.abs(cz - oracle.direct(1, omega, r, ez))) <= 10 * 1e-9 * np.abs(ez).sum()
+
+
+def test_batched_adjoint():
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import batch_problems
+    probs = batch_problems(count=10, lo=100, hi=2000, nu_max=20, seed=76)
+    nus = [p[0] for p in probs]
+    n = [p[1].size for p in probs]
+    m = [p[2].size for p in probs]
+    es = [np.random.default_rng(77 + i).standard_normal(mi) for i, mi in enumerate(m)]
+    with Plan.many(nus, to_dev(np.concatenate([p[1] for p in probs])), n,
+                   to_dev(np.concatenate([p[2] for p in probs])), m, 1e-8) as bp:
+        ca = bp.adjoint(to_dev(np.concatenate(es))).cpu().numpy()
+    off = 0
+    for (nu, rr, ww, _), e in zip(probs, es):
+        ref = oracle.direct(nu, ww, rr, e)
+        assert np.max(np.abs(ca[off:off + rr.size] - ref)) <= tol(1e-8, e)
+        off += rr.size
+
+
+def test_full_size_adjoint_sampled():
+    eps = 1e-12
+    r, omega, _ = uniform_problem(1_000_000, 1_000_000, omega_max=1e5, seed=6)
+    e = np.random.default_rng(78).standard_normal(omega.size)
+    ca, _ = _adjoint(0, r, omega, e, eps)
+    rows = sample_rows(r.size, 100, seed=79)
+    ref = oracle.direct_rows(0, omega, r, e, rows)
+    assert np.max(np.abs(ca[rows] - ref)) <= tol(eps, e)
+
+
+@pytest.mark.parametrize("nu", [0, 2])
+def test_autograd_gradients_match_oracle(nu):
+    # loss 1/2 ||g - g*||^2 with g* from a perturbed c (n = m = 2000), eps = 1e-10
+    from paper_2411_09583_gb300 import nuht_autograd
+    eps = 1e-10
+    r, omega, c = uniform_problem(2000, 2000, omega_max=3000.0, seed=7 + nu)
+    rng = np.random.default_rng(80)
+    gstar = oracle.direct(nu, r, omega, c + 0.01 * rng.standard_normal(c.size))
+    L, dc, dr, dw = OG.gradients(nu, r, omega, c, gstar)
+    tc = to_dev(c).requires_grad_(True)
+    tr = to_dev(r).requires_grad_(True)
+    tw = to_dev(omega).requires_grad_(True)
+    g = nuht_autograd(tc, tr, tw, nu, eps)
+    loss = 0.5 * ((g - to_dev(gstar)) ** 2).sum()
+    loss.backward()
+    e = oracle.direct(nu, r, omega, c) - gstar
+    assert abs(loss.item() - L) <= 1e-6 * L
+    # first-order error bounds: the transforms in the gradient are accurate to
+    # 10 eps ||input||_1, and e itself carries the forward error 10 eps ||c||_1
+    de = 10 * eps * np.abs(c).sum()
+    assert np.max(np.abs(tc.grad.cpu().numpy() - dc)) <= 10 * eps * np.abs(e).sum() + de * omega.size
+    bound_r = np.abs(c) * (10 * eps * np.abs(omega * e).sum() + de * np.abs(omega).sum())
+    assert np.all(np.abs(tr.grad.cpu().numpy() - dr) <= bound_r + 1e-12)
+    bound_w = np.abs(r * c).sum() * (10 * eps * np.abs(e) + de)
+    assert np.all(np.abs(tw.grad.cpu().numpy() - dw) <= bound_w + 1e-12)
+
+
+def test_autograd_finite_differences():
+    # central differences of the GPU loss itself in a few coordinates of c and r
+    from paper_2411_09583_gb300 import nuht_autograd
+    eps = 1e-12
+    r, omega, c = uniform_problem(400, 300, omega_max=800.0, seed=81)
+    gstar = to_dev(np.random.default_rng(82).standard_normal(omega.size))
+
+    def loss_of(cc, rr):
+        g = nuht_autograd(cc, rr, to_dev(omega), 0, eps)
+        return 0.5 * ((g - gstar) ** 2).sum()
+
+    tc = to_dev(c).requires_grad_(True)
+    tr = to_dev(r).requires_grad_(True)
+    loss_of(tc, tr).backward()
+    h = 1e-6
+    for j in (3, 150, 399):
+        for which in ("c", "r"):
+            base_c, base_r = to_dev(c), to_dev(r)
+            dp = torch.zeros_like(base_c)
+            dp[j] = h
+            if which == "c":
+                lp, lm = loss_of(base_c + dp, base_r).item(), loss_of(base_c - dp, base_r).item()
+                grad = tc.grad[j].item()
+            else:
+                lp, lm = loss_of(base_c, base_r + dp).item(), loss_of(base_c, base_r - dp).item()
+                grad = tr.grad[j].item()
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - grad) <= 1e-5 * max(1.0, abs(grad)), (which, j, fd, grad)
