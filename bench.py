@@ -255,18 +255,24 @@ def run_batched(dev, steps):
     dc = torch.tensor(np.concatenate([p[3] for p in probs]), device=dev)
     units = int(sum(n) + sum(m))
     stream = torch.cuda.current_stream(dev)
+    # options picked by the autotuner (execute time of the batch); the orders
+    # differ between problems, so M stays per-problem (heuristic)
+    from paper_2411_09583_gb300.autotune import autotune, candidates
+    grid = candidates(nus, 1e-8, min_sizes=(512, 1024, 2048), spread_tiles=(0, 128), m_offsets=(0,))
+    best, table = autotune(nus, dr, dw, dc, 1e-8, sizes=(n, m), objective="execute", reps=3, grid=grid)
+    default_ms = [t for t, o in table if o == {"min_size": 1024, "spread_tile": 0, "m_terms": 0}]
     for _ in range(2):
-        Plan.many(nus, dr, n, dw, m, 1e-8).close()
+        Plan.many(nus, dr, n, dw, m, 1e-8, **best).close()
     plan_ms = []
     for _ in range(max(3, steps // 4)):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        bp = Plan.many(nus, dr, n, dw, m, 1e-8)
+        bp = Plan.many(nus, dr, n, dw, m, 1e-8, **best)
         s1.record(stream)
         torch.cuda.synchronize(dev)
         plan_ms.append(s0.elapsed_time(s1))
         bp.close()
-    bp = Plan.many(nus, dr, n, dw, m, 1e-8)
+    bp = Plan.many(nus, dr, n, dw, m, 1e-8, **best)
     g = torch.empty(sum(m), dtype=torch.float64, device=dev)
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
@@ -298,6 +304,8 @@ def run_batched(dev, steps):
             "units_n_plus_m": units, "execute_graph_ms": exe, "plan_ms": pl,
             "value_execute": units / (exe * 1e-3), "value_plan_execute": units / ((exe + pl) * 1e-3),
             "unit": UNIT, "execute": "one CUDA graph replay (one launch per stage over all problems)",
+            "autotuned_opts": best, "autotune_default_execute_ms": default_ms[0] if default_ms else None,
+            "autotune_best_execute_ms": table[0][0],
             "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]]}
 
 

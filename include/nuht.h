@@ -72,7 +72,9 @@ typedef struct {
     int class_mask;    /* bit c set = apply blocks of class c (testing aid); default 7 */
     int timing;        /* nonzero: execute records a CUDA event pair around each stage
                           (see nuht_stage_times); default 0 */
-    int reserved[6];   /* must be zero */
+    int spread_tile;   /* points per spreading CTA: 0 = automatic (256, or 128 when
+                          2M > 16); else 64..256, a multiple of 32 */
+    int reserved[5];   /* must be zero */
 } nuht_opts;
 
 /* Execute stages, in launch order (nuht_stage_times / nuht_stage_name). */

@@ -923,11 +923,10 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
 }
 
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* r_s,
+                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s,
                                   const double* c_s, double2* grid_b, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const int nt = (qmax > 16) ? 128 : 256;
     size_t smem = sizeof(float2) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -952,11 +951,10 @@ cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks,
 }
 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, Tables tab, const double* r_s,
+                              int ntiles, int qmax, int nt, Tables tab, const double* r_s,
                               const double* c_s, double2* grid_b, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const int nt = (qmax > 16) ? 128 : 256;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

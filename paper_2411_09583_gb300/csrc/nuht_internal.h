@@ -141,7 +141,7 @@ cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, 
                               const double* r_s, const double* w_s, const double* g_s, double* c_s,
                               cudaStream_t s);
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, Tables tab, const double* r_s,
+                              int ntiles, int qmax, int nt, Tables tab, const double* r_s,
                               const double* c_s, double2* grid_b, cudaStream_t s);
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
@@ -150,7 +150,7 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
                                   int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
                                   double* c_s, cudaStream_t s);
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* r_s,
+                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s,
                                   const double* c_s, double2* grid_b, cudaStream_t s);
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,

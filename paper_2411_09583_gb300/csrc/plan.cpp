@@ -98,6 +98,7 @@ struct nuht_plan_s {
     int n_dir = 0;
     int64_t mom_len = 0, gb_len = 0, gq_len = 0;
     int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, ntop_max = 0, eval_threads = 0;
+    int spread_threads = 256;
     bool has_large_fft = false;
     Tables tab{};
     std::vector<HBlock> hb[3];
@@ -424,7 +425,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         P->local_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
     }
     P->mom_len = mom_off;
-    const int sp_tile = spread_tile_points(P->qmax);
+    const int sp_tile = P->opt.spread_tile ? P->opt.spread_tile : spread_tile_points(P->qmax);
+    P->spread_threads = sp_tile;
     int64_t gb_off = 0, gq_off = 0;
     for (size_t b = 0; b < AB.size(); ++b) {
         const HBlock& h = AB[b];
@@ -642,8 +644,10 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
     if (o.min_size < 1 || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
+    if (o.spread_tile != 0 && (o.spread_tile < 64 || o.spread_tile > 256 || o.spread_tile % 32))
+        return NUHT_ERR_INVALID_ARG;
     return NUHT_OK;
 }
 
@@ -757,11 +761,11 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
         if (P->opt.precision == NUHT_PREC_MIXED)
-            NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab,
-                                          P->d_r, P->d_cs, P->d_gb, s));
+            NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax,
+                                          P->spread_threads, P->tab, P->d_r, P->d_cs, P->d_gb, s));
         else
-            NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab,
-                                      P->d_r, P->d_cs, P->d_gb, s));
+            NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax,
+                                      P->spread_threads, P->tab, P->d_r, P->d_cs, P->d_gb, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_gb,

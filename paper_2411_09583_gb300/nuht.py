@@ -30,7 +30,7 @@ def _dev_f64(x, name):
 
 
 def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class_mask=7,
-              timing=False):
+              timing=False, spread_tile=0):
     o = N.NuhtOpts()
     N.lib().nuht_default_opts(ctypes.byref(o))
     o.precision = {"fp64": N.PREC_FP64, "mixed": N.PREC_MIXED}[precision]
@@ -39,6 +39,7 @@ def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class
     o.m_terms = int(m_terms)
     o.class_mask = int(class_mask)
     o.timing = 1 if timing else 0
+    o.spread_tile = int(spread_tile)
     return o
 
 

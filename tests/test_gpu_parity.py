@@ -281,3 +281,22 @@ def test_mixed_precision_full_size_sampled():
     ref = oracle.direct_rows(1, r, omega, c, rows)
     err = np.max(np.abs(g[rows] - ref))
     assert err <= 10 * eps * np.abs(c).sum(), err
+
+
+def test_autotuner_picks_valid_fast_options():
+    from paper_2411_09583_gb300.autotune import autotune, candidates
+    r, omega, c = uniform_problem(20000, 20000, omega_max=5000.0, seed=90)
+    grid = candidates([0], 1e-10, min_sizes=(512, 2048), spread_tiles=(0, 128), m_offsets=(0, 1))
+    best, table = autotune(0, to_dev(r), to_dev(omega), to_dev(c), 1e-10, grid=grid, reps=2)
+    assert len(table) == len(grid) and table[0][0] <= table[-1][0]
+    g, _, _ = run_forward(0, r, omega, c, 1e-10, **best)
+    rows = np.arange(0, omega.size, 97)
+    ref = oracle.direct_rows(0, r, omega, c, rows)
+    assert np.max(np.abs(g[rows] - ref)) <= tol(1e-10, c)
+
+
+@pytest.mark.parametrize("opts", [{"min_size": 64}, {"min_size": 5000}, {"m_terms": 2},
+                                  {"m_terms": 7}, {"spread_tile": 64}, {"n_split_cand": 3}])
+def test_option_variants_keep_accuracy(opts):
+    r, omega, c = uniform_problem(1500, 1400, omega_max=2500.0, seed=91)
+    _check(1, r, omega, c, 1e-10, **opts)
