@@ -63,10 +63,14 @@ extern "C" {
 #define NUHT_BLOCK_ASY    1
 #define NUHT_BLOCK_DIRECT 2
 
+/* Upper limit of nuht_opts.min_size: a direct block's row (or column) sums
+   and its entry list stay in one CTA's shared memory. */
+#define NUHT_MAX_MIN_SIZE 16384
+
 typedef struct {
     int precision;     /* NUHT_PREC_FP64 (default) or NUHT_PREC_MIXED */
     int min_size;      /* largest area (rows*cols) of a mixed block summed directly;
-                          default 1024 (Sec. 4.1) */
+                          default 1024, at most NUHT_MAX_MIN_SIZE (Sec. 4.1) */
     int n_split_cand;  /* candidate rows tried by SplitIndices (Sec. 4.1); default 16 */
     int m_terms;       /* asymptotic terms M; 0 = the heuristic of Sec. 3.3 */
     int class_mask;    /* bit c set = apply blocks of class c (testing aid); default 7 */

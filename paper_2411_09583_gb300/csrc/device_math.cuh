@@ -111,4 +111,59 @@ __device__ __forceinline__ double jn_hankel(const ProbParams& P, double w, doubl
     return sqrt(0.6366197723675814 * y) * (p * cchi - q * schi);
 }
 
+// ---------------------------------------------------------- FP32 variants
+// (for tolerances eps >= 1e-6, where FP32 evaluation error stays far below eps)
+
+// J_n(x), 1 <= x, Miller's recurrence in FP32 (rescaled by 2^-60 past 2^60).
+__device__ inline float jn_miller_f32(int n, float x)
+{
+    const int ns = miller_start(n, (double)x);
+    const float inv2x = 2.0f / x;
+    float jp1 = 0.f, jc = 1.f, S = 2.f, res = 0.f;
+    for (int i = ns; i >= 2; i -= 2) {
+        const float jm = fmaf((float)i * inv2x, jc, -jp1);
+        const float jmm = fmaf((float)(i - 1) * inv2x, jm, -jc);
+        if (i - 1 == n) res = jm;
+        if (i - 2 == n) res = jmm;
+        S = fmaf(2.f, jmm, S);
+        jp1 = jm;
+        jc = jmm;
+        if (fabsf(jc) > 1.152921504606847e18f) {
+            const float sc = 8.673617379884035e-19f;
+            jc *= sc; jp1 *= sc; S *= sc; res *= sc;
+        }
+    }
+    return res / (S - jc);
+}
+
+// Hankel's expansion in FP32 after an FP64 reduction of the exact product w*r modulo pi/2.
+__device__ inline float jn_hankel_f32(const ProbParams& P, double w, double r)
+{
+    const double p = w * r;
+    const double e = fma(w, r, -p);
+    const double k = rint(p * 0.6366197723675814);
+    double t = fma(-k, 1.5707963267948966, p);
+    t = fma(-k, 6.123233995736766e-17, t) + e;
+    float s0, c0;
+    sincosf((float)t, &s0, &c0);
+    float sx, cx;
+    switch ((int)((long long)k & 3)) {
+        case 0: sx = s0; cx = c0; break;
+        case 1: sx = c0; cx = -s0; break;
+        case 2: sx = -s0; cx = -c0; break;
+        default: sx = -c0; cx = s0; break;
+    }
+    const float y = (float)(1.0 / p), y2 = y * y;
+    float pp = 0.f, qq = 0.f;
+    for (int l = P.M - 1; l >= 0; --l) {
+        const float sg = (l & 1) ? -1.f : 1.f;
+        pp = fmaf(pp, y2, sg * (float)P.a[2 * l]);
+        qq = fmaf(qq, y2, sg * (float)P.a[2 * l + 1]);
+    }
+    qq *= y;
+    const float cph = (float)P.cphi, sph = (float)P.sphi;
+    const float cchi = cx * cph - sx * sph, schi = sx * cph + cx * sph;
+    return sqrtf(0.6366197723675814f * y) * (pp * cchi - qq * schi);
+}
+
 }  // namespace nuht

@@ -206,6 +206,50 @@ __device__ void smem_fft(double2* X, int logN, const double2* __restrict__ tw, i
     }
 }
 
+// nlines independent FFTs of N = 2^logN points stored one after the other
+// (each bit-reversed), sharing every butterfly stage.
+__device__ void smem_fft_lines(double2* X, int logN, int nlines, const double2* __restrict__ tw, int tw_log2)
+{
+    const int N = 1 << logN, half = N >> 1;
+    for (int st = 0; st < logN; ++st) {
+        const int len = 1 << st;
+        const int tw_shift = tw_log2 - (st + 1);
+        for (int b = threadIdx.x; b < nlines * half; b += blockDim.x) {
+            const int line = b >> (logN - 1);
+            const int bb = b & (half - 1);
+            const int pos = bb & (len - 1);
+            const int i0 = line * N + ((bb >> st) << (st + 1)) + pos;
+            const int i1 = i0 + len;
+            const double2 wv = tw[pos << tw_shift];
+            const double2 u = X[i0], v = X[i1];
+            const double2 vw = make_double2(v.x * wv.x - v.y * wv.y, v.x * wv.y + v.y * wv.x);
+            X[i0] = make_double2(u.x + vw.x, u.y + vw.y);
+            X[i1] = make_double2(u.x - vw.x, u.y - vw.y);
+        }
+        __syncthreads();
+    }
+}
+
+// Split of a two-pass FFT of 2^LN points into lines: N2 = 2^ceil(LN/2)
+// points per pass-A line, N1 = 2^floor(LN/2) per pass-B line; each CTA takes
+// as many lines as fit kFftLineBatch points.
+struct FourStep {
+    int logN1, logN2, N1, N2, lpcA, lpcB, groupsA, groupsB;
+};
+__host__ __device__ __forceinline__ FourStep four_step(int LN)
+{
+    FourStep f;
+    f.logN2 = (LN + 1) >> 1;
+    f.logN1 = LN - f.logN2;
+    f.N1 = 1 << f.logN1;
+    f.N2 = 1 << f.logN2;
+    f.lpcA = kFftLineBatch >> f.logN2; if (f.lpcA < 1) f.lpcA = 1;
+    f.lpcB = kFftLineBatch >> f.logN1; if (f.lpcB < 1) f.lpcB = 1;
+    f.groupsA = (f.N1 + f.lpcA - 1) / f.lpcA;
+    f.groupsB = (f.N2 + f.lpcB - 1) / f.lpcB;
+    return f;
+}
+
 // Spread-grid value at FFT index t (mode l = t or t - nf2), corrected by
 // 1/psi^(alpha2 l); zero outside |l| <= N1.
 __device__ __forceinline__ double2 corrected_mode(const AsyBlock& B, const Tables& tab,
@@ -339,10 +383,11 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
     }
 }
 
-// Four-step FFT for nf2 = N1 * N2 > kFftSmemMax, N2 = kFftSmemMax.
-// Pass A (line = n1): FFT over n2 of x[n1 + N1 n2], times e^{2 pi i n1 k2 / N},
-// stored at tmp[n1 + N1 k2].  Pass B (line = k2): FFT over n1 of
-// tmp[n1 + N1 k2], stored at X[k2 + N2 k1].
+// Two-pass (four-step) FFT for nf2 = N1 * N2 > kFftSingleMax.
+// Pass A: for each n1, FFT over n2 of x[n1 + N1 n2], times e^{2 pi i n1 k2 / N},
+// stored at tmp[n1 + N1 k2].  Pass B: for each k2, FFT over n1 of
+// tmp[n1 + N1 k2], which is X[k2 + N2 k1].  Work item ordinal = q * groups + g,
+// g a group of lines handled by one CTA.
 template <bool ADJ>
 __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
@@ -353,22 +398,27 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
     const int N = B.nf2;
-    const int logN2 = 12, N2 = 1 << logN2;
-    const int N1 = N >> logN2;
-    const int iq = (int)(it.start / N1);
-    const int n1 = (int)(it.start - (int64_t)iq * N1);
-    for (int n2 = threadIdx.x; n2 < N2; n2 += blockDim.x)
-        X[__brev(n2) >> (32 - logN2)] = fft_in<ADJ>(B, tab, src, Q, iq, n1 + N1 * n2);
+    const FourStep f = four_step(B.log2nf2);
+    const int iq = (int)(it.start / f.groupsA);
+    const int g = (int)(it.start - (int64_t)iq * f.groupsA);
+    const int l0 = g * f.lpcA;
+    const int nl = (f.N1 - l0) < f.lpcA ? (f.N1 - l0) : f.lpcA;
+    for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
+        const int li = idx >> f.logN2, n2 = idx & (f.N2 - 1);
+        X[li * f.N2 + (__brev(n2) >> (32 - f.logN2))] = fft_in<ADJ>(B, tab, src, Q, iq, (l0 + li) + f.N1 * n2);
+    }
     __syncthreads();
-    smem_fft(X, logN2, tab.tw, tab.tw_log2);
+    smem_fft_lines(X, f.logN2, nl, tab.tw, tab.tw_log2);
     double2* tq = tmp + B.q_off;
-    for (int k2 = threadIdx.x; k2 < N2; k2 += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
+        const int li = idx >> f.logN2, k2 = idx & (f.N2 - 1);
+        const int n1 = l0 + li;
         double s, c;
         // e^{2 pi i n1 k2 / N}: the argument (2 n1 k2 mod 2N) / N is exact in FP64
         const long long num = (2LL * n1 * k2) % (2LL * N);
         sincospi((double)num / (double)N, &s, &c);
-        const double2 v = X[k2];
-        tq[(int64_t)(n1 + N1 * k2) * Q + iq] = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+        const double2 v = X[idx];
+        tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
     }
 }
 
@@ -381,16 +431,23 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
-    const int logN2 = 12, N2 = 1 << logN2;
-    const int logN1 = B.log2nf2 - logN2, N1 = 1 << logN1;
-    const int iq = (int)(it.start >> logN2);
-    const int k2 = (int)(it.start & (N2 - 1));
+    const FourStep f = four_step(B.log2nf2);
+    const int iq = (int)(it.start / f.groupsB);
+    const int g = (int)(it.start - (int64_t)iq * f.groupsB);
+    const int k20 = g * f.lpcB;
+    const int nl = (f.N2 - k20) < f.lpcB ? (f.N2 - k20) : f.lpcB;
     const double2* tq = tmp + B.q_off;
-    for (int n1 = threadIdx.x; n1 < N1; n1 += blockDim.x)
-        X[logN1 > 0 ? (__brev(n1) >> (32 - logN1)) : 0] = tq[(int64_t)(n1 + N1 * k2) * Q + iq];
+    for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
+        const int li = idx >> f.logN1, n1 = idx & (f.N1 - 1);
+        X[li * f.N1 + (f.logN1 > 0 ? (__brev(n1) >> (32 - f.logN1)) : 0)] =
+            tq[(int64_t)(n1 + f.N1 * (k20 + li)) * Q + iq];
+    }
     __syncthreads();
-    smem_fft(X, logN1, tab.tw, tab.tw_log2);
-    for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, iq, k2 + N2 * k1, X[k1]);
+    smem_fft_lines(X, f.logN1, nl, tab.tw, tab.tw_log2);
+    for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
+        const int li = idx >> f.logN1, k1 = idx & (f.N1 - 1);
+        fft_out<ADJ>(B, tab, dst, Q, iq, (k20 + li) + f.N2 * k1, X[idx]);
+    }
 }
 
 // ------------------------------------------------------------ interpolate
@@ -1001,7 +1058,7 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
                                  cudaStream_t s, bool adj)
 {
     if (nitems_a <= 0) return cudaSuccess;
-    size_t smem = sizeof(double2) * (size_t)kFftSmemMax;
+    size_t smem = sizeof(double2) * (size_t)kFftLineBatch;
     auto ka = adj ? k_asy_fft_pass_a<true> : k_asy_fft_pass_a<false>;
     auto kb = adj ? k_asy_fft_pass_b<true> : k_asy_fft_pass_b<false>;
     cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

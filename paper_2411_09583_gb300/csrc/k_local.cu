@@ -222,27 +222,54 @@ __device__ __forceinline__ double jn_miller_df(int n, double x)
     return df_to(res) / df_to(S);
 }
 
-// One CTA per direct block (area <= min_size): entries in parallel, row sums
-// in shared memory, then one atomic add per row.
+// J_nu at the exact product w*r: asymptotic side (Hankel, FP64 phase
+// reduction) or local side (series; Miller in double-float, or FP32 when lowp).
+__device__ __forceinline__ double direct_entry(const ProbParams& P, double w, double r, bool asy, bool lowp)
+{
+    if (asy) return lowp ? (double)jn_hankel_f32(P, w, r) : jn_hankel(P, w, r);
+    const double x = w * r;
+    if (x < 1.0) return jn_series(P.nu, x);
+    return lowp ? (double)jn_miller_f32(P.nu, (float)x) : jn_miller_df(P.nu, x);
+}
+
+// Splits the entries of a direct block into a local list (omega r <= z, from
+// the front) and an asymptotic list (from the back) in shared memory, so that
+// warps run one branch each.  Returns the number of local entries.
+__device__ __forceinline__ int direct_partition(const ProbParams& P, const DirectBlock& B, int cols, int area,
+                                                const double* __restrict__ r_s, const double* __restrict__ w_s,
+                                                int* list, int* cnt)
+{
+    if (threadIdx.x == 0) { cnt[0] = 0; cnt[1] = 0; }
+    __syncthreads();
+    for (int e = threadIdx.x; e < area; e += blockDim.x) {
+        const int rr = e / cols, cc = e - rr * cols;
+        if (w_s[B.k0 + rr] * r_s[B.j0 + cc] > P.z) list[area - 1 - atomicAdd(&cnt[1], 1)] = e;
+        else list[atomicAdd(&cnt[0], 1)] = e;
+    }
+    __syncthreads();
+    return cnt[0];
+}
+
+// One CTA per direct block (area <= min_size): entries in parallel after the
+// branch split, row sums in shared memory, then one atomic add per row.
+// lowp (eps >= 1e-6): the local and Hankel branches evaluate in FP32.
 __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
                          const double* __restrict__ r_s, const double* __restrict__ w_s,
-                         const double* __restrict__ c_s, double* __restrict__ g_s)
+                         const double* __restrict__ c_s, double* __restrict__ g_s, int lowp)
 {
     extern __shared__ double rowacc[];
+    __shared__ int cnt[2];
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
     const int area = rows * cols;
+    int* list = (int*)(rowacc + rows);
     for (int i = threadIdx.x; i < rows; i += blockDim.x) rowacc[i] = 0.0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < area; e += blockDim.x) {
+    const int nloc = direct_partition(P, B, cols, area, r_s, w_s, list, cnt);
+    for (int t = threadIdx.x; t < area; t += blockDim.x) {
+        const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
-        const double w = w_s[B.k0 + rr], r = r_s[B.j0 + cc];
-        const double x = w * r;
-        double v;
-        if (x > P.z) v = jn_hankel(P, w, r);
-        else if (x < 1.0) v = jn_series(P.nu, x);
-        else v = jn_miller_df(P.nu, x);
+        const double v = direct_entry(P, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
         atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
     }
     __syncthreads();
@@ -345,26 +372,25 @@ k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restr
     }
 }
 
-// Transposed direct block: column sums, one atomic add per column.
+// Transposed direct block: column sums (entries split by branch as in
+// k_direct), one atomic add per column.
 __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
                              const double* __restrict__ r_s, const double* __restrict__ w_s,
-                             const double* __restrict__ g_s, double* __restrict__ c_s)
+                             const double* __restrict__ g_s, double* __restrict__ c_s, int lowp)
 {
     extern __shared__ double colacc[];
+    __shared__ int cnt[2];
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
     const int area = rows * cols;
+    int* list = (int*)(colacc + cols);
     for (int i = threadIdx.x; i < cols; i += blockDim.x) colacc[i] = 0.0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < area; e += blockDim.x) {
+    const int nloc = direct_partition(P, B, cols, area, r_s, w_s, list, cnt);
+    for (int t = threadIdx.x; t < area; t += blockDim.x) {
+        const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
-        const double w = w_s[B.k0 + rr], r = r_s[B.j0 + cc];
-        const double x = w * r;
-        double v;
-        if (x > P.z) v = jn_hankel(P, w, r);
-        else if (x < 1.0) v = jn_series(P.nu, x);
-        else v = jn_miller_df(P.nu, x);
+        const double v = direct_entry(P, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
         atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
     }
     __syncthreads();
@@ -409,14 +435,14 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
 }
 
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
-                              const double* r_s, const double* w_s, const double* g_s, double* c_s,
-                              cudaStream_t s)
+                              int max_area, int lowp, const double* r_s, const double* w_s, const double* g_s,
+                              double* c_s, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)(max_cols > 0 ? max_cols : 1);
+    size_t smem = sizeof(double) * (size_t)(max_cols > 0 ? max_cols : 1) + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, g_s, c_s);
+    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, g_s, c_s, lowp);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -460,14 +486,14 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
 }
 
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
-                               const double* r_s, const double* w_s, const double* c_s, double* g_s,
-                               cudaStream_t s)
+                          int max_area, int lowp, const double* r_s, const double* w_s, const double* c_s,
+                          double* g_s, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)(max_rows > 0 ? max_rows : 1);
+    size_t smem = sizeof(double) * (size_t)(max_rows > 0 ? max_rows : 1) + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, c_s, g_s);
+    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, c_s, g_s, lowp);
     count_launches(1);
     return cudaGetLastError();
 }

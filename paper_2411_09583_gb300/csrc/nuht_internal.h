@@ -17,8 +17,10 @@ constexpr int kMaxQ = 2 * kMaxM;    // weight powers q = 0..2M-1
 constexpr int kMaxW = 16;           // ES kernel width
 constexpr int kMaxDeg = 20;         // degree of the kernel piece polynomials
 constexpr int kMaxNtop = 256;       // largest Bessel index kept by the local evaluation
-constexpr int kFftSmemMax = 4096;   // largest FFT done by one CTA in shared memory
-constexpr int kFftMaxLog2 = 24;     // largest FFT (two passes of <= 4096)
+constexpr int kFftSmemMax = 4096;   // points of all Q grids of a block FFT'd by one CTA
+constexpr int kFftSingleMax = 8192; // largest single-grid FFT done by one CTA (128 KiB)
+constexpr int kFftLineBatch = 4096; // points per CTA in the passes of a two-pass FFT
+constexpr int kFftMaxLog2 = 24;     // largest FFT (two passes of <= 4096-point lines)
 
 // Per-problem constants.
 struct ProbParams {
@@ -128,8 +130,8 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
                               int ntiles, int ntop_max, int threads, const double* w_s,
                               const double* mom, double* g_s, cudaStream_t s);
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
-                          const double* r_s, const double* w_s, const double* c_s, double* g_s,
-                          cudaStream_t s);
+                          int max_area, int lowp, const double* r_s, const double* w_s, const double* c_s,
+                          double* g_s, cudaStream_t s);
 int local_adj_threads(int ntop_max, int lmax);
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                      int ntiles, int ntop_max, int lmax, int threads, const double* w_s,
@@ -138,8 +140,8 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
                                   int ntiles, int lmax, const double* r_s, const double* mom, double* c_s,
                                   cudaStream_t s);
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
-                              const double* r_s, const double* w_s, const double* g_s, double* c_s,
-                              cudaStream_t s);
+                              int max_area, int lowp, const double* r_s, const double* w_s, const double* g_s,
+                              double* c_s, cudaStream_t s);
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, int nt, Tables tab, const double* r_s,
                               const double* c_s, double2* grid_b, cudaStream_t s);

@@ -220,8 +220,8 @@ const HostTables& kernel_tables(int w)
         const float hi = (float)T.ph[i];
         T.ph2[i] = make_float2(hi, (float)(T.ph[i] - (double)hi));
     }
-    // twiddles e^{2 pi i k / 4096}, k < 2048
-    T.tw_log2 = 12;
+    // twiddles e^{2 pi i k / 8192}, k < 4096 (single-CTA FFTs up to 8192 points)
+    T.tw_log2 = 13;
     T.tw.assign((size_t)1 << (T.tw_log2 - 1), make_double2(0.0, 0.0));
     for (int k = 0; k < (1 << (T.tw_log2 - 1)); ++k) {
         const double a = 2.0 * M_PI * k / (double)(1 << T.tw_log2);

@@ -97,7 +97,7 @@ struct nuht_plan_s {
     int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fblock = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
     int n_dir = 0;
     int64_t mom_len = 0, gb_len = 0, gq_len = 0;
-    int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, ntop_max = 0, eval_threads = 0;
+    int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, max_dir_area = 0, ntop_max = 0, eval_threads = 0;
     int spread_threads = 256;
     bool has_large_fft = false;
     Tables tab{};
@@ -465,13 +465,18 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         sinterp.add((int32_t)b, h.k0, h.k1, kInterpTile);
         if ((int64_t)ab.nf2 * Q <= kFftSmemMax) {
             sfk.add((int32_t)b, 0, 0, 1);                // all Q grids in one CTA
-        } else if (ab.nf2 <= kFftSmemMax) {
+        } else if (ab.nf2 <= kFftSingleMax) {
             if (ab.nf2 > P->max_nf2_small) P->max_nf2_small = ab.nf2;
             sfs.add((int32_t)b, 0, Q - 1, 1);
         } else {
+            // two passes; each CTA takes a group of lines (see four_step in the kernels)
             P->has_large_fft = true;
-            sfa.add((int32_t)b, 0, (int64_t)Q * (ab.nf2 / kFftSmemMax) - 1, 1);
-            sfb.add((int32_t)b, 0, (int64_t)Q * kFftSmemMax - 1, 1);
+            const int logN2 = (lg + 1) >> 1, logN1 = lg - logN2;
+            const int lpcA = (kFftLineBatch >> logN2) > 0 ? (kFftLineBatch >> logN2) : 1;
+            const int lpcB = (kFftLineBatch >> logN1) > 0 ? (kFftLineBatch >> logN1) : 1;
+            const int64_t groupsA = ((1 << logN1) + lpcA - 1) / lpcA, groupsB = ((1 << logN2) + lpcB - 1) / lpcB;
+            sfa.add((int32_t)b, 0, (int64_t)Q * groupsA - 1, 1);
+            sfb.add((int32_t)b, 0, (int64_t)Q * groupsB - 1, 1);
         }
         P->asy_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
         P->fft_points += ab.nf2;
@@ -485,6 +490,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         const int rows = (int)(h.k1 - h.k0 + 1), cols = (int)(h.j1 - h.j0 + 1);
         if (rows > P->max_dir_rows) P->max_dir_rows = rows;
         if (cols > P->max_dir_cols) P->max_dir_cols = cols;
+        if (rows * cols > P->max_dir_area) P->max_dir_area = rows * cols;
         P->direct_entries += (h.k1 - h.k0 + 1) * (h.j1 - h.j0 + 1);
     }
     P->n_loc = (int)vloc.size(); P->n_tmom = smom.total(); P->n_teval = seval.total();
@@ -641,7 +647,7 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
 {
     nuht_default_opts(&o);
     if (opt) o = *opt;
-    if (o.min_size < 1 || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
+    if (o.min_size < 1 || o.min_size > NUHT_MAX_MIN_SIZE || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
     for (int i = 0; i < 5; ++i)
@@ -753,8 +759,8 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     }
     if ((mask & 4) && P->n_dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
-        NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->d_r, P->d_w, P->d_cs,
-                              P->d_gs, ls));
+        NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area,
+                              P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_cs, P->d_gs, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if ((mask & 2) && P->n_asy) {
@@ -834,8 +840,8 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     }
     if ((mask & 4) && P->n_dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, s));
-        NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->d_r, P->d_w, P->d_gs,
-                                  P->d_cs, s));
+        NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->max_dir_area,
+                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_gs, P->d_cs, s));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, s));
     }
     if ((mask & 2) && P->n_asy) {

@@ -63,3 +63,12 @@ def test_invalid_arguments(lib):
     o = N.NuhtOpts()
     lib.nuht_default_opts(ctypes.byref(o))
     assert (o.precision, o.min_size, o.n_split_cand, o.m_terms, o.class_mask) == (0, 1024, 16, 0, 7)
+    # option checks run before any device work
+    one = (ctypes.c_double * 1)(0.5)
+    for field, bad in (("min_size", 0), ("min_size", 16385), ("n_split_cand", 1), ("spread_tile", 96 + 1),
+                       ("precision", 2), ("m_terms", 21)):
+        b = N.NuhtOpts()
+        lib.nuht_default_opts(ctypes.byref(b))
+        setattr(b, field, bad)
+        assert lib.nuht_plan(ctypes.byref(h), 0, one, 1, one, 1, 1e-8, ctypes.byref(b), None) == \
+            N.NUHT_ERR_INVALID_ARG, field
