@@ -70,20 +70,256 @@ __device__ __forceinline__ df psihat_df(const Tables& T, double xi)
 }
 
 // ------------------------------------------------------------------ spread
-// One CTA per tile of consecutive (sorted) points of one block.  Phase 1:
-// each thread prepares one point (grid cell l0, w kernel taps, the 2M
-// weighted, pre-phased values).  Phase 2: each (cell, q) output of the tile's
-// window is owned by one thread, which sums over the points whose taps cover
-// that cell and adds the sum to the block's global grid.
-__global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                             const Tile* __restrict__ tiles, Tables tab,
-                             const double* __restrict__ r_s, const double* __restrict__ c_s,
-                             double2* __restrict__ grid_b)
+// A point r_j of a block covers the w grid cells l0 + i, i < w, with
+// l0 = ceil((r_j - r_c)/h - w/2), and tap i of the ES kernel is the
+// polynomial piece psi_i(v), v = 2 (l0 - (r_j - r_c)/h + w/2) - 1 in [-1, 1].
+__device__ __forceinline__ int spread_cell(const AsyBlock& B, const Tables& tab, double rj, double* v)
 {
-    extern __shared__ float4 smem4[];
-    const Tile t = tiles[blockIdx.x];
-    const AsyBlock B = blks[t.blk];
-    const int Q = probs[B.prob].Q;
+    // explicit roundings: every call site computes the same cell
+    const double a = __dadd_rn(__dmul_rn(__dadd_rn(rj, -B.rc), B.inv_h), -tab.half_w);
+    const double lf = ceil(a);
+    double z0 = lf - a;
+    z0 = fmin(fmax(z0, 0.0), 1.0);
+    *v = 2.0 * z0 - 1.0;
+    return (int)lf;
+}
+
+// c_j (r_j/rho)^(-1/2) e^{i w_c (r_j - r_c)} as double-float (re, im), and the
+// ratio (r_j/rho)^(-1) that steps the weight from q to q + 1.
+__device__ __forceinline__ void spread_weight(const AsyBlock& B, double rj, double cj, df* wr, df* wi, df* rat)
+{
+    df sn, cs;
+    df_sincos_prod(B.wc, rj - B.rc, &sn, &cs);
+    *rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));
+    const df w0 = df_mul(df_from(cj), df_sqrt(*rat));
+    *wr = df_mul(w0, cs);
+    *wi = df_mul(w0, sn);
+}
+
+constexpr int kSpreadSub = 8;       // point sub-ranges per moment, combined by shuffles
+constexpr int kMomMinPerBin = 16;   // tiles with at least this many points per bin use moments
+constexpr int kMaxTileBins = 32;
+
+// Row strides of the moment path's shared arrays: = 2 mod 4 elements, so
+// that the eight point rows a quarter-warp reads (16-byte loads of float2
+// pairs, or 8-byte loads of float pairs) fall in distinct banks.
+__host__ __device__ __forceinline__ int mom_stride(int n) { return ((n + 1) & ~1) + (((n + 1) & 2) ? 0 : 2); }
+
+struct MomLayout {
+    int ndf, nf;     // degree pairs accumulated in double-float / in FP32
+    int sud, suf;    // row strides of the basis: double-float part (float2), FP32 part (float)
+    int sx;          // row stride of the weighted values (float2)
+    int dpad;        // rows of the moment matrix (2 ndf + 2 nf)
+};
+
+__host__ __device__ __forceinline__ MomLayout mom_layout(int nb, int dcs, int Q2)
+{
+    MomLayout L;
+    L.ndf = (dcs + 1) >> 1;
+    L.nf = (nb - dcs + 1) >> 1;
+    L.sud = mom_stride(2 * L.ndf);
+    L.suf = L.nf > 0 ? mom_stride(2 * L.nf) : 0;
+    L.sx = mom_stride(Q2);
+    L.dpad = 2 * (L.ndf + L.nf);
+    return L;
+}
+
+// Degree of row e of the moment matrix (pairs of double-float degrees
+// 0..2 ndf - 1, then pairs of FP32 degrees from dcs); -1 for padding.
+__device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
+{
+    const int d = e < 2 * ndf ? e : dcs + (e - 2 * ndf);
+    return (e < 2 * ndf ? d < dcs : d < nb) ? d : -1;
+}
+
+// Dense tile: all points of one bin (same l0) share the cells, so
+//   grid[l0 + i][q'] += sum_d A[i][d] M[d][q'],  M[d][q'] = sum_{p in bin} T_d(v_p) x_q'(p),
+// where psi_i(v) = sum_d A[i][d] T_d(v) is tap i in the Chebyshev basis and
+// x_q'(p) runs over (re, im) of the 2M weighted values.  The moments are a
+// small dense contraction over the bin's points (register-blocked, 2 degrees
+// x 4 values per thread, the point range split over 8 lanes); degrees >=
+// tab.dcs, whose coefficients are tiny, accumulate in plain FP32, the rest
+// in double-float.
+__device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
+                               const double* __restrict__ r_s, const double* __restrict__ c_s,
+                               double2* __restrict__ gb, float2* sm)
+{
+    const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
+    const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
+    const int Q2 = 2 * Q;
+    const MomLayout L = mom_layout(nb, dcs, Q2);
+    const int nq = Q2 >> 2;
+    float2* Ud = sm;                                  // [nt][sud]  T_d(v_p), d < dcs
+    float2* X = Ud + nt * L.sud;                      // [nt][sx]   x_q'(p)
+    float2* Mb = X + nt * L.sx;                       // [dpad][Q2] moments of the current bin
+    float2* Ach = Mb + L.dpad * Q2;                   // [w][dpad]  Chebyshev coefficients, row order of Mb
+    float* Uf = (float*)(Ach + w * L.dpad);           // [nt][suf]  T_d(v_p), d >= dcs
+    int* l0s = (int*)(Uf + nt * L.suf);               // [nt]
+    __shared__ int bstart[kMaxTileBins + 3];
+    for (int i = tid; i < w * L.dpad; i += nt) {
+        const int r = i / L.dpad, e = i - r * L.dpad;
+        const int d = mom_degree(e, L.ndf, dcs, nb);
+        Ach[i] = d >= 0 ? tab.ch2[r * (tab.deg + 1) + d] : make_float2(0.f, 0.f);
+    }
+    if (tid < cnt) {
+        const int64_t j = t.start + tid;
+        const double rj = r_s[j];
+        double v;
+        l0s[tid] = spread_cell(B, tab, rj, &v);
+        // Chebyshev basis by T_{d+1} = 2 v T_d - T_{d-1}
+        float2* ud = Ud + tid * L.sud;
+        float* uf = Uf + tid * L.suf;
+        const float vh = (float)v, vl = (float)(v - (double)vh);
+        df tm{1.f, 0.f}, tc{vh, vl};
+        ud[0] = make_float2(1.f, 0.f);
+        ud[1] = make_float2(vh, vl);                 // dcs >= 2
+        const df v2{2.f * vh, 2.f * vl};
+        int d = 2;
+        for (; d < dcs; ++d) {
+            const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+            ud[d] = make_float2(tn.h, tn.l);
+            tm = tc;
+            tc = tn;
+        }
+        for (int e = dcs; e < L.sud; ++e) ud[e] = make_float2(0.f, 0.f);
+        float fm = tm.h, fc = tc.h;
+        for (; d < nb; ++d) {
+            const float fn = fmaf(2.f * vh, fc, -fm);
+            uf[d - dcs] = fn;
+            fm = fc;
+            fc = fn;
+        }
+        for (int e = nb - dcs; e < L.suf; ++e) uf[e] = 0.f;
+        df wr, wi, rat;
+        spread_weight(B, rj, c_s[j], &wr, &wi, &rat);
+        float2* x = X + tid * L.sx;
+        for (int q = 0; q < Q; ++q) {
+            x[2 * q] = make_float2(wr.h, wr.l);
+            x[2 * q + 1] = make_float2(wi.h, wi.l);
+            wr = df_mul(wr, rat);
+            wi = df_mul(wi, rat);
+        }
+    }
+    __syncthreads();
+    const int lfirst = l0s[0];
+    const int nbins = l0s[cnt - 1] - lfirst + 1;
+    // first point of each bin (the tile's points are sorted, so bins are runs)
+    for (int b = tid; b <= nbins; b += nt) {
+        const int key = lfirst + b;
+        int lo = 0, hi = cnt;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
+        bstart[b] = lo;
+    }
+    __syncthreads();
+    const int nf1 = 2 * B.N1 + 1;
+    const int npairs = L.ndf + L.nf;
+    const int nitems = npairs * nq * kSpreadSub;
+    const int nitems_pad = (nitems + 31) & ~31;
+    for (int b = 0; b < nbins; ++b) {
+        const int p0 = bstart[b], p1 = bstart[b + 1];
+        if (p0 == p1) continue;
+        for (int it = tid; it < nitems_pad; it += nt) {
+            const bool live = it < nitems;
+            const int sub = it & (kSpreadSub - 1);
+            const int o = live ? it / kSpreadSub : 0;
+            const int dp = o / nq, qq = o - dp * nq;
+            const bool lowp = dp >= L.ndf;
+            acc2 A[2][4];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) A[e][f] = acc2{0.f, 0.f};
+            if (live && !lowp) {
+                const float2* up = Ud + 2 * dp;
+                for (int p = p0 + sub; p < p1; p += kSpreadSub) {
+                    const float4 uu = *(const float4*)(up + p * L.sud);
+                    const float4 xa = *(const float4*)(X + p * L.sx + 4 * qq);
+                    const float4 xb = *(const float4*)(X + p * L.sx + 4 * qq + 2);
+                    const df xs[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        acc_fma(A[0][f], df{uu.x, uu.y}, xs[f]);
+                        acc_fma(A[1][f], df{uu.z, uu.w}, xs[f]);
+                    }
+                }
+            } else if (live) {
+                const float* up = Uf + 2 * (dp - L.ndf);
+                for (int p = p0 + sub; p < p1; p += kSpreadSub) {
+                    const float2 uu = *(const float2*)(up + p * L.suf);
+                    const float4 xa = *(const float4*)(X + p * L.sx + 4 * qq);
+                    const float4 xb = *(const float4*)(X + p * L.sx + 4 * qq + 2);
+                    const float xs[4] = {xa.x, xa.z, xb.x, xb.z};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        A[0][f].s = fmaf(uu.x, xs[f], A[0][f].s);
+                        A[1][f].s = fmaf(uu.y, xs[f], A[1][f].s);
+                    }
+                }
+            }
+            // combine the kSpreadSub partial sums (adjacent lanes)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    acc2 a = A[e][f];
+#pragma unroll
+                    for (int off = kSpreadSub >> 1; off > 0; off >>= 1) {
+                        const float os = __shfl_xor_sync(0xffffffffu, a.s, off);
+                        const float oc = __shfl_xor_sync(0xffffffffu, a.c, off);
+                        float s2, q2;
+                        two_sum(a.s, os, s2, q2);
+                        a.s = s2;
+                        a.c += oc + q2;
+                    }
+                    if (live && sub == 0) {
+                        const df m = fast_two_sum(a.s, a.c);
+                        Mb[(2 * dp + e) * Q2 + 4 * qq + f] = make_float2(m.h, m.l);
+                    }
+                }
+        }
+        __syncthreads();
+        // grid[l0 + i][q'] += sum_d A[i][d] M[d][q']
+        const int l0 = lfirst + b;
+        for (int o = tid; o < w * Q2; o += nt) {
+            const int i = o / Q2, qv = o - i * Q2;
+            const int idx = l0 + i + B.N1;
+            if (idx < 0 || idx >= nf1) continue;
+            acc2 s{0.f, 0.f};
+            const float2* ar = Ach + i * L.dpad;
+            for (int e = 0; e < 2 * L.ndf; ++e) {
+                const float2 a2 = ar[e], m2 = Mb[e * Q2 + qv];
+                acc_fma(s, df{a2.x, a2.y}, df{m2.x, m2.y});
+            }
+            float sf = 0.f;
+            for (int e = 2 * L.ndf; e < L.dpad; ++e) sf = fmaf(ar[e].x, Mb[e * Q2 + qv].x, sf);
+            const double val = acc_value(s) + (double)sf;
+            if (val != 0.0) {
+                double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
+                atomicAdd(dst, val);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Shared memory (bytes) of the moment path for nt points and Q = 2M.
+__host__ __device__ __forceinline__ size_t spread_moments_smem(int nt, int Q, int w, int nb, int dcs)
+{
+    const MomLayout L = mom_layout(nb, dcs, 2 * Q);
+    return sizeof(float2) * ((size_t)nt * L.sud + (size_t)nt * L.sx + (size_t)L.dpad * 2 * Q +
+                             (size_t)w * L.dpad) +
+           sizeof(float) * (size_t)nt * L.suf + sizeof(int) * (size_t)nt;
+}
+
+// Sparse tile (points spread over many cells): each thread prepares one point
+// (cell l0, w kernel taps, the 2M weighted, pre-phased values), then each
+// (cell, q) output of the tile's window is owned by one thread, which sums
+// over the points whose taps cover that cell and adds the sum to the block's
+// global grid.
+__device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
+                            const double* __restrict__ r_s, const double* __restrict__ c_s,
+                            double2* __restrict__ gb, float4* smem4)
+{
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
     float4* aval = smem4;                                   // [nt][Q]: (re.h, re.l, im.h, im.l)
@@ -96,23 +332,15 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     if (tid < cnt) {
         const int64_t j = t.start + tid;
         const double rj = r_s[j];
-        const double x = rj - B.rc;
-        const double a = x * B.inv_h - tab.half_w;
-        const double lf = ceil(a);
-        double z0 = lf - a;
-        z0 = fmin(fmax(z0, 0.0), 1.0);
-        const double v = 2.0 * z0 - 1.0;
+        double v;
+        l0s[tid] = spread_cell(B, tab, rj, &v);
         const float vh = (float)v, vl = (float)(v - (double)vh);
         for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
-        l0s[tid] = (int)lf;
-        df sn, cs;
-        df_sincos_prod(B.wc, x, &sn, &cs);
-        const df rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1)
-        const df w0 = df_mul(df_from(c_s[j]), df_sqrt(rat));            // c_j (r/rho)^(-1/2)
-        df wr = df_mul(w0, cs), wi = df_mul(w0, sn);
+        df wr, wi, rat;
+        spread_weight(B, rj, c_s[j], &wr, &wi, &rat);
         for (int q = 0; q < Q; ++q) {
             aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
             wr = df_mul(wr, rat);
@@ -123,15 +351,13 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     const int lfirst = l0s[0];
     const int span = l0s[cnt - 1] - lfirst + w;
     const int nf1 = 2 * B.N1 + 1;
-    double2* gb = grid_b + B.b_off;
-    // Outputs (cell, q), q fastest.  For a dense tile (span of cells close to
-    // the kernel width) every thread walks all the tile's points in lockstep,
-    // so each step reads one row of taps / values (broadcast or contiguous,
-    // no bank conflicts) and skips points whose taps miss its cell.  A sparse
-    // tile (points spread over many cells) instead binary-searches the few
-    // points that reach each cell.  Each output is split between kSub lanes
-    // (halves of the point range) combined by a shuffle, so that more threads
-    // than outputs can work.
+    // Outputs (cell, q), q fastest.  For a tile whose span of cells is close
+    // to the kernel width every thread walks all the tile's points in
+    // lockstep (one row of taps / values per step: broadcast or contiguous
+    // reads) and skips points whose taps miss its cell; otherwise it
+    // binary-searches the few points that reach its cell.  Each output is
+    // split between kSub lanes (halves of the point range) combined by a
+    // shuffle, so that more threads than outputs can work.
     constexpr int kSub = 2;
     const bool dense = span <= 2 * w;
     const int nout = span * Q;
@@ -180,6 +406,33 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
             atomicAdd(&gb[(int64_t)idx * Q + q].y, vi);
         }
     }
+}
+
+// One CTA per tile of consecutive (sorted) points of one block; the tile
+// takes the moment path when its points are dense in the grid's bins.
+__global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+                             const Tile* __restrict__ tiles, Tables tab,
+                             const double* __restrict__ r_s, const double* __restrict__ c_s,
+                             double2* __restrict__ grid_b)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ int use_mom;
+    const Tile t = tiles[blockIdx.x];
+    const AsyBlock B = blks[t.blk];
+    const int Q = probs[B.prob].Q;
+    if (t.count <= 0) return;
+    if (threadIdx.x == 0) {
+        double v;
+        const int lfirst = spread_cell(B, tab, r_s[t.start], &v);
+        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &v) - lfirst + 1;
+        use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
+    }
+    __syncthreads();
+    double2* gb = grid_b + B.b_off;
+    if (use_mom)
+        spread_moments(B, Q, t, tab, r_s, c_s, gb, (float2*)smem4);
+    else
+        spread_taps(B, Q, t, tab, r_s, c_s, gb, smem4);
 }
 
 // -------------------------------------------------------------------- FFT
@@ -451,22 +704,40 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
 }
 
 // ------------------------------------------------------------ interpolate
+constexpr int kInterpHBytes = 16384;    // shared bytes for the per-bin sums of a dense tile
+
+// Shared memory (bytes) of k_asy_interp for 2M = qmax.
+__host__ __device__ __forceinline__ size_t interp_smem(int qmax, int w, int deg)
+{
+    const int us = (deg + 1 > w ? deg + 1 : w) | 1;
+    return sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)((w * (deg + 1) + 1) & ~1) +
+           kInterpHBytes + sizeof(float2) * (size_t)kInterpTileThreads * us + sizeof(int) * kInterpTileThreads;
+}
+
 // One thread per frequency: interpolate the 2M FFT grids at theta = s h,
-// deconvolve, post-phase, and combine the Hankel terms into g.
-__global__ void __launch_bounds__(128, 4) k_asy_interp(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                             const Tile* __restrict__ tiles, Tables tab,
-                             const double* __restrict__ w_s, const float4* __restrict__ grid_q,
-                             double* __restrict__ g_s)
+// deconvolve, post-phase, and combine the Hankel terms into g.  A frequency
+// at FFT-grid position a + w/2 reads the cells t0 + i, i < w, t0 = ceil(a),
+// with taps psi_i(v).  Dense tiles (many frequencies per t0) form, once per
+// bin, H[d][q'] = sum_i A[i][d] G[t0 + i][q'] (the taps in the Chebyshev
+// basis, A[i][d]), and each frequency sums P_q' = sum_d T_d(v) H[d][q'];
+// sparse tiles evaluate the w taps of each frequency.  Each thread keeps its
+// basis (or taps) in a row of shared memory.
+__global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
+    const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
+    Tables tab, const double* __restrict__ w_s, const float4* __restrict__ grid_q, double* __restrict__ g_s)
 {
     extern __shared__ float4 win[];          // [kWinCells][Q] grid cells of this tile
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
-    const int w = tab.w, deg = tab.deg;
-    const int Q = P.Q;
-    float2* coef2 = (float2*)(win + kWinCells * Q);
-    int* t0s = (int*)(coef2 + w * (deg + 1));
-    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    const int w = tab.w, deg = tab.deg, nb = tab.nb, dci = tab.dci;
+    const int Q = P.Q, Q2 = 2 * Q;
+    const int us = (deg + 1 > w ? deg + 1 : w) | 1;
+    const int hs = nb * Q2 + 2;                                  // bin stride of H (float2)
+    float2* coef2 = (float2*)(win + kWinCells * Q);              // [w][deg + 1] taps, or [w][nb] Chebyshev
+    float2* H = coef2 + ((w * (deg + 1) + 1) & ~1);              // [bins][hs], 16-byte aligned
+    float2* U = H + kInterpHBytes / sizeof(float2);              // [threads][us]
+    int* t0s = (int*)(U + kInterpTileThreads * us);              // [threads]
     const bool valid = (int)threadIdx.x < t.count;
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
     const double wk = w_s[k];
@@ -482,30 +753,85 @@ __global__ void __launch_bounds__(128, 4) k_asy_interp(const ProbParams* __restr
     if (valid) t0s[threadIdx.x] = t0;
     __syncthreads();
     const int wstart = t0s[0];
-    const int wlen = t0s[t.count - 1] - wstart + w;
+    const int nbins = t0s[t.count - 1] - wstart + 1;
+    const int wlen = nbins - 1 + w;
     const int mask = B.nf2 - 1;
     const float4* gq = grid_q + B.q_off;
     const bool staged = wlen <= kWinCells;
+    const int maxbins = kInterpHBytes / (int)(sizeof(float2) * hs);
+    const bool mom = staged && nbins <= maxbins && t.count >= kMomMinPerBin * nbins;
     if (staged) {
         for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
             const int cc = idx / Q;
             win[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
         }
     }
+    if (mom) {
+        for (int i = threadIdx.x; i < w * nb; i += blockDim.x) {
+            const int r = i / nb, d = i - r * nb;
+            coef2[i] = tab.ch2[r * (deg + 1) + d];
+        }
+    } else {
+        for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    }
     __syncthreads();
+    if (mom) {
+        // H[b][d][q'] = sum_i A[i][d] G[wstart + b + i][q'], double-float for d < dci
+        for (int o = threadIdx.x; o < nbins * nb * Q2; o += blockDim.x) {
+            const int b = o / (nb * Q2), rem = o - b * nb * Q2;
+            const int d = rem / Q2, qv = rem - d * Q2;
+            const int q = qv >> 1, im = qv & 1;
+            float2 hv;
+            if (d < dci) {
+                acc2 acc{0.f, 0.f};
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = win[(b + i) * Q + q];
+                    const float2 c2 = coef2[i * nb + d];
+                    acc_fma(acc, df{c2.x, c2.y}, im ? df{gv.z, gv.w} : df{gv.x, gv.y});
+                }
+                const df h2 = fast_two_sum(acc.s, acc.c);
+                hv = make_float2(h2.h, h2.l);
+            } else {
+                float acc = 0.f;
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = win[(b + i) * Q + q];
+                    acc = fmaf(coef2[i * nb + d].x, im ? gv.z : gv.x, acc);
+                }
+                hv = make_float2(acc, 0.f);
+            }
+            H[b * hs + rem] = hv;
+        }
+        __syncthreads();
+    }
     if (!valid) return;
-    float th[kMaxW], tl[kMaxW];
-#pragma unroll
-    for (int i = 0; i < kMaxW; ++i) {
-        if (i < w) {
+    // this thread's Chebyshev basis T_d(v) (dense tile) or taps psi_i(v)
+    float2* u = U + threadIdx.x * us;
+    if (mom) {
+        u[0] = make_float2(1.f, 0.f);
+        u[1] = make_float2(vh, vl);
+        df tm{1.f, 0.f}, tc{vh, vl};
+        const df v2{2.f * vh, 2.f * vl};
+        int d = 2;
+        for (; d < dci; ++d) {
+            const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+            u[d] = make_float2(tn.h, tn.l);
+            tm = tc;
+            tc = tn;
+        }
+        float fm = tm.h, fc = tc.h;
+        for (; d < nb; ++d) {
+            const float fn = fmaf(2.f * vh, fc, -fm);
+            u[d] = make_float2(fn, 0.f);
+            fm = fc;
+            fc = fn;
+        }
+    } else {
+        for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
-            th[i] = tp.h;
-            tl[i] = tp.l;
-        } else {
-            th[i] = 0.f;
-            tl[i] = 0.f;
+            u[i] = make_float2(tp.h, tp.l);
         }
     }
+    const float2* Hb = H + (t0 - wstart) * hs;
     const df m1d = df_recip(df_from(wk * B.rho));   // 1/(omega rho) < 1/z
     // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
     acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
@@ -513,31 +839,57 @@ __global__ void __launch_bounds__(128, 4) k_asy_interp(const ProbParams* __restr
     const int qs = P.qs;
     for (int q = 0; q < Q; ++q) {
         df prd, pid;
-        if (q < qs) {
-            acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
-#pragma unroll
-            for (int i = 0; i < kMaxW; ++i) {
-                if (i < w) {
-                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q]
-                                             : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                    const df tp{th[i], tl[i]};
-                    acc_fma(pr, tp, df{gv.x, gv.y});
-                    acc_fma(pi, tp, df{gv.z, gv.w});
+        if (mom) {
+            const float2* hq = Hb + 2 * q;
+            if (q < qs) {
+                acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
+                int d = 0;
+                for (; d < dci; ++d) {
+                    const float2 tp = u[d];
+                    const float4 hv = *(const float4*)(hq + d * Q2);
+                    acc_fma(pr, df{tp.x, tp.y}, df{hv.x, hv.y});
+                    acc_fma(pi, df{tp.x, tp.y}, df{hv.z, hv.w});
                 }
+                float fr = 0.f, fi = 0.f;
+                for (; d < nb; ++d) {
+                    const float tp = u[d].x;
+                    const float4 hv = *(const float4*)(hq + d * Q2);
+                    fr = fmaf(tp, hv.x, fr);
+                    fi = fmaf(tp, hv.z, fi);
+                }
+                pr.c += fr;
+                pi.c += fi;
+                prd = fast_two_sum(pr.s, pr.c);
+                pid = fast_two_sum(pi.s, pi.c);
+            } else {
+                // small Hankel term: FP32 is accurate enough
+                float pr = 0.f, pi = 0.f;
+                for (int d = 0; d < nb; ++d) {
+                    const float tp = u[d].x;
+                    const float4 hv = *(const float4*)(hq + d * Q2);
+                    pr = fmaf(tp, hv.x, pr);
+                    pi = fmaf(tp, hv.z, pi);
+                }
+                prd = df{pr, 0.f};
+                pid = df{pi, 0.f};
+            }
+        } else if (q < qs) {
+            acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                const float2 tp = u[i];
+                acc_fma(pr, df{tp.x, tp.y}, df{gv.x, gv.y});
+                acc_fma(pi, df{tp.x, tp.y}, df{gv.z, gv.w});
             }
             prd = fast_two_sum(pr.s, pr.c);
             pid = fast_two_sum(pi.s, pi.c);
         } else {
-            // small Hankel term: FP32 interpolation is accurate enough
             float pr = 0.f, pi = 0.f;
-#pragma unroll
-            for (int i = 0; i < kMaxW; ++i) {
-                if (i < w) {
-                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q]
-                                             : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                    pr = fmaf(th[i], gv.x, pr);
-                    pi = fmaf(th[i], gv.z, pi);
-                }
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                const float tp = u[i].x;
+                pr = fmaf(tp, gv.x, pr);
+                pi = fmaf(tp, gv.z, pi);
             }
             prd = df{pr, 0.f};
             pid = df{pi, 0.f};
@@ -1014,6 +1366,8 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
+    const size_t smem_mom = spread_moments_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
+    if (smem_mom > smem) smem = smem_mom;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
@@ -1078,11 +1432,10 @@ cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, con
                               double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
-                  sizeof(int) * 128;
+    const size_t smem = interp_smem(qmax, tab.w, tab.deg);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
+    k_asy_interp<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();
 }

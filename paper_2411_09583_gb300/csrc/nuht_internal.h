@@ -90,6 +90,10 @@ struct Tables {
     const float2* es2;     // the same as double-float (hi, lo)
     int w, deg;
     int deg_comp;          // degrees above this one are evaluated in plain FP32
+    const float2* ch2;     // [w][deg + 1] pieces in the Chebyshev basis T_d(v), double-float
+    int nb;                // Chebyshev terms kept (tail below 1e-3 eps)
+    int dcs;               // spreading moments of degree >= dcs accumulate in plain FP32
+    int dci;               // interpolation terms of degree >= dci are summed in plain FP32
     double half_w;         // w / 2
     const double* ph;      // psi-hat pieces [ph_pieces][ph_deg + 1] in v in [-1, 1]
     const float2* ph2;     // the same as double-float

@@ -113,9 +113,10 @@ static double es_kernel(double t, double beta)
 }
 
 // Chebyshev interpolant of f on [-1, 1] (deg + 1 first-kind nodes), returned
-// as monomial coefficients in v.
+// as monomial coefficients in v (and, if cheb is given, as the coefficients of
+// T_0..T_deg).
 template <class F>
-static void cheb_monomial(F f, int deg, double* out)
+static void cheb_monomial(F f, int deg, double* out, double* cheb = nullptr)
 {
     const int n = deg + 1;
     std::vector<double> fv(n), c(n, 0.0);
@@ -126,6 +127,8 @@ static void cheb_monomial(F f, int deg, double* out)
         c[j] = 2.0 * s / n;
     }
     c[0] *= 0.5;
+    if (cheb)
+        for (int j = 0; j < n; ++j) cheb[j] = c[j];
     // monomial coefficients of T_j by T_j = 2 v T_{j-1} - T_{j-2}
     std::vector<double> tm2(n, 0.0), tm1(n, 0.0), tj(n, 0.0);
     for (int i = 0; i < n; ++i) out[i] = 0.0;
@@ -193,14 +196,18 @@ const HostTables& kernel_tables(int w)
     T.beta = 2.30 * w;
     T.deg = w + 1 > kMaxDeg ? kMaxDeg : w + 1;
     T.es.assign((size_t)w * (T.deg + 1), 0.0);
+    T.ch.assign((size_t)w * (T.deg + 1), 0.0);
     for (int i = 0; i < w; ++i) {
         auto f = [&](double v) { return es_kernel(-1.0 + ((v + 1.0) * 0.5 + i) * 2.0 / w, T.beta); };
-        cheb_monomial(f, T.deg, &T.es[(size_t)i * (T.deg + 1)]);
+        cheb_monomial(f, T.deg, &T.es[(size_t)i * (T.deg + 1)], &T.ch[(size_t)i * (T.deg + 1)]);
     }
     T.es2.resize(T.es.size());
+    T.ch2.resize(T.ch.size());
     for (size_t i = 0; i < T.es.size(); ++i) {
         const float hi = (float)T.es[i];
         T.es2[i] = make_float2(hi, (float)(T.es[i] - (double)hi));
+        const float ch = (float)T.ch[i];
+        T.ch2[i] = make_float2(ch, (float)(T.ch[i] - (double)ch));
     }
     // psi^ on [0, xmax], xmax slightly above w pi / 4 (the largest argument used)
     std::vector<double> gx, gw;

@@ -506,6 +506,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_dir = A.reserve<DirectBlock>(vdir.size());
     size_t a_es = A.reserve<double>(T.es.size()), a_ph = A.reserve<double>(T.ph.size());
     size_t a_es2 = A.reserve<float2>(T.es2.size()), a_ph2 = A.reserve<float2>(T.ph2.size());
+    size_t a_ch2 = A.reserve<float2>(T.ch2.size());
     size_t a_tw = A.reserve<double2>(T.tw.size());
     constexpr int kLists = 8;
     SegList* lists[kLists] = {&smom, &seval, &sspread, &sinterp, &sfs, &sfa, &sfb, &sfk};
@@ -539,6 +540,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     put(a_dir, vdir.data(), sizeof(DirectBlock) * vdir.size());
     put(a_es, T.es.data(), sizeof(double) * T.es.size());
     put(a_es2, T.es2.data(), sizeof(float2) * T.es2.size());
+    put(a_ch2, T.ch2.data(), sizeof(float2) * T.ch2.size());
     put(a_ph, T.ph.data(), sizeof(double) * T.ph.size());
     put(a_ph2, T.ph2.data(), sizeof(float2) * T.ph2.size());
     put(a_tw, T.tw.data(), sizeof(double2) * T.tw.size());
@@ -590,6 +592,38 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
             tail = sum > tail ? sum : tail;
         }
         if (tail * 1.1920928955078125e-07 <= 1e-2 * P->eps) tb.deg_comp = k; else break;
+    }
+    // Chebyshev form of the taps (moment paths): nb terms, dropping a tail
+    // below 1e-3 eps; degrees >= dcs of the spreading moments accumulate in
+    // FP32 over at most ceil(tile / 8) points each, degrees >= dci of the
+    // interpolation sum in FP32, both with rounding below 1e-2 eps.
+    tb.ch2 = (const float2*)(D + a_ch2);
+    {
+        const int nc = T.deg + 1;
+        std::vector<double> tailmax(nc + 1, 0.0), colsum(nc, 0.0);
+        for (int i = 0; i < T.w; ++i) {
+            double sum = 0.0;
+            for (int d = nc - 1; d >= 0; --d) {
+                const double a = std::fabs(T.ch[(size_t)i * nc + d]);
+                sum += a;
+                colsum[d] += a;
+                tailmax[d] = sum > tailmax[d] ? sum : tailmax[d];
+            }
+        }
+        int nb = nc;
+        while (nb > 2 && tailmax[nb - 1] <= 1e-3 * P->eps) --nb;
+        tb.nb = nb;
+        const int nsub = (P->spread_threads + 7) / 8;
+        int dcs = nb;
+        while (dcs > 2 && tailmax[dcs - 1] * (nsub + nb) * 1.1920928955078125e-07 <= 1e-2 * P->eps) --dcs;
+        tb.dcs = dcs;
+        int dci = nb;
+        double acc = 0.0;
+        while (dci > 2) {
+            acc += colsum[dci - 1] * (dci + 2) * 5.9604644775390625e-08;
+            if (acc <= 1e-2 * P->eps) --dci; else break;
+        }
+        tb.dci = dci;
     }
     tb.ph = P->d_ph; tb.ph2 = (const float2*)(D + a_ph2);
     tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
