@@ -1,0 +1,227 @@
+// Algorithm 1 (Subdivide) with SplitIndices (Sec. 4.1) on the device.
+//
+// The host version (subdivide.cpp) walks a first-in first-out work list.
+// Here one CTA processes that list level by level: every mixed block of a
+// level is split at once (16 candidate rows read from the staircase), its
+// four children are classified, and block-wide prefix sums give each child
+// its place in the local / asymptotic / direct lists or in the next level.
+// Children are placed in the order the sequential walk would append them
+// (parents in list order, children upper-left, lower-right, upper-right,
+// lower-left), so for one problem the lists equal the host's, entry for
+// entry.  A batch's roots start together; the host orders the lists by
+// problem afterwards (a stable reordering).
+//
+// The staircase stair[w_off + k] = max{j : omega_k r_j <= z} (problem-local
+// column, or -1) is non-increasing in k, so a block is all local iff
+// stair[k1] >= j1 and all asymptotic iff stair[k0] < j0.
+#include <cstdint>
+
+#include "nuht_internal.h"
+
+namespace nuht {
+
+namespace {
+
+constexpr int kSubThreads = 1024;
+constexpr int kSubWarps = kSubThreads / 32;
+
+// 0 empty, 1 local, 2 asymptotic, 3 direct, 4 mixed (split further)
+__device__ __forceinline__ int classify(const int32_t* __restrict__ st, const SubBlk& b, int64_t min_size)
+{
+    if (b.k1 < b.k0 || b.j1 < b.j0) return 0;
+    if (st[b.k1] >= b.j1) return 1;
+    if (st[b.k0] < b.j0) return 2;
+    if ((int64_t)(b.k1 - b.k0 + 1) * (int64_t)(b.j1 - b.j0 + 1) <= min_size) return 3;
+    return 4;
+}
+
+// Exclusive block-wide prefix sum of a 64-bit value (four 16-bit counters
+// packed; no carries since a chunk adds at most 4 x kSubThreads per field).
+__device__ __forceinline__ uint64_t block_scan(uint64_t v, uint64_t* wsum, uint64_t* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t s = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    const uint64_t before = (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+    *total = wsum[kSubWarps - 1];
+    __syncthreads();
+    return before;
+}
+
+struct SubState {
+    int64_t nout[3];   // local, asymptotic, direct blocks written so far
+    int64_t nnext;     // blocks of the next level written so far
+    int ovf;
+};
+
+// Places up to four children per thread (classes cls[i], 0 = none) in
+// order: class lists out[c * ocap ...] and the next level's queue.
+__device__ __forceinline__ void emit(const SubBlk* ch, const int* cls, int nch, SubState& S, uint64_t* wsum,
+                                     SubBlk* __restrict__ out, int64_t ocap, SubBlk* __restrict__ next,
+                                     int64_t qcap)
+{
+    uint64_t cnt = 0;
+    for (int i = 0; i < nch; ++i)
+        if (cls[i] > 0) cnt += (uint64_t)1 << (16 * (cls[i] - 1));
+    uint64_t total;
+    const uint64_t off = block_scan(cnt, wsum, &total);
+    int64_t pos[4];
+    for (int c = 0; c < 3; ++c) pos[c] = S.nout[c] + (int64_t)((off >> (16 * c)) & 0xffff);
+    pos[3] = S.nnext + (int64_t)(off >> 48);
+    bool fits = S.ovf == 0;
+    for (int c = 0; c < 3; ++c) fits = fits && S.nout[c] + (int64_t)((total >> (16 * c)) & 0xffff) <= ocap;
+    fits = fits && S.nnext + (int64_t)(total >> 48) <= qcap;
+    if (fits) {
+        for (int i = 0; i < nch; ++i) {
+            const int c = cls[i];
+            if (c == 0) continue;
+            if (c == 4) next[pos[3]++] = ch[i];
+            else out[(c - 1) * ocap + pos[c - 1]++] = ch[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!fits) S.ovf = 1;
+        for (int c = 0; c < 3; ++c) S.nout[c] += (int64_t)((total >> (16 * c)) & 0xffff);
+        S.nnext += (int64_t)(total >> 48);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSubThreads) k_subdivide(
+    const int32_t* __restrict__ stair, const ProbParams* __restrict__ probs, int nprob, int64_t min_size,
+    int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* __restrict__ out, int64_t ocap,
+    int64_t* __restrict__ res)
+{
+    __shared__ uint64_t wsum[kSubWarps];
+    __shared__ SubState S;
+    if (threadIdx.x == 0) {
+        S.nout[0] = S.nout[1] = S.nout[2] = 0;
+        S.nnext = 0;
+        S.ovf = 0;
+    }
+    __syncthreads();
+    // the roots, one per problem
+    for (int base = 0; base < nprob; base += kSubThreads) {
+        const int p = base + threadIdx.x;
+        SubBlk ch{0, -1, 0, -1, 0};
+        int cls = 0;
+        if (p < nprob) {
+            const ProbParams& P = probs[p];
+            ch = SubBlk{0, (int32_t)P.m - 1, 0, (int32_t)P.n - 1, p};
+            cls = classify(stair + P.w_off, ch, min_size);
+        }
+        emit(&ch, &cls, 1, S, wsum, out, ocap, qa, qcap);
+    }
+    int64_t na = S.nnext;
+    while (na > 0 && S.ovf == 0) {
+        __syncthreads();   // every thread has read S.nnext and S.ovf
+        if (threadIdx.x == 0) S.nnext = 0;
+        __syncthreads();
+        for (int64_t base = 0; base < na; base += kSubThreads) {
+            const int64_t i = base + threadIdx.x;
+            SubBlk ch[4];
+            int cls[4] = {0, 0, 0, 0};
+            if (i < na) {
+                const SubBlk b = qa[i];
+                const int32_t* st = stair + probs[b.prob].w_off;
+                // SplitIndices: the candidate row minimising the mixed area,
+                // its column the last local one (ties keep the first)
+                const int rows = b.k1 - b.k0 + 1;
+                const int nc = rows <= n_cand ? rows : n_cand;
+                int64_t best = -1;
+                int bk = b.k0, bj = b.j0 - 1;
+                for (int c = 0; c < nc; ++c) {
+                    const int k = rows <= n_cand ? b.k0 + c
+                                                 : b.k0 + (int)(((int64_t)c * (b.k1 - b.k0)) / (n_cand - 1));
+                    int j = st[k];
+                    if (j > b.j1) j = b.j1;
+                    if (j < b.j0) j = b.j0 - 1;
+                    const int64_t area = (int64_t)(k - b.k0 + 1) * (b.j1 - j) + (int64_t)(b.k1 - k) * (j - b.j0 + 1);
+                    if (best < 0 || area < best) {
+                        best = area;
+                        bk = k;
+                        bj = j;
+                    }
+                }
+                ch[0] = SubBlk{b.k0, bk, b.j0, bj, b.prob};           // upper left: local
+                ch[1] = SubBlk{bk + 1, b.k1, bj + 1, b.j1, b.prob};   // lower right: asymptotic
+                ch[2] = SubBlk{b.k0, bk, bj + 1, b.j1, b.prob};       // upper right: mixed
+                ch[3] = SubBlk{bk + 1, b.k1, b.j0, bj, b.prob};       // lower left: mixed
+                for (int c = 0; c < 4; ++c) cls[c] = classify(st, ch[c], min_size);
+            }
+            emit(ch, cls, 4, S, wsum, out, ocap, qb, qcap);
+        }
+        na = S.nnext;
+        SubBlk* tmp = qa;
+        qa = qb;
+        qb = tmp;
+    }
+    if (threadIdx.x == 0) {
+        res[0] = S.nout[0];
+        res[1] = S.nout[1];
+        res[2] = S.nout[2];
+        res[3] = S.ovf;
+    }
+}
+
+// Sorted values at the block edges: local blocks R = r_{j1}; asymptotic
+// blocks (r_{j0}, r_{j1}, omega_{k0}, omega_{k1}).
+__global__ void k_block_bounds(const SubBlk* __restrict__ loc, int64_t nl, const SubBlk* __restrict__ asy,
+                               int64_t na, const ProbParams* __restrict__ probs, const double* __restrict__ r_s,
+                               const double* __restrict__ w_s, double* __restrict__ bl, double4* __restrict__ ba)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl + na;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nl) {
+            const SubBlk b = loc[i];
+            bl[i] = r_s[probs[b.prob].r_off + b.j1];
+        } else {
+            const SubBlk b = asy[i - nl];
+            const ProbParams& P = probs[b.prob];
+            ba[i - nl] = make_double4(r_s[P.r_off + b.j0], r_s[P.r_off + b.j1], w_s[P.w_off + b.k0],
+                                      w_s[P.w_off + b.k1]);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_subdivide(const int32_t* stair, const ProbParams* probs, int nprob, int64_t min_size,
+                             int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* out, int64_t ocap,
+                             int64_t* res, cudaStream_t s)
+{
+    k_subdivide<<<1, kSubThreads, 0, s>>>(stair, probs, nprob, min_size, n_cand, qa, qb, qcap, out, ocap, res);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_bounds(const SubBlk* loc, int64_t nl, const SubBlk* asy, int64_t na,
+                                const ProbParams* probs, const double* r_s, const double* w_s, double* bl,
+                                double4* ba, cudaStream_t s)
+{
+    if (nl + na <= 0) return cudaSuccess;
+    int64_t g = (nl + na + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_block_bounds<<<(int)g, 256, 0, s>>>(loc, nl, asy, na, probs, r_s, w_s, bl, ba);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nuht

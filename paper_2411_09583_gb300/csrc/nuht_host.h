@@ -38,6 +38,8 @@ const HostTables& kernel_tables(int w);
 struct HBlock {
     int64_t k0, k1, j0, j1;
     int32_t prob = 0;   // problem of a batch
+    // sorted values at the edges (r_j0, r_j1, omega_k0, omega_k1), filled by the plan
+    double b[4] = {0.0, 0.0, 0.0, 0.0};
 };
 
 // Algorithm 1 with SplitIndices on the sorted matrix, from the staircase

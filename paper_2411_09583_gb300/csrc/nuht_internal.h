@@ -84,6 +84,12 @@ struct Seg {
     int64_t first, last;
 };
 
+// A block of the subdivision in problem-local sorted indices: rows k0..k1
+// (frequencies), columns j0..j1 (points), problem prob of a batch.
+struct SubBlk {
+    int32_t k0, k1, j0, j1, prob;
+};
+
 // Kernel tables shared by every asymptotic block of a plan.
 struct Tables {
     const double* es;      // [w][deg + 1] monomial coefficients in v = 2 z0 - 1
@@ -117,6 +123,14 @@ size_t radix_sort_scratch_bytes(int64_t n);
 
 cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_t m, double z,
                              int32_t* s_out, cudaStream_t s);
+// Algorithm 1 on the device (one CTA): lists out[0..ocap) local,
+// out[ocap..2 ocap) asymptotic, out[2 ocap..3 ocap) direct; res = {counts, overflow}.
+cudaError_t launch_subdivide(const int32_t* stair, const ProbParams* probs, int nprob, int64_t min_size,
+                             int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* out, int64_t ocap,
+                             int64_t* res, cudaStream_t s);
+cudaError_t launch_block_bounds(const SubBlk* loc, int64_t nl, const SubBlk* asy, int64_t na,
+                                const ProbParams* probs, const double* r_s, const double* w_s, double* bl,
+                                double4* ba, cudaStream_t s);
 cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
                                   int nprob, int32_t* s_out, cudaStream_t s);
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,

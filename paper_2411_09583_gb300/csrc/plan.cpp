@@ -1,5 +1,6 @@
 // C ABI of the NUHT library: plan (sort + subdivision + work lists), execute
 // (Algorithm 2 on the device), info and helpers.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -320,6 +321,12 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t o_flag = sa.reserve<int>(2);
     size_t o_prb = sa.reserve<ProbParams>(probs.size());
     size_t o_roff = sa.reserve<int64_t>(probs.size() + 1), o_woff = sa.reserve<int64_t>(probs.size() + 1);
+    // device subdivision: two level queues, the three block lists, edge values
+    const int64_t qcap = (n + m) / 4 + 4096 + nprob, ocap = (n + m) / 8 + 16384 + nprob;
+    size_t o_qa = sa.reserve<SubBlk>(qcap), o_qb = sa.reserve<SubBlk>(qcap);
+    size_t o_out = sa.reserve<SubBlk>(3 * ocap);
+    size_t o_bl = sa.reserve<double>(ocap), o_ba = sa.reserve<double4>(ocap);
+    size_t o_res = sa.reserve<int64_t>(4);
     size_t o_scr = sa.size;
     size_t scr = radix_sort_scratch_bytes(n > m ? n : m);
     sa.size += align256(scr);
@@ -360,27 +367,74 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     NUHT_CK(radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr, scr, s, d_woff, nprob));
     if (nprob == 1) NUHT_CK(launch_staircase(r_s, n, w_s, m, probs[0].z, stair, s));
     else NUHT_CK(launch_staircase_many(r_s, w_s, m, d_prb, nprob, stair, s));
-    // sorted values (block geometry) and the staircase (subdivision) to pinned host memory
-    const size_t in_bytes = align256(8) + align256(sizeof(double) * n) + align256(sizeof(double) * m) +
-                            align256(sizeof(int32_t) * m);
-    NUHT_CK(g_stage_in.reserve(in_bytes));
+    // ---- subdivision (Algorithm 1) on the device ---------------------------
+    SubBlk* d_out = (SubBlk*)(sort_mem + o_out);
+    int64_t* d_res = (int64_t*)(sort_mem + o_res);
+    NUHT_CK(launch_subdivide(stair, d_prb, nprob, P->opt.min_size, P->opt.n_split_cand, (SubBlk*)(sort_mem + o_qa),
+                             (SubBlk*)(sort_mem + o_qb), qcap, d_out, ocap, d_res, s));
+    NUHT_CK(g_stage_in.reserve(256 + sizeof(int64_t) * 4));
     int* hflag = (int*)g_stage_in.p;
-    double* hr_p = (double*)(g_stage_in.p + align256(8));
-    double* hw_p = (double*)((char*)hr_p + align256(sizeof(double) * n));
-    int32_t* hst = (int32_t*)((char*)hw_p + align256(sizeof(double) * m));
+    int64_t* hres = (int64_t*)(g_stage_in.p + 128);
     NUHT_CK(cudaMemcpyAsync(hflag, d_flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-    if (n) NUHT_CK(cudaMemcpyAsync(hr_p, r_s, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (m) NUHT_CK(cudaMemcpyAsync(hw_p, w_s, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
-    if (m) NUHT_CK(cudaMemcpyAsync(hst, stair, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+    NUHT_CK(cudaMemcpyAsync(hres, d_res, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
     NUHT_CK(cudaStreamSynchronize(s));
     if (hflag[0] || hflag[1]) return NUHT_ERR_DOMAIN;
     P->plan_ms[0] = ms_since(clk);
-    const double* hr = hr_p;
-    const double* hw = hw_p;
-
-    // ---- subdivision (host, Algorithm 1), problem by problem ------------
     for (int c = 0; c < 3; ++c) P->hb[c].clear();
-    {
+    if (!hres[3]) {
+        // the lists and their edge values to pinned host memory
+        const int64_t nc[3] = {hres[0], hres[1], hres[2]};
+        double* d_bl = (double*)(sort_mem + o_bl);
+        double4* d_ba = (double4*)(sort_mem + o_ba);
+        NUHT_CK(launch_block_bounds(d_out, nc[0], d_out + ocap, nc[1], d_prb, r_s, w_s, d_bl, d_ba, s));
+        size_t off[5], tot = 0;
+        for (int c = 0; c < 3; ++c) { off[c] = tot; tot += align256(sizeof(SubBlk) * nc[c]); }
+        off[3] = tot; tot += align256(sizeof(double) * nc[0]);
+        off[4] = tot; tot += align256(sizeof(double4) * nc[1]);
+        NUHT_CK(g_stage_in.reserve(tot));
+        for (int c = 0; c < 3; ++c)
+            if (nc[c]) NUHT_CK(cudaMemcpyAsync(g_stage_in.p + off[c], d_out + c * ocap, sizeof(SubBlk) * nc[c],
+                                               cudaMemcpyDeviceToHost, s));
+        if (nc[0]) NUHT_CK(cudaMemcpyAsync(g_stage_in.p + off[3], d_bl, sizeof(double) * nc[0],
+                                           cudaMemcpyDeviceToHost, s));
+        if (nc[1]) NUHT_CK(cudaMemcpyAsync(g_stage_in.p + off[4], d_ba, sizeof(double4) * nc[1],
+                                           cudaMemcpyDeviceToHost, s));
+        NUHT_CK(cudaStreamSynchronize(s));
+        const double* hbl = (const double*)(g_stage_in.p + off[3]);
+        const double4* hba = (const double4*)(g_stage_in.p + off[4]);
+        // problem-major order (stable): the order of the host walk, problem by problem
+        std::vector<int64_t> start(nprob + 1);
+        for (int c = 0; c < 3; ++c) {
+            const SubBlk* sb = (const SubBlk*)(g_stage_in.p + off[c]);
+            std::vector<HBlock>& dst = P->hb[c];
+            dst.resize((size_t)nc[c]);
+            std::fill(start.begin(), start.end(), 0);
+            for (int64_t i = 0; i < nc[c]; ++i) ++start[sb[i].prob + 1];
+            for (int ip = 0; ip < nprob; ++ip) start[ip + 1] += start[ip];
+            for (int64_t i = 0; i < nc[c]; ++i) {
+                const SubBlk& b = sb[i];
+                const ProbParams& q = probs[b.prob];
+                HBlock h;
+                h.k0 = b.k0 + q.w_off; h.k1 = b.k1 + q.w_off;
+                h.j0 = b.j0 + q.r_off; h.j1 = b.j1 + q.r_off;
+                h.prob = b.prob;
+                if (c == 0) h.b[1] = hbl[i];
+                if (c == 1) { h.b[0] = hba[i].x; h.b[1] = hba[i].y; h.b[2] = hba[i].z; h.b[3] = hba[i].w; }
+                dst[(size_t)start[b.prob]++] = h;
+            }
+        }
+    } else {
+        // list capacity exceeded: sorted values and staircase to the host, Algorithm 1 there
+        const size_t in_bytes = align256(sizeof(double) * n) + align256(sizeof(double) * m) +
+                                align256(sizeof(int32_t) * m);
+        NUHT_CK(g_stage_in.reserve(in_bytes));
+        double* hr = (double*)g_stage_in.p;
+        double* hw = (double*)((char*)hr + align256(sizeof(double) * n));
+        int32_t* hst = (int32_t*)((char*)hw + align256(sizeof(double) * m));
+        if (n) NUHT_CK(cudaMemcpyAsync(hr, r_s, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (m) NUHT_CK(cudaMemcpyAsync(hw, w_s, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+        if (m) NUHT_CK(cudaMemcpyAsync(hst, stair, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+        NUHT_CK(cudaStreamSynchronize(s));
         std::vector<HBlock> lb, ab, db;
         for (int ip = 0; ip < nprob; ++ip) {
             const ProbParams& q = probs[ip];
@@ -390,6 +444,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
                 for (HBlock h : *src[c]) {
                     h.k0 += q.w_off; h.k1 += q.w_off; h.j0 += q.r_off; h.j1 += q.r_off;
                     h.prob = ip;
+                    h.b[0] = hr[h.j0]; h.b[1] = hr[h.j1]; h.b[2] = hw[h.k0]; h.b[3] = hw[h.k1];
                     P->hb[c].push_back(h);
                 }
         }
@@ -416,7 +471,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         LocalBlock lb{};
         lb.prob = h.prob;
         lb.k0 = (int32_t)h.k0; lb.k1 = (int32_t)h.k1; lb.j0 = (int32_t)h.j0; lb.j1 = (int32_t)h.j1;
-        lb.R = hr[h.j1];
+        lb.R = h.b[1];
         lb.mom_off = mom_off;
         mom_off += pp.L + 1;
         vloc.push_back(lb);
@@ -434,8 +489,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         AsyBlock ab{};
         ab.prob = h.prob;
         ab.k0 = (int32_t)h.k0; ab.k1 = (int32_t)h.k1; ab.j0 = (int32_t)h.j0; ab.j1 = (int32_t)h.j1;
-        const double rlo = hr[h.j0], rhi = hr[h.j1];
-        const double wlo = hw[h.k0], whi = hw[h.k1];
+        const double rlo = h.b[0], rhi = h.b[1];
+        const double wlo = h.b[2], whi = h.b[3];
         ab.rc = 0.5 * (rlo + rhi);
         const double X = 0.5 * (rhi - rlo);
         ab.wc = 0.5 * (wlo + whi);
