@@ -1147,16 +1147,139 @@ __device__ __forceinline__ float horner_f32(const float2* __restrict__ c, int de
     return acc;
 }
 
-// FP32 spreading (same structure as k_asy_spread; coordinates in FP64).
-__global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                                 const Tile* __restrict__ tiles, Tables tab,
-                                 const double* __restrict__ r_s, const double* __restrict__ c_s,
-                                 double2* __restrict__ grid_b)
+// Row stride (floats) for 16-byte loads by eight rows: = 4 mod 8.
+__host__ __device__ __forceinline__ int f32_stride4(int n)
 {
-    extern __shared__ float2 smf[];
-    const Tile t = tiles[blockIdx.x];
-    const AsyBlock B = blks[t.blk];
-    const int Q = probs[B.prob].Q;
+    const int r = (n + 3) & ~3;
+    return (r & 4) ? r : r + 4;
+}
+
+// FP32 spreading, dense tile: the moment form of spread_moments in single
+// precision (each of the 8 partial sums of a moment covers at most
+// ceil(tile / 8) points).
+__device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
+                                   const double* __restrict__ r_s, const double* __restrict__ c_s,
+                                   double2* __restrict__ gb, float* sm)
+{
+    const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
+    const int w = tab.w, nb = tab.nb;
+    const int Q2 = 2 * Q;
+    const int ndp = (nb + 1) >> 1, dpad = 2 * ndp, nq = Q2 >> 2;
+    const int su = mom_stride(nb), sx = f32_stride4(Q2);
+    float* U = sm;                               // [nt][su]
+    float* X = U + nt * su;                      // [nt][sx]
+    float* Mb = X + nt * sx;                     // [dpad][Q2]
+    float* Ach = Mb + dpad * Q2;                 // [w][dpad]
+    int* l0s = (int*)(Ach + w * dpad);           // [nt]
+    __shared__ int bstart[kMaxTileBins + 3];
+    for (int i = tid; i < w * dpad; i += nt) {
+        const int r = i / dpad, d = i - r * dpad;
+        Ach[i] = d < nb ? tab.ch2[r * (tab.deg + 1) + d].x : 0.f;
+    }
+    if (tid < cnt) {
+        const int64_t j = t.start + tid;
+        const double rj = r_s[j];
+        double vd;
+        l0s[tid] = spread_cell(B, tab, rj, &vd);
+        const float v = (float)vd;
+        float* u = U + tid * su;
+        float tm = 1.f, tc = v;
+        u[0] = 1.f;
+        u[1] = v;
+        for (int d = 2; d < nb; ++d) {
+            const float tn = fmaf(2.f * v, tc, -tm);
+            u[d] = tn;
+            tm = tc;
+            tc = tn;
+        }
+        for (int d = nb; d < su; ++d) u[d] = 0.f;
+        float sn, cs;
+        f32_sincos_prod(B.wc, rj - B.rc, &sn, &cs);
+        const float ratio = (float)(B.rho / rj);
+        const float w0 = (float)c_s[j] * sqrtf(ratio);
+        float wr = w0 * cs, wi = w0 * sn;
+        float* x = X + tid * sx;
+        for (int q = 0; q < Q; ++q) {
+            x[2 * q] = wr;
+            x[2 * q + 1] = wi;
+            wr *= ratio;
+            wi *= ratio;
+        }
+    }
+    __syncthreads();
+    const int lfirst = l0s[0];
+    const int nbins = l0s[cnt - 1] - lfirst + 1;
+    for (int b = tid; b <= nbins; b += nt) {
+        const int key = lfirst + b;
+        int lo = 0, hi = cnt;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
+        bstart[b] = lo;
+    }
+    __syncthreads();
+    const int nf1 = 2 * B.N1 + 1;
+    const int nitems = ndp * nq * kSpreadSub;
+    const int nitems_pad = (nitems + 31) & ~31;
+    for (int b = 0; b < nbins; ++b) {
+        const int p0 = bstart[b], p1 = bstart[b + 1];
+        if (p0 == p1) continue;
+        for (int it = tid; it < nitems_pad; it += nt) {
+            const bool live = it < nitems;
+            const int sub = it & (kSpreadSub - 1);
+            const int o = live ? it / kSpreadSub : 0;
+            const int dp = o / nq, qq = o - dp * nq;
+            float A[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            if (live) {
+                for (int p = p0 + sub; p < p1; p += kSpreadSub) {
+                    const float2 uu = *(const float2*)(U + p * su + 2 * dp);
+                    const float4 xx = *(const float4*)(X + p * sx + 4 * qq);
+                    const float xs[4] = {xx.x, xx.y, xx.z, xx.w};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        A[0][f] = fmaf(uu.x, xs[f], A[0][f]);
+                        A[1][f] = fmaf(uu.y, xs[f], A[1][f]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    float a = A[e][f];
+#pragma unroll
+                    for (int off = kSpreadSub >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+                    if (live && sub == 0) Mb[(2 * dp + e) * Q2 + 4 * qq + f] = a;
+                }
+        }
+        __syncthreads();
+        const int l0 = lfirst + b;
+        for (int o = tid; o < w * Q2; o += nt) {
+            const int i = o / Q2, qv = o - i * Q2;
+            const int idx = l0 + i + B.N1;
+            if (idx < 0 || idx >= nf1) continue;
+            float sacc = 0.f;
+            for (int d = 0; d < nb; ++d) sacc = fmaf(Ach[i * dpad + d], Mb[d * Q2 + qv], sacc);
+            if (sacc != 0.f) {
+                double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
+                atomicAdd(dst, (double)sacc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__host__ __device__ __forceinline__ size_t spread_moments_f32_smem(int nt, int Q, int w, int nb)
+{
+    const int dpad = 2 * ((nb + 1) >> 1);
+    return sizeof(float) * ((size_t)nt * mom_stride(nb) + (size_t)nt * f32_stride4(2 * Q) +
+                            (size_t)dpad * 2 * Q + (size_t)w * dpad) +
+           sizeof(int) * (size_t)nt;
+}
+
+// FP32 spreading, sparse tile: taps per point, one thread per (cell, q).
+__device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
+                                const double* __restrict__ r_s, const double* __restrict__ c_s,
+                                double2* __restrict__ gb, float2* smf)
+{
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
     float2* aval = smf;                              // [nt][Q]
@@ -1169,15 +1292,12 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     if (tid < cnt) {
         const int64_t j = t.start + tid;
         const double rj = r_s[j];
-        const double x = rj - B.rc;
-        const double a = x * B.inv_h - tab.half_w;
-        const double lf = ceil(a);
-        const float z0 = fminf(fmaxf((float)(lf - a), 0.f), 1.f);
-        const float v = 2.f * z0 - 1.f;
+        double vd;
+        l0s[tid] = spread_cell(B, tab, rj, &vd);
+        const float v = (float)vd;
         for (int i = 0; i < w; ++i) taps[tid * w + i] = horner_f32(coef + i * (deg + 1), deg, v);
-        l0s[tid] = (int)lf;
         float sn, cs;
-        f32_sincos_prod(B.wc, x, &sn, &cs);
+        f32_sincos_prod(B.wc, rj - B.rc, &sn, &cs);
         const float ratio = (float)(B.rho / rj);
         const float w0 = (float)c_s[j] * sqrtf(ratio);
         float wr = w0 * cs, wi = w0 * sn;
@@ -1191,7 +1311,6 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     const int lfirst = l0s[0];
     const int span = l0s[cnt - 1] - lfirst + w;
     const int nf1 = 2 * B.N1 + 1;
-    double2* gb = grid_b + B.b_off;
     const bool dense = span <= 2 * w;
     for (int item = tid; item < span * Q; item += nt) {
         const int c = item / Q, q = item - c * Q;
@@ -1224,8 +1343,44 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     }
 }
 
-// FP32 interpolation and Hankel combination (coordinates and phase reduction in FP64).
-__global__ void __launch_bounds__(128) k_asy_interp_f32(
+// FP32 spreading (coordinates and phase reduction in FP64).
+__global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+                                 const Tile* __restrict__ tiles, Tables tab,
+                                 const double* __restrict__ r_s, const double* __restrict__ c_s,
+                                 double2* __restrict__ grid_b)
+{
+    extern __shared__ float2 smf[];
+    __shared__ int use_mom;
+    const Tile t = tiles[blockIdx.x];
+    const AsyBlock B = blks[t.blk];
+    const int Q = probs[B.prob].Q;
+    if (t.count <= 0) return;
+    if (threadIdx.x == 0) {
+        double v;
+        const int lfirst = spread_cell(B, tab, r_s[t.start], &v);
+        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &v) - lfirst + 1;
+        use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
+    }
+    __syncthreads();
+    double2* gb = grid_b + B.b_off;
+    if (use_mom)
+        spread_moments_f32(B, Q, t, tab, r_s, c_s, gb, (float*)smf);
+    else
+        spread_taps_f32(B, Q, t, tab, r_s, c_s, gb, smf);
+}
+
+// Shared memory (bytes) of k_asy_interp_f32 for 2M = qmax.
+__host__ __device__ __forceinline__ size_t interp_f32_smem(int qmax, int w, int deg)
+{
+    const int us = (deg + 1 > w ? deg + 1 : w) | 1;
+    return sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)((w * (deg + 1) + 1) & ~1) +
+           kInterpHBytes + sizeof(float) * (size_t)kInterpTileThreads * us + sizeof(int) * kInterpTileThreads;
+}
+
+// FP32 interpolation and Hankel combination (coordinates and phase
+// reduction in FP64); dense tiles by per-bin Chebyshev sums as in
+// k_asy_interp, sparse tiles by taps.
+__global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
     Tables tab, const double* __restrict__ w_s, const float4* __restrict__ grid_q, double* __restrict__ g_s)
 {
@@ -1233,11 +1388,14 @@ __global__ void __launch_bounds__(128) k_asy_interp_f32(
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
-    const int w = tab.w, deg = tab.deg;
-    const int Q = P.Q;
+    const int w = tab.w, deg = tab.deg, nb = tab.nb;
+    const int Q = P.Q, Q2 = 2 * Q;
+    const int us = (deg + 1 > w ? deg + 1 : w) | 1;
+    const int hs = nb * Q2 + 2;                                  // bin stride of H (floats, even)
     float2* coef2 = (float2*)(winf + kWinCells * Q);
-    int* t0s = (int*)(coef2 + w * (deg + 1));
-    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    float* H = (float*)(coef2 + ((w * (deg + 1) + 1) & ~1));     // [bins][hs]
+    float* U = H + kInterpHBytes / sizeof(float);                // [threads][us]
+    int* t0s = (int*)(U + kInterpTileThreads * us);
     const bool valid = (int)threadIdx.x < t.count;
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
     const double wk = w_s[k];
@@ -1249,31 +1407,72 @@ __global__ void __launch_bounds__(128) k_asy_interp_f32(
     if (valid) t0s[threadIdx.x] = t0;
     __syncthreads();
     const int wstart = t0s[0];
-    const int wlen = t0s[t.count - 1] - wstart + w;
+    const int nbins = t0s[t.count - 1] - wstart + 1;
+    const int wlen = nbins - 1 + w;
     const int mask = B.nf2 - 1;
     const float4* gq = grid_q + B.q_off;
     const bool staged = wlen <= kWinCells;
+    const int maxbins = kInterpHBytes / (int)(sizeof(float) * hs);
+    const bool mom = staged && nbins <= maxbins && t.count >= kMomMinPerBin * nbins;
     if (staged)
         for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
             const int cc = idx / Q;
             winf[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
         }
+    if (mom) {
+        for (int i = threadIdx.x; i < w * nb; i += blockDim.x) {
+            const int r = i / nb, d = i - r * nb;
+            coef2[i] = tab.ch2[r * (deg + 1) + d];
+        }
+    } else {
+        for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    }
     __syncthreads();
+    if (mom) {
+        for (int o = threadIdx.x; o < nbins * nb * Q2; o += blockDim.x) {
+            const int b = o / (nb * Q2), rem = o - b * nb * Q2;
+            const int d = rem / Q2, qv = rem - d * Q2;
+            const int q = qv >> 1, im = qv & 1;
+            float acc = 0.f;
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = winf[(b + i) * Q + q];
+                acc = fmaf(coef2[i * nb + d].x, im ? gv.z : gv.x, acc);
+            }
+            H[b * hs + rem] = acc;
+        }
+        __syncthreads();
+    }
     if (!valid) return;
-    float tp[kMaxW];
-#pragma unroll
-    for (int i = 0; i < kMaxW; ++i) tp[i] = (i < w) ? horner_f32(coef2 + i * (deg + 1), deg, v) : 0.f;
+    float* u = U + threadIdx.x * us;
+    if (mom) {
+        float tm = 1.f, tc = v;
+        u[0] = 1.f;
+        u[1] = v;
+        for (int d = 2; d < nb; ++d) {
+            const float tn = fmaf(2.f * v, tc, -tm);
+            u[d] = tn;
+            tm = tc;
+            tc = tn;
+        }
+    } else {
+        for (int i = 0; i < w; ++i) u[i] = horner_f32(coef2 + i * (deg + 1), deg, v);
+    }
+    const float* Hb = H + (t0 - wstart) * hs;
     const float m1 = (float)(1.0 / (wk * B.rho));
     float tr = 0.f, ti = 0.f, mq = 1.f;
     for (int q = 0; q < Q; ++q) {
         float pr = 0.f, pi = 0.f;
-#pragma unroll
-        for (int i = 0; i < kMaxW; ++i) {
-            if (i < w) {
-                const float4 gv = staged ? winf[(t0 + i - wstart) * Q + q]
-                                         : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                pr = fmaf(tp[i], gv.x, pr);
-                pi = fmaf(tp[i], gv.z, pi);
+        if (mom) {
+            for (int d = 0; d < nb; ++d) {
+                const float2 hv = *(const float2*)(Hb + d * Q2 + 2 * q);
+                pr = fmaf(u[d], hv.x, pr);
+                pi = fmaf(u[d], hv.y, pi);
+            }
+        } else {
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = staged ? winf[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                pr = fmaf(u[i], gv.x, pr);
+                pi = fmaf(u[i], gv.z, pi);
             }
         }
         const float cq = P.a2[q].x * mq;
@@ -1338,6 +1537,8 @@ cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks,
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float2) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
+    const size_t smem_mom = spread_moments_f32_smem(nt, qmax, tab.w, tab.nb);
+    if (smem_mom > smem) smem = smem_mom;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
@@ -1350,11 +1551,10 @@ cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks,
                                   double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
-                  sizeof(int) * 128;
+    const size_t smem = interp_f32_smem(qmax, tab.w, tab.deg);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp_f32<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
+    k_asy_interp_f32<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -177,6 +177,31 @@ struct Staging {
 std::mutex g_stage_mu;
 Staging g_stage_in, g_stage_out;
 
+// Per-device auxiliary stream (and fork / join events) for the independent
+// halves of a plan build, used under g_stage_mu.
+struct Aux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+Aux g_aux[64];
+
+cudaError_t aux_stream(Aux** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    Aux& a = g_aux[dev];
+    if (!a.s) {
+        e = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    *out = &a;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 namespace {
@@ -328,8 +353,10 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t o_bl = sa.reserve<double>(ocap), o_ba = sa.reserve<double4>(ocap);
     size_t o_res = sa.reserve<int64_t>(4);
     size_t o_scr = sa.size;
-    size_t scr = radix_sort_scratch_bytes(n > m ? n : m);
+    const size_t scr = radix_sort_scratch_bytes(n), scr_w = radix_sort_scratch_bytes(m);
     sa.size += align256(scr);
+    const size_t o_scr_w = sa.size;
+    sa.size += align256(scr_w);
     char* sort_mem = nullptr;
     NUHT_CK(pool_alloc((void**)&sort_mem, sa.size, s));
     struct Free {
@@ -363,8 +390,22 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     int32_t* pr = (int32_t*)(sort_mem + o_pr);
     int32_t* pw = (int32_t*)(sort_mem + o_pw);
     int32_t* stair = (int32_t*)(sort_mem + o_st);
-    NUHT_CK(radix_sort_f64(r, n, r_s, pr, sort_mem + o_scr, scr, s, d_roff, nprob));
-    NUHT_CK(radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr, scr, s, d_woff, nprob));
+    // the two sorts are independent: omega on the auxiliary stream
+    {
+        Aux* ax = nullptr;
+        NUHT_CK(aux_stream(&ax));
+        NUHT_CK(cudaEventRecord(ax->fork, s));
+        NUHT_CK(cudaStreamWaitEvent(ax->s, ax->fork, 0));
+        const cudaError_t ew = radix_sort_f64(omega, m, w_s, pw, sort_mem + o_scr_w, scr_w, ax->s, d_woff, nprob);
+        const cudaError_t ej = cudaEventRecord(ax->join, ax->s);
+        const cudaError_t er = radix_sort_f64(r, n, r_s, pr, sort_mem + o_scr, scr, s, d_roff, nprob);
+        // join before anything can free the sort memory
+        const cudaError_t ek = ej == cudaSuccess ? cudaStreamWaitEvent(s, ax->join, 0) : cudaStreamSynchronize(ax->s);
+        NUHT_CK(ew);
+        NUHT_CK(ej);
+        NUHT_CK(er);
+        NUHT_CK(ek);
+    }
     if (nprob == 1) NUHT_CK(launch_staircase(r_s, n, w_s, m, probs[0].z, stair, s));
     else NUHT_CK(launch_staircase_many(r_s, w_s, m, d_prb, nprob, stair, s));
     // ---- subdivision (Algorithm 1) on the device ---------------------------
