@@ -192,24 +192,29 @@ def run_reference(a):
 
 # ---------------------------------------------------------------- our arm
 def _dominant_flops(stage, info, blocks, tab):
-    """Algorithmic FP64 FLOPs of one launch of the stage (see the design notes)."""
-    w, d, Q, L = tab["w"], tab["deg"], 2 * info["M"], info["L"]
-    asy = blocks[1]
-    loc = blocks[0]
+    """Algorithmic FP64 FLOPs of one launch of the stage: the work the method
+    must do per unit (Sec. 3-4), not the kernels' own operation counts.
+
+    asymptotic point or frequency: 2M w complex-by-real tap updates, 4 w Q flops
+    (Q = 2M); local point or frequency: (L+1) term updates, 4 (L+1) flops;
+    direct entry: one J_nu evaluation, counted as 150 flops."""
+    w, Q, L = tab["w"], 2 * info["M"], info["L"]
+    asy, loc, dirb = blocks[1], blocks[0], blocks[2]
     if stage == "asy_spread":
         units = float((asy[:, 3] - asy[:, 2] + 1).sum())
-        return units * (2 * w * d + 4 * w * Q), units
+        return units * 4 * w * Q, units
     if stage == "asy_interp":
         units = float((asy[:, 1] - asy[:, 0] + 1).sum())
-        return units * (2 * w * d + 4 * w * Q), units
+        return units * 4 * w * Q, units
     if stage == "local_moments":
         units = float((loc[:, 3] - loc[:, 2] + 1).sum())
         return units * 4 * (L + 1), units
     if stage == "local_eval":
-        # per row: 2 multiply-adds per Miller step (ns ~ max(L + 8, y + 20 + 4 sqrt y))
-        # and 2 per Wimp term
         units = float((loc[:, 1] - loc[:, 0] + 1).sum())
-        return units * (4 * (L + 28) + 4 * (L + 1)), units
+        return units * 4 * (L + 1), units
+    if stage == "direct":
+        units = float(((dirb[:, 1] - dirb[:, 0] + 1) * (dirb[:, 3] - dirb[:, 2] + 1)).sum())
+        return units * 150.0, units
     return None, None
 
 
