@@ -73,25 +73,26 @@ __device__ __forceinline__ df psihat_df(const Tables& T, double xi)
 // A point r_j of a block covers the w grid cells l0 + i, i < w, with
 // l0 = ceil((r_j - r_c)/h - w/2), and tap i of the ES kernel is the
 // polynomial piece psi_i(v), v = 2 (l0 - (r_j - r_c)/h + w/2) - 1 in [-1, 1].
-__device__ __forceinline__ int spread_cell(const AsyBlock& B, const Tables& tab, double rj, double* v)
+__device__ __forceinline__ int spread_cell(const AsyBlock& B, const Tables& tab, double rj, double* x, double* v)
 {
     // explicit roundings: every call site computes the same cell
-    const double a = __dadd_rn(__dmul_rn(__dadd_rn(rj, -B.rc), B.inv_h), -tab.half_w);
+    *x = __dadd_rn(rj, -B.rc);
+    const double a = __dadd_rn(__dmul_rn(*x, B.inv_h), -tab.half_w);
     const double lf = ceil(a);
-    double z0 = lf - a;
-    z0 = fmin(fmax(z0, 0.0), 1.0);
-    *v = 2.0 * z0 - 1.0;
+    *v = __fma_rn(2.0, lf - a, -1.0);   // lf - a in [0, 1], exact or rounded into the range
     return (int)lf;
 }
 
-// c_j (r_j/rho)^(-1/2) e^{i w_c (r_j - r_c)} as double-float (re, im), and the
-// ratio (r_j/rho)^(-1) that steps the weight from q to q + 1.
-__device__ __forceinline__ void spread_weight(const AsyBlock& B, double rj, double cj, df* wr, df* wi, df* rat)
+// c_j (r_j/rho)^(-1/2) e^{i w_c x_j} as double-float (re, im), x_j = r_j - r_c,
+// and the ratio (r_j/rho)^(-1) that steps the weight from q to q + 1; r_j and
+// c_j come as double-float pairs.
+__device__ __forceinline__ void spread_weight(const AsyBlock& B, double x, float2 r2, float2 c2, df* wr, df* wi,
+                                              df* rat)
 {
     df sn, cs;
-    df_sincos_prod(B.wc, rj - B.rc, &sn, &cs);
-    *rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));
-    const df w0 = df_mul(df_from(cj), df_sqrt(*rat));
+    df_sincos_prod(B.wc, x, &sn, &cs);
+    *rat = df_mul(df{B.rho_h, B.rho_l}, df_recip(df{r2.x, r2.y}));
+    const df w0 = df_mul(df{c2.x, c2.y}, df_sqrt(*rat));
     *wr = df_mul(w0, cs);
     *wi = df_mul(w0, sn);
 }
@@ -141,8 +142,8 @@ __device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
 // tab.dcs, whose coefficients are tiny, accumulate in plain FP32, the rest
 // in double-float.
 __device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
-                               const double* __restrict__ r_s, const double* __restrict__ c_s,
-                               double2* __restrict__ gb, float2* sm)
+                               const double* __restrict__ r_s, const float2* __restrict__ r2,
+                               const float2* __restrict__ c2, double2* __restrict__ gb, float2* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -163,9 +164,8 @@ __device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Ta
     }
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        const double rj = r_s[j];
-        double v;
-        l0s[tid] = spread_cell(B, tab, rj, &v);
+        double x, v;
+        l0s[tid] = spread_cell(B, tab, r_s[j], &x, &v);
         // Chebyshev basis by T_{d+1} = 2 v T_d - T_{d-1}
         float2* ud = Ud + tid * L.sud;
         float* uf = Uf + tid * L.suf;
@@ -191,11 +191,11 @@ __device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Ta
         }
         for (int e = nb - dcs; e < L.suf; ++e) uf[e] = 0.f;
         df wr, wi, rat;
-        spread_weight(B, rj, c_s[j], &wr, &wi, &rat);
-        float2* x = X + tid * L.sx;
+        spread_weight(B, x, r2[j], c2[j], &wr, &wi, &rat);
+        float2* xq = X + tid * L.sx;
         for (int q = 0; q < Q; ++q) {
-            x[2 * q] = make_float2(wr.h, wr.l);
-            x[2 * q + 1] = make_float2(wi.h, wi.l);
+            xq[2 * q] = make_float2(wr.h, wr.l);
+            xq[2 * q + 1] = make_float2(wi.h, wi.l);
             wr = df_mul(wr, rat);
             wi = df_mul(wi, rat);
         }
@@ -317,8 +317,8 @@ __host__ __device__ __forceinline__ size_t spread_moments_smem(int nt, int Q, in
 // over the points whose taps cover that cell and adds the sum to the block's
 // global grid.
 __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
-                            const double* __restrict__ r_s, const double* __restrict__ c_s,
-                            double2* __restrict__ gb, float4* smem4)
+                            const double* __restrict__ r_s, const float2* __restrict__ r2,
+                            const float2* __restrict__ c2, double2* __restrict__ gb, float4* smem4)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -331,16 +331,15 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
     const int cnt = t.count;
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        const double rj = r_s[j];
-        double v;
-        l0s[tid] = spread_cell(B, tab, rj, &v);
+        double x, v;
+        l0s[tid] = spread_cell(B, tab, r_s[j], &x, &v);
         const float vh = (float)v, vl = (float)(v - (double)vh);
         for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
         df wr, wi, rat;
-        spread_weight(B, rj, c_s[j], &wr, &wi, &rat);
+        spread_weight(B, x, r2[j], c2[j], &wr, &wi, &rat);
         for (int q = 0; q < Q; ++q) {
             aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
             wr = df_mul(wr, rat);
@@ -412,8 +411,8 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
 // takes the moment path when its points are dense in the grid's bins.
 __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, Tables tab,
-                             const double* __restrict__ r_s, const double* __restrict__ c_s,
-                             double2* __restrict__ grid_b)
+                             const double* __restrict__ r_s, const float2* __restrict__ r2,
+                             const float2* __restrict__ c2, double2* __restrict__ grid_b)
 {
     extern __shared__ float4 smem4[];
     __shared__ int use_mom;
@@ -422,17 +421,17 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     const int Q = probs[B.prob].Q;
     if (t.count <= 0) return;
     if (threadIdx.x == 0) {
-        double v;
-        const int lfirst = spread_cell(B, tab, r_s[t.start], &v);
-        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &v) - lfirst + 1;
+        double x, v;
+        const int lfirst = spread_cell(B, tab, r_s[t.start], &x, &v);
+        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &x, &v) - lfirst + 1;
         use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
     }
     __syncthreads();
     double2* gb = grid_b + B.b_off;
     if (use_mom)
-        spread_moments(B, Q, t, tab, r_s, c_s, gb, (float2*)smem4);
+        spread_moments(B, Q, t, tab, r_s, r2, c2, gb, (float2*)smem4);
     else
-        spread_taps(B, Q, t, tab, r_s, c_s, gb, smem4);
+        spread_taps(B, Q, t, tab, r_s, r2, c2, gb, smem4);
 }
 
 // -------------------------------------------------------------------- FFT
@@ -724,7 +723,8 @@ __host__ __device__ __forceinline__ size_t interp_smem(int qmax, int w, int deg)
 // basis (or taps) in a row of shared memory.
 __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
-    Tables tab, const double* __restrict__ w_s, const float4* __restrict__ grid_q, double* __restrict__ g_s)
+    Tables tab, const double* __restrict__ w_s, const float2* __restrict__ w2, const float4* __restrict__ grid_q,
+    double* __restrict__ g_s)
 {
     extern __shared__ float4 win[];          // [kWinCells][Q] grid cells of this tile
     const Tile t = tiles[blockIdx.x];
@@ -742,11 +742,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
     const double wk = w_s[k];
     const double s = wk - B.wc;
-    const double a = s * B.h * B.inv_delta - tab.half_w;
+    const double a = s * B.hd - tab.half_w;
     const double tf = ceil(a);
-    double z0 = tf - a;
-    z0 = fmin(fmax(z0, 0.0), 1.0);
-    const double v = 2.0 * z0 - 1.0;
+    const double v = fma(2.0, tf - a, -1.0);   // tf - a in [0, 1]
     const float vh = (float)v, vl = (float)(v - (double)vh);
     // the tile's targets are sorted, so their cells form one window
     const int t0 = (int)tf;
@@ -832,7 +830,8 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
         }
     }
     const float2* Hb = H + (t0 - wstart) * hs;
-    const df m1d = df_recip(df_from(wk * B.rho));   // 1/(omega rho) < 1/z
+    const float2 wk2 = w2[k];
+    const df m1d = df_recip(df_mul(df{wk2.x, wk2.y}, df{B.rho_h, B.rho_l}));   // 1/(omega rho) < 1/z
     // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
     acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
     df mq{1.f, 0.f};
@@ -1158,8 +1157,8 @@ __host__ __device__ __forceinline__ int f32_stride4(int n)
 // precision (each of the 8 partial sums of a moment covers at most
 // ceil(tile / 8) points).
 __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
-                                   const double* __restrict__ r_s, const double* __restrict__ c_s,
-                                   double2* __restrict__ gb, float* sm)
+                                   const double* __restrict__ r_s, const float2* __restrict__ r2,
+                                   const float2* __restrict__ c2, double2* __restrict__ gb, float* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb;
@@ -1178,9 +1177,8 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
     }
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        const double rj = r_s[j];
-        double vd;
-        l0s[tid] = spread_cell(B, tab, rj, &vd);
+        double xd, vd;
+        l0s[tid] = spread_cell(B, tab, r_s[j], &xd, &vd);
         const float v = (float)vd;
         float* u = U + tid * su;
         float tm = 1.f, tc = v;
@@ -1194,14 +1192,14 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
         }
         for (int d = nb; d < su; ++d) u[d] = 0.f;
         float sn, cs;
-        f32_sincos_prod(B.wc, rj - B.rc, &sn, &cs);
-        const float ratio = (float)(B.rho / rj);
-        const float w0 = (float)c_s[j] * sqrtf(ratio);
+        f32_sincos_prod(B.wc, xd, &sn, &cs);
+        const float ratio = B.rho_h / r2[j].x;
+        const float w0 = c2[j].x * sqrtf(ratio);
         float wr = w0 * cs, wi = w0 * sn;
-        float* x = X + tid * sx;
+        float* xq = X + tid * sx;
         for (int q = 0; q < Q; ++q) {
-            x[2 * q] = wr;
-            x[2 * q + 1] = wi;
+            xq[2 * q] = wr;
+            xq[2 * q + 1] = wi;
             wr *= ratio;
             wi *= ratio;
         }
@@ -1277,8 +1275,8 @@ __host__ __device__ __forceinline__ size_t spread_moments_f32_smem(int nt, int Q
 
 // FP32 spreading, sparse tile: taps per point, one thread per (cell, q).
 __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
-                                const double* __restrict__ r_s, const double* __restrict__ c_s,
-                                double2* __restrict__ gb, float2* smf)
+                                const double* __restrict__ r_s, const float2* __restrict__ r2,
+                                const float2* __restrict__ c2, double2* __restrict__ gb, float2* smf)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -1291,15 +1289,14 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
     const int cnt = t.count;
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        const double rj = r_s[j];
-        double vd;
-        l0s[tid] = spread_cell(B, tab, rj, &vd);
+        double xd, vd;
+        l0s[tid] = spread_cell(B, tab, r_s[j], &xd, &vd);
         const float v = (float)vd;
         for (int i = 0; i < w; ++i) taps[tid * w + i] = horner_f32(coef + i * (deg + 1), deg, v);
         float sn, cs;
-        f32_sincos_prod(B.wc, rj - B.rc, &sn, &cs);
-        const float ratio = (float)(B.rho / rj);
-        const float w0 = (float)c_s[j] * sqrtf(ratio);
+        f32_sincos_prod(B.wc, xd, &sn, &cs);
+        const float ratio = B.rho_h / r2[j].x;
+        const float w0 = c2[j].x * sqrtf(ratio);
         float wr = w0 * cs, wi = w0 * sn;
         for (int q = 0; q < Q; ++q) {
             aval[tid * Q + q] = make_float2(wr, wi);
@@ -1346,8 +1343,8 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
 // FP32 spreading (coordinates and phase reduction in FP64).
 __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ tiles, Tables tab,
-                                 const double* __restrict__ r_s, const double* __restrict__ c_s,
-                                 double2* __restrict__ grid_b)
+                                 const double* __restrict__ r_s, const float2* __restrict__ r2,
+                                 const float2* __restrict__ c2, double2* __restrict__ grid_b)
 {
     extern __shared__ float2 smf[];
     __shared__ int use_mom;
@@ -1356,17 +1353,17 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     const int Q = probs[B.prob].Q;
     if (t.count <= 0) return;
     if (threadIdx.x == 0) {
-        double v;
-        const int lfirst = spread_cell(B, tab, r_s[t.start], &v);
-        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &v) - lfirst + 1;
+        double x, v;
+        const int lfirst = spread_cell(B, tab, r_s[t.start], &x, &v);
+        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &x, &v) - lfirst + 1;
         use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
     }
     __syncthreads();
     double2* gb = grid_b + B.b_off;
     if (use_mom)
-        spread_moments_f32(B, Q, t, tab, r_s, c_s, gb, (float*)smf);
+        spread_moments_f32(B, Q, t, tab, r_s, r2, c2, gb, (float*)smf);
     else
-        spread_taps_f32(B, Q, t, tab, r_s, c_s, gb, smf);
+        spread_taps_f32(B, Q, t, tab, r_s, r2, c2, gb, smf);
 }
 
 // Shared memory (bytes) of k_asy_interp_f32 for 2M = qmax.
@@ -1382,7 +1379,8 @@ __host__ __device__ __forceinline__ size_t interp_f32_smem(int qmax, int w, int 
 // k_asy_interp, sparse tiles by taps.
 __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
-    Tables tab, const double* __restrict__ w_s, const float4* __restrict__ grid_q, double* __restrict__ g_s)
+    Tables tab, const double* __restrict__ w_s, const float2* __restrict__ w2, const float4* __restrict__ grid_q,
+    double* __restrict__ g_s)
 {
     extern __shared__ float4 winf[];
     const Tile t = tiles[blockIdx.x];
@@ -1400,9 +1398,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
     const double wk = w_s[k];
     const double s = wk - B.wc;
-    const double a = s * B.h * B.inv_delta - tab.half_w;
+    const double a = s * B.hd - tab.half_w;
     const double tf = ceil(a);
-    const float v = 2.f * fminf(fmaxf((float)(tf - a), 0.f), 1.f) - 1.f;
+    const float v = (float)fma(2.0, tf - a, -1.0);   // tf - a in [0, 1]
     const int t0 = (int)tf;
     if (valid) t0s[threadIdx.x] = t0;
     __syncthreads();
@@ -1458,7 +1456,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
         for (int i = 0; i < w; ++i) u[i] = horner_f32(coef2 + i * (deg + 1), deg, v);
     }
     const float* Hb = H + (t0 - wstart) * hs;
-    const float m1 = (float)(1.0 / (wk * B.rho));
+    const float m1 = 1.f / (w2[k].x * B.rho_h);
     float tr = 0.f, ti = 0.f, mq = 1.f;
     for (int q = 0; q < Q; ++q) {
         float pr = 0.f, pi = 0.f;
@@ -1531,8 +1529,8 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
 }
 
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                                  const double* c_s, double2* grid_b, cudaStream_t s)
+                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
+                                  const float2* c2, double2* grid_b, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float2) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
@@ -1541,27 +1539,27 @@ cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks,
     if (smem_mom > smem) smem = smem_mom;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
+    k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, r2, c2, grid_b);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
-                                  double* g_s, cudaStream_t s)
+                                  int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                                  const float4* grid_q, double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     const size_t smem = interp_f32_smem(qmax, tab.w, tab.deg);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp_f32<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
+    k_asy_interp_f32<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                              const double* c_s, double2* grid_b, cudaStream_t s)
+                              int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
+                              const float2* c2, double2* grid_b, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
@@ -1570,7 +1568,7 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     if (smem_mom > smem) smem = smem_mom;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, c_s, grid_b);
+    k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, r2, c2, grid_b);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1628,14 +1626,14 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
 }
 
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
-                              double* g_s, cudaStream_t s)
+                              int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                              const float4* grid_q, double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     const size_t smem = interp_smem(qmax, tab.w, tab.deg);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, grid_q, g_s);
+    k_asy_interp<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -175,11 +175,28 @@ __global__ void k_sort_finish(const uint64_t* __restrict__ keys, int64_t n, doub
 }
 
 __global__ void k_gather(const double* __restrict__ c, const int32_t* __restrict__ perm, int64_t n,
-                         int stride, int comp, double* __restrict__ out)
+                         int stride, int comp, double* __restrict__ out, float2* __restrict__ out2)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = c[(int64_t)perm[i] * stride + comp];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = c[(int64_t)perm[i] * stride + comp];
+        out[i] = v;
+        if (out2) {
+            const float h = (float)v;
+            out2[i] = make_float2(h, (float)(v - (double)h));
+        }
+    }
+}
+
+// x as double-float pairs (hi = nearest float, lo = nearest float to the rest)
+__global__ void k_split_f64(const double* __restrict__ x, int64_t n, float2* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const float h = (float)v;
+        out[i] = make_float2(h, (float)(v - (double)h));
+    }
 }
 
 __global__ void k_scatter(const double* __restrict__ gs, const int32_t* __restrict__ perm, int64_t m,
@@ -380,10 +397,18 @@ cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg
 }
 
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
-                          double* out, cudaStream_t s)
+                          double* out, float2* out2, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, out);
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, out, out2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_split_f64<<<grid_for(n, 256), 256, 0, s>>>(x, n, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -62,6 +62,8 @@ struct AsyBlock {
     double alpha;      // w h / 2: outer deconvolution argument scale
     double alpha2;     // w Delta / 2 with Delta = 2 pi / nf2
     double inv_delta;  // nf2 / (2 pi)
+    double hd;         // h * inv_delta: a frequency offset s sits at FFT-grid position s * hd
+    float rho_h, rho_l;   // rho as double-float
 };
 
 struct DirectBlock {
@@ -134,7 +136,7 @@ cudaError_t launch_block_bounds(const SubBlk* loc, int64_t nl, const SubBlk* asy
 cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
                                   int nprob, int32_t* s_out, cudaStream_t s);
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
-                          double* out, cudaStream_t s);
+                          double* out, float2* out2, cudaStream_t s);
 cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg, int total, Tile* out,
                                 cudaStream_t s);
 cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
@@ -160,9 +162,11 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
                               int max_area, int lowp, const double* r_s, const double* w_s, const double* g_s,
                               double* c_s, cudaStream_t s);
+// x[i] as double-float (hi, lo)
+cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream_t s);
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                              const double* c_s, double2* grid_b, cudaStream_t s);
+                              int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
+                              const float2* c2, double2* grid_b, cudaStream_t s);
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
                                   double2* tgrid, cudaStream_t s);
@@ -170,11 +174,11 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
                                   int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
                                   double* c_s, cudaStream_t s);
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                                  const double* c_s, double2* grid_b, cudaStream_t s);
+                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
+                                  const float2* c2, double2* grid_b, cudaStream_t s);
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
-                                  double* g_s, cudaStream_t s);
+                                  int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                                  const float4* grid_q, double* g_s, cudaStream_t s);
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* src,
                                  float4* dst, cudaStream_t s, bool adj = false);
@@ -186,7 +190,7 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
                                  const double2* src, double2* tmp, float4* dst,
                                  cudaStream_t s, bool adj = false);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, Tables tab, const double* w_s, const float4* grid_q,
-                              double* g_s, cudaStream_t s);
+                              int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                              const float4* grid_q, double* g_s, cudaStream_t s);
 
 }  // namespace nuht

@@ -91,6 +91,7 @@ struct nuht_plan_s {
     double2* d_tg = nullptr;  // adjoint: frequencies spread onto the FFT grid
     float4* d_bq = nullptr;   // adjoint: corrected modes, double-float parts
     double *d_cs = nullptr, *d_gs = nullptr;
+    float2 *d_r2 = nullptr, *d_w2 = nullptr, *d_cs2 = nullptr;   // double-float copies
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
 
@@ -552,6 +553,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         ab.alpha = 0.5 * P->w * ab.h;
         ab.alpha2 = P->w * M_PI / ab.nf2;
         ab.inv_delta = ab.nf2 / (2.0 * M_PI);
+        ab.hd = ab.h * ab.inv_delta;
+        ab.rho_h = (float)ab.rho;
+        ab.rho_l = (float)(ab.rho - (double)ab.rho_h);
         ab.b_off = gb_off;
         gb_off += nf1 * Q;
         ab.q_off = gq_off;
@@ -621,6 +625,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
     size_t a_gt = A.reserve<double2>(P->has_large_fft ? (size_t)P->gq_len : 1);
     size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
+    size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m), a_cs2 = A.reserve<float2>(n);
     size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
@@ -673,6 +678,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_mom = (double*)(D + a_mom);
     P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (double2*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
+    P->d_r2 = (float2*)(D + a_r2); P->d_w2 = (float2*)(D + a_w2); P->d_cs2 = (float2*)(D + a_cs2);
+    NUHT_CK(launch_split_f64(P->d_r, n, P->d_r2, s));
+    NUHT_CK(launch_split_f64(P->d_w, m, P->d_w2, s));
     P->d_tg = (double2*)(D + a_tg); P->d_bq = (float4*)(D + a_bq);
     Tables& tb = P->tab;
     tb.es = P->d_es; tb.es2 = (const float2*)(D + a_es2);
@@ -898,10 +906,10 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax,
-                                          P->spread_threads, P->tab, P->d_r, P->d_cs, P->d_gb, s));
+                                          P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, s));
         else
             NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax,
-                                      P->spread_threads, P->tab, P->d_r, P->d_cs, P->d_gb, s));
+                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_gb,
@@ -915,10 +923,10 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                          P->d_w, P->d_gq, P->d_gs, s));
+                                          P->d_w, P->d_w2, P->d_gq, P->d_gs, s));
         else
             NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                      P->d_w, P->d_gq, P->d_gs, s));
+                                      P->d_w, P->d_w2, P->d_gq, P->d_gs, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
     }
     return NUHT_OK;
@@ -940,7 +948,7 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         StageTimer T{P, comp};
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
         NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * P->m, s));
-        NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, s));
+        NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, P->d_cs2, s));
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_forward(P, T, s));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
@@ -1013,7 +1021,7 @@ int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_com
         StageTimer T{P, comp};
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
         NUHT_CK(cudaMemsetAsync(P->d_cs, 0, sizeof(double) * P->n, s));
-        NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_gs, s));
+        NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_gs, nullptr, s));
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_adjoint(P, T, s));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
