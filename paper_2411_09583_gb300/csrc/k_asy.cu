@@ -141,7 +141,7 @@ __device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
 // x 4 values per thread, the point range split over 8 lanes); degrees >=
 // tab.dcs, whose coefficients are tiny, accumulate in plain FP32, the rest
 // in double-float.
-__device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
+__device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, const Tables& tab,
                                const double* __restrict__ r_s, const float2* __restrict__ r2,
                                const float2* __restrict__ c2, double2* __restrict__ gb, float2* sm)
 {
@@ -214,6 +214,8 @@ __device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Ta
     const int nf1 = 2 * B.N1 + 1;
     const int npairs = L.ndf + L.nf;
     const int nitems = npairs * nq * kSpreadSub;
+    const int nqA = min(nq, (qs + 1) >> 1);        // quads holding a term q < qs
+    const int nA = L.ndf * nqA, nB = L.ndf * (nq - nqA);
     const int nitems_pad = (nitems + 31) & ~31;
     for (int b = 0; b < nbins; ++b) {
         const int p0 = bstart[b], p1 = bstart[b + 1];
@@ -222,14 +224,43 @@ __device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Ta
             const bool live = it < nitems;
             const int sub = it & (kSpreadSub - 1);
             const int o = live ? it / kSpreadSub : 0;
-            const int dp = o / nq, qq = o - dp * nq;
-            const bool lowp = dp >= L.ndf;
+            // outputs (degree pair dp, value quad qq) ordered by cost so that warps
+            // are uniform: double-float degrees with a quad holding a term q < qs,
+            // then double-float degrees with quads of small terms, then FP32 degrees
+            int dp, qq;
+            if (o < nA) {
+                dp = o / nqA;
+                qq = o - dp * nqA;
+            } else if (o < nA + nB) {
+                const int ob = o - nA;
+                dp = ob / (nq - nqA);
+                qq = nqA + (ob - dp * (nq - nqA));
+            } else {
+                const int ob = o - nA - nB;
+                dp = L.ndf + ob / nq;
+                qq = ob - (dp - L.ndf) * nq;
+            }
+            const bool lowd = dp >= L.ndf;       // FP32-tier degrees
+            const bool lowq = o >= nA && !lowd;  // double-float degrees, small Hankel terms only
             acc2 A[2][4];
 #pragma unroll
             for (int e = 0; e < 2; ++e)
 #pragma unroll
                 for (int f = 0; f < 4; ++f) A[e][f] = acc2{0.f, 0.f};
-            if (live && !lowp) {
+            if (live && !lowd && lowq) {
+                const float2* up = Ud + 2 * dp;
+                for (int p = p0 + sub; p < p1; p += kSpreadSub) {
+                    const float4 uu = *(const float4*)(up + p * L.sud);
+                    const float4 xa = *(const float4*)(X + p * L.sx + 4 * qq);
+                    const float4 xb = *(const float4*)(X + p * L.sx + 4 * qq + 2);
+                    const float xs[4] = {xa.x, xa.z, xb.x, xb.z};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        A[0][f].s = fmaf(uu.x, xs[f], A[0][f].s);
+                        A[1][f].s = fmaf(uu.z, xs[f], A[1][f].s);
+                    }
+                }
+            } else if (live && !lowd) {
                 const float2* up = Ud + 2 * dp;
                 for (int p = p0 + sub; p < p1; p += kSpreadSub) {
                     const float4 uu = *(const float4*)(up + p * L.sud);
@@ -286,12 +317,15 @@ __device__ void spread_moments(const AsyBlock& B, int Q, const Tile& t, const Ta
             if (idx < 0 || idx >= nf1) continue;
             acc2 s{0.f, 0.f};
             const float2* ar = Ach + i * L.dpad;
-            for (int e = 0; e < 2 * L.ndf; ++e) {
-                const float2 a2 = ar[e], m2 = Mb[e * Q2 + qv];
-                acc_fma(s, df{a2.x, a2.y}, df{m2.x, m2.y});
-            }
             float sf = 0.f;
-            for (int e = 2 * L.ndf; e < L.dpad; ++e) sf = fmaf(ar[e].x, Mb[e * Q2 + qv].x, sf);
+            int e = 0;
+            if ((qv >> 1) < qs) {
+                for (; e < 2 * L.ndf; ++e) {
+                    const float2 a2 = ar[e], m2 = Mb[e * Q2 + qv];
+                    acc_fma(s, df{a2.x, a2.y}, df{m2.x, m2.y});
+                }
+            }
+            for (; e < L.dpad; ++e) sf = fmaf(ar[e].x, Mb[e * Q2 + qv].x, sf);
             const double val = acc_value(s) + (double)sf;
             if (val != 0.0) {
                 double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
@@ -429,7 +463,7 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     __syncthreads();
     double2* gb = grid_b + B.b_off;
     if (use_mom)
-        spread_moments(B, Q, t, tab, r_s, r2, c2, gb, (float2*)smem4);
+        spread_moments(B, Q, probs[B.prob].qs, t, tab, r_s, r2, c2, gb, (float2*)smem4);
     else
         spread_taps(B, Q, t, tab, r_s, r2, c2, gb, smem4);
 }
