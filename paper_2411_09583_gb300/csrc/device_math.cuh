@@ -1,4 +1,4 @@
-// Device helpers: phase reduction, Bessel recurrences and Hankel's expansion.
+// Device helpers: Bessel recurrences and series (FP64, FP32), FP32 Hankel expansion.
 #pragma once
 
 #include <cstdint>
@@ -6,23 +6,6 @@
 #include "nuht_internal.h"
 
 namespace nuht {
-
-// sin and cos of the exact product a*b.  The product is split into
-// hi + lo (FMA two-product), hi is reduced modulo 2 pi against a two-term
-// 2 pi, and the small remainder goes to sincos().  Arguments up to ~1e9 keep
-// an absolute phase error near 1e-16.
-__device__ __forceinline__ void sincos_prod(double a, double b, double* s, double* c)
-{
-    const double kTwoPiHi = 6.283185307179586;        // nearest double to 2 pi
-    const double kTwoPiLo = 2.4492935982947064e-16;   // 2 pi - kTwoPiHi
-    const double kInvTwoPi = 0.15915494309189535;
-    double p = a * b;
-    double e = fma(a, b, -p);
-    double k = rint(p * kInvTwoPi);
-    double t = fma(-k, kTwoPiHi, p);
-    t = fma(-k, kTwoPiLo, t) + e;
-    sincos(t, s, c);
-}
 
 // True when |v| > 2^498 (~1e150): checked on the high word with integer ops.
 __device__ __forceinline__ bool too_big(double v)
@@ -89,27 +72,6 @@ __device__ __forceinline__ double jn_small_arg(int n, double x)
     return jn_miller(n, x);
 }
 
-// Hankel's expansion with M pairs of terms (Sec. 3.2) at x = w * r (exact
-// product), accurate to eps for x > z by the choice of z (Sec. 3.3).
-__device__ __forceinline__ double jn_hankel(const ProbParams& P, double w, double r)
-{
-    double x = w * r;
-    double y = 1.0 / x;
-    double y2 = y * y;
-    // P(x) = sum_l (-1)^l a_2l y^2l, Q(x) = sum_l (-1)^l a_{2l+1} y^{2l+1} (Horner in y^2)
-    double p = 0.0, q = 0.0;
-    for (int l = P.M - 1; l >= 0; --l) {
-        double sg = (l & 1) ? -1.0 : 1.0;
-        p = fma(p, y2, sg * P.a[2 * l]);
-        q = fma(q, y2, sg * P.a[2 * l + 1]);
-    }
-    q *= y;
-    double sx, cx;
-    sincos_prod(w, r, &sx, &cx);
-    double cchi = cx * P.cphi - sx * P.sphi;   // cos(x + phi)
-    double schi = sx * P.cphi + cx * P.sphi;   // sin(x + phi)
-    return sqrt(0.6366197723675814 * y) * (p * cchi - q * schi);
-}
 
 // ---------------------------------------------------------- FP32 variants
 // (for tolerances eps >= 1e-6, where FP32 evaluation error stays far below eps)

@@ -39,24 +39,6 @@ namespace {
 constexpr int kWinCells = 64;   // grid cells an interpolation tile stages in shared memory
 constexpr int kInterpTileThreads = 128;   // frequencies per interpolation tile (host: kInterpTile)
 
-__device__ __forceinline__ double horner(const double* c, int deg, double v)
-{
-    double acc = c[deg];
-    for (int k = deg - 1; k >= 0; --k) acc = fma(acc, v, c[k]);
-    return acc;
-}
-
-// psi^(xi) from the piecewise-polynomial table (xi >= 0 within the table).
-__device__ __forceinline__ double psihat(const Tables& T, double xi)
-{
-    xi = fabs(xi);
-    double t = xi * T.ph_scale;
-    int piece = (int)t;
-    if (piece > T.ph_pieces - 1) piece = T.ph_pieces - 1;
-    double v = 2.0 * (t - (double)piece) - 1.0;
-    return horner(T.ph + piece * (T.ph_deg + 1), T.ph_deg, v);
-}
-
 // psi^(xi) in double-float from the split table (compensated Horner); xi >= 0.
 __device__ __forceinline__ df psihat_df(const Tables& T, double xi)
 {
@@ -469,32 +451,41 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
 }
 
 // -------------------------------------------------------------------- FFT
-// In-place radix-2 FFT (e^{+2 pi i k n / N}) of N = 2^logN complex values in
-// shared memory that were stored in bit-reversed order.  tw[k] =
-// e^{2 pi i k / 2^tw_log2}.
-__device__ void smem_fft(double2* X, int logN, const double2* __restrict__ tw, int tw_log2)
+// Complex double-float values are float4 (re.h, re.l, im.h, im.l); the FFTs
+// run in double-float on the FP32 pipes (FP64 is 1/64 of the FP32 rate).
+__device__ __forceinline__ float4 cdf(df re, df im) { return make_float4(re.h, re.l, im.h, im.l); }
+
+__device__ __forceinline__ float4 cdf_mul(float4 a, float4 b)
 {
-    const int N = 1 << logN;
-    for (int s = 0; s < logN; ++s) {
-        const int len = 1 << s;
-        const int tw_shift = tw_log2 - (s + 1);
-        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const int pos = b & (len - 1);
-            const int i0 = ((b >> s) << (s + 1)) + pos;
-            const int i1 = i0 + len;
-            const double2 wv = tw[pos << tw_shift];
-            const double2 u = X[i0], v = X[i1];
-            const double2 vw = make_double2(v.x * wv.x - v.y * wv.y, v.x * wv.y + v.y * wv.x);
-            X[i0] = make_double2(u.x + vw.x, u.y + vw.y);
-            X[i1] = make_double2(u.x - vw.x, u.y - vw.y);
-        }
-        __syncthreads();
-    }
+    const df ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+    return cdf(df_add(df_mul(ar, br), df_negate(df_mul(ai, bi))), df_add(df_mul(ar, bi), df_mul(ai, br)));
 }
 
-// nlines independent FFTs of N = 2^logN points stored one after the other
-// (each bit-reversed), sharing every butterfly stage.
-__device__ void smem_fft_lines(double2* X, int logN, int nlines, const double2* __restrict__ tw, int tw_log2)
+__device__ __forceinline__ float4 cdf_scale(float4 a, df s)
+{
+    return cdf(df_mul(df{a.x, a.y}, s), df_mul(df{a.z, a.w}, s));
+}
+
+// u + v w and u - v w
+__device__ __forceinline__ void cdf_butterfly(float4& u, float4& v, float4 w)
+{
+    const float4 vw = cdf_mul(v, w);
+    const df ur{u.x, u.y}, ui{u.z, u.w}, vr{vw.x, vw.y}, vi{vw.z, vw.w};
+    u = cdf(df_add(ur, vr), df_add(ui, vi));
+    v = cdf(df_add(ur, df_negate(vr)), df_add(ui, df_negate(vi)));
+}
+
+// FP64 complex as double-float
+__device__ __forceinline__ float4 cdf_from(double2 v)
+{
+    const df re = df_from(v.x), im = df_from(v.y);
+    return cdf(re, im);
+}
+
+// nlines independent FFTs (e^{+2 pi i k n / N}) of N = 2^logN points stored
+// one after the other in shared memory, each in bit-reversed order, sharing
+// every butterfly stage.  tw2[k] = e^{2 pi i k / 2^tw_log2} as double-float.
+__device__ void smem_fft_lines(float4* X, int logN, int nlines, const float4* __restrict__ tw2, int tw_log2)
 {
     const int N = 1 << logN, half = N >> 1;
     for (int st = 0; st < logN; ++st) {
@@ -506,14 +497,40 @@ __device__ void smem_fft_lines(double2* X, int logN, int nlines, const double2* 
             const int pos = bb & (len - 1);
             const int i0 = line * N + ((bb >> st) << (st + 1)) + pos;
             const int i1 = i0 + len;
-            const double2 wv = tw[pos << tw_shift];
-            const double2 u = X[i0], v = X[i1];
-            const double2 vw = make_double2(v.x * wv.x - v.y * wv.y, v.x * wv.y + v.y * wv.x);
-            X[i0] = make_double2(u.x + vw.x, u.y + vw.y);
-            X[i1] = make_double2(u.x - vw.x, u.y - vw.y);
+            float4 u = X[i0], v = X[i1];
+            cdf_butterfly(u, v, tw2[pos << tw_shift]);
+            X[i0] = u;
+            X[i1] = v;
         }
         __syncthreads();
     }
+}
+
+// e^{2 pi i m / N} for 0 <= m < N = 2^logN as double-float: the table entry for
+// the top bits of m / N times the rotation by the rest, an angle below
+// 2 pi / 2^tw_log2, from its Taylor series (five terms, truncation < 1e-19).
+__device__ __forceinline__ float4 cdf_twiddle(const Tables& tab, int logN, long long m)
+{
+    const int sh = logN - tab.tw_log2;
+    const int hi = sh > 0 ? (int)(m >> sh) : (int)(m << -sh);   // table index, < 2^tw_log2
+    const int half = 1 << (tab.tw_log2 - 1);
+    float4 t = tab.tw2[hi & (half - 1)];
+    if (hi >= half) t = make_float4(-t.x, -t.y, -t.z, -t.w);
+    const int lo = sh > 0 ? (int)(m & ((1LL << sh) - 1)) : 0;
+    if (lo == 0) return t;
+    // angle 2 pi lo / N: lo / N is exact in FP32 (lo < 2^sh <= 2^11, N a power of two)
+    const df twopi{6.2831854820251465f, -1.7484555314695172e-07f};
+    const df a = df_mul(twopi, df{ldexpf((float)lo, -logN), 0.f});
+    const df a2 = df_mul(a, a);
+    // sin a = a (1 - a^2/6 (1 - a^2/20 (1 - a^2/42))), cos a = 1 - a^2/2 (1 - a^2/12 (1 - a^2/30))
+    df sn = df_add(df{1.f, 0.f}, df_negate(df_mul(a2, df{1.f / 42.f, 0.f})));
+    sn = df_add(df{1.f, 0.f}, df_negate(df_mul(df_mul(a2, df{0.05f, -7.450580707946131e-10f}), sn)));
+    sn = df_add(df{1.f, 0.f}, df_negate(df_mul(df_mul(a2, df{0.1666666716337204f, -4.967053879312289e-09f}), sn)));
+    sn = df_mul(a, sn);
+    df cs = df_add(df{1.f, 0.f}, df_negate(df_mul(a2, df{0.03333333507180214f, -1.7384682293e-09f})));
+    cs = df_add(df{1.f, 0.f}, df_negate(df_mul(df_mul(a2, df{0.0833333358168602f, -2.4835269e-09f}), cs)));
+    cs = df_add(df{1.f, 0.f}, df_negate(df_mul(df_mul(a2, df{0.5f, 0.f}), cs)));
+    return cdf_mul(t, cdf(cs, sn));
 }
 
 // Split of a two-pass FFT of 2^LN points into lines: N2 = 2^ceil(LN/2)
@@ -536,52 +553,39 @@ __host__ __device__ __forceinline__ FourStep four_step(int LN)
     return f;
 }
 
-// Spread-grid value at FFT index t (mode l = t or t - nf2), corrected by
-// 1/psi^(alpha2 l); zero outside |l| <= N1.
-__device__ __forceinline__ double2 corrected_mode(const AsyBlock& B, const Tables& tab,
-                                                  const double2* __restrict__ gb, int Q, int q, int tt)
+// 1 / psi^(alpha2 l): the correction of mode l of the inner FFT.
+__device__ __forceinline__ df mode_correction(const AsyBlock& B, const Tables& tab, int l)
 {
-    const int l = (tt < (B.nf2 >> 1)) ? tt : tt - B.nf2;
-    if (l < -B.N1 || l > B.N1) return make_double2(0.0, 0.0);
-    const double2 v = gb[(int64_t)(l + B.N1) * Q + q];
-    const double s = 1.0 / psihat(tab, B.alpha2 * (double)l);
-    return make_double2(v.x * s, v.y * s);
-}
-
-// Complex FP64 value stored as double-float parts (re.h, re.l, im.h, im.l).
-__device__ __forceinline__ float4 split4(double2 v)
-{
-    const float rh = (float)v.x, ih = (float)v.y;
-    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    return df_recip(psihat_df(tab, B.alpha2 * (double)l));
 }
 
 // FFT input / output of the forward (ADJ = false) and the transposed
 // (ADJ = true) type-3 pipelines.  Forward: modes l (|l| <= N1) of the spread
 // grid src (at b_off), corrected by 1/psi^(alpha2 l), transformed to every t
-// and stored split at dst + q_off.  Transposed: the target grid src (at q_off,
+// and stored at dst + q_off.  Transposed: the target grid src (at q_off,
 // every t) is transformed (the DFT matrix e^{2 pi i l t / nf2} is symmetric),
-// and only the modes |l| <= N1 are kept, corrected, and stored split at
-// dst + b_off.
+// and only the modes |l| <= N1 are kept, corrected, and stored at dst + b_off.
 template <bool ADJ>
-__device__ __forceinline__ double2 fft_in(const AsyBlock& B, const Tables& tab, const double2* __restrict__ src,
-                                          int Q, int q, int tt)
+__device__ __forceinline__ float4 fft_in(const AsyBlock& B, const Tables& tab, const double2* __restrict__ src,
+                                         int Q, int q, int tt)
 {
-    if (ADJ) return src[B.q_off + (int64_t)tt * Q + q];
-    return corrected_mode(B, tab, src + B.b_off, Q, q, tt);
+    if (ADJ) return cdf_from(src[B.q_off + (int64_t)tt * Q + q]);
+    const int l = (tt < (B.nf2 >> 1)) ? tt : tt - B.nf2;
+    if (l < -B.N1 || l > B.N1) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return cdf_scale(cdf_from(src[B.b_off + (int64_t)(l + B.N1) * Q + q]), mode_correction(B, tab, l));
 }
 
 template <bool ADJ>
 __device__ __forceinline__ void fft_out(const AsyBlock& B, const Tables& tab, float4* __restrict__ dst, int Q,
-                                        int q, int tt, double2 v)
+                                        int q, int tt, float4 v)
 {
     if (!ADJ) {
-        dst[B.q_off + (int64_t)tt * Q + q] = split4(v);
+        dst[B.q_off + (int64_t)tt * Q + q] = v;
         return;
     }
     const int l = (tt < (B.nf2 >> 1)) ? tt : tt - B.nf2;
     if (l < -B.N1 || l > B.N1) return;
-    const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
-    dst[B.b_off + (int64_t)(l + B.N1) * Q + q] = split4(make_double2(v.x * sc, v.y * sc));
+    dst[B.b_off + (int64_t)(l + B.N1) * Q + q] = cdf_scale(v, mode_correction(B, tab, l));
 }
 
 template <bool ADJ>
@@ -589,17 +593,17 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
                                 const Tile* __restrict__ items, Tables tab,
                                 const double2* __restrict__ src, float4* __restrict__ dst)
 {
-    extern __shared__ double2 X[];
+    extern __shared__ float4 Xs[];
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
     const int q = (int)it.start;
     const int N = B.nf2, logN = B.log2nf2;
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x)
-        X[__brev(tt) >> (32 - logN)] = fft_in<ADJ>(B, tab, src, Q, q, tt);
+        Xs[__brev(tt) >> (32 - logN)] = fft_in<ADJ>(B, tab, src, Q, q, tt);
     __syncthreads();
-    smem_fft(X, logN, tab.tw, tab.tw_log2);
-    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, q, tt, X[tt]);
+    smem_fft_lines(Xs, logN, 1, tab.tw2, tab.tw_log2);
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, q, tt, Xs[tt]);
 }
 
 // All Q grids of one small block (nf2 * Q <= kFftSmemMax) in one CTA: the
@@ -610,7 +614,7 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
                                 const Tile* __restrict__ items, Tables tab,
                                 const double2* __restrict__ src, float4* __restrict__ dst)
 {
-    extern __shared__ double2 X[];   // [Q][N], each grid bit-reversed
+    extern __shared__ float4 Xs[];   // [Q][N], each grid bit-reversed
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
@@ -620,51 +624,30 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
         const int dst_i = __brev(tt) >> (32 - logN);
         if (ADJ) {
             const double2* row = src + B.q_off + (int64_t)tt * Q;
-            for (int q = 0; q < Q; ++q) X[q * N + dst_i] = row[q];
+            for (int q = 0; q < Q; ++q) Xs[q * N + dst_i] = cdf_from(row[q]);
         } else if (l < -B.N1 || l > B.N1) {
-            for (int q = 0; q < Q; ++q) X[q * N + dst_i] = make_double2(0.0, 0.0);
+            for (int q = 0; q < Q; ++q) Xs[q * N + dst_i] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
-            const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
+            const df sc = mode_correction(B, tab, l);
             const double2* row = src + B.b_off + (int64_t)(l + B.N1) * Q;
-            for (int q = 0; q < Q; ++q) {
-                const double2 v = row[q];
-                X[q * N + dst_i] = make_double2(v.x * sc, v.y * sc);
-            }
+            for (int q = 0; q < Q; ++q) Xs[q * N + dst_i] = cdf_scale(cdf_from(row[q]), sc);
         }
     }
     __syncthreads();
-    for (int st = 0; st < logN; ++st) {
-        const int len = 1 << st;
-        const int tw_shift = tab.tw_log2 - (st + 1);
-        for (int b = threadIdx.x; b < Q * half; b += blockDim.x) {
-            const int q = b >> (logN - 1);
-            const int bb = b & (half - 1);
-            const int pos = bb & (len - 1);
-            const int i0 = q * N + ((bb >> st) << (st + 1)) + pos;
-            const int i1 = i0 + len;
-            const double2 wv = tab.tw[pos << tw_shift];
-            const double2 u = X[i0], v = X[i1];
-            const double2 vw = make_double2(v.x * wv.x - v.y * wv.y, v.x * wv.y + v.y * wv.x);
-            X[i0] = make_double2(u.x + vw.x, u.y + vw.y);
-            X[i1] = make_double2(u.x - vw.x, u.y - vw.y);
-        }
-        __syncthreads();
-    }
+    smem_fft_lines(Xs, logN, Q, tab.tw2, tab.tw_log2);
     if (!ADJ) {
         float4* gq = dst + B.q_off;
         for (int idx = threadIdx.x; idx < N * Q; idx += blockDim.x) {
             const int tt = idx / Q, q = idx - tt * Q;
-            gq[idx] = split4(X[q * N + tt]);
+            gq[idx] = Xs[q * N + tt];
         }
     } else {
         const int nf1 = 2 * B.N1 + 1;
         float4* gb = dst + B.b_off;
-        for (int idx = threadIdx.x; idx < nf1 * Q; idx += blockDim.x) {
-            const int li = idx / Q, q = idx - li * Q;
+        for (int li = threadIdx.x; li < nf1; li += blockDim.x) {
             const int l = li - B.N1;
-            const double sc = 1.0 / psihat(tab, B.alpha2 * (double)l);
-            const double2 v = X[q * N + (l & (N - 1))];
-            gb[idx] = split4(make_double2(v.x * sc, v.y * sc));
+            const df sc = mode_correction(B, tab, l);
+            for (int q = 0; q < Q; ++q) gb[(int64_t)li * Q + q] = cdf_scale(Xs[q * N + (l & (N - 1))], sc);
         }
     }
 }
@@ -677,9 +660,9 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
 template <bool ADJ>
 __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
-                                 const double2* __restrict__ src, double2* __restrict__ tmp)
+                                 const double2* __restrict__ src, float4* __restrict__ tmp)
 {
-    extern __shared__ double2 X[];
+    extern __shared__ float4 Xs[];
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
@@ -691,29 +674,25 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
     const int nl = (f.N1 - l0) < f.lpcA ? (f.N1 - l0) : f.lpcA;
     for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
         const int li = idx >> f.logN2, n2 = idx & (f.N2 - 1);
-        X[li * f.N2 + (__brev(n2) >> (32 - f.logN2))] = fft_in<ADJ>(B, tab, src, Q, iq, (l0 + li) + f.N1 * n2);
+        Xs[li * f.N2 + (__brev(n2) >> (32 - f.logN2))] = fft_in<ADJ>(B, tab, src, Q, iq, (l0 + li) + f.N1 * n2);
     }
     __syncthreads();
-    smem_fft_lines(X, f.logN2, nl, tab.tw, tab.tw_log2);
-    double2* tq = tmp + B.q_off;
+    smem_fft_lines(Xs, f.logN2, nl, tab.tw2, tab.tw_log2);
+    float4* tq = tmp + B.q_off;
     for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
         const int li = idx >> f.logN2, k2 = idx & (f.N2 - 1);
         const int n1 = l0 + li;
-        double s, c;
-        // e^{2 pi i n1 k2 / N}: the argument (2 n1 k2 mod 2N) / N is exact in FP64
-        const long long num = (2LL * n1 * k2) % (2LL * N);
-        sincospi((double)num / (double)N, &s, &c);
-        const double2 v = X[idx];
-        tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = make_double2(v.x * c - v.y * s, v.x * s + v.y * c);
+        const long long m = ((long long)n1 * k2) & (N - 1);   // e^{2 pi i n1 k2 / N}
+        tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = cdf_mul(Xs[idx], cdf_twiddle(tab, B.log2nf2, m));
     }
 }
 
 template <bool ADJ>
 __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
-                                 const double2* __restrict__ tmp, float4* __restrict__ dst)
+                                 const float4* __restrict__ tmp, float4* __restrict__ dst)
 {
-    extern __shared__ double2 X[];
+    extern __shared__ float4 Xs[];
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
@@ -722,17 +701,17 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
     const int g = (int)(it.start - (int64_t)iq * f.groupsB);
     const int k20 = g * f.lpcB;
     const int nl = (f.N2 - k20) < f.lpcB ? (f.N2 - k20) : f.lpcB;
-    const double2* tq = tmp + B.q_off;
+    const float4* tq = tmp + B.q_off;
     for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
         const int li = idx >> f.logN1, n1 = idx & (f.N1 - 1);
-        X[li * f.N1 + (f.logN1 > 0 ? (__brev(n1) >> (32 - f.logN1)) : 0)] =
+        Xs[li * f.N1 + (f.logN1 > 0 ? (__brev(n1) >> (32 - f.logN1)) : 0)] =
             tq[(int64_t)(n1 + f.N1 * (k20 + li)) * Q + iq];
     }
     __syncthreads();
-    smem_fft_lines(X, f.logN1, nl, tab.tw, tab.tw_log2);
+    smem_fft_lines(Xs, f.logN1, nl, tab.tw2, tab.tw_log2);
     for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
         const int li = idx >> f.logN1, k1 = idx & (f.N1 - 1);
-        fft_out<ADJ>(B, tab, dst, Q, iq, (k20 + li) + f.N2 * k1, X[idx]);
+        fft_out<ADJ>(B, tab, dst, Q, iq, (k20 + li) + f.N2 * k1, Xs[idx]);
     }
 }
 
@@ -1612,7 +1591,7 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
                                  float4* dst, cudaStream_t s, bool adj)
 {
     if (nitems <= 0) return cudaSuccess;
-    size_t smem = sizeof(double2) * (size_t)max_nf2;
+    size_t smem = sizeof(float4) * (size_t)max_nf2;
     auto kern = adj ? k_asy_fft_small<true> : k_asy_fft_small<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1629,7 +1608,7 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
                                  cudaStream_t s, bool adj)
 {
     if (nitems <= 0) return cudaSuccess;
-    size_t smem = sizeof(double2) * (size_t)kFftSmemMax;
+    size_t smem = sizeof(float4) * (size_t)kFftSmemMax;
     auto kern = adj ? k_asy_fft_block<true> : k_asy_fft_block<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1640,11 +1619,11 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
 
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
-                                 const double2* src, double2* tmp, float4* dst,
+                                 const double2* src, float4* tmp, float4* dst,
                                  cudaStream_t s, bool adj)
 {
     if (nitems_a <= 0) return cudaSuccess;
-    size_t smem = sizeof(double2) * (size_t)kFftLineBatch;
+    size_t smem = sizeof(float4) * (size_t)kFftLineBatch;
     auto ka = adj ? k_asy_fft_pass_a<true> : k_asy_fft_pass_a<false>;
     auto kb = adj ? k_asy_fft_pass_b<true> : k_asy_fft_pass_b<false>;
     cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

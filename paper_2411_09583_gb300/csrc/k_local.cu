@@ -222,11 +222,39 @@ __device__ __forceinline__ double jn_miller_df(int n, double x)
     return df_to(res) / df_to(S);
 }
 
-// J_nu at the exact product w*r: asymptotic side (Hankel, FP64 phase
-// reduction) or local side (series; Miller in double-float, or FP32 when lowp).
+// Hankel's expansion (Sec. 3.2, M pairs) at the exact product x = w r in
+// double-float: the phase x mod pi/2 is reduced in FP64 (df_sincos_prod),
+// 1/x, the two series in 1/x^2 and the amplitude sqrt(2/(pi x)) in double-float.
+__device__ __forceinline__ double jn_hankel_df(const ProbParams& P, double w, double r)
+{
+    const double p = w * r;
+    const double e = fma(w, r, -p);
+    const float ph = (float)p;
+    const df x = fast_two_sum(ph, (float)(p - (double)ph) + (float)e);
+    const df y = df_recip(x);
+    const df y2 = df_mul(y, y);
+    df pp{0.f, 0.f}, qq{0.f, 0.f};
+    for (int l = P.M - 1; l >= 0; --l) {
+        const float2 a0 = P.a2[2 * l], a1 = P.a2[2 * l + 1];
+        const bool neg = l & 1;
+        pp = df_add(df_mul(pp, y2), neg ? df{-a0.x, -a0.y} : df{a0.x, a0.y});
+        qq = df_add(df_mul(qq, y2), neg ? df{-a1.x, -a1.y} : df{a1.x, a1.y});
+    }
+    qq = df_mul(qq, y);
+    df sx, cx;
+    df_sincos_prod(w, r, &sx, &cx);
+    const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
+    const df cchi = df_add(df_mul(cx, cph), df_negate(df_mul(sx, sph)));   // cos(x + phi)
+    const df schi = df_add(df_mul(sx, cph), df_mul(cx, sph));              // sin(x + phi)
+    const df amp = df_sqrt(df_mul(df{0.6366197466850281f, 2.5682552973194106e-08f}, y));   // sqrt(2 / (pi x))
+    return df_to(df_mul(amp, df_add(df_mul(pp, cchi), df_negate(df_mul(qq, schi)))));
+}
+
+// J_nu at the exact product w*r: asymptotic side (Hankel in double-float, or
+// FP32 when lowp) or local side (series; Miller in double-float, or FP32 when lowp).
 __device__ __forceinline__ double direct_entry(const ProbParams& P, double w, double r, bool asy, bool lowp)
 {
-    if (asy) return lowp ? (double)jn_hankel_f32(P, w, r) : jn_hankel(P, w, r);
+    if (asy) return lowp ? (double)jn_hankel_f32(P, w, r) : jn_hankel_df(P, w, r);
     const double x = w * r;
     if (x < 1.0) return jn_series(P.nu, x);
     return lowp ? (double)jn_miller_f32(P.nu, (float)x) : jn_miller_df(P.nu, x);

@@ -31,6 +31,7 @@ struct HostTables {
     std::vector<float2> ph2;    // the same split into (hi, lo) floats
     int tw_log2 = 0;
     std::vector<double2> tw;
+    std::vector<float4> tw2;    // the same as double-float (cos.h, cos.l, sin.h, sin.l)
 };
 const HostTables& kernel_tables(int w);
 

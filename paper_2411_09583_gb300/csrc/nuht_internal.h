@@ -110,6 +110,7 @@ struct Tables {
     double ph_scale;       // pieces per unit of xi
     double ph_xmax;        // table covers xi in [0, ph_xmax]
     const double2* tw;     // e^{2 pi i k / 2^tw_log2}, k < 2^(tw_log2 - 1)
+    const float4* tw2;     // the same as double-float (cos.h, cos.l, sin.h, sin.l)
     int tw_log2;
 };
 
@@ -187,7 +188,7 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
                                  cudaStream_t s, bool adj = false);
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
-                                 const double2* src, double2* tmp, float4* dst,
+                                 const double2* src, float4* tmp, float4* dst,
                                  cudaStream_t s, bool adj = false);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,

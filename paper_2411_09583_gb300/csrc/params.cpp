@@ -234,6 +234,11 @@ const HostTables& kernel_tables(int w)
         const double a = 2.0 * M_PI * k / (double)(1 << T.tw_log2);
         T.tw[k] = make_double2(std::cos(a), std::sin(a));
     }
+    T.tw2.resize(T.tw.size());
+    for (size_t k = 0; k < T.tw.size(); ++k) {
+        const float ch = (float)T.tw[k].x, sh = (float)T.tw[k].y;
+        T.tw2[k] = make_float4(ch, (float)(T.tw[k].x - (double)ch), sh, (float)(T.tw[k].y - (double)sh));
+    }
     return cache.emplace(w, std::move(T)).first->second;
 }
 

@@ -86,7 +86,8 @@ struct nuht_plan_s {
     Tile *d_fblock = nullptr, *d_fsmall = nullptr, *d_fa = nullptr, *d_fb = nullptr;
     DirectBlock* d_dir = nullptr;
     double* d_mom = nullptr;
-    double2 *d_gb = nullptr, *d_gtmp = nullptr;
+    double2* d_gb = nullptr;
+    float4* d_gtmp = nullptr;   // two-pass FFT intermediate (double-float)
     float4* d_gq = nullptr;   // FFT output, complex values as double-float parts
     double2* d_tg = nullptr;  // adjoint: frequencies spread onto the FFT grid
     float4* d_bq = nullptr;   // adjoint: corrected modes, double-float parts
@@ -607,7 +608,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_es = A.reserve<double>(T.es.size()), a_ph = A.reserve<double>(T.ph.size());
     size_t a_es2 = A.reserve<float2>(T.es2.size()), a_ph2 = A.reserve<float2>(T.ph2.size());
     size_t a_ch2 = A.reserve<float2>(T.ch2.size());
-    size_t a_tw = A.reserve<double2>(T.tw.size());
+    size_t a_tw = A.reserve<double2>(T.tw.size()), a_tw2 = A.reserve<float4>(T.tw2.size());
     constexpr int kLists = 8;
     SegList* lists[kLists] = {&smom, &seval, &sspread, &sinterp, &sfs, &sfa, &sfb, &sfk};
     size_t a_seg[kLists], a_pre[kLists];
@@ -623,7 +624,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_mom = A.reserve<double>((size_t)P->mom_len);
     size_t a_gb = A.reserve<double2>((size_t)P->gb_len);
     size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
-    size_t a_gt = A.reserve<double2>(P->has_large_fft ? (size_t)P->gq_len : 1);
+    size_t a_gt = A.reserve<float4>(P->has_large_fft ? (size_t)P->gq_len : 1);
     size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
     size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m), a_cs2 = A.reserve<float2>(n);
     size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
@@ -645,6 +646,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     put(a_ph, T.ph.data(), sizeof(double) * T.ph.size());
     put(a_ph2, T.ph2.data(), sizeof(float2) * T.ph2.size());
     put(a_tw, T.tw.data(), sizeof(double2) * T.tw.size());
+    put(a_tw2, T.tw2.data(), sizeof(float4) * T.tw2.size());
     for (int i = 0; i < kLists; ++i) {
         put(a_seg[i], lists[i]->segs.data(), sizeof(Seg) * lists[i]->segs.size());
         put(a_pre[i], lists[i]->prefix.data(), sizeof(int32_t) * lists[i]->prefix.size());
@@ -676,7 +678,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_dir = (DirectBlock*)(D + a_dir);
     P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
     P->d_mom = (double*)(D + a_mom);
-    P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (double2*)(D + a_gt);
+    P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (float4*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
     P->d_r2 = (float2*)(D + a_r2); P->d_w2 = (float2*)(D + a_w2); P->d_cs2 = (float2*)(D + a_cs2);
     NUHT_CK(launch_split_f64(P->d_r, n, P->d_r2, s));
@@ -734,6 +736,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     tb.interp_const = std::sqrt(2.0 / M_PI) * 4.0 / ((double)T.w * (double)T.w);
     tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
     tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
+    tb.tw2 = (const float4*)(D + a_tw2);
     // the staging buffer must outlive the copy
     NUHT_CK(cudaStreamSynchronize(s));
     P->plan_ms[3] = ms_since(clk);
