@@ -18,7 +18,8 @@ __device__ __forceinline__ bool too_big(double v)
 // for y <= 60, ntop <= 80, checked against an independent evaluator).
 __device__ __forceinline__ int miller_start(int ntop, double y)
 {
-    double a = y + 20.0 + 4.0 * sqrt(y);
+    const float yf = (float)y;
+    const float a = yf + 20.f + 4.f * sqrtf(yf);
     int ns = (int)a + 1;
     if (ns < ntop + 8) ns = ntop + 8;
     return ns + (ns & 1);

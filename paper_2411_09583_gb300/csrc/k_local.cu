@@ -50,8 +50,8 @@ __device__ __forceinline__ df df_imul(float fi, float ih, float il)
 // and added to the block's moments.
 __global__ void __launch_bounds__(kMomThreads)
 k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                const Tile* __restrict__ tiles, const double* __restrict__ r_s,
-                const double* __restrict__ c_s, double* __restrict__ mom)
+                const Tile* __restrict__ tiles, const float2* __restrict__ r2,
+                const float2* __restrict__ c2, double* __restrict__ mom)
 {
     extern __shared__ acc2 acc[];
     const Tile t = tiles[blockIdx.x];
@@ -60,15 +60,16 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
     const int odd = probs[B.prob].nu & 1;
     const int nt = blockDim.x, tid = threadIdx.x;
     for (int l = 0; l <= L; ++l) acc[l * nt + tid] = acc2{0.f, 0.f};
-    const double invR = B.R > 0.0 ? 1.0 / B.R : 0.0;
+    const df invR{B.iR_h, B.iR_l};
     for (int64_t j = t.start + tid; j < t.start + t.count; j += nt) {
-        const double y = r_s[j] * invR;
-        const df cj = df_from(c_s[j]);
-        const double u = fma(2.0 * y, y, -1.0);   // T_2(y)
-        const df u2 = df_from(2.0 * u);
+        const float2 rj = r2[j], cc = c2[j];
+        const df y = df_mul(df{rj.x, rj.y}, invR);                          // r_j / R in [0, 1]
+        const df cj{cc.x, cc.y};
+        const df u = df_add(df_mul(df{2.f * y.h, 2.f * y.l}, y), df{-1.f, 0.f});   // T_2(y)
+        const df u2{2.f * u.h, 2.f * u.l};
         // even: T_{2l}(y) = T_l(u); odd: T_{2l+1}(y) with T_1 = y, T_3 = y (2u - 1)
-        df t0 = odd ? df_from(y) : df{1.f, 0.f};
-        df t1 = odd ? df_from(y * (2.0 * u - 1.0)) : df_from(u);
+        df t0 = odd ? y : df{1.f, 0.f};
+        df t1 = odd ? df_mul(y, df_add(u2, df{-1.f, 0.f})) : u;
         acc_fma(acc[tid], cj, t0);
         if (L >= 1) acc_fma(acc[nt + tid], cj, t1);
         for (int l = 2; l <= L; ++l) {
@@ -93,10 +94,10 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
 // (double-float); returns the normalisation S = J_0 + 2 sum_k J_2k of the same
 // scale.  Miller's backward recurrence from ns (even), rescaled by 2^-60
 // whenever a value passes 2^60.  Needs y >= 1 (growth per step <= 2 ns / y).
-__device__ __forceinline__ df miller_store_df(double y, int ntop, int ns, float2* jb, int nt, int tid)
+__device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb, int nt, int tid)
 {
-    const double inv2y = 2.0 / y;
-    const float ih = (float)inv2y, il = (float)(inv2y - (double)ih);
+    const df iy = df_recip(y);
+    const float ih = 2.f * iy.h, il = 2.f * iy.l;   // 2 / y
     df jp1{0.f, 0.f}, jc{1.f, 0.f}, S{2.f, 0.f};
     if (ns <= ntop) jb[ns * nt + tid] = make_float2(jc.h, jc.l);
     for (int i = ns; i >= 2; i -= 2) {
@@ -143,7 +144,7 @@ __device__ __forceinline__ double series_store_fp64(double y, int ntop, float2* 
 // recurrence, kept (unnormalised) in this thread's column of shared memory,
 // then sum_l C_l mu_l divided by the square of the normalisation.
 __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                             const Tile* __restrict__ tiles, const double* __restrict__ w_s,
+                             const Tile* __restrict__ tiles, const float2* __restrict__ w2,
                              const double* __restrict__ mom, double* __restrict__ g_s)
 {
     extern __shared__ float2 sm2[];
@@ -162,22 +163,23 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
     __syncthreads();
     if (tid >= t.count) return;
     const int64_t k = t.start + tid;
-    const double x = w_s[k] * B.R;
-    const double y = 0.5 * x;
+    const float2 wk = w2[k];
+    const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});   // y = omega R / 2
     double val;
-    if (y < 1e-100) {
-        // J_n(y) = delta_n0 to far below rounding: only C_0 survives, and only for nu = 0
+    if (!(ydf.h > 0.f)) {
+        // y below the FP32 range: J_n(y) = delta_n0 to far below rounding, so
+        // only C_0 survives, and only for nu = 0
         val = (nu == 0) ? (double)mu[0].x + (double)mu[0].y : 0.0;
     } else {
         const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
         const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
         const int ntop = hp + L;
-        const int ns = miller_start(ntop, y);
+        const int ns = miller_start(ntop, (double)ydf.h);
         df S;
-        if (y >= 1.0) {
-            S = miller_store_df(y, ntop, ns, jb, nt, tid);
+        if (ydf.h >= 1.f) {
+            S = miller_store_df(ydf, ntop, ns, jb, nt, tid);
         } else {
-            S = df_from(series_store_fp64(y, ntop, jb, nt, tid));
+            S = df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
         }
         // scale by a power of two near 1/S so that products of two values stay in FP32 range
         const float p2 = exp2f(-(float)ilogbf(S.h));
@@ -192,8 +194,8 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
             const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
             acc_fma(sum, cl, df{mu[l].x, mu[l].y});
         }
-        const double Sd = df_to(S);
-        val = acc_value(sum) / (Sd * Sd);
+        const df iS = df_recip(S);
+        val = df_to(df_mul(df_mul(fast_two_sum(sum.s, sum.c), iS), iS));
     }
     atomicAdd(&g_s[k], (double)P.sgn * val);
 }
@@ -310,7 +312,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
 //   nu_l = sum_{k in block} g_k C_l(omega_k R)          (rows, Miller per row)
 // then c_j += sum_l T_{2l(+1)}(r_j / R) nu_l              (columns).
 __global__ void k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                                    const Tile* __restrict__ tiles, const double* __restrict__ w_s,
+                                    const Tile* __restrict__ tiles, const float2* __restrict__ w2,
                                     const double* __restrict__ g_s, double* __restrict__ mom)
 {
     extern __shared__ float2 sm2[];
@@ -326,21 +328,27 @@ __global__ void k_local_adj_moments(const ProbParams* __restrict__ probs, const 
     for (int row = tid; row < t.count; row += nt) {
         const int64_t k = t.start + row;
         const double gk = (double)P.sgn * g_s[k];
-        const double y = 0.5 * w_s[k] * B.R;
-        if (y < 1e-100) {
-            if (nu == 0) acc[tid] = acc2{(float)gk, (float)(gk - (double)(float)gk)};
+        // the same arithmetic as k_local_eval (the transpose of the same operator)
+        const float2 wk = w2[k];
+        const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});
+        if (!(ydf.h > 0.f)) {
+            if (nu == 0) {
+                acc2 a = acc[tid];
+                acc_fma(a, df_from(gk), df{1.f, 0.f});
+                acc[tid] = a;
+            }
         } else {
             const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;
             const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;
             const int ntop = hp + L;
-            const int ns = miller_start(ntop, y);
-            df S = (y >= 1.0) ? miller_store_df(y, ntop, ns, jb, nt, tid)
-                              : df_from(series_store_fp64(y, ntop, jb, nt, tid));
+            const int ns = miller_start(ntop, (double)ydf.h);
+            df S = (ydf.h >= 1.f) ? miller_store_df(ydf, ntop, ns, jb, nt, tid)
+                                  : df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
             const float p2 = exp2f(-(float)ilogbf(S.h));
             S = df_scale(S, p2);
             // g_k / S^2 (the normalisation of both Bessel factors)
-            const double Sd = df_to(S);
-            const df gs = df_from(gk / (Sd * Sd));
+            const df iS = df_recip(S);
+            const df gs = df_mul(df_mul(df_from(gk), iS), iS);
             for (int l = 0; l <= L; ++l) {
                 const int b = hm - l;
                 const float2 va = jb[(hp + l) * nt + tid];
@@ -365,7 +373,7 @@ __global__ void k_local_adj_moments(const ProbParams* __restrict__ probs, const 
 
 __global__ void __launch_bounds__(kMomThreads)
 k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                 const Tile* __restrict__ tiles, const double* __restrict__ r_s,
+                 const Tile* __restrict__ tiles, const float2* __restrict__ r2,
                  const double* __restrict__ mom, double* __restrict__ c_s)
 {
     extern __shared__ float2 mu2[];
@@ -380,13 +388,15 @@ k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restr
         mu2[l] = make_float2(h, (float)(v - (double)h));
     }
     __syncthreads();
-    const double invR = B.R > 0.0 ? 1.0 / B.R : 0.0;
+    const df invR{B.iR_h, B.iR_l};
     for (int64_t j = t.start + tid; j < t.start + t.count; j += nt) {
-        const double y = r_s[j] * invR;
-        const double u = fma(2.0 * y, y, -1.0);
-        const df u2 = df_from(2.0 * u);
-        df t0 = odd ? df_from(y) : df{1.f, 0.f};
-        df t1 = odd ? df_from(y * (2.0 * u - 1.0)) : df_from(u);
+        // the same arithmetic as k_local_moments (the transpose of the same operator)
+        const float2 rj = r2[j];
+        const df y = df_mul(df{rj.x, rj.y}, invR);
+        const df u = df_add(df_mul(df{2.f * y.h, 2.f * y.l}, y), df{-1.f, 0.f});
+        const df u2{2.f * u.h, 2.f * u.l};
+        df t0 = odd ? y : df{1.f, 0.f};
+        df t1 = odd ? df_mul(y, df_add(u2, df{-1.f, 0.f})) : u;
         acc2 sum{0.f, 0.f};
         acc_fma(sum, t0, df{mu2[0].x, mu2[0].y});
         if (L >= 1) acc_fma(sum, t1, df{mu2[1].x, mu2[1].y});
@@ -438,7 +448,7 @@ int local_adj_threads(int ntop_max, int lmax)
 }
 
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                     int ntiles, int ntop_max, int lmax, int threads, const double* w_s,
+                                     int ntiles, int ntop_max, int lmax, int threads, const float2* w2,
                                      const double* g_s, double* mom, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
@@ -446,18 +456,18 @@ cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* 
     cudaError_t e = cudaFuncSetAttribute(k_local_adj_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_adj_moments<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w_s, g_s, mom);
+    k_local_adj_moments<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, g_s, mom);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                  int ntiles, int lmax, const double* r_s, const double* mom, double* c_s,
+                                  int ntiles, int lmax, const float2* r2, const double* mom, double* c_s,
                                   cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float2) * (size_t)(lmax + 1);
-    k_local_adj_eval<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r_s, mom, c_s);
+    k_local_adj_eval<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r2, mom, c_s);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -476,7 +486,7 @@ cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, 
 }
 
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                 int ntiles, int lmax, const double* r_s, const double* c_s,
+                                 int ntiles, int lmax, const float2* r2, const float2* c2,
                                  double* mom, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
@@ -484,7 +494,7 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
     cudaError_t e = cudaFuncSetAttribute(k_local_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_moments<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r_s, c_s, mom);
+    k_local_moments<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r2, c2, mom);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -500,7 +510,7 @@ int local_eval_threads(int ntop_max)
 }
 
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                   int ntiles, int ntop_max, int threads, const double* w_s,
+                                   int ntiles, int ntop_max, int threads, const float2* w2,
                                    const double* mom, double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
@@ -508,7 +518,7 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
     cudaError_t e = cudaFuncSetAttribute(k_local_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_eval<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w_s, mom, g_s);
+    k_local_eval<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -45,6 +45,8 @@ struct LocalBlock {
     int32_t prob, k0, k1, j0, j1, pad;
     double R;
     int64_t mom_off;   // offset of the block's L+1 moments
+    float R_h, R_l;    // R as double-float
+    float iR_h, iR_l;  // 1 / R as double-float (0 when R = 0)
 };
 
 // Asymptotic block: type-3 NUFFT geometry (centres, grid spacings, sizes).
@@ -144,21 +146,21 @@ cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int
                            double* g, cudaStream_t s);
 
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                 int ntiles, int lmax, const double* r_s, const double* c_s,
+                                 int ntiles, int lmax, const float2* r2, const float2* c2,
                                  double* mom, cudaStream_t s);
 int local_eval_threads(int ntop_max);
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                              int ntiles, int ntop_max, int threads, const double* w_s,
+                              int ntiles, int ntop_max, int threads, const float2* w2,
                               const double* mom, double* g_s, cudaStream_t s);
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           int max_area, int lowp, const double* r_s, const double* w_s, const double* c_s,
                           double* g_s, cudaStream_t s);
 int local_adj_threads(int ntop_max, int lmax);
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                     int ntiles, int ntop_max, int lmax, int threads, const double* w_s,
+                                     int ntiles, int ntop_max, int lmax, int threads, const float2* w2,
                                      const double* g_s, double* mom, cudaStream_t s);
 cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                  int ntiles, int lmax, const double* r_s, const double* mom, double* c_s,
+                                  int ntiles, int lmax, const float2* r2, const double* mom, double* c_s,
                                   cudaStream_t s);
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
                               int max_area, int lowp, const double* r_s, const double* w_s, const double* g_s,

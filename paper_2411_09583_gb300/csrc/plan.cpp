@@ -515,6 +515,11 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         lb.prob = h.prob;
         lb.k0 = (int32_t)h.k0; lb.k1 = (int32_t)h.k1; lb.j0 = (int32_t)h.j0; lb.j1 = (int32_t)h.j1;
         lb.R = h.b[1];
+        lb.R_h = (float)lb.R;
+        lb.R_l = (float)(lb.R - (double)lb.R_h);
+        const double iR = lb.R > 0.0 ? 1.0 / lb.R : 0.0;
+        lb.iR_h = (float)iR;
+        lb.iR_l = (float)(iR - (double)lb.iR_h);
         lb.mom_off = mom_off;
         mom_off += pp.L + 1;
         vloc.push_back(lb);
@@ -890,12 +895,12 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if ((mask & 1) && P->n_loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
-        NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r,
-                                     P->d_cs, P->d_mom, ls));
+        NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
+                                     P->d_cs2, P->d_mom, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
         NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                  P->eval_threads, P->d_w, P->d_mom, P->d_gs, ls));
+                                  P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if ((mask & 4) && P->n_dir) {
@@ -972,10 +977,10 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, s));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
         NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, P->lmax,
-                                         thr, P->d_w, P->d_gs, P->d_mom, s));
+                                         thr, P->d_w2, P->d_gs, P->d_mom, s));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, s));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, s));
-        NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r, P->d_mom,
+        NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, P->d_mom,
                                       P->d_cs, s));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, s));
     }
