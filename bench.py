@@ -475,14 +475,15 @@ def run_ours(a):
     hr = torch.from_numpy(r).pin_memory().numpy()
     hw = torch.from_numpy(omega).pin_memory().numpy()
     hc = torch.from_numpy(c).pin_memory().numpy()
-    transform_host(a.nu, hr, hw, hc, a.eps)
+    hg = torch.empty(a.m, dtype=torch.float64).pin_memory().numpy()
+    transform_host(a.nu, hr, hw, hc, a.eps, out=hg)
     e2e_ms = []
     for i in range(max(3, a.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize(dev)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        gh = transform_host(a.nu, hr, hw, hc, a.eps)
+        gh = transform_host(a.nu, hr, hw, hc, a.eps, out=hg)
         s1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms.append(s0.elapsed_time(s1))

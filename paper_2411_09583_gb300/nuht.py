@@ -213,13 +213,22 @@ def nuht(nu, r, omega, c, eps, **opts):
         return p.execute(c)
 
 
-def transform_host(nu, r, omega, c, eps, stream=None, **opts):
-    """Whole transform from host arrays through nuht_transform_host (real c)."""
+def transform_host(nu, r, omega, c, eps, stream=None, out=None, **opts):
+    """Whole transform from host arrays through nuht_transform_host (real c).
+
+    out: optional C-contiguous float64 host array of shape (m,) + c.shape[1:]
+    for the result (pinned memory makes the device-to-host copy direct)."""
     r = np.ascontiguousarray(r, dtype=np.float64)
     omega = np.ascontiguousarray(omega, dtype=np.float64)
     c = np.ascontiguousarray(c, dtype=np.float64)
     nvec = 1 if c.ndim == 1 else int(np.prod(c.shape[1:]))
-    g = np.empty((omega.size,) + c.shape[1:], dtype=np.float64)
+    shape = (omega.size,) + c.shape[1:]
+    if out is None:
+        g = np.empty(shape, dtype=np.float64)
+    else:
+        g = out
+        if g.shape != shape or g.dtype != np.float64 or not g.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of shape %s" % (shape,))
     o = make_opts(**opts)
     N.check(N.lib().nuht_transform_host(int(nu), r.ctypes.data_as(ctypes.c_void_p), r.size,
                                         omega.ctypes.data_as(ctypes.c_void_p), omega.size,
