@@ -23,6 +23,7 @@ namespace nuht {
 namespace {
 
 constexpr int kSubThreads = 1024;
+constexpr int kSubCandUnroll = 16;   // candidate rows loaded together (the default n_cand)
 constexpr int kSubWarps = kSubThreads / 32;
 
 // 0 empty, 1 local, 2 asymptotic, 3 direct, 4 mixed (split further)
@@ -31,6 +32,16 @@ __device__ __forceinline__ int classify(const int32_t* __restrict__ st, const Su
     if (b.k1 < b.k0 || b.j1 < b.j0) return 0;
     if (st[b.k1] >= b.j1) return 1;
     if (st[b.k0] < b.j0) return 2;
+    if ((int64_t)(b.k1 - b.k0 + 1) * (int64_t)(b.j1 - b.j0 + 1) <= min_size) return 3;
+    return 4;
+}
+
+// classify with the staircase values at the block's first and last rows given
+__device__ __forceinline__ int classify_v(const SubBlk& b, int s0, int s1, int64_t min_size)
+{
+    if (b.k1 < b.k0 || b.j1 < b.j0) return 0;
+    if (s1 >= b.j1) return 1;
+    if (s0 < b.j0) return 2;
     if ((int64_t)(b.k1 - b.k0 + 1) * (int64_t)(b.j1 - b.j0 + 1) <= min_size) return 3;
     return 4;
 }
@@ -147,10 +158,10 @@ __global__ void __launch_bounds__(kSubThreads) k_subdivide(
                 const int nc = rows <= n_cand ? rows : n_cand;
                 int64_t best = -1;
                 int bk = b.k0, bj = b.j0 - 1;
-                for (int c = 0; c < nc; ++c) {
-                    const int k = rows <= n_cand ? b.k0 + c
-                                                 : b.k0 + (int)(((int64_t)c * (b.k1 - b.k0)) / (n_cand - 1));
-                    int j = st[k];
+                auto cand_row = [&](int c) {
+                    return rows <= n_cand ? b.k0 + c : b.k0 + (int)(((int64_t)c * (b.k1 - b.k0)) / (n_cand - 1));
+                };
+                auto consider = [&](int k, int j) {
                     if (j > b.j1) j = b.j1;
                     if (j < b.j0) j = b.j0 - 1;
                     const int64_t area = (int64_t)(k - b.k0 + 1) * (b.j1 - j) + (int64_t)(b.k1 - k) * (j - b.j0 + 1);
@@ -159,12 +170,35 @@ __global__ void __launch_bounds__(kSubThreads) k_subdivide(
                         bk = k;
                         bj = j;
                     }
+                };
+                if (nc <= kSubCandUnroll) {
+                    // all candidate loads in flight at once
+                    int jv[kSubCandUnroll];
+#pragma unroll
+                    for (int c = 0; c < kSubCandUnroll; ++c) jv[c] = c < nc ? st[cand_row(c)] : 0;
+#pragma unroll
+                    for (int c = 0; c < kSubCandUnroll; ++c)
+                        if (c < nc) consider(cand_row(c), jv[c]);
+                } else {
+                    for (int c = 0; c < nc; ++c) {
+                        const int k = cand_row(c);
+                        consider(k, st[k]);
+                    }
                 }
                 ch[0] = SubBlk{b.k0, bk, b.j0, bj, b.prob};           // upper left: local
                 ch[1] = SubBlk{bk + 1, b.k1, bj + 1, b.j1, b.prob};   // lower right: asymptotic
                 ch[2] = SubBlk{b.k0, bk, bj + 1, b.j1, b.prob};       // upper right: mixed
                 ch[3] = SubBlk{bk + 1, b.k1, b.j0, bj, b.prob};       // lower left: mixed
-                for (int c = 0; c < 4; ++c) cls[c] = classify(st, ch[c], min_size);
+                // the children's end rows, loaded together
+                int sk1[4], sk0[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool ne = ch[c].k1 >= ch[c].k0 && ch[c].j1 >= ch[c].j0;
+                    sk1[c] = ne ? st[ch[c].k1] : 0;
+                    sk0[c] = ne ? st[ch[c].k0] : 0;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cls[c] = classify_v(ch[c], sk0[c], sk1[c], min_size);
             }
             emit(ch, cls, 4, S, wsum, out, ocap, qb, qcap);
         }

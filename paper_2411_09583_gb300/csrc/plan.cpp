@@ -57,6 +57,11 @@ struct SegList {
         segs.push_back(Seg{blk, len, first, last});
         prefix.push_back(prefix.back() + (int32_t)cnt);
     }
+    void reserve(size_t k)
+    {
+        segs.reserve(k);
+        prefix.reserve(k + 1);
+    }
     int nseg() const { return (int)segs.size(); }
     int total() const { return prefix.back(); }
 };
@@ -503,6 +508,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     std::vector<AsyBlock> vasy;
     std::vector<DirectBlock> vdir;
     SegList smom, seval, sspread, sinterp, sfs, sfa, sfb, sfk;
+    smom.reserve(LB.size()); seval.reserve(LB.size());
+    sspread.reserve(AB.size()); sinterp.reserve(AB.size()); sfk.reserve(AB.size());
     vloc.reserve(LB.size());
     vasy.reserve(AB.size());
     vdir.reserve(DB.size());
@@ -545,20 +552,20 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         const double S = 0.5 * (whi - wlo);
         const double Seff = S > 0.0 ? S : 1.0;
         ab.h = M_PI / (2.0 * Seff);
-        ab.inv_h = 1.0 / ab.h;
-        const double n1f = std::ceil(X / ab.h + 0.5 * P->w) + 1.0;   // one cell of rounding margin
+        ab.inv_h = (2.0 / M_PI) * Seff;
+        const double n1f = std::ceil(X * ab.inv_h + 0.5 * P->w) + 1.0;   // one cell of rounding margin
         if (n1f > (double)(1 << 22)) return NUHT_ERR_UNSUPPORTED;
         ab.N1 = (int32_t)n1f;
         const int64_t nf1 = 2 * (int64_t)ab.N1 + 1;
-        int lg = 5;
-        while (((int64_t)1 << lg) < 2 * nf1) ++lg;
+        int lg = 64 - __builtin_clzll((unsigned long long)(2 * nf1 - 1));   // smallest 2^lg >= 2 nf1
+        if (lg < 5) lg = 5;
         if (lg > kFftMaxLog2) return NUHT_ERR_UNSUPPORTED;
         ab.log2nf2 = lg;
         ab.nf2 = 1 << lg;
         ab.rho = rlo;
         ab.alpha = 0.5 * P->w * ab.h;
-        ab.alpha2 = P->w * M_PI / ab.nf2;
-        ab.inv_delta = ab.nf2 / (2.0 * M_PI);
+        ab.alpha2 = std::ldexp(P->w * M_PI, -lg);
+        ab.inv_delta = ab.nf2 * (0.5 / M_PI);
         ab.hd = ab.h * ab.inv_delta;
         ab.rho_h = (float)ab.rho;
         ab.rho_l = (float)(ab.rho - (double)ab.rho_h);
