@@ -231,6 +231,7 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
                 for (int f = 0; f < 4; ++f) A[e][f] = acc2{0.f, 0.f};
             if (live && !lowd && lowq) {
                 const float2* up = Ud + 2 * dp;
+#pragma unroll 2
                 for (int p = p0 + sub; p < p1; p += kSpreadSub) {
                     const float4 uu = *(const float4*)(up + p * L.sud);
                     const float4 xa = *(const float4*)(X + p * L.sx + 4 * qq);
@@ -244,6 +245,7 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
                 }
             } else if (live && !lowd) {
                 const float2* up = Ud + 2 * dp;
+#pragma unroll 2
                 for (int p = p0 + sub; p < p1; p += kSpreadSub) {
                     const float4 uu = *(const float4*)(up + p * L.sud);
                     const float4 xa = *(const float4*)(X + p * L.sx + 4 * qq);
@@ -257,6 +259,7 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
                 }
             } else if (live) {
                 const float* up = Uf + 2 * (dp - L.ndf);
+#pragma unroll 2
                 for (int p = p0 + sub; p < p1; p += kSpreadSub) {
                     const float2 uu = *(const float2*)(up + p * L.suf);
                     const float4 xa = *(const float4*)(X + p * L.sx + 4 * qq);
@@ -795,6 +798,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
             float2 hv;
             if (d < dci) {
                 acc2 acc{0.f, 0.f};
+#pragma unroll 4
                 for (int i = 0; i < w; ++i) {
                     const float4 gv = win[(b + i) * Q + q];
                     const float2 c2 = coef2[i * nb + d];
@@ -804,6 +808,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
                 hv = make_float2(h2.h, h2.l);
             } else {
                 float acc = 0.f;
+#pragma unroll 4
                 for (int i = 0; i < w; ++i) {
                     const float4 gv = win[(b + i) * Q + q];
                     acc = fmaf(coef2[i * nb + d].x, im ? gv.z : gv.x, acc);
@@ -856,6 +861,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
             if (q < qs) {
                 acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
                 int d = 0;
+#pragma unroll 3
                 for (; d < dci; ++d) {
                     const float2 tp = u[d];
                     const float4 hv = *(const float4*)(hq + d * Q2);
@@ -863,6 +869,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
                     acc_fma(pi, df{tp.x, tp.y}, df{hv.z, hv.w});
                 }
                 float fr = 0.f, fi = 0.f;
+#pragma unroll 3
                 for (; d < nb; ++d) {
                     const float tp = u[d].x;
                     const float4 hv = *(const float4*)(hq + d * Q2);
@@ -876,6 +883,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
             } else {
                 // small Hankel term: FP32 is accurate enough
                 float pr = 0.f, pi = 0.f;
+#pragma unroll 4
                 for (int d = 0; d < nb; ++d) {
                     const float tp = u[d].x;
                     const float4 hv = *(const float4*)(hq + d * Q2);
