@@ -56,6 +56,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched / mixed-precision side measurements")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="library default options instead of the autotuned ones (min_size is chosen "
+                         "from experiments, Algorithm 2)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the oracle sample")
     return ap.parse_args(argv)
@@ -226,15 +229,16 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+def stored_traffic(kernel, workload, opts=None):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel, the
+    workload and the plan options are those of the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         db = json.load(open(path))
         ent = db.get(kernel)
-        if not ent or ent.get("workload") != workload:
+        if not ent or ent.get("workload") != workload or ent.get("opts", {}) != (opts or {}):
             return None
         if ent.get("source_hash") != source_hash(*ent.get("sources", [])):
             return None
@@ -412,8 +416,20 @@ def run_ours(a):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # plan options from the autotuner (min_size, spreading tile, M around the
+    # heuristic), chosen before and outside the timed region
+    opts, tuned = {}, None
+    if not a.no_autotune:
+        from paper_2411_09583_gb300.autotune import autotune, candidates
+        grid = candidates([a.nu], a.eps, min_sizes=(1024, 2048, 4096, 8192), spread_tiles=(0, 128),
+                          m_offsets=(0, 1))
+        opts, table = autotune(a.nu, dr, dw, dc, a.eps, objective="plan+execute", reps=3, grid=grid)
+        dflt = [t for t, o in table if o == {"min_size": 1024, "spread_tile": 0, "m_terms": 0}]
+        tuned = {"opts": opts, "best_ms": table[0][0], "default_opts_ms": dflt[0] if dflt else None,
+                 "candidates": len(grid), "objective": "plan+execute"}
+
     def step(timing=False):
-        p = Plan(a.nu, dr, dw, a.eps, timing=timing)
+        p = Plan(a.nu, dr, dw, a.eps, timing=timing, **opts)
         g = p.execute(dc)
         return p, g
 
@@ -456,7 +472,7 @@ def run_ours(a):
     value = ws * a.steps * (a.n + a.m) / total_s
 
     # execute only (plan reused)
-    p = Plan(a.nu, dr, dw, a.eps)
+    p = Plan(a.nu, dr, dw, a.eps, **opts)
     for _ in range(2):
         p.execute(dc)
     exe_ms = []
@@ -476,14 +492,14 @@ def run_ours(a):
     hw = torch.from_numpy(omega).pin_memory().numpy()
     hc = torch.from_numpy(c).pin_memory().numpy()
     hg = torch.empty(a.m, dtype=torch.float64).pin_memory().numpy()
-    transform_host(a.nu, hr, hw, hc, a.eps, out=hg)
+    transform_host(a.nu, hr, hw, hc, a.eps, out=hg, **opts)
     e2e_ms = []
     for i in range(max(3, a.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize(dev)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        gh = transform_host(a.nu, hr, hw, hc, a.eps, out=hg)
+        gh = transform_host(a.nu, hr, hw, hc, a.eps, out=hg, **opts)
         s1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms.append(s0.elapsed_time(s1))
@@ -511,7 +527,7 @@ def run_ours(a):
                 "algorithmic_flops_per_launch": flops, "units_per_launch": units,
                 "launch_ms": mean_stage[dom],
                 "traffic": stored_traffic(kernel_of.get(dom, dom),
-                                          workload_config(a)["workload"])}
+                                          workload_config(a)["workload"], opts)}
 
     extra_batched = extra_mixed = extra_grad = None
     if not a.no_extra and ws == 1:
@@ -531,7 +547,9 @@ def run_ours(a):
                 "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic (seeded uniform r, omega; Gaussian c)",
-                "config": dict(workload_config(a), parallelism="replicas" if ws > 1 else "1 GPU"),
+                "config": dict(workload_config(a), parallelism="replicas" if ws > 1 else "1 GPU",
+                               opts=opts or "library defaults"),
+                "autotune": tuned,
                 "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": 8 * (a.n + a.m + a.n),
