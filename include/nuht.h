@@ -126,10 +126,15 @@ int nuht_choose_params(int nu, double eps, int m_terms, int *M, double *z, int *
 
 /* Build a plan for order nu, points r[0..n), frequencies omega[0..m) (device
  * FP64, any order, values >= 0), tolerance eps in [1e-15, 1e-1].  Sorts r and
- * omega on the device, subdivides the matrix on the host (Algorithm 1) and
- * uploads the block work lists.  The plan copies what it needs; r and omega
- * may be freed after return.  opt may be NULL (defaults).  Negative nu is
- * mapped through J_{-nu} = (-1)^nu J_nu.  n = 0 or m = 0 is allowed. */
+ * omega, subdivides the matrix (Algorithm 1) and builds the block work lists,
+ * all on the device; the host waits once for the list sizes.  The call
+ * returns with the rest of the build queued on the stream (stream-ordered
+ * like every call).  The plan copies what it needs; r and omega are consumed
+ * before that wait and may be freed after return.  opt may be NULL (defaults).  Negative
+ * nu is mapped through J_{-nu} = (-1)^nu J_nu.  n = 0 or m = 0 is allowed.
+ * Block lists beyond the device capacity ((n+m)/16 + 16384 per class; the
+ * environment variable NUHT_SUBDIVIDE_CAPACITY lowers it, for testing) are
+ * built by a host walk of Algorithm 1 instead, with the same result. */
 int nuht_plan(nuht_plan_t *out, int nu, const double *r, int64_t n,
               const double *omega, int64_t m, double eps, const nuht_opts *opt,
               void *stream);

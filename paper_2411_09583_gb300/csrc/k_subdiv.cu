@@ -108,9 +108,12 @@ __device__ __forceinline__ void emit(const SubBlk* ch, const int* cls, int nch, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (!fits) S.ovf = 1;
-        for (int c = 0; c < 3; ++c) S.nout[c] += (int64_t)((total >> (16 * c)) & 0xffff);
-        S.nnext += (int64_t)(total >> 48);
+        if (fits) {
+            for (int c = 0; c < 3; ++c) S.nout[c] += (int64_t)((total >> (16 * c)) & 0xffff);
+            S.nnext += (int64_t)(total >> 48);
+        } else {
+            S.ovf = 1;   // the counts stay at what was written (within the capacities)
+        }
     }
     __syncthreads();
 }
@@ -216,11 +219,13 @@ __global__ void __launch_bounds__(kSubThreads) k_subdivide(
 }
 
 // Sorted values at the block edges: local blocks R = r_{j1}; asymptotic
-// blocks (r_{j0}, r_{j1}, omega_{k0}, omega_{k1}).
-__global__ void k_block_bounds(const SubBlk* __restrict__ loc, int64_t nl, const SubBlk* __restrict__ asy,
-                               int64_t na, const ProbParams* __restrict__ probs, const double* __restrict__ r_s,
-                               const double* __restrict__ w_s, double* __restrict__ bl, double4* __restrict__ ba)
+// blocks (r_{j0}, r_{j1}, omega_{k0}, omega_{k1}).  Counts from res (device).
+__global__ void k_block_bounds(const SubBlk* __restrict__ loc, const SubBlk* __restrict__ asy,
+                               const int64_t* __restrict__ res, const ProbParams* __restrict__ probs,
+                               const double* __restrict__ r_s, const double* __restrict__ w_s,
+                               double* __restrict__ bl, double4* __restrict__ ba)
 {
+    const int64_t nl = res[0], na = res[1];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl + na;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < nl) {
@@ -246,14 +251,10 @@ cudaError_t launch_subdivide(const int32_t* stair, const ProbParams* probs, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_bounds(const SubBlk* loc, int64_t nl, const SubBlk* asy, int64_t na,
-                                const ProbParams* probs, const double* r_s, const double* w_s, double* bl,
-                                double4* ba, cudaStream_t s)
+cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int64_t* res, const ProbParams* probs,
+                                const double* r_s, const double* w_s, double* bl, double4* ba, cudaStream_t s)
 {
-    if (nl + na <= 0) return cudaSuccess;
-    int64_t g = (nl + na + 255) / 256;
-    if (g > 4096) g = 4096;
-    k_block_bounds<<<(int)g, 256, 0, s>>>(loc, nl, asy, na, probs, r_s, w_s, bl, ba);
+    k_block_bounds<<<152 * 8, 256, 0, s>>>(loc, asy, res, probs, r_s, w_s, bl, ba);
     count_launches(1);
     return cudaGetLastError();
 }

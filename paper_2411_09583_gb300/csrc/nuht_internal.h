@@ -94,6 +94,48 @@ struct SubBlk {
     int32_t k0, k1, j0, j1, prob;
 };
 
+// Building the work lists on the device (k_blocks.cu): per-block counters
+// (columns), their exclusive prefix sums and totals, maxima, and the tile lists.
+enum { LC_MOM, LC_TMOM, LC_TEVAL, LC_RC, kLocalCols };
+enum { AC_GB, AC_GQ, AC_TSPREAD, AC_TINTERP, AC_NFK, AC_NFS, AC_NFL, AC_IFK, AC_IFS, AC_IFA, AC_IFB,
+       AC_RC, AC_NF2, kAsyCols };
+enum { DC_ENTRIES, kDirCols };
+enum { TOT_LOCAL = 0, TOT_ASY = kLocalCols, TOT_DIR = kLocalCols + kAsyCols,
+       kTotals = kLocalCols + kAsyCols + kDirCols };
+enum { MX_DIR_ROWS, MX_DIR_COLS, MX_DIR_AREA, MX_NF2_SMALL, MX_LARGE, MX_ERR, kMaxv };
+enum { LIST_MOM, LIST_EVAL, LIST_SPREAD, LIST_INTERP, LIST_FSMALL, LIST_FA, LIST_FB, LIST_FBLOCK, kLists };
+
+struct BlockBuild {
+    const int64_t* res;       // counts of local, asymptotic, direct blocks (device)
+    const SubBlk* sub;        // [3][ocap] the subdivision's lists, problem-local indices
+    int64_t ocap;
+    const double* bl;         // [nl] r at the last column of each local block
+    const double4* ba;        // [na] (r_j0, r_j1, omega_k0, omega_k1) of each asymptotic block
+    const ProbParams* probs;
+    int w, mom_tile, eval_tile, spread_tile, interp_tile;
+    LocalBlock* loc;          // descriptors before their offsets are known
+    AsyBlock* asy;
+    DirectBlock* dir;
+    int8_t* fcls;             // FFT class of each asymptotic block (0 one CTA, 1 per grid, 2 two passes)
+    int64_t* lcnt;            // [nl][kLocalCols] counters, then exclusive prefix sums
+    int64_t* acnt;            // [na][kAsyCols]
+    int64_t* dcnt;            // [nd][kDirCols]
+    int64_t* totals;          // [kTotals] column sums
+    int64_t* maxv;            // [kMaxv]
+};
+
+struct BuildLists {
+    LocalBlock* loc;
+    AsyBlock* asy;
+    DirectBlock* dir;
+    Seg* seg[kLists];
+    int32_t* pre[kLists];     // [nseg + 1] tiles before each segment
+    SubBlk* blk;              // [nl + na + nd] every block in global sorted indices
+};
+
+cudaError_t launch_block_build(const BlockBuild& bb, cudaStream_t s);
+cudaError_t launch_block_fill(const BlockBuild& bb, const BuildLists& L, cudaStream_t s);
+
 // Kernel tables shared by every asymptotic block of a plan.
 struct Tables {
     const double* es;      // [w][deg + 1] monomial coefficients in v = 2 z0 - 1
@@ -133,9 +175,8 @@ cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_
 cudaError_t launch_subdivide(const int32_t* stair, const ProbParams* probs, int nprob, int64_t min_size,
                              int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* out, int64_t ocap,
                              int64_t* res, cudaStream_t s);
-cudaError_t launch_block_bounds(const SubBlk* loc, int64_t nl, const SubBlk* asy, int64_t na,
-                                const ProbParams* probs, const double* r_s, const double* w_s, double* bl,
-                                double4* ba, cudaStream_t s);
+cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int64_t* res, const ProbParams* probs,
+                                const double* r_s, const double* w_s, double* bl, double4* ba, cudaStream_t s);
 cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
                                   int nprob, int32_t* s_out, cudaStream_t s);
 cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <mutex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -109,7 +110,7 @@ struct nuht_plan_s {
     int spread_threads = 256;
     bool has_large_fft = false;
     Tables tab{};
-    std::vector<HBlock> hb[3];
+    SubBlk* d_blk = nullptr;          // every block (local, asymptotic, direct), global sorted indices
     int64_t direct_entries = 0, local_rc = 0, asy_rc = 0, fft_points = 0;
     double plan_ms[4] = {0, 0, 0, 0};
 
@@ -189,7 +190,9 @@ Staging g_stage_in, g_stage_out;
 struct Aux {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t stage_done = nullptr;   // the last upload from g_stage_out on this device
 };
+cudaEvent_t g_stage_out_event = nullptr;   // set with the last upload; waited on before reuse
 Aux g_aux[64];
 
 cudaError_t aux_stream(Aux** out)
@@ -203,6 +206,7 @@ cudaError_t aux_stream(Aux** out)
         e = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.stage_done, cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
     }
     *out = &a;
@@ -329,6 +333,39 @@ static double ms_since(std::chrono::steady_clock::time_point& t)
     return ms;
 }
 
+// Temporaries of the device work-list build (offsets into an arena).
+struct BuildTemps {
+    size_t loc, asy, dir, fcls, lcnt, acnt, dcnt, tot, maxv;
+};
+
+static BuildTemps reserve_build_temps(Arena& a, int64_t cap)
+{
+    BuildTemps t;
+    t.loc = a.reserve<LocalBlock>(cap);
+    t.asy = a.reserve<AsyBlock>(cap);
+    t.dir = a.reserve<DirectBlock>(cap);
+    t.fcls = a.reserve<int8_t>(cap);
+    t.lcnt = a.reserve<int64_t>(cap * kLocalCols);
+    t.acnt = a.reserve<int64_t>(cap * kAsyCols);
+    t.dcnt = a.reserve<int64_t>(cap * kDirCols);
+    t.tot = a.reserve<int64_t>(kTotals);
+    t.maxv = a.reserve<int64_t>(kMaxv);
+    return t;
+}
+
+static void bind_build_temps(BlockBuild& bb, char* base, const BuildTemps& t)
+{
+    bb.loc = (LocalBlock*)(base + t.loc);
+    bb.asy = (AsyBlock*)(base + t.asy);
+    bb.dir = (DirectBlock*)(base + t.dir);
+    bb.fcls = (int8_t*)(base + t.fcls);
+    bb.lcnt = (int64_t*)(base + t.lcnt);
+    bb.acnt = (int64_t*)(base + t.acnt);
+    bb.dcnt = (int64_t*)(base + t.dcnt);
+    bb.totals = (int64_t*)(base + t.tot);
+    bb.maxv = (int64_t*)(base + t.maxv);
+}
+
 static int build_plan(nuht_plan_t P, const double* r, const double* omega)
 {
     auto clk = std::chrono::steady_clock::now();
@@ -353,12 +390,22 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t o_flag = sa.reserve<int>(2);
     size_t o_prb = sa.reserve<ProbParams>(probs.size());
     size_t o_roff = sa.reserve<int64_t>(probs.size() + 1), o_woff = sa.reserve<int64_t>(probs.size() + 1);
-    // device subdivision: two level queues, the three block lists, edge values
-    const int64_t qcap = (n + m) / 4 + 4096 + nprob, ocap = (n + m) / 8 + 16384 + nprob;
+    // device subdivision: two level queues, the three block lists, edge values;
+    // work-list build: descriptors, FFT classes, per-block counters, totals
+    int64_t qcap = (n + m) / 4 + 4096 + nprob, ocap = (n + m) / 16 + 16384 + nprob;
+    if (const char* cap = std::getenv("NUHT_SUBDIVIDE_CAPACITY")) {
+        // test knob: smaller device lists exercise the host fallback
+        const long long c = std::atoll(cap);
+        if (c > 0) {
+            qcap = c < qcap ? c : qcap;
+            ocap = c < ocap ? c : ocap;
+        }
+    }
     size_t o_qa = sa.reserve<SubBlk>(qcap), o_qb = sa.reserve<SubBlk>(qcap);
     size_t o_out = sa.reserve<SubBlk>(3 * ocap);
     size_t o_bl = sa.reserve<double>(ocap), o_ba = sa.reserve<double4>(ocap);
     size_t o_res = sa.reserve<int64_t>(4);
+    BuildTemps bt = reserve_build_temps(sa, ocap);
     size_t o_scr = sa.size;
     const size_t scr = radix_sort_scratch_bytes(n), scr_w = radix_sort_scratch_bytes(m);
     sa.size += align256(scr);
@@ -373,6 +420,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     int* d_flag = (int*)(sort_mem + o_flag);
     NUHT_CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * 2, s));
     std::lock_guard<std::mutex> stage_lock(g_stage_mu);
+    // a previous build's upload from the shared staging buffer may still be in flight
+    if (g_stage_out_event) NUHT_CK(cudaEventSynchronize(g_stage_out_event));
     // problems and segment offsets (needed by the segmented sort and the staircase)
     ProbParams* d_prb = (ProbParams*)(sort_mem + o_prb);
     int64_t* d_roff = (int64_t*)(sort_mem + o_roff);
@@ -415,222 +464,155 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     }
     if (nprob == 1) NUHT_CK(launch_staircase(r_s, n, w_s, m, probs[0].z, stair, s));
     else NUHT_CK(launch_staircase_many(r_s, w_s, m, d_prb, nprob, stair, s));
-    // ---- subdivision (Algorithm 1) on the device ---------------------------
+    // ---- subdivision (Algorithm 1) and work lists, on the device ------------
     SubBlk* d_out = (SubBlk*)(sort_mem + o_out);
     int64_t* d_res = (int64_t*)(sort_mem + o_res);
+    double* d_bl = (double*)(sort_mem + o_bl);
+    double4* d_ba = (double4*)(sort_mem + o_ba);
     NUHT_CK(launch_subdivide(stair, d_prb, nprob, P->opt.min_size, P->opt.n_split_cand, (SubBlk*)(sort_mem + o_qa),
                              (SubBlk*)(sort_mem + o_qb), qcap, d_out, ocap, d_res, s));
-    NUHT_CK(g_stage_in.reserve(256 + sizeof(int64_t) * 4));
-    int* hflag = (int*)g_stage_in.p;
-    int64_t* hres = (int64_t*)(g_stage_in.p + 128);
-    NUHT_CK(cudaMemcpyAsync(hflag, d_flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-    NUHT_CK(cudaMemcpyAsync(hres, d_res, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
-    NUHT_CK(cudaStreamSynchronize(s));
+    NUHT_CK(launch_block_bounds(d_out, d_out + ocap, d_res, d_prb, r_s, w_s, d_bl, d_ba, s));
+    P->eval_threads = local_eval_threads(P->ntop_max);
+    const int sp_tile = P->opt.spread_tile ? P->opt.spread_tile : spread_tile_points(P->qmax);
+    P->spread_threads = sp_tile;
+    BlockBuild bb{};
+    bb.res = d_res;
+    bb.sub = d_out;
+    bb.ocap = ocap;
+    bb.bl = d_bl;
+    bb.ba = d_ba;
+    bb.probs = d_prb;
+    bb.w = P->w;
+    bb.mom_tile = kMomentTile;
+    bb.eval_tile = P->eval_threads;
+    bb.spread_tile = sp_tile;
+    bb.interp_tile = kInterpTile;
+    bind_build_temps(bb, sort_mem, bt);
+    char* tmp_mem = nullptr;   // temporaries of the host fallback
+    struct FreeTmp {
+        char** p; cudaStream_t s;
+        ~FreeTmp() { pool_free(*p, s); }
+    } free_tmp{&tmp_mem, s};
+    NUHT_CK(cudaMemsetAsync(bb.totals, 0, sizeof(int64_t) * (kTotals + 0), s));
+    NUHT_CK(cudaMemsetAsync(bb.maxv, 0, sizeof(int64_t) * kMaxv, s));
+    NUHT_CK(launch_block_build(bb, s));
+    // the one wait of the build: flags, counts, totals and maxima to the host
+    const size_t o_hf = 0, o_hr = 64, o_ht = o_hr + 64, o_hm = o_ht + align256(sizeof(int64_t) * kTotals);
+    NUHT_CK(g_stage_in.reserve(o_hm + 256));
+    int* hflag = (int*)(g_stage_in.p + o_hf);
+    int64_t* hres = (int64_t*)(g_stage_in.p + o_hr);
+    int64_t* htot = (int64_t*)(g_stage_in.p + o_ht);
+    int64_t* hmax = (int64_t*)(g_stage_in.p + o_hm);
+    auto fetch_results = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(hflag, d_flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hres, bb.res, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(htot, bb.totals, sizeof(int64_t) * kTotals, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hmax, bb.maxv, sizeof(int64_t) * kMaxv, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    };
+    NUHT_CK(fetch_results());
     if (hflag[0] || hflag[1]) return NUHT_ERR_DOMAIN;
     P->plan_ms[0] = ms_since(clk);
-    for (int c = 0; c < 3; ++c) P->hb[c].clear();
-    if (!hres[3]) {
-        // the lists and their edge values to pinned host memory
-        const int64_t nc[3] = {hres[0], hres[1], hres[2]};
-        double* d_bl = (double*)(sort_mem + o_bl);
-        double4* d_ba = (double4*)(sort_mem + o_ba);
-        NUHT_CK(launch_block_bounds(d_out, nc[0], d_out + ocap, nc[1], d_prb, r_s, w_s, d_bl, d_ba, s));
-        size_t off[5], tot = 0;
-        for (int c = 0; c < 3; ++c) { off[c] = tot; tot += align256(sizeof(SubBlk) * nc[c]); }
-        off[3] = tot; tot += align256(sizeof(double) * nc[0]);
-        off[4] = tot; tot += align256(sizeof(double4) * nc[1]);
-        NUHT_CK(g_stage_in.reserve(tot));
-        for (int c = 0; c < 3; ++c)
-            if (nc[c]) NUHT_CK(cudaMemcpyAsync(g_stage_in.p + off[c], d_out + c * ocap, sizeof(SubBlk) * nc[c],
-                                               cudaMemcpyDeviceToHost, s));
-        if (nc[0]) NUHT_CK(cudaMemcpyAsync(g_stage_in.p + off[3], d_bl, sizeof(double) * nc[0],
-                                           cudaMemcpyDeviceToHost, s));
-        if (nc[1]) NUHT_CK(cudaMemcpyAsync(g_stage_in.p + off[4], d_ba, sizeof(double4) * nc[1],
-                                           cudaMemcpyDeviceToHost, s));
-        NUHT_CK(cudaStreamSynchronize(s));
-        const double* hbl = (const double*)(g_stage_in.p + off[3]);
-        const double4* hba = (const double4*)(g_stage_in.p + off[4]);
-        // problem-major order (stable): the order of the host walk, problem by problem
-        std::vector<int64_t> start(nprob + 1);
-        for (int c = 0; c < 3; ++c) {
-            const SubBlk* sb = (const SubBlk*)(g_stage_in.p + off[c]);
-            std::vector<HBlock>& dst = P->hb[c];
-            dst.resize((size_t)nc[c]);
-            std::fill(start.begin(), start.end(), 0);
-            for (int64_t i = 0; i < nc[c]; ++i) ++start[sb[i].prob + 1];
-            for (int ip = 0; ip < nprob; ++ip) start[ip + 1] += start[ip];
-            for (int64_t i = 0; i < nc[c]; ++i) {
-                const SubBlk& b = sb[i];
-                const ProbParams& q = probs[b.prob];
-                HBlock h;
-                h.k0 = b.k0 + q.w_off; h.k1 = b.k1 + q.w_off;
-                h.j0 = b.j0 + q.r_off; h.j1 = b.j1 + q.r_off;
-                h.prob = b.prob;
-                if (c == 0) h.b[1] = hbl[i];
-                if (c == 1) { h.b[0] = hba[i].x; h.b[1] = hba[i].y; h.b[2] = hba[i].z; h.b[3] = hba[i].w; }
-                dst[(size_t)start[b.prob]++] = h;
-            }
-        }
-    } else {
-        // list capacity exceeded: sorted values and staircase to the host, Algorithm 1 there
+    if (hres[3]) {
+        // list capacity exceeded: sorted values and staircase to the host,
+        // Algorithm 1 there, the lists back to the device, the build again
         const size_t in_bytes = align256(sizeof(double) * n) + align256(sizeof(double) * m) +
                                 align256(sizeof(int32_t) * m);
-        NUHT_CK(g_stage_in.reserve(in_bytes));
-        double* hr = (double*)g_stage_in.p;
+        std::vector<char> hbuf(in_bytes);
+        double* hr = (double*)hbuf.data();
         double* hw = (double*)((char*)hr + align256(sizeof(double) * n));
         int32_t* hst = (int32_t*)((char*)hw + align256(sizeof(double) * m));
         if (n) NUHT_CK(cudaMemcpyAsync(hr, r_s, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
         if (m) NUHT_CK(cudaMemcpyAsync(hw, w_s, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
         if (m) NUHT_CK(cudaMemcpyAsync(hst, stair, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
         NUHT_CK(cudaStreamSynchronize(s));
+        std::vector<SubBlk> hl[3];
+        std::vector<double> hbl;
+        std::vector<double4> hba;
         std::vector<HBlock> lb, ab, db;
         for (int ip = 0; ip < nprob; ++ip) {
             const ProbParams& q = probs[ip];
             subdivide(hst + q.w_off, q.n, q.m, P->opt.min_size, P->opt.n_split_cand, lb, ab, db);
-            std::vector<HBlock>* src[3] = {&lb, &ab, &db};
+            const std::vector<HBlock>* src[3] = {&lb, &ab, &db};
             for (int c = 0; c < 3; ++c)
-                for (HBlock h : *src[c]) {
-                    h.k0 += q.w_off; h.k1 += q.w_off; h.j0 += q.r_off; h.j1 += q.r_off;
-                    h.prob = ip;
-                    h.b[0] = hr[h.j0]; h.b[1] = hr[h.j1]; h.b[2] = hw[h.k0]; h.b[3] = hw[h.k1];
-                    P->hb[c].push_back(h);
+                for (const HBlock& h : *src[c]) {
+                    hl[c].push_back(SubBlk{(int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, ip});
+                    if (c == 0) hbl.push_back(hr[q.r_off + h.j1]);
+                    if (c == 1)
+                        hba.push_back(make_double4(hr[q.r_off + h.j0], hr[q.r_off + h.j1], hw[q.w_off + h.k0],
+                                                   hw[q.w_off + h.k1]));
                 }
         }
+        int64_t cap = 1;
+        for (int c = 0; c < 3; ++c) cap = (int64_t)hl[c].size() > cap ? (int64_t)hl[c].size() : cap;
+        Arena ta;
+        const size_t t_sub = ta.reserve<SubBlk>(3 * cap), t_bl = ta.reserve<double>(cap);
+        const size_t t_ba = ta.reserve<double4>(cap), t_res = ta.reserve<int64_t>(4);
+        BuildTemps tt = reserve_build_temps(ta, cap);
+        NUHT_CK(pool_alloc((void**)&tmp_mem, ta.size, s));
+        std::vector<char> up(t_res + 64, 0);
+        for (int c = 0; c < 3; ++c)
+            if (!hl[c].empty()) std::memcpy(up.data() + t_sub + sizeof(SubBlk) * c * cap, hl[c].data(),
+                                            sizeof(SubBlk) * hl[c].size());
+        if (!hbl.empty()) std::memcpy(up.data() + t_bl, hbl.data(), sizeof(double) * hbl.size());
+        if (!hba.empty()) std::memcpy(up.data() + t_ba, hba.data(), sizeof(double4) * hba.size());
+        int64_t* ures = (int64_t*)(up.data() + t_res);
+        ures[0] = (int64_t)hl[0].size(); ures[1] = (int64_t)hl[1].size(); ures[2] = (int64_t)hl[2].size(); ures[3] = 0;
+        NUHT_CK(cudaMemcpyAsync(tmp_mem, up.data(), t_res + sizeof(int64_t) * 4, cudaMemcpyHostToDevice, s));
+        bb.res = (const int64_t*)(tmp_mem + t_res);
+        bb.sub = (const SubBlk*)(tmp_mem + t_sub);
+        bb.ocap = cap;
+        bb.bl = (const double*)(tmp_mem + t_bl);
+        bb.ba = (const double4*)(tmp_mem + t_ba);
+        bind_build_temps(bb, tmp_mem, tt);
+        NUHT_CK(cudaMemsetAsync(bb.totals, 0, sizeof(int64_t) * kTotals, s));
+        NUHT_CK(cudaMemsetAsync(bb.maxv, 0, sizeof(int64_t) * kMaxv, s));
+        NUHT_CK(launch_block_build(bb, s));
+        NUHT_CK(fetch_results());   // (the upload buffer lives until here)
     }
-    const auto& LB = P->hb[0];
-    const auto& AB = P->hb[1];
-    const auto& DB = P->hb[2];
+    if (hmax[MX_ERR]) return NUHT_ERR_UNSUPPORTED;
+    const int64_t nl = hres[0], na = hres[1], nd = hres[2];
+    const int64_t* tl = htot + TOT_LOCAL;
+    const int64_t* ta_ = htot + TOT_ASY;
+    P->n_loc = (int)nl; P->n_asy = (int)na; P->n_dir = (int)nd;
+    P->mom_len = tl[LC_MOM];
+    P->n_tmom = (int)tl[LC_TMOM]; P->n_teval = (int)tl[LC_TEVAL];
+    P->local_rc = tl[LC_RC];
+    P->gb_len = ta_[AC_GB]; P->gq_len = ta_[AC_GQ];
+    P->n_tspread = (int)ta_[AC_TSPREAD]; P->n_tinterp = (int)ta_[AC_TINTERP];
+    P->n_fblock = (int)ta_[AC_IFK]; P->n_fsmall = (int)ta_[AC_IFS];
+    P->n_fa = (int)ta_[AC_IFA]; P->n_fb = (int)ta_[AC_IFB];
+    P->asy_rc = ta_[AC_RC]; P->fft_points = ta_[AC_NF2];
+    P->direct_entries = htot[TOT_DIR + DC_ENTRIES];
+    P->max_dir_rows = (int)hmax[MX_DIR_ROWS]; P->max_dir_cols = (int)hmax[MX_DIR_COLS];
+    P->max_dir_area = (int)hmax[MX_DIR_AREA];
+    P->max_nf2_small = (int)hmax[MX_NF2_SMALL];
+    P->has_large_fft = hmax[MX_LARGE] != 0;
+    const int64_t nseg[kLists] = {nl, nl, na, na, ta_[AC_NFS], ta_[AC_NFL], ta_[AC_NFL], ta_[AC_NFK]};
+    const int64_t ntile[kLists] = {tl[LC_TMOM], tl[LC_TEVAL], ta_[AC_TSPREAD], ta_[AC_TINTERP],
+                                   ta_[AC_IFS], ta_[AC_IFA], ta_[AC_IFB], ta_[AC_IFK]};
     P->plan_ms[1] = ms_since(clk);
 
-    // ---- per-block work lists --------------------------------------------
-    const HostTables& T = kernel_tables(P->w);
-    std::vector<LocalBlock> vloc;
-    std::vector<AsyBlock> vasy;
-    std::vector<DirectBlock> vdir;
-    SegList smom, seval, sspread, sinterp, sfs, sfa, sfb, sfk;
-    smom.reserve(LB.size()); seval.reserve(LB.size());
-    sspread.reserve(AB.size()); sinterp.reserve(AB.size()); sfk.reserve(AB.size());
-    vloc.reserve(LB.size());
-    vasy.reserve(AB.size());
-    vdir.reserve(DB.size());
-    P->eval_threads = local_eval_threads(P->ntop_max);
-    int64_t mom_off = 0;
-    for (size_t b = 0; b < LB.size(); ++b) {
-        const HBlock& h = LB[b];
-        const ProbParams& pp = probs[h.prob];
-        LocalBlock lb{};
-        lb.prob = h.prob;
-        lb.k0 = (int32_t)h.k0; lb.k1 = (int32_t)h.k1; lb.j0 = (int32_t)h.j0; lb.j1 = (int32_t)h.j1;
-        lb.R = h.b[1];
-        lb.R_h = (float)lb.R;
-        lb.R_l = (float)(lb.R - (double)lb.R_h);
-        const double iR = lb.R > 0.0 ? 1.0 / lb.R : 0.0;
-        lb.iR_h = (float)iR;
-        lb.iR_l = (float)(iR - (double)lb.iR_h);
-        lb.mom_off = mom_off;
-        mom_off += pp.L + 1;
-        vloc.push_back(lb);
-        smom.add((int32_t)b, h.j0, h.j1, kMomentTile);
-        seval.add((int32_t)b, h.k0, h.k1, P->eval_threads);
-        P->local_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
-    }
-    P->mom_len = mom_off;
-    const int sp_tile = P->opt.spread_tile ? P->opt.spread_tile : spread_tile_points(P->qmax);
-    P->spread_threads = sp_tile;
-    int64_t gb_off = 0, gq_off = 0;
-    for (size_t b = 0; b < AB.size(); ++b) {
-        const HBlock& h = AB[b];
-        const int Q = probs[h.prob].Q;
-        AsyBlock ab{};
-        ab.prob = h.prob;
-        ab.k0 = (int32_t)h.k0; ab.k1 = (int32_t)h.k1; ab.j0 = (int32_t)h.j0; ab.j1 = (int32_t)h.j1;
-        const double rlo = h.b[0], rhi = h.b[1];
-        const double wlo = h.b[2], whi = h.b[3];
-        ab.rc = 0.5 * (rlo + rhi);
-        const double X = 0.5 * (rhi - rlo);
-        ab.wc = 0.5 * (wlo + whi);
-        const double S = 0.5 * (whi - wlo);
-        const double Seff = S > 0.0 ? S : 1.0;
-        ab.h = M_PI / (2.0 * Seff);
-        ab.inv_h = (2.0 / M_PI) * Seff;
-        const double n1f = std::ceil(X * ab.inv_h + 0.5 * P->w) + 1.0;   // one cell of rounding margin
-        if (n1f > (double)(1 << 22)) return NUHT_ERR_UNSUPPORTED;
-        ab.N1 = (int32_t)n1f;
-        const int64_t nf1 = 2 * (int64_t)ab.N1 + 1;
-        int lg = 64 - __builtin_clzll((unsigned long long)(2 * nf1 - 1));   // smallest 2^lg >= 2 nf1
-        if (lg < 5) lg = 5;
-        if (lg > kFftMaxLog2) return NUHT_ERR_UNSUPPORTED;
-        ab.log2nf2 = lg;
-        ab.nf2 = 1 << lg;
-        ab.rho = rlo;
-        ab.alpha = 0.5 * P->w * ab.h;
-        ab.alpha2 = std::ldexp(P->w * M_PI, -lg);
-        ab.inv_delta = ab.nf2 * (0.5 / M_PI);
-        ab.hd = ab.h * ab.inv_delta;
-        ab.rho_h = (float)ab.rho;
-        ab.rho_l = (float)(ab.rho - (double)ab.rho_h);
-        ab.b_off = gb_off;
-        gb_off += nf1 * Q;
-        ab.q_off = gq_off;
-        gq_off += (int64_t)ab.nf2 * Q;
-        vasy.push_back(ab);
-        sspread.add((int32_t)b, h.j0, h.j1, sp_tile);
-        sinterp.add((int32_t)b, h.k0, h.k1, kInterpTile);
-        if ((int64_t)ab.nf2 * Q <= kFftSmemMax) {
-            sfk.add((int32_t)b, 0, 0, 1);                // all Q grids in one CTA
-        } else if (ab.nf2 <= kFftSingleMax) {
-            if (ab.nf2 > P->max_nf2_small) P->max_nf2_small = ab.nf2;
-            sfs.add((int32_t)b, 0, Q - 1, 1);
-        } else {
-            // two passes; each CTA takes a group of lines (see four_step in the kernels)
-            P->has_large_fft = true;
-            const int logN2 = (lg + 1) >> 1, logN1 = lg - logN2;
-            const int lpcA = (kFftLineBatch >> logN2) > 0 ? (kFftLineBatch >> logN2) : 1;
-            const int lpcB = (kFftLineBatch >> logN1) > 0 ? (kFftLineBatch >> logN1) : 1;
-            const int64_t groupsA = ((1 << logN1) + lpcA - 1) / lpcA, groupsB = ((1 << logN2) + lpcB - 1) / lpcB;
-            sfa.add((int32_t)b, 0, (int64_t)Q * groupsA - 1, 1);
-            sfb.add((int32_t)b, 0, (int64_t)Q * groupsB - 1, 1);
-        }
-        P->asy_rc += (h.k1 - h.k0 + 1) + (h.j1 - h.j0 + 1);
-        P->fft_points += ab.nf2;
-    }
-    P->gb_len = gb_off;
-    P->gq_len = gq_off;
-    for (size_t b = 0; b < DB.size(); ++b) {
-        const HBlock& h = DB[b];
-        DirectBlock db{h.prob, (int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, 0};
-        vdir.push_back(db);
-        const int rows = (int)(h.k1 - h.k0 + 1), cols = (int)(h.j1 - h.j0 + 1);
-        if (rows > P->max_dir_rows) P->max_dir_rows = rows;
-        if (cols > P->max_dir_cols) P->max_dir_cols = cols;
-        if (rows * cols > P->max_dir_area) P->max_dir_area = rows * cols;
-        P->direct_entries += (h.k1 - h.k0 + 1) * (h.j1 - h.j0 + 1);
-    }
-    P->n_loc = (int)vloc.size(); P->n_tmom = smom.total(); P->n_teval = seval.total();
-    P->n_asy = (int)vasy.size(); P->n_tspread = sspread.total(); P->n_tinterp = sinterp.total();
-    P->n_fblock = sfk.total(); P->n_fsmall = sfs.total(); P->n_fa = sfa.total(); P->n_fb = sfb.total();
-    P->n_dir = (int)vdir.size();
-
     // ---- one device arena for everything the plan keeps -------------------
+    const HostTables& T = kernel_tables(P->w);
     Arena A;
     size_t a_prob = A.reserve<ProbParams>(probs.size());
-    size_t a_loc = A.reserve<LocalBlock>(vloc.size());
-    size_t a_asy = A.reserve<AsyBlock>(vasy.size());
-    size_t a_dir = A.reserve<DirectBlock>(vdir.size());
     size_t a_es = A.reserve<double>(T.es.size()), a_ph = A.reserve<double>(T.ph.size());
     size_t a_es2 = A.reserve<float2>(T.es2.size()), a_ph2 = A.reserve<float2>(T.ph2.size());
     size_t a_ch2 = A.reserve<float2>(T.ch2.size());
     size_t a_tw = A.reserve<double2>(T.tw.size()), a_tw2 = A.reserve<float4>(T.tw2.size());
-    constexpr int kLists = 8;
-    SegList* lists[kLists] = {&smom, &seval, &sspread, &sinterp, &sfs, &sfa, &sfb, &sfk};
-    size_t a_seg[kLists], a_pre[kLists];
-    for (int i = 0; i < kLists; ++i) {
-        a_seg[i] = A.reserve<Seg>(lists[i]->segs.size());
-        a_pre[i] = A.reserve<int32_t>(lists[i]->prefix.size());
-    }
     size_t host_part = A.size;   // everything above is uploaded from one staging buffer
-    size_t a_tile[kLists];
-    for (int i = 0; i < kLists; ++i) a_tile[i] = A.reserve<Tile>((size_t)lists[i]->total());
+    size_t a_loc = A.reserve<LocalBlock>(nl);
+    size_t a_asy = A.reserve<AsyBlock>(na);
+    size_t a_dir = A.reserve<DirectBlock>(nd);
+    size_t a_blk = A.reserve<SubBlk>(nl + na + nd);
+    size_t a_seg[kLists], a_pre[kLists], a_tile[kLists];
+    for (int i = 0; i < kLists; ++i) {
+        a_seg[i] = A.reserve<Seg>(nseg[i]);
+        a_pre[i] = A.reserve<int32_t>(nseg[i] + 1);
+        a_tile[i] = A.reserve<Tile>(ntile[i]);
+    }
     size_t a_r = A.reserve<double>(n), a_w = A.reserve<double>(m);
     size_t a_pr = A.reserve<int32_t>(n), a_pw = A.reserve<int32_t>(m);
     size_t a_mom = A.reserve<double>((size_t)P->mom_len);
@@ -649,9 +631,6 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         if (bytes) std::memcpy(stage + off, src, bytes);
     };
     put(a_prob, probs.data(), sizeof(ProbParams) * probs.size());
-    put(a_loc, vloc.data(), sizeof(LocalBlock) * vloc.size());
-    put(a_asy, vasy.data(), sizeof(AsyBlock) * vasy.size());
-    put(a_dir, vdir.data(), sizeof(DirectBlock) * vdir.size());
     put(a_es, T.es.data(), sizeof(double) * T.es.size());
     put(a_es2, T.es2.data(), sizeof(float2) * T.es2.size());
     put(a_ch2, T.ch2.data(), sizeof(float2) * T.ch2.size());
@@ -659,20 +638,34 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     put(a_ph2, T.ph2.data(), sizeof(float2) * T.ph2.size());
     put(a_tw, T.tw.data(), sizeof(double2) * T.tw.size());
     put(a_tw2, T.tw2.data(), sizeof(float4) * T.tw2.size());
-    for (int i = 0; i < kLists; ++i) {
-        put(a_seg[i], lists[i]->segs.data(), sizeof(Seg) * lists[i]->segs.size());
-        put(a_pre[i], lists[i]->prefix.data(), sizeof(int32_t) * lists[i]->prefix.size());
-    }
     P->plan_ms[2] = ms_since(clk);
     NUHT_CK(cudaMemcpyAsync(D, stage, host_part, cudaMemcpyHostToDevice, s));
+    {
+        Aux* ax = nullptr;
+        NUHT_CK(aux_stream(&ax));
+        NUHT_CK(cudaEventRecord(ax->stage_done, s));   // the next build waits on it before reusing the buffer
+        g_stage_out_event = ax->stage_done;
+    }
+    BuildLists bl{};
+    bl.loc = (LocalBlock*)(D + a_loc);
+    bl.asy = (AsyBlock*)(D + a_asy);
+    bl.dir = (DirectBlock*)(D + a_dir);
+    bl.blk = (SubBlk*)(D + a_blk);
+    for (int i = 0; i < kLists; ++i) {
+        bl.seg[i] = (Seg*)(D + a_seg[i]);
+        bl.pre[i] = (int32_t*)(D + a_pre[i]);
+    }
+    NUHT_CK(launch_block_fill(bb, bl, s));
     Tile* tiles[kLists];
     for (int i = 0; i < kLists; ++i) {
         tiles[i] = (Tile*)(D + a_tile[i]);
-        NUHT_CK(launch_expand_tiles((const Seg*)(D + a_seg[i]), (const int32_t*)(D + a_pre[i]),
-                                    lists[i]->nseg(), lists[i]->total(), tiles[i], s));
+        NUHT_CK(launch_expand_tiles(bl.seg[i], bl.pre[i], (int)nseg[i], (int)ntile[i], tiles[i], s));
     }
-    P->d_tmom = tiles[0]; P->d_teval = tiles[1]; P->d_tspread = tiles[2]; P->d_tinterp = tiles[3];
-    P->d_fsmall = tiles[4]; P->d_fa = tiles[5]; P->d_fb = tiles[6]; P->d_fblock = tiles[7];
+    P->d_tmom = tiles[LIST_MOM]; P->d_teval = tiles[LIST_EVAL];
+    P->d_tspread = tiles[LIST_SPREAD]; P->d_tinterp = tiles[LIST_INTERP];
+    P->d_fsmall = tiles[LIST_FSMALL]; P->d_fa = tiles[LIST_FA]; P->d_fb = tiles[LIST_FB];
+    P->d_fblock = tiles[LIST_FBLOCK];
+    P->d_blk = bl.blk;
     // sorted arrays and permutations stay on the device
     P->d_r = (double*)(D + a_r); P->d_w = (double*)(D + a_w);
     P->d_pr = (int32_t*)(D + a_pr); P->d_pw = (int32_t*)(D + a_pw);
@@ -685,9 +678,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         NUHT_CK(cudaMemcpyAsync(P->d_pw, pw, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
     }
     P->d_prob = (ProbParams*)(D + a_prob);
-    P->d_loc = (LocalBlock*)(D + a_loc);
-    P->d_asy = (AsyBlock*)(D + a_asy);
-    P->d_dir = (DirectBlock*)(D + a_dir);
+    P->d_loc = bl.loc;
+    P->d_asy = bl.asy;
+    P->d_dir = bl.dir;
     P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
     P->d_mom = (double*)(D + a_mom);
     P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (float4*)(D + a_gt);
@@ -749,8 +742,6 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
     tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
     tb.tw2 = (const float4*)(D + a_tw2);
-    // the staging buffer must outlive the copy
-    NUHT_CK(cudaStreamSynchronize(s));
     P->plan_ms[3] = ms_since(clk);
     return NUHT_OK;
 }
@@ -1092,9 +1083,9 @@ int nuht_info(nuht_plan_t P, nuht_plan_info* out)
     out->eps = P->eps;
     out->n = P->n;
     out->m = P->m;
-    out->n_local = (int64_t)P->hb[0].size();
-    out->n_asy = (int64_t)P->hb[1].size();
-    out->n_direct = (int64_t)P->hb[2].size();
+    out->n_local = P->n_loc;
+    out->n_asy = P->n_asy;
+    out->n_direct = P->n_dir;
     out->direct_entries = P->direct_entries;
     out->local_rows_cols = P->local_rc;
     out->asy_rows_cols = P->asy_rc;
@@ -1107,9 +1098,13 @@ int nuht_info(nuht_plan_t P, nuht_plan_info* out)
 int nuht_get_blocks(nuht_plan_t P, int cls, int64_t* ranges, int64_t cap, int64_t* count)
 {
     if (!P || cls < 0 || cls > 2 || !count || cap < 0 || (cap > 0 && !ranges)) return NUHT_ERR_INVALID_ARG;
-    const auto& v = P->hb[cls];
-    *count = (int64_t)v.size();
+    const int64_t first = cls == 0 ? 0 : (cls == 1 ? P->n_loc : (int64_t)P->n_loc + P->n_asy);
+    *count = cls == 0 ? P->n_loc : (cls == 1 ? P->n_asy : P->n_dir);
     const int64_t nc = cap < *count ? cap : *count;
+    if (nc <= 0) return NUHT_OK;
+    std::vector<SubBlk> v((size_t)nc);
+    NUHT_CK(cudaMemcpyAsync(v.data(), P->d_blk + first, sizeof(SubBlk) * nc, cudaMemcpyDeviceToHost, P->stream));
+    NUHT_CK(cudaStreamSynchronize(P->stream));
     for (int64_t i = 0; i < nc; ++i) {
         ranges[4 * i + 0] = v[(size_t)i].k0;
         ranges[4 * i + 1] = v[(size_t)i].k1;

@@ -300,3 +300,34 @@ def test_autotuner_picks_valid_fast_options():
 def test_option_variants_keep_accuracy(opts):
     r, omega, c = uniform_problem(1500, 1400, omega_max=2500.0, seed=91)
     _check(1, r, omega, c, 1e-10, **opts)
+
+
+def test_host_subdivision_fallback_matches(monkeypatch):
+    """Device block lists over capacity: the plan falls back to the host walk
+    of Algorithm 1 and builds the same transform."""
+    r, omega, c = uniform_problem(2500, 2300, omega_max=3000.0, seed=11)
+    g0, info0, b0 = run_forward(2, r, omega, c, 1e-9)
+    monkeypatch.setenv("NUHT_SUBDIVIDE_CAPACITY", "16")
+    g1, info1, b1 = run_forward(2, r, omega, c, 1e-9)
+    for x, y in zip(b0, b1):
+        assert sorted(map(tuple, x.tolist())) == sorted(map(tuple, y.tolist()))
+    assert max(len(x) for x in b1) > 16          # the fallback was needed
+    assert np.max(np.abs(g0 - g1)) <= 1e-12 * np.abs(c).sum()
+
+
+def test_batched_host_subdivision_fallback_matches(monkeypatch):
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import batch_problems
+    probs = batch_problems(count=5, lo=300, hi=1500, nu_max=4, seed=21)
+    nus = [q[0] for q in probs]
+    n = [q[1].size for q in probs]
+    m = [q[2].size for q in probs]
+    dr = to_dev(np.concatenate([q[1] for q in probs]))
+    dw = to_dev(np.concatenate([q[2] for q in probs]))
+    cc = np.concatenate([q[3] for q in probs])
+    with Plan.many(nus, dr, n, dw, m, 1e-8) as p:
+        g0 = p.execute(to_dev(cc)).cpu().numpy()
+    monkeypatch.setenv("NUHT_SUBDIVIDE_CAPACITY", "8")
+    with Plan.many(nus, dr, n, dw, m, 1e-8) as p:
+        g1 = p.execute(to_dev(cc)).cpu().numpy()
+    assert np.max(np.abs(g0 - g1)) <= 1e-12 * np.abs(cc).sum()
