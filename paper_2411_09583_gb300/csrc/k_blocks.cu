@@ -133,52 +133,102 @@ __global__ void k_block_sizes(BlockBuild bb)
     }
 }
 
-// Exclusive prefix sums of the columns of mat[n][ncol] in place (one CTA);
-// totals[c] = sum of column c.  Each thread scans a contiguous chunk.
-constexpr int kScanThreads = 1024;
-__device__ void scan_columns(int64_t* mat, int64_t n, int ncol, int64_t* totals)
+// Exclusive prefix sums of the columns of the three counter matrices
+// (row-major, rows = blocks) in place, and the column totals: tile sums (one
+// CTA per kScanTile rows), one CTA over the tile sums, then each tile again
+// with its offset.  blockIdx.y picks the matrix.
+constexpr int kScanTile = 256;
+
+struct ScanMat {
+    int64_t* mat;
+    int64_t n;
+    int ncol;
+    int64_t* totals;
+};
+
+__device__ __forceinline__ ScanMat scan_mat(const BlockBuild& bb, int which)
 {
-    __shared__ int64_t wsum[kScanThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
-    const int64_t r0 = tid * chunk, r1 = (r0 + chunk < n) ? r0 + chunk : n;
-    for (int c = 0; c < ncol; ++c) {
-        int64_t sum = 0;
-        for (int64_t r = r0; r < r1; ++r) sum += mat[r * ncol + c];
-        int64_t x = sum;
+    if (which == 0) return ScanMat{bb.lcnt, clamp_count(bb.res[0], bb.ocap), kLocalCols, bb.totals + TOT_LOCAL};
+    if (which == 1) return ScanMat{bb.acnt, clamp_count(bb.res[1], bb.ocap), kAsyCols, bb.totals + TOT_ASY};
+    return ScanMat{bb.dcnt, clamp_count(bb.res[2], bb.ocap), kDirCols, bb.totals + TOT_DIR};
+}
+
+// block-wide inclusive scan of one value per thread (kScanTile threads)
+__device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t* wsum, int64_t* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t s = lane < kScanTile / 32 ? wsum[lane] : 0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, x, off);
-            if (lane >= off) x += y;
+            const int64_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
         }
-        if (lane == 31) wsum[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            int64_t s = wsum[lane];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int64_t y = __shfl_up_sync(0xffffffffu, s, off);
-                if (lane >= off) s += y;
-            }
-            wsum[lane] = s;
-        }
-        __syncthreads();
-        int64_t run = (wid > 0 ? wsum[wid - 1] : 0) + x - sum;
-        for (int64_t r = r0; r < r1; ++r) {
-            const int64_t v = mat[r * ncol + c];
-            mat[r * ncol + c] = run;
-            run += v;
-        }
-        if (tid == kScanThreads - 1) totals[c] = wsum[kScanThreads / 32 - 1];
-        __syncthreads();
+        if (lane < kScanTile / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    const int64_t r = x + (wid > 0 ? wsum[wid - 1] : 0);
+    *total = wsum[kScanTile / 32 - 1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_tiles(BlockBuild bb, int64_t* part, int64_t ptiles)
+{
+    __shared__ int64_t wsum[kScanTile / 32];
+    const ScanMat S = scan_mat(bb, blockIdx.y);
+    const int64_t row = blockIdx.x * (int64_t)kScanTile + threadIdx.x;
+    if ((int64_t)blockIdx.x * kScanTile >= S.n) return;   // whole CTA
+    for (int c = 0; c < S.ncol; ++c) {
+        int64_t tot;
+        block_incl_scan(row < S.n ? S.mat[row * S.ncol + c] : 0, wsum, &tot);
+        if (threadIdx.x == 0) part[((int64_t)blockIdx.y * ptiles + blockIdx.x) * kAsyCols + c] = tot;
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_block_scan(BlockBuild bb)
+__global__ void __launch_bounds__(kScanTile) k_scan_top(BlockBuild bb, int64_t* part, int64_t ptiles)
 {
-    scan_columns(bb.lcnt, clamp_count(bb.res[0], bb.ocap), kLocalCols, bb.totals + TOT_LOCAL);
-    scan_columns(bb.acnt, clamp_count(bb.res[1], bb.ocap), kAsyCols, bb.totals + TOT_ASY);
-    scan_columns(bb.dcnt, clamp_count(bb.res[2], bb.ocap), kDirCols, bb.totals + TOT_DIR);
+    __shared__ int64_t wsum[kScanTile / 32];
+    for (int which = 0; which < 3; ++which) {
+        const ScanMat S = scan_mat(bb, which);
+        const int64_t nt = (S.n + kScanTile - 1) / kScanTile;
+        for (int c = 0; c < S.ncol; ++c) {
+            int64_t carry = 0;
+            for (int64_t t0 = 0; t0 < nt; t0 += kScanTile) {
+                const int64_t t = t0 + threadIdx.x;
+                int64_t* pp = part + ((int64_t)which * ptiles + t) * kAsyCols + c;
+                const int64_t v = t < nt ? *pp : 0;
+                int64_t tot;
+                const int64_t incl = block_incl_scan(v, wsum, &tot);
+                if (t < nt) *pp = carry + incl - v;   // exclusive offset of the tile
+                carry += tot;
+            }
+            if (threadIdx.x == 0) S.totals[c] = carry;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_apply(BlockBuild bb, const int64_t* part, int64_t ptiles)
+{
+    __shared__ int64_t wsum[kScanTile / 32];
+    const ScanMat S = scan_mat(bb, blockIdx.y);
+    const int64_t row = blockIdx.x * (int64_t)kScanTile + threadIdx.x;
+    if ((int64_t)blockIdx.x * kScanTile >= S.n) return;
+    for (int c = 0; c < S.ncol; ++c) {
+        const int64_t v = row < S.n ? S.mat[row * S.ncol + c] : 0;
+        int64_t tot;
+        const int64_t incl = block_incl_scan(v, wsum, &tot);
+        if (row < S.n)
+            S.mat[row * S.ncol + c] = part[((int64_t)blockIdx.y * ptiles + blockIdx.x) * kAsyCols + c] + incl - v;
+    }
 }
 
 __device__ __forceinline__ void put_seg(const BuildLists& L, int list, int64_t idx, int32_t blk, int32_t len,
@@ -251,13 +301,21 @@ __global__ void k_block_fill(BlockBuild bb, BuildLists L)
 
 }  // namespace
 
-cudaError_t launch_block_build(const BlockBuild& bb, cudaStream_t s)
+int64_t block_scan_scratch(int64_t cap) { return 3 * ((cap + kScanTile - 1) / kScanTile) * kAsyCols; }
+
+cudaError_t launch_block_build(const BlockBuild& bb, int64_t* scratch, cudaStream_t s)
 {
     k_block_sizes<<<152 * 8, 256, 0, s>>>(bb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_block_scan<<<1, kScanThreads, 0, s>>>(bb);
-    count_launches(2);
+    const int64_t ptiles = (bb.ocap + kScanTile - 1) / kScanTile;
+    if (ptiles > 0) {
+        const dim3 grid((unsigned)ptiles, 3);
+        k_scan_tiles<<<grid, kScanTile, 0, s>>>(bb, scratch, ptiles);
+        k_scan_top<<<1, kScanTile, 0, s>>>(bb, scratch, ptiles);
+        k_scan_apply<<<grid, kScanTile, 0, s>>>(bb, scratch, ptiles);
+    }
+    count_launches(4);
     return cudaGetLastError();
 }
 

@@ -133,7 +133,8 @@ struct BuildLists {
     SubBlk* blk;              // [nl + na + nd] every block in global sorted indices
 };
 
-cudaError_t launch_block_build(const BlockBuild& bb, cudaStream_t s);
+int64_t block_scan_scratch(int64_t cap);   // int64 elements of scratch for launch_block_build
+cudaError_t launch_block_build(const BlockBuild& bb, int64_t* scratch, cudaStream_t s);
 cudaError_t launch_block_fill(const BlockBuild& bb, const BuildLists& L, cudaStream_t s);
 
 // Kernel tables shared by every asymptotic block of a plan.

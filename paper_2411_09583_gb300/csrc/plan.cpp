@@ -335,7 +335,7 @@ static double ms_since(std::chrono::steady_clock::time_point& t)
 
 // Temporaries of the device work-list build (offsets into an arena).
 struct BuildTemps {
-    size_t loc, asy, dir, fcls, lcnt, acnt, dcnt, tot, maxv;
+    size_t loc, asy, dir, fcls, lcnt, acnt, dcnt, tot, maxv, scan;
 };
 
 static BuildTemps reserve_build_temps(Arena& a, int64_t cap)
@@ -350,6 +350,7 @@ static BuildTemps reserve_build_temps(Arena& a, int64_t cap)
     t.dcnt = a.reserve<int64_t>(cap * kDirCols);
     t.tot = a.reserve<int64_t>(kTotals);
     t.maxv = a.reserve<int64_t>(kMaxv);
+    t.scan = a.reserve<int64_t>(block_scan_scratch(cap));
     return t;
 }
 
@@ -488,6 +489,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     bb.spread_tile = sp_tile;
     bb.interp_tile = kInterpTile;
     bind_build_temps(bb, sort_mem, bt);
+    int64_t* bb_scan = (int64_t*)(sort_mem + bt.scan);
     char* tmp_mem = nullptr;   // temporaries of the host fallback
     struct FreeTmp {
         char** p; cudaStream_t s;
@@ -495,7 +497,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     } free_tmp{&tmp_mem, s};
     NUHT_CK(cudaMemsetAsync(bb.totals, 0, sizeof(int64_t) * (kTotals + 0), s));
     NUHT_CK(cudaMemsetAsync(bb.maxv, 0, sizeof(int64_t) * kMaxv, s));
-    NUHT_CK(launch_block_build(bb, s));
+    NUHT_CK(launch_block_build(bb, bb_scan, s));
     // the one wait of the build: flags, counts, totals and maxima to the host
     const size_t o_hf = 0, o_hr = 64, o_ht = o_hr + 64, o_hm = o_ht + align256(sizeof(int64_t) * kTotals);
     NUHT_CK(g_stage_in.reserve(o_hm + 256));
@@ -566,9 +568,10 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         bb.bl = (const double*)(tmp_mem + t_bl);
         bb.ba = (const double4*)(tmp_mem + t_ba);
         bind_build_temps(bb, tmp_mem, tt);
+        bb_scan = (int64_t*)(tmp_mem + tt.scan);
         NUHT_CK(cudaMemsetAsync(bb.totals, 0, sizeof(int64_t) * kTotals, s));
         NUHT_CK(cudaMemsetAsync(bb.maxv, 0, sizeof(int64_t) * kMaxv, s));
-        NUHT_CK(launch_block_build(bb, s));
+        NUHT_CK(launch_block_build(bb, bb_scan, s));
         NUHT_CK(fetch_results());   // (the upload buffer lives until here)
     }
     if (hmax[MX_ERR]) return NUHT_ERR_UNSUPPORTED;
