@@ -229,22 +229,29 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel, workload, opts=None):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel, the
-    workload and the plan options are those of the capture."""
+def stored_traffic(kernel, workload, opts=None, units=None):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, if its
+    sources are unchanged: as captured when the plan options are those of the
+    capture, else scaled by the units the launch processes.  Returns (bytes,
+    basis) or (None, reason)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
-        return None
+        return None, "no capture"
     try:
         db = json.load(open(path))
         ent = db.get(kernel)
-        if not ent or ent.get("workload") != workload or ent.get("opts", {}) != (opts or {}):
-            return None
+        if not ent or ent.get("workload") != workload:
+            return None, "no capture of this kernel and workload"
         if ent.get("source_hash") != source_hash(*ent.get("sources", [])):
-            return None
-        return ent.get("bytes_per_launch")
-    except Exception:
-        return None
+            return None, "kernel changed since the capture"
+        if ent.get("opts", {}) == (opts or {}):
+            return ent.get("bytes_per_launch"), "ncu capture of this launch configuration"
+        if units and ent.get("units_per_launch"):
+            return (ent["bytes_per_launch"] * units / ent["units_per_launch"],
+                    "ncu capture at options %s scaled by units processed" % ent.get("opts"))
+        return None, "captured at other options"
+    except Exception as e:
+        return None, "unreadable capture (%s)" % e
 
 
 def run_batched(dev, steps):
@@ -508,7 +515,8 @@ def run_ours(a):
 
     # dominant kernel and its roofline (FP64 ALU bound)
     mean_stage = {k: sum(v) / len(v) for k, v in stage_ms.items()}
-    dom = max(mean_stage, key=mean_stage.get)
+    rated = ("asy_spread", "asy_interp", "local_moments", "local_eval", "direct")
+    dom = max((k for k in mean_stage if k in rated), key=mean_stage.get)
     tab = {"w": info["nufft_width"], "deg": info["nufft_degree"]}
     flops, units = _dominant_flops(dom, info, blocks, tab)
     kernel_of = {"asy_spread": "k_asy_spread", "asy_interp": "k_asy_interp",
@@ -525,9 +533,10 @@ def run_ours(a):
                                "per compensated multiply-add x 2 FLOP (native FP64 pipe: "
                                "%.3f TFLOP/s)" % FP64_PEAK_TFLOPS,
                 "algorithmic_flops_per_launch": flops, "units_per_launch": units,
-                "launch_ms": mean_stage[dom],
-                "traffic": stored_traffic(kernel_of.get(dom, dom),
-                                          workload_config(a)["workload"], opts)}
+                "launch_ms": mean_stage[dom]}
+        tr, basis = stored_traffic(kernel_of.get(dom, dom), workload_config(a)["workload"], opts, units)
+        roof["traffic"] = tr
+        roof["traffic_basis"] = basis
 
     extra_batched = extra_mixed = extra_grad = None
     if not a.no_extra and ws == 1:
