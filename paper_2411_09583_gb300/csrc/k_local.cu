@@ -94,13 +94,48 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
 // (double-float); returns the normalisation S = J_0 + 2 sum_k J_2k of the same
 // scale.  Miller's backward recurrence from ns (even), rescaled by 2^-60
 // whenever a value passes 2^60.  Needs y >= 1 (growth per step <= 2 ns / y).
+// Steps above both the highest order needed and the turning point (n > y)
+// run in FP32: there the recurrence damps any perturbation relative to J_n
+// (it acts like a change of the arbitrary start values), so only the steps
+// that produce the returned values need double-float.
+__device__ __forceinline__ int miller_fp32_floor(int ntop, float y)
+{
+    const int t = (int)(y + 8.f + 2.f * sqrtf(y)) + 1;
+    return (t > ntop + 2 ? t : ntop + 2);
+}
+
+// FP32 steps of Miller's recurrence from ns down to (above) lo; returns the
+// state (J_{i+1}, J_i, S) and the next index i.
+__device__ __forceinline__ int miller_fp32_head(int ns, int lo, float ih, float* jp1, float* jc, float* S)
+{
+    float fp1 = 0.f, fc = 1.f, fS = 2.f;
+    int i = ns;
+    for (; i - 2 >= lo; i -= 2) {
+        const float fm = fmaf((float)i * ih, fc, -fp1);
+        const float fmm = fmaf((float)(i - 1) * ih, fm, -fc);
+        fS = fmaf(2.f, fmm, fS);
+        fp1 = fm;
+        fc = fmm;
+        if (fabsf(fc) > 1.152921504606847e18f) {
+            const float sc = 8.673617379884035e-19f;   // 2^-60
+            fc *= sc; fp1 *= sc; fS *= sc;
+        }
+    }
+    *jp1 = fp1;
+    *jc = fc;
+    *S = fS;
+    return i;
+}
+
 __device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb, int nt, int tid)
 {
     const df iy = df_recip(y);
     const float ih = 2.f * iy.h, il = 2.f * iy.l;   // 2 / y
-    df jp1{0.f, 0.f}, jc{1.f, 0.f}, S{2.f, 0.f};
-    if (ns <= ntop) jb[ns * nt + tid] = make_float2(jc.h, jc.l);
-    for (int i = ns; i >= 2; i -= 2) {
+    float f1, f0, fS;
+    const int i0 = miller_fp32_head(ns, miller_fp32_floor(ntop, y.h), ih, &f1, &f0, &fS);
+    df jp1{f1, 0.f}, jc{f0, 0.f}, S{fS, 0.f};
+    if (i0 <= ntop) jb[i0 * nt + tid] = make_float2(jc.h, jc.l);
+    for (int i = i0; i >= 2; i -= 2) {
         const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
         const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
         if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = make_float2(jm.h, jm.l);
@@ -111,7 +146,7 @@ __device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb
         if (df_big(jc)) {
             const float sc = 8.673617379884035e-19f;   // 2^-60
             jc = df_scale(jc, sc); jp1 = df_scale(jp1, sc); S = df_scale(S, sc);
-            const int top = ntop < ns ? ntop : ns;
+            const int top = ntop < i0 ? ntop : i0;
             for (int q = i - 2; q <= top; ++q) {
                 const float2 v = jb[q * nt + tid];
                 jb[q * nt + tid] = make_float2(v.x * sc, v.y * sc);
@@ -206,8 +241,10 @@ __device__ __forceinline__ double jn_miller_df(int n, double x)
     const int ns = miller_start(n, x);
     const double inv2x = 2.0 / x;
     const float ih = (float)inv2x, il = (float)(inv2x - (double)ih);
-    df jp1{0.f, 0.f}, jc{1.f, 0.f}, S{2.f, 0.f}, res{0.f, 0.f};
-    for (int i = ns; i >= 2; i -= 2) {
+    float f1, f0, fS;
+    const int i0 = miller_fp32_head(ns, miller_fp32_floor(n, (float)x), ih, &f1, &f0, &fS);
+    df jp1{f1, 0.f}, jc{f0, 0.f}, S{fS, 0.f}, res{0.f, 0.f};
+    for (int i = i0; i >= 2; i -= 2) {
         const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
         const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
         if (i - 1 == n) res = jm;
