@@ -116,14 +116,15 @@ __device__ inline float jn_hankel_f32(const ProbParams& P, double w, double r)
         case 2: sx = -s0; cx = -c0; break;
         default: sx = -c0; cx = s0; break;
     }
-    const float y = (float)(1.0 / p), y2 = y * y;
+    const float y = (float)(1.0 / p);
+    const float u = y * P.z2.x, u2 = u * u;   // z / x < 1, with the coefficients a_q z^-q
     float pp = 0.f, qq = 0.f;
     for (int l = P.M - 1; l >= 0; --l) {
         const float sg = (l & 1) ? -1.f : 1.f;
-        pp = fmaf(pp, y2, sg * (float)P.a[2 * l]);
-        qq = fmaf(qq, y2, sg * (float)P.a[2 * l + 1]);
+        pp = fmaf(pp, u2, sg * P.a2[2 * l].x);
+        qq = fmaf(qq, u2, sg * P.a2[2 * l + 1].x);
     }
-    qq *= y;
+    qq *= u;
     const float cph = (float)P.cphi, sph = (float)P.sphi;
     const float cchi = cx * cph - sx * sph, schi = sx * cph + cx * sph;
     return sqrtf(0.6366197723675814f * y) * (pp * cchi - qq * schi);

@@ -850,6 +850,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const float2* Hb = H + (t0 - wstart) * hs;
     const float2 wk2 = w2[k];
     const df m1d = df_recip(df_mul(df{wk2.x, wk2.y}, df{B.rho_h, B.rho_l}));   // 1/(omega rho) < 1/z
+    const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});                               // z/(omega rho) < 1
     // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
     acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
     df mq{1.f, 0.f};
@@ -922,7 +923,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
             case 2: acc_fma(tr, df{-cq.h, -cq.l}, prd); acc_fma(ti, df{-cq.h, -cq.l}, pid); break;
             default: acc_fma(tr, cq, pid); acc_fma(ti, df{-cq.h, -cq.l}, prd); break;
         }
-        mq = df_mul(mq, m1d);
+        mq = df_mul(mq, mz);
     }
     df sn, cs;
     df_sincos_prod(wk, B.rc, &sn, &cs);
@@ -986,6 +987,7 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
         t0s[tid] = (int)tf;
         // g_k sqrt(2/pi) (4/w^2) / psi^(alpha s) (omega rho)^(-1/2) e^{i (omega r_c + phi)}
         const df m1d = df_recip(df_from(wk * B.rho));
+        const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});
         df sn, cs;
         df_sincos_prod(wk, B.rc, &sn, &cs);
         const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
@@ -1008,7 +1010,7 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
             ur = df_mul(ur, cq);
             ui = df_mul(ui, cq);
             uval[tid * Q + q] = make_float4(ur.h, ur.l, ui.h, ui.l);
-            mq = df_mul(mq, m1d);
+            mq = df_mul(mq, mz);
         }
     }
     __syncthreads();
@@ -1501,7 +1503,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
             case 2: tr = fmaf(-cq, pr, tr); ti = fmaf(-cq, pi, ti); break;
             default: tr = fmaf(cq, pi, tr); ti = fmaf(-cq, pr, ti); break;
         }
-        mq *= m1;
+        mq *= m1 * P.z2.x;
     }
     float sn, cs;
     f32_sincos_prod(wk, B.rc, &sn, &cs);

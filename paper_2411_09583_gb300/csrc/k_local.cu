@@ -271,15 +271,17 @@ __device__ __forceinline__ double jn_hankel_df(const ProbParams& P, double w, do
     const float ph = (float)p;
     const df x = fast_two_sum(ph, (float)(p - (double)ph) + (float)e);
     const df y = df_recip(x);
-    const df y2 = df_mul(y, y);
+    // the series in u = z / x (< 1) with the coefficients a_q z^-q
+    const df u = df_mul(y, df{P.z2.x, P.z2.y});
+    const df u2 = df_mul(u, u);
     df pp{0.f, 0.f}, qq{0.f, 0.f};
     for (int l = P.M - 1; l >= 0; --l) {
         const float2 a0 = P.a2[2 * l], a1 = P.a2[2 * l + 1];
         const bool neg = l & 1;
-        pp = df_add(df_mul(pp, y2), neg ? df{-a0.x, -a0.y} : df{a0.x, a0.y});
-        qq = df_add(df_mul(qq, y2), neg ? df{-a1.x, -a1.y} : df{a1.x, a1.y});
+        pp = df_add(df_mul(pp, u2), neg ? df{-a0.x, -a0.y} : df{a0.x, a0.y});
+        qq = df_add(df_mul(qq, u2), neg ? df{-a1.x, -a1.y} : df{a1.x, a1.y});
     }
-    qq = df_mul(qq, y);
+    qq = df_mul(qq, u);
     df sx, cx;
     df_sincos_prod(w, r, &sx, &cx);
     const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
@@ -527,13 +529,24 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
                                  double* mom, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(acc2) * (size_t)(lmax + 1) * kMomThreads;
+    const int threads = local_moment_threads(lmax);
+    size_t smem = sizeof(acc2) * (size_t)(lmax + 1) * threads;
     cudaError_t e = cudaFuncSetAttribute(k_local_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_moments<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r2, c2, mom);
+    k_local_moments<<<ntiles, threads, smem, s>>>(probs, blks, tiles, r2, c2, mom);
     count_launches(1);
     return cudaGetLastError();
+}
+
+int local_moment_threads(int lmax)
+{
+    // (lmax + 1) 8-byte accumulators per thread must fit in ~200 KB of shared memory
+    int t = (int)(200 * 1024 / (8 * (lmax + 1)));
+    t = (t / 32) * 32;
+    if (t > kMomThreads) t = kMomThreads;
+    if (t < 32) t = 32;
+    return t;
 }
 
 int local_eval_threads(int ntop_max)

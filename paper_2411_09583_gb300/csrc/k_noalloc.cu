@@ -191,13 +191,14 @@ extern "C" int nuht_local_apply_noalloc(int nu, double eps, const double* r, int
     const double R = r_max > 0.0 ? r_max : 1.0;   // any R >= max r_j with omega_max R <= z
     const double Rm = (r_max > 0.0) ? r_max : 0.0;
     {
-        const size_t smem = sizeof(double) * (size_t)(L + 1) * kNoallocThreads;
+        const int threads = local_moment_threads(L);   // (L + 1) doubles per thread
+        const size_t smem = sizeof(double) * (size_t)(L + 1) * threads;
         e = cudaFuncSetAttribute(k_noalloc_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return NUHT_ERR_CUDA;
-        int64_t blocks = (n + kNoallocThreads - 1) / kNoallocThreads;
+        int64_t blocks = (n + threads - 1) / threads;
         if (blocks > 152 * 8) blocks = 152 * 8;
         dim3 grid((unsigned)blocks, (unsigned)nvec);
-        k_noalloc_moments<<<grid, kNoallocThreads, smem, s>>>(anu, L, r, n, Rm > 0.0 ? 1.0 / R : 0.0,
+        k_noalloc_moments<<<grid, threads, smem, s>>>(anu, L, r, n, Rm > 0.0 ? 1.0 / R : 0.0,
                                                               c, nvec, mom);
         e = cudaGetLastError();
         if (e != cudaSuccess) return NUHT_ERR_CUDA;

@@ -16,7 +16,8 @@ constexpr int kMaxM = 20;           // Hankel term pairs (Sec. 3.3 caps M at 20)
 constexpr int kMaxQ = 2 * kMaxM;    // weight powers q = 0..2M-1
 constexpr int kMaxW = 16;           // ES kernel width
 constexpr int kMaxDeg = 20;         // degree of the kernel piece polynomials
-constexpr int kMaxNtop = 256;       // largest Bessel index kept by the local evaluation
+constexpr int kMaxNtop = 400;       // largest Bessel index kept by the local evaluation
+                                    // (the transposed moments then stay within 205 KB of shared memory)
 constexpr int kFftSmemMax = 4096;   // points of all Q grids of a block FFT'd by one CTA
 constexpr int kFftSingleMax = 8192; // largest single-grid FFT done by one CTA (128 KiB)
 constexpr int kFftLineBatch = 4096; // points per CTA in the passes of a two-pass FFT
@@ -33,7 +34,8 @@ struct ProbParams {
     double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
     float2 cphi2, sphi2;         // the same as double-float
     double a[kMaxQ];             // Hankel coefficients a_q(nu), q < Q
-    float2 a2[kMaxQ];            // the same as double-float (hi, lo)
+    float2 a2[kMaxQ];            // a_q z^-q as double-float (in FP32 range for every order)
+    float2 z2;                   // z as double-float
     int64_t r_off, w_off;        // offsets of this problem in the sorted arrays
     int64_t n, m;
     int64_t c_off, g_off;        // offsets of this problem's c and g (batched)
@@ -190,6 +192,7 @@ cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                  int ntiles, int lmax, const float2* r2, const float2* c2,
                                  double* mom, cudaStream_t s);
+int local_moment_threads(int lmax);
 int local_eval_threads(int ntop_max);
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                               int ntiles, int ntop_max, int threads, const float2* w2,

@@ -781,10 +781,18 @@ static int init_problem(ProbParams& pp, int nu, double eps, int m_terms, int64_t
         if (std::fabs(hankel_coeff(q, anu)) * std::pow(pp.z, -q) * 1e-6 <= 1e-2 * eps) pp.qs = q;
         else break;
     }
+    // the kernels sum a_q (omega rho)^-q as (a_q z^-q) (z / (omega rho))^q: the
+    // first factor stays in the FP32 range of the double-float parts (a_q alone
+    // does not for large orders), the second is at most one
     for (int q = 0; q < kMaxQ; ++q) {
         pp.a[q] = q < pp.Q ? hankel_coeff(q, anu) : 0.0;
-        const float hi = (float)pp.a[q];
-        pp.a2[q] = make_float2(hi, (float)(pp.a[q] - (double)hi));
+        const double as = pp.a[q] * std::pow(pp.z, -q);
+        const float hi = (float)as;
+        pp.a2[q] = make_float2(hi, (float)(as - (double)hi));
+    }
+    {
+        const float zh = (float)pp.z;
+        pp.z2 = make_float2(zh, (float)(pp.z - (double)zh));
     }
     pp.r_off = r_off; pp.w_off = w_off; pp.n = n; pp.m = m; pp.c_off = r_off; pp.g_off = w_off;
     return NUHT_OK;

@@ -29,6 +29,17 @@ def test_adjoint_matches_oracle_transpose(nu):
     assert np.max(np.abs(ca - ref)) <= tol(eps, e)
 
 
+@pytest.mark.parametrize("nu,eps", [(50, 1e-8), (100, 1e-6), (100, 1e-12), (20, 1e-14)])
+def test_adjoint_extreme_orders(nu, eps):
+    """High orders (Hankel coefficients beyond the FP32 range unless scaled,
+    Bessel indices above 256) through the transposed block kernels."""
+    r, omega, _ = uniform_problem(1100, 1000, omega_max=3000.0 + 30 * nu, seed=90 + nu)
+    e = np.random.default_rng(91 + nu).standard_normal(omega.size)
+    ca, _ = _adjoint(nu, r, omega, e, eps)
+    ref = oracle.direct(nu, omega, r, e)
+    assert np.max(np.abs(ca - ref)) <= tol(eps, e)
+
+
 @pytest.mark.parametrize("nu", [0, 3])
 def test_dot_product_identity(nu):
     # <A c, e> = <c, A^T e> for the approximate operator itself (exact transpose)

@@ -48,6 +48,15 @@ def test_orders(nu):
     _check(nu, r, omega, c, 1e-10)
 
 
+@pytest.mark.parametrize("nu,eps,opts", [(50, 1e-8, {}), (100, 1e-6, {}), (100, 1e-12, {}), (0, 1e-10, {"m_terms": 20}),
+                                         (3, 1e-2, {}), (0, 1e-3, {}), (20, 1e-14, {})])
+def test_extreme_orders_terms_and_tolerances(nu, eps, opts):
+    """Orders up to the supported 100, the largest number of Hankel terms
+    (2M = 40), and the loosest / tightest tolerances."""
+    r, omega, c = uniform_problem(1100, 1000, omega_max=3000.0 + 30 * nu, seed=300 + nu)
+    _check(nu, r, omega, c, eps, **opts)
+
+
 @pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9, 1e-12, 1e-14])
 def test_tolerances(eps):
     r, omega, c = uniform_problem(1200, 1250, omega_max=2500.0, seed=7)
@@ -251,7 +260,7 @@ def test_batched_edge_problems():
         assert np.max(np.abs(gi - ref), initial=0.0) <= 10 * 1e-9 * max(np.abs(cc).sum(), 1e-300)
 
 
-@pytest.mark.parametrize("nu", [0, 1, 4])
+@pytest.mark.parametrize("nu", [0, 1, 4, 20])
 def test_mixed_precision_small(nu):
     # FP32 spreading / interpolation at eps = 1e-5 (and 1e-6) against the FP64 oracle
     r, omega, c = loguniform_problem(3000, 2500, omega_max=4e4, seed=50 + nu, complex_c=True)

@@ -51,7 +51,8 @@ def test_no_alloc_matches_planned_path_twice():
     from paper_2411_09583_gb300 import choose_params
     L = _lib()
     rng = np.random.default_rng(2024)
-    cases = [(0, 1e-12, 6000, 5000, 1), (3, 1e-9, 1700, 2300, 3)]
+    # the last case reaches Bessel index 375 (order 100 at 1e-12)
+    cases = [(0, 1e-12, 6000, 5000, 1), (3, 1e-9, 1700, 2300, 3), (100, 1e-12, 900, 800, 2)]
     for nu, eps, n, m, nvec in cases:
         M, z, Lw = choose_params(nu, eps)
         r = rng.uniform(0.0, 1.0, n)
