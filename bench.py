@@ -408,6 +408,48 @@ def run_grad(dev, steps):
             "step": "plan + forward + adjoint (dL/dc) + plans and adjoints of orders nu-1, nu+1 (dL/dr)"}
 
 
+def run_stress(dev, steps):
+    """Sec. 5.1.1's cases with p = O(n), nu = 0, eps = 1e-8, n = m: the
+    Fourier-Bessel grid and the exponential grid (the subdivision's worst
+    case), plan + execute at n = 1e4, 1e5, 1e6 (the scaling with n of the
+    paper's timing study), library default options."""
+    import numpy as np
+    import torch
+
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import exponential_grid, fourier_bessel_grid
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "nu = 0, eps 1e-8, n = m, Fourier-Bessel and exponential grids, c ~ N(0,1)",
+           "unit": UNIT, "step": "plan + execute"}
+    for name, grid in (("fourier_bessel", lambda n: fourier_bessel_grid(0, n)), ("exponential", exponential_grid)):
+        res = {}
+        for n in (10_000, 100_000, 1_000_000):
+            r, omega = grid(n)
+            c = np.random.default_rng(8).standard_normal(n)
+            dr, dw, c = (torch.tensor(x, device=dev) for x in (r, omega, c))
+            for _ in range(2):
+                with Plan(0, dr, dw, 1e-8) as p:
+                    p.execute(c)
+            ms = []
+            for _ in range(max(3, steps // 4)):
+                flush.zero_()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                p = Plan(0, dr, dw, 1e-8)
+                p.execute(c)
+                s1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(s0.elapsed_time(s1))
+                info = p.info()
+                p.close()
+            t = statistics.median(ms)
+            res["%.0e" % n] = {"ms_per_step": t, "value": 2 * n / (t * 1e-3),
+                               "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]]}
+        out[name] = res
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -546,11 +588,12 @@ def run_ours(a):
         roof["traffic"] = tr
         roof["traffic_basis"] = basis
 
-    extra_batched = extra_mixed = extra_grad = None
+    extra_batched = extra_mixed = extra_grad = extra_stress = None
     if not a.no_extra and ws == 1:
         extra_batched = run_batched(dev, a.steps)
         extra_mixed = run_mixed(dev, a.steps)
         extra_grad = run_grad(dev, a.steps)
+        extra_stress = run_stress(dev, a.steps)
 
     line = None
     if rank == 0:
@@ -580,6 +623,7 @@ def run_ours(a):
                 "batched": extra_batched,
                 "mixed_precision": extra_mixed,
                 "differentiation": extra_grad,
+                "stress": extra_stress,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],

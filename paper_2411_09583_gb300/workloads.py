@@ -2,7 +2,7 @@
 
 Holds no arithmetic of the transform itself: only the random draws that
 stand in for the paper's synthetic experiments (Sec. 5.1: uniform,
-clustered and exponential point sets).  Draw order is r, omega, c (for a
+clustered, exponential and Fourier-Bessel point sets, sparse coefficients).  Draw order is r, omega, c (for a
 complex c: real part, then imaginary part), from numpy's PCG64.
 """
 import numpy as np
@@ -41,6 +41,26 @@ def exponential_grid(n):
     j = np.arange(1, n + 1, dtype=np.float64)
     v = 10.0 ** (np.log10(j) - 0.5 * np.log10(n))
     return v.copy(), v.copy()
+
+
+def fourier_bessel_grid(nu, n):
+    """The Fourier-Bessel case of Sec. 5.1.1 (n = m): omega_k = j_{nu,k},
+    r_j = j_{nu,j} / j_{nu,n+1} for j, k = 1..n, where j_{nu,k} is the k-th
+    positive root of J_nu (from scipy.special.jn_zeros, a library routine).
+    A fixed grid (no random draws), in ascending order."""
+    from scipy.special import jn_zeros
+    roots = jn_zeros(int(abs(nu)), n + 1)
+    return roots[:n] / roots[n], roots[:n].copy()
+
+
+def sparse_coefficients(n, nnz=1000, seed=0):
+    """Sec. 5.1.3's input: nnz entries at random distinct indices with
+    standard Gaussian values, zero elsewhere.  Returns (c, indices)."""
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(n, size=min(nnz, n), replace=False))
+    c = np.zeros(n)
+    c[idx] = rng.standard_normal(idx.size)
+    return c, idx
 
 
 def batch_problems(count=256, lo=1e3, hi=1e5, nu_max=20, seed=5):

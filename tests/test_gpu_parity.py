@@ -8,7 +8,8 @@ import pytest
 
 import oracle
 from oracle import subdivide as OS
-from paper_2411_09583_gb300.workloads import (exponential_grid, loguniform_problem, sample_rows,
+from paper_2411_09583_gb300.workloads import (exponential_grid, fourier_bessel_grid, loguniform_problem,
+                                              sample_rows, sparse_coefficients,
                                               uniform_problem)
 
 pytestmark = pytest.mark.gpu
@@ -207,6 +208,36 @@ def test_relative_l2_error_tracks_eps(nu):
         g, _, _ = run_forward(nu, r, omega, c, eps)
         rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
         assert rel <= max(10 * eps, 3e-13), (eps, rel)
+
+
+@pytest.mark.parametrize("nu,eps", [(0, 1e-8), (3, 1e-12), (10, 1e-10)])
+def test_fourier_bessel_grid(nu, eps):
+    # Sec. 5.1.1's Fourier-Bessel case (n = m): frequencies at the roots of
+    # J_nu, points at the roots scaled by the (n+1)-th
+    r, omega = fourier_bessel_grid(nu, 2000)
+    c = np.random.default_rng(40 + nu).standard_normal(r.size)
+    _check(nu, r, omega, c, eps)
+
+
+@pytest.mark.parametrize("n", [1000, 100000])
+def test_sparse_input_relative_error(n):
+    # Sec. 5.1.3's accuracy experiment: nu = 0 on the Fourier-Bessel grid with
+    # 1000 nonzero Gaussian coefficients; the NUHT of the full c against the
+    # direct sum over the nonzeros only, as relative 2-norm error.  It follows
+    # eps down to a floor: that of the double-float loops (~1e-13) at n = 1e3,
+    # and at larger n the saturation the paper reports, error ~ n times the
+    # FP64 rounding unit (the arguments omega_k r_j reach ~ n pi, rounded
+    # differently by the oracle and the transform); measured 4.8e-12 at n = 1e5
+    r, omega = fourier_bessel_grid(0, n)
+    c, idx = sparse_coefficients(n, 1000, seed=41)
+    ref = oracle.direct(0, r[idx], omega, c[idx])
+    floor = max(3e-13, n * 2.0 ** -53)
+    rels = {}
+    for eps in (1e-4, 1e-6, 1e-8, 1e-10, 1e-12, 1e-14):
+        g, _, _ = run_forward(0, r, omega, c, eps)
+        rels[eps] = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+    bad = {eps: rel for eps, rel in rels.items() if not rel <= max(10 * eps, floor)}
+    assert not bad, ("failing", bad, "all", sorted(rels.items()))
 
 
 def _batch(count, lo, hi, nu_max, seed):
