@@ -130,12 +130,10 @@ __device__ __forceinline__ df df_sqrt(df a)
     return fast_two_sum(y0, r * (0.5f / y0));
 }
 
-// sin and cos of the exact product a*b (a, b doubles, |a*b| up to ~1e12).
-// The product is split exactly (FMA two-product) and reduced modulo pi/2 in
-// FP64 against a two-term pi/2; the remainder |t| <= pi/4 goes to the Taylor
-// series sin t = t sum_k (-t^2)^k/(2k+1)!, cos t = sum_k (-t^2)^k/(2k)!, summed
-// in double-float (truncation below 5e-17), then the quadrant is applied.
-__device__ __forceinline__ void df_sincos_prod(double a, double b, df* sn, df* cs)
+// sin and cos of x + q pi/2 for |x| <= pi/4 (double-float): the Taylor
+// series sin x = x sum_k (-x^2)^k/(2k+1)!, cos x = sum_k (-x^2)^k/(2k)!,
+// summed in double-float (truncation below 5e-17), then the quadrant q.
+__device__ __forceinline__ void df_sincos_quadrant(df x, int q, df* sn, df* cs)
 {
     // 1/n! split into float hi + lo parts (odd n for sin, even n for cos)
     const float2 ks[8] = {{1.0f, 0.0f}, {-0.1666666716337204f, 4.967053879312289e-09f},
@@ -152,15 +150,6 @@ __device__ __forceinline__ void df_sincos_prod(double a, double b, df* sn, df* c
                           {2.0876755879584152e-09f, 1.1082839147459852e-16f},
                           {-1.147074536050896e-11f, -2.372207689231238e-19f},
                           {4.7794772561329454e-14f, 7.62544404448643e-22f}};
-    const double kPio2Hi = 1.5707963267948966;       // nearest double to pi/2
-    const double kPio2Lo = 6.123233995736766e-17;    // pi/2 - kPio2Hi
-    const double k2OverPi = 0.6366197723675814;
-    const double p = a * b;
-    const double e = fma(a, b, -p);
-    const double k = rint(p * k2OverPi);
-    double t = fma(-k, kPio2Hi, p);
-    t = fma(-k, kPio2Lo, t) + e;
-    const df x = df_from(t);
     const df y = df_mul(x, x);
     df ps{ks[7].x, ks[7].y};
 #pragma unroll
@@ -169,13 +158,71 @@ __device__ __forceinline__ void df_sincos_prod(double a, double b, df* sn, df* c
 #pragma unroll
     for (int i = 7; i >= 0; --i) pc = df_add(df_mul(pc, y), df{kc[i].x, kc[i].y});
     const df s0 = df_mul(x, ps);
-    const int q = (int)((long long)k & 3);
-    switch (q) {
+    switch (q & 3) {
         case 0: *sn = s0; *cs = pc; break;
         case 1: *sn = pc; *cs = df_negate(s0); break;
         case 2: *sn = df_negate(s0); *cs = df_negate(pc); break;
         default: *sn = df_negate(pc); *cs = s0; break;
     }
+}
+
+// sin and cos of the exact product a*b (a, b doubles, |a*b| up to ~1e12).
+// The product is split exactly (FMA two-product) and reduced modulo pi/2 in
+// FP64 against a two-term pi/2; the remainder |t| <= pi/4 goes to
+// df_sincos_quadrant.
+__device__ __forceinline__ void df_sincos_prod(double a, double b, df* sn, df* cs)
+{
+    const double kPio2Hi = 1.5707963267948966;       // nearest double to pi/2
+    const double kPio2Lo = 6.123233995736766e-17;    // pi/2 - kPio2Hi
+    const double k2OverPi = 0.6366197723675814;
+    const double p = a * b;
+    const double e = fma(a, b, -p);
+    const double k = rint(p * k2OverPi);
+    double t = fma(-k, kPio2Hi, p);
+    t = fma(-k, kPio2Lo, t) + e;
+    df_sincos_quadrant(df_from(t), (int)((long long)k & 3), sn, cs);
+}
+
+// sin and cos of 2 pi F / 2^64 (F a fraction of a turn in 64-bit fixed
+// point), with integer arithmetic down to the FP32 pipes: the quadrant is the
+// top two bits (rounded), the rest an exact sum of three floats times 2 pi.
+__device__ __forceinline__ void df_sincos_turns(unsigned long long F, df* sn, df* cs)
+{
+    const unsigned long long Fq = F + (1ULL << 61);
+    const int quad = (int)(Fq >> 62);
+    const long long rem = (long long)(Fq & ((1ULL << 62) - 1)) - (1LL << 61);   // [-2^61, 2^61)
+    const float f1 = (float)(int)(rem >> 40) * 5.9604644775390625e-08f;          // 2^-24
+    const float f2 = (float)(int)((rem >> 16) & 0xFFFFFF) * 3.552713678800501e-15f;   // 2^-48
+    const float f3 = (float)(int)(rem & 0xFFFF) * 5.421010862427522e-20f;        // 2^-64
+    float s, e;
+    two_sum(f1, f2, s, e);
+    const df turns = fast_two_sum(s, e + f3);
+    const df x = df_mul(turns, df{6.2831854820251465f, -1.7484555314695172e-07f});   // 2 pi
+    df_sincos_quadrant(x, quad, sn, cs);
+}
+
+// Bits [s, s + 63] of the signed 128-bit product X * K, 0 <= s <= 64.
+__device__ __forceinline__ unsigned long long mul128_bits(long long X, long long K, int s)
+{
+    const unsigned long long lo = (unsigned long long)X * (unsigned long long)K;
+    const unsigned long long hi = (unsigned long long)__mul64hi(X, K);
+    if (s <= 0) return lo;
+    if (s >= 64) return hi;
+    return (hi << (64 - s)) | (lo >> s);
+}
+
+// round(r 2^fr) for finite r >= 0 with r 2^fr < 2^62, from the bits of r
+// (integer instructions only).
+__device__ __forceinline__ long long fx_from_double(double r, int fr)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;                                   // zero or subnormal
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+    const int sh = e - 1075 + fr;                           // r 2^fr = m 2^sh
+    if (sh >= 0) return m << sh;
+    if (sh <= -54) return 0;
+    return (m + (1LL << (-sh - 1))) >> (-sh);
 }
 
 }  // namespace nuht

@@ -79,6 +79,45 @@ __device__ __forceinline__ void spread_weight(const AsyBlock& B, double x, float
     *wi = df_mul(w0, sn);
 }
 
+// floor(X K / 2^s) for the signed 128-bit product, 1 <= s <= 127 (the
+// result fits in 64 bits).
+__device__ __forceinline__ long long mul128_shr(long long X, long long K, int s)
+{
+    const unsigned long long lo = (unsigned long long)X * (unsigned long long)K;
+    const long long hi = __mul64hi(X, K);
+    if (s >= 64) return hi >> (s - 64);
+    return (long long)(((unsigned long long)hi << (64 - s)) | (lo >> s));
+}
+
+// spread_cell in the block's fixed-point frame (integer instructions, exact
+// to 2^-41 cells): cell l0 and kernel coordinate v (double-float) of r_j,
+// and its offset X = R_j - R_c for the phase.
+__device__ __forceinline__ int spread_cell_fx(const AsyBlock& B, int w, double rj, long long* Xo, df* v)
+{
+    const long long X = fx_from_double(rj, B.fr) - B.Rc_fx;
+    *Xo = X;
+    const long long A = mul128_shr(X, B.KH, B.sA) - ((long long)w << 40);   // (x/h - w/2) 2^41
+    const long long l0 = (A + ((1LL << 41) - 1)) >> 41;                     // ceil
+    const long long sv = ((l0 << 41) - A) - (1LL << 40);                    // v 2^40, v in [-1, 1)
+    float s2, e2;
+    two_sum((float)(int)(sv >> 20) * 9.5367431640625e-07f, (float)(int)(sv & 0xFFFFF) * 9.094947017729282e-13f,
+            s2, e2);
+    *v = df{s2, e2};
+    return (int)l0;
+}
+
+// spread_weight with the phase w_c x_j / (2 pi) from the fixed-point offset.
+__device__ __forceinline__ void spread_weight_fx(const AsyBlock& B, long long X, float2 r2, float2 c2, df* wr,
+                                                 df* wi, df* rat)
+{
+    df sn, cs;
+    df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+    *rat = df_mul(df{B.rho_h, B.rho_l}, df_recip(df{r2.x, r2.y}));
+    const df w0 = df_mul(df{c2.x, c2.y}, df_sqrt(*rat));
+    *wr = df_mul(w0, cs);
+    *wi = df_mul(w0, sn);
+}
+
 constexpr int kSpreadSub = 8;       // point sub-ranges per moment, combined by shuffles
 constexpr int kMomMinPerBin = 16;   // tiles with at least this many points per bin use moments
 constexpr int kMaxTileBins = 32;
@@ -146,12 +185,13 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
     }
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        double x, v;
-        l0s[tid] = spread_cell(B, tab, r_s[j], &x, &v);
+        long long Xp;
+        df vd;
+        l0s[tid] = spread_cell_fx(B, w, r_s[j], &Xp, &vd);
         // Chebyshev basis by T_{d+1} = 2 v T_d - T_{d-1}
         float2* ud = Ud + tid * L.sud;
         float* uf = Uf + tid * L.suf;
-        const float vh = (float)v, vl = (float)(v - (double)vh);
+        const float vh = vd.h, vl = vd.l;
         df tm{1.f, 0.f}, tc{vh, vl};
         ud[0] = make_float2(1.f, 0.f);
         ud[1] = make_float2(vh, vl);                 // dcs >= 2
@@ -173,7 +213,7 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
         }
         for (int e = nb - dcs; e < L.suf; ++e) uf[e] = 0.f;
         df wr, wi, rat;
-        spread_weight(B, x, r2[j], c2[j], &wr, &wi, &rat);
+        spread_weight_fx(B, Xp, r2[j], c2[j], &wr, &wi, &rat);
         float2* xq = X + tid * L.sx;
         for (int q = 0; q < Q; ++q) {
             xq[2 * q] = make_float2(wr.h, wr.l);
@@ -330,6 +370,340 @@ __host__ __device__ __forceinline__ size_t spread_moments_smem(int nt, int Q, in
            sizeof(float) * (size_t)nt * L.suf + sizeof(int) * (size_t)nt;
 }
 
+// q-folded dense tile.  Within the bin of cell L, r_p = R_L - (h/2) v_p with
+// R_L = r_c + h (L + (w - 1)/2), so the weights are (rho/r_p)^q = s^q (1 - eta v_p)^-q,
+// s = rho / R_L, eta = h / (2 R_L): a smooth function of v_p.  Its Chebyshev
+// form sum_k beta_qk T_k(v) (from the Taylor series sum_j C(q+j-1, j) (eta v)^j
+// and v^j = sum_k MC(j, k) T_k(v)) and T_d T_k = (T_{d+k} + T_{|d-k|}) / 2 give
+//   M[d][q] = sum_p T_d(v_p) (rho/r_p)^q y_p = sum_k beta_qk (N[d+k] + N[|d-k|]) / 2,
+//   N[e] = sum_p T_e(v_p) y_p,   y_p = c_p (r_p/rho)^(-1/2) e^{i w_c x_p},
+// so each point adds to 2 (nb + K - 1) moments N instead of nb x 2M moments M.
+// K terms are kept where the Taylor tail is below tab.fold_tol; N is
+// double-float for degrees below dcs plus those reached with a beta above
+// tab.fold_df_tol, plain FP32 above.  M then feeds the same grid update as
+// the plain moment path.  Tiles whose bins are too wide for their radius
+// (eta too large for kFoldMax terms) take the plain moment path.
+constexpr int kFoldMax = 8;          // Chebyshev terms of the weights' dependence on v within a bin
+constexpr int kFoldDfMax = 4;        // extra double-float degrees of N the fold may need
+constexpr int kFoldGroupBytes = 8192;
+
+struct FoldPlan {
+    int K;      // terms k < K of the weights' Chebyshev form
+    int E;      // moments N[e], e < E (even)
+    int Edf;    // N[e] in double-float for e < Edf (even)
+};
+
+// The fold's sizes for a tile whose first bin is cell lfirst; false when it
+// does not apply (plain moment path).  Bounds with q = Q - 1, the largest,
+// in FP32 (a bound, evaluated by one thread while the tile waits: FP64 here
+// would stall the CTA).
+__device__ bool fold_plan(const AsyBlock& B, const Tables& tab, int Q, int lfirst, FoldPlan* fp)
+{
+    const float R = (float)B.rc + (float)B.h * ((float)lfirst + 0.5f * (float)(tab.w - 1));
+    if (!(R > 0.f)) return false;
+    const float eta = (float)B.h / (2.f * R);
+    const int qm = Q - 1;
+    float t[kFoldMax + 1], tail[kFoldMax + 1];
+    t[0] = 1.f;
+#pragma unroll
+    for (int j = 0; j < kFoldMax; ++j) t[j + 1] = t[j] * eta * (float)(qm + j) * (1.f / (float)(j + 1));
+    const float ratio = eta * (float)(qm + kFoldMax) * (1.f / (float)(kFoldMax + 1));
+    if (!(ratio < 0.5f)) return false;
+    tail[kFoldMax] = 2.f * t[kFoldMax];   // geometric tail, ratio < 1/2
+#pragma unroll
+    for (int k = kFoldMax - 1; k >= 0; --k) tail[k] = tail[k + 1] + t[k];
+    // 1.01: room for the FP32 rounding of the bound itself
+    int K = 1;
+    while (K <= kFoldMax && 1.01f * tail[K] > tab.fold_tol) ++K;
+    if (K > kFoldMax) return false;
+    int kd = 0;
+    while (kd + 1 < K && 1.01f * tail[kd + 1] > tab.fold_df_tol) ++kd;
+    if (kd > kFoldDfMax) return false;
+    fp->K = K;
+    fp->E = (tab.nb + K - 1 + 1) & ~1;
+    const int edf = (tab.dcs + kd + 1) & ~1;
+    fp->Edf = edf < fp->E ? edf : fp->E;
+    return true;
+}
+
+__host__ __device__ __forceinline__ int fold_group_bins(int dpad, int Q2)
+{
+    int g = kFoldGroupBytes / (int)(sizeof(float2) * dpad * Q2);
+    if (g < 1) g = 1;
+    return g < kMaxTileBins ? g : kMaxTileBins;
+}
+
+__host__ __device__ __forceinline__ int fold_emax(int nb) { return (nb + kFoldMax - 1 + 1) & ~1; }
+__host__ __device__ __forceinline__ int fold_edf_max(int nb, int dcs)
+{
+    const int e = (dcs + kFoldDfMax + 1) & ~1, em = fold_emax(nb);
+    return e < em ? e : em;
+}
+
+// Shared memory (bytes) of the folded path for nt points and Q = 2M (its largest layout).
+__host__ __device__ __forceinline__ size_t spread_fold_smem(int nt, int Q, int w, int nb, int dcs)
+{
+    const MomLayout L = mom_layout(nb, dcs, 2 * Q);
+    const int G = fold_group_bins(L.dpad, 2 * Q);
+    const int em = fold_emax(nb), edm = fold_edf_max(nb, dcs);
+    const int sud = mom_stride(edm), suf = mom_stride(em - 2);
+    return sizeof(float4) * ((size_t)nt + (size_t)G * em) +
+           sizeof(float2) * ((size_t)nt * sud + (size_t)G * L.dpad * 2 * Q + (size_t)G * Q * kFoldMax +
+                             (size_t)w * L.dpad) +
+           sizeof(float) * (size_t)nt * suf + sizeof(int) * (size_t)nt;
+}
+
+__device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, const Tables& tab, FoldPlan F,
+                            const double* __restrict__ r_s, const float2* __restrict__ r2,
+                            const float2* __restrict__ c2, double2* __restrict__ gb, float4* sm4)
+{
+    const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
+    const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
+    const int Q2 = 2 * Q, K = F.K, E = F.E, Edf = F.Edf;
+    const MomLayout L = mom_layout(nb, dcs, Q2);
+    const int G = fold_group_bins(L.dpad, Q2);
+    const int sud = mom_stride(Edf), suf = mom_stride(E - Edf);
+    float4* Y = sm4;                                  // [nt] y_p as (re.h, re.l, im.h, im.l)
+    float4* N = Y + nt;                               // [G][E] N[e] of a group of bins
+    float2* Ud = (float2*)(N + G * E);                // [nt][sud] T_e(v_p), e < Edf
+    float2* Mb = Ud + nt * sud;                       // [G][dpad][Q2] M of a group of bins
+    float2* beta = Mb + G * L.dpad * Q2;              // [G][Q][kFoldMax] beta_qk
+    float2* Ach = beta + G * Q * kFoldMax;            // [w][dpad] Chebyshev coefficients of the taps
+    float* Uf = (float*)(Ach + w * L.dpad);           // [nt][suf] T_e(v_p), Edf <= e < E
+    int* l0s = (int*)(Uf + nt * suf);                 // [nt]
+    __shared__ int bstart[kMaxTileBins + 3];
+    for (int i = tid; i < w * L.dpad; i += nt) {
+        const int r = i / L.dpad, e = i - r * L.dpad;
+        const int d = mom_degree(e, L.ndf, dcs, nb);
+        Ach[i] = d >= 0 ? tab.ch2[r * (tab.deg + 1) + d] : make_float2(0.f, 0.f);
+    }
+    if (tid < cnt) {
+        const int64_t j = t.start + tid;
+        long long X;
+        df vd;
+        l0s[tid] = spread_cell_fx(B, w, r_s[j], &X, &vd);
+        float2* ud = Ud + tid * sud;
+        float* uf = Uf + tid * suf;
+        const float vh = vd.h, vl = vd.l;
+        df tm{1.f, 0.f}, tc{vh, vl};
+        ud[0] = make_float2(1.f, 0.f);
+        ud[1] = make_float2(vh, vl);                 // Edf >= 2
+        const df v2{2.f * vh, 2.f * vl};
+        int d = 2;
+        for (; d < Edf; ++d) {
+            const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+            ud[d] = make_float2(tn.h, tn.l);
+            tm = tc;
+            tc = tn;
+        }
+        float fm = tm.h, fc = tc.h;
+        for (; d < E; ++d) {
+            const float fn = fmaf(2.f * vh, fc, -fm);
+            uf[d - Edf] = fn;
+            fm = fc;
+            fc = fn;
+        }
+        df wr, wi, rat;
+        spread_weight_fx(B, X, r2[j], c2[j], &wr, &wi, &rat);
+        Y[tid] = make_float4(wr.h, wr.l, wi.h, wi.l);
+    }
+    __syncthreads();
+    const int lfirst = l0s[0];
+    const int nbins = l0s[cnt - 1] - lfirst + 1;
+    for (int b = tid; b <= nbins; b += nt) {
+        const int key = lfirst + b;
+        int lo = 0, hi = cnt;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (l0s[mid] < key) lo = mid + 1; else hi = mid; }
+        bstart[b] = lo;
+    }
+    __syncthreads();
+    const int nf1 = 2 * B.N1 + 1;
+    const int npd = Edf >> 1, npf = (E - Edf) >> 1;
+    const df rho{B.rho_h, B.rho_l};
+    for (int g0 = 0; g0 < nbins; g0 += G) {
+        const int gn = nbins - g0 < G ? nbins - g0 : G;
+        // (a) N of the group's bins: items (bin, degree pair) split over
+        // kSpreadSub lanes each, double-float items first
+        const int nitems = gn * (npd + npf) * kSpreadSub;
+        const int nitems_pad = (nitems + 31) & ~31;
+        for (int it = tid; it < nitems_pad; it += nt) {
+            const bool live = it < nitems;
+            const int sub = it & (kSpreadSub - 1);
+            const int o = live ? it / kSpreadSub : 0;
+            int b, pr;
+            bool dfi;
+            if (o < gn * npd) {
+                b = o / npd;
+                pr = o - b * npd;
+                dfi = true;
+            } else {
+                const int o2 = o - gn * npd;
+                b = o2 / npf;
+                pr = o2 - b * npf;
+                dfi = false;
+            }
+            const int p0 = bstart[g0 + b], p1 = bstart[g0 + b + 1];
+            acc2 a00{0.f, 0.f}, a01{0.f, 0.f}, a10{0.f, 0.f}, a11{0.f, 0.f};
+            if (live && dfi) {
+                const float2* up = Ud + 2 * pr;
+#pragma unroll 2
+                for (int p = p0 + sub; p < p1; p += kSpreadSub) {
+                    const float4 uu = *(const float4*)(up + p * sud);
+                    const float4 yv = Y[p];
+                    const df u0{uu.x, uu.y}, u1{uu.z, uu.w}, yr{yv.x, yv.y}, yi{yv.z, yv.w};
+                    acc_fma(a00, u0, yr);
+                    acc_fma(a01, u0, yi);
+                    acc_fma(a10, u1, yr);
+                    acc_fma(a11, u1, yi);
+                }
+            } else if (live) {
+                const float* up = Uf + 2 * pr;
+#pragma unroll 4
+                for (int p = p0 + sub; p < p1; p += kSpreadSub) {
+                    const float2 uu = *(const float2*)(up + p * suf);
+                    const float4 yv = Y[p];
+                    a00.s = fmaf(uu.x, yv.x, a00.s);
+                    a01.s = fmaf(uu.x, yv.z, a01.s);
+                    a10.s = fmaf(uu.y, yv.x, a10.s);
+                    a11.s = fmaf(uu.y, yv.z, a11.s);
+                }
+            }
+            acc2* accs[4] = {&a00, &a01, &a10, &a11};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                acc2 a = *accs[f];
+#pragma unroll
+                for (int off = kSpreadSub >> 1; off > 0; off >>= 1) {
+                    const float os = __shfl_xor_sync(0xffffffffu, a.s, off);
+                    const float oc = __shfl_xor_sync(0xffffffffu, a.c, off);
+                    float s2, q2;
+                    two_sum(a.s, os, s2, q2);
+                    a.s = s2;
+                    a.c += oc + q2;
+                }
+                *accs[f] = a;
+            }
+            if (live && sub == 0) {
+                const int e0 = dfi ? 2 * pr : Edf + 2 * pr;
+                const df n00 = fast_two_sum(a00.s, a00.c), n01 = fast_two_sum(a01.s, a01.c);
+                const df n10 = fast_two_sum(a10.s, a10.c), n11 = fast_two_sum(a11.s, a11.c);
+                N[b * E + e0] = make_float4(n00.h, n00.l, n01.h, n01.l);
+                N[b * E + e0 + 1] = make_float4(n10.h, n10.l, n11.h, n11.l);
+            }
+        }
+        // beta_qk = s^q sum_{j >= k, j = k mod 2} t_j MC(j, k), t_j = C(q+j-1, j) eta^j,
+        // MC(j, k) = 2^(1-j) C(j, (j-k)/2) (halved for k = 0)
+        for (int sl = tid; sl < gn * Q; sl += nt) {
+            const int b = sl / Q, q = sl - b * Q;
+            const double R = B.rc + B.h * ((lfirst + g0 + b) + 0.5 * (w - 1));
+            const df iR = df_recip(df_from(R));
+            const df s = df_mul(rho, iR);
+            const df eta = df_mul(df_from(0.5 * B.h), iR);
+            df tj[kFoldMax];
+            tj[0] = df{1.f, 0.f};
+            for (int j = 0; j + 1 < K; ++j) {
+                const df f = df_mul(df{(float)(q + j), 0.f}, df_recip(df{(float)(j + 1), 0.f}));
+                tj[j + 1] = df_mul(df_mul(tj[j], eta), f);
+            }
+            df sq{1.f, 0.f};
+            for (int i = 0; i < q; ++i) sq = df_mul(sq, s);
+            float2* bt = beta + (b * Q + q) * kFoldMax;
+            for (int k = 0; k < K; ++k) {
+                df acc{0.f, 0.f};
+                float cjk = 1.f;                     // C(j, (j - k)/2) for j = k
+                for (int j = k; j < K; j += 2) {
+                    const float mc = ldexpf(cjk, 1 - j) * (k == 0 ? 0.5f : 1.f);
+                    acc = df_add(acc, df_mul(tj[j], df{mc, 0.f}));
+                    // C(j+2, i+1) = C(j, i) (j+1)(j+2) / ((i+1)(j+2-i-1)), i = (j-k)/2
+                    const int i = (j - k) >> 1;
+                    cjk = cjk * (float)((j + 1) * (j + 2)) / (float)((i + 1) * (j + 1 - i));
+                }
+                const df bk = df_mul(sq, acc);
+                bt[k] = make_float2(bk.h, bk.l);
+            }
+        }
+        __syncthreads();
+        // (b) M[d][q] = sum_k beta_qk (N[d+k] + N[|d-k|]) / 2 into the row order of Mb
+        for (int o = tid; o < gn * L.dpad * Q; o += nt) {
+            const int b = o / (L.dpad * Q), rem = o - b * (L.dpad * Q);
+            const int e = rem / Q, q = rem - e * Q;
+            const int d = mom_degree(e, L.ndf, dcs, nb);
+            float2 mr = make_float2(0.f, 0.f), mi = make_float2(0.f, 0.f);
+            if (d >= 0) {
+                const float2* bt = beta + (b * Q + q) * kFoldMax;
+                const float4* Nb = N + b * E;
+                const float2 b0 = bt[0];
+                const float4 n0 = Nb[d];
+                if (e < 2 * L.ndf && q < qs) {
+                    acc2 ar{0.f, 0.f}, ai{0.f, 0.f};
+                    acc_fma(ar, df{b0.x, b0.y}, df{n0.x, n0.y});
+                    acc_fma(ai, df{b0.x, b0.y}, df{n0.z, n0.w});
+                    for (int k = 1; k < K; ++k) {
+                        const float4 n1 = Nb[d + k], n2 = Nb[d >= k ? d - k : k - d];
+                        const df sr = df_add(df{n1.x, n1.y}, df{n2.x, n2.y});
+                        const df si = df_add(df{n1.z, n1.w}, df{n2.z, n2.w});
+                        const float2 bk = bt[k];
+                        const df hb{0.5f * bk.x, 0.5f * bk.y};
+                        acc_fma(ar, hb, sr);
+                        acc_fma(ai, hb, si);
+                    }
+                    const df vr = fast_two_sum(ar.s, ar.c), vi = fast_two_sum(ai.s, ai.c);
+                    mr = make_float2(vr.h, vr.l);
+                    mi = make_float2(vi.h, vi.l);
+                } else {
+                    float fr = b0.x * n0.x, fi = b0.x * n0.z;
+                    for (int k = 1; k < K; ++k) {
+                        const float4 n1 = Nb[d + k], n2 = Nb[d >= k ? d - k : k - d];
+                        const float hb = 0.5f * bt[k].x;
+                        fr = fmaf(hb, n1.x + n2.x, fr);
+                        fi = fmaf(hb, n1.z + n2.z, fi);
+                    }
+                    mr = make_float2(fr, 0.f);
+                    mi = make_float2(fi, 0.f);
+                }
+            }
+            Mb[(b * L.dpad + e) * Q2 + 2 * q] = mr;
+            Mb[(b * L.dpad + e) * Q2 + 2 * q + 1] = mi;
+        }
+        __syncthreads();
+        // (c) grid[lfirst + g0 + c][q'] += sum_b sum_d A[c - b][d] M_b[d][q'] over
+        // the group's bins b with 0 <= c - b < w
+        const int ncell = gn + w - 1;
+        for (int o = tid; o < ncell * Q2; o += nt) {
+            const int c = o / Q2, qv = o - c * Q2;
+            const int idx = lfirst + g0 + c + B.N1;
+            if (idx < 0 || idx >= nf1) continue;
+            const int b_lo = c - w + 1 > 0 ? c - w + 1 : 0;
+            const int b_hi = c < gn - 1 ? c : gn - 1;
+            const bool dq = (qv >> 1) < qs;
+            acc2 sacc{0.f, 0.f};
+            for (int b = b_lo; b <= b_hi; ++b) {
+                const float2* ar = Ach + (c - b) * L.dpad;
+                const float2* mb = Mb + b * L.dpad * Q2 + qv;
+                float sf = 0.f;
+                int e = 0;
+                if (dq) {
+                    for (; e < 2 * L.ndf; ++e) {
+                        const float2 a2 = ar[e], m2 = mb[e * Q2];
+                        acc_fma(sacc, df{a2.x, a2.y}, df{m2.x, m2.y});
+                    }
+                }
+                for (; e < L.dpad; ++e) sf = fmaf(ar[e].x, mb[e * Q2].x, sf);
+                float s2, e2;
+                two_sum(sacc.s, sf, s2, e2);
+                sacc.s = s2;
+                sacc.c += e2;
+            }
+            const double val = acc_value(sacc);
+            if (val != 0.0) {
+                double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
+                atomicAdd(dst, val);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Sparse tile (points spread over many cells): each thread prepares one point
 // (cell l0, w kernel taps, the 2M weighted, pre-phased values), then each
 // (cell, q) output of the tile's window is owned by one thread, which sums
@@ -350,15 +724,16 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
     const int cnt = t.count;
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        double x, v;
-        l0s[tid] = spread_cell(B, tab, r_s[j], &x, &v);
-        const float vh = (float)v, vl = (float)(v - (double)vh);
+        long long X;
+        df vd;
+        l0s[tid] = spread_cell_fx(B, w, r_s[j], &X, &vd);
+        const float vh = vd.h, vl = vd.l;
         for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
         df wr, wi, rat;
-        spread_weight(B, x, r2[j], c2[j], &wr, &wi, &rat);
+        spread_weight_fx(B, X, r2[j], c2[j], &wr, &wi, &rat);
         for (int q = 0; q < Q; ++q) {
             aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
             wr = df_mul(wr, rat);
@@ -435,19 +810,28 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
 {
     extern __shared__ float4 smem4[];
     __shared__ int use_mom;
+    __shared__ FoldPlan fplan;
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
     if (t.count <= 0) return;
     if (threadIdx.x == 0) {
-        double x, v;
-        const int lfirst = spread_cell(B, tab, r_s[t.start], &x, &v);
-        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &x, &v) - lfirst + 1;
+        long long X;
+        df vd;
+        const int lfirst = spread_cell_fx(B, tab.w, r_s[t.start], &X, &vd);
+        const int nbins = spread_cell_fx(B, tab.w, r_s[t.start + t.count - 1], &X, &vd) - lfirst + 1;
         use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
+        FoldPlan fp;
+        if (use_mom && fold_plan(B, tab, Q, lfirst, &fp)) {
+            use_mom = 2;
+            fplan = fp;
+        }
     }
     __syncthreads();
     double2* gb = grid_b + B.b_off;
-    if (use_mom)
+    if (use_mom == 2)
+        spread_fold(B, Q, probs[B.prob].qs, t, tab, fplan, r_s, r2, c2, gb, smem4);
+    else if (use_mom)
         spread_moments(B, Q, probs[B.prob].qs, t, tab, r_s, r2, c2, gb, (float2*)smem4);
     else
         spread_taps(B, Q, t, tab, r_s, r2, c2, gb, smem4);
@@ -1074,12 +1458,9 @@ __global__ void __launch_bounds__(128, 4) k_asy_adj_interp(
         const bool valid = base + (int)threadIdx.x < t.count;
         const int64_t j = t.start + base + (valid ? threadIdx.x : 0);
         const double rj = r_s[j];
-        const double x = rj - B.rc;
-        const double a = x * B.inv_h - tab.half_w;
-        const double lf = ceil(a);
-        const double z0 = fmin(fmax(lf - a, 0.0), 1.0);
-        const double v = 2.0 * z0 - 1.0;
-        const int l0 = (int)lf;
+        long long X;
+        df vd;
+        const int l0 = spread_cell_fx(B, w, rj, &X, &vd);
         __syncthreads();
         if (valid) l0s[threadIdx.x] = l0;
         __syncthreads();
@@ -1096,7 +1477,7 @@ __global__ void __launch_bounds__(128, 4) k_asy_adj_interp(
             }
         __syncthreads();
         if (!valid) continue;
-        const float vh = (float)v, vl = (float)(v - (double)vh);
+        const float vh = vd.h, vl = vd.l;
         float th[kMaxW], tl[kMaxW];
 #pragma unroll
         for (int i = 0; i < kMaxW; ++i) {
@@ -1133,7 +1514,7 @@ __global__ void __launch_bounds__(128, 4) k_asy_adj_interp(
         }
         // c_j += Re( e^{i w_c x} (r/rho)^(-1/2) T )
         df sn, cs;
-        df_sincos_prod(B.wc, x, &sn, &cs);
+        df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
         const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
         const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
         atomicAdd(&c_s[j], df_to(df_mul(df_sqrt(rat), re)));
@@ -1589,6 +1970,8 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
                   sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     const size_t smem_mom = spread_moments_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
     if (smem_mom > smem) smem = smem_mom;
+    const size_t smem_fold = spread_fold_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
+    if (smem_fold > smem) smem = smem_fold;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, r2, c2, grid_b);

@@ -59,18 +59,44 @@ __global__ void k_block_sizes(BlockBuild bb)
             ab.prob = b.prob;
             ab.k0 = (int32_t)(b.k0 + P.w_off); ab.k1 = (int32_t)(b.k1 + P.w_off);
             ab.j0 = (int32_t)(b.j0 + P.r_off); ab.j1 = (int32_t)(b.j1 + P.r_off);
-            ab.rc = 0.5 * (e.x + e.y);
+            // r_c rounded to a multiple of 2^(10 - fr) (any centre serves the
+            // type-3 transform); the fixed-point frame keeps r < 2^(62 - fr)
+            int er;
+            frexp(e.y, &er);
+            ab.fr = 62 - er;
+            ab.rc = ldexp(rint(ldexp(0.5 * (e.x + e.y), ab.fr - 10)), 10 - ab.fr);
+            ab.Rc_fx = (int64_t)ldexp(ab.rc, ab.fr);
             const double X = 0.5 * (e.y - e.x);
             ab.wc = 0.5 * (e.z + e.w);
             const double S = 0.5 * (e.w - e.z);
             const double Seff = S > 0.0 ? S : 1.0;
             ab.h = M_PI / (2.0 * Seff);
             ab.inv_h = (2.0 / M_PI) * Seff;
+            {
+                int eh, ew;
+                frexp(ab.inv_h, &eh);
+                ab.KH = (int64_t)ldexp(ab.inv_h, 62 - eh);      // exact: 53-bit mantissa
+                ab.sA = ab.fr + 62 - eh - 41;
+                // w_c / (2 pi) in double-double, then 62 bits of it
+                const double c_hi = 0.15915494309189535, c_lo = -9.839338337591243e-18;
+                const double p = ab.wc * c_hi;
+                const double err = fma(ab.wc, c_hi, -p) + ab.wc * c_lo;
+                frexp(p, &ew);
+                int64_t kw = llrint(ldexp(p, 62 - ew)) + llrint(ldexp(err, 62 - ew));
+                int sw = ab.fr + 62 - ew - 64;
+                if (sw > 64) {
+                    kw = sw - 64 < 63 ? kw >> (sw - 64) : 0;
+                    sw = 64;
+                }
+                ab.KW = kw;
+                ab.sW = sw;
+            }
+            const bool fx_bad = ab.sA < 1 || ab.sA > 127 || ab.sW < 0;
             const double n1f = ceil(X * ab.inv_h + 0.5 * bb.w) + 1.0;   // one cell of rounding margin
             int64_t* c = bb.acnt + a * kAsyCols;
             for (int k = 0; k < kAsyCols; ++k) c[k] = 0;
             bb.fcls[a] = -1;
-            if (!(n1f <= (double)(1 << 22))) {
+            if (fx_bad || !(n1f <= (double)(1 << 22))) {
                 atomic_max64(&bb.maxv[MX_ERR], 1);
                 continue;
             }

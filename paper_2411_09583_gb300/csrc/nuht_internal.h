@@ -16,6 +16,7 @@ constexpr int kMaxM = 20;           // Hankel term pairs (Sec. 3.3 caps M at 20)
 constexpr int kMaxQ = 2 * kMaxM;    // weight powers q = 0..2M-1
 constexpr int kMaxW = 16;           // ES kernel width
 constexpr int kMaxDeg = 20;         // degree of the kernel piece polynomials
+constexpr int kMomFold = 32;        // FP32 partial sums of the spreading moments span at most this many points
 constexpr int kMaxNtop = 400;       // largest Bessel index kept by the local evaluation
                                     // (the transposed moments then stay within 205 KB of shared memory)
 constexpr int kFftSmemMax = 4096;   // points of all Q grids of a block FFT'd by one CTA
@@ -68,6 +69,14 @@ struct AsyBlock {
     double inv_delta;  // nf2 / (2 pi)
     double hd;         // h * inv_delta: a frequency offset s sits at FFT-grid position s * hd
     float rho_h, rho_l;   // rho as double-float
+    // Fixed-point frame of the points (integer arithmetic instead of FP64,
+    // whose rate is 1/64 of FP32 here): R = round(r 2^fr) < 2^62, X = R - Rc_fx
+    // (r_c is a multiple of 2^(10 - fr), so Rc_fx is exact); the cell
+    // coordinate a = x / h is bits [sA, sA + 63] of X * KH (41 fractional
+    // bits; KH = inv_h 2^(sA + 41 - fr) exactly), and the phase w_c x / (2 pi)
+    // in turns is bits [sW, sW + 63] of X * KW (64 fractional bits).
+    int64_t Rc_fx, KH, KW;
+    int32_t fr, sA, sW, pad_fx;
 };
 
 struct DirectBlock {
@@ -149,6 +158,8 @@ struct Tables {
     int nb;                // Chebyshev terms kept (tail below 1e-3 eps)
     int dcs;               // spreading moments of degree >= dcs accumulate in plain FP32
     int dci;               // interpolation terms of degree >= dci are summed in plain FP32
+    float fold_tol;        // truncation of the spreading weights' Chebyshev form within a bin
+    float fold_df_tol;     // weights' Chebyshev terms above this need double-float moments
     double half_w;         // w / 2
     const double* ph;      // psi-hat pieces [ph_pieces][ph_deg + 1] in v in [-1, 1]
     const float2* ph2;     // the same as double-float

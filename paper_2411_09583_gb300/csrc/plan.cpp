@@ -738,6 +738,12 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
             if (acc <= 1e-2 * P->eps) --dci; else break;
         }
         tb.dci = dci;
+        // q-folded spreading: the weights' Chebyshev terms are kept down to
+        // 1e-3 eps; a term above 1e-2 eps / ((kMomFold + 2) 2^-23) multiplies
+        // moments whose FP32 partial sums (kMomFold points) would show, so
+        // those moments stay double-float
+        tb.fold_tol = (float)(1e-3 * P->eps);
+        tb.fold_df_tol = (float)(1e-2 * P->eps / ((kMomFold + 2) * 1.1920928955078125e-07));
     }
     tb.ph = P->d_ph; tb.ph2 = (const float2*)(D + a_ph2);
     tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
