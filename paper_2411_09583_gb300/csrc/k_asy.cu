@@ -89,6 +89,15 @@ __device__ __forceinline__ long long mul128_shr(long long X, long long K, int s)
     return (long long)(((unsigned long long)hi << (64 - s)) | (lo >> s));
 }
 
+// v 2^40 (|v| <= 1) as double-float, exactly.
+__device__ __forceinline__ df df_from_sv(long long sv)
+{
+    float s2, e2;
+    two_sum((float)(int)(sv >> 20) * 9.5367431640625e-07f, (float)(int)(sv & 0xFFFFF) * 9.094947017729282e-13f,
+            s2, e2);
+    return df{s2, e2};
+}
+
 // spread_cell in the block's fixed-point frame (integer instructions, exact
 // to 2^-41 cells): cell l0 and kernel coordinate v (double-float) of r_j,
 // and its offset X = R_j - R_c for the phase.
@@ -98,11 +107,7 @@ __device__ __forceinline__ int spread_cell_fx(const AsyBlock& B, int w, double r
     *Xo = X;
     const long long A = mul128_shr(X, B.KH, B.sA) - ((long long)w << 40);   // (x/h - w/2) 2^41
     const long long l0 = (A + ((1LL << 41) - 1)) >> 41;                     // ceil
-    const long long sv = ((l0 << 41) - A) - (1LL << 40);                    // v 2^40, v in [-1, 1)
-    float s2, e2;
-    two_sum((float)(int)(sv >> 20) * 9.5367431640625e-07f, (float)(int)(sv & 0xFFFFF) * 9.094947017729282e-13f,
-            s2, e2);
-    *v = df{s2, e2};
+    *v = df_from_sv(((l0 << 41) - A) - (1LL << 40));                       // v 2^40, v in [-1, 1)
     return (int)l0;
 }
 
@@ -116,6 +121,51 @@ __device__ __forceinline__ void spread_weight_fx(const AsyBlock& B, long long X,
     const df w0 = df_mul(df{c2.x, c2.y}, df_sqrt(*rat));
     *wr = df_mul(w0, cs);
     *wi = df_mul(w0, sn);
+}
+
+// A signed 64-bit integer as double-float (relative error 2^-48): three
+// exact 21-bit parts.
+__device__ __forceinline__ df df_from_i64(long long x)
+{
+    const int a = (int)(x >> 42);
+    const int b = (int)((x >> 21) & 0x1FFFFF);
+    const int c = (int)(x & 0x1FFFFF);
+    float s, e;
+    two_sum((float)a * 4398046511104.f, (float)b * 2097152.f, s, e);   // 2^42, 2^21
+    return fast_two_sum(s, e + (float)c);
+}
+
+// FFT-grid cell t0 = ceil(s hd - w/2) of a frequency omega_k and its kernel
+// coordinate as sv = v 2^40 (v in [-1, 1)), in the block's fixed-point
+// frequency frame (integer instructions, exact to 2^-40 cells); Om and
+// S = Om - Wc_fx for the phase and the deconvolution argument.
+__device__ __forceinline__ int interp_cell_sv(const AsyBlock& B, int w, double wk, long long* Om, long long* Sw,
+                                              long long* svo)
+{
+    const long long O = fx_from_double(wk, B.fw);
+    const long long S = O - B.Wc_fx;
+    *Om = O;
+    *Sw = S;
+    const long long A = mul128_shr(S, B.KD, B.sD) - ((long long)w << 39);   // (s hd - w/2) 2^40
+    const long long t0 = (A + ((1LL << 40) - 1)) >> 40;                     // ceil
+    *svo = 2 * ((t0 << 40) - A) - (1LL << 40);
+    return (int)t0;
+}
+
+// psi^(xi) for xi = alpha s (s from the fixed-point offset S), double-float
+// throughout: the piece and its coordinate as in psihat_df.
+__device__ __forceinline__ df psihat_fx(const Tables& T, const AsyBlock& B, long long S)
+{
+    const float sc = ldexpf(1.f, -B.fw);
+    const df s = df_from_i64(S < 0 ? -S : S);
+    const df xi = df_mul(df{B.alpha_h, B.alpha_l}, df{s.h * sc, s.l * sc});
+    const df t = df_mul(xi, df{T.ph_scale2.x, T.ph_scale2.y});
+    int piece = (int)t.h;
+    if ((float)piece == t.h && t.l < 0.f && piece > 0) --piece;
+    if (piece > T.ph_pieces - 1) piece = T.ph_pieces - 1;
+    const df u = df_add(t, df{-(float)piece, 0.f});
+    const df v = df_add(df{2.f * u.h, 2.f * u.l}, df{-1.f, 0.f});
+    return horner_comp(T.ph2 + piece * (T.ph_deg + 1), T.ph_deg, v.h, v.l);
 }
 
 constexpr int kSpreadSub = 8;       // point sub-ranges per moment, combined by shuffles
@@ -1140,14 +1190,11 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     int* t0s = (int*)(U + kInterpTileThreads * us);              // [threads]
     const bool valid = (int)threadIdx.x < t.count;
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
-    const double wk = w_s[k];
-    const double s = wk - B.wc;
-    const double a = s * B.hd - tab.half_w;
-    const double tf = ceil(a);
-    const double v = fma(2.0, tf - a, -1.0);   // tf - a in [0, 1]
-    const float vh = (float)v, vl = (float)(v - (double)vh);
+    long long Om, Sw, svw;
+    const int t0 = interp_cell_sv(B, tab.w, w_s[k], &Om, &Sw, &svw);
+    const df vdf = df_from_sv(svw);
+    const float vh = vdf.h, vl = vdf.l;
     // the tile's targets are sorted, so their cells form one window
-    const int t0 = (int)tf;
     if (valid) t0s[threadIdx.x] = t0;
     __syncthreads();
     const int wstart = t0s[0];
@@ -1310,7 +1357,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
         mq = df_mul(mq, mz);
     }
     df sn, cs;
-    df_sincos_prod(wk, B.rc, &sn, &cs);
+    df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
     // Re(e^{i (omega r_c + phi)} T) = Re(e^{i omega r_c} (e^{i phi} T))
     const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
     const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
@@ -1318,9 +1365,10 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const df ui = df_add(df_mul(sph, tre), df_mul(cph, tim));
     const df re = df_add(df_mul(cs, ur), df_negate(df_mul(sn, ui)));
     // sqrt(2/pi) (omega rho)^(-1/2) (4 / w^2) / psi^(alpha s)
-    const df scale = df_mul(df_sqrt(m1d), df_recip(psihat_df(tab, B.alpha * s)));
-    const double val = tab.interp_const * df_to(df_mul(scale, re));
-    atomicAdd(&g_s[k], (double)P.sgn * val);
+    const df scale = df_mul(df_sqrt(m1d), df_recip(psihat_fx(tab, B, Sw)));
+    df outv = df_mul(df_mul(scale, re), df{tab.ic2.x, tab.ic2.y});
+    if (P.sgn < 0) outv = df_negate(outv);
+    atomicAdd(&g_s[k], df_to(outv));
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1358,27 +1406,25 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
     if (tid < cnt) {
         const int64_t k = t.start + tid;
         const double wk = w_s[k];
-        const double s = wk - B.wc;
-        const double a = s * B.h * B.inv_delta - tab.half_w;
-        const double tf = ceil(a);
-        double z0 = fmin(fmax(tf - a, 0.0), 1.0);
-        const double v = 2.0 * z0 - 1.0;
-        const float vh = (float)v, vl = (float)(v - (double)vh);
+        long long Om, Sw, svw;
+        const int t0 = interp_cell_sv(B, w, wk, &Om, &Sw, &svw);
+        const df vdf = df_from_sv(svw);
+        const float vh = vdf.h, vl = vdf.l;
         for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
-        t0s[tid] = (int)tf;
+        t0s[tid] = t0;
         // g_k sqrt(2/pi) (4/w^2) / psi^(alpha s) (omega rho)^(-1/2) e^{i (omega r_c + phi)}
         const df m1d = df_recip(df_from(wk * B.rho));
         const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});
         df sn, cs;
-        df_sincos_prod(wk, B.rc, &sn, &cs);
+        df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
         const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
         const df er = df_add(df_mul(cs, cph), df_negate(df_mul(sn, sph)));
         const df ei = df_add(df_mul(sn, cph), df_mul(cs, sph));
         const df amp = df_mul(df_mul(df_from((double)P.sgn * g_s[k] * tab.interp_const), df_sqrt(m1d)),
-                              df_recip(psihat_df(tab, B.alpha * s)));
+                              df_recip(psihat_fx(tab, B, Sw)));
         df fr = df_mul(amp, er), fi = df_mul(amp, ei);
         df mq{1.f, 0.f};
         for (int q = 0; q < Q; ++q) {

@@ -67,7 +67,14 @@ __global__ void k_block_sizes(BlockBuild bb)
             ab.rc = ldexp(rint(ldexp(0.5 * (e.x + e.y), ab.fr - 10)), 10 - ab.fr);
             ab.Rc_fx = (int64_t)ldexp(ab.rc, ab.fr);
             const double X = 0.5 * (e.y - e.x);
-            ab.wc = 0.5 * (e.z + e.w);
+            {
+                // w_c rounded to a multiple of 2^(10 - fw), like r_c
+                int eo;
+                frexp(e.w, &eo);
+                ab.fw = 62 - eo;
+                ab.wc = ldexp(rint(ldexp(0.5 * (e.z + e.w), ab.fw - 10)), 10 - ab.fw);
+                ab.Wc_fx = (int64_t)ldexp(ab.wc, ab.fw);
+            }
             const double S = 0.5 * (e.w - e.z);
             const double Seff = S > 0.0 ? S : 1.0;
             ab.h = M_PI / (2.0 * Seff);
@@ -115,6 +122,30 @@ __global__ void k_block_sizes(BlockBuild bb)
             ab.alpha2 = ldexp(bb.w * M_PI, -lg);
             ab.inv_delta = ab.nf2 * (0.5 / M_PI);
             ab.hd = ab.h * ab.inv_delta;
+            ab.alpha_h = (float)ab.alpha;
+            ab.alpha_l = (float)(ab.alpha - (double)ab.alpha_h);
+            {
+                int ed, er2;
+                frexp(ab.hd, &ed);
+                ab.KD = (int64_t)ldexp(ab.hd, 62 - ed);          // exact: 53-bit mantissa
+                ab.sD = ab.fw + 62 - ed - 40;   // 40 fractional bits: |s hd| <= nf2 / 4 <= 2^22
+                const double c_hi = 0.15915494309189535, c_lo = -9.839338337591243e-18;
+                const double p = ab.rc * c_hi;
+                const double err = fma(ab.rc, c_hi, -p) + ab.rc * c_lo;
+                frexp(p, &er2);
+                int64_t kr = llrint(ldexp(p, 62 - er2)) + llrint(ldexp(err, 62 - er2));
+                int sr = ab.fw + 62 - er2 - 64;
+                if (sr > 64) {
+                    kr = sr - 64 < 63 ? kr >> (sr - 64) : 0;
+                    sr = 64;
+                }
+                ab.KRc = kr;
+                ab.sR = sr;
+                if (ab.sD < 1 || ab.sD > 127 || sr < 0) {
+                    atomic_max64(&bb.maxv[MX_ERR], 1);
+                    continue;
+                }
+            }
             ab.rho_h = (float)ab.rho;
             ab.rho_l = (float)(ab.rho - (double)ab.rho_h);
             bb.asy[a] = ab;

@@ -77,6 +77,14 @@ struct AsyBlock {
     // in turns is bits [sW, sW + 63] of X * KW (64 fractional bits).
     int64_t Rc_fx, KH, KW;
     int32_t fr, sA, sW, pad_fx;
+    // The same for the frequencies: Om = round(omega 2^fw) < 2^62, S = Om - Wc_fx
+    // (w_c a multiple of 2^(10 - fw)); the FFT-grid coordinate s hd is bits
+    // [sD, sD + 63] of S * KD (40 fractional bits), the phase omega r_c / (2 pi)
+    // in turns bits [sR, sR + 63] of Om * KRc (64 fractional bits).
+    int64_t Wc_fx, KD, KRc;
+    int32_t fw, sD, sR;
+    float alpha_h, alpha_l;   // alpha as double-float
+    int32_t pad_fx2;
 };
 
 struct DirectBlock {
@@ -164,6 +172,8 @@ struct Tables {
     const double* ph;      // psi-hat pieces [ph_pieces][ph_deg + 1] in v in [-1, 1]
     const float2* ph2;     // the same as double-float
     double interp_const;   // sqrt(2/pi) * 4 / w^2
+    float2 ic2;            // the same as double-float
+    float2 ph_scale2;      // ph_scale as double-float
     int ph_pieces, ph_deg;
     double ph_scale;       // pieces per unit of xi
     double ph_xmax;        // table covers xi in [0, ph_xmax]

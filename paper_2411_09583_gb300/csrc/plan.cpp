@@ -748,7 +748,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     tb.ph = P->d_ph; tb.ph2 = (const float2*)(D + a_ph2);
     tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
     tb.interp_const = std::sqrt(2.0 / M_PI) * 4.0 / ((double)T.w * (double)T.w);
+    tb.ic2 = make_float2((float)tb.interp_const, (float)(tb.interp_const - (double)(float)tb.interp_const));
     tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
+    tb.ph_scale2 = make_float2((float)T.ph_scale, (float)(T.ph_scale - (double)(float)T.ph_scale));
     tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
     tb.tw2 = (const float4*)(D + a_tw2);
     P->plan_ms[3] = ms_since(clk);
