@@ -1221,13 +1221,14 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     }
     __syncthreads();
     if (mom) {
-        // H[b][d][q'] = sum_i A[i][d] G[wstart + b + i][q'], double-float for d < dci
+        // H[b][d][q'] = sum_i A[i][d] G[wstart + b + i][q'], double-float for
+        // d < dci and q < qs (the frequencies read only the FP32 part of the rest)
         for (int o = threadIdx.x; o < nbins * nb * Q2; o += blockDim.x) {
             const int b = o / (nb * Q2), rem = o - b * nb * Q2;
             const int d = rem / Q2, qv = rem - d * Q2;
             const int q = qv >> 1, im = qv & 1;
             float2 hv;
-            if (d < dci) {
+            if (d < dci && q < P.qs) {
                 acc2 acc{0.f, 0.f};
 #pragma unroll 4
                 for (int i = 0; i < w; ++i) {
