@@ -21,8 +21,8 @@ namespace nuht {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;                       // elements per thread per tile
-constexpr int kSortTile = kSortThreads * kSortItems; // 4096
+constexpr int kSortItems = 4;                       // elements per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems; // 1024: ~4 CTAs per SM at n = 1e6 (4096 left the scatter passes latency-bound)
 constexpr int kRadix = 256;
 static_assert(kSortThreads == kRadix, "the scatter kernel scans one digit total per thread");
 
