@@ -291,6 +291,94 @@ __device__ __forceinline__ double jn_hankel_df(const ProbParams& P, double w, do
     return df_to(df_mul(amp, df_add(df_mul(pp, cchi), df_negate(df_mul(qq, schi)))));
 }
 
+// Direct entries in a fixed-point frame per direct block: Om = omega 2^fw and
+// R = r 2^fr are integers below 2^62, so P = Om R = omega r 2^(fw + fr) is
+// exact in 128 bits.  x = omega r comes from its top bits as double-float and
+// the phase omega r / (2 pi) in turns from bits of P * round(2^64 / (2 pi)),
+// all with integer instructions (FP64 runs at 1/64 of the FP32 rate here).
+struct DirFx {
+    int fr, fw;
+};
+
+// (hi 2^64 + lo) 2^-s as double-float (relative 2^-48); 0 for 0.
+__device__ __forceinline__ df df_from_u128(unsigned long long hi, unsigned long long lo, int s)
+{
+    if (hi == 0 && lo == 0) return df{0.f, 0.f};
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+    unsigned long long t;
+    if (lz == 0) t = hi;
+    else if (lz < 64) t = (hi << lz) | (lo >> (64 - lz));
+    else t = lo << (lz - 64);
+    const int e = 64 - lz - s;   // value = t 2^e
+    const float h = ldexpf((float)(unsigned)(t >> 40), e + 40);
+    const float l = ldexpf((float)(unsigned)((t >> 16) & 0xFFFFFF), e + 16);
+    return fast_two_sum(h, l);
+}
+
+// The fraction of a turn of P 2^-s / (2 pi) in 64-bit fixed point, 64 <= s <= 127.
+__device__ __forceinline__ unsigned long long turns_u128(unsigned long long Ph, unsigned long long Pl, int s)
+{
+    const unsigned long long C = 2935890503282001226ULL;   // round(2^64 / (2 pi))
+    const unsigned long long a_lo = Ph * C, a_hi = __umul64hi(Ph, C);
+    const unsigned long long b_hi = __umul64hi(Pl, C);
+    const int t = s - 64;
+    const unsigned long long A = t == 0 ? a_lo : (a_hi << (64 - t)) | (a_lo >> t);
+    return A + (b_hi >> t);
+}
+
+// jn_hankel_df with x = omega r given as double-float and its phase in turns.
+__device__ __forceinline__ double jn_hankel_dfx(const ProbParams& P, df x, unsigned long long turns)
+{
+    const df y = df_recip(x);
+    const df u = df_mul(y, df{P.z2.x, P.z2.y});
+    const df u2 = df_mul(u, u);
+    df pp{0.f, 0.f}, qq{0.f, 0.f};
+    for (int l = P.M - 1; l >= 0; --l) {
+        const float2 a0 = P.a2[2 * l], a1 = P.a2[2 * l + 1];
+        const bool neg = l & 1;
+        pp = df_add(df_mul(pp, u2), neg ? df{-a0.x, -a0.y} : df{a0.x, a0.y});
+        qq = df_add(df_mul(qq, u2), neg ? df{-a1.x, -a1.y} : df{a1.x, a1.y});
+    }
+    qq = df_mul(qq, u);
+    df sx, cx;
+    df_sincos_turns(turns, &sx, &cx);
+    const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
+    const df cchi = df_add(df_mul(cx, cph), df_negate(df_mul(sx, sph)));   // cos(x + phi)
+    const df schi = df_add(df_mul(sx, cph), df_mul(cx, sph));              // sin(x + phi)
+    const df amp = df_sqrt(df_mul(df{0.6366197466850281f, 2.5682552973194106e-08f}, y));   // sqrt(2 / (pi x))
+    return df_to(df_mul(amp, df_add(df_mul(pp, cchi), df_negate(df_mul(qq, schi)))));
+}
+
+// jn_miller_df with x >= 1 given as double-float (no FP64 divisions).
+__device__ __forceinline__ double jn_miller_dfx(int n, df x)
+{
+    const float xf = x.h;
+    const float a = xf + 20.f + 4.f * sqrtf(xf);
+    int ns = (int)a + 1;
+    if (ns < n + 8) ns = n + 8;
+    ns += ns & 1;
+    const df i2 = df_recip(df{0.5f * x.h, 0.5f * x.l});   // 2 / x
+    const float ih = i2.h, il = i2.l;
+    float f1, f0, fS;
+    const int i0 = miller_fp32_head(ns, miller_fp32_floor(n, xf), ih, &f1, &f0, &fS);
+    df jp1{f1, 0.f}, jc{f0, 0.f}, S{fS, 0.f}, res{0.f, 0.f};
+    for (int i = i0; i >= 2; i -= 2) {
+        const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
+        const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
+        if (i - 1 == n) res = jm;
+        if (i - 2 == n) res = jmm;
+        S = df_add(S, df{2.f * jmm.h, 2.f * jmm.l});
+        jp1 = jm;
+        jc = jmm;
+        if (df_big(jc)) {
+            const float sc = 8.673617379884035e-19f;   // 2^-60
+            jc = df_scale(jc, sc); jp1 = df_scale(jp1, sc); S = df_scale(S, sc); res = df_scale(res, sc);
+        }
+    }
+    S = df_add(S, df_neg(jc));
+    return df_to(df_mul(res, df_recip(S)));
+}
+
 // J_nu at the exact product w*r: asymptotic side (Hankel in double-float, or
 // FP32 when lowp) or local side (series; Miller in double-float, or FP32 when lowp).
 __device__ __forceinline__ double direct_entry(const ProbParams& P, double w, double r, bool asy, bool lowp)
@@ -299,6 +387,32 @@ __device__ __forceinline__ double direct_entry(const ProbParams& P, double w, do
     const double x = w * r;
     if (x < 1.0) return jn_series(P.nu, x);
     return lowp ? (double)jn_miller_f32(P.nu, (float)x) : jn_miller_df(P.nu, x);
+}
+
+// direct_entry in the block's fixed-point frame (double-float paths); the
+// series for x < 1 and the FP32 paths as in direct_entry.
+__device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, double w, double r, bool asy,
+                                                  bool lowp)
+{
+    const int s = F.fr + F.fw;
+    if (lowp || s < 64 || s > 127) return direct_entry(P, w, r, asy, lowp);
+    const unsigned long long Om = (unsigned long long)fx_from_double(w, F.fw);
+    const unsigned long long R = (unsigned long long)fx_from_double(r, F.fr);
+    const unsigned long long Pl = Om * R, Ph = __umul64hi(Om, R);
+    const df x = df_from_u128(Ph, Pl, s);
+    if (asy) return jn_hankel_dfx(P, x, turns_u128(Ph, Pl, s));
+    if (x.h < 1.f) return jn_series(P.nu, w * r);
+    return jn_miller_dfx(P.nu, x);
+}
+
+// The fixed-point frame of a direct block: r < 2^(62 - fr), omega < 2^(62 - fw).
+__device__ __forceinline__ DirFx direct_frame(const double* __restrict__ r_s, const double* __restrict__ w_s,
+                                              const DirectBlock& B)
+{
+    int er, ew;
+    frexp(r_s[B.j1], &er);
+    frexp(w_s[B.k1], &ew);
+    return DirFx{62 - er, 62 - ew};
 }
 
 // Splits the entries of a direct block into a local list (omega r <= z, from
@@ -335,10 +449,11 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
     int* list = (int*)(rowacc + rows);
     for (int i = threadIdx.x; i < rows; i += blockDim.x) rowacc[i] = 0.0;
     const int nloc = direct_partition(P, B, cols, area, r_s, w_s, list, cnt);
+    const DirFx F = direct_frame(r_s, w_s, B);
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
-        const double v = direct_entry(P, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
+        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
         atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
     }
     __syncthreads();
@@ -464,10 +579,11 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
     int* list = (int*)(colacc + cols);
     for (int i = threadIdx.x; i < cols; i += blockDim.x) colacc[i] = 0.0;
     const int nloc = direct_partition(P, B, cols, area, r_s, w_s, list, cnt);
+    const DirFx F = direct_frame(r_s, w_s, B);
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
-        const double v = direct_entry(P, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
+        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
         atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
     }
     __syncthreads();
