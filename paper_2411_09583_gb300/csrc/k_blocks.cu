@@ -76,7 +76,9 @@ __global__ void k_block_sizes(BlockBuild bb)
                 ab.Wc_fx = (int64_t)ldexp(ab.wc, ab.fw);
             }
             const double S = 0.5 * (e.w - e.z);
-            const double Seff = S > 0.0 ? S : 1.0;
+            // a single frequency (S = 0) takes any spacing: one that puts the
+            // block's points within a few cells (scale-free, unlike a constant)
+            const double Seff = S > 0.0 ? S : (X > 0.0 ? 1.0 / X : 1.0);
             ab.h = M_PI / (2.0 * Seff);
             ab.inv_h = (2.0 / M_PI) * Seff;
             {

@@ -26,7 +26,19 @@ constexpr int kSubThreads = 1024;
 constexpr int kSubCandUnroll = 16;   // candidate rows loaded together (the default n_cand)
 constexpr int kSubWarps = kSubThreads / 32;
 
-// 0 empty, 1 local, 2 asymptotic, 3 direct, 4 mixed (split further)
+// An asymptotic block too large for one FFT (X S > kAsyMaxXS) is queued like
+// a mixed one, flagged in its problem index, and cut into quadrants; the host
+// walk does the same in the same order.
+constexpr int32_t kQuadFlag = 0x40000000;
+
+__device__ __forceinline__ bool asy_too_big(const double* __restrict__ r, const double* __restrict__ w,
+                                            const SubBlk& b)
+{
+    return 0.5 * (r[b.j1] - r[b.j0]) * 0.5 * (w[b.k1] - w[b.k0]) > kAsyMaxXS;
+}
+
+// 0 empty, 1 local, 2 asymptotic, 3 direct, 4 mixed (split further), 5
+// asymptotic but too large (cut into quadrants)
 __device__ __forceinline__ int classify(const int32_t* __restrict__ st, const SubBlk& b, int64_t min_size)
 {
     if (b.k1 < b.k0 || b.j1 < b.j0) return 0;
@@ -89,7 +101,7 @@ __device__ __forceinline__ void emit(const SubBlk* ch, const int* cls, int nch, 
 {
     uint64_t cnt = 0;
     for (int i = 0; i < nch; ++i)
-        if (cls[i] > 0) cnt += (uint64_t)1 << (16 * (cls[i] - 1));
+        if (cls[i] > 0) cnt += (uint64_t)1 << (16 * ((cls[i] < 4 ? cls[i] : 4) - 1));
     uint64_t total;
     const uint64_t off = block_scan(cnt, wsum, &total);
     int64_t pos[4];
@@ -102,8 +114,13 @@ __device__ __forceinline__ void emit(const SubBlk* ch, const int* cls, int nch, 
         for (int i = 0; i < nch; ++i) {
             const int c = cls[i];
             if (c == 0) continue;
-            if (c == 4) next[pos[3]++] = ch[i];
-            else out[(c - 1) * ocap + pos[c - 1]++] = ch[i];
+            if (c >= 4) {
+                SubBlk q = ch[i];
+                if (c == 5) q.prob |= kQuadFlag;
+                next[pos[3]++] = q;
+            } else {
+                out[(c - 1) * ocap + pos[c - 1]++] = ch[i];
+            }
         }
     }
     __syncthreads();
@@ -119,7 +136,8 @@ __device__ __forceinline__ void emit(const SubBlk* ch, const int* cls, int nch, 
 }
 
 __global__ void __launch_bounds__(kSubThreads) k_subdivide(
-    const int32_t* __restrict__ stair, const ProbParams* __restrict__ probs, int nprob, int64_t min_size,
+    const int32_t* __restrict__ stair, const double* __restrict__ r_s, const double* __restrict__ w_s,
+    const ProbParams* __restrict__ probs, int nprob, int64_t min_size,
     int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* __restrict__ out, int64_t ocap,
     int64_t* __restrict__ res)
 {
@@ -140,6 +158,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subdivide(
             const ProbParams& P = probs[p];
             ch = SubBlk{0, (int32_t)P.m - 1, 0, (int32_t)P.n - 1, p};
             cls = classify(stair + P.w_off, ch, min_size);
+            if (cls == 2 && asy_too_big(r_s + P.r_off, w_s + P.w_off, ch)) cls = 5;
         }
         emit(&ch, &cls, 1, S, wsum, out, ocap, qa, qcap);
     }
@@ -152,7 +171,22 @@ __global__ void __launch_bounds__(kSubThreads) k_subdivide(
             const int64_t i = base + threadIdx.x;
             SubBlk ch[4];
             int cls[4] = {0, 0, 0, 0};
-            if (i < na) {
+            if (i < na && (qa[i].prob & kQuadFlag)) {
+                // an asymptotic block too large for one FFT: its quadrants
+                SubBlk b = qa[i];
+                b.prob &= ~kQuadFlag;
+                const ProbParams& P = probs[b.prob];
+                const int km = (b.k0 + b.k1) >> 1, jm = (b.j0 + b.j1) >> 1;
+                ch[0] = SubBlk{b.k0, km, b.j0, jm, b.prob};
+                ch[1] = SubBlk{km + 1, b.k1, jm + 1, b.j1, b.prob};
+                ch[2] = SubBlk{b.k0, km, jm + 1, b.j1, b.prob};
+                ch[3] = SubBlk{km + 1, b.k1, b.j0, jm, b.prob};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool ne = ch[c].k1 >= ch[c].k0 && ch[c].j1 >= ch[c].j0;
+                    cls[c] = ne ? (asy_too_big(r_s + P.r_off, w_s + P.w_off, ch[c]) ? 5 : 2) : 0;
+                }
+            } else if (i < na) {
                 const SubBlk b = qa[i];
                 const int32_t* st = stair + probs[b.prob].w_off;
                 // SplitIndices: the candidate row minimising the mixed area,
@@ -200,8 +234,12 @@ __global__ void __launch_bounds__(kSubThreads) k_subdivide(
                     sk1[c] = ne ? st[ch[c].k1] : 0;
                     sk0[c] = ne ? st[ch[c].k0] : 0;
                 }
+                const ProbParams& P = probs[b.prob];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) cls[c] = classify_v(ch[c], sk0[c], sk1[c], min_size);
+                for (int c = 0; c < 4; ++c) {
+                    cls[c] = classify_v(ch[c], sk0[c], sk1[c], min_size);
+                    if (cls[c] == 2 && asy_too_big(r_s + P.r_off, w_s + P.w_off, ch[c])) cls[c] = 5;
+                }
             }
             emit(ch, cls, 4, S, wsum, out, ocap, qb, qcap);
         }
@@ -242,11 +280,13 @@ __global__ void k_block_bounds(const SubBlk* __restrict__ loc, const SubBlk* __r
 
 }  // namespace
 
-cudaError_t launch_subdivide(const int32_t* stair, const ProbParams* probs, int nprob, int64_t min_size,
+cudaError_t launch_subdivide(const int32_t* stair, const double* r_s, const double* w_s, const ProbParams* probs,
+                             int nprob, int64_t min_size,
                              int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* out, int64_t ocap,
                              int64_t* res, cudaStream_t s)
 {
-    k_subdivide<<<1, kSubThreads, 0, s>>>(stair, probs, nprob, min_size, n_cand, qa, qb, qcap, out, ocap, res);
+    k_subdivide<<<1, kSubThreads, 0, s>>>(stair, r_s, w_s, probs, nprob, min_size, n_cand, qa, qb, qcap, out, ocap,
+                                          res);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -45,8 +45,10 @@ struct HBlock {
 
 // Algorithm 1 with SplitIndices on the sorted matrix, from the staircase
 // stair[k] = max{j : omega_k r_j <= z} (or -1) of every row.
-void subdivide(const int32_t* stair, int64_t n, int64_t m, int64_t min_size, int n_cand,
-               std::vector<HBlock>& loc, std::vector<HBlock>& asy, std::vector<HBlock>& dir);
+// r, omega: the problem's sorted values (for the size limit of asymptotic blocks).
+void subdivide(const int32_t* stair, const double* r, const double* omega, int64_t n, int64_t m,
+               int64_t min_size, int n_cand, std::vector<HBlock>& loc, std::vector<HBlock>& asy,
+               std::vector<HBlock>& dir);
 
 // Device memory from the library's pool (kept reserved between plans) and
 // pinned host staging buffers (grow-only, used under stage_lock()).

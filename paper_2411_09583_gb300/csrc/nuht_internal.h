@@ -16,6 +16,11 @@ constexpr int kMaxM = 20;           // Hankel term pairs (Sec. 3.3 caps M at 20)
 constexpr int kMaxQ = 2 * kMaxM;    // weight powers q = 0..2M-1
 constexpr int kMaxW = 16;           // ES kernel width
 constexpr int kMaxDeg = 20;         // degree of the kernel piece polynomials
+// An asymptotic block whose half-widths X (in r) and S (in omega) have
+// X S above this is cut into quadrants (all asymptotic) until it is not: its
+// spreading grid then has N1 ~ 2 X S / pi + w/2 <= ~2.04e6 cells and its FFT
+// at most 2^23 points (the single-FFT limit is 2^kFftMaxLog2).
+constexpr double kAsyMaxXS = 3.2e6;
 constexpr int kMomFold = 32;        // FP32 partial sums of the spreading moments span at most this many points
 constexpr int kMaxNtop = 400;       // largest Bessel index kept by the local evaluation
                                     // (the transposed moments then stay within 205 KB of shared memory)
@@ -196,7 +201,8 @@ cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_
                              int32_t* s_out, cudaStream_t s);
 // Algorithm 1 on the device (one CTA): lists out[0..ocap) local,
 // out[ocap..2 ocap) asymptotic, out[2 ocap..3 ocap) direct; res = {counts, overflow}.
-cudaError_t launch_subdivide(const int32_t* stair, const ProbParams* probs, int nprob, int64_t min_size,
+cudaError_t launch_subdivide(const int32_t* stair, const double* r_s, const double* w_s, const ProbParams* probs,
+                             int nprob, int64_t min_size,
                              int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* out, int64_t ocap,
                              int64_t* res, cudaStream_t s);
 cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int64_t* res, const ProbParams* probs,

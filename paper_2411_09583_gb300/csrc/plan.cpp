@@ -470,7 +470,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     int64_t* d_res = (int64_t*)(sort_mem + o_res);
     double* d_bl = (double*)(sort_mem + o_bl);
     double4* d_ba = (double4*)(sort_mem + o_ba);
-    NUHT_CK(launch_subdivide(stair, d_prb, nprob, P->opt.min_size, P->opt.n_split_cand, (SubBlk*)(sort_mem + o_qa),
+    NUHT_CK(launch_subdivide(stair, r_s, w_s, d_prb, nprob, P->opt.min_size, P->opt.n_split_cand, (SubBlk*)(sort_mem + o_qa),
                              (SubBlk*)(sort_mem + o_qb), qcap, d_out, ocap, d_res, s));
     NUHT_CK(launch_block_bounds(d_out, d_out + ocap, d_res, d_prb, r_s, w_s, d_bl, d_ba, s));
     P->eval_threads = local_eval_threads(P->ntop_max);
@@ -535,7 +535,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         std::vector<HBlock> lb, ab, db;
         for (int ip = 0; ip < nprob; ++ip) {
             const ProbParams& q = probs[ip];
-            subdivide(hst + q.w_off, q.n, q.m, P->opt.min_size, P->opt.n_split_cand, lb, ab, db);
+            subdivide(hst + q.w_off, hr + q.r_off, hw + q.w_off, q.n, q.m, P->opt.min_size, P->opt.n_split_cand,
+                      lb, ab, db);
             const std::vector<HBlock>* src[3] = {&lb, &ab, &db};
             for (int c = 0; c < 3; ++c)
                 for (const HBlock& h : *src[c]) {

@@ -16,14 +16,20 @@
 //  * blocks that are entirely local (or asymptotic) go to the local (or
 //    asymptotic) list whatever their size; empty blocks are dropped;
 //  * the work list is first-in first-out.
+// One rule of this implementation, not the paper's: an asymptotic block whose
+// space-frequency product is above what one FFT of the device handles
+// (X S > kAsyMaxXS) goes back on the work list to be cut into quadrants
+// (every part of an asymptotic block is asymptotic), in the same order as the
+// device subdivision.
 #include <deque>
 
 #include "nuht_host.h"
 
 namespace nuht {
 
-void subdivide(const int32_t* stair, int64_t n, int64_t m, int64_t min_size, int n_cand,
-               std::vector<HBlock>& loc, std::vector<HBlock>& asy, std::vector<HBlock>& dir)
+void subdivide(const int32_t* stair, const double* r, const double* omega, int64_t n, int64_t m,
+               int64_t min_size, int n_cand, std::vector<HBlock>& loc, std::vector<HBlock>& asy,
+               std::vector<HBlock>& dir)
 {
     // stair[k] = max{j : omega_k r_j <= z} over the whole sorted r (or -1), so
     // within columns j0..j1: last local column = min(stair[k], j1), or j0 - 1
@@ -33,19 +39,32 @@ void subdivide(const int32_t* stair, int64_t n, int64_t m, int64_t min_size, int
     asy.clear();
     dir.clear();
     if (n <= 0 || m <= 0) return;
-    std::deque<HBlock> work;
+    std::deque<std::pair<HBlock, bool>> work;   // (block, cut into quadrants)
     auto place = [&](int64_t k0, int64_t k1, int64_t j0, int64_t j1) {
         if (k1 < k0 || j1 < j0) return;
         const HBlock b{k0, k1, j0, j1};
         if (stair[k1] >= j1) { loc.push_back(b); return; }
-        if (stair[k0] < j0) { asy.push_back(b); return; }
+        if (stair[k0] < j0) {
+            if (0.5 * (r[j1] - r[j0]) * 0.5 * (omega[k1] - omega[k0]) > kAsyMaxXS) work.push_back({b, true});
+            else asy.push_back(b);
+            return;
+        }
         if ((k1 - k0 + 1) * (j1 - j0 + 1) <= min_size) { dir.push_back(b); return; }
-        work.push_back(b);
+        work.push_back({b, false});
     };
     place(0, m - 1, 0, n - 1);
     while (!work.empty()) {
-        const HBlock b = work.front();
+        const HBlock b = work.front().first;
+        const bool quad = work.front().second;
         work.pop_front();
+        if (quad) {
+            const int64_t km = (b.k0 + b.k1) >> 1, jm = (b.j0 + b.j1) >> 1;
+            place(b.k0, km, b.j0, jm);
+            place(km + 1, b.k1, jm + 1, b.j1);
+            place(b.k0, km, jm + 1, b.j1);
+            place(km + 1, b.k1, b.j0, jm);
+            continue;
+        }
         const int64_t rows = b.k1 - b.k0 + 1;
         int64_t best_area = -1, bk = b.k0, bj = b.j0 - 1;
         const int64_t ncand = rows <= n_cand ? rows : n_cand;

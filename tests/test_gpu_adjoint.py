@@ -40,6 +40,16 @@ def test_adjoint_extreme_orders(nu, eps):
     assert np.max(np.abs(ca - ref)) <= tol(eps, e)
 
 
+def test_adjoint_scaled_inputs():
+    # the fixed-point frames of the transposed kernels far from unit scale
+    r, omega, _ = uniform_problem(1200, 1100, omega_max=3000.0, seed=92)
+    e = np.random.default_rng(93).standard_normal(omega.size)
+    for sr, sw in ((1e5, 1e-5), (1e-6, 1e6)):
+        ca, _ = _adjoint(2, r * sr, omega * sw, e, 1e-10)
+        ref = oracle.direct(2, omega * sw, r * sr, e)
+        assert np.max(np.abs(ca - ref)) <= tol(1e-10, e)
+
+
 @pytest.mark.parametrize("nu", [0, 3])
 def test_dot_product_identity(nu):
     # <A c, e> = <c, A^T e> for the approximate operator itself (exact transpose)

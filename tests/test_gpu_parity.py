@@ -210,6 +210,27 @@ def test_relative_l2_error_tracks_eps(nu):
         assert rel <= max(10 * eps, 3e-13), (eps, rel)
 
 
+@pytest.mark.parametrize("scale_r,scale_w", [(1e4, 1e-4), (1e-5, 1e5), (3e7, 3e-7), (1e-9, 1e9)])
+def test_scaled_inputs(scale_r, scale_w):
+    # J_nu(omega r) depends on omega r only: the same matrix with r scaled up
+    # and omega down (or the reverse) exercises the fixed-point frames of the
+    # blocks (bit positions set by each block's largest r and omega) far from
+    # unit scale; the oracle sees the same scaled inputs
+    r, omega, c = uniform_problem(1500, 1400, omega_max=3000.0, seed=80)
+    _check(0, r * scale_r, omega * scale_w, c, 1e-10)
+
+
+def test_wide_dynamic_range():
+    # r log-uniform over 11 decades, omega over 8: blocks whose points (or
+    # frequencies) span many binary orders of magnitude
+    rng = np.random.default_rng(81)
+    r = 10.0 ** rng.uniform(-8, 3, 1600)
+    omega = 10.0 ** rng.uniform(-3, 5, 1500)
+    c = rng.standard_normal(1600)
+    for nu, eps in ((0, 1e-9), (5, 1e-12)):
+        _check(nu, r, omega, c, eps)
+
+
 @pytest.mark.parametrize("nu,eps", [(0, 1e-8), (3, 1e-12), (10, 1e-10)])
 def test_fourier_bessel_grid(nu, eps):
     # Sec. 5.1.1's Fourier-Bessel case (n = m): frequencies at the roots of
