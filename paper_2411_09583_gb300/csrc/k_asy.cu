@@ -1590,6 +1590,23 @@ __device__ __forceinline__ void f32_sincos_prod(double a, double b, float* sn, f
     }
 }
 
+// sin, cos of 2 pi F / 2^64 (a fraction of a turn in 64-bit fixed point) in
+// FP32: the quadrant from the top bits, sincosf of the remainder.
+__device__ __forceinline__ void f32_sincos_turns(unsigned long long F, float* sn, float* cs)
+{
+    const unsigned long long Fq = F + (1ULL << 61);
+    const long long rem = (long long)(Fq & ((1ULL << 62) - 1)) - (1LL << 61);
+    const float t = (float)(int)(rem >> 32) * 1.4629180792671596e-09f;   // 2 pi 2^-32
+    float s0, c0;
+    sincosf(t, &s0, &c0);
+    switch ((int)(Fq >> 62)) {
+        case 0: *sn = s0; *cs = c0; break;
+        case 1: *sn = c0; *cs = -s0; break;
+        case 2: *sn = -s0; *cs = -c0; break;
+        default: *sn = -c0; *cs = s0; break;
+    }
+}
+
 __device__ __forceinline__ float horner_f32(const float2* __restrict__ c, int deg, float v)
 {
     float acc = c[deg].x;
@@ -1628,9 +1645,10 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
     }
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        double xd, vd;
-        l0s[tid] = spread_cell(B, tab, r_s[j], &xd, &vd);
-        const float v = (float)vd;
+        long long Xp;
+        df vdf;
+        l0s[tid] = spread_cell_fx(B, tab.w, r_s[j], &Xp, &vdf);
+        const float v = vdf.h;
         float* u = U + tid * su;
         float tm = 1.f, tc = v;
         u[0] = 1.f;
@@ -1643,7 +1661,7 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
         }
         for (int d = nb; d < su; ++d) u[d] = 0.f;
         float sn, cs;
-        f32_sincos_prod(B.wc, xd, &sn, &cs);
+        f32_sincos_turns(mul128_bits(Xp, B.KW, B.sW), &sn, &cs);
         const float ratio = B.rho_h / r2[j].x;
         const float w0 = c2[j].x * sqrtf(ratio);
         float wr = w0 * cs, wi = w0 * sn;
@@ -1740,12 +1758,13 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
     const int cnt = t.count;
     if (tid < cnt) {
         const int64_t j = t.start + tid;
-        double xd, vd;
-        l0s[tid] = spread_cell(B, tab, r_s[j], &xd, &vd);
-        const float v = (float)vd;
+        long long Xp;
+        df vdf;
+        l0s[tid] = spread_cell_fx(B, tab.w, r_s[j], &Xp, &vdf);
+        const float v = vdf.h;
         for (int i = 0; i < w; ++i) taps[tid * w + i] = horner_f32(coef + i * (deg + 1), deg, v);
         float sn, cs;
-        f32_sincos_prod(B.wc, xd, &sn, &cs);
+        f32_sincos_turns(mul128_bits(Xp, B.KW, B.sW), &sn, &cs);
         const float ratio = B.rho_h / r2[j].x;
         const float w0 = c2[j].x * sqrtf(ratio);
         float wr = w0 * cs, wi = w0 * sn;
@@ -1804,9 +1823,10 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     const int Q = probs[B.prob].Q;
     if (t.count <= 0) return;
     if (threadIdx.x == 0) {
-        double x, v;
-        const int lfirst = spread_cell(B, tab, r_s[t.start], &x, &v);
-        const int nbins = spread_cell(B, tab, r_s[t.start + t.count - 1], &x, &v) - lfirst + 1;
+        long long X;
+        df vd;
+        const int lfirst = spread_cell_fx(B, tab.w, r_s[t.start], &X, &vd);
+        const int nbins = spread_cell_fx(B, tab.w, r_s[t.start + t.count - 1], &X, &vd) - lfirst + 1;
         use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
     }
     __syncthreads();
@@ -1847,12 +1867,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     int* t0s = (int*)(U + kInterpTileThreads * us);
     const bool valid = (int)threadIdx.x < t.count;
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
-    const double wk = w_s[k];
-    const double s = wk - B.wc;
-    const double a = s * B.hd - tab.half_w;
-    const double tf = ceil(a);
-    const float v = (float)fma(2.0, tf - a, -1.0);   // tf - a in [0, 1]
-    const int t0 = (int)tf;
+    long long Om, Sw, svw;
+    const int t0 = interp_cell_sv(B, tab.w, w_s[k], &Om, &Sw, &svw);
+    const float v = df_from_sv(svw).h;
     if (valid) t0s[threadIdx.x] = t0;
     __syncthreads();
     const int wstart = t0s[0];
@@ -1934,18 +1951,18 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
         mq *= m1 * P.z2.x;
     }
     float sn, cs;
-    f32_sincos_prod(wk, B.rc, &sn, &cs);
-    const float cph = (float)P.cphi, sph = (float)P.sphi;
+    f32_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+    const float cph = P.cphi2.x, sph = P.sphi2.x;
     const float ur = cph * tr - sph * ti, ui = sph * tr + cph * ti;
     const float re = cs * ur - sn * ui;
     // psi^(alpha s) in FP32 from the table's high parts
-    const double xi = fabs(B.alpha * s) * tab.ph_scale;
+    const float sf = df_from_i64(Sw < 0 ? -Sw : Sw).h * ldexpf(1.f, -B.fw);
+    const float xi = B.alpha_h * sf * tab.ph_scale2.x;
     int piece = (int)xi;
     if (piece > tab.ph_pieces - 1) piece = tab.ph_pieces - 1;
-    const float ph = horner_f32(tab.ph2 + piece * (tab.ph_deg + 1), tab.ph_deg,
-                                (float)(2.0 * (xi - (double)piece) - 1.0));
-    const float val = (float)tab.interp_const * sqrtf(m1) / ph * re;
-    atomicAdd(&g_s[k], (double)P.sgn * (double)val);
+    const float ph = horner_f32(tab.ph2 + piece * (tab.ph_deg + 1), tab.ph_deg, 2.f * (xi - (float)piece) - 1.f);
+    const float val = tab.ic2.x * sqrtf(m1) / ph * re;
+    atomicAdd(&g_s[k], (double)(P.sgn < 0 ? -val : val));
 }
 
 }  // namespace
