@@ -201,6 +201,23 @@ __device__ __forceinline__ void df_sincos_turns(unsigned long long F, df* sn, df
     df_sincos_quadrant(x, quad, sn, cs);
 }
 
+// sin, cos of 2 pi F / 2^64 (a fraction of a turn in 64-bit fixed point) in
+// FP32: the quadrant from the top bits, sincosf of the remainder.
+__device__ __forceinline__ void f32_sincos_turns(unsigned long long F, float* sn, float* cs)
+{
+    const unsigned long long Fq = F + (1ULL << 61);
+    const long long rem = (long long)(Fq & ((1ULL << 62) - 1)) - (1LL << 61);
+    const float t = (float)(int)(rem >> 32) * 1.4629180792671596e-09f;   // 2 pi 2^-32
+    float s0, c0;
+    sincosf(t, &s0, &c0);
+    switch ((int)(Fq >> 62)) {
+        case 0: *sn = s0; *cs = c0; break;
+        case 1: *sn = c0; *cs = -s0; break;
+        case 2: *sn = -s0; *cs = -c0; break;
+        default: *sn = -c0; *cs = s0; break;
+    }
+}
+
 // Bits [s, s + 63] of the signed 128-bit product X * K, 0 <= s <= 64.
 __device__ __forceinline__ unsigned long long mul128_bits(long long X, long long K, int s)
 {

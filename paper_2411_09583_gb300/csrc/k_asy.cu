@@ -1590,23 +1590,6 @@ __device__ __forceinline__ void f32_sincos_prod(double a, double b, float* sn, f
     }
 }
 
-// sin, cos of 2 pi F / 2^64 (a fraction of a turn in 64-bit fixed point) in
-// FP32: the quadrant from the top bits, sincosf of the remainder.
-__device__ __forceinline__ void f32_sincos_turns(unsigned long long F, float* sn, float* cs)
-{
-    const unsigned long long Fq = F + (1ULL << 61);
-    const long long rem = (long long)(Fq & ((1ULL << 62) - 1)) - (1LL << 61);
-    const float t = (float)(int)(rem >> 32) * 1.4629180792671596e-09f;   // 2 pi 2^-32
-    float s0, c0;
-    sincosf(t, &s0, &c0);
-    switch ((int)(Fq >> 62)) {
-        case 0: *sn = s0; *cs = c0; break;
-        case 1: *sn = c0; *cs = -s0; break;
-        case 2: *sn = -s0; *cs = -c0; break;
-        default: *sn = -c0; *cs = s0; break;
-    }
-}
-
 __device__ __forceinline__ float horner_f32(const float2* __restrict__ c, int deg, float v)
 {
     float acc = c[deg].x;

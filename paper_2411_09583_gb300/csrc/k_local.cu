@@ -389,20 +389,65 @@ __device__ __forceinline__ double direct_entry(const ProbParams& P, double w, do
     return lowp ? (double)jn_miller_f32(P.nu, (float)x) : jn_miller_df(P.nu, x);
 }
 
-// direct_entry in the block's fixed-point frame (double-float paths); the
-// series for x < 1 and the FP32 paths as in direct_entry.
+// jn_hankel_f32 with x = omega r in FP32 and its phase in turns.
+__device__ __forceinline__ float jn_hankel_f32x(const ProbParams& P, float x, unsigned long long turns)
+{
+    float sx, cx;
+    f32_sincos_turns(turns, &sx, &cx);
+    const float y = 1.f / x;
+    const float u = y * P.z2.x, u2 = u * u;   // z / x < 1, with the coefficients a_q z^-q
+    float pp = 0.f, qq = 0.f;
+    for (int l = P.M - 1; l >= 0; --l) {
+        const float sg = (l & 1) ? -1.f : 1.f;
+        pp = fmaf(pp, u2, sg * P.a2[2 * l].x);
+        qq = fmaf(qq, u2, sg * P.a2[2 * l + 1].x);
+    }
+    qq *= u;
+    const float cph = P.cphi2.x, sph = P.sphi2.x;
+    const float cchi = cx * cph - sx * sph, schi = sx * cph + cx * sph;
+    return sqrtf(0.6366197723675814f * y) * (pp * cchi - qq * schi);
+}
+
+// jn_miller_f32 with the start index from FP32 x (no FP64).
+__device__ __forceinline__ float jn_miller_f32x(int n, float x)
+{
+    const float a = x + 20.f + 4.f * sqrtf(x);
+    int ns = (int)a + 1;
+    if (ns < n + 8) ns = n + 8;
+    ns += ns & 1;
+    const float inv2x = 2.0f / x;
+    float jp1 = 0.f, jc = 1.f, S = 2.f, res = 0.f;
+    for (int i = ns; i >= 2; i -= 2) {
+        const float jm = fmaf((float)i * inv2x, jc, -jp1);
+        const float jmm = fmaf((float)(i - 1) * inv2x, jm, -jc);
+        if (i - 1 == n) res = jm;
+        if (i - 2 == n) res = jmm;
+        S = fmaf(2.f, jmm, S);
+        jp1 = jm;
+        jc = jmm;
+        if (fabsf(jc) > 1.152921504606847e18f) {
+            const float sc = 8.673617379884035e-19f;   // 2^-60
+            jc *= sc; jp1 *= sc; S *= sc; res *= sc;
+        }
+    }
+    return res / (S - jc);
+}
+
+// direct_entry in the block's fixed-point frame; the series for x < 1 as in
+// direct_entry.
 __device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, double w, double r, bool asy,
                                                   bool lowp)
 {
     const int s = F.fr + F.fw;
-    if (lowp || s < 64 || s > 127) return direct_entry(P, w, r, asy, lowp);
+    if (s < 64 || s > 127) return direct_entry(P, w, r, asy, lowp);
     const unsigned long long Om = (unsigned long long)fx_from_double(w, F.fw);
     const unsigned long long R = (unsigned long long)fx_from_double(r, F.fr);
     const unsigned long long Pl = Om * R, Ph = __umul64hi(Om, R);
     const df x = df_from_u128(Ph, Pl, s);
-    if (asy) return jn_hankel_dfx(P, x, turns_u128(Ph, Pl, s));
+    if (asy) return lowp ? (double)jn_hankel_f32x(P, x.h, turns_u128(Ph, Pl, s))
+                         : jn_hankel_dfx(P, x, turns_u128(Ph, Pl, s));
     if (x.h < 1.f) return jn_series(P.nu, w * r);
-    return jn_miller_dfx(P.nu, x);
+    return lowp ? (double)jn_miller_f32x(P.nu, x.h) : jn_miller_dfx(P.nu, x);
 }
 
 // The fixed-point frame of a direct block: r < 2^(62 - fr), omega < 2^(62 - fw).
