@@ -1222,32 +1222,58 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     __syncthreads();
     if (mom) {
         // H[b][d][q'] = sum_i A[i][d] G[wstart + b + i][q'], double-float for
-        // d < dci and q < qs (the frequencies read only the FP32 part of the rest)
-        for (int o = threadIdx.x; o < nbins * nb * Q2; o += blockDim.x) {
-            const int b = o / (nb * Q2), rem = o - b * nb * Q2;
-            const int d = rem / Q2, qv = rem - d * Q2;
-            const int q = qv >> 1, im = qv & 1;
-            float2 hv;
-            if (d < dci && q < P.qs) {
-                acc2 acc{0.f, 0.f};
+        // d < dci and q < qs (the frequencies read only the FP32 part of the
+        // rest); each thread forms two degrees x (re, im) of one q, four
+        // independent sums over the w cells
+        const int npr = (nb + 1) >> 1;
+        for (int o = threadIdx.x; o < nbins * npr * Q; o += blockDim.x) {
+            const int b = o / (npr * Q), rem = o - b * (npr * Q);
+            const int dp = rem / Q, q = rem - dp * Q;
+            const int d0 = 2 * dp, d1 = d0 + 1;
+            const bool has1 = d1 < nb;
+            float2* h0 = H + b * hs + d0 * Q2 + 2 * q;
+            if (d0 < dci && q < P.qs) {
+                acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
 #pragma unroll 4
                 for (int i = 0; i < w; ++i) {
                     const float4 gv = win[(b + i) * Q + q];
-                    const float2 c2 = coef2[i * nb + d];
-                    acc_fma(acc, df{c2.x, c2.y}, im ? df{gv.z, gv.w} : df{gv.x, gv.y});
+                    const float2 c0 = coef2[i * nb + d0];
+                    const float2 c1 = has1 ? coef2[i * nb + d1] : make_float2(0.f, 0.f);
+                    const df gr{gv.x, gv.y}, gi{gv.z, gv.w};
+                    acc_fma(a0r, df{c0.x, c0.y}, gr);
+                    acc_fma(a0i, df{c0.x, c0.y}, gi);
+                    acc_fma(a1r, df{c1.x, c1.y}, gr);
+                    acc_fma(a1i, df{c1.x, c1.y}, gi);
                 }
-                const df h2 = fast_two_sum(acc.s, acc.c);
-                hv = make_float2(h2.h, h2.l);
+                df v = fast_two_sum(a0r.s, a0r.c);
+                h0[0] = make_float2(v.h, v.l);
+                v = fast_two_sum(a0i.s, a0i.c);
+                h0[1] = make_float2(v.h, v.l);
+                if (has1) {
+                    v = fast_two_sum(a1r.s, a1r.c);
+                    h0[Q2] = make_float2(v.h, v.l);
+                    v = fast_two_sum(a1i.s, a1i.c);
+                    h0[Q2 + 1] = make_float2(v.h, v.l);
+                }
             } else {
-                float acc = 0.f;
+                float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
 #pragma unroll 4
                 for (int i = 0; i < w; ++i) {
                     const float4 gv = win[(b + i) * Q + q];
-                    acc = fmaf(coef2[i * nb + d].x, im ? gv.z : gv.x, acc);
+                    const float c0 = coef2[i * nb + d0].x;
+                    const float c1 = has1 ? coef2[i * nb + d1].x : 0.f;
+                    a0r = fmaf(c0, gv.x, a0r);
+                    a0i = fmaf(c0, gv.z, a0i);
+                    a1r = fmaf(c1, gv.x, a1r);
+                    a1i = fmaf(c1, gv.z, a1i);
                 }
-                hv = make_float2(acc, 0.f);
+                h0[0] = make_float2(a0r, 0.f);
+                h0[1] = make_float2(a0i, 0.f);
+                if (has1) {
+                    h0[Q2] = make_float2(a1r, 0.f);
+                    h0[Q2 + 1] = make_float2(a1i, 0.f);
+                }
             }
-            H[b * hs + rem] = hv;
         }
         __syncthreads();
     }
@@ -1287,66 +1313,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
     df mq{1.f, 0.f};
     const int qs = P.qs;
-    for (int q = 0; q < Q; ++q) {
-        df prd, pid;
-        if (mom) {
-            const float2* hq = Hb + 2 * q;
-            if (q < qs) {
-                acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
-                int d = 0;
-#pragma unroll 3
-                for (; d < dci; ++d) {
-                    const float2 tp = u[d];
-                    const float4 hv = *(const float4*)(hq + d * Q2);
-                    acc_fma(pr, df{tp.x, tp.y}, df{hv.x, hv.y});
-                    acc_fma(pi, df{tp.x, tp.y}, df{hv.z, hv.w});
-                }
-                float fr = 0.f, fi = 0.f;
-#pragma unroll 3
-                for (; d < nb; ++d) {
-                    const float tp = u[d].x;
-                    const float4 hv = *(const float4*)(hq + d * Q2);
-                    fr = fmaf(tp, hv.x, fr);
-                    fi = fmaf(tp, hv.z, fi);
-                }
-                pr.c += fr;
-                pi.c += fi;
-                prd = fast_two_sum(pr.s, pr.c);
-                pid = fast_two_sum(pi.s, pi.c);
-            } else {
-                // small Hankel term: FP32 is accurate enough
-                float pr = 0.f, pi = 0.f;
-#pragma unroll 4
-                for (int d = 0; d < nb; ++d) {
-                    const float tp = u[d].x;
-                    const float4 hv = *(const float4*)(hq + d * Q2);
-                    pr = fmaf(tp, hv.x, pr);
-                    pi = fmaf(tp, hv.z, pi);
-                }
-                prd = df{pr, 0.f};
-                pid = df{pi, 0.f};
-            }
-        } else if (q < qs) {
-            acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
-            for (int i = 0; i < w; ++i) {
-                const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                const float2 tp = u[i];
-                acc_fma(pr, df{tp.x, tp.y}, df{gv.x, gv.y});
-                acc_fma(pi, df{tp.x, tp.y}, df{gv.z, gv.w});
-            }
-            prd = fast_two_sum(pr.s, pr.c);
-            pid = fast_two_sum(pi.s, pi.c);
-        } else {
-            float pr = 0.f, pi = 0.f;
-            for (int i = 0; i < w; ++i) {
-                const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                const float tp = u[i].x;
-                pr = fmaf(tp, gv.x, pr);
-                pi = fmaf(tp, gv.z, pi);
-            }
-            prd = df{pr, 0.f};
-            pid = df{pi, 0.f};
-        }
+    auto combine = [&](int q, df prd, df pid) {
         const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
         // multiply by i^q: (pr + i pi) i^q
         switch (q & 3) {
@@ -1356,6 +1323,86 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
             default: acc_fma(tr, cq, pid); acc_fma(ti, df{-cq.h, -cq.l}, prd); break;
         }
         mq = df_mul(mq, mz);
+    };
+    if (mom) {
+        // Hankel terms in pairs (Q = 2M is even): four independent sums over
+        // the degrees, one basis load per degree
+        for (int q = 0; q < Q; q += 2) {
+            const float2* hq = Hb + 2 * q;
+            if (q < qs) {
+                acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
+                int d = 0;
+#pragma unroll 3
+                for (; d < dci; ++d) {
+                    const float2 tp = u[d];
+                    const df t{tp.x, tp.y};
+                    const float4 h0 = *(const float4*)(hq + d * Q2);
+                    const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
+                    acc_fma(a0r, t, df{h0.x, h0.y});
+                    acc_fma(a0i, t, df{h0.z, h0.w});
+                    acc_fma(a1r, t, df{h1.x, h1.y});
+                    acc_fma(a1i, t, df{h1.z, h1.w});
+                }
+                float f0r = 0.f, f0i = 0.f, f1r = 0.f, f1i = 0.f;
+#pragma unroll 3
+                for (; d < nb; ++d) {
+                    const float tp = u[d].x;
+                    const float4 h0 = *(const float4*)(hq + d * Q2);
+                    const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
+                    f0r = fmaf(tp, h0.x, f0r);
+                    f0i = fmaf(tp, h0.z, f0i);
+                    f1r = fmaf(tp, h1.x, f1r);
+                    f1i = fmaf(tp, h1.z, f1i);
+                }
+                a0r.c += f0r;
+                a0i.c += f0i;
+                a1r.c += f1r;
+                a1i.c += f1i;
+                combine(q, fast_two_sum(a0r.s, a0r.c), fast_two_sum(a0i.s, a0i.c));
+                combine(q + 1, fast_two_sum(a1r.s, a1r.c), fast_two_sum(a1i.s, a1i.c));
+            } else {
+                // small Hankel terms: FP32 is accurate enough
+                float p0r = 0.f, p0i = 0.f, p1r = 0.f, p1i = 0.f;
+#pragma unroll 4
+                for (int d = 0; d < nb; ++d) {
+                    const float tp = u[d].x;
+                    const float4 h0 = *(const float4*)(hq + d * Q2);
+                    const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
+                    p0r = fmaf(tp, h0.x, p0r);
+                    p0i = fmaf(tp, h0.z, p0i);
+                    p1r = fmaf(tp, h1.x, p1r);
+                    p1i = fmaf(tp, h1.z, p1i);
+                }
+                combine(q, df{p0r, 0.f}, df{p0i, 0.f});
+                combine(q + 1, df{p1r, 0.f}, df{p1i, 0.f});
+            }
+        }
+    } else {
+        for (int q = 0; q < Q; ++q) {
+            df prd, pid;
+            if (q < qs) {
+                acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                    const float2 tp = u[i];
+                    acc_fma(pr, df{tp.x, tp.y}, df{gv.x, gv.y});
+                    acc_fma(pi, df{tp.x, tp.y}, df{gv.z, gv.w});
+                }
+                prd = fast_two_sum(pr.s, pr.c);
+                pid = fast_two_sum(pi.s, pi.c);
+            } else {
+                float pr = 0.f, pi = 0.f;
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                    const float tp = u[i].x;
+                    pr = fmaf(tp, gv.x, pr);
+                    pi = fmaf(tp, gv.z, pi);
+                }
+                prd = df{pr, 0.f};
+                pid = df{pi, 0.f};
+            }
+            combine(q, prd, pid);
+        }
     }
     df sn, cs;
     df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
