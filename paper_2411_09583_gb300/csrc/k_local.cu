@@ -61,22 +61,39 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
     const int nt = blockDim.x, tid = threadIdx.x;
     for (int l = 0; l <= L; ++l) acc[l * nt + tid] = acc2{0.f, 0.f};
     const df invR{B.iR_h, B.iR_l};
-    for (int64_t j = t.start + tid; j < t.start + t.count; j += nt) {
-        const float2 rj = r2[j], cc = c2[j];
-        const df y = df_mul(df{rj.x, rj.y}, invR);                          // r_j / R in [0, 1]
-        const df cj{cc.x, cc.y};
-        const df u = df_add(df_mul(df{2.f * y.h, 2.f * y.l}, y), df{-1.f, 0.f});   // T_2(y)
-        const df u2{2.f * u.h, 2.f * u.l};
+    // two points per step: two independent recurrences (a point beyond the
+    // tile enters with c = 0)
+    const int64_t jend = t.start + t.count;
+    for (int64_t j = t.start + tid; j < jend; j += 2 * nt) {
+        const int64_t jb = j + nt < jend ? j + nt : j;
+        const float2 ra = r2[j], ca = c2[j], rb = r2[jb];
+        const float2 cb = j + nt < jend ? c2[jb] : make_float2(0.f, 0.f);
+        const df ya = df_mul(df{ra.x, ra.y}, invR), yb = df_mul(df{rb.x, rb.y}, invR);   // r_j / R in [0, 1]
+        const df cja{ca.x, ca.y}, cjb{cb.x, cb.y};
+        const df ua = df_add(df_mul(df{2.f * ya.h, 2.f * ya.l}, ya), df{-1.f, 0.f});   // T_2(y)
+        const df ub = df_add(df_mul(df{2.f * yb.h, 2.f * yb.l}, yb), df{-1.f, 0.f});
+        const df u2a{2.f * ua.h, 2.f * ua.l}, u2b{2.f * ub.h, 2.f * ub.l};
         // even: T_{2l}(y) = T_l(u); odd: T_{2l+1}(y) with T_1 = y, T_3 = y (2u - 1)
-        df t0 = odd ? y : df{1.f, 0.f};
-        df t1 = odd ? df_mul(y, df_add(u2, df{-1.f, 0.f})) : u;
-        acc_fma(acc[tid], cj, t0);
-        if (L >= 1) acc_fma(acc[nt + tid], cj, t1);
+        df t0a = odd ? ya : df{1.f, 0.f}, t0b = odd ? yb : df{1.f, 0.f};
+        df t1a = odd ? df_mul(ya, df_add(u2a, df{-1.f, 0.f})) : ua;
+        df t1b = odd ? df_mul(yb, df_add(u2b, df{-1.f, 0.f})) : ub;
+        acc_fma(acc[tid], cja, t0a);
+        acc_fma(acc[tid], cjb, t0b);
+        if (L >= 1) {
+            acc_fma(acc[nt + tid], cja, t1a);
+            acc_fma(acc[nt + tid], cjb, t1b);
+        }
         for (int l = 2; l <= L; ++l) {
-            const df t2 = df_add(df_mul(u2, t1), df_neg(t0));
-            acc_fma(acc[l * nt + tid], cj, t2);
-            t0 = t1;
-            t1 = t2;
+            const df t2a = df_add(df_mul(u2a, t1a), df_neg(t0a));
+            const df t2b = df_add(df_mul(u2b, t1b), df_neg(t0b));
+            acc2 a = acc[l * nt + tid];
+            acc_fma(a, cja, t2a);
+            acc_fma(a, cjb, t2b);
+            acc[l * nt + tid] = a;
+            t0a = t1a;
+            t1a = t2a;
+            t0b = t1b;
+            t1b = t2b;
         }
     }
     __syncthreads();
