@@ -44,6 +44,34 @@ __device__ __forceinline__ df df_imul(float fi, float ih, float il)
     return fast_two_sum(p, e);
 }
 
+// dst[l] += sum over the CTA's threads of acc[l * nt + thread], l <= L: one
+// warp per l, compensated FP32 sums (two-sums through the shuffles), one
+// conversion and one FP64 atomic per l (FP64 runs at 1/64 of the FP32 rate).
+__device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int L, double* dst)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int l = warp; l <= L; l += nw) {
+        acc2 a{0.f, 0.f};
+        for (int k = lane; k < nt; k += 32) {
+            const acc2 v = acc[l * nt + k];
+            float s, e;
+            two_sum(a.s, v.s, s, e);
+            a.s = s;
+            a.c += v.c + e;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_down_sync(0xffffffffu, a.s, off);
+            const float oc = __shfl_down_sync(0xffffffffu, a.c, off);
+            float s, e;
+            two_sum(a.s, os, s, e);
+            a.s = s;
+            a.c += oc + e;
+        }
+        if (lane == 0) atomicAdd(&dst[l], acc_value(a));
+    }
+}
+
 // One CTA per tile of columns of one local block.  Each thread keeps its own
 // column of partial moments (compensated double-float accumulators) in shared
 // memory, acc[l * blockDim + tid]; the columns are summed in FP64 at the end
@@ -97,14 +125,7 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
         }
     }
     __syncthreads();
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int l = warp; l <= L; l += nw) {
-        double s = 0.0;
-        for (int k = lane; k < nt; k += 32) s += acc_value(acc[l * nt + k]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) atomicAdd(&mom[B.mom_off + l], s);
-    }
+    reduce_columns_add(acc, nt, L, mom + B.mom_off);
 }
 
 // J_0..J_ntop(y), unnormalised, into this thread's column jb[n * nt + tid]
@@ -577,14 +598,7 @@ __global__ void k_local_adj_moments(const ProbParams* __restrict__ probs, const 
         }
     }
     __syncthreads();
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int l = warp; l <= L; l += nw) {
-        double s = 0.0;
-        for (int k = lane; k < nt; k += 32) s += acc_value(acc[l * nt + k]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) atomicAdd(&mom[B.mom_off + l], s);
-    }
+    reduce_columns_add(acc, nt, L, mom + B.mom_off);
 }
 
 __global__ void __launch_bounds__(kMomThreads)
