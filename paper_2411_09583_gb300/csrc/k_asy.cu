@@ -55,29 +55,6 @@ __device__ __forceinline__ df psihat_df(const Tables& T, double xi)
 // A point r_j of a block covers the w grid cells l0 + i, i < w, with
 // l0 = ceil((r_j - r_c)/h - w/2), and tap i of the ES kernel is the
 // polynomial piece psi_i(v), v = 2 (l0 - (r_j - r_c)/h + w/2) - 1 in [-1, 1].
-__device__ __forceinline__ int spread_cell(const AsyBlock& B, const Tables& tab, double rj, double* x, double* v)
-{
-    // explicit roundings: every call site computes the same cell
-    *x = __dadd_rn(rj, -B.rc);
-    const double a = __dadd_rn(__dmul_rn(*x, B.inv_h), -tab.half_w);
-    const double lf = ceil(a);
-    *v = __fma_rn(2.0, lf - a, -1.0);   // lf - a in [0, 1], exact or rounded into the range
-    return (int)lf;
-}
-
-// c_j (r_j/rho)^(-1/2) e^{i w_c x_j} as double-float (re, im), x_j = r_j - r_c,
-// and the ratio (r_j/rho)^(-1) that steps the weight from q to q + 1; r_j and
-// c_j come as double-float pairs.
-__device__ __forceinline__ void spread_weight(const AsyBlock& B, double x, float2 r2, float2 c2, df* wr, df* wi,
-                                              df* rat)
-{
-    df sn, cs;
-    df_sincos_prod(B.wc, x, &sn, &cs);
-    *rat = df_mul(df{B.rho_h, B.rho_l}, df_recip(df{r2.x, r2.y}));
-    const df w0 = df_mul(df{c2.x, c2.y}, df_sqrt(*rat));
-    *wr = df_mul(w0, cs);
-    *wi = df_mul(w0, sn);
-}
 
 // floor(X K / 2^s) for the signed 128-bit product, 1 <= s <= 127 (the
 // result fits in 64 bits).
@@ -98,9 +75,9 @@ __device__ __forceinline__ df df_from_sv(long long sv)
     return df{s2, e2};
 }
 
-// spread_cell in the block's fixed-point frame (integer instructions, exact
-// to 2^-41 cells): cell l0 and kernel coordinate v (double-float) of r_j,
-// and its offset X = R_j - R_c for the phase.
+// The cell l0 and kernel coordinate v (double-float) of r_j in the block's
+// fixed-point frame (integer instructions, exact to 2^-41 cells), and its
+// offset X = R_j - R_c for the phase.
 __device__ __forceinline__ int spread_cell_fx(const AsyBlock& B, int w, double rj, long long* Xo, df* v)
 {
     const long long X = fx_from_double(rj, B.fr) - B.Rc_fx;
@@ -111,7 +88,10 @@ __device__ __forceinline__ int spread_cell_fx(const AsyBlock& B, int w, double r
     return (int)l0;
 }
 
-// spread_weight with the phase w_c x_j / (2 pi) from the fixed-point offset.
+// c_j (r_j/rho)^(-1/2) e^{i w_c x_j} as double-float (re, im), x_j = r_j - r_c,
+// and the ratio (r_j/rho)^(-1) that steps the weight from q to q + 1; r_j and
+// c_j come as double-float pairs, the phase w_c x_j / (2 pi) from the
+// fixed-point offset.
 __device__ __forceinline__ void spread_weight_fx(const AsyBlock& B, long long X, float2 r2, float2 c2, df* wr,
                                                  df* wi, df* rat)
 {
@@ -212,9 +192,14 @@ __device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
 // x 4 values per thread, the point range split over 8 lanes); degrees >=
 // tab.dcs, whose coefficients are tiny, accumulate in plain FP32, the rest
 // in double-float.
-__device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, const Tables& tab,
-                               const double* __restrict__ r_s, const float2* __restrict__ r2,
-                               const float2* __restrict__ c2, double2* __restrict__ gb, float2* sm)
+//
+// Shared by the spreading of points (forward) and of frequencies (adjoint):
+// target(j, &v, xq) gives target j's cell and kernel coordinate v and writes
+// its 2M weighted values as double-float (re, im) pairs xq[2q], xq[2q + 1];
+// cell(c) is the grid index of cell c, or -1 for a cell outside the grid.
+template <class Target, class Cell>
+__device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, const Tables& tab, Target&& target,
+                                               Cell&& cell, double2* __restrict__ gb, float2* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -234,10 +219,8 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
         Ach[i] = d >= 0 ? tab.ch2[r * (tab.deg + 1) + d] : make_float2(0.f, 0.f);
     }
     if (tid < cnt) {
-        const int64_t j = t.start + tid;
-        long long Xp;
         df vd;
-        l0s[tid] = spread_cell_fx(B, w, r_s[j], &Xp, &vd);
+        l0s[tid] = target(t.start + tid, &vd, X + tid * L.sx);
         // Chebyshev basis by T_{d+1} = 2 v T_d - T_{d-1}
         float2* ud = Ud + tid * L.sud;
         float* uf = Uf + tid * L.suf;
@@ -262,15 +245,6 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
             fc = fn;
         }
         for (int e = nb - dcs; e < L.suf; ++e) uf[e] = 0.f;
-        df wr, wi, rat;
-        spread_weight_fx(B, Xp, r2[j], c2[j], &wr, &wi, &rat);
-        float2* xq = X + tid * L.sx;
-        for (int q = 0; q < Q; ++q) {
-            xq[2 * q] = make_float2(wr.h, wr.l);
-            xq[2 * q + 1] = make_float2(wi.h, wi.l);
-            wr = df_mul(wr, rat);
-            wi = df_mul(wi, rat);
-        }
     }
     __syncthreads();
     const int lfirst = l0s[0];
@@ -283,7 +257,6 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
         bstart[b] = lo;
     }
     __syncthreads();
-    const int nf1 = 2 * B.N1 + 1;
     const int npairs = L.ndf + L.nf;
     const int nitems = npairs * nq * kSpreadSub;
     const int nqA = min(nq, (qs + 1) >> 1);        // quads holding a term q < qs
@@ -388,8 +361,8 @@ __device__ void spread_moments(const AsyBlock& B, int Q, int qs, const Tile& t, 
         const int l0 = lfirst + b;
         for (int o = tid; o < w * Q2; o += nt) {
             const int i = o / Q2, qv = o - i * Q2;
-            const int idx = l0 + i + B.N1;
-            if (idx < 0 || idx >= nf1) continue;
+            const int64_t idx = cell(l0 + i);
+            if (idx < 0) continue;
             acc2 s{0.f, 0.f};
             const float2* ar = Ach + i * L.dpad;
             float sf = 0.f;
@@ -881,8 +854,26 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     double2* gb = grid_b + B.b_off;
     if (use_mom == 2)
         spread_fold(B, Q, probs[B.prob].qs, t, tab, fplan, r_s, r2, c2, gb, smem4);
-    else if (use_mom)
-        spread_moments(B, Q, probs[B.prob].qs, t, tab, r_s, r2, c2, gb, (float2*)smem4);
+    else if (use_mom) {
+        // c_j (r_j/rho)^(-q-1/2) e^{i w_c x_j} onto the 2 N1 + 1 modes
+        const int nf1 = 2 * B.N1 + 1;
+        spread_moments(Q, probs[B.prob].qs, t, tab,
+            [&](int64_t j, df* v, float2* xq) {
+                long long Xp;
+                const int l0 = spread_cell_fx(B, tab.w, r_s[j], &Xp, v);
+                df wr, wi, rat;
+                spread_weight_fx(B, Xp, r2[j], c2[j], &wr, &wi, &rat);
+                for (int q = 0; q < Q; ++q) {
+                    xq[2 * q] = make_float2(wr.h, wr.l);
+                    xq[2 * q + 1] = make_float2(wi.h, wi.l);
+                    wr = df_mul(wr, rat);
+                    wi = df_mul(wi, rat);
+                }
+                return l0;
+            },
+            [&](int c) -> int64_t { const int x = c + B.N1; return (x >= 0 && x < nf1) ? x : -1; },
+            gb, (float2*)smem4);
+    }
     else
         spread_taps(B, Q, t, tab, r_s, r2, c2, gb, smem4);
 }
@@ -1163,6 +1154,180 @@ __host__ __device__ __forceinline__ size_t interp_smem(int qmax, int w, int deg)
            kInterpHBytes + sizeof(float2) * (size_t)kInterpTileThreads * us + sizeof(int) * kInterpTileThreads;
 }
 
+// Per-bin sums of a staged window (dense interpolation tiles):
+// H[b][d][q'] = sum_i A[i][d] G[b + i][q'], b < nbins, A[i][d] the taps in the
+// Chebyshev basis (coef2, [w][nb]) and G the window ([cells][Q] of (re_h,
+// re_l, im_h, im_l)); bin stride nb 2Q + 2 float2.  Double-float for d < dci
+// and q < qs (the targets read only the FP32 part of the rest); each thread
+// forms two degrees x (re, im) of one q, four independent sums over the w
+// cells.
+__device__ __forceinline__ void bin_sums_build(const float4* win, const float2* coef2, float2* H, int nbins,
+                                               int w, int nb, int dci, int Q, int qs)
+{
+    const int Q2 = 2 * Q, hs = nb * Q2 + 2;
+    const int npr = (nb + 1) >> 1;
+    for (int o = threadIdx.x; o < nbins * npr * Q; o += blockDim.x) {
+        const int b = o / (npr * Q), rem = o - b * (npr * Q);
+        const int dp = rem / Q, q = rem - dp * Q;
+        const int d0 = 2 * dp, d1 = d0 + 1;
+        const bool has1 = d1 < nb;
+        float2* h0 = H + b * hs + d0 * Q2 + 2 * q;
+        if (d0 < dci && q < qs) {
+            acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
+#pragma unroll 4
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = win[(b + i) * Q + q];
+                const float2 c0 = coef2[i * nb + d0];
+                const float2 c1 = has1 ? coef2[i * nb + d1] : make_float2(0.f, 0.f);
+                const df gr{gv.x, gv.y}, gi{gv.z, gv.w};
+                acc_fma(a0r, df{c0.x, c0.y}, gr);
+                acc_fma(a0i, df{c0.x, c0.y}, gi);
+                acc_fma(a1r, df{c1.x, c1.y}, gr);
+                acc_fma(a1i, df{c1.x, c1.y}, gi);
+            }
+            df v = fast_two_sum(a0r.s, a0r.c);
+            h0[0] = make_float2(v.h, v.l);
+            v = fast_two_sum(a0i.s, a0i.c);
+            h0[1] = make_float2(v.h, v.l);
+            if (has1) {
+                v = fast_two_sum(a1r.s, a1r.c);
+                h0[Q2] = make_float2(v.h, v.l);
+                v = fast_two_sum(a1i.s, a1i.c);
+                h0[Q2 + 1] = make_float2(v.h, v.l);
+            }
+        } else {
+            float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+#pragma unroll 4
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = win[(b + i) * Q + q];
+                const float c0 = coef2[i * nb + d0].x;
+                const float c1 = has1 ? coef2[i * nb + d1].x : 0.f;
+                a0r = fmaf(c0, gv.x, a0r);
+                a0i = fmaf(c0, gv.z, a0i);
+                a1r = fmaf(c1, gv.x, a1r);
+                a1i = fmaf(c1, gv.z, a1i);
+            }
+            h0[0] = make_float2(a0r, 0.f);
+            h0[1] = make_float2(a0i, 0.f);
+            if (has1) {
+                h0[Q2] = make_float2(a1r, 0.f);
+                h0[Q2 + 1] = make_float2(a1i, 0.f);
+            }
+        }
+    }
+}
+
+// A target's Chebyshev basis T_d(v), d < nb, into u (double-float for d < dci).
+__device__ __forceinline__ void cheb_basis_row(float2* u, float vh, float vl, int dci, int nb)
+{
+    u[0] = make_float2(1.f, 0.f);
+    u[1] = make_float2(vh, vl);
+    df tm{1.f, 0.f}, tc{vh, vl};
+    const df v2{2.f * vh, 2.f * vl};
+    int d = 2;
+    for (; d < dci; ++d) {
+        const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+        u[d] = make_float2(tn.h, tn.l);
+        tm = tc;
+        tc = tn;
+    }
+    float fm = tm.h, fc = tc.h;
+    for (; d < nb; ++d) {
+        const float fn = fmaf(2.f * vh, fc, -fm);
+        u[d] = make_float2(fn, 0.f);
+        fm = fc;
+        fc = fn;
+    }
+}
+
+// P_q = sum_d T_d(v) H[d][q], q < Q (Q = 2M is even), handed to
+// combine(q, re, im) in increasing q: Hankel terms in pairs, four independent
+// sums over the degrees, one basis load per degree; from q = qs on in FP32
+// (small Hankel terms).
+template <class F>
+__device__ __forceinline__ void bin_sums_eval(const float2* Hb, const float2* u, int nb, int dci, int Q, int qs,
+                                              F&& combine)
+{
+    const int Q2 = 2 * Q;
+    for (int q = 0; q < Q; q += 2) {
+        const float2* hq = Hb + 2 * q;
+        if (q < qs) {
+            acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
+            int d = 0;
+#pragma unroll 3
+            for (; d < dci; ++d) {
+                const float2 tp = u[d];
+                const df t{tp.x, tp.y};
+                const float4 h0 = *(const float4*)(hq + d * Q2);
+                const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
+                acc_fma(a0r, t, df{h0.x, h0.y});
+                acc_fma(a0i, t, df{h0.z, h0.w});
+                acc_fma(a1r, t, df{h1.x, h1.y});
+                acc_fma(a1i, t, df{h1.z, h1.w});
+            }
+            float f0r = 0.f, f0i = 0.f, f1r = 0.f, f1i = 0.f;
+#pragma unroll 3
+            for (; d < nb; ++d) {
+                const float tp = u[d].x;
+                const float4 h0 = *(const float4*)(hq + d * Q2);
+                const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
+                f0r = fmaf(tp, h0.x, f0r);
+                f0i = fmaf(tp, h0.z, f0i);
+                f1r = fmaf(tp, h1.x, f1r);
+                f1i = fmaf(tp, h1.z, f1i);
+            }
+            a0r.c += f0r;
+            a0i.c += f0i;
+            a1r.c += f1r;
+            a1i.c += f1i;
+            combine(q, fast_two_sum(a0r.s, a0r.c), fast_two_sum(a0i.s, a0i.c));
+            combine(q + 1, fast_two_sum(a1r.s, a1r.c), fast_two_sum(a1i.s, a1i.c));
+        } else {
+            float p0r = 0.f, p0i = 0.f, p1r = 0.f, p1i = 0.f;
+#pragma unroll 4
+            for (int d = 0; d < nb; ++d) {
+                const float tp = u[d].x;
+                const float4 h0 = *(const float4*)(hq + d * Q2);
+                const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
+                p0r = fmaf(tp, h0.x, p0r);
+                p0i = fmaf(tp, h0.z, p0i);
+                p1r = fmaf(tp, h1.x, p1r);
+                p1i = fmaf(tp, h1.z, p1i);
+            }
+            combine(q, df{p0r, 0.f}, df{p0i, 0.f});
+            combine(q + 1, df{p1r, 0.f}, df{p1i, 0.f});
+        }
+    }
+}
+
+// P_q = sum_i psi_i(v) G[i][q], q < Q, from the taps psi_i(v) in u (sparse
+// tiles); cell(i, q) returns the grid value; FP32 from q = qs on.
+template <class C, class F>
+__device__ __forceinline__ void tap_sums_eval(const float2* u, int w, int Q, int qs, C&& cell, F&& combine)
+{
+    for (int q = 0; q < Q; ++q) {
+        if (q < qs) {
+            acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = cell(i, q);
+                const float2 tp = u[i];
+                acc_fma(pr, df{tp.x, tp.y}, df{gv.x, gv.y});
+                acc_fma(pi, df{tp.x, tp.y}, df{gv.z, gv.w});
+            }
+            combine(q, fast_two_sum(pr.s, pr.c), fast_two_sum(pi.s, pi.c));
+        } else {
+            float pr = 0.f, pi = 0.f;
+            for (int i = 0; i < w; ++i) {
+                const float4 gv = cell(i, q);
+                const float tp = u[i].x;
+                pr = fmaf(tp, gv.x, pr);
+                pi = fmaf(tp, gv.z, pi);
+            }
+            combine(q, df{pr, 0.f}, df{pi, 0.f});
+        }
+    }
+}
+
 // One thread per frequency: interpolate the 2M FFT grids at theta = s h,
 // deconvolve, post-phase, and combine the Hankel terms into g.  A frequency
 // at FFT-grid position a + w/2 reads the cells t0 + i, i < w, t0 = ceil(a),
@@ -1221,84 +1386,14 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     }
     __syncthreads();
     if (mom) {
-        // H[b][d][q'] = sum_i A[i][d] G[wstart + b + i][q'], double-float for
-        // d < dci and q < qs (the frequencies read only the FP32 part of the
-        // rest); each thread forms two degrees x (re, im) of one q, four
-        // independent sums over the w cells
-        const int npr = (nb + 1) >> 1;
-        for (int o = threadIdx.x; o < nbins * npr * Q; o += blockDim.x) {
-            const int b = o / (npr * Q), rem = o - b * (npr * Q);
-            const int dp = rem / Q, q = rem - dp * Q;
-            const int d0 = 2 * dp, d1 = d0 + 1;
-            const bool has1 = d1 < nb;
-            float2* h0 = H + b * hs + d0 * Q2 + 2 * q;
-            if (d0 < dci && q < P.qs) {
-                acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
-#pragma unroll 4
-                for (int i = 0; i < w; ++i) {
-                    const float4 gv = win[(b + i) * Q + q];
-                    const float2 c0 = coef2[i * nb + d0];
-                    const float2 c1 = has1 ? coef2[i * nb + d1] : make_float2(0.f, 0.f);
-                    const df gr{gv.x, gv.y}, gi{gv.z, gv.w};
-                    acc_fma(a0r, df{c0.x, c0.y}, gr);
-                    acc_fma(a0i, df{c0.x, c0.y}, gi);
-                    acc_fma(a1r, df{c1.x, c1.y}, gr);
-                    acc_fma(a1i, df{c1.x, c1.y}, gi);
-                }
-                df v = fast_two_sum(a0r.s, a0r.c);
-                h0[0] = make_float2(v.h, v.l);
-                v = fast_two_sum(a0i.s, a0i.c);
-                h0[1] = make_float2(v.h, v.l);
-                if (has1) {
-                    v = fast_two_sum(a1r.s, a1r.c);
-                    h0[Q2] = make_float2(v.h, v.l);
-                    v = fast_two_sum(a1i.s, a1i.c);
-                    h0[Q2 + 1] = make_float2(v.h, v.l);
-                }
-            } else {
-                float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
-#pragma unroll 4
-                for (int i = 0; i < w; ++i) {
-                    const float4 gv = win[(b + i) * Q + q];
-                    const float c0 = coef2[i * nb + d0].x;
-                    const float c1 = has1 ? coef2[i * nb + d1].x : 0.f;
-                    a0r = fmaf(c0, gv.x, a0r);
-                    a0i = fmaf(c0, gv.z, a0i);
-                    a1r = fmaf(c1, gv.x, a1r);
-                    a1i = fmaf(c1, gv.z, a1i);
-                }
-                h0[0] = make_float2(a0r, 0.f);
-                h0[1] = make_float2(a0i, 0.f);
-                if (has1) {
-                    h0[Q2] = make_float2(a1r, 0.f);
-                    h0[Q2 + 1] = make_float2(a1i, 0.f);
-                }
-            }
-        }
+        bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, P.qs);
         __syncthreads();
     }
     if (!valid) return;
     // this thread's Chebyshev basis T_d(v) (dense tile) or taps psi_i(v)
     float2* u = U + threadIdx.x * us;
     if (mom) {
-        u[0] = make_float2(1.f, 0.f);
-        u[1] = make_float2(vh, vl);
-        df tm{1.f, 0.f}, tc{vh, vl};
-        const df v2{2.f * vh, 2.f * vl};
-        int d = 2;
-        for (; d < dci; ++d) {
-            const df tn = df_add(df_mul(v2, tc), df_negate(tm));
-            u[d] = make_float2(tn.h, tn.l);
-            tm = tc;
-            tc = tn;
-        }
-        float fm = tm.h, fc = tc.h;
-        for (; d < nb; ++d) {
-            const float fn = fmaf(2.f * vh, fc, -fm);
-            u[d] = make_float2(fn, 0.f);
-            fm = fc;
-            fc = fn;
-        }
+        cheb_basis_row(u, vh, vl, dci, nb);
     } else {
         for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
@@ -1324,86 +1419,12 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
         }
         mq = df_mul(mq, mz);
     };
-    if (mom) {
-        // Hankel terms in pairs (Q = 2M is even): four independent sums over
-        // the degrees, one basis load per degree
-        for (int q = 0; q < Q; q += 2) {
-            const float2* hq = Hb + 2 * q;
-            if (q < qs) {
-                acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
-                int d = 0;
-#pragma unroll 3
-                for (; d < dci; ++d) {
-                    const float2 tp = u[d];
-                    const df t{tp.x, tp.y};
-                    const float4 h0 = *(const float4*)(hq + d * Q2);
-                    const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
-                    acc_fma(a0r, t, df{h0.x, h0.y});
-                    acc_fma(a0i, t, df{h0.z, h0.w});
-                    acc_fma(a1r, t, df{h1.x, h1.y});
-                    acc_fma(a1i, t, df{h1.z, h1.w});
-                }
-                float f0r = 0.f, f0i = 0.f, f1r = 0.f, f1i = 0.f;
-#pragma unroll 3
-                for (; d < nb; ++d) {
-                    const float tp = u[d].x;
-                    const float4 h0 = *(const float4*)(hq + d * Q2);
-                    const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
-                    f0r = fmaf(tp, h0.x, f0r);
-                    f0i = fmaf(tp, h0.z, f0i);
-                    f1r = fmaf(tp, h1.x, f1r);
-                    f1i = fmaf(tp, h1.z, f1i);
-                }
-                a0r.c += f0r;
-                a0i.c += f0i;
-                a1r.c += f1r;
-                a1i.c += f1i;
-                combine(q, fast_two_sum(a0r.s, a0r.c), fast_two_sum(a0i.s, a0i.c));
-                combine(q + 1, fast_two_sum(a1r.s, a1r.c), fast_two_sum(a1i.s, a1i.c));
-            } else {
-                // small Hankel terms: FP32 is accurate enough
-                float p0r = 0.f, p0i = 0.f, p1r = 0.f, p1i = 0.f;
-#pragma unroll 4
-                for (int d = 0; d < nb; ++d) {
-                    const float tp = u[d].x;
-                    const float4 h0 = *(const float4*)(hq + d * Q2);
-                    const float4 h1 = *(const float4*)(hq + d * Q2 + 2);
-                    p0r = fmaf(tp, h0.x, p0r);
-                    p0i = fmaf(tp, h0.z, p0i);
-                    p1r = fmaf(tp, h1.x, p1r);
-                    p1i = fmaf(tp, h1.z, p1i);
-                }
-                combine(q, df{p0r, 0.f}, df{p0i, 0.f});
-                combine(q + 1, df{p1r, 0.f}, df{p1i, 0.f});
-            }
-        }
-    } else {
-        for (int q = 0; q < Q; ++q) {
-            df prd, pid;
-            if (q < qs) {
-                acc2 pr{0.f, 0.f}, pi{0.f, 0.f};
-                for (int i = 0; i < w; ++i) {
-                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                    const float2 tp = u[i];
-                    acc_fma(pr, df{tp.x, tp.y}, df{gv.x, gv.y});
-                    acc_fma(pi, df{tp.x, tp.y}, df{gv.z, gv.w});
-                }
-                prd = fast_two_sum(pr.s, pr.c);
-                pid = fast_two_sum(pi.s, pi.c);
-            } else {
-                float pr = 0.f, pi = 0.f;
-                for (int i = 0; i < w; ++i) {
-                    const float4 gv = staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                    const float tp = u[i].x;
-                    pr = fmaf(tp, gv.x, pr);
-                    pi = fmaf(tp, gv.z, pi);
-                }
-                prd = df{pr, 0.f};
-                pid = df{pi, 0.f};
-            }
-            combine(q, prd, pid);
-        }
-    }
+    if (mom)
+        bin_sums_eval(Hb, u, nb, dci, Q, qs, combine);
+    else
+        tap_sums_eval(u, w, Q, qs, [&](int i, int q) {
+            return staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+        }, combine);
     df sn, cs;
     df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
     // Re(e^{i (omega r_c + phi)} T) = Re(e^{i omega r_c} (e^{i phi} T))
@@ -1431,18 +1452,81 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
 // g_k D_out onto the FFT grid (I^T), the same FFT and correction follow, and
 // the points interpolate the corrected modes (S^T) with D_in.
 
-// Frequencies of a tile -> FFT grid (periodic, atomics into tgrid).
+// The weighted values of frequency omega_k in the transposed interpolation
+// (g_k D_out, one per Hankel term):
+//   x_q = g_k sqrt(2/pi) (4/w^2) / psi^(alpha s) (omega rho)^(-1/2)
+//         e^{i (omega r_c + phi)} i^q a_q z^-q (z/(omega rho))^q,
+// as double-float (re, im) pairs xq[2q], xq[2q + 1]; returns the FFT-grid cell
+// t0 of omega_k and its kernel coordinate v.
+__device__ __forceinline__ int adj_spread_values(const AsyBlock& B, const ProbParams& P, const Tables& tab,
+                                                 double wk, double gk, df* v, float2* xq)
+{
+    long long Om, Sw, svw;
+    const int t0 = interp_cell_sv(B, tab.w, wk, &Om, &Sw, &svw);
+    *v = df_from_sv(svw);
+    const df m1d = df_recip(df_from(wk * B.rho));
+    const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});
+    df sn, cs;
+    df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+    const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
+    const df er = df_add(df_mul(cs, cph), df_negate(df_mul(sn, sph)));
+    const df ei = df_add(df_mul(sn, cph), df_mul(cs, sph));
+    const df amp = df_mul(df_mul(df_from((double)P.sgn * gk * tab.interp_const), df_sqrt(m1d)),
+                          df_recip(psihat_fx(tab, B, Sw)));
+    const df fr = df_mul(amp, er), fi = df_mul(amp, ei);
+    df mq{1.f, 0.f};
+    for (int q = 0; q < P.Q; ++q) {
+        const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
+        // (fr + i fi) i^q cq
+        df ur, ui;
+        switch (q & 3) {
+            case 0: ur = fr; ui = fi; break;
+            case 1: ur = df_negate(fi); ui = fr; break;
+            case 2: ur = df_negate(fr); ui = df_negate(fi); break;
+            default: ur = fi; ui = df_negate(fr); break;
+        }
+        ur = df_mul(ur, cq);
+        ui = df_mul(ui, cq);
+        xq[2 * q] = make_float2(ur.h, ur.l);
+        xq[2 * q + 1] = make_float2(ui.h, ui.l);
+        mq = df_mul(mq, mz);
+    }
+    return t0;
+}
+
+// Frequencies of a tile -> FFT grid (periodic, atomics into tgrid).  Dense
+// tiles (many frequencies per cell) take the per-bin moment path of the
+// forward spreading; sparse tiles evaluate each frequency's w taps and sum,
+// per grid cell, the frequencies that reach it.
 __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ tiles, Tables tab,
                                  const double* __restrict__ w_s, const double* __restrict__ g_s,
                                  double2* __restrict__ tgrid)
 {
     extern __shared__ float4 sma[];
+    __shared__ int use_mom;
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
     const int Q = P.Q;
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
+    const int mask = B.nf2 - 1;
+    double2* tg = tgrid + B.q_off;
+    const int cnt = t.count;
+    if (cnt <= 0) return;
+    if (tid == 0) {
+        long long Om, Sw, svw;
+        const int tfirst = interp_cell_sv(B, w, w_s[t.start], &Om, &Sw, &svw);
+        const int nbins = interp_cell_sv(B, w, w_s[t.start + cnt - 1], &Om, &Sw, &svw) - tfirst + 1;
+        use_mom = nbins <= kMaxTileBins && cnt >= kMomMinPerBin * nbins;
+    }
+    __syncthreads();
+    if (use_mom) {
+        spread_moments(Q, P.qs, t, tab,
+            [&](int64_t k, df* v, float2* xq) { return adj_spread_values(B, P, tab, w_s[k], g_s[k], v, xq); },
+            [&](int c) -> int64_t { return c & mask; }, tg, (float2*)sma);
+        return;
+    }
     const int ncoef = w * (deg + 1);
     float4* uval = sma;                                 // [nt][Q]
     float2* coef = (float2*)(uval + nt * Q);            // [w][deg+1]
@@ -1450,52 +1534,19 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
     int* t0s = (int*)(taps + nt * w);                   // [nt]
     for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
     __syncthreads();
-    const int cnt = t.count;
     if (tid < cnt) {
         const int64_t k = t.start + tid;
-        const double wk = w_s[k];
-        long long Om, Sw, svw;
-        const int t0 = interp_cell_sv(B, w, wk, &Om, &Sw, &svw);
-        const df vdf = df_from_sv(svw);
-        const float vh = vdf.h, vl = vdf.l;
+        df vdf;
+        const int t0 = adj_spread_values(B, P, tab, w_s[k], g_s[k], &vdf, (float2*)(uval + tid * Q));
         for (int i = 0; i < w; ++i) {
-            const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
+            const df tp = horner_comp(coef + i * (deg + 1), deg, vdf.h, vdf.l, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
         t0s[tid] = t0;
-        // g_k sqrt(2/pi) (4/w^2) / psi^(alpha s) (omega rho)^(-1/2) e^{i (omega r_c + phi)}
-        const df m1d = df_recip(df_from(wk * B.rho));
-        const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});
-        df sn, cs;
-        df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
-        const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
-        const df er = df_add(df_mul(cs, cph), df_negate(df_mul(sn, sph)));
-        const df ei = df_add(df_mul(sn, cph), df_mul(cs, sph));
-        const df amp = df_mul(df_mul(df_from((double)P.sgn * g_s[k] * tab.interp_const), df_sqrt(m1d)),
-                              df_recip(psihat_fx(tab, B, Sw)));
-        df fr = df_mul(amp, er), fi = df_mul(amp, ei);
-        df mq{1.f, 0.f};
-        for (int q = 0; q < Q; ++q) {
-            const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
-            // (fr + i fi) i^q cq
-            df ur, ui;
-            switch (q & 3) {
-                case 0: ur = fr; ui = fi; break;
-                case 1: ur = df_negate(fi); ui = fr; break;
-                case 2: ur = df_negate(fr); ui = df_negate(fi); break;
-                default: ur = fi; ui = df_negate(fr); break;
-            }
-            ur = df_mul(ur, cq);
-            ui = df_mul(ui, cq);
-            uval[tid * Q + q] = make_float4(ur.h, ur.l, ui.h, ui.l);
-            mq = df_mul(mq, mz);
-        }
     }
     __syncthreads();
     const int tfirst = t0s[0];
     const int span = t0s[cnt - 1] - tfirst + w;
-    const int mask = B.nf2 - 1;
-    double2* tg = tgrid + B.q_off;
     const bool dense = span <= 2 * w;
     for (int item = tid; item < span * Q; item += nt) {
         const int c = item / Q, q = item - c * Q;
@@ -1532,111 +1583,107 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
 }
 
 // Points of a tile: interpolate the corrected modes b' (split, at b_off) with
-// the spreading kernel, apply D_in and sum the Hankel terms into c.
-__global__ void __launch_bounds__(128, 4) k_asy_adj_interp(
+// the spreading kernel, apply D_in and sum the Hankel terms into c; the
+// transpose of the spreading, computed like k_asy_interp (one thread per
+// point, in passes of blockDim points).  A point at cell l0 reads the modes
+// l0 + i, i < w (zero outside the 2 N1 + 1 modes).  Dense passes (many points
+// per cell) form the per-bin sums H[d][q'] once per bin and each point sums
+// P_q = sum_d T_d(v) H[d][q]; sparse passes evaluate the w taps of each point.
+__global__ void __launch_bounds__(kInterpTileThreads) k_asy_adj_interp(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
     Tables tab, const double* __restrict__ r_s, const float4* __restrict__ bgrid, double* __restrict__ c_s)
 {
-    extern __shared__ float4 winb[];
+    extern __shared__ float4 win[];          // [kWinCells][Q] modes of this pass
     const Tile t = tiles[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
-    const int w = tab.w, deg = tab.deg;
-    const int Q = P.Q;
-    float2* coef2 = (float2*)(winb + kWinCells * Q);
-    int* l0s = (int*)(coef2 + w * (deg + 1));
-    for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
+    const int w = tab.w, deg = tab.deg, nb = tab.nb, dci = tab.dci;
+    const int Q = P.Q, Q2 = 2 * Q, qs = P.qs;
+    const int us = (deg + 1 > w ? deg + 1 : w) | 1;
+    const int hs = nb * Q2 + 2;
+    float2* coef2 = (float2*)(win + kWinCells * Q);              // [w][deg + 1] taps, or [w][nb] Chebyshev
+    float2* H = coef2 + ((w * (deg + 1) + 1) & ~1);              // [bins][hs], 16-byte aligned
+    float2* U = H + kInterpHBytes / sizeof(float2);              // [threads][us]
+    int* l0s = (int*)(U + kInterpTileThreads * us);              // [threads]
     const float4* gb = bgrid + B.b_off;
     const int nf1 = 2 * B.N1 + 1;
+    const int maxbins = kInterpHBytes / (int)(sizeof(float2) * hs);
     for (int base = 0; base < t.count; base += blockDim.x) {
-        const bool valid = base + (int)threadIdx.x < t.count;
+        const int cnt = t.count - base < (int)blockDim.x ? t.count - base : (int)blockDim.x;
+        const bool valid = (int)threadIdx.x < cnt;
         const int64_t j = t.start + base + (valid ? threadIdx.x : 0);
         const double rj = r_s[j];
         long long X;
         df vd;
         const int l0 = spread_cell_fx(B, w, rj, &X, &vd);
-        __syncthreads();
         if (valid) l0s[threadIdx.x] = l0;
         __syncthreads();
-        const int last = (t.count - base < (int)blockDim.x ? t.count - base : (int)blockDim.x) - 1;
+        // the tile's points are sorted, so their cells form one window
         const int wstart = l0s[0];
-        const int wlen = l0s[last] - wstart + w;
+        const int nbins = l0s[cnt - 1] - wstart + 1;
+        const int wlen = nbins - 1 + w;
         const bool staged = wlen <= kWinCells;
+        const bool mom = staged && nbins <= maxbins && cnt >= kMomMinPerBin * nbins;
         if (staged)
             for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
                 const int cc = idx / Q;
                 const int li = wstart + cc + B.N1;
-                winb[idx] = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + (idx - cc * Q)]
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                win[idx] = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + (idx - cc * Q)]
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-        __syncthreads();
-        if (!valid) continue;
-        const float vh = vd.h, vl = vd.l;
-        float th[kMaxW], tl[kMaxW];
-#pragma unroll
-        for (int i = 0; i < kMaxW; ++i) {
-            if (i < w) {
-                const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
-                th[i] = tp.h;
-                tl[i] = tp.l;
-            } else {
-                th[i] = 0.f;
-                tl[i] = 0.f;
+        if (mom) {
+            for (int i = threadIdx.x; i < w * nb; i += blockDim.x) {
+                const int r = i / nb, d = i - r * nb;
+                coef2[i] = tab.ch2[r * (deg + 1) + d];
             }
+        } else {
+            for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
         }
-        // T = sum_q (r/rho)^(-q) y_q, y_q = sum_i tap_i b'_{l0 + i, q}
-        const df rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1)
-        acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
-        df mq{1.f, 0.f};
-        for (int q = 0; q < Q; ++q) {
-            acc2 yr{0.f, 0.f}, yi{0.f, 0.f};
-#pragma unroll
-            for (int i = 0; i < kMaxW; ++i) {
-                if (i < w) {
-                    const int li = l0 + i + B.N1;
-                    float4 gv;
-                    if (staged) gv = winb[(l0 + i - wstart) * Q + q];
-                    else gv = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const df tp{th[i], tl[i]};
-                    acc_fma(yr, tp, df{gv.x, gv.y});
-                    acc_fma(yi, tp, df{gv.z, gv.w});
+        __syncthreads();
+        if (mom) {
+            bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, qs);
+            __syncthreads();
+        }
+        if (valid) {
+            const float vh = vd.h, vl = vd.l;
+            float2* u = U + threadIdx.x * us;
+            if (mom) {
+                cheb_basis_row(u, vh, vl, dci, nb);
+            } else {
+                for (int i = 0; i < w; ++i) {
+                    const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
+                    u[i] = make_float2(tp.h, tp.l);
                 }
             }
-            acc_fma(tr, mq, fast_two_sum(yr.s, yr.c));
-            acc_fma(ti, mq, fast_two_sum(yi.s, yi.c));
-            mq = df_mul(mq, rat);
+            // T = sum_q (r/rho)^(-q) P_q, P_q = sum_i psi_i(v) b'_{l0 + i, q}
+            const df rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1) <= 1
+            acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
+            df mq{1.f, 0.f};
+            auto combine = [&](int, df prd, df pid) {
+                acc_fma(tr, mq, prd);
+                acc_fma(ti, mq, pid);
+                mq = df_mul(mq, rat);
+            };
+            if (mom)
+                bin_sums_eval(H + (l0 - wstart) * hs, u, nb, dci, Q, qs, combine);
+            else
+                tap_sums_eval(u, w, Q, qs, [&](int i, int q) {
+                    const int li = l0 + i + B.N1;
+                    if (staged) return win[(l0 + i - wstart) * Q + q];
+                    return (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }, combine);
+            // c_j += Re( e^{i w_c x} (r/rho)^(-1/2) T )
+            df sn, cs;
+            df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+            const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
+            const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
+            atomicAdd(&c_s[j], df_to(df_mul(df_sqrt(rat), re)));
         }
-        // c_j += Re( e^{i w_c x} (r/rho)^(-1/2) T )
-        df sn, cs;
-        df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
-        const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
-        const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
-        atomicAdd(&c_s[j], df_to(df_mul(df_sqrt(rat), re)));
+        __syncthreads();   // l0s, the window and H are rewritten by the next pass
     }
 }
 
 // ------------------------------------------------------ mixed precision (FP32)
-// sin, cos of the exact product a*b: FP64 reduction modulo pi/2 (as in
-// df_sincos_prod), FP32 sine and cosine of the remainder |t| <= pi/4.
-__device__ __forceinline__ void f32_sincos_prod(double a, double b, float* sn, float* cs)
-{
-    const double kPio2Hi = 1.5707963267948966;
-    const double kPio2Lo = 6.123233995736766e-17;
-    const double p = a * b;
-    const double e = fma(a, b, -p);
-    const double k = rint(p * 0.6366197723675814);
-    double t = fma(-k, kPio2Hi, p);
-    t = fma(-k, kPio2Lo, t) + e;
-    float s0, c0;
-    sincosf((float)t, &s0, &c0);
-    switch ((int)((long long)k & 3)) {
-        case 0: *sn = s0; *cs = c0; break;
-        case 1: *sn = c0; *cs = -s0; break;
-        case 2: *sn = -s0; *cs = -c0; break;
-        default: *sn = -c0; *cs = s0; break;
-    }
-}
-
 __device__ __forceinline__ float horner_f32(const float2* __restrict__ c, int deg, float v)
 {
     float acc = c[deg].x;
@@ -2005,6 +2052,8 @@ cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks,
     const int nt = kInterpTileThreads;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
+    const size_t smem_mom = spread_moments_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
+    if (smem_mom > smem) smem = smem_mom;
     cudaError_t e = cudaFuncSetAttribute(k_asy_adj_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_asy_adj_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, g_s, tgrid);
@@ -2017,11 +2066,10 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
                                   double* c_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
-                  sizeof(int) * 128;
+    const size_t smem = interp_smem(qmax, tab.w, tab.deg);
     cudaError_t e = cudaFuncSetAttribute(k_asy_adj_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_adj_interp<<<ntiles, 128, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, c_s);
+    k_asy_adj_interp<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, c_s);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -44,9 +44,25 @@ __device__ __forceinline__ df df_imul(float fi, float ih, float il)
     return fast_two_sum(p, e);
 }
 
+// Sum of a compensated accumulator over the warp (two-sums through the
+// shuffles); the total is in lane 0.
+__device__ __forceinline__ acc2 warp_sum_acc(acc2 a)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, a.s, off);
+        const float oc = __shfl_down_sync(0xffffffffu, a.c, off);
+        float s, e;
+        two_sum(a.s, os, s, e);
+        a.s = s;
+        a.c += oc + e;
+    }
+    return a;
+}
+
 // dst[l] += sum over the CTA's threads of acc[l * nt + thread], l <= L: one
-// warp per l, compensated FP32 sums (two-sums through the shuffles), one
-// conversion and one FP64 atomic per l (FP64 runs at 1/64 of the FP32 rate).
+// warp per l, compensated FP32 sums, one conversion and one FP64 atomic per l
+// (FP64 runs at 1/64 of the FP32 rate).
 __device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int L, double* dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -59,23 +75,15 @@ __device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int 
             a.s = s;
             a.c += v.c + e;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float os = __shfl_down_sync(0xffffffffu, a.s, off);
-            const float oc = __shfl_down_sync(0xffffffffu, a.c, off);
-            float s, e;
-            two_sum(a.s, os, s, e);
-            a.s = s;
-            a.c += oc + e;
-        }
+        a = warp_sum_acc(a);
         if (lane == 0) atomicAdd(&dst[l], acc_value(a));
     }
 }
 
 // One CTA per tile of columns of one local block.  Each thread keeps its own
 // column of partial moments (compensated double-float accumulators) in shared
-// memory, acc[l * blockDim + tid]; the columns are summed in FP64 at the end
-// and added to the block's moments.
+// memory, acc[l * blockDim + tid]; the columns are summed at the end
+// (reduce_columns_add) and added to the block's moments.
 __global__ void __launch_bounds__(kMomThreads)
 k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
                 const Tile* __restrict__ tiles, const float2* __restrict__ r2,
@@ -548,57 +556,91 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
 // Transposed local block A_blk^T = T C^T: adjoint moments
 //   nu_l = sum_{k in block} g_k C_l(omega_k R)          (rows, Miller per row)
 // then c_j += sum_l T_{2l(+1)}(r_j / R) nu_l              (columns).
-__global__ void k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                                    const Tile* __restrict__ tiles, const float2* __restrict__ w2,
-                                    const double* __restrict__ g_s, double* __restrict__ mom)
+//
+// One CTA per tile of rows, in passes of blockDim rows.  Phase 1: each thread
+// runs the Miller recurrence of one row into its column of jb (as in
+// k_local_eval) and leaves g_k / S^2 and its power-of-two scale in shared
+// memory.  Phase 2: warp w takes l = w, w + nwarps, ... and sums
+// C_l(row) g_row / S_row^2 over the pass's rows straight from jb (compensated
+// FP32 sums, one FP64 atomic per moment and pass).  No per-thread moment
+// accumulators: the CTA holds as little shared memory as k_local_eval.
+constexpr int kAdjRowsPerLane = kMomThreads / 32;
+
+__global__ void __launch_bounds__(kMomThreads)
+k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                    const Tile* __restrict__ tiles, const float2* __restrict__ w2,
+                    const double* __restrict__ g_s, double* __restrict__ mom)
 {
     extern __shared__ float2 sm2[];
     const Tile t = tiles[blockIdx.x];
     const LocalBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
     const int nt = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int nu = P.nu, L = P.L;
-    float2* jb = sm2;                                   // [ntop + 1][nt]
-    acc2* acc = (acc2*)(sm2 + (P.ntop + 1) * nt);      // [L + 1][nt]
-    for (int l = 0; l <= L; ++l) acc[l * nt + tid] = acc2{0.f, 0.f};
-    // the tile's rows in passes of blockDim (the tile may be longer)
-    for (int row = tid; row < t.count; row += nt) {
-        const int64_t k = t.start + row;
-        const double gk = (double)P.sgn * g_s[k];
-        // the same arithmetic as k_local_eval (the transpose of the same operator)
-        const float2 wk = w2[k];
-        const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});
-        if (!(ydf.h > 0.f)) {
-            if (nu == 0) {
-                acc2 a = acc[tid];
-                acc_fma(a, df_from(gk), df{1.f, 0.f});
-                acc[tid] = a;
-            }
-        } else {
-            const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;
-            const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;
-            const int ntop = hp + L;
-            const int ns = miller_start(ntop, (double)ydf.h);
-            df S = (ydf.h >= 1.f) ? miller_store_df(ydf, ntop, ns, jb, nt, tid)
-                                  : df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
-            const float p2 = exp2f(-(float)ilogbf(S.h));
-            S = df_scale(S, p2);
-            // g_k / S^2 (the normalisation of both Bessel factors)
-            const df iS = df_recip(S);
-            const df gs = df_mul(df_mul(df_from(gk), iS), iS);
-            for (int l = 0; l <= L; ++l) {
-                const int b = hm - l;
-                const float2 va = jb[(hp + l) * nt + tid];
-                const float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
-                float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
-                if (l > 0 || (nu & 1)) sgn *= 2.f;
-                const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
-                acc_fma(acc[l * nt + tid], cl, gs);
+    const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
+    const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
+    const int ntop = hp + L;
+    float2* jb = sm2;                                  // [ntop + 1][nt]
+    float2* gsm = sm2 + (size_t)(P.ntop + 1) * nt;     // [nt] g_k / S^2 per row
+    float* p2m = (float*)(gsm + nt);                   // [nt] scale per row
+    for (int base = 0; base < t.count; base += nt) {
+        const int cnt = t.count - base < nt ? t.count - base : nt;
+        if (tid < cnt) {
+            const int64_t k = t.start + base + tid;
+            const double gk = (double)P.sgn * g_s[k];
+            const float2 wk = w2[k];
+            const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});   // y = omega R / 2
+            if (!(ydf.h > 0.f)) {
+                // y below the FP32 range: J_n(y) = delta_n0 to far below rounding
+                for (int q = 0; q <= ntop; ++q) jb[q * nt + tid] = make_float2(q == 0 ? 1.f : 0.f, 0.f);
+                const df g = df_from(gk);
+                gsm[tid] = make_float2(g.h, g.l);
+                p2m[tid] = 1.f;
+            } else {
+                const int ns = miller_start(ntop, (double)ydf.h);
+                df S = (ydf.h >= 1.f) ? miller_store_df(ydf, ntop, ns, jb, nt, tid)
+                                      : df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+                // a power of two near 1/S keeps products of two values in FP32 range
+                const float p2 = exp2f(-(float)ilogbf(S.h));
+                S = df_scale(S, p2);
+                const df iS = df_recip(S);
+                const df gs = df_mul(df_mul(df_from(gk), iS), iS);   // g_k / S^2
+                gsm[tid] = make_float2(gs.h, gs.l);
+                p2m[tid] = p2;
             }
         }
+        __syncthreads();
+        float pr[kAdjRowsPerLane];
+        df gr[kAdjRowsPerLane];
+#pragma unroll
+        for (int i = 0; i < kAdjRowsPerLane; ++i) {
+            const int kk = lane + 32 * i;
+            pr[i] = kk < cnt ? p2m[kk] : 0.f;
+            const float2 g = kk < cnt ? gsm[kk] : make_float2(0.f, 0.f);
+            gr[i] = df{g.x, g.y};
+        }
+        for (int l = warp; l <= L; l += nw) {
+            const int b = hm - l, bi = b >= 0 ? b : -b;
+            float sgn = (b < 0 && (bi & 1)) ? -1.f : 1.f;
+            if (l > 0 || (nu & 1)) sgn *= 2.f;
+            acc2 a{0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < kAdjRowsPerLane; ++i) {
+                const int kk = lane + 32 * i;
+                if (kk < cnt) {
+                    const float2 va = jb[(hp + l) * nt + kk];
+                    const float2 vb = jb[bi * nt + kk];
+                    const float p = pr[i], ps = p * sgn;
+                    const df cl = df_mul(df{va.x * p, va.y * p}, df{vb.x * ps, vb.y * ps});
+                    acc_fma(a, cl, gr[i]);
+                }
+            }
+            a = warp_sum_acc(a);
+            if (lane == 0) atomicAdd(&mom[B.mom_off + l], acc_value(a));
+        }
+        __syncthreads();   // jb and gsm are rewritten by the next pass
     }
-    __syncthreads();
-    reduce_columns_add(acc, nt, L, mom + B.mom_off);
 }
 
 __global__ void __launch_bounds__(kMomThreads)
@@ -669,21 +711,23 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
 
 }  // namespace
 
-int local_adj_threads(int ntop_max, int lmax)
+int local_adj_threads(int ntop_max)
 {
-    int t = (int)(200 * 1024 / (8 * (ntop_max + 1 + lmax + 1)));
+    // (ntop + 1) double-float values plus 12 bytes of row data per thread
+    int t = (int)(200 * 1024 / (8 * (ntop_max + 1) + 12));
     t = (t / 32) * 32;
-    if (t > 128) t = 128;
+    if (t > kMomThreads) t = kMomThreads;
     if (t < 32) t = 32;
     return t;
 }
 
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                     int ntiles, int ntop_max, int lmax, int threads, const float2* w2,
+                                     int ntiles, int ntop_max, int threads, const float2* w2,
                                      const double* g_s, double* mom, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float2) * (size_t)(ntop_max + 1 + lmax + 1) * threads;
+    if (threads < 32 || threads > kMomThreads || (threads & 31)) return cudaErrorInvalidValue;
+    size_t smem = sizeof(float2) * (size_t)(ntop_max + 1) * threads + (sizeof(float2) + sizeof(float)) * threads;
     cudaError_t e = cudaFuncSetAttribute(k_local_adj_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -227,9 +227,9 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           int max_area, int lowp, const double* r_s, const double* w_s, const double* c_s,
                           double* g_s, cudaStream_t s);
-int local_adj_threads(int ntop_max, int lmax);
+int local_adj_threads(int ntop_max);
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                     int ntiles, int ntop_max, int lmax, int threads, const float2* w2,
+                                     int ntiles, int ntop_max, int threads, const float2* w2,
                                      const double* g_s, double* mom, cudaStream_t s);
 cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                   int ntiles, int lmax, const float2* r2, const double* mom, double* c_s,

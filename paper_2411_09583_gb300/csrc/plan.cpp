@@ -991,11 +991,11 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
     if ((mask & 1) && P->n_loc) {
-        const int thr = local_adj_threads(P->ntop_max, P->lmax);
+        const int thr = local_adj_threads(P->ntop_max);
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, s));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
-        NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, P->lmax,
-                                         thr, P->d_w2, P->d_gs, P->d_mom, s));
+        NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, thr,
+                                         P->d_w2, P->d_gs, P->d_mom, s));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, s));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, s));
         NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, P->d_mom,

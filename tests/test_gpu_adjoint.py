@@ -171,3 +171,32 @@ def test_autograd_finite_differences():
                 grad = tr.grad[j].item()
             fd = (lp - lm) / (2 * h)
             assert abs(fd - grad) <= 1e-5 * max(1.0, abs(grad)), (which, j, fd, grad)
+
+
+@pytest.mark.parametrize("layout", ["frequencies", "points"])
+@pytest.mark.parametrize("nu", [0, 3])
+def test_dense_bins_both_directions(layout, nu):
+    # One asymptotic region (omega r >= 1000 > z) with a small product of the
+    # r and omega ranges, so its FFT grid is short: 20000 frequencies (or
+    # points) fall in a few dozen cells, and the tiles take the per-bin moment
+    # paths (adjoint spreading of frequencies, adjoint interpolation at points,
+    # and their forward counterparts).
+    rng = np.random.default_rng(95 + nu)
+    if layout == "frequencies":
+        r, omega = rng.uniform(1.0, 2.0, 2000), rng.uniform(1000.0, 1010.0, 20000)
+    else:
+        r, omega = rng.uniform(1.0, 1.01, 20000), rng.uniform(1000.0, 2000.0, 2000)
+    c = rng.standard_normal(r.size)
+    e = rng.standard_normal(omega.size)
+    eps = 1e-10
+    from paper_2411_09583_gb300 import Plan
+    with Plan(nu, to_dev(r), to_dev(omega), eps) as p:
+        info = p.info()
+        assert info["n_asy"] > 0
+        # at least 20 packed targets per FFT point: the moment paths' tiles
+        # need 16 per cell
+        assert max(r.size, omega.size) >= 20 * info["fft_points"]
+        g = p.execute(to_dev(c)).cpu().numpy()
+        ca = p.adjoint(to_dev(e)).cpu().numpy()
+    assert np.max(np.abs(g - oracle.direct(nu, r, omega, c))) <= tol(eps, c)
+    assert np.max(np.abs(ca - oracle.direct(nu, omega, r, e))) <= tol(eps, e)
