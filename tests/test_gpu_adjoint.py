@@ -173,17 +173,20 @@ def test_autograd_finite_differences():
             assert abs(fd - grad) <= 1e-5 * max(1.0, abs(grad)), (which, j, fd, grad)
 
 
-@pytest.mark.parametrize("layout", ["frequencies", "points"])
+@pytest.mark.parametrize("layout", ["frequencies", "narrow", "points"])
 @pytest.mark.parametrize("nu", [0, 3])
 def test_dense_bins_both_directions(layout, nu):
     # One asymptotic region (omega r >= 1000 > z) with a small product of the
     # r and omega ranges, so its FFT grid is short: 20000 frequencies (or
     # points) fall in a few dozen cells, and the tiles take the per-bin moment
     # paths (adjoint spreading of frequencies, adjoint interpolation at points,
-    # and their forward counterparts).
+    # and their forward counterparts).  "narrow" (r range 1e-3) puts all
+    # frequencies in one or two FFT cells wider than the omega range.
     rng = np.random.default_rng(95 + nu)
     if layout == "frequencies":
         r, omega = rng.uniform(1.0, 2.0, 2000), rng.uniform(1000.0, 1010.0, 20000)
+    elif layout == "narrow":
+        r, omega = rng.uniform(1.0, 1.001, 2000), rng.uniform(1000.0, 1010.0, 20000)
     else:
         r, omega = rng.uniform(1.0, 1.01, 20000), rng.uniform(1000.0, 2000.0, 2000)
     c = rng.standard_normal(r.size)
