@@ -213,6 +213,55 @@ cudaError_t aux_stream(Aux** out)
     return cudaSuccess;
 }
 
+// Per host thread and device: the second stream (and fork / join events) on
+// which an execute runs the local and direct blocks beside the asymptotic
+// pipeline.  Per thread, so that executes from several host threads never
+// share an event.
+struct ExecAux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+thread_local ExecAux t_exec_aux[64];
+
+// Forks a second stream off s and joins it back into s on close() or when it
+// goes out of scope (also on an early error return, so that no work of the
+// execute outlives the caller's stream).  Graph capture follows the event
+// record / wait pairs.
+struct ClassFork {
+    ExecAux* ax = nullptr;
+    cudaStream_t main = nullptr;
+    cudaError_t open(cudaStream_t s)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        ExecAux& a = t_exec_aux[dev];
+        if (!a.s) {
+            e = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaEventRecord(a.fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a.s, a.fork, 0);
+        if (e != cudaSuccess) return e;
+        ax = &a;
+        main = s;
+        return cudaSuccess;
+    }
+    cudaStream_t stream(cudaStream_t s) const { return ax ? ax->s : s; }
+    cudaError_t close()
+    {
+        if (!ax) return cudaSuccess;
+        cudaError_t e = cudaEventRecord(ax->join, ax->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ax->join, 0);
+        ax = nullptr;
+        return e;
+    }
+    ~ClassFork() { close(); }
+};
+
 }  // namespace
 
 namespace {
@@ -909,8 +958,15 @@ int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, 
 static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
-    cudaStream_t ls = s;
-    if ((mask & 1) && P->n_loc) {
+    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
+    // The block classes share no scratch and only add into g (FP64 atomics):
+    // the local and direct blocks run on a second stream beside the
+    // asymptotic pipeline.  With stage timing on, every stage stays on s in
+    // order, so that each stage's time is its own.
+    ClassFork fk;
+    if (!P->opt.timing && asy && (loc || dir)) NUHT_CK(fk.open(s));
+    const cudaStream_t ls = fk.stream(s);
+    if (loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
@@ -921,13 +977,13 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                   P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
-    if ((mask & 4) && P->n_dir) {
+    if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area,
                               P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_cs, P->d_gs, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
-    if ((mask & 2) && P->n_asy) {
+    if (asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
         if (P->opt.precision == NUHT_PREC_MIXED)
@@ -955,6 +1011,7 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                       P->d_w, P->d_w2, P->d_gq, P->d_gs, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
     }
+    NUHT_CK(fk.close());
     return NUHT_OK;
 }
 
@@ -990,25 +1047,30 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
 static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
-    if ((mask & 1) && P->n_loc) {
+    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
+    // local and direct blocks on a second stream, as in apply_forward
+    ClassFork fk;
+    if (!P->opt.timing && asy && (loc || dir)) NUHT_CK(fk.open(s));
+    const cudaStream_t ls = fk.stream(s);
+    if (loc) {
         const int thr = local_adj_threads(P->ntop_max);
-        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, s));
-        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
         NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, thr,
-                                         P->d_w2, P->d_gs, P->d_mom, s));
-        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, s));
-        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, s));
+                                         P->d_w2, P->d_gs, P->d_mom, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
         NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, P->d_mom,
-                                      P->d_cs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, s));
+                                      P->d_cs, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
-    if ((mask & 4) && P->n_dir) {
-        NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, s));
+    if (dir) {
+        NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->max_dir_area,
-                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_gs, P->d_cs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_DIRECT, s));
+                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_gs, P->d_cs, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
-    if ((mask & 2) && P->n_asy) {
+    if (asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_tg, 0, sizeof(double2) * P->gq_len, s));
         NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab, P->d_w,
@@ -1028,6 +1090,7 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                       P->d_bq, P->d_cs, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
     }
+    NUHT_CK(fk.close());
     return NUHT_OK;
 }
 
