@@ -207,20 +207,42 @@ __global__ void k_scatter(const double* __restrict__ gs, const int32_t* __restri
         g[(int64_t)perm[i] * stride + comp] = gs[i];
 }
 
-// s[k] = max{j : omega_k * r_j <= z} (or -1): the boundary of the local region
-// in row k of the sorted matrix (non-increasing in k).  Binary search per row.
-__global__ void k_staircase(const double* __restrict__ r, int64_t n, const double* __restrict__ w,
-                            int64_t m, double z, int32_t* __restrict__ s)
+// First j in [lo, hi) with wk * r_j > z (hi if none); r ascending.
+__device__ __forceinline__ int64_t first_above(const double* __restrict__ r, int64_t lo, int64_t hi, double wk,
+                                               double z)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const double wk = w[k];
-        int64_t lo = 0, hi = n;   // first j with wk * r_j > z
-        while (lo < hi) {
-            const int64_t mid = lo + ((hi - lo) >> 1);
-            if (wk * r[mid] <= z) lo = mid + 1; else hi = mid;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (wk * r[mid] <= z) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kStairThreads = 256;
+constexpr int kStairRows = 4;   // rows per thread
+
+// s[k] = max{j : omega_k * r_j <= z} (or -1): the boundary of the local region
+// in row k of the sorted matrix.  f(k) = s[k] + 1 is non-increasing in k (the
+// FP64 product is monotone in both factors), so each CTA searches its first
+// and last rows over all of r and its other rows only between those two
+// bounds: one full search of latency per CTA instead of one per row.
+__global__ void __launch_bounds__(kStairThreads) k_staircase(const double* __restrict__ r, int64_t n,
+                                                             const double* __restrict__ w, int64_t m, double z,
+                                                             int32_t* __restrict__ s)
+{
+    __shared__ int64_t fb[2];
+    const int64_t span = (int64_t)kStairThreads * kStairRows;
+    for (int64_t base = (int64_t)blockIdx.x * span; base < m; base += (int64_t)gridDim.x * span) {
+        const int64_t last = (base + span < m ? base + span : m) - 1;
+        if (threadIdx.x < 2) fb[threadIdx.x] = first_above(r, 0, n, w[threadIdx.x == 0 ? base : last], z);
+        __syncthreads();
+        const int64_t hi = fb[0], lo = fb[1];   // f(last) <= f(k) <= f(base)
+#pragma unroll
+        for (int i = 0; i < kStairRows; ++i) {
+            const int64_t k = base + threadIdx.x + (int64_t)i * kStairThreads;
+            if (k <= last) s[k] = (int32_t)(first_above(r, lo, hi, w[k], z) - 1);
         }
-        s[k] = (int32_t)(lo - 1);
+        __syncthreads();   // fb is rewritten by the next range
     }
 }
 
@@ -358,14 +380,7 @@ __global__ void k_staircase_many(const double* __restrict__ r, const double* __r
             if (probs[mid].w_off <= k) lo = mid; else hi = mid;
         }
         const ProbParams& P = probs[lo];
-        const double wk = w[k];
-        const double* rp = r + P.r_off;
-        int64_t a = 0, b = P.n;
-        while (a < b) {
-            const int64_t mid = a + ((b - a) >> 1);
-            if (wk * rp[mid] <= P.z) a = mid + 1; else b = mid;
-        }
-        s[k] = (int32_t)(a - 1);
+        s[k] = (int32_t)(first_above(r + P.r_off, 0, P.n, w[k], P.z) - 1);
     }
 }
 
@@ -373,7 +388,7 @@ cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_
                              int32_t* s_out, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    k_staircase<<<grid_for(m, 256), 256, 0, s>>>(r, n, w, m, z, s_out);
+    k_staircase<<<grid_for(m, kStairThreads * kStairRows), kStairThreads, 0, s>>>(r, n, w, m, z, s_out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -80,8 +80,14 @@ def test_clustered_and_exponential_points():
     _check(0, v, v * 40.0, c, 1e-8)
 
 
-def test_block_lists_match_oracle_subdivision():
+@pytest.mark.parametrize("ties", [False, True])
+def test_block_lists_match_oracle_subdivision(ties):
+    # m = 2300 rows: the staircase's per-CTA ranges (1024 rows) with a ragged
+    # tail; "ties" repeats frequencies and points and puts zeros among them
     r, omega, c = uniform_problem(2500, 2300, omega_max=3000.0, seed=11)
+    if ties:
+        r, omega = np.round(r, 3), np.round(omega, -1)
+        omega[::7] = 0.0
     g, info, blocks = run_forward(2, r, omega, c, 1e-9)
     rs, ws = np.sort(r), np.sort(omega)
     Lb, Ab, Db = OS.subdivide(list(rs), list(ws), info["z"], 1024, 16)
