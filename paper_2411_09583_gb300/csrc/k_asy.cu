@@ -826,35 +826,54 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
 
 // One CTA per tile of consecutive (sorted) points of one block; the tile
 // takes the moment path when its points are dense in the grid's bins.
+// Path of a spreading tile, packed: bits 0-1 the path (0 taps, 1 plain
+// moments, 2 q-folded moments), bits 2-5 the fold's K, bits 6-11 its E,
+// bits 12-17 its Edf.  The path depends only on the sorted points and the
+// block, so it is decided once per plan (k_spread_modes).
+__device__ __forceinline__ FoldPlan fold_unpack(int mode)
+{
+    return FoldPlan{(mode >> 2) & 15, (mode >> 6) & 63, (mode >> 12) & 63};
+}
+
+__global__ void k_spread_modes(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+                               const Tile* __restrict__ tiles, int ntiles, Tables tab,
+                               const double* __restrict__ r_s, int32_t* __restrict__ modes)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntiles; i += gridDim.x * blockDim.x) {
+        const Tile t = tiles[i];
+        int mode = 0;
+        if (t.count > 0) {
+            const AsyBlock B = blks[t.blk];
+            long long X;
+            df vd;
+            const int lfirst = spread_cell_fx(B, tab.w, r_s[t.start], &X, &vd);
+            const int nbins = spread_cell_fx(B, tab.w, r_s[t.start + t.count - 1], &X, &vd) - lfirst + 1;
+            if (nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins) {
+                mode = 1;
+                FoldPlan fp;
+                if (fold_plan(B, tab, probs[B.prob].Q, lfirst, &fp))
+                    mode = 2 | (fp.K << 2) | (fp.E << 6) | (fp.Edf << 12);
+            }
+        }
+        modes[i] = mode;
+    }
+}
+
 __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                             const Tile* __restrict__ tiles, Tables tab,
+                             const Tile* __restrict__ tiles, const int32_t* __restrict__ modes, Tables tab,
                              const double* __restrict__ r_s, const float2* __restrict__ r2,
                              const float2* __restrict__ c2, double2* __restrict__ grid_b)
 {
     extern __shared__ float4 smem4[];
-    __shared__ int use_mom;
-    __shared__ FoldPlan fplan;
     const Tile t = tiles[blockIdx.x];
+    if (t.count <= 0) return;
+    const int mode = modes[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
-    if (t.count <= 0) return;
-    if (threadIdx.x == 0) {
-        long long X;
-        df vd;
-        const int lfirst = spread_cell_fx(B, tab.w, r_s[t.start], &X, &vd);
-        const int nbins = spread_cell_fx(B, tab.w, r_s[t.start + t.count - 1], &X, &vd) - lfirst + 1;
-        use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
-        FoldPlan fp;
-        if (use_mom && fold_plan(B, tab, Q, lfirst, &fp)) {
-            use_mom = 2;
-            fplan = fp;
-        }
-    }
-    __syncthreads();
     double2* gb = grid_b + B.b_off;
-    if (use_mom == 2)
-        spread_fold(B, Q, probs[B.prob].qs, t, tab, fplan, r_s, r2, c2, gb, smem4);
-    else if (use_mom) {
+    if ((mode & 3) == 2)
+        spread_fold(B, Q, probs[B.prob].qs, t, tab, fold_unpack(mode), r_s, r2, c2, gb, smem4);
+    else if (mode & 3) {
         // c_j (r_j/rho)^(-q-1/2) e^{i w_c x_j} onto the 2 N1 + 1 modes
         const int nf1 = 2 * B.N1 + 1;
         spread_moments(Q, probs[B.prob].qs, t, tab,
@@ -1888,27 +1907,19 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
 }
 
 // FP32 spreading (coordinates and phase reduction in FP64).
+// Mixed precision: the plain moment path for every dense tile (mode != 0).
 __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
-                                 const Tile* __restrict__ tiles, Tables tab,
+                                 const Tile* __restrict__ tiles, const int32_t* __restrict__ modes, Tables tab,
                                  const double* __restrict__ r_s, const float2* __restrict__ r2,
                                  const float2* __restrict__ c2, double2* __restrict__ grid_b)
 {
     extern __shared__ float2 smf[];
-    __shared__ int use_mom;
     const Tile t = tiles[blockIdx.x];
+    if (t.count <= 0) return;
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
-    if (t.count <= 0) return;
-    if (threadIdx.x == 0) {
-        long long X;
-        df vd;
-        const int lfirst = spread_cell_fx(B, tab.w, r_s[t.start], &X, &vd);
-        const int nbins = spread_cell_fx(B, tab.w, r_s[t.start + t.count - 1], &X, &vd) - lfirst + 1;
-        use_mom = nbins <= kMaxTileBins && t.count >= kMomMinPerBin * nbins;
-    }
-    __syncthreads();
     double2* gb = grid_b + B.b_off;
-    if (use_mom)
+    if (modes[blockIdx.x] & 3)
         spread_moments_f32(B, Q, t, tab, r_s, r2, c2, gb, (float*)smf);
     else
         spread_taps_f32(B, Q, t, tab, r_s, r2, c2, gb, smf);
@@ -2075,8 +2086,9 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
 }
 
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
-                                  const float2* c2, double2* grid_b, cudaStream_t s)
+                                  const int32_t* modes, int ntiles, int qmax, int nt, Tables tab,
+                                  const double* r_s, const float2* r2, const float2* c2, double2* grid_b,
+                                  cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float2) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
@@ -2085,7 +2097,7 @@ cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks,
     if (smem_mom > smem) smem = smem_mom;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, r2, c2, grid_b);
+    k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, grid_b);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -2103,9 +2115,19 @@ cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks,
     return cudaGetLastError();
 }
 
+cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles, int ntiles,
+                                Tables tab, const double* r_s, int32_t* modes, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    const int nb = (ntiles + 255) / 256;
+    k_spread_modes<<<nb < 152 * 16 ? nb : 152 * 16, 256, 0, s>>>(probs, blks, tiles, ntiles, tab, r_s, modes);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
-                              const float2* c2, double2* grid_b, cudaStream_t s)
+                              const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
+                              const float2* r2, const float2* c2, double2* grid_b, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
@@ -2116,7 +2138,7 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     if (smem_fold > smem) smem = smem_fold;
     cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, r_s, r2, c2, grid_b);
+    k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, grid_b);
     count_launches(1);
     return cudaGetLastError();
 }

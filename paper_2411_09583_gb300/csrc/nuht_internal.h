@@ -239,9 +239,12 @@ cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, 
                               double* c_s, cudaStream_t s);
 // x[i] as double-float (hi, lo)
 cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream_t s);
+// Per spreading tile, the path of k_asy_spread (plan time; modes[ntiles]).
+cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles, int ntiles,
+                                Tables tab, const double* r_s, int32_t* modes, cudaStream_t s);
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
-                              const float2* c2, double2* grid_b, cudaStream_t s);
+                              const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
+                              const float2* r2, const float2* c2, double2* grid_b, cudaStream_t s);
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
                                   double2* tgrid, cudaStream_t s);
@@ -249,8 +252,9 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
                                   int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
                                   double* c_s, cudaStream_t s);
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, int nt, Tables tab, const double* r_s, const float2* r2,
-                                  const float2* c2, double2* grid_b, cudaStream_t s);
+                                  const int32_t* modes, int ntiles, int qmax, int nt, Tables tab,
+                                  const double* r_s, const float2* r2, const float2* c2, double2* grid_b,
+                                  cudaStream_t s);
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
                                   const float4* grid_q, double* g_s, cudaStream_t s);

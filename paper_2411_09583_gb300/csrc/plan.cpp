@@ -89,6 +89,7 @@ struct nuht_plan_s {
     Tile *d_tmom = nullptr, *d_teval = nullptr;
     AsyBlock* d_asy = nullptr;
     Tile *d_tspread = nullptr, *d_tinterp = nullptr;
+    int32_t* d_smode = nullptr;   // path of each spreading tile (k_spread_modes)
     Tile *d_fblock = nullptr, *d_fsmall = nullptr, *d_fa = nullptr, *d_fb = nullptr;
     DirectBlock* d_dir = nullptr;
     double* d_mom = nullptr;
@@ -675,6 +676,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
     size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m), a_cs2 = A.reserve<float2>(n);
     size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
+    size_t a_sm = A.reserve<int32_t>((size_t)ntile[LIST_SPREAD]);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
@@ -803,6 +805,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     tb.ph_scale2 = make_float2((float)T.ph_scale, (float)(T.ph_scale - (double)(float)T.ph_scale));
     tb.tw = P->d_tw; tb.tw_log2 = T.tw_log2;
     tb.tw2 = (const float4*)(D + a_tw2);
+    P->d_smode = (int32_t*)(D + a_sm);
+    NUHT_CK(launch_spread_modes(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, tb, P->d_r, P->d_smode, s));
     P->plan_ms[3] = ms_since(clk);
     return NUHT_OK;
 }
@@ -987,10 +991,10 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
         if (P->opt.precision == NUHT_PREC_MIXED)
-            NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax,
+            NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
                                           P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, s));
         else
-            NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax,
+            NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
                                       P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, s));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
