@@ -214,18 +214,20 @@ cudaError_t aux_stream(Aux** out)
     return cudaSuccess;
 }
 
-// Per host thread and device: the second stream (and fork / join events) on
-// which an execute runs the local and direct blocks beside the asymptotic
-// pipeline.  Per thread, so that executes from several host threads never
-// share an event.
+// Per host thread and device: the two streams (and fork / join events) on
+// which an execute runs its block classes: the asymptotic pipeline on a
+// stream of the greatest priority, the local and direct blocks on one of the
+// default priority, so that their CTAs take what the asymptotic kernels'
+// CTAs leave free on an SM.  Per thread, so that executes from several host
+// threads never share an event.
 struct ExecAux {
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t lo = nullptr, hi = nullptr;
+    cudaEvent_t fork = nullptr, join_lo = nullptr, join_hi = nullptr;
 };
 thread_local ExecAux t_exec_aux[64];
 
-// Forks a second stream off s and joins it back into s on close() or when it
-// goes out of scope (also on an early error return, so that no work of the
+// Forks the two streams off s and joins them back into s on close() or when
+// it goes out of scope (also on an early error return, so that no work of the
 // execute outlives the caller's stream).  Graph capture follows the event
 // record / wait pairs.
 struct ClassFork {
@@ -238,25 +240,33 @@ struct ClassFork {
         if (e != cudaSuccess) return e;
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
         ExecAux& a = t_exec_aux[dev];
-        if (!a.s) {
-            e = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking);
+        if (!a.lo) {
+            int least = 0, greatest = 0;
+            e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, greatest);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a.lo, cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join_lo, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join_hi, cudaEventDisableTiming);
             if (e != cudaSuccess) return e;
         }
         e = cudaEventRecord(a.fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(a.s, a.fork, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a.lo, a.fork, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a.hi, a.fork, 0);
         if (e != cudaSuccess) return e;
         ax = &a;
         main = s;
         return cudaSuccess;
     }
-    cudaStream_t stream(cudaStream_t s) const { return ax ? ax->s : s; }
+    cudaStream_t local(cudaStream_t s) const { return ax ? ax->lo : s; }
+    cudaStream_t asy(cudaStream_t s) const { return ax ? ax->hi : s; }
     cudaError_t close()
     {
         if (!ax) return cudaSuccess;
-        cudaError_t e = cudaEventRecord(ax->join, ax->s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ax->join, 0);
+        cudaError_t e = cudaEventRecord(ax->join_lo, ax->lo);
+        if (e == cudaSuccess) e = cudaEventRecord(ax->join_hi, ax->hi);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ax->join_lo, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ax->join_hi, 0);
         ax = nullptr;
         return e;
     }
@@ -964,12 +974,12 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     const int mask = P->opt.class_mask;
     const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
     // The block classes share no scratch and only add into g (FP64 atomics):
-    // the local and direct blocks run on a second stream beside the
-    // asymptotic pipeline.  With stage timing on, every stage stays on s in
-    // order, so that each stage's time is its own.
+    // the local and direct blocks run beside the asymptotic pipeline (ClassFork).
+    // With stage timing on, every stage stays on s in order, so that each
+    // stage's time is its own.
     ClassFork fk;
     if (!P->opt.timing && asy && (loc || dir)) NUHT_CK(fk.open(s));
-    const cudaStream_t ls = fk.stream(s);
+    const cudaStream_t ls = fk.local(s), as = fk.asy(s);
     if (loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
@@ -988,32 +998,32 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
-        NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, as));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                          P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, s));
+                                          P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, as));
         else
             NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
+                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, as));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_gb,
-                                     P->d_gq, s));
+                                     P->d_gq, as));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small,
-                                     P->tab, P->d_gb, P->d_gq, s));
+                                     P->tab, P->d_gb, P->d_gq, as));
         if (P->has_large_fft)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
-                                         P->d_gb, P->d_gtmp, P->d_gq, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, s));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
+                                         P->d_gb, P->d_gtmp, P->d_gq, as));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                          P->d_w, P->d_w2, P->d_gq, P->d_gs, s));
+                                          P->d_w, P->d_w2, P->d_gq, P->d_gs, as));
         else
             NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                      P->d_w, P->d_w2, P->d_gq, P->d_gs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
+                                      P->d_w, P->d_w2, P->d_gq, P->d_gs, as));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
     return NUHT_OK;
@@ -1055,7 +1065,7 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     // local and direct blocks on a second stream, as in apply_forward
     ClassFork fk;
     if (!P->opt.timing && asy && (loc || dir)) NUHT_CK(fk.open(s));
-    const cudaStream_t ls = fk.stream(s);
+    const cudaStream_t ls = fk.local(s), as = fk.asy(s);
     if (loc) {
         const int thr = local_adj_threads(P->ntop_max);
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
@@ -1075,24 +1085,24 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, s));
-        NUHT_CK(cudaMemsetAsync(P->d_tg, 0, sizeof(double2) * P->gq_len, s));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_CK(cudaMemsetAsync(P->d_tg, 0, sizeof(double2) * P->gq_len, as));
         NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab, P->d_w,
-                                      P->d_gs, P->d_tg, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, s));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, s));
+                                      P->d_gs, P->d_tg, as));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_tg, P->d_bq,
-                                     s, true));
+                                     as, true));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small, P->tab,
-                                     P->d_tg, P->d_bq, s, true));
+                                     P->d_tg, P->d_bq, as, true));
         if (P->has_large_fft)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
-                                         P->d_tg, P->d_gtmp, P->d_bq, s, true));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, s));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, s));
+                                         P->d_tg, P->d_gtmp, P->d_bq, as, true));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
+        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
         NUHT_CK(launch_asy_adj_interp(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab, P->d_r,
-                                      P->d_bq, P->d_cs, s));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, s));
+                                      P->d_bq, P->d_cs, as));
+        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
     return NUHT_OK;
