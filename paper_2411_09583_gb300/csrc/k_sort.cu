@@ -10,8 +10,8 @@
 // compare like unsigned integers, so an 8-pass, 8-bit LSD radix sort on the
 // raw 64-bit patterns sorts them.  Each pass: per-tile digit histogram,
 // one exclusive scan over (digit, tile), then a stable scatter in which each
-// CTA ranks its tile's elements round by round (warp match + per-warp
-// prefix counts), so equal keys keep their input order.
+// warp ranks its run of the tile (warp match + per-warp digit counts) and one
+// prefix over the warps places the runs, so equal keys keep their input order.
 #include <cstdint>
 
 #include "nuht_internal.h"
@@ -106,16 +106,24 @@ __global__ void k_sort_rowscan(uint32_t* __restrict__ hist, int ntiles, uint32_t
     if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
-__global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
-                               int64_t n, int shift, int ntiles,
-                               const uint32_t* __restrict__ offs, const uint32_t* __restrict__ tot,
-                               uint64_t* __restrict__ kout, int32_t* __restrict__ vout)
+// Stable scatter of one pass.  Warp w of a tile owns its 128 consecutive
+// elements, in rounds of 32, so (warp, round, lane) is the input order: each
+// warp ranks its elements among equal digits with a per-warp digit count in
+// shared memory (warp-synchronous, no CTA barrier per round), then one
+// exclusive prefix over the warps per digit places every warp's run after
+// the earlier warps' in the tile's part of each digit bucket.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+    const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n, int shift, int ntiles,
+    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ tot, uint64_t* __restrict__ kout,
+    int32_t* __restrict__ vout)
 {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t base[kRadix];            // running position of each digit in this tile
-    __shared__ uint32_t wcnt[kWarps][kRadix];    // per-warp counts, then per-warp prefixes
+    __shared__ uint32_t wcnt[kWarps][kRadix];   // per-warp digit counts, then the warps' starts
+    __shared__ uint32_t wsum[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // start of each digit's bucket: exclusive scan of the 256 digit totals
+    // start of digit threadIdx.x's bucket for this tile: exclusive scan of the
+    // 256 digit totals plus this tile's offset inside the bucket
+    uint32_t mybase;
     {
         const uint32_t v = tot[threadIdx.x];     // blockDim.x == kRadix
         uint32_t x = v;
@@ -123,47 +131,52 @@ __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* 
             const uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
             if (lane >= off) x += t;
         }
-        if (lane == 31) wcnt[0][warp] = x;
+        if (lane == 31) wsum[warp] = x;
+        for (int i = threadIdx.x; i < kWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
         __syncthreads();
         uint32_t pre = 0;
-        for (int w = 0; w < warp; ++w) pre += wcnt[0][w];
-        base[threadIdx.x] = pre + x - v + offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-        __syncthreads();
+        for (int w = 0; w < warp; ++w) pre += wsum[w];
+        mybase = pre + x - v + offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     }
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortItems);
+    uint64_t key[kSortItems];
+    int32_t val[kSortItems];
+    unsigned dig[kSortItems];
+    uint32_t rk[kSortItems];
+#pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-        int64_t i = tbase + it * kSortThreads + threadIdx.x;
-        bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
-        int32_t val = valid ? vin[i] : 0;
-        unsigned d = valid ? (unsigned)((key >> shift) & 0xFF) : 0x100u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned wrank = __popc(peers & lt);
-        bool leader = (peers & lt) == 0;
-        if (valid && leader) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        // exclusive prefix over warps for each digit, advance the tile base
-        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) {
-            uint32_t run = base[dd];
-            for (int w = 0; w < kWarps; ++w) {
-                uint32_t t = wcnt[w][dd];
-                wcnt[w][dd] = run;
-                run += t;
-            }
-            base[dd] = run;
+        const int64_t i = wbase + it * 32 + lane;
+        const bool valid = i < n;
+        key[it] = valid ? kin[i] : 0ull;
+        val[it] = valid ? vin[i] : 0;
+        const unsigned d = valid ? (unsigned)((key[it] >> shift) & 0xFF) : 0x100u;
+        dig[it] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t prior = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wcnt[warp][d] = prior + __popc(peers);
+        __syncwarp();
+        rk[it] = prior + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = mybase;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += t;
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = wcnt[warp][d] + wrank;
-            kout[pos] = key;
-            vout[pos] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        if (dig[it] < 0x100u) {
+            const uint32_t pos = wcnt[warp][dig[it]] + rk[it];
+            kout[pos] = key[it];
+            vout[pos] = val[it];
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < kWarps * kRadix; k += blockDim.x) (&wcnt[0][0])[k] = 0;
-        __syncthreads();
     }
 }
 
