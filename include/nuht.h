@@ -67,6 +67,15 @@ extern "C" {
    and its entry list stay in one CTA's shared memory. */
 #define NUHT_MAX_MIN_SIZE 16384
 
+/* opts.timing: NUHT_TIMING_OFF records nothing; NUHT_TIMING_LIVE records a
+ * CUDA event pair around each stage on the stream the stage runs on (the
+ * block classes run concurrently as in an untimed execute, so the stage times
+ * of different classes overlap); NUHT_TIMING_SERIAL runs every stage in order
+ * on the caller's stream, so each time is that stage alone. */
+#define NUHT_TIMING_OFF    0
+#define NUHT_TIMING_LIVE   1
+#define NUHT_TIMING_SERIAL 2
+
 typedef struct {
     int precision;     /* NUHT_PREC_FP64 (default) or NUHT_PREC_MIXED */
     int min_size;      /* largest area (rows*cols) of a mixed block summed directly;
@@ -74,8 +83,7 @@ typedef struct {
     int n_split_cand;  /* candidate rows tried by SplitIndices (Sec. 4.1); default 16 */
     int m_terms;       /* asymptotic terms M; 0 = the heuristic of Sec. 3.3 */
     int class_mask;    /* bit c set = apply blocks of class c (testing aid); default 7 */
-    int timing;        /* nonzero: execute records a CUDA event pair around each stage
-                          (see nuht_stage_times); default 0 */
+    int timing;        /* NUHT_TIMING_*: stage events (see nuht_stage_times); default 0 */
     int spread_tile;   /* points per spreading CTA: 0 = automatic (256, or 128 when
                           2M > 16); else 64..256, a multiple of 32 */
     int reserved[5];   /* must be zero */
@@ -189,7 +197,9 @@ int nuht_get_blocks(nuht_plan_t p, int cls, int64_t *ranges, int64_t cap, int64_
 int nuht_get_permutations(nuht_plan_t p, int32_t *perm_r, int32_t *perm_omega);
 
 /* Device time (milliseconds) of each stage of the most recent nuht_execute
- * of a plan built with opts.timing != 0, summed over the vectors of that call;
+ * of a plan built with opts.timing != NUHT_TIMING_OFF, summed over the vectors
+ * of that call (with NUHT_TIMING_LIVE the stages of different block classes
+ * overlap);
  * ms has room for cap doubles (NUHT_NUM_STAGES suffices); stages that did not
  * run report 0.  Waits for the events of that call.  NUHT_ERR_INVALID_ARG if
  * timing is off or nothing ran yet. */

@@ -881,6 +881,7 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
         if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
     if (o.spread_tile != 0 && (o.spread_tile < 64 || o.spread_tile > 256 || o.spread_tile % 32))
         return NUHT_ERR_INVALID_ARG;
+    if (o.timing < NUHT_TIMING_OFF || o.timing > NUHT_TIMING_SERIAL) return NUHT_ERR_INVALID_ARG;
     return NUHT_OK;
 }
 
@@ -974,11 +975,11 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     const int mask = P->opt.class_mask;
     const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
     // The block classes share no scratch and only add into g (FP64 atomics):
-    // the local and direct blocks run beside the asymptotic pipeline (ClassFork).
-    // With stage timing on, every stage stays on s in order, so that each
-    // stage's time is its own.
+    // the local and direct blocks run beside the asymptotic pipeline (ClassFork),
+    // each stage's events on its own stream.  NUHT_TIMING_SERIAL keeps every
+    // stage in order on s, so that each stage's time is its own.
     ClassFork fk;
-    if (!P->opt.timing && asy && (loc || dir)) NUHT_CK(fk.open(s));
+    if (P->opt.timing != NUHT_TIMING_SERIAL && asy && (loc || dir)) NUHT_CK(fk.open(s));
     const cudaStream_t ls = fk.local(s), as = fk.asy(s);
     if (loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
@@ -1062,9 +1063,9 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
     const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
-    // local and direct blocks on a second stream, as in apply_forward
+    // local and direct blocks beside the asymptotic pipeline, as in apply_forward
     ClassFork fk;
-    if (!P->opt.timing && asy && (loc || dir)) NUHT_CK(fk.open(s));
+    if (P->opt.timing != NUHT_TIMING_SERIAL && asy && (loc || dir)) NUHT_CK(fk.open(s));
     const cudaStream_t ls = fk.local(s), as = fk.asy(s);
     if (loc) {
         const int thr = local_adj_threads(P->ntop_max);

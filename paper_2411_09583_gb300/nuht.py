@@ -38,7 +38,9 @@ def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class
     o.n_split_cand = int(n_split_cand)
     o.m_terms = int(m_terms)
     o.class_mask = int(class_mask)
-    o.timing = 1 if timing else 0
+    # False: off; True: stage events on each stage's stream (the block classes
+    # overlap); "serial": every stage in order on the caller's stream
+    o.timing = 2 if timing == "serial" else (1 if timing else 0)
     o.spread_tile = int(spread_tile)
     return o
 
@@ -153,7 +155,8 @@ class Plan:
         return out
 
     def stage_times(self):
-        """{stage: device ms} of the most recent execute (plan built with timing=True)."""
+        """{stage: device ms} of the most recent execute (plan built with timing=True or
+        "serial"; with True the stages of different block classes overlap)."""
         ms = (ctypes.c_double * N.NUM_STAGES)()
         N.check(N.lib().nuht_stage_times(self._h, ms, N.NUM_STAGES), "nuht_stage_times")
         return dict(zip(stage_names(), list(ms)))
