@@ -602,8 +602,31 @@ def run_ours(a):
         roof["traffic"] = tr
         roof["traffic_basis"] = basis
 
-    extra_batched = extra_mixed = extra_grad = extra_stress = None
+    extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = None
     if not a.no_extra and ws == 1:
+        # the same workload at the other order of the scaled plain-NUHT
+        # configuration (nu = 10), same options and timing as the main line
+        o_nu = 10 if a.nu != 10 else 0
+        for _ in range(2):
+            with Plan(o_nu, dr, dw, a.eps, **opts) as pw:
+                pw.execute(dc)
+        o_ms = []
+        for _ in range(a.steps):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            po = Plan(o_nu, dr, dw, a.eps, **opts)
+            po.execute(dc)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            o_ms.append(s0.elapsed_time(s1))
+            po.close()
+        with Plan(o_nu, dr, dw, a.eps, **opts) as pw:
+            oi = pw.info()
+        extra_order = {"nu": o_nu, "ms_per_step": statistics.median(o_ms),
+                       "value": (a.n + a.m) / (statistics.median(o_ms) * 1e-3), "unit": UNIT,
+                       "step": "plan + execute, same workload and options as the main line",
+                       "M": oi["M"], "L": oi["L"], "z": oi["z"]}
         extra_batched = run_batched(dev, a.steps)
         extra_mixed = run_mixed(dev, a.steps)
         extra_grad = run_grad(dev, a.steps)
@@ -643,6 +666,7 @@ def run_ours(a):
                 "mixed_precision": extra_mixed,
                 "differentiation": extra_grad,
                 "stress": extra_stress,
+                "other_order": extra_order,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],
