@@ -17,6 +17,7 @@
 // J_nu: Miller recurrence (or the power series) where omega r <= z, and the
 // M-term Hankel expansion, accurate to eps there by the choice of z, where
 // omega r > z.
+#include <algorithm>
 #include <cstdint>
 
 #include "device_math.cuh"
@@ -496,6 +497,20 @@ __device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, 
     return lowp ? (double)jn_miller_f32x(P.nu, x.h) : jn_miller_dfx(P.nu, x);
 }
 
+// direct_entry_fx for lowp as an FP32 value (no FP64 beyond the rare series).
+__device__ __forceinline__ float direct_entry_f32x(const ProbParams& P, DirFx F, double w, double r, bool asy)
+{
+    const int s = F.fr + F.fw;
+    if (s < 64 || s > 127) return (float)direct_entry(P, w, r, asy, true);
+    const unsigned long long Om = (unsigned long long)fx_from_double(w, F.fw);
+    const unsigned long long R = (unsigned long long)fx_from_double(r, F.fr);
+    const unsigned long long Pl = Om * R, Ph = __umul64hi(Om, R);
+    const df x = df_from_u128(Ph, Pl, s);
+    if (asy) return jn_hankel_f32x(P, x.h, turns_u128(Ph, Pl, s));
+    if (x.h < 1.f) return (float)jn_series(P.nu, w * r);
+    return jn_miller_f32x(P.nu, x.h);
+}
+
 // The fixed-point frame of a direct block: r < 2^(62 - fr), omega < 2^(62 - fw).
 __device__ __forceinline__ DirFx direct_frame(const double* __restrict__ r_s, const double* __restrict__ w_s,
                                               const DirectBlock& B)
@@ -508,17 +523,40 @@ __device__ __forceinline__ DirFx direct_frame(const double* __restrict__ r_s, co
 
 // Splits the entries of a direct block into a local list (omega r <= z, from
 // the front) and an asymptotic list (from the back) in shared memory, so that
-// warps run one branch each.  Returns the number of local entries.
+// warps run one branch each.  The split uses the FP32 parts of omega and r
+// (either branch is accurate to eps near the crossover) and one counter update
+// per warp and list.  Returns the number of local entries.  blockDim is a
+// multiple of 32.
 __device__ __forceinline__ int direct_partition(const ProbParams& P, const DirectBlock& B, int cols, int area,
-                                                const double* __restrict__ r_s, const double* __restrict__ w_s,
+                                                const float2* __restrict__ r2, const float2* __restrict__ w2,
                                                 int* list, int* cnt)
 {
     if (threadIdx.x == 0) { cnt[0] = 0; cnt[1] = 0; }
     __syncthreads();
-    for (int e = threadIdx.x; e < area; e += blockDim.x) {
-        const int rr = e / cols, cc = e - rr * cols;
-        if (w_s[B.k0 + rr] * r_s[B.j0 + cc] > P.z) list[area - 1 - atomicAdd(&cnt[1], 1)] = e;
-        else list[atomicAdd(&cnt[0], 1)] = e;
+    const float zf = (float)P.z;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int area_pad = (area + 31) & ~31;
+    for (int e = threadIdx.x; e < area_pad; e += blockDim.x) {
+        const bool valid = e < area;
+        bool asy = false;
+        if (valid) {
+            const int rr = e / cols, cc = e - rr * cols;
+            asy = w2[B.k0 + rr].x * r2[B.j0 + cc].x > zf;
+        }
+        const unsigned ma = __ballot_sync(0xffffffffu, valid && asy);
+        const unsigned ml = __ballot_sync(0xffffffffu, valid && !asy);
+        int ba = 0, bl = 0;
+        if (lane == 0) {
+            if (ma) ba = atomicAdd(&cnt[1], __popc(ma));
+            if (ml) bl = atomicAdd(&cnt[0], __popc(ml));
+        }
+        ba = __shfl_sync(0xffffffffu, ba, 0);
+        bl = __shfl_sync(0xffffffffu, bl, 0);
+        if (valid) {
+            if (asy) list[area - 1 - (ba + __popc(ma & lt))] = e;
+            else list[bl + __popc(ml & lt)] = e;
+        }
     }
     __syncthreads();
     return cnt[0];
@@ -526,25 +564,57 @@ __device__ __forceinline__ int direct_partition(const ProbParams& P, const Direc
 
 // One CTA per direct block (area <= min_size): entries in parallel after the
 // branch split, row sums in shared memory, then one atomic add per row.
-// lowp (eps >= 1e-6): the local and Hankel branches evaluate in FP32.
+// mode 0: double-float entries, FP64 row sums.  mode 1 (eps >= 1e-6): FP32
+// entries, FP64 row sums.  mode 2: FP32 entries whose products with the FP32
+// parts of c accumulate in FP32 atomics, each row spread over S = kDirSlots
+// slots (fewer when S rows > kDirSlotFloats) by list position, the slots of a
+// row then added in FP64 (direct_sum_mode picks it when its rounding bound
+// fits the tolerance).
+constexpr int kDirSlots = 32;
+constexpr int kDirSlotFloats = 4096;
+
 __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
                          const double* __restrict__ r_s, const double* __restrict__ w_s,
-                         const double* __restrict__ c_s, double* __restrict__ g_s, int lowp)
+                         const float2* __restrict__ r2, const float2* __restrict__ w2,
+                         const double* __restrict__ c_s, const float2* __restrict__ c2, double* __restrict__ g_s,
+                         int mode)
 {
-    extern __shared__ double rowacc[];
+    extern __shared__ double rowacc[];   // [rows] FP64 row sums, or [rows][S] FP32 slots (mode 2)
     __shared__ int cnt[2];
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
     const int area = rows * cols;
-    int* list = (int*)(rowacc + rows);
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) rowacc[i] = 0.0;
-    const int nloc = direct_partition(P, B, cols, area, r_s, w_s, list, cnt);
+    int S = kDirSlots;
+    while (S > 1 && S * rows > kDirSlotFloats) S >>= 1;
+    float* rowf = (float*)rowacc;
+    int* list = (int*)(rowacc + (mode == 2 ? kDirSlotFloats / 2 : rows));
+    if (mode == 2) {
+        for (int i = threadIdx.x; i < S * rows; i += blockDim.x) rowf[i] = 0.f;
+    } else {
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) rowacc[i] = 0.0;
+    }
+    const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt);
     const DirFx F = direct_frame(r_s, w_s, B);
+    if (mode == 2) {
+        for (int t = threadIdx.x; t < area; t += blockDim.x) {
+            const int e = list[t];
+            const int rr = e / cols, cc = e - rr * cols;
+            const float v = direct_entry_f32x(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc);
+            atomicAdd(&rowf[rr * S + (t & (S - 1))], v * c2[B.j0 + cc].x);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+            double sum = 0.0;
+            for (int k = 0; k < S; ++k) sum += (double)rowf[i * S + k];
+            atomicAdd(&g_s[B.k0 + i], (double)P.sgn * sum);
+        }
+        return;
+    }
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
-        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
+        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
         atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
     }
     __syncthreads();
@@ -686,6 +756,7 @@ k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restr
 // k_direct), one atomic add per column.
 __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
                              const double* __restrict__ r_s, const double* __restrict__ w_s,
+                             const float2* __restrict__ r2, const float2* __restrict__ w2,
                              const double* __restrict__ g_s, double* __restrict__ c_s, int lowp)
 {
     extern __shared__ double colacc[];
@@ -696,7 +767,7 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
     const int area = rows * cols;
     int* list = (int*)(colacc + cols);
     for (int i = threadIdx.x; i < cols; i += blockDim.x) colacc[i] = 0.0;
-    const int nloc = direct_partition(P, B, cols, area, r_s, w_s, list, cnt);
+    const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt);
     const DirFx F = direct_frame(r_s, w_s, B);
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
@@ -748,14 +819,14 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
 }
 
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
-                              int max_area, int lowp, const double* r_s, const double* w_s, const double* g_s,
-                              double* c_s, cudaStream_t s)
+                              int max_area, int lowp, const double* r_s, const double* w_s, const float2* r2,
+                              const float2* w2, const double* g_s, double* c_s, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
     size_t smem = sizeof(double) * (size_t)(max_cols > 0 ? max_cols : 1) + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, g_s, c_s, lowp);
+    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, g_s, c_s, lowp);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -809,15 +880,33 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
     return cudaGetLastError();
 }
 
+// The direct kernel's mode for tolerance eps and the tallest and widest direct
+// blocks.  In mode 2 a slot's chain of FP32 additions holds at most
+// 3 cols / 32 + 4 terms when S = 32 (a row's entries fill at most cols / 32 + 2
+// warp chunks of the lists, each adding at most one entry to a slot per list),
+// and at most cols <= 127 terms when a block has more than 128 rows (S < 32):
+// the rounding of one output's direct sums is below that count times
+// 2^-24 sum |J c| (a row's direct blocks have disjoint columns), and mode 2 is
+// used when that is at most 2 eps ||c||_1, a fifth of the tolerance.
+int direct_sum_mode(double eps, int max_rows, int max_cols)
+{
+    if (eps < 1e-6) return 0;
+    const int c = max_cols > 0 ? max_cols : 1;
+    double chain = 3.0 * c / kDirSlots + 4.0;
+    if (max_rows > kDirSlotFloats / kDirSlots) chain = std::max(chain, (double)std::min(c, 127));
+    return chain * 5.9604644775390625e-08 <= 2.0 * eps ? 2 : 1;
+}
+
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
-                          int max_area, int lowp, const double* r_s, const double* w_s, const double* c_s,
-                          double* g_s, cudaStream_t s)
+                          int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
+                          const float2* w2, const double* c_s, const float2* c2, double* g_s, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)(max_rows > 0 ? max_rows : 1) + sizeof(int) * (size_t)max_area;
+    const size_t acc = mode == 2 ? (size_t)kDirSlotFloats / 2 : (size_t)(max_rows > 0 ? max_rows : 1);
+    size_t smem = sizeof(double) * acc + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, c_s, g_s, lowp);
+    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, mode);
     count_launches(1);
     return cudaGetLastError();
 }

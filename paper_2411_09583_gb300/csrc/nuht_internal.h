@@ -224,9 +224,12 @@ int local_eval_threads(int ntop_max);
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                               int ntiles, int ntop_max, int threads, const float2* w2,
                               const double* mom, double* g_s, cudaStream_t s);
+// Mode of the direct kernel (0 double-float; 1 FP32 entries, FP64 sums; 2 FP32
+// entries and sums) for tolerance eps and the tallest and widest direct blocks.
+int direct_sum_mode(double eps, int max_rows, int max_cols);
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
-                          int max_area, int lowp, const double* r_s, const double* w_s, const double* c_s,
-                          double* g_s, cudaStream_t s);
+                          int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
+                          const float2* w2, const double* c_s, const float2* c2, double* g_s, cudaStream_t s);
 int local_adj_threads(int ntop_max);
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                      int ntiles, int ntop_max, int threads, const float2* w2,
@@ -235,8 +238,8 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
                                   int ntiles, int lmax, const float2* r2, const double* mom, double* c_s,
                                   cudaStream_t s);
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
-                              int max_area, int lowp, const double* r_s, const double* w_s, const double* g_s,
-                              double* c_s, cudaStream_t s);
+                              int max_area, int lowp, const double* r_s, const double* w_s, const float2* r2,
+                              const float2* w2, const double* g_s, double* c_s, cudaStream_t s);
 // x[i] as double-float (hi, lo)
 cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream_t s);
 // Per spreading tile, the path of k_asy_spread (plan time; modes[ntiles]).

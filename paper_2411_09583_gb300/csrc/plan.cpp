@@ -995,7 +995,8 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area,
-                              P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_cs, P->d_gs, ls));
+                              direct_sum_mode(P->eps, P->max_dir_rows, P->max_dir_cols), P->d_r, P->d_w, P->d_r2, P->d_w2,
+                              P->d_cs, P->d_cs2, P->d_gs, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
@@ -1082,7 +1083,8 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->max_dir_area,
-                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_gs, P->d_cs, ls));
+                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_r2, P->d_w2, P->d_gs, P->d_cs,
+                                  ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
