@@ -39,18 +39,6 @@ namespace {
 constexpr int kWinCells = 64;   // grid cells an interpolation tile stages in shared memory
 constexpr int kInterpTileThreads = 128;   // frequencies per interpolation tile (host: kInterpTile)
 
-// psi^(xi) in double-float from the split table (compensated Horner); xi >= 0.
-__device__ __forceinline__ df psihat_df(const Tables& T, double xi)
-{
-    xi = fabs(xi);
-    const double t = xi * T.ph_scale;
-    int piece = (int)t;
-    if (piece > T.ph_pieces - 1) piece = T.ph_pieces - 1;
-    const double v = 2.0 * (t - (double)piece) - 1.0;
-    const float vh = (float)v, vl = (float)(v - (double)vh);
-    return horner_comp(T.ph2 + piece * (T.ph_deg + 1), T.ph_deg, vh, vl);
-}
-
 // ------------------------------------------------------------------ spread
 // A point r_j of a block covers the w grid cells l0 + i, i < w, with
 // l0 = ceil((r_j - r_c)/h - w/2), and tap i of the ES kernel is the
@@ -132,13 +120,12 @@ __device__ __forceinline__ int interp_cell_sv(const AsyBlock& B, int w, double w
     return (int)t0;
 }
 
-// psi^(xi) for xi = alpha s (s from the fixed-point offset S), double-float
-// throughout: the piece and its coordinate as in psihat_df.
-__device__ __forceinline__ df psihat_fx(const Tables& T, const AsyBlock& B, long long S)
+// psi^(xi) for xi >= 0 given as double-float, double-float throughout: with
+// t = xi times the table's pieces per unit, piece floor(t) (clamped to the
+// table) and v = 2 (t - piece) - 1 in [-1, 1], the compensated Horner sum of
+// that piece's polynomial.
+__device__ __forceinline__ df psihat_of(const Tables& T, df xi)
 {
-    const float sc = ldexpf(1.f, -B.fw);
-    const df s = df_from_i64(S < 0 ? -S : S);
-    const df xi = df_mul(df{B.alpha_h, B.alpha_l}, df{s.h * sc, s.l * sc});
     const df t = df_mul(xi, df{T.ph_scale2.x, T.ph_scale2.y});
     int piece = (int)t.h;
     if ((float)piece == t.h && t.l < 0.f && piece > 0) --piece;
@@ -146,6 +133,14 @@ __device__ __forceinline__ df psihat_fx(const Tables& T, const AsyBlock& B, long
     const df u = df_add(t, df{-(float)piece, 0.f});
     const df v = df_add(df{2.f * u.h, 2.f * u.l}, df{-1.f, 0.f});
     return horner_comp(T.ph2 + piece * (T.ph_deg + 1), T.ph_deg, v.h, v.l);
+}
+
+// psi^(xi) for xi = alpha s (s from the fixed-point offset S).
+__device__ __forceinline__ df psihat_fx(const Tables& T, const AsyBlock& B, long long S)
+{
+    const float sc = ldexpf(1.f, -B.fw);
+    const df s = df_from_i64(S < 0 ? -S : S);
+    return psihat_of(T, df_mul(df{B.alpha_h, B.alpha_l}, df{s.h * sc, s.l * sc}));
 }
 
 constexpr int kSpreadSub = 8;       // point sub-ranges per moment, combined by shuffles
@@ -922,16 +917,50 @@ __device__ __forceinline__ void cdf_butterfly(float4& u, float4& v, float4 w)
     v = cdf(df_add(ur, df_negate(vr)), df_add(ui, df_negate(vi)));
 }
 
+// The same on the FP32 parts (x, z) alone (mixed-precision FFTs): the low
+// parts of the results are zero.
+__device__ __forceinline__ float4 cf_mul(float4 a, float4 b)
+{
+    return make_float4(a.x * b.x - a.z * b.z, 0.f, a.x * b.z + a.z * b.x, 0.f);
+}
+
+__device__ __forceinline__ void cf_butterfly(float4& u, float4& v, float4 w)
+{
+    const float4 vw = cf_mul(v, w);
+    const float ur = u.x, ui = u.z;
+    u = make_float4(ur + vw.x, 0.f, ui + vw.z, 0.f);
+    v = make_float4(ur - vw.x, 0.f, ui - vw.z, 0.f);
+}
+
+// A finite double as double-float from its bits (integer and FP32
+// instructions only; FP64 runs at 1/64 of the FP32 rate): the top 24 bits of
+// the significand exactly, the next 29 rounded; zero and subnormals give 0.
+__device__ __forceinline__ df df_from_bits(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return df{0.f, 0.f};
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);   // x = +-m 2^(e - 1075)
+    float h = ldexpf((float)(int)(m >> 29), e - 1075 + 29);
+    float l = ldexpf((float)(int)(m & 0x1FFFFFFF), e - 1075);
+    if (b < 0) {
+        h = -h;
+        l = -l;
+    }
+    return fast_two_sum(h, l);
+}
+
 // FP64 complex as double-float
 __device__ __forceinline__ float4 cdf_from(double2 v)
 {
-    const df re = df_from(v.x), im = df_from(v.y);
-    return cdf(re, im);
+    return cdf(df_from_bits(v.x), df_from_bits(v.y));
 }
 
 // nlines independent FFTs (e^{+2 pi i k n / N}) of N = 2^logN points stored
 // one after the other in shared memory, each in bit-reversed order, sharing
 // every butterfly stage.  tw2[k] = e^{2 pi i k / 2^tw_log2} as double-float.
+// LOWP: the butterflies in FP32 on the values' FP32 parts (mixed precision).
+template <bool LOWP>
 __device__ void smem_fft_lines(float4* X, int logN, int nlines, const float4* __restrict__ tw2, int tw_log2)
 {
     const int N = 1 << logN, half = N >> 1;
@@ -945,7 +974,8 @@ __device__ void smem_fft_lines(float4* X, int logN, int nlines, const float4* __
             const int i0 = line * N + ((bb >> st) << (st + 1)) + pos;
             const int i1 = i0 + len;
             float4 u = X[i0], v = X[i1];
-            cdf_butterfly(u, v, tw2[pos << tw_shift]);
+            if (LOWP) cf_butterfly(u, v, tw2[pos << tw_shift]);
+            else cdf_butterfly(u, v, tw2[pos << tw_shift]);
             X[i0] = u;
             X[i1] = v;
         }
@@ -1000,10 +1030,12 @@ __host__ __device__ __forceinline__ FourStep four_step(int LN)
     return f;
 }
 
-// 1 / psi^(alpha2 l): the correction of mode l of the inner FFT.
+// 1 / psi^(alpha2 l): the correction of mode l of the inner FFT, in
+// double-float (|l| <= N1 < 2^24 is exact in FP32).
 __device__ __forceinline__ df mode_correction(const AsyBlock& B, const Tables& tab, int l)
 {
-    return df_recip(psihat_df(tab, B.alpha2 * (double)l));
+    const df a2 = df_from_bits(B.alpha2);
+    return df_recip(psihat_of(tab, df_mul(a2, df{(float)(l < 0 ? -l : l), 0.f})));
 }
 
 // FFT input / output of the forward (ADJ = false) and the transposed
@@ -1035,7 +1067,7 @@ __device__ __forceinline__ void fft_out(const AsyBlock& B, const Tables& tab, fl
     dst[B.b_off + (int64_t)(l + B.N1) * Q + q] = cdf_scale(v, mode_correction(B, tab, l));
 }
 
-template <bool ADJ>
+template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
                                 const double2* __restrict__ src, float4* __restrict__ dst)
@@ -1049,14 +1081,14 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x)
         Xs[__brev(tt) >> (32 - logN)] = fft_in<ADJ>(B, tab, src, Q, q, tt);
     __syncthreads();
-    smem_fft_lines(Xs, logN, 1, tab.tw2, tab.tw_log2);
+    smem_fft_lines<LOWP>(Xs, logN, 1, tab.tw2, tab.tw_log2);
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, q, tt, Xs[tt]);
 }
 
 // All Q grids of one small block (nf2 * Q <= kFftSmemMax) in one CTA: the
 // deconvolution factor of each mode is computed once and used for every q;
 // the Q transforms share every butterfly stage.
-template <bool ADJ>
+template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
                                 const double2* __restrict__ src, float4* __restrict__ dst)
@@ -1081,7 +1113,7 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
         }
     }
     __syncthreads();
-    smem_fft_lines(Xs, logN, Q, tab.tw2, tab.tw_log2);
+    smem_fft_lines<LOWP>(Xs, logN, Q, tab.tw2, tab.tw_log2);
     if (!ADJ) {
         float4* gq = dst + B.q_off;
         for (int idx = threadIdx.x; idx < N * Q; idx += blockDim.x) {
@@ -1104,7 +1136,7 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
 // stored at tmp[n1 + N1 k2].  Pass B: for each k2, FFT over n1 of
 // tmp[n1 + N1 k2], which is X[k2 + N2 k1].  Work item ordinal = q * groups + g,
 // g a group of lines handled by one CTA.
-template <bool ADJ>
+template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
                                  const double2* __restrict__ src, float4* __restrict__ tmp)
@@ -1124,17 +1156,18 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
         Xs[li * f.N2 + (__brev(n2) >> (32 - f.logN2))] = fft_in<ADJ>(B, tab, src, Q, iq, (l0 + li) + f.N1 * n2);
     }
     __syncthreads();
-    smem_fft_lines(Xs, f.logN2, nl, tab.tw2, tab.tw_log2);
+    smem_fft_lines<LOWP>(Xs, f.logN2, nl, tab.tw2, tab.tw_log2);
     float4* tq = tmp + B.q_off;
     for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
         const int li = idx >> f.logN2, k2 = idx & (f.N2 - 1);
         const int n1 = l0 + li;
         const long long m = ((long long)n1 * k2) & (N - 1);   // e^{2 pi i n1 k2 / N}
-        tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = cdf_mul(Xs[idx], cdf_twiddle(tab, B.log2nf2, m));
+        const float4 tw = cdf_twiddle(tab, B.log2nf2, m);
+        tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = LOWP ? cf_mul(Xs[idx], tw) : cdf_mul(Xs[idx], tw);
     }
 }
 
-template <bool ADJ>
+template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
                                  const float4* __restrict__ tmp, float4* __restrict__ dst)
@@ -1155,7 +1188,7 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
             tq[(int64_t)(n1 + f.N1 * (k20 + li)) * Q + iq];
     }
     __syncthreads();
-    smem_fft_lines(Xs, f.logN1, nl, tab.tw2, tab.tw_log2);
+    smem_fft_lines<LOWP>(Xs, f.logN1, nl, tab.tw2, tab.tw_log2);
     for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
         const int li = idx >> f.logN1, k1 = idx & (f.N1 - 1);
         fft_out<ADJ>(B, tab, dst, Q, iq, (k20 + li) + f.N2 * k1, Xs[idx]);
@@ -2145,11 +2178,12 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
 
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* src,
-                                 float4* dst, cudaStream_t s, bool adj)
+                                 float4* dst, cudaStream_t s, bool adj, bool lowp)
 {
     if (nitems <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)max_nf2;
-    auto kern = adj ? k_asy_fft_small<true> : k_asy_fft_small<false>;
+    auto kern = adj ? (lowp ? k_asy_fft_small<true, true> : k_asy_fft_small<true, false>)
+                    : (lowp ? k_asy_fft_small<false, true> : k_asy_fft_small<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nt = max_nf2 / 2;
@@ -2161,15 +2195,22 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
 }
 
 cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
-                                 int nitems, Tables tab, const double2* src, float4* dst,
-                                 cudaStream_t s, bool adj)
+                                 int nitems, int max_pts, Tables tab, const double2* src, float4* dst,
+                                 cudaStream_t s, bool adj, bool lowp)
 {
     if (nitems <= 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * (size_t)kFftSmemMax;
-    auto kern = adj ? k_asy_fft_block<true> : k_asy_fft_block<false>;
+    if (max_pts < 1 || max_pts > kFftSmemMax) max_pts = kFftSmemMax;
+    // shared memory for the largest block of the list only, and about two
+    // points per thread (small blocks leave room for more CTAs per SM)
+    size_t smem = sizeof(float4) * (size_t)max_pts;
+    int nt = ((max_pts / 2 + 31) / 32) * 32;
+    if (nt > 256) nt = 256;
+    if (nt < 32) nt = 32;
+    auto kern = adj ? (lowp ? k_asy_fft_block<true, true> : k_asy_fft_block<true, false>)
+                    : (lowp ? k_asy_fft_block<false, true> : k_asy_fft_block<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<nitems, 256, smem, s>>>(probs, blks, items, tab, src, dst);
+    kern<<<nitems, nt, smem, s>>>(probs, blks, items, tab, src, dst);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -2177,12 +2218,14 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
                                  const double2* src, float4* tmp, float4* dst,
-                                 cudaStream_t s, bool adj)
+                                 cudaStream_t s, bool adj, bool lowp)
 {
     if (nitems_a <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)kFftLineBatch;
-    auto ka = adj ? k_asy_fft_pass_a<true> : k_asy_fft_pass_a<false>;
-    auto kb = adj ? k_asy_fft_pass_b<true> : k_asy_fft_pass_b<false>;
+    auto ka = adj ? (lowp ? k_asy_fft_pass_a<true, true> : k_asy_fft_pass_a<true, false>)
+                  : (lowp ? k_asy_fft_pass_a<false, true> : k_asy_fft_pass_a<false, false>);
+    auto kb = adj ? (lowp ? k_asy_fft_pass_b<true, true> : k_asy_fft_pass_b<true, false>)
+                  : (lowp ? k_asy_fft_pass_b<false, true> : k_asy_fft_pass_b<false, false>);
     cudaError_t e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -160,6 +160,7 @@ __global__ void k_block_sizes(BlockBuild bb)
                 bb.fcls[a] = 0;
                 c[AC_NFK] = 1;
                 c[AC_IFK] = 1;
+                atomic_max64(&bb.maxv[MX_FBLOCK_PTS], (int64_t)ab.nf2 * Q);
             } else if (ab.nf2 <= kFftSingleMax) {                 // one CTA per grid
                 bb.fcls[a] = 1;
                 c[AC_NFS] = 1;

@@ -126,7 +126,7 @@ enum { AC_GB, AC_GQ, AC_TSPREAD, AC_TINTERP, AC_NFK, AC_NFS, AC_NFL, AC_IFK, AC_
 enum { DC_ENTRIES, kDirCols };
 enum { TOT_LOCAL = 0, TOT_ASY = kLocalCols, TOT_DIR = kLocalCols + kAsyCols,
        kTotals = kLocalCols + kAsyCols + kDirCols };
-enum { MX_DIR_ROWS, MX_DIR_COLS, MX_DIR_AREA, MX_NF2_SMALL, MX_LARGE, MX_ERR, kMaxv };
+enum { MX_DIR_ROWS, MX_DIR_COLS, MX_DIR_AREA, MX_NF2_SMALL, MX_LARGE, MX_ERR, MX_FBLOCK_PTS, kMaxv };
 enum { LIST_MOM, LIST_EVAL, LIST_SPREAD, LIST_INTERP, LIST_FSMALL, LIST_FA, LIST_FB, LIST_FBLOCK, kLists };
 
 struct BlockBuild {
@@ -261,16 +261,18 @@ cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks,
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
                                   const float4* grid_q, double* g_s, cudaStream_t s);
+// lowp: FP32 butterflies on the FP32 parts of the values (mixed precision).
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* src,
-                                 float4* dst, cudaStream_t s, bool adj = false);
+                                 float4* dst, cudaStream_t s, bool adj = false, bool lowp = false);
+// max_pts: the largest nf2 * Q among the blocks of the list (sizes the CTA).
 cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
-                                 int nitems, Tables tab, const double2* src, float4* dst,
-                                 cudaStream_t s, bool adj = false);
+                                 int nitems, int max_pts, Tables tab, const double2* src, float4* dst,
+                                 cudaStream_t s, bool adj = false, bool lowp = false);
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
                                  const double2* src, float4* tmp, float4* dst,
-                                 cudaStream_t s, bool adj = false);
+                                 cudaStream_t s, bool adj = false, bool lowp = false);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
                               const float4* grid_q, double* g_s, cudaStream_t s);

@@ -107,6 +107,7 @@ struct nuht_plan_s {
     int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fblock = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
     int n_dir = 0;
     int64_t mom_len = 0, gb_len = 0, gq_len = 0;
+    int max_fblock_pts = 0;   // largest nf2 * Q among the blocks FFT'd whole by one CTA
     int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, max_dir_area = 0, ntop_max = 0, eval_threads = 0;
     int spread_threads = 256;
     bool has_large_fft = false;
@@ -652,6 +653,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->max_dir_rows = (int)hmax[MX_DIR_ROWS]; P->max_dir_cols = (int)hmax[MX_DIR_COLS];
     P->max_dir_area = (int)hmax[MX_DIR_AREA];
     P->max_nf2_small = (int)hmax[MX_NF2_SMALL];
+    P->max_fblock_pts = (int)hmax[MX_FBLOCK_PTS];
     P->has_large_fft = hmax[MX_LARGE] != 0;
     const int64_t nseg[kLists] = {nl, nl, na, na, ta_[AC_NFS], ta_[AC_NFL], ta_[AC_NFL], ta_[AC_NFK]};
     const int64_t ntile[kLists] = {tl[LC_TMOM], tl[LC_TEVAL], ta_[AC_TSPREAD], ta_[AC_TINTERP],
@@ -1010,13 +1012,14 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                       P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
-        NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_gb,
-                                     P->d_gq, as));
+        const bool lowp = P->opt.precision == NUHT_PREC_MIXED;   // FP32 butterflies
+        NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->max_fblock_pts, P->tab,
+                                     P->d_gb, P->d_gq, as, false, lowp));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small,
-                                     P->tab, P->d_gb, P->d_gq, as));
+                                     P->tab, P->d_gb, P->d_gq, as, false, lowp));
         if (P->has_large_fft)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
-                                         P->d_gb, P->d_gtmp, P->d_gq, as));
+                                         P->d_gb, P->d_gtmp, P->d_gq, as, false, lowp));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
         if (P->opt.precision == NUHT_PREC_MIXED)
@@ -1094,8 +1097,8 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                       P->d_gs, P->d_tg, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
-        NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->tab, P->d_tg, P->d_bq,
-                                     as, true));
+        NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->max_fblock_pts, P->tab,
+                                     P->d_tg, P->d_bq, as, true));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small, P->tab,
                                      P->d_tg, P->d_bq, as, true));
         if (P->has_large_fft)
