@@ -54,9 +54,10 @@ extern "C" {
 
 /* --------------------------------------------------------------- options */
 #define NUHT_PREC_FP64  0   /* every stage in FP64 (or FP64-accurate arithmetic) */
-#define NUHT_PREC_MIXED 1   /* FP32 spreading / interpolation (FP32 accumulation), FP64 phase
-                               reduction, FFT, moments and local / direct blocks; needs
-                               eps >= 1e-6 (else NUHT_ERR_UNSUPPORTED) */
+#define NUHT_PREC_MIXED 1   /* FP32 spreading / interpolation (FP32 accumulation), FFT
+                               butterflies, local evaluation and direct entries; fixed-point /
+                               double-float positions, phase reduction, Hankel coefficients and
+                               moments; needs eps >= 1e-6 (else NUHT_ERR_UNSUPPORTED) */
 
 /* Block classes (Sec. 4.1). */
 #define NUHT_BLOCK_LOCAL  0

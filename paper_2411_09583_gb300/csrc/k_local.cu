@@ -282,6 +282,70 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
     atomicAdd(&g_s[k], (double)P.sgn * val);
 }
 
+// Mixed precision (eps >= 1e-6): k_local_eval in FP32.  J_0..J_ntop(y) by
+// Miller's recurrence in FP32 (rescaled by 2^-60 when a value passes 2^60,
+// the stored ones with it), normalised by S = J_0 + 2 sum_k J_2k, then
+// sum_l C_l mu_l with FP32 products.  The recurrence and the products round
+// at ~1e-6 relative, and |C_l| <= 2 with sum over a row's local blocks of
+// |mu_l| <= ||c||_1 (disjoint columns): a few 1e-6 ||c||_1, inside
+// 10 eps ||c||_1.  y below 1e-7 keeps J_n = delta_n0 (J_1(y) < 5e-8); above
+// it two steps grow a value by at most (2 ns / y)^2 < 2^60, so with the rescale
+// at 2^60 nothing passes 2^121.
+__global__ void k_local_eval_f32(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                                 const Tile* __restrict__ tiles, const float2* __restrict__ w2,
+                                 const double* __restrict__ mom, double* __restrict__ g_s)
+{
+    extern __shared__ float smf[];
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int nu = P.nu, L = P.L;
+    float* mu = smf;                   // [L + 1]
+    float* jb = smf + (P.ntop + 1);    // [ntop + 1][nt]
+    for (int l = tid; l <= L; l += nt) mu[l] = (float)mom[B.mom_off + l];
+    __syncthreads();
+    if (tid >= t.count) return;
+    const int64_t k = t.start + tid;
+    const float y = w2[k].x * (0.5f * B.R_h);   // omega R / 2
+    const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;
+    const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;
+    const int ntop = hp + L;
+    float val = 0.f;
+    if (!(y >= 1e-7f)) {
+        if (nu == 0) val = mu[0];
+    } else {
+        const int ns = miller_start(ntop, (double)y);
+        const float inv2y = 2.f / y;
+        float jp1 = 0.f, jc = 1.f, S = 2.f;
+        if (ns <= ntop) jb[ns * nt + tid] = jc;
+        for (int i = ns; i >= 2; i -= 2) {
+            const float jm = fmaf((float)i * inv2y, jc, -jp1);
+            const float jmm = fmaf((float)(i - 1) * inv2y, jm, -jc);
+            if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = jm;
+            if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = jmm;
+            S = fmaf(2.f, jmm, S);
+            jp1 = jm;
+            jc = jmm;
+            if (fabsf(jc) > 1.152921504606847e18f) {
+                const float sc = 8.673617379884035e-19f;   // 2^-60
+                jc *= sc; jp1 *= sc; S *= sc;
+                for (int q = i - 2; q <= ntop; ++q) jb[q * nt + tid] *= sc;
+            }
+        }
+        const float iS = 1.f / (S - jc);   // J_0 was added with weight 2; it counts once
+        for (int l = 0; l <= L; ++l) {
+            const int b = hm - l;
+            const float va = jb[(hp + l) * nt + tid] * iS;
+            const float vb = jb[(b >= 0 ? b : -b) * nt + tid] * iS;
+            float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
+            if (l > 0 || (nu & 1)) sgn *= 2.f;
+            val = fmaf(va * vb * sgn, mu[l], val);
+        }
+    }
+    atomicAdd(&g_s[k], (double)(P.sgn < 0 ? -val : val));
+}
+
 // J_n(x) for 1 <= x by Miller's recurrence in double-float (no storage).
 __device__ __forceinline__ double jn_miller_df(int n, double x)
 {
@@ -895,6 +959,20 @@ int direct_sum_mode(double eps, int max_rows, int max_cols)
     double chain = 3.0 * c / kDirSlots + 4.0;
     if (max_rows > kDirSlotFloats / kDirSlots) chain = std::max(chain, (double)std::min(c, 127));
     return chain * 5.9604644775390625e-08 <= 2.0 * eps ? 2 : 1;
+}
+
+cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                  int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
+                                  double* g_s, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    size_t smem = sizeof(float) * ((size_t)(ntop_max + 1) * threads + (size_t)(ntop_max + 1));
+    cudaError_t e = cudaFuncSetAttribute(k_local_eval_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_eval_f32<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,

@@ -221,6 +221,10 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
                                  double* mom, cudaStream_t s);
 int local_moment_threads(int lmax);
 int local_eval_threads(int ntop_max);
+// Mixed precision: k_local_eval with the recurrence and the sum in FP32.
+cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                  int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
+                                  double* g_s, cudaStream_t s);
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                               int ntiles, int ntop_max, int threads, const float2* w2,
                               const double* mom, double* g_s, cudaStream_t s);

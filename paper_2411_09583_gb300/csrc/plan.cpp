@@ -990,8 +990,12 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
                                      P->d_cs2, P->d_mom, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
-        NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                  P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
+        if (P->opt.precision == NUHT_PREC_MIXED)
+            NUHT_CK(launch_local_eval_f32(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
+                                          P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
+        else
+            NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
+                                      P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
