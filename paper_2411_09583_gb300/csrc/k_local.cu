@@ -633,7 +633,9 @@ __device__ __forceinline__ int direct_partition(const ProbParams& P, const Direc
 // parts of c accumulate in FP32 atomics, each row spread over S = kDirSlots
 // slots (fewer when S rows > kDirSlotFloats) by list position, the slots of a
 // row then added in FP64 (direct_sum_mode picks it when its rounding bound
-// fits the tolerance).
+// fits the tolerance).  With g_sb set, every entry is also applied to a second
+// coefficient vector (c_sb, c2b) into g_sb: the entries are evaluated once for
+// both (the two real components of complex c, or two vectors).
 constexpr int kDirSlots = 32;
 constexpr int kDirSlotFloats = 4096;
 
@@ -641,22 +643,34 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
                          const double* __restrict__ r_s, const double* __restrict__ w_s,
                          const float2* __restrict__ r2, const float2* __restrict__ w2,
                          const double* __restrict__ c_s, const float2* __restrict__ c2, double* __restrict__ g_s,
+                         const double* __restrict__ c_sb, const float2* __restrict__ c2b, double* __restrict__ g_sb,
                          int mode)
 {
-    extern __shared__ double rowacc[];   // [rows] FP64 row sums, or [rows][S] FP32 slots (mode 2)
+    // per vector: [rows] FP64 row sums, or [rows][S] FP32 slots (mode 2)
+    extern __shared__ double rowacc[];
     __shared__ int cnt[2];
+    const bool two = g_sb != nullptr;
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
     const int area = rows * cols;
     int S = kDirSlots;
     while (S > 1 && S * rows > kDirSlotFloats) S >>= 1;
+    const int accd = mode == 2 ? kDirSlotFloats / 2 : rows;   // doubles per vector
+    double* rowaccb = rowacc + accd;
     float* rowf = (float*)rowacc;
-    int* list = (int*)(rowacc + (mode == 2 ? kDirSlotFloats / 2 : rows));
+    float* rowfb = (float*)rowaccb;
+    int* list = (int*)(rowacc + (two ? 2 : 1) * accd);
     if (mode == 2) {
-        for (int i = threadIdx.x; i < S * rows; i += blockDim.x) rowf[i] = 0.f;
+        for (int i = threadIdx.x; i < S * rows; i += blockDim.x) {
+            rowf[i] = 0.f;
+            if (two) rowfb[i] = 0.f;
+        }
     } else {
-        for (int i = threadIdx.x; i < rows; i += blockDim.x) rowacc[i] = 0.0;
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+            rowacc[i] = 0.0;
+            if (two) rowaccb[i] = 0.0;
+        }
     }
     const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt);
     const DirFx F = direct_frame(r_s, w_s, B);
@@ -665,13 +679,19 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
             const int e = list[t];
             const int rr = e / cols, cc = e - rr * cols;
             const float v = direct_entry_f32x(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc);
-            atomicAdd(&rowf[rr * S + (t & (S - 1))], v * c2[B.j0 + cc].x);
+            const int slot = rr * S + (t & (S - 1));
+            atomicAdd(&rowf[slot], v * c2[B.j0 + cc].x);
+            if (two) atomicAdd(&rowfb[slot], v * c2b[B.j0 + cc].x);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-            double sum = 0.0;
-            for (int k = 0; k < S; ++k) sum += (double)rowf[i * S + k];
+            double sum = 0.0, sumb = 0.0;
+            for (int k = 0; k < S; ++k) {
+                sum += (double)rowf[i * S + k];
+                if (two) sumb += (double)rowfb[i * S + k];
+            }
             atomicAdd(&g_s[B.k0 + i], (double)P.sgn * sum);
+            if (two) atomicAdd(&g_sb[B.k0 + i], (double)P.sgn * sumb);
         }
         return;
     }
@@ -680,10 +700,13 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         const int rr = e / cols, cc = e - rr * cols;
         const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
         atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
+        if (two) atomicAdd(&rowaccb[rr], v * c_sb[B.j0 + cc]);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < rows; i += blockDim.x)
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
         atomicAdd(&g_s[B.k0 + i], (double)P.sgn * rowacc[i]);
+        if (two) atomicAdd(&g_sb[B.k0 + i], (double)P.sgn * rowaccb[i]);
+    }
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -977,14 +1000,16 @@ cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blk
 
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
-                          const float2* w2, const double* c_s, const float2* c2, double* g_s, cudaStream_t s)
+                          const float2* w2, const double* c_s, const float2* c2, double* g_s,
+                          const double* c_sb, const float2* c2b, double* g_sb, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
-    const size_t acc = mode == 2 ? (size_t)kDirSlotFloats / 2 : (size_t)(max_rows > 0 ? max_rows : 1);
+    const size_t acc = (g_sb ? 2 : 1) *
+                       (mode == 2 ? (size_t)kDirSlotFloats / 2 : (size_t)(max_rows > 0 ? max_rows : 1));
     size_t smem = sizeof(double) * acc + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, mode);
+    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, c_sb, c2b, g_sb, mode);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -233,7 +233,8 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
 int direct_sum_mode(double eps, int max_rows, int max_cols);
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
-                          const float2* w2, const double* c_s, const float2* c2, double* g_s, cudaStream_t s);
+                          const float2* w2, const double* c_s, const float2* c2, double* g_s,
+                          const double* c_sb, const float2* c2b, double* g_sb, cudaStream_t s);
 int local_adj_threads(int ntop_max);
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                      int ntiles, int ntop_max, int threads, const float2* w2,

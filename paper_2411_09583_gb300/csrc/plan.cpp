@@ -100,6 +100,10 @@ struct nuht_plan_s {
     float4* d_bq = nullptr;   // adjoint: corrected modes, double-float parts
     double *d_cs = nullptr, *d_gs = nullptr;
     float2 *d_r2 = nullptr, *d_w2 = nullptr, *d_cs2 = nullptr;   // double-float copies
+    // the next real component of a pair (complex c, or two vectors), whose
+    // direct blocks are applied together with the first: its c and direct sums
+    double *d_csb = nullptr, *d_gsb = nullptr;
+    float2* d_cs2b = nullptr;
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
 
@@ -689,6 +693,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m), a_cs2 = A.reserve<float2>(n);
     size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
     size_t a_sm = A.reserve<int32_t>((size_t)ntile[LIST_SPREAD]);
+    size_t a_csb = A.reserve<double>(n), a_gsb = A.reserve<double>(m), a_cs2b = A.reserve<float2>(n);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
@@ -753,6 +758,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (float4*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
     P->d_r2 = (float2*)(D + a_r2); P->d_w2 = (float2*)(D + a_w2); P->d_cs2 = (float2*)(D + a_cs2);
+    P->d_csb = (double*)(D + a_csb); P->d_gsb = (double*)(D + a_gsb); P->d_cs2b = (float2*)(D + a_cs2b);
     NUHT_CK(launch_split_f64(P->d_r, n, P->d_r2, s));
     NUHT_CK(launch_split_f64(P->d_w, m, P->d_w2, s));
     P->d_tg = (double2*)(D + a_tg); P->d_bq = (float4*)(D + a_bq);
@@ -972,10 +978,13 @@ int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, 
 // accumulating into g in sorted order (FP64 atomics).  They run one after the
 // other on the caller's stream: each kernel fills the GPU, and running them
 // concurrently only makes them compete for shared memory.
-static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
+// pair: 0 this component's direct blocks; 1 also those of the next component
+// (d_csb, d_cs2b into d_gsb); 2 none (applied with the previous component).
+static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
 {
     const int mask = P->opt.class_mask;
-    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
+    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir && pair != 2;
+    const bool asy = (mask & 2) && P->n_asy;
     // The block classes share no scratch and only add into g (FP64 atomics):
     // the local and direct blocks run beside the asymptotic pipeline (ClassFork),
     // each stage's events on its own stream.  NUHT_TIMING_SERIAL keeps every
@@ -1001,8 +1010,9 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s)
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area,
-                              direct_sum_mode(P->eps, P->max_dir_rows, P->max_dir_cols), P->d_r, P->d_w, P->d_r2, P->d_w2,
-                              P->d_cs, P->d_cs2, P->d_gs, ls));
+                              direct_sum_mode(P->eps, P->max_dir_rows, P->max_dir_cols), P->d_r, P->d_w,
+                              P->d_r2, P->d_w2, P->d_cs, P->d_cs2, P->d_gs, pair == 1 ? P->d_csb : nullptr,
+                              pair == 1 ? P->d_cs2b : nullptr, pair == 1 ? P->d_gsb : nullptr, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
@@ -1050,13 +1060,25 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         return NUHT_OK;
     }
     NUHT_TRY(ensure_events(P, comps));
+    // real components in pairs share the direct blocks' Bessel evaluations:
+    // the first of a pair applies them to both, the second starts from the
+    // second's direct sums (d_gsb)
+    const bool pairs = (P->opt.class_mask & 4) && P->n_dir > 0;
     for (int comp = 0; comp < comps; ++comp) {
         StageTimer T{P, comp};
+        const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
-        NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * P->m, s));
+        if (pair == 2)
+            NUHT_CK(cudaMemcpyAsync(P->d_gs, P->d_gsb, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, s));
+        else
+            NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * P->m, s));
         NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, P->d_cs2, s));
+        if (pair == 1) {
+            NUHT_CK(cudaMemsetAsync(P->d_gsb, 0, sizeof(double) * P->m, s));
+            NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp + 1, P->d_csb, P->d_cs2b, s));
+        }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
-        NUHT_TRY(apply_forward(P, T, s));
+        NUHT_TRY(apply_forward(P, T, s, pair));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
         NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, g, s));
         NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));

@@ -331,6 +331,20 @@ def test_mixed_precision_small(nu):
         assert rel <= 10 * eps, (eps, rel)
 
 
+@pytest.mark.parametrize("cls", [0, 1, 2])
+@pytest.mark.parametrize("eps,min_size", [(1e-6, 1024), (1e-5, 4096)])
+def test_mixed_precision_each_class_alone(cls, eps, min_size):
+    # one block class at a time in mixed precision: FP32 local evaluation,
+    # FP32 direct entries and (where the rounding bound allows) FP32 row sums,
+    # FP32 spreading, FFT butterflies and interpolation
+    r, omega, c = loguniform_problem(3000, 2500, omega_max=4e4, seed=58, complex_c=False)
+    g, info, blocks = run_forward(1, r, omega, c, eps, precision="mixed", class_mask=1 << cls,
+                                  min_size=min_size)
+    assert len(blocks[cls]) > 0
+    ref = class_reference(1, r, omega, c, blocks[cls])
+    assert np.max(np.abs(g - ref)) <= tol(eps, c)
+
+
 def test_mixed_precision_rejects_tight_eps():
     from paper_2411_09583_gb300 import Plan
     from paper_2411_09583_gb300._native import NUHT_ERR_UNSUPPORTED, NuhtError
