@@ -1087,16 +1087,20 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
 
 // All Q grids of one small block (nf2 * Q <= kFftSmemMax) in one CTA: the
 // deconvolution factor of each mode is computed once and used for every q;
-// the Q transforms share every butterfly stage.
+// the Q transforms share every butterfly stage.  A launch takes the blocks
+// with pts_lo < nf2 * Q <= pts_hi (the others return at once), so that small
+// blocks run in CTAs sized for them.
 template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
-                                const double2* __restrict__ src, float4* __restrict__ dst)
+                                const double2* __restrict__ src, float4* __restrict__ dst, int pts_lo, int pts_hi)
 {
     extern __shared__ float4 Xs[];   // [Q][N], each grid bit-reversed
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
+    const int pts = B.nf2 * Q;
+    if (pts <= pts_lo || pts > pts_hi) return;
     const int N = B.nf2, logN = B.log2nf2, half = N >> 1;
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x) {
         const int l = (tt < half) ? tt : tt - N;
@@ -2200,19 +2204,31 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
 {
     if (nitems <= 0) return cudaSuccess;
     if (max_pts < 1 || max_pts > kFftSmemMax) max_pts = kFftSmemMax;
-    // shared memory for the largest block of the list only, and about two
-    // points per thread (small blocks leave room for more CTAs per SM)
-    size_t smem = sizeof(float4) * (size_t)max_pts;
-    int nt = ((max_pts / 2 + 31) / 32) * 32;
-    if (nt > 256) nt = 256;
-    if (nt < 32) nt = 32;
     auto kern = adj ? (lowp ? k_asy_fft_block<true, true> : k_asy_fft_block<true, false>)
                     : (lowp ? k_asy_fft_block<false, true> : k_asy_fft_block<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<nitems, nt, smem, s>>>(probs, blks, items, tab, src, dst);
-    count_launches(1);
-    return cudaGetLastError();
+    // blocks of up to kFftSmallPts points in small CTAs (16 KiB, many per SM),
+    // the larger ones in CTAs sized for the largest; each launch skips the
+    // other size class at once
+    constexpr int kFftSmallPts = 1024;
+    const int ranges[2][2] = {{0, max_pts < kFftSmallPts ? max_pts : kFftSmallPts}, {kFftSmallPts, max_pts}};
+    int launched = 0;
+    for (int r = 0; r < 2; ++r) {
+        const int lo = ranges[r][0], hi = ranges[r][1];
+        if (hi <= lo) continue;
+        const size_t smem = sizeof(float4) * (size_t)hi;
+        int nt = ((hi / 2 + 31) / 32) * 32;
+        if (r == 0 && nt > 128) nt = 128;
+        if (nt > 256) nt = 256;
+        if (nt < 32) nt = 32;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<nitems, nt, smem, s>>>(probs, blks, items, tab, src, dst, lo, hi);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ++launched;
+    }
+    count_launches(launched);
+    return cudaSuccess;
 }
 
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
