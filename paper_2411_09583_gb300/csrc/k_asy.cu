@@ -21,11 +21,15 @@
 // smoothing of the two spreading steps (Poisson summation); 4 / w^2 collects
 // the grid spacings h and 2 pi / nf2 against alpha and alpha2.
 //
-// Arithmetic: per-point set-up (coordinates, phases, weights' base) in FP64;
-// kernel taps, weighted values and all tap sums in double-float (df64.cuh,
-// ~48 bits, on the FP32 pipes); grids and the FFT in FP64.  The FFT output is
-// stored split into (hi, lo) floats so that the interpolation reads it as
-// double-float without FP64 work.
+// Arithmetic: a point's or frequency's grid cell, kernel coordinate and phase
+// come from 64-bit fixed-point products with per-block constants (integer
+// instructions); kernel taps, weighted values, the per-bin moments and sums
+// and the FFT run in double-float (df64.cuh, ~48 bits, on the FP32 pipes);
+// the spreading grids accumulate in FP64 atomics.  The FFT output is stored
+// split into (hi, lo) floats so that the interpolation reads it as
+// double-float without FP64 work.  Mixed precision (the _f32 kernels and the
+// LOWP FFT instances) keeps the fixed-point positions and phases and runs the
+// taps, sums and butterflies in FP32.
 #include <cstdint>
 
 #include "device_math.cuh"

@@ -10,13 +10,17 @@
 // theorem with both arguments x/2).
 //
 // Arithmetic: the Chebyshev recurrences, the Miller recurrence and the sums
-// run in double-float (df64.cuh, ~48 bits on the FP32 pipes); coordinates,
-// normalisation and the rare small-argument rows in FP64.
+// run in double-float (df64.cuh, ~48 bits on the FP32 pipes); the moments'
+// column sums end in one FP64 atomic per moment, and the rare small-argument
+// rows use the FP64 power series.  Mixed precision evaluates the local blocks
+// in FP32 (k_local_eval_f32; the moments stay double-float).
 //
 // Direct blocks are small mixed blocks summed entry by entry with a device
 // J_nu: Miller recurrence (or the power series) where omega r <= z, and the
 // M-term Hankel expansion, accurate to eps there by the choice of z, where
-// omega r > z.
+// omega r > z.  omega r is the exact 128-bit product of the block's
+// fixed-point omega and r; at eps >= 1e-6 the entries are FP32 values, summed
+// in FP32 slots where the rounding bound allows (direct_sum_mode).
 #include <algorithm>
 #include <cstdint>
 
