@@ -18,6 +18,7 @@ whole transform.
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -221,11 +222,19 @@ def _dominant_flops(stage, info, blocks, tab):
     return None, None
 
 
+def _code_only(text):
+    """C/CUDA source without comments and blank lines (comment edits keep a
+    capture valid; any code change invalidates it)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def source_hash(*names):
     h = hashlib.sha256()
     for nm in names:
-        with open(os.path.join(ROOT, "paper_2411_09583_gb300", "csrc", nm), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2411_09583_gb300", "csrc", nm), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
