@@ -118,6 +118,24 @@ def test_complex_and_multiple_vectors():
     assert np.max(np.abs(gz - refz)) <= 10 * 1e-9 * np.abs(cz).sum()
 
 
+@pytest.mark.parametrize("nvec", [1, 2])
+def test_host_buffer_entry_point(nvec):
+    # nuht_transform_host: host arrays in and out
+    from paper_2411_09583_gb300.nuht import transform_host
+    r, omega, c = uniform_problem(2000, 1800, omega_max=2500.0, seed=44, nvec=nvec)
+    eps = 1e-10
+    g = transform_host(0, r, omega, c, eps)
+    ref = oracle.direct(0, r, omega, c)
+    assert g.shape == ref.shape
+    assert np.all(np.max(np.abs(g - ref), axis=0) <= tol(eps, c))
+    # pinned output buffer, repeated calls
+    import torch
+    out = torch.empty(g.shape, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(2):
+        g2 = transform_host(0, r, omega, c, eps, out=out)
+        assert np.max(np.abs(g2 - g)) <= 1e-12 * np.abs(c).sum()
+
+
 def test_edge_cases():
     rng = np.random.default_rng(14)
     # empty sides
