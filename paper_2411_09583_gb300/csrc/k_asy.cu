@@ -1222,7 +1222,7 @@ __host__ __device__ __forceinline__ size_t interp_smem(int qmax, int w, int deg)
 // forms two degrees x (re, im) of one q, four independent sums over the w
 // cells.
 __device__ __forceinline__ void bin_sums_build(const float4* win, const float2* coef2, float2* H, int nbins,
-                                               int w, int nb, int dci, int Q, int qs)
+                                               int w, int nb, int dci, int Q, int qs, const int8_t* dcp)
 {
     const int Q2 = 2 * Q, hs = nb * Q2 + 2;
     const int npr = (nb + 1) >> 1;
@@ -1232,7 +1232,7 @@ __device__ __forceinline__ void bin_sums_build(const float4* win, const float2* 
         const int d0 = 2 * dp, d1 = d0 + 1;
         const bool has1 = d1 < nb;
         float2* h0 = H + b * hs + d0 * Q2 + 2 * q;
-        if (d0 < dci && q < qs) {
+        if (d0 < min(dci, (int)dcp[q >> 1]) && q < qs) {
             acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
 #pragma unroll 4
             for (int i = 0; i < w; ++i) {
@@ -1306,16 +1306,17 @@ __device__ __forceinline__ void cheb_basis_row(float2* u, float vh, float vl, in
 // (small Hankel terms).
 template <class F>
 __device__ __forceinline__ void bin_sums_eval(const float2* Hb, const float2* u, int nb, int dci, int Q, int qs,
-                                              F&& combine)
+                                              const int8_t* dcp, F&& combine)
 {
     const int Q2 = 2 * Q;
     for (int q = 0; q < Q; q += 2) {
         const float2* hq = Hb + 2 * q;
         if (q < qs) {
             acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
+            const int dq = min(dci, (int)dcp[q >> 1]);
             int d = 0;
 #pragma unroll 3
-            for (; d < dci; ++d) {
+            for (; d < dq; ++d) {
                 const float2 tp = u[d];
                 const df t{tp.x, tp.y};
                 const float4 h0 = *(const float4*)(hq + d * Q2);
@@ -1446,7 +1447,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     }
     __syncthreads();
     if (mom) {
-        bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, P.qs);
+        bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, P.qs, P.dcp);
         __syncthreads();
     }
     if (!valid) return;
@@ -1480,7 +1481,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
         mq = df_mul(mq, mz);
     };
     if (mom)
-        bin_sums_eval(Hb, u, nb, dci, Q, qs, combine);
+        bin_sums_eval(Hb, u, nb, dci, Q, qs, P.dcp, combine);
     else
         tap_sums_eval(u, w, Q, qs, [&](int i, int q) {
             return staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
@@ -1701,7 +1702,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_adj_interp(
         }
         __syncthreads();
         if (mom) {
-            bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, qs);
+            bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, qs, P.dcp);
             __syncthreads();
         }
         if (valid) {
@@ -1725,7 +1726,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_adj_interp(
                 mq = df_mul(mq, rat);
             };
             if (mom)
-                bin_sums_eval(H + (l0 - wstart) * hs, u, nb, dci, Q, qs, combine);
+                bin_sums_eval(H + (l0 - wstart) * hs, u, nb, dci, Q, qs, P.dcp, combine);
             else
                 tap_sums_eval(u, w, Q, qs, [&](int i, int q) {
                     const int li = l0 + i + B.N1;

@@ -36,6 +36,7 @@ struct ProbParams {
     int M, L, Q;   // Q = 2M
     int qs;        // terms q >= qs are small enough to be summed in FP32
     int ntop;      // largest Bessel index used by the local evaluation
+    int8_t dcp[kMaxQ / 2];   // per Hankel pair (2p, 2p+1): double-float degrees of the interpolation sums
     double z;      // crossover
     double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
     float2 cphi2, sphi2;         // the same as double-float

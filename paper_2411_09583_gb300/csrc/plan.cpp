@@ -702,6 +702,30 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     auto put = [&](size_t off, const void* src, size_t bytes) {
         if (bytes) std::memcpy(stage + off, src, bytes);
     };
+    // Per Hankel pair, the degrees of the interpolation's per-bin and
+    // per-frequency sums that need double-float: term q enters g with weight
+    // at most |a_q| z^-q, so degree d may round in FP32 once the rounding bound
+    // of the degrees from d on (as for tab.dci, whose weight is one) times the
+    // pair's larger weight stays below 1e-2 eps.
+    {
+        const int nc = T.deg + 1;
+        std::vector<double> colsum(nc, 0.0);
+        for (int i = 0; i < T.w; ++i)
+            for (int d = 0; d < nc; ++d) colsum[d] += std::fabs(T.ch[(size_t)i * nc + d]);
+        for (ProbParams& pp : probs)
+            for (int pr = 0; pr < kMaxQ / 2; ++pr) {
+                double wmax = 0.0;
+                for (int q = 2 * pr; q < 2 * pr + 2 && q < pp.Q; ++q)
+                    wmax = std::max(wmax, std::fabs(pp.a[q] * std::pow(pp.z, -q)));
+                int d = nc;
+                double acc = 0.0;
+                while (d > 2) {
+                    acc += colsum[d - 1] * (d + 2) * 5.9604644775390625e-08;
+                    if (acc * wmax <= 1e-2 * P->eps) --d; else break;
+                }
+                pp.dcp[pr] = (int8_t)d;
+            }
+    }
     put(a_prob, probs.data(), sizeof(ProbParams) * probs.size());
     put(a_es, T.es.data(), sizeof(double) * T.es.size());
     put(a_es2, T.es2.data(), sizeof(float2) * T.es2.size());
