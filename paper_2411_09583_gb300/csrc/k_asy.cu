@@ -1226,9 +1226,11 @@ __device__ __forceinline__ void bin_sums_build(const float4* win, const float2* 
 {
     const int Q2 = 2 * Q, hs = nb * Q2 + 2;
     const int npr = (nb + 1) >> 1;
+    // q is the slowest index, so that a warp's items mostly share q (and with
+    // it the double-float / FP32 branch)
     for (int o = threadIdx.x; o < nbins * npr * Q; o += blockDim.x) {
-        const int b = o / (npr * Q), rem = o - b * (npr * Q);
-        const int dp = rem / Q, q = rem - dp * Q;
+        const int q = o / (nbins * npr), rem = o - q * (nbins * npr);
+        const int b = rem / npr, dp = rem - b * npr;
         const int d0 = 2 * dp, d1 = d0 + 1;
         const bool has1 = d1 < nb;
         float2* h0 = H + b * hs + d0 * Q2 + 2 * q;
