@@ -271,14 +271,28 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
         const float p2 = exp2f(-(float)ilogbf(S.h));
         S = df_scale(S, p2);
         acc2 sum{0.f, 0.f};
-        for (int l = 0; l <= L; ++l) {
-            const int b = hm - l;
-            const float2 va = jb[(hp + l) * nt + tid];
-            float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
-            float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
-            if (l > 0 || (nu & 1)) sgn *= 2.f;
-            const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
-            acc_fma(sum, cl, df{mu[l].x, mu[l].y});
+        if (nu == 0) {
+            // C_l = (2 - delta_l0) (-1)^l J_l^2: one stored value per term, squared
+            for (int l = 0; l <= L; ++l) {
+                const float2 v = jb[l * nt + tid];
+                const float xh = v.x * p2, xl = v.y * p2;
+                const float p = xh * xh;
+                float e = fmaf(xh, xh, -p);
+                e = fmaf(2.f * xh, xl, e);
+                const df sq = fast_two_sum(p, e);
+                const float sgn = l == 0 ? 1.f : ((l & 1) ? -2.f : 2.f);
+                acc_fma(sum, df{sgn * sq.h, sgn * sq.l}, df{mu[l].x, mu[l].y});
+            }
+        } else {
+            for (int l = 0; l <= L; ++l) {
+                const int b = hm - l;
+                const float2 va = jb[(hp + l) * nt + tid];
+                float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
+                float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
+                if (l > 0 || (nu & 1)) sgn *= 2.f;
+                const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
+                acc_fma(sum, cl, df{mu[l].x, mu[l].y});
+            }
         }
         const df iS = df_recip(S);
         val = df_to(df_mul(df_mul(fast_two_sum(sum.s, sum.c), iS), iS));
