@@ -228,10 +228,13 @@ __device__ __forceinline__ double series_store_fp64(double y, int ntop, float2* 
 
 // One thread per row of a local block.  J_0..J_ntop(x/2) by Miller's backward
 // recurrence, kept (unnormalised) in this thread's column of shared memory,
-// then sum_l C_l mu_l divided by the square of the normalisation.
+// then sum_l C_l mu_l divided by the square of the normalisation.  With momb
+// (the moments of a second real component) the same C_l also give
+// sum_l C_l mub_l into g_sb.
 __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, const float2* __restrict__ w2,
-                             const double* __restrict__ mom, double* __restrict__ g_s)
+                             const double* __restrict__ mom, double* __restrict__ g_s,
+                             const double* __restrict__ momb, double* __restrict__ g_sb)
 {
     extern __shared__ float2 sm2[];
     const Tile t = tiles[blockIdx.x];
@@ -239,23 +242,31 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
     const ProbParams& P = probs[B.prob];
     const int nt = blockDim.x, tid = threadIdx.x;
     const int nu = P.nu, L = P.L;
+    const bool two = momb != nullptr;
     float2* mu = sm2;                 // [L + 1] moments of this block, double-float
-    float2* jb = sm2 + (P.ntop + 1);  // [ntop + 1][nt]
+    float2* mub = sm2 + (P.ntop + 1); // [L + 1] the second component's (two)
+    float2* jb = sm2 + (two ? 2 : 1) * (P.ntop + 1);  // [ntop + 1][nt]
     for (int l = tid; l <= L; l += nt) {
         const double v = mom[B.mom_off + l];
         const float h = (float)v;
         mu[l] = make_float2(h, (float)(v - (double)h));
+        if (two) {
+            const double vb = momb[B.mom_off + l];
+            const float hb = (float)vb;
+            mub[l] = make_float2(hb, (float)(vb - (double)hb));
+        }
     }
     __syncthreads();
     if (tid >= t.count) return;
     const int64_t k = t.start + tid;
     const float2 wk = w2[k];
     const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});   // y = omega R / 2
-    double val;
+    double val, valb = 0.0;
     if (!(ydf.h > 0.f)) {
         // y below the FP32 range: J_n(y) = delta_n0 to far below rounding, so
         // only C_0 survives, and only for nu = 0
         val = (nu == 0) ? (double)mu[0].x + (double)mu[0].y : 0.0;
+        if (two) valb = (nu == 0) ? (double)mub[0].x + (double)mub[0].y : 0.0;
     } else {
         const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
         const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
@@ -270,7 +281,7 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
         // scale by a power of two near 1/S so that products of two values stay in FP32 range
         const float p2 = exp2f(-(float)ilogbf(S.h));
         S = df_scale(S, p2);
-        acc2 sum{0.f, 0.f};
+        acc2 sum{0.f, 0.f}, sumb{0.f, 0.f};
         if (nu == 0) {
             // C_l = (2 - delta_l0) (-1)^l J_l^2: one stored value per term, squared
             for (int l = 0; l <= L; ++l) {
@@ -281,7 +292,9 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
                 e = fmaf(2.f * xh, xl, e);
                 const df sq = fast_two_sum(p, e);
                 const float sgn = l == 0 ? 1.f : ((l & 1) ? -2.f : 2.f);
-                acc_fma(sum, df{sgn * sq.h, sgn * sq.l}, df{mu[l].x, mu[l].y});
+                const df cl{sgn * sq.h, sgn * sq.l};
+                acc_fma(sum, cl, df{mu[l].x, mu[l].y});
+                if (two) acc_fma(sumb, cl, df{mub[l].x, mub[l].y});
             }
         } else {
             for (int l = 0; l <= L; ++l) {
@@ -292,12 +305,15 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
                 if (l > 0 || (nu & 1)) sgn *= 2.f;
                 const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
                 acc_fma(sum, cl, df{mu[l].x, mu[l].y});
+                if (two) acc_fma(sumb, cl, df{mub[l].x, mub[l].y});
             }
         }
         const df iS = df_recip(S);
         val = df_to(df_mul(df_mul(fast_two_sum(sum.s, sum.c), iS), iS));
+        if (two) valb = df_to(df_mul(df_mul(fast_two_sum(sumb.s, sumb.c), iS), iS));
     }
     atomicAdd(&g_s[k], (double)P.sgn * val);
+    if (two) atomicAdd(&g_sb[k], (double)P.sgn * valb);
 }
 
 // Mixed precision (eps >= 1e-6): k_local_eval in FP32.  J_0..J_ntop(y) by
@@ -311,7 +327,8 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
 // at 2^60 nothing passes 2^121.
 __global__ void k_local_eval_f32(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
                                  const Tile* __restrict__ tiles, const float2* __restrict__ w2,
-                                 const double* __restrict__ mom, double* __restrict__ g_s)
+                                 const double* __restrict__ mom, double* __restrict__ g_s,
+                                 const double* __restrict__ momb, double* __restrict__ g_sb)
 {
     extern __shared__ float smf[];
     const Tile t = tiles[blockIdx.x];
@@ -319,9 +336,14 @@ __global__ void k_local_eval_f32(const ProbParams* __restrict__ probs, const Loc
     const ProbParams& P = probs[B.prob];
     const int nt = blockDim.x, tid = threadIdx.x;
     const int nu = P.nu, L = P.L;
+    const bool two = momb != nullptr;
     float* mu = smf;                   // [L + 1]
-    float* jb = smf + (P.ntop + 1);    // [ntop + 1][nt]
-    for (int l = tid; l <= L; l += nt) mu[l] = (float)mom[B.mom_off + l];
+    float* mub = smf + (P.ntop + 1);   // [L + 1] the second component's (two)
+    float* jb = smf + (two ? 2 : 1) * (P.ntop + 1);    // [ntop + 1][nt]
+    for (int l = tid; l <= L; l += nt) {
+        mu[l] = (float)mom[B.mom_off + l];
+        if (two) mub[l] = (float)momb[B.mom_off + l];
+    }
     __syncthreads();
     if (tid >= t.count) return;
     const int64_t k = t.start + tid;
@@ -329,9 +351,12 @@ __global__ void k_local_eval_f32(const ProbParams* __restrict__ probs, const Loc
     const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;
     const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;
     const int ntop = hp + L;
-    float val = 0.f;
+    float val = 0.f, valb = 0.f;
     if (!(y >= 1e-7f)) {
-        if (nu == 0) val = mu[0];
+        if (nu == 0) {
+            val = mu[0];
+            if (two) valb = mub[0];
+        }
     } else {
         const int ns = miller_start(ntop, (double)y);
         const float inv2y = 2.f / y;
@@ -358,10 +383,13 @@ __global__ void k_local_eval_f32(const ProbParams* __restrict__ probs, const Loc
             const float vb = jb[(b >= 0 ? b : -b) * nt + tid] * iS;
             float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
             if (l > 0 || (nu & 1)) sgn *= 2.f;
-            val = fmaf(va * vb * sgn, mu[l], val);
+            const float cl = va * vb * sgn;
+            val = fmaf(cl, mu[l], val);
+            if (two) valb = fmaf(cl, mub[l], valb);
         }
     }
     atomicAdd(&g_s[k], (double)(P.sgn < 0 ? -val : val));
+    if (two) atomicAdd(&g_sb[k], (double)(P.sgn < 0 ? -valb : valb));
 }
 
 // J_n(x) for 1 <= x by Miller's recurrence in double-float (no storage).
@@ -973,14 +1001,16 @@ int local_eval_threads(int ntop_max)
 
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                    int ntiles, int ntop_max, int threads, const float2* w2,
-                                   const double* mom, double* g_s, cudaStream_t s)
+                                   const double* mom, double* g_s, const double* momb, double* g_sb,
+                                   cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float2) * ((size_t)(ntop_max + 1) * threads + (size_t)(ntop_max + 1));
+    const size_t nmu = momb ? 2 : 1;
+    size_t smem = sizeof(float2) * ((size_t)(ntop_max + 1) * threads + nmu * (size_t)(ntop_max + 1));
     cudaError_t e = cudaFuncSetAttribute(k_local_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_eval<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s);
+    k_local_eval<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s, momb, g_sb);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1004,14 +1034,15 @@ int direct_sum_mode(double eps, int max_rows, int max_cols)
 
 cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                   int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
-                                  double* g_s, cudaStream_t s)
+                                  double* g_s, const double* momb, double* g_sb, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float) * ((size_t)(ntop_max + 1) * threads + (size_t)(ntop_max + 1));
+    const size_t nmu = momb ? 2 : 1;
+    size_t smem = sizeof(float) * ((size_t)(ntop_max + 1) * threads + nmu * (size_t)(ntop_max + 1));
     cudaError_t e = cudaFuncSetAttribute(k_local_eval_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_eval_f32<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s);
+    k_local_eval_f32<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s, momb, g_sb);
     count_launches(1);
     return cudaGetLastError();
 }

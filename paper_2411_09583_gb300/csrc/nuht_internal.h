@@ -223,12 +223,15 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
 int local_moment_threads(int lmax);
 int local_eval_threads(int ntop_max);
 // Mixed precision: k_local_eval with the recurrence and the sum in FP32.
+// momb / g_sb (may be null): a second real component's moments and sums,
+// evaluated with the same Bessel values.
 cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                   int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
-                                  double* g_s, cudaStream_t s);
+                                  double* g_s, const double* momb, double* g_sb, cudaStream_t s);
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                               int ntiles, int ntop_max, int threads, const float2* w2,
-                              const double* mom, double* g_s, cudaStream_t s);
+                              const double* mom, double* g_s, const double* momb, double* g_sb,
+                              cudaStream_t s);
 // Mode of the direct kernel (0 double-float; 1 FP32 entries, FP64 sums; 2 FP32
 // entries and sums) for tolerance eps and the tallest and widest direct blocks.
 int direct_sum_mode(double eps, int max_rows, int max_cols);

@@ -101,8 +101,9 @@ struct nuht_plan_s {
     double *d_cs = nullptr, *d_gs = nullptr;
     float2 *d_r2 = nullptr, *d_w2 = nullptr, *d_cs2 = nullptr;   // double-float copies
     // the next real component of a pair (complex c, or two vectors), whose
-    // direct blocks are applied together with the first: its c and direct sums
-    double *d_csb = nullptr, *d_gsb = nullptr;
+    // local and direct blocks are applied together with the first: its c, local
+    // moments and sums
+    double *d_csb = nullptr, *d_gsb = nullptr, *d_momb = nullptr;
     float2* d_cs2b = nullptr;
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
@@ -685,7 +686,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     }
     size_t a_r = A.reserve<double>(n), a_w = A.reserve<double>(m);
     size_t a_pr = A.reserve<int32_t>(n), a_pw = A.reserve<int32_t>(m);
-    size_t a_mom = A.reserve<double>((size_t)P->mom_len);
+    size_t a_mom = A.reserve<double>((size_t)P->mom_len), a_momb = A.reserve<double>((size_t)P->mom_len);
     size_t a_gb = A.reserve<double2>((size_t)P->gb_len);
     size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
     size_t a_gt = A.reserve<float4>(P->has_large_fft ? (size_t)P->gq_len : 1);
@@ -778,7 +779,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_asy = bl.asy;
     P->d_dir = bl.dir;
     P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
-    P->d_mom = (double*)(D + a_mom);
+    P->d_mom = (double*)(D + a_mom); P->d_momb = (double*)(D + a_momb);
     P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (float4*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
     P->d_r2 = (float2*)(D + a_r2); P->d_w2 = (float2*)(D + a_w2); P->d_cs2 = (float2*)(D + a_cs2);
@@ -1002,12 +1003,13 @@ int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, 
 // accumulating into g in sorted order (FP64 atomics).  They run one after the
 // other on the caller's stream: each kernel fills the GPU, and running them
 // concurrently only makes them compete for shared memory.
-// pair: 0 this component's direct blocks; 1 also those of the next component
-// (d_csb, d_cs2b into d_gsb); 2 none (applied with the previous component).
+// pair: 0 this component's local and direct blocks; 1 also those of the next
+// component (d_csb, d_cs2b into d_gsb, one Bessel evaluation for both); 2 none
+// (applied with the previous component).
 static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
 {
     const int mask = P->opt.class_mask;
-    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir && pair != 2;
+    const bool loc = (mask & 1) && P->n_loc && pair != 2, dir = (mask & 4) && P->n_dir && pair != 2;
     const bool asy = (mask & 2) && P->n_asy;
     // The block classes share no scratch and only add into g (FP64 atomics):
     // the local and direct blocks run beside the asymptotic pipeline (ClassFork),
@@ -1021,14 +1023,21 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
                                      P->d_cs2, P->d_mom, ls));
+        double* momb = pair == 1 ? P->d_momb : nullptr;
+        if (momb) {
+            NUHT_CK(cudaMemsetAsync(momb, 0, sizeof(double) * P->mom_len, ls));
+            NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
+                                         P->d_cs2b, momb, ls));
+        }
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
+        double* gsb = momb ? P->d_gsb : nullptr;
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_local_eval_f32(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                          P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
+                                          P->eval_threads, P->d_w2, P->d_mom, P->d_gs, momb, gsb, ls));
         else
             NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                      P->eval_threads, P->d_w2, P->d_mom, P->d_gs, ls));
+                                      P->eval_threads, P->d_w2, P->d_mom, P->d_gs, momb, gsb, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
@@ -1084,10 +1093,10 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         return NUHT_OK;
     }
     NUHT_TRY(ensure_events(P, comps));
-    // real components in pairs share the direct blocks' Bessel evaluations:
-    // the first of a pair applies them to both, the second starts from the
-    // second's direct sums (d_gsb)
-    const bool pairs = (P->opt.class_mask & 4) && P->n_dir > 0;
+    // real components in pairs share the local and direct blocks' Bessel
+    // evaluations: the first of a pair applies those blocks to both, the
+    // second starts from the second's local and direct sums (d_gsb)
+    const bool pairs = ((P->opt.class_mask & 4) && P->n_dir > 0) || ((P->opt.class_mask & 1) && P->n_loc > 0);
     for (int comp = 0; comp < comps; ++comp) {
         StageTimer T{P, comp};
         const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
