@@ -766,13 +766,16 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
 // memory.  Phase 2: warp w takes l = w, w + nwarps, ... and sums
 // C_l(row) g_row / S_row^2 over the pass's rows straight from jb (compensated
 // FP32 sums, one FP64 atomic per moment and pass).  No per-thread moment
-// accumulators: the CTA holds as little shared memory as k_local_eval.
+// accumulators: the CTA holds as little shared memory as k_local_eval.  TWO:
+// a second real component's g (g_sb) summed into momb with the same C_l.
 constexpr int kAdjRowsPerLane = kMomThreads / 32;
 
+template <bool TWO>
 __global__ void __launch_bounds__(kMomThreads)
 k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
                     const Tile* __restrict__ tiles, const float2* __restrict__ w2,
-                    const double* __restrict__ g_s, double* __restrict__ mom)
+                    const double* __restrict__ g_s, double* __restrict__ mom,
+                    const double* __restrict__ g_sb, double* __restrict__ momb)
 {
     extern __shared__ float2 sm2[];
     const Tile t = tiles[blockIdx.x];
@@ -787,11 +790,13 @@ k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __re
     float2* jb = sm2;                                  // [ntop + 1][nt]
     float2* gsm = sm2 + (size_t)(P.ntop + 1) * nt;     // [nt] g_k / S^2 per row
     float* p2m = (float*)(gsm + nt);                   // [nt] scale per row
+    float2* gsmb = (float2*)(p2m + nt);                // [nt] second g_k / S^2 (TWO)
     for (int base = 0; base < t.count; base += nt) {
         const int cnt = t.count - base < nt ? t.count - base : nt;
         if (tid < cnt) {
             const int64_t k = t.start + base + tid;
             const double gk = (double)P.sgn * g_s[k];
+            const double gkb = TWO ? (double)P.sgn * g_sb[k] : 0.0;
             const float2 wk = w2[k];
             const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});   // y = omega R / 2
             if (!(ydf.h > 0.f)) {
@@ -799,6 +804,10 @@ k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __re
                 for (int q = 0; q <= ntop; ++q) jb[q * nt + tid] = make_float2(q == 0 ? 1.f : 0.f, 0.f);
                 const df g = df_from(gk);
                 gsm[tid] = make_float2(g.h, g.l);
+                if (TWO) {
+                    const df gb = df_from(gkb);
+                    gsmb[tid] = make_float2(gb.h, gb.l);
+                }
                 p2m[tid] = 1.f;
             } else {
                 const int ns = miller_start(ntop, (double)ydf.h);
@@ -810,24 +819,32 @@ k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __re
                 const df iS = df_recip(S);
                 const df gs = df_mul(df_mul(df_from(gk), iS), iS);   // g_k / S^2
                 gsm[tid] = make_float2(gs.h, gs.l);
+                if (TWO) {
+                    const df gsb = df_mul(df_mul(df_from(gkb), iS), iS);
+                    gsmb[tid] = make_float2(gsb.h, gsb.l);
+                }
                 p2m[tid] = p2;
             }
         }
         __syncthreads();
         float pr[kAdjRowsPerLane];
-        df gr[kAdjRowsPerLane];
+        df gr[kAdjRowsPerLane], grb[TWO ? kAdjRowsPerLane : 1];
 #pragma unroll
         for (int i = 0; i < kAdjRowsPerLane; ++i) {
             const int kk = lane + 32 * i;
             pr[i] = kk < cnt ? p2m[kk] : 0.f;
             const float2 g = kk < cnt ? gsm[kk] : make_float2(0.f, 0.f);
             gr[i] = df{g.x, g.y};
+            if (TWO) {
+                const float2 gb = kk < cnt ? gsmb[kk] : make_float2(0.f, 0.f);
+                grb[TWO ? i : 0] = df{gb.x, gb.y};
+            }
         }
         for (int l = warp; l <= L; l += nw) {
             const int b = hm - l, bi = b >= 0 ? b : -b;
             float sgn = (b < 0 && (bi & 1)) ? -1.f : 1.f;
             if (l > 0 || (nu & 1)) sgn *= 2.f;
-            acc2 a{0.f, 0.f};
+            acc2 a{0.f, 0.f}, ab{0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < kAdjRowsPerLane; ++i) {
                 const int kk = lane + 32 * i;
@@ -837,10 +854,15 @@ k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __re
                     const float p = pr[i], ps = p * sgn;
                     const df cl = df_mul(df{va.x * p, va.y * p}, df{vb.x * ps, vb.y * ps});
                     acc_fma(a, cl, gr[i]);
+                    if (TWO) acc_fma(ab, cl, grb[TWO ? i : 0]);
                 }
             }
             a = warp_sum_acc(a);
             if (lane == 0) atomicAdd(&mom[B.mom_off + l], acc_value(a));
+            if (TWO) {
+                ab = warp_sum_acc(ab);
+                if (lane == 0) atomicAdd(&momb[B.mom_off + l], acc_value(ab));
+            }
         }
         __syncthreads();   // jb and gsm are rewritten by the next pass
     }
@@ -927,15 +949,19 @@ int local_adj_threads(int ntop_max)
 
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                      int ntiles, int ntop_max, int threads, const float2* w2,
-                                     const double* g_s, double* mom, cudaStream_t s)
+                                     const double* g_s, double* mom, const double* g_sb, double* momb,
+                                     cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (threads < 32 || threads > kMomThreads || (threads & 31)) return cudaErrorInvalidValue;
-    size_t smem = sizeof(float2) * (size_t)(ntop_max + 1) * threads + (sizeof(float2) + sizeof(float)) * threads;
-    cudaError_t e = cudaFuncSetAttribute(k_local_adj_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    if ((g_sb == nullptr) != (momb == nullptr)) return cudaErrorInvalidValue;
+    const bool two = g_sb != nullptr;
+    size_t smem = sizeof(float2) * (size_t)(ntop_max + 1) * threads + (sizeof(float2) + sizeof(float)) * threads +
+                  (two ? sizeof(float2) * threads : 0);
+    auto kern = two ? k_local_adj_moments<true> : k_local_adj_moments<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_local_adj_moments<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, g_s, mom);
+    kern<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, g_s, mom, g_sb, momb);
     count_launches(1);
     return cudaGetLastError();
 }

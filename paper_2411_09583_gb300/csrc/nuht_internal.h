@@ -240,9 +240,12 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
                           const float2* w2, const double* c_s, const float2* c2, double* g_s,
                           const double* c_sb, const float2* c2b, double* g_sb, cudaStream_t s);
 int local_adj_threads(int ntop_max);
+// g_sb / momb (both null, or both set): a second real component's g and
+// moments, summed with the same Bessel values.
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                      int ntiles, int ntop_max, int threads, const float2* w2,
-                                     const double* g_s, double* mom, cudaStream_t s);
+                                     const double* g_s, double* mom, const double* g_sb, double* momb,
+                                     cudaStream_t s);
 cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                   int ntiles, int lmax, const float2* r2, const double* mom, double* c_s,
                                   cudaStream_t s);

@@ -1121,11 +1121,14 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
 
 // Transpose of apply_forward: g (sorted, d_gs) -> c (sorted, d_cs).  Each
 // block class runs its transposed pipeline; column contributions of blocks at
-// different levels meet in c with FP64 atomics.
-static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
+// different levels meet in c with FP64 atomics.  pair as in apply_forward,
+// for the local blocks only (d_gsb into d_csb); the direct blocks run per
+// component.
+static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
 {
     const int mask = P->opt.class_mask;
-    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir, asy = (mask & 2) && P->n_asy;
+    const bool loc = (mask & 1) && P->n_loc && pair != 2, dir = (mask & 4) && P->n_dir;
+    const bool asy = (mask & 2) && P->n_asy;
     // local and direct blocks beside the asymptotic pipeline, as in apply_forward
     ClassFork fk;
     if (P->opt.timing != NUHT_TIMING_SERIAL && asy && (loc || dir)) NUHT_CK(fk.open(s));
@@ -1134,12 +1137,17 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s)
         const int thr = local_adj_threads(P->ntop_max);
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
+        double* momb = pair == 1 ? P->d_momb : nullptr;
+        if (momb) NUHT_CK(cudaMemsetAsync(momb, 0, sizeof(double) * P->mom_len, ls));
         NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, thr,
-                                         P->d_w2, P->d_gs, P->d_mom, ls));
+                                         P->d_w2, P->d_gs, P->d_mom, momb ? P->d_gsb : nullptr, momb, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
         NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, P->d_mom,
                                       P->d_cs, ls));
+        if (momb)
+            NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, momb,
+                                          P->d_csb, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
@@ -1185,13 +1193,25 @@ int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_com
         return NUHT_OK;
     }
     NUHT_TRY(ensure_events(P, comps));
+    // real components in pairs share the local blocks' Bessel evaluations: the
+    // first of a pair sums both components' moments, the second starts from
+    // its local sums (d_csb)
+    const bool pairs = (P->opt.class_mask & 1) && P->n_loc > 0;
     for (int comp = 0; comp < comps; ++comp) {
         StageTimer T{P, comp};
+        const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
-        NUHT_CK(cudaMemsetAsync(P->d_cs, 0, sizeof(double) * P->n, s));
+        if (pair == 2)
+            NUHT_CK(cudaMemcpyAsync(P->d_cs, P->d_csb, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s));
+        else
+            NUHT_CK(cudaMemsetAsync(P->d_cs, 0, sizeof(double) * P->n, s));
         NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_gs, nullptr, s));
+        if (pair == 1) {
+            NUHT_CK(cudaMemsetAsync(P->d_csb, 0, sizeof(double) * P->n, s));
+            NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp + 1, P->d_gsb, nullptr, s));
+        }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
-        NUHT_TRY(apply_adjoint(P, T, s));
+        NUHT_TRY(apply_adjoint(P, T, s, pair));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
         NUHT_CK(launch_scatter(P->d_cs, P->d_pr, P->n, comps, comp, c, s));
         NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
