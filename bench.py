@@ -41,6 +41,52 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2070e6 / 1e12
 FP32_ISSUE_PER_S = 128 * 152 * 2070e6
 DF_PEAK_TFLOPS = 2 * FP32_ISSUE_PER_S / 12 / 1e12
 L2_FLUSH_BYTES = 512 << 20
+HBM_FALLBACK_GBS = 6800.0
+DTYPE = ("df64: double-float (pairs of FP32, ~48-bit) tap, moment and Bessel arithmetic; "
+         "64-bit fixed-point positions and phases; FP64 set-up and FP64 atomic accumulation")
+
+
+def measured_hbm_peak():
+    """(GB/s, source): the machine's measured copy bandwidth, else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback (no MEASURED_PEAKS.json)"
+
+
+def probe_alu_peaks(dev):
+    """Issue-rate probe of the arithmetic the kernels run (nuht_probe_alu), timed
+    with CUDA events on this GPU: FP32 FMA, FP64 FMA and the double-float
+    compensated multiply-add acc_fma, in TFLOP/s (2 FLOP per multiply-add)."""
+    from paper_2411_09583_gb300.nuht import probe_alu
+    out = {}
+    for kind, iters in (("ffma", 1 << 20), ("dfma", 1 << 14), ("acc_fma", 1 << 17)):
+        probe_alu(kind, 1 << 8)
+        best = max(probe_alu(kind, iters)[2] for _ in range(3))
+        out[kind + "_tflops"] = best / 1e12
+    out["basis"] = ("nuht_probe_alu: 8 independent chains per thread, 4 CTAs x 256 threads per SM, "
+                    "CUDA events, best of 3 launches; acc_fma is the double-float product added to a "
+                    "compensated FP32 sum exactly as the execute kernels do it (FP64-equivalent FLOPs)")
+    return out
+
+
+def sampled_error(nu, r, omega, c, g, eps, rows, ref=None):
+    """Worst max_k |g_k - oracle_k| / (eps ||c||_1) over the vectors, on the
+    sampled output rows (the oracle's direct sum, outside any timed region).
+    The accuracy contract is <= 10, i.e. err_over_tol <= 1."""
+    import numpy as np
+
+    import oracle
+    if ref is None:
+        ref = oracle.direct_rows(nu, r, omega, c, rows)
+    gr = np.asarray(g)[rows]
+    err = np.max(np.abs(gr - ref), axis=0)
+    c1 = np.abs(np.asarray(c)).sum(axis=0)
+    v = float(np.max(err / (eps * c1)))
+    return {"err_over_eps_c1": v, "err_over_tol": v / 10.0, "rows": int(len(rows)),
+            "against": "oracle direct sum on sampled rows"}
 
 
 def parse_args(argv=None):
@@ -62,11 +108,15 @@ def parse_args(argv=None):
                          "from experiments, Algorithm 2)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the oracle sample")
+    ap.add_argument("--opts", type=str, default=None,
+                    help="plan options as JSON (e.g. '{\"min_size\": 2048}') instead of the autotuner's")
     return ap.parse_args(argv)
 
 
 def workload_config(a):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
     return {"workload": "nuht_fp64_uniform_n%d_m%d_nu%d_eps%g" % (a.n, a.m, a.nu, a.eps),
+            "parallelism": "replicas" if ws > 1 else "1 GPU",
             "n": a.n, "m": a.m, "nu": a.nu, "eps": a.eps,
             "r": "U[0,1]", "omega": "U[0,%g]" % a.omega_max, "c": "N(0,1) real",
             "seed": 2, "step": "plan+execute from unsorted device inputs",
@@ -159,10 +209,10 @@ def oracle_sample(a, r, omega, c, target_s):
     nrows = int(min(max(32, 32 * target_s / dt), omega.size, 20000))
     rows = sample_rows(omega.size, nrows, seed=4321)
     t0 = time.perf_counter()
-    oracle.direct_rows(a.nu, r, omega, c, rows)
+    ref = oracle.direct_rows(a.nu, r, omega, c, rows)
     dt = time.perf_counter() - t0
     full = dt * omega.size / nrows
-    return (r.size + omega.size) / full, nrows, dt
+    return (r.size + omega.size) / full, nrows, dt, rows, ref
 
 
 # ---------------------------------------------------------------- reference arm
@@ -176,7 +226,7 @@ def run_reference(a):
         oracle_sample(a, r, omega, c, per_step * 0.3)
     vals, rows_used, secs = [], 0, 0.0
     for _ in range(a.steps):
-        v, nrows, dt = oracle_sample(a, r, omega, c, per_step)
+        v, nrows, dt, _, _ = oracle_sample(a, r, omega, c, per_step)
         vals.append(v)
         rows_used, secs = nrows, secs + dt
     value = statistics.median(vals)
@@ -325,13 +375,24 @@ def run_batched(dev, steps):
     bp.close()
     exe = statistics.median(ex_ms)
     pl = statistics.median(plan_ms)
+    # accuracy of the graph's result: 10 sampled rows of every problem
+    gh = g.cpu().numpy()
+    rng = np.random.default_rng(77)
+    worst, off = 0.0, 0
+    for nu_i, rr, ww, cc in probs:
+        rows = np.sort(rng.choice(ww.size, size=min(10, ww.size), replace=False))
+        e = sampled_error(nu_i, rr, ww, cc, gh[off:off + ww.size], 1e-8, rows)
+        worst = max(worst, e["err_over_eps_c1"])
+        off += ww.size
     return {"workload": "256 problems, n, m ~ 10^U[3,5], nu ~ U{0..20}, omega ~ U[0, m], eps 1e-8",
             "units_n_plus_m": units, "execute_graph_ms": exe, "plan_ms": pl,
             "value_execute": units / (exe * 1e-3), "value_plan_execute": units / ((exe + pl) * 1e-3),
             "unit": UNIT, "execute": "one CUDA graph replay (one launch per stage over all problems)",
             "autotuned_opts": best, "autotune_default_execute_ms": default_ms[0] if default_ms else None,
             "autotune_best_execute_ms": table[0][0],
-            "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]]}
+            "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
+            "error": {"err_over_eps_c1": worst, "err_over_tol": worst / 10.0, "rows": 10 * len(probs),
+                      "against": "oracle direct sum, 10 sampled rows of every problem (worst problem)"}}
 
 
 def run_mixed(dev, steps):
@@ -340,7 +401,7 @@ def run_mixed(dev, steps):
     import torch
 
     from paper_2411_09583_gb300 import Plan
-    from paper_2411_09583_gb300.workloads import loguniform_problem
+    from paper_2411_09583_gb300.workloads import loguniform_problem, sample_rows
     r, omega, c = loguniform_problem(4_000_000, 4_000_000, omega_max=4e4, seed=4, complex_c=True)
     dr, dw, dc = (torch.tensor(x, device=dev) for x in (r, omega, c))
     stream = torch.cuda.current_stream(dev)
@@ -367,7 +428,11 @@ def run_mixed(dev, steps):
             ms.append(s0.elapsed_time(s1))
             p.close()
         t = statistics.median(ms)
-        out[prec] = {"ms_per_step": t, "value": 8e6 / (t * 1e-3), "opts": opts}
+        with Plan(1, dr, dw, 1e-5, precision=prec, **opts) as p:
+            gh = p.execute(dc).cpu().numpy()
+        rows = sample_rows(omega.size, 100, seed=98)
+        out[prec] = {"ms_per_step": t, "value": 8e6 / (t * 1e-3), "opts": opts,
+                     "error": sampled_error(1, r, omega, c, gh, 1e-5, rows)}
     return out
 
 
@@ -412,7 +477,25 @@ def run_grad(dev, steps):
         torch.cuda.synchronize(dev)
         ms.append(s0.elapsed_time(s1))
     t = statistics.median(ms)
+    # accuracy of the gradients on 100 sampled points: dL/dc_j = sum_k e_k J_nu(omega_k r_j)
+    # within 10 eps ||e||_1, dL/dr_j = c_j sum_k e_k omega_k J_nu'(omega_k r_j) within
+    # 10 eps |c_j| ||omega e||_1, with e = A c - g* from the same forward
+    import oracle
+    from paper_2411_09583_gb300.workloads import sample_rows
+    gc, gr = one()
+    with Plan(0, dr, dw, 1e-10, **opts) as p:
+        e = (p.execute(dc) - gstar).cpu().numpy()
+    cols = sample_rows(r.size, 100, seed=96)
+    gc, gr = gc.cpu().numpy()[cols], gr.cpu().numpy()[cols]
+    ref_c = oracle.direct_rows(0, omega, r, e, cols)
+    we = omega * e
+    ref_r = c[cols] * 0.5 * (oracle.direct_rows(-1, omega, r, we, cols) - oracle.direct_rows(1, omega, r, we, cols))
+    err_c = float(np.max(np.abs(gc - ref_c)) / (1e-10 * np.abs(e).sum()))
+    err_r = float(np.max(np.abs(gr - ref_r) / (1e-10 * np.abs(c[cols]) * np.abs(we).sum())))
     return {"workload": "n = m = 1e6, nu = 0, eps 1e-10, loss 1/2||A c - g*||^2, grads c and r",
+            "error": {"grad_c_err_over_eps_e1": err_c, "grad_r_err_over_eps_c_we1": err_r,
+                      "err_over_tol": max(err_c, err_r) / 10.0, "rows": 100,
+                      "against": "oracle direct sums (orders nu, nu - 1, nu + 1) at 100 sampled points"},
             "ms_per_step": t, "value": 2e6 / (t * 1e-3), "unit": UNIT, "opts": opts,
             "step": "plan + forward + adjoint (dL/dc) + plans and adjoints of orders nu-1, nu+1 (dL/dr)"}
 
@@ -426,7 +509,7 @@ def run_stress(dev, steps):
     import torch
 
     from paper_2411_09583_gb300 import Plan
-    from paper_2411_09583_gb300.workloads import exponential_grid, fourier_bessel_grid
+    from paper_2411_09583_gb300.workloads import exponential_grid, fourier_bessel_grid, sample_rows
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {"workload": "nu = 0, eps 1e-8, n = m, Fourier-Bessel and exponential grids, c ~ N(0,1)",
@@ -453,8 +536,12 @@ def run_stress(dev, steps):
                 info = p.info()
                 p.close()
             t = statistics.median(ms)
+            with Plan(0, dr, dw, 1e-8) as p:
+                gh = p.execute(c).cpu().numpy()
+            rows = sample_rows(n, 100, seed=97)
             res["%.0e" % n] = {"ms_per_step": t, "value": 2 * n / (t * 1e-3),
-                               "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]]}
+                               "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
+                               "error": sampled_error(0, r, omega, c.cpu().numpy(), gh, 1e-8, rows)}
         out[name] = res
     return out
 
@@ -485,7 +572,9 @@ def run_ours(a):
     # plan options from the autotuner (min_size, spreading tile, M around the
     # heuristic), chosen before and outside the timed region
     opts, tuned = {}, None
-    if not a.no_autotune:
+    if a.opts:
+        opts = json.loads(a.opts)
+    elif not a.no_autotune:
         from paper_2411_09583_gb300.autotune import autotune, candidates
         grid = candidates([a.nu], a.eps, min_sizes=(1024, 2048, 4096, 8192), spread_tiles=(0, 128),
                           m_offsets=(0, 1))
@@ -498,6 +587,13 @@ def run_ours(a):
         p = Plan(a.nu, dr, dw, a.eps, timing=timing, **opts)
         g = p.execute(dc)
         return p, g
+
+    # measured arithmetic peaks of this GPU (outside the timed region), with
+    # the SM clock sampled while the probes run
+    psampler = ClockSampler(dev.index if dev.index is not None else 0)
+    psampler.start()
+    alu = probe_alu_peaks(dev)
+    alu["clocks"] = psampler.stop()
 
     # warm-up
     for _ in range(max(a.warmup, 0)):
@@ -530,6 +626,7 @@ def run_ours(a):
         p.close()
     torch.cuda.synchronize(dev)
     launches = kernel_launch_count() - launches0
+    g_main = g.cpu().numpy()
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
@@ -550,6 +647,7 @@ def run_ours(a):
         s1.record(stream)
         torch.cuda.synchronize(dev)
         exe_ms.append(s0.elapsed_time(s1))
+    g_exec = p.execute(dc).cpu().numpy()
     p.close()
     exe_s = max_over_ranks(sum(exe_ms) / 1e3, ws, dev)
 
@@ -569,6 +667,7 @@ def run_ours(a):
         s1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms.append(s0.elapsed_time(s1))
+    g_e2e = np.array(gh, copy=True)
     e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, ws, dev)
     e2e_value = ws * len(e2e_ms) * (a.n + a.m) / e2e_s
 
@@ -596,20 +695,38 @@ def run_ours(a):
                  "local_moments": "k_local_moments", "local_eval": "k_local_eval",
                  "direct": "k_direct", "asy_fft": "k_asy_fft_small"}
     roof = None
+    hbm_peak, hbm_src = measured_hbm_peak()
     if flops is not None:
         ach = flops / (mean_stage[dom] * 1e-3) / 1e12
+        peak = alu["acc_fma_tflops"]
         roof = {"bound": "alu", "kernel": kernel_of.get(dom, dom), "stage": dom,
-                "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / DF_PEAK_TFLOPS,
-                "peak_source": "FP64-equivalent FLOPs of double-float arithmetic on the FP32 "
-                               "pipes: 128 FP32 instr/clk/SM x 152 SMs x 2070 MHz / 12 instr "
-                               "per compensated multiply-add x 2 FLOP (native FP64 pipe: "
-                               "%.3f TFLOP/s)" % FP64_PEAK_TFLOPS,
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "peak_source": "measured in this run (nuht_probe_alu, burst): FP64-equivalent FLOP/s of "
+                               "the double-float compensated multiply-add acc_fma on the FP32 pipes; "
+                               "FP32 FMA %.1f, FP64 FMA %.3f TFLOP/s measured beside it; unit-count model "
+                               "%.3f (128 FP32 instr/clk/SM x 152 SMs x 2070 MHz / 12 instr x 2 FLOP)"
+                               % (alu["ffma_tflops"], alu["dfma_tflops"], DF_PEAK_TFLOPS),
                 "algorithmic_flops_per_launch": flops, "units_per_launch": units,
                 "launch_ms": mean_stage[dom], "launch_ms_alone": mean_serial[dom]}
         tr, basis = stored_traffic(kernel_of.get(dom, dom), workload_config(a)["workload"], opts, units)
         roof["traffic"] = tr
         roof["traffic_basis"] = basis
+        if tr:
+            gbs = tr / (mean_stage[dom] * 1e-3) / 1e9
+            roof["hbm_gbs"] = gbs
+            roof["hbm_frac"] = gbs / hbm_peak
+    exe_ms_step = 1e3 * exe_s / a.steps
+    compulsory = 8 * (2 * a.n + 2 * a.m)   # c, sorted r and omega read; g written
+    hbm = {"peak_gbs": hbm_peak, "peak_source": hbm_src,
+           "execute_compulsory_bytes": compulsory,
+           "execute_gbs": compulsory / (exe_ms_step * 1e-3) / 1e9,
+           "execute_frac": compulsory / (exe_ms_step * 1e-3) / 1e9 / hbm_peak,
+           "dominant_kernel": roof["kernel"] if roof else None,
+           "dominant_kernel_gbs": roof.get("hbm_gbs") if roof else None,
+           "dominant_kernel_frac": roof.get("hbm_frac") if roof else None,
+           "basis": "execute: compulsory bytes (c, sorted r and omega, g) over the execute-only time; "
+                    "dominant kernel: ncu DRAM bytes per launch over its live launch time"}
 
     extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = None
     if not a.no_extra and ws == 1:
@@ -632,7 +749,10 @@ def run_ours(a):
             po.close()
         with Plan(o_nu, dr, dw, a.eps, **opts) as pw:
             oi = pw.info()
+            g_o = pw.execute(dc).cpu().numpy()
+        from paper_2411_09583_gb300.workloads import sample_rows
         extra_order = {"nu": o_nu, "ms_per_step": statistics.median(o_ms),
+                       "error": sampled_error(o_nu, r, omega, c, g_o, a.eps, sample_rows(a.m, 200, seed=95)),
                        "value": (a.n + a.m) / (statistics.median(o_ms) * 1e-3), "unit": UNIT,
                        "step": "plan + execute, same workload and options as the main line",
                        "M": oi["M"], "L": oi["L"], "z": oi["z"]}
@@ -644,17 +764,27 @@ def run_ours(a):
     line = None
     if rank == 0:
         cpu = None
+        rows = ref = None
         if ws == 1 and not a.no_cpu_baseline:
-            v, nrows, dt = oracle_sample(a, r, omega, c, a.cpu_seconds)
+            v, nrows, dt, rows, ref = oracle_sample(a, r, omega, c, a.cpu_seconds)
             cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "oracle direct sum over all n points for %d random output rows "
                              "(%.1f s), extrapolated to m rows" % (nrows, dt)}
+        if rows is None:
+            from paper_2411_09583_gb300.workloads import sample_rows
+            rows = sample_rows(a.m, 200, seed=94)
+            import oracle
+            ref = oracle.direct_rows(a.nu, r, omega, c, rows)
+        error = sampled_error(a.nu, r, omega, c, g_main, a.eps, rows, ref)
+        error["execute_only"] = sampled_error(a.nu, r, omega, c, g_exec, a.eps, rows, ref)["err_over_eps_c1"]
+        error["e2e"] = sampled_error(a.nu, r, omega, c, g_e2e, a.eps, rows, ref)["err_over_eps_c1"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic (seeded uniform r, omega; Gaussian c)",
-                "config": dict(workload_config(a), parallelism="replicas" if ws > 1 else "1 GPU",
-                               opts=opts or "library defaults"),
+                "dtype": DTYPE, "data": "synthetic (seeded uniform r, omega; Gaussian c)",
+                "error": error,
+                "config": workload_config(a),
+                "plan_opts": opts or "library defaults",
                 "autotune": tuned,
                 "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT,
@@ -662,6 +792,8 @@ def run_ours(a):
                         "d2h_bytes_per_step": 8 * a.m},
                 "gpu_launches": launches,
                 "roofline": roof,
+                "hbm": hbm,
+                "alu_peaks": alu,
                 "cpu_baseline": cpu,
                 "execute_only": {"value": ws * a.steps * (a.n + a.m) / exe_s, "unit": UNIT,
                                  "ms_per_step": 1e3 * exe_s / a.steps},

@@ -51,6 +51,7 @@ extern "C" {
 #define NUHT_ERR_TIMEOUT     5   /* a bounded device wait gave up (reserved) */
 #define NUHT_ERR_UNSUPPORTED 6   /* option combination not built (e.g. order |nu| > 100) */
 #define NUHT_ERR_SCRATCH     7   /* request exceeds the fixed scratch of nuht_local_apply_noalloc */
+#define NUHT_ERR_BAD_BLOCKS  8   /* a block work list failed its check (nuht_check_blocks) */
 
 /* --------------------------------------------------------------- options */
 #define NUHT_PREC_FP64  0   /* every stage in FP64 (or FP64-accurate arithmetic) */
@@ -183,6 +184,25 @@ int nuht_transform_host(int nu, const double *r, int64_t n, const double *omega,
                         int64_t m, double eps, const double *c, double *g, int nvec,
                         const nuht_opts *opt, void *stream);
 
+/* Host-only check of a work list: the subdivision (Algorithm 1, Sec. 4.1) of
+ * one problem with order nu, tolerance eps and m_terms as in the plan
+ * options; the crossover z is the one nuht_choose_params gives.  r_sorted (n) and omega_sorted
+ * (m) are HOST arrays in ascending order; ranges holds count blocks as
+ * (k0, k1, j0, j1) (inclusive indices into omega_sorted / r_sorted, the
+ * layout of nuht_get_blocks) and cls their classes (NUHT_BLOCK_*), both host
+ * arrays.  Returns NUHT_OK when the blocks cover every entry of the m x n
+ * matrix exactly once, every local block has omega_k1 r_j1 <= z, every
+ * asymptotic block omega_k0 r_j0 > z, and every direct block an area of at
+ * most min_size; NUHT_ERR_BAD_BLOCKS otherwise (or when the arrays are not
+ * sorted); NUHT_ERR_INVALID_ARG / NUHT_ERR_UNSUPPORTED for bad arguments.
+ * The plan runs the same check on the host subdivision's lists before using
+ * them, and on its device-built lists when the environment variable
+ * NUHT_CHECKED is set (and not "0"); nuht_plan then fails with
+ * NUHT_ERR_BAD_BLOCKS instead of executing an invalid list.  No GPU needed. */
+int nuht_check_blocks(int nu, double eps, int m_terms, const double *r_sorted, int64_t n,
+                      const double *omega_sorted, int64_t m, int min_size, const int64_t *ranges,
+                      const int32_t *cls, int64_t count);
+
 /* Plan summary (orders, block counts, work sizes). */
 int nuht_info(nuht_plan_t p, nuht_plan_info *out);
 
@@ -213,6 +233,17 @@ const char *nuht_stage_name(int i);
  * (a diagnostic counter). */
 int64_t nuht_kernel_launch_count(void);
 
+/* Throughput probe (the paper has no counterpart; a measurement aid).  Times,
+ * with CUDA events on the given stream, one launch of kind 0 = FP32 fused
+ * multiply-adds, 1 = FP64 fused multiply-adds, 2 = the double-float
+ * compensated multiply-add the execute kernels accumulate with (a product of
+ * two double-float numbers added to a compensated FP32 sum), iters iterations
+ * of 8 independent chains per thread on 4 CTAs of 256 threads per SM.
+ * *ms receives the launch time, *ops the number of operations (multiply-adds)
+ * it ran; 2 * ops / ms gives FLOP/ms (for kind 2, FP64-equivalent FLOPs).
+ * Synchronises the stream.  iters in [1, 2^32]. */
+int nuht_probe_alu(int kind, int64_t iters, double *ms, double *ops, void *stream);
+
 /* ------------------------------------------------- no-allocation entry point
  * The paper has no counterpart to this call; it is a service for callers that
  * cannot let a library call cudaMalloc -- frameworks that reserve nearly all
@@ -237,7 +268,8 @@ int64_t nuht_kernel_launch_count(void);
  * overlap on the GPU -- e.g. on two streams -- race.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with
  * that device current) and caches it; make that first call before any stream
- * capture.  Errors: NUHT_ERR_INVALID_ARG (sizes, pointers, eps),
+ * capture, and do not use the call across a cudaDeviceReset (the array may
+ * move when the module is loaded again).  Errors: NUHT_ERR_INVALID_ARG (sizes, pointers, eps),
  * NUHT_ERR_DOMAIN (omega_max * r_max > z, or a bound negative / not finite),
  * NUHT_ERR_UNSUPPORTED (|nu| > 100), NUHT_ERR_SCRATCH, NUHT_ERR_CUDA. */
 #define NUHT_NOALLOC_MAX_MOMENTS 32768

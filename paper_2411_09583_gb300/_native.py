@@ -20,6 +20,7 @@ NUHT_ERR_CUDA = 4
 NUHT_ERR_TIMEOUT = 5
 NUHT_ERR_UNSUPPORTED = 6
 NUHT_ERR_SCRATCH = 7
+NUHT_ERR_BAD_BLOCKS = 8
 NOALLOC_MAX_MOMENTS = 32768
 
 PREC_FP64 = 0
@@ -31,7 +32,8 @@ EXPORTED = ["nuht_default_opts", "nuht_choose_params", "nuht_plan", "nuht_execut
             "nuht_adjoint", "nuht_transform_host", "nuht_info", "nuht_get_blocks",
             "nuht_get_permutations", "nuht_destroy", "nuht_strerror",
             "nuht_last_cuda_error", "nuht_stage_times", "nuht_stage_name",
-            "nuht_kernel_launch_count", "nuht_local_apply_noalloc", "nuht_plan_many"]
+            "nuht_kernel_launch_count", "nuht_local_apply_noalloc", "nuht_plan_many",
+            "nuht_probe_alu", "nuht_check_blocks"]
 NUM_STAGES = 8
 
 
@@ -122,5 +124,9 @@ def lib():
         L.nuht_plan_many.argtypes = [ctypes.POINTER(p), i, p, p, p, p, p, d,
                                      ctypes.POINTER(NuhtOpts), p]
         L.nuht_plan_many.restype = i
+        L.nuht_probe_alu.argtypes = [i, i64, ctypes.POINTER(d), ctypes.POINTER(d), p]
+        L.nuht_probe_alu.restype = i
+        L.nuht_check_blocks.argtypes = [i, d, i, p, i64, p, i64, i, p, p, i64]
+        L.nuht_check_blocks.restype = i
         _lib = L
         return _lib

@@ -18,7 +18,10 @@
 // host that name is only a stand-in.  The device address is looked up with
 // cudaGetSymbolAddress the first time the entry point runs on a device (with
 // that device current) and cached; that first call therefore does a little
-// set-up and should come before any stream capture.
+// set-up and should come before any stream capture.  The cached address is
+// that of the device's current context: after cudaDeviceReset the module is
+// loaded again and the array may move, so the entry point must not be used
+// across a device reset.
 #include <cstdint>
 #include <mutex>
 
@@ -112,26 +115,45 @@ __global__ void k_noalloc_eval(int nu, int sgn, int L, int ntop, const double* _
     }
     const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;
     const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;
-    const int ns = miller_start(ntop, y);
-    const double inv2y = 2.0 / y;
-    double jp1 = 0.0, jc = 1.0, S = 2.0;
-    if (ns <= ntop) jb[ns * nt + tid] = jc;
-    for (int i = ns; i >= 2; i -= 2) {
-        const double jm = fma((double)i * inv2y, jc, -jp1);
-        const double jmm = fma((double)(i - 1) * inv2y, jm, -jc);
-        if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = jm;
-        if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = jmm;
-        S = fma(2.0, jmm, S);
-        jp1 = jm;
-        jc = jmm;
-        if (too_big(jc)) {
-            const double sc = 1e-150;
-            jc *= sc; jp1 *= sc; S *= sc;
-            const int top = ntop < ns ? ntop : ns;
-            for (int q = i - 2; q <= top; ++q) jb[q * nt + tid] *= sc;
+    double S = 1.0;
+    if (y < 1.0) {
+        // power series (DLMF 10.2.2), already normalised: for small y each
+        // backward step multiplies by about 2i/y, faster than the rescaling
+        // below could follow
+        const double h = 0.5 * y, q = -h * h;
+        double lead = 1.0;   // (y/2)^i / i!
+        for (int i = 0; i <= ntop; ++i) {
+            if (i > 0) lead *= h / (double)i;
+            double term = lead, sum = lead;
+            for (int t = 1; t <= 12; ++t) {
+                term *= q / ((double)t * (double)(i + t));
+                sum += term;
+            }
+            jb[i * nt + tid] = sum;
         }
+    } else {
+        const int ns = miller_start(ntop, y);
+        const double inv2y = 2.0 / y;
+        double jp1 = 0.0, jc = 1.0;
+        S = 2.0;
+        if (ns <= ntop) jb[ns * nt + tid] = jc;
+        for (int i = ns; i >= 2; i -= 2) {
+            const double jm = fma((double)i * inv2y, jc, -jp1);
+            const double jmm = fma((double)(i - 1) * inv2y, jm, -jc);
+            if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = jm;
+            if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = jmm;
+            S = fma(2.0, jmm, S);
+            jp1 = jm;
+            jc = jmm;
+            if (too_big(jc)) {
+                const double sc = 1e-150;
+                jc *= sc; jp1 *= sc; S *= sc;
+                const int top = ntop < ns ? ntop : ns;
+                for (int q = i - 2; q <= top; ++q) jb[q * nt + tid] *= sc;
+            }
+        }
+        S -= jc;
     }
-    S -= jc;
     const double inv_s2 = 1.0 / (S * S);
     for (int v = 0; v < nvec; ++v) {
         const double* mu = mom + (int64_t)v * (L + 1);
@@ -195,8 +217,12 @@ extern "C" int nuht_local_apply_noalloc(int nu, double eps, const double* r, int
         const size_t smem = sizeof(double) * (size_t)(L + 1) * threads;
         e = cudaFuncSetAttribute(k_noalloc_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return NUHT_ERR_CUDA;
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return NUHT_ERR_CUDA;
         int64_t blocks = (n + threads - 1) / threads;
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;   // grid-stride beyond 8 CTAs per SM
         dim3 grid((unsigned)blocks, (unsigned)nvec);
         k_noalloc_moments<<<grid, threads, smem, s>>>(anu, L, r, n, Rm > 0.0 ? 1.0 / R : 0.0,
                                                               c, nvec, mom);

@@ -50,6 +50,11 @@ void subdivide(const int32_t* stair, const double* r, const double* omega, int64
                int64_t min_size, int n_cand, std::vector<HBlock>& loc, std::vector<HBlock>& asy,
                std::vector<HBlock>& dir);
 
+// Host check of a work list (exact cover, block classes, direct-block area);
+// ranges holds (k0, k1, j0, j1) per block in sorted indices, cls its class.
+bool check_blocks(const double* r, int64_t n, const double* omega, int64_t m, double z, int64_t min_size,
+                  const int64_t* ranges, const int32_t* cls, int64_t count);
+
 // Device memory from the library's pool (kept reserved between plans) and
 // pinned host staging buffers (grow-only, used under stage_lock()).
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);

@@ -137,10 +137,37 @@ std::mutex g_pool_mu;
 cudaMemPool_t g_pool[kMaxDev] = {};
 }  // namespace
 
+namespace {
+// Host-side fault injection (testing aid): with NUHT_FAULT_ALLOC=k in the
+// environment, the k-th device allocation of the library counted from when
+// that value was first seen fails as if the device were out of memory.  It
+// acts before any CUDA call, so it also runs without a GPU.
+std::mutex g_fault_mu;
+std::string g_fault_val;
+long g_fault_count = 0;
+
+bool injected_alloc_failure()
+{
+    const char* f = std::getenv("NUHT_FAULT_ALLOC");
+    if (!f || !*f) return false;
+    std::lock_guard<std::mutex> lock(g_fault_mu);
+    if (g_fault_val != f) {
+        g_fault_val = f;
+        g_fault_count = 0;
+    }
+    const long k = std::atol(f);
+    return k > 0 && ++g_fault_count == k;
+}
+}  // namespace
+
 // One memory pool per device, owned by the library, whose release threshold
 // keeps freed plan memory reserved for the next plan (no re-mapping per plan).
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s)
 {
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -344,6 +371,7 @@ const char* nuht_strerror(int code)
         case NUHT_ERR_TIMEOUT: return "device wait timed out";
         case NUHT_ERR_UNSUPPORTED: return "unsupported parameters";
         case NUHT_ERR_SCRATCH: return "request exceeds the no-allocation scratch (nvec * (L + 1) > NUHT_NOALLOC_MAX_MOMENTS)";
+        case NUHT_ERR_BAD_BLOCKS: return "a block work list failed its check (cover, classes or sizes)";
         default: return "unknown status";
     }
 }
@@ -357,6 +385,21 @@ int nuht_choose_params(int nu, double eps, int m_terms, int* M, double* z, int* 
     if (m_terms < 0 || m_terms > kMaxM) return NUHT_ERR_INVALID_ARG;
     if (nu > 100 || nu < -100) return NUHT_ERR_UNSUPPORTED;
     return choose_params(nu, eps, m_terms, M, z, L);
+}
+
+int nuht_check_blocks(int nu, double eps, int m_terms, const double* r_sorted, int64_t n,
+                      const double* omega_sorted, int64_t m, int min_size, const int64_t* ranges,
+                      const int32_t* cls, int64_t count)
+{
+    if (n < 0 || m < 0 || count < 0 || min_size < 1) return NUHT_ERR_INVALID_ARG;
+    if ((n > 0 && !r_sorted) || (m > 0 && !omega_sorted) || (count > 0 && (!ranges || !cls)))
+        return NUHT_ERR_INVALID_ARG;
+    int M = 0, L = 0;
+    double z = 0.0;
+    const int rc = nuht_choose_params(nu, eps, m_terms, &M, &z, &L);
+    if (rc != NUHT_OK) return rc;
+    return check_blocks(r_sorted, n, omega_sorted, m, z, min_size, ranges, cls, count) ? NUHT_OK
+                                                                                         : NUHT_ERR_BAD_BLOCKS;
 }
 
 void nuht_destroy(nuht_plan_t p)
@@ -432,6 +475,45 @@ static void bind_build_temps(BlockBuild& bb, char* base, const BuildTemps& t)
     bb.totals = (int64_t*)(base + t.tot);
     bb.maxv = (int64_t*)(base + t.maxv);
 }
+
+// Checked mode (NUHT_CHECKED set and not "0"): the device-built block lists
+// and sorted values go back to the host and each problem's list is checked
+// (exact cover, classes, direct-block areas) before the plan is returned.
+static int verify_lists(nuht_plan_t P)
+{
+    const int64_t nb = (int64_t)P->n_loc + P->n_asy + P->n_dir;
+    std::vector<SubBlk> blk((size_t)nb);
+    std::vector<double> hr((size_t)P->n), hw((size_t)P->m);
+    if (nb) NUHT_CK(cudaMemcpyAsync(blk.data(), P->d_blk, sizeof(SubBlk) * nb, cudaMemcpyDeviceToHost, P->stream));
+    if (P->n) NUHT_CK(cudaMemcpyAsync(hr.data(), P->d_r, sizeof(double) * P->n, cudaMemcpyDeviceToHost, P->stream));
+    if (P->m) NUHT_CK(cudaMemcpyAsync(hw.data(), P->d_w, sizeof(double) * P->m, cudaMemcpyDeviceToHost, P->stream));
+    NUHT_CK(cudaStreamSynchronize(P->stream));
+    const size_t np = P->probs.size();
+    std::vector<std::vector<int64_t>> rg(np);
+    std::vector<std::vector<int32_t>> cl(np);
+    for (int64_t b = 0; b < nb; ++b) {
+        const SubBlk& x = blk[(size_t)b];
+        if (x.prob < 0 || (size_t)x.prob >= np) return NUHT_ERR_BAD_BLOCKS;
+        const ProbParams& q = P->probs[(size_t)x.prob];
+        rg[(size_t)x.prob].insert(rg[(size_t)x.prob].end(),
+                                  {x.k0 - q.w_off, x.k1 - q.w_off, x.j0 - q.r_off, x.j1 - q.r_off});
+        cl[(size_t)x.prob].push_back(b < P->n_loc ? NUHT_BLOCK_LOCAL
+                                                  : (b < (int64_t)P->n_loc + P->n_asy ? NUHT_BLOCK_ASY : NUHT_BLOCK_DIRECT));
+    }
+    for (size_t i = 0; i < np; ++i) {
+        const ProbParams& q = P->probs[i];
+        if (!check_blocks(hr.data() + q.r_off, q.n, hw.data() + q.w_off, q.m, q.z, P->opt.min_size, rg[i].data(),
+                          cl[i].data(), (int64_t)cl[i].size()))
+            return NUHT_ERR_BAD_BLOCKS;
+    }
+    return NUHT_OK;
+}
+
+#define NUHT_TRY_BUILD(x)               \
+    do {                                \
+        int rc_ = (x);                  \
+        if (rc_ != NUHT_OK) return rc_; \
+    } while (0)
 
 static int build_plan(nuht_plan_t P, const double* r, const double* omega)
 {
@@ -604,6 +686,19 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
             subdivide(hst + q.w_off, hr + q.r_off, hw + q.w_off, q.n, q.m, P->opt.min_size, P->opt.n_split_cand,
                       lb, ab, db);
             const std::vector<HBlock>* src[3] = {&lb, &ab, &db};
+            {
+                // the host walk's lists are checked before they reach the device
+                std::vector<int64_t> rg;
+                std::vector<int32_t> cl;
+                for (int c = 0; c < 3; ++c)
+                    for (const HBlock& h : *src[c]) {
+                        rg.insert(rg.end(), {h.k0, h.k1, h.j0, h.j1});
+                        cl.push_back(c);
+                    }
+                if (!check_blocks(hr + q.r_off, q.n, hw + q.w_off, q.m, q.z, P->opt.min_size, rg.data(), cl.data(),
+                                  (int64_t)cl.size()))
+                    return NUHT_ERR_BAD_BLOCKS;
+            }
             for (int c = 0; c < 3; ++c)
                 for (const HBlock& h : *src[c]) {
                     hl[c].push_back(SubBlk{(int32_t)h.k0, (int32_t)h.k1, (int32_t)h.j0, (int32_t)h.j1, ip});
@@ -851,6 +946,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_smode = (int32_t*)(D + a_sm);
     NUHT_CK(launch_spread_modes(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, tb, P->d_r, P->d_smode, s));
     P->plan_ms[3] = ms_since(clk);
+    if (const char* ck = std::getenv("NUHT_CHECKED"))
+        if (*ck && *ck != '0') NUHT_TRY_BUILD(verify_lists(P));
     return NUHT_OK;
 }
 

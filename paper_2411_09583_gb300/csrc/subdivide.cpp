@@ -21,7 +21,9 @@
 // (X S > kAsyMaxXS) goes back on the work list to be cut into quadrants
 // (every part of an asymptotic block is asymptotic), in the same order as the
 // device subdivision.
+#include <algorithm>
 #include <deque>
+#include <map>
 
 #include "nuht_host.h"
 
@@ -85,6 +87,83 @@ void subdivide(const int32_t* stair, const double* r, const double* omega, int64
         place(b.k0, bk, bj + 1, b.j1);         // upper right: mixed
         place(bk + 1, b.k1, b.j0, bj);         // lower left: mixed
     }
+}
+
+}  // namespace nuht
+
+namespace nuht {
+
+// Host check of a subdivision (a work list) of one sorted problem: every
+// block lies in the matrix and is non-empty; the blocks cover every entry
+// exactly once; local blocks hold only entries with omega_k r_j <= z
+// (omega_k1 r_j1 <= z, the sorted corner), asymptotic blocks only entries
+// with omega_k r_j > z (omega_k0 r_j0 > z), and direct blocks have area at
+// most min_size (Algorithm 1).  The cover is checked by sweeping the rows:
+// the set of blocks crossing a row only changes where a block starts or
+// ends, and at each such row the crossing blocks' column ranges must tile
+// 0..n-1 in order.  O(B log B) for B blocks.
+bool check_blocks(const double* r, int64_t n, const double* omega, int64_t m, double z, int64_t min_size,
+                  const int64_t* ranges, const int32_t* cls, int64_t count)
+{
+    if (n < 0 || m < 0 || count < 0) return false;
+    for (int64_t j = 1; j < n; ++j)
+        if (!(r[j - 1] <= r[j])) return false;
+    for (int64_t k = 1; k < m; ++k)
+        if (!(omega[k - 1] <= omega[k])) return false;
+    if (n == 0 || m == 0) return count == 0;
+    struct Ev {
+        int64_t row;
+        int64_t blk;
+        bool start;
+    };
+    std::vector<Ev> ev;
+    ev.reserve(2 * (size_t)count);
+    for (int64_t b = 0; b < count; ++b) {
+        const int64_t k0 = ranges[4 * b], k1 = ranges[4 * b + 1], j0 = ranges[4 * b + 2], j1 = ranges[4 * b + 3];
+        if (k0 < 0 || k1 < k0 || k1 >= m || j0 < 0 || j1 < j0 || j1 >= n) return false;
+        switch (cls[b]) {
+            case NUHT_BLOCK_LOCAL:
+                if (!(omega[k1] * r[j1] <= z)) return false;
+                break;
+            case NUHT_BLOCK_ASY:
+                if (!(omega[k0] * r[j0] > z)) return false;
+                break;
+            case NUHT_BLOCK_DIRECT:
+                if ((k1 - k0 + 1) * (j1 - j0 + 1) > min_size) return false;
+                break;
+            default:
+                return false;
+        }
+        ev.push_back(Ev{k0, b, true});
+        ev.push_back(Ev{k1 + 1, b, false});
+    }
+    std::sort(ev.begin(), ev.end(), [](const Ev& a, const Ev& b) {
+        return a.row != b.row ? a.row < b.row : (a.start < b.start);   // ends before starts
+    });
+    std::map<int64_t, int64_t> active;   // j0 -> j1 of the blocks crossing the current row
+    size_t i = 0;
+    if (ev.empty() || ev[0].row != 0) return false;   // row 0 uncovered
+    while (i < ev.size()) {
+        const int64_t row = ev[i].row;
+        for (; i < ev.size() && ev[i].row == row; ++i) {
+            const int64_t b = ev[i].blk, j0 = ranges[4 * b + 2], j1 = ranges[4 * b + 3];
+            if (ev[i].start) {
+                if (!active.emplace(j0, j1).second) return false;   // two blocks start at one column
+            } else {
+                auto it = active.find(j0);
+                if (it == active.end() || it->second != j1) return false;
+                active.erase(it);
+            }
+        }
+        if (row >= m) break;
+        int64_t next = 0;   // the crossing blocks must tile the columns of this row
+        for (const auto& a : active) {
+            if (a.first != next) return false;
+            next = a.second + 1;
+        }
+        if (next != n) return false;
+    }
+    return active.empty();
 }
 
 }  // namespace nuht

@@ -50,6 +50,33 @@ def kernel_launch_count():
     return int(N.lib().nuht_kernel_launch_count())
 
 
+def probe_alu(kind, iters=1 << 16, stream=None):
+    """Time the throughput probe nuht_probe_alu: kind "ffma" (FP32), "dfma"
+    (FP64) or "acc_fma" (double-float compensated multiply-add).  Returns
+    (milliseconds, multiply-adds, FLOP/s with 2 FLOP per multiply-add)."""
+    k = {"ffma": 0, "dfma": 1, "acc_fma": 2}[kind]
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    N.check(N.lib().nuht_probe_alu(k, int(iters), ctypes.byref(ms), ctypes.byref(ops),
+                                   _stream_ptr(stream)), "nuht_probe_alu")
+    return ms.value, ops.value, 2.0 * ops.value / (ms.value * 1e-3)
+
+
+def check_blocks(nu, eps, r_sorted, omega_sorted, ranges, classes, min_size=1024, m_terms=0):
+    """Host check of a work list through nuht_check_blocks: ranges (count, 4) of
+    (k0, k1, j0, j1) into the sorted arrays, classes (count,) of NUHT_BLOCK_*.
+    Returns the status code (NUHT_OK when the list is a valid subdivision)."""
+    r = np.ascontiguousarray(r_sorted, dtype=np.float64)
+    w = np.ascontiguousarray(omega_sorted, dtype=np.float64)
+    rg = np.ascontiguousarray(np.asarray(ranges, dtype=np.int64).reshape(-1, 4))
+    cl = np.ascontiguousarray(classes, dtype=np.int32)
+    if cl.size != rg.shape[0]:
+        raise ValueError("one class per block")
+    return int(N.lib().nuht_check_blocks(int(nu), float(eps), int(m_terms), r.ctypes.data_as(ctypes.c_void_p),
+                                         r.size, w.ctypes.data_as(ctypes.c_void_p), w.size, int(min_size),
+                                         rg.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
+                                         cl.size))
+
+
 def stage_names():
     return [N.lib().nuht_stage_name(i).decode() for i in range(N.NUM_STAGES)]
 

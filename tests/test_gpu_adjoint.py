@@ -205,16 +205,19 @@ def test_dense_bins_both_directions(layout, nu):
     assert np.max(np.abs(ca - oracle.direct(nu, omega, r, e))) <= tol(eps, e)
 
 
+@pytest.mark.parametrize("nu", [0, 3, 100])
 @pytest.mark.parametrize("precision,eps", [("fp64", 1e-10), ("mixed", 1e-6)])
-def test_three_vectors_pair_and_single(precision, eps):
+def test_three_vectors_pair_and_single(precision, eps, nu):
     # three real vectors: the first two share the local and direct blocks'
-    # Bessel values, the third runs alone; both directions against the oracle
+    # Bessel values, the third runs alone; both directions against the oracle.
+    # Orders 3 and 100 take the general C_l products (odd order, and the
+    # largest Bessel index and shared-memory columns).
     from paper_2411_09583_gb300 import Plan
     r, omega, _ = uniform_problem(2500, 2300, omega_max=3000.0, seed=78)
     rng = np.random.default_rng(79)
     c = rng.standard_normal((r.size, 3))
     e = rng.standard_normal((omega.size, 3))
-    with Plan(0, to_dev(r), to_dev(omega), eps, precision=precision) as p:
+    with Plan(nu, to_dev(r), to_dev(omega), eps, precision=precision) as p:
         assert p.info()["n_local"] > 0
         g = p.execute(to_dev(c)).cpu().numpy()
         ca = p.adjoint(to_dev(e)).cpu().numpy()
@@ -222,5 +225,5 @@ def test_three_vectors_pair_and_single(precision, eps):
     cols = np.arange(0, r.size, 5)
     for v in range(3):
         cv, ev = np.ascontiguousarray(c[:, v]), np.ascontiguousarray(e[:, v])
-        assert np.max(np.abs(g[rows, v] - oracle.direct_rows(0, r, omega, cv, rows))) <= tol(eps, cv)
-        assert np.max(np.abs(ca[cols, v] - oracle.direct_rows(0, omega, r, ev, cols))) <= tol(eps, ev)
+        assert np.max(np.abs(g[rows, v] - oracle.direct_rows(nu, r, omega, cv, rows))) <= tol(eps, cv)
+        assert np.max(np.abs(ca[cols, v] - oracle.direct_rows(nu, omega, r, ev, cols))) <= tol(eps, ev)

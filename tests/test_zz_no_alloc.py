@@ -6,8 +6,10 @@ synchronisation of cudaMalloc / cudaFree) use this call for transforms whose
 whole matrix is local.  Its scratch is a fixed device array shared by all
 calls, so the test runs it twice in a row (second call with other sizes and
 data) and compares each result with the planned path (nuht_plan +
-nuht_execute) on the same inputs, within the accuracy contract.  This file is
-collected last so that a run stopping at the first failure has run the others.
+nuht_execute) on the same inputs, and with the oracle's direct sum, within the
+accuracy contract.  Frequencies down to 1e-90 (and exactly 0) check the small
+argument path of the Bessel values.  This file is collected last so that a run
+stopping at the first failure has run the others.
 """
 import ctypes
 
@@ -17,6 +19,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
 
 
 def _lib():
@@ -59,11 +63,18 @@ def test_no_alloc_matches_planned_path_twice():
         r[0] = 1.0
         w = rng.uniform(0.0, z, m)                 # omega_max * r_max = z: all local
         c = rng.standard_normal((n, nvec)) if nvec > 1 else rng.standard_normal(n)
+        w[:5] = [0.0, 1e-90, 1e-60, 1e-20, 1e-3]   # small arguments of the Bessel values
         rc, g = _noalloc(L, nu, eps, r, 1.0, w, z, c, nvec)
         assert rc == N.NUHT_OK, N.lib().nuht_strerror(rc)
+        assert np.all(np.isfinite(g))
         ref = _planned(nu, eps, r, w, c)
         tol = 10 * eps * np.abs(c).sum(axis=0)
         assert np.all(np.max(np.abs(g - ref), axis=0) <= tol)
+        # against the exact sum on a sample of rows (and every small-argument row)
+        rows = np.concatenate([np.arange(5), rng.choice(np.arange(5, m), 60, replace=False)])
+        cm = c.reshape(n, -1)
+        exact = np.stack([oracle.direct_rows(nu, r, w, cm[:, v], rows) for v in range(cm.shape[1])], axis=1)
+        assert np.all(np.max(np.abs(g.reshape(m, -1)[rows] - exact), axis=0) <= tol)
 
 
 def test_no_alloc_rejects_requests_beyond_its_scratch():
