@@ -728,7 +728,7 @@ def run_ours(a):
            "basis": "execute: compulsory bytes (c, sorted r and omega, g) over the execute-only time; "
                     "dominant kernel: ncu DRAM bytes per launch over its live launch time"}
 
-    extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = None
+    extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = extra_det = None
     if not a.no_extra and ws == 1:
         # the same workload at the other order of the scaled plain-NUHT
         # configuration (nu = 10), same options and timing as the main line
@@ -756,6 +756,33 @@ def run_ours(a):
                        "value": (a.n + a.m) / (statistics.median(o_ms) * 1e-3), "unit": UNIT,
                        "step": "plan + execute, same workload and options as the main line",
                        "M": oi["M"], "L": oi["L"], "z": oi["z"]}
+        # the same workload in the deterministic mode (bitwise reproducible:
+        # exact fixed-point accumulation instead of FP64 atomics)
+        for _ in range(2):
+            with Plan(a.nu, dr, dw, a.eps, deterministic=True, **opts) as pdt:
+                pdt.execute(dc)
+        d_ms, d_ex = [], []
+        for _ in range(max(3, a.steps // 2)):
+            flush.zero_()
+            s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            s0.record(stream)
+            pdt = Plan(a.nu, dr, dw, a.eps, deterministic=True, **opts)
+            s1.record(stream)
+            g_d = pdt.execute(dc)
+            s2.record(stream)
+            torch.cuda.synchronize(dev)
+            d_ms.append(s0.elapsed_time(s2))
+            d_ex.append(s1.elapsed_time(s2))
+            g_d2 = pdt.execute(dc)
+            same = bool(torch.equal(g_d.view(torch.int64), g_d2.view(torch.int64)))
+            pdt.close()
+        from paper_2411_09583_gb300.workloads import sample_rows
+        extra_det = {"ms_per_step": statistics.median(d_ms), "execute_ms": statistics.median(d_ex),
+                     "value": (a.n + a.m) / (statistics.median(d_ms) * 1e-3), "unit": UNIT,
+                     "repeat_bitwise_equal": same,
+                     "error": sampled_error(a.nu, r, omega, c, g_d.cpu().numpy(), a.eps,
+                                            sample_rows(a.m, 200, seed=93)),
+                     "step": "plan + execute with deterministic=1, same workload and options as the main line"}
         extra_batched = run_batched(dev, a.steps)
         extra_mixed = run_mixed(dev, a.steps)
         extra_grad = run_grad(dev, a.steps)
@@ -808,6 +835,7 @@ def run_ours(a):
                 "differentiation": extra_grad,
                 "stress": extra_stress,
                 "other_order": extra_order,
+                "deterministic": extra_det,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],

@@ -88,7 +88,15 @@ typedef struct {
     int timing;        /* NUHT_TIMING_*: stage events (see nuht_stage_times); default 0 */
     int spread_tile;   /* points per spreading CTA: 0 = automatic (256, or 128 when
                           2M > 16); else 64..256, a multiple of 32 */
-    int reserved[5];   /* must be zero */
+    int deterministic; /* 1 = bitwise reproducible results: every block class adds its
+                          contributions to g (c for the adjoint), to the spreading grids and
+                          to the moments as exact 128-bit fixed-point integers (scaled per
+                          call by the largest input magnitude, rounded once per
+                          contribution at about 2^-54 of it), so the order of the additions
+                          does not matter; the same inputs on the same GPU then give the same
+                          bits on every run.  Slower (more atomics, no FP32 row sums in the
+                          direct blocks, extra device memory).  Default 0 (FP64 atomics). */
+    int reserved[4];   /* must be zero */
 } nuht_opts;
 
 /* Execute stages, in launch order (nuht_stage_times / nuht_stage_name). */

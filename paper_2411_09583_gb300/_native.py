@@ -41,7 +41,8 @@ class NuhtOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("min_size", ctypes.c_int),
                 ("n_split_cand", ctypes.c_int), ("m_terms", ctypes.c_int),
                 ("class_mask", ctypes.c_int), ("timing", ctypes.c_int),
-                ("spread_tile", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("spread_tile", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class NuhtPlanInfo(ctypes.Structure):

@@ -198,7 +198,7 @@ __device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
 // cell(c) is the grid index of cell c, or -1 for a cell outside the grid.
 template <class Target, class Cell>
 __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, const Tables& tab, Target&& target,
-                                               Cell&& cell, double2* __restrict__ gb, float2* sm)
+                                               Cell&& cell, Accum gb, float2* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -374,10 +374,7 @@ __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, con
             }
             for (; e < L.dpad; ++e) sf = fmaf(ar[e].x, Mb[e * Q2 + qv].x, sf);
             const double val = acc_value(s) + (double)sf;
-            if (val != 0.0) {
-                double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
-                atomicAdd(dst, val);
-            }
+            if (val != 0.0) gb.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
         }
         __syncthreads();
     }
@@ -477,7 +474,7 @@ __host__ __device__ __forceinline__ size_t spread_fold_smem(int nt, int Q, int w
 
 __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, const Tables& tab, FoldPlan F,
                             const double* __restrict__ r_s, const float2* __restrict__ r2,
-                            const float2* __restrict__ c2, double2* __restrict__ gb, float4* sm4)
+                            const float2* __restrict__ c2, Accum gb, float4* sm4)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -717,10 +714,7 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
                 sacc.c += e2;
             }
             const double val = acc_value(sacc);
-            if (val != 0.0) {
-                double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
-                atomicAdd(dst, val);
-            }
+            if (val != 0.0) gb.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
         }
         __syncthreads();
     }
@@ -733,7 +727,7 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
 // global grid.
 __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                             const double* __restrict__ r_s, const float2* __restrict__ r2,
-                            const float2* __restrict__ c2, double2* __restrict__ gb, float4* smem4)
+                            const float2* __restrict__ c2, Accum gb, float4* smem4)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -817,8 +811,8 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
         vi += __shfl_down_sync(gmask, vi, 1, kSub);
         const int idx = cell + B.N1;
         if (live && sub == 0 && idx >= 0 && idx < nf1 && (vr != 0.0 || vi != 0.0)) {
-            atomicAdd(&gb[(int64_t)idx * Q + q].x, vr);
-            atomicAdd(&gb[(int64_t)idx * Q + q].y, vi);
+            gb.add(2 * ((int64_t)idx * Q + q), vr);
+            gb.add(2 * ((int64_t)idx * Q + q) + 1, vi);
         }
     }
 }
@@ -869,7 +863,7 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     const int mode = modes[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
-    double2* gb = grid_b + B.b_off;
+    const Accum gb = Accum{(double*)grid_b, probs[B.prob].fxs}.at(2 * B.b_off);
     if ((mode & 3) == 2)
         spread_fold(B, Q, probs[B.prob].qs, t, tab, fold_unpack(mode), r_s, r2, c2, gb, smem4);
     else if (mode & 3) {
@@ -1500,7 +1494,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const df scale = df_mul(df_sqrt(m1d), df_recip(psihat_fx(tab, B, Sw)));
     df outv = df_mul(df_mul(scale, re), df{tab.ic2.x, tab.ic2.y});
     if (P.sgn < 0) outv = df_negate(outv);
-    atomicAdd(&g_s[k], df_to(outv));
+    Accum{g_s, P.fxs}.add(k, df_to(outv));
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1574,7 +1568,7 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
     const int Q = P.Q;
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int mask = B.nf2 - 1;
-    double2* tg = tgrid + B.q_off;
+    const Accum tg = Accum{(double*)tgrid, P.fxs}.at(2 * B.q_off);
     const int cnt = t.count;
     if (cnt <= 0) return;
     if (tid == 0) {
@@ -1639,8 +1633,8 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
         }
         if (any) {
             const int64_t o = (int64_t)(cell & mask) * Q + q;
-            atomicAdd(&tg[o].x, acc_value(ar));
-            atomicAdd(&tg[o].y, acc_value(ai));
+            tg.add(2 * o, acc_value(ar));
+            tg.add(2 * o + 1, acc_value(ai));
         }
     }
 }
@@ -1740,7 +1734,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_adj_interp(
             df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
             const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
             const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
-            atomicAdd(&c_s[j], df_to(df_mul(df_sqrt(rat), re)));
+            Accum{c_s, P.fxs}.add(j, df_to(df_mul(df_sqrt(rat), re)));
         }
         __syncthreads();   // l0s, the window and H are rewritten by the next pass
     }
@@ -1766,7 +1760,7 @@ __host__ __device__ __forceinline__ int f32_stride4(int n)
 // ceil(tile / 8) points).
 __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                                    const double* __restrict__ r_s, const float2* __restrict__ r2,
-                                   const float2* __restrict__ c2, double2* __restrict__ gb, float* sm)
+                                   const float2* __restrict__ c2, Accum gb, float* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb;
@@ -1865,10 +1859,7 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
             if (idx < 0 || idx >= nf1) continue;
             float sacc = 0.f;
             for (int d = 0; d < nb; ++d) sacc = fmaf(Ach[i * dpad + d], Mb[d * Q2 + qv], sacc);
-            if (sacc != 0.f) {
-                double* dst = (qv & 1) ? &gb[(int64_t)idx * Q + (qv >> 1)].y : &gb[(int64_t)idx * Q + (qv >> 1)].x;
-                atomicAdd(dst, (double)sacc);
-            }
+            if (sacc != 0.f) gb.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), (double)sacc);
         }
         __syncthreads();
     }
@@ -1885,7 +1876,7 @@ __host__ __device__ __forceinline__ size_t spread_moments_f32_smem(int nt, int Q
 // FP32 spreading, sparse tile: taps per point, one thread per (cell, q).
 __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                                 const double* __restrict__ r_s, const float2* __restrict__ r2,
-                                const float2* __restrict__ c2, double2* __restrict__ gb, float2* smf)
+                                const float2* __restrict__ c2, Accum gb, float2* smf)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -1944,8 +1935,8 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
         }
         const int idx = cell + B.N1;
         if (idx >= 0 && idx < nf1 && (sr != 0.f || si != 0.f)) {
-            atomicAdd(&gb[(int64_t)idx * Q + q].x, (double)sr);
-            atomicAdd(&gb[(int64_t)idx * Q + q].y, (double)si);
+            gb.add(2 * ((int64_t)idx * Q + q), (double)sr);
+            gb.add(2 * ((int64_t)idx * Q + q) + 1, (double)si);
         }
     }
 }
@@ -1962,7 +1953,7 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     if (t.count <= 0) return;
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
-    double2* gb = grid_b + B.b_off;
+    const Accum gb = Accum{(double*)grid_b, probs[B.prob].fxs}.at(2 * B.b_off);
     if (modes[blockIdx.x] & 3)
         spread_moments_f32(B, Q, t, tab, r_s, r2, c2, gb, (float*)smf);
     else
@@ -2094,7 +2085,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     if (piece > tab.ph_pieces - 1) piece = tab.ph_pieces - 1;
     const float ph = horner_f32(tab.ph2 + piece * (tab.ph_deg + 1), tab.ph_deg, 2.f * (xi - (float)piece) - 1.f);
     const float val = tab.ic2.x * sqrtf(m1) / ph * re;
-    atomicAdd(&g_s[k], (double)(P.sgn < 0 ? -val : val));
+    Accum{g_s, P.fxs}.add(k, (double)(P.sgn < 0 ? -val : val));
 }
 
 }  // namespace

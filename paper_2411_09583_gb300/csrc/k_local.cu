@@ -68,7 +68,7 @@ __device__ __forceinline__ acc2 warp_sum_acc(acc2 a)
 // dst[l] += sum over the CTA's threads of acc[l * nt + thread], l <= L: one
 // warp per l, compensated FP32 sums, one conversion and one FP64 atomic per l
 // (FP64 runs at 1/64 of the FP32 rate).
-__device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int L, double* dst)
+__device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int L, Accum dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int l = warp; l <= L; l += nw) {
@@ -81,7 +81,7 @@ __device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int 
             a.c += v.c + e;
         }
         a = warp_sum_acc(a);
-        if (lane == 0) atomicAdd(&dst[l], acc_value(a));
+        if (lane == 0) dst.add(l, acc_value(a));
     }
 }
 
@@ -138,7 +138,7 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
         }
     }
     __syncthreads();
-    reduce_columns_add(acc, nt, L, mom + B.mom_off);
+    reduce_columns_add(acc, nt, L, Accum{mom, probs[B.prob].fxs}.at(B.mom_off));
 }
 
 // J_0..J_ntop(y), unnormalised, into this thread's column jb[n * nt + tid]
@@ -312,8 +312,8 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
         val = df_to(df_mul(df_mul(fast_two_sum(sum.s, sum.c), iS), iS));
         if (two) valb = df_to(df_mul(df_mul(fast_two_sum(sumb.s, sumb.c), iS), iS));
     }
-    atomicAdd(&g_s[k], (double)P.sgn * val);
-    if (two) atomicAdd(&g_sb[k], (double)P.sgn * valb);
+    Accum{g_s, P.fxs}.add(k, (double)P.sgn * val);
+    if (two) Accum{g_sb, P.fxs}.add(k, (double)P.sgn * valb);
 }
 
 // Mixed precision (eps >= 1e-6): k_local_eval in FP32.  J_0..J_ntop(y) by
@@ -388,8 +388,8 @@ __global__ void k_local_eval_f32(const ProbParams* __restrict__ probs, const Loc
             if (two) valb = fmaf(cl, mub[l], valb);
         }
     }
-    atomicAdd(&g_s[k], (double)(P.sgn < 0 ? -val : val));
-    if (two) atomicAdd(&g_sb[k], (double)(P.sgn < 0 ? -valb : valb));
+    Accum{g_s, P.fxs}.add(k, (double)(P.sgn < 0 ? -val : val));
+    if (two) Accum{g_sb, P.fxs}.add(k, (double)(P.sgn < 0 ? -valb : valb));
 }
 
 // J_n(x) for 1 <= x by Miller's recurrence in double-float (no storage).
@@ -690,9 +690,11 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
                          const float2* __restrict__ r2, const float2* __restrict__ w2,
                          const double* __restrict__ c_s, const float2* __restrict__ c2, double* __restrict__ g_s,
                          const double* __restrict__ c_sb, const float2* __restrict__ c2b, double* __restrict__ g_sb,
-                         int mode)
+                         int mode, int det)
 {
-    // per vector: [rows] FP64 row sums, or [rows][S] FP32 slots (mode 2)
+    // per vector: [rows] FP64 row sums or [rows][S] FP32 slots (mode 2); none in
+    // the deterministic mode (never mode 2), where every entry's product goes
+    // straight into the exact fixed-point sums of g
     extern __shared__ double rowacc[];
     __shared__ int cnt[2];
     const bool two = g_sb != nullptr;
@@ -702,7 +704,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
     const int area = rows * cols;
     int S = kDirSlots;
     while (S > 1 && S * rows > kDirSlotFloats) S >>= 1;
-    const int accd = mode == 2 ? kDirSlotFloats / 2 : rows;   // doubles per vector
+    const int accd = det ? 0 : (mode == 2 ? kDirSlotFloats / 2 : rows);   // doubles per vector
     double* rowaccb = rowacc + accd;
     float* rowf = (float*)rowacc;
     float* rowfb = (float*)rowaccb;
@@ -713,7 +715,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
             if (two) rowfb[i] = 0.f;
         }
     } else {
-        for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        for (int i = threadIdx.x; i < accd; i += blockDim.x) {
             rowacc[i] = 0.0;
             if (two) rowaccb[i] = 0.0;
         }
@@ -745,9 +747,15 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
         const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
-        atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
-        if (two) atomicAdd(&rowaccb[rr], v * c_sb[B.j0 + cc]);
+        if (det) {
+            fx_add(reinterpret_cast<Fx128*>(g_s) + B.k0 + rr, (double)P.sgn * (v * c_s[B.j0 + cc]), P.fxs);
+            if (two) fx_add(reinterpret_cast<Fx128*>(g_sb) + B.k0 + rr, (double)P.sgn * (v * c_sb[B.j0 + cc]), P.fxs);
+        } else {
+            atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
+            if (two) atomicAdd(&rowaccb[rr], v * c_sb[B.j0 + cc]);
+        }
     }
+    if (det) return;
     __syncthreads();
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
         atomicAdd(&g_s[B.k0 + i], (double)P.sgn * rowacc[i]);
@@ -858,10 +866,10 @@ k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __re
                 }
             }
             a = warp_sum_acc(a);
-            if (lane == 0) atomicAdd(&mom[B.mom_off + l], acc_value(a));
+            if (lane == 0) Accum{mom, P.fxs}.add(B.mom_off + l, acc_value(a));
             if (TWO) {
                 ab = warp_sum_acc(ab);
-                if (lane == 0) atomicAdd(&momb[B.mom_off + l], acc_value(ab));
+                if (lane == 0) Accum{momb, P.fxs}.add(B.mom_off + l, acc_value(ab));
             }
         }
         __syncthreads();   // jb and gsm are rewritten by the next pass
@@ -903,7 +911,7 @@ k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restr
             t0 = t1;
             t1 = t2;
         }
-        atomicAdd(&c_s[j], acc_value(sum));
+        Accum{c_s, probs[B.prob].fxs}.add(j, acc_value(sum));
     }
 }
 
@@ -912,24 +920,29 @@ k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restr
 __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
                              const double* __restrict__ r_s, const double* __restrict__ w_s,
                              const float2* __restrict__ r2, const float2* __restrict__ w2,
-                             const double* __restrict__ g_s, double* __restrict__ c_s, int lowp)
+                             const double* __restrict__ g_s, double* __restrict__ c_s, int lowp, int det)
 {
+    // [cols] FP64 column sums; none in the deterministic mode, where every
+    // entry's product goes straight into the exact fixed-point sums of c
     extern __shared__ double colacc[];
     __shared__ int cnt[2];
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
     const int area = rows * cols;
-    int* list = (int*)(colacc + cols);
-    for (int i = threadIdx.x; i < cols; i += blockDim.x) colacc[i] = 0.0;
+    const int accd = det ? 0 : cols;
+    int* list = (int*)(colacc + accd);
+    for (int i = threadIdx.x; i < accd; i += blockDim.x) colacc[i] = 0.0;
     const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt);
     const DirFx F = direct_frame(r_s, w_s, B);
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
         const int rr = e / cols, cc = e - rr * cols;
         const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
-        atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
+        if (det) fx_add(reinterpret_cast<Fx128*>(c_s) + B.j0 + cc, (double)P.sgn * (v * g_s[B.k0 + rr]), P.fxs);
+        else atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
     }
+    if (det) return;
     __syncthreads();
     for (int i = threadIdx.x; i < cols; i += blockDim.x)
         atomicAdd(&c_s[B.j0 + i], (double)P.sgn * colacc[i]);
@@ -979,13 +992,14 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
 
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
                               int max_area, int lowp, const double* r_s, const double* w_s, const float2* r2,
-                              const float2* w2, const double* g_s, double* c_s, cudaStream_t s)
+                              const float2* w2, const double* g_s, double* c_s, int det, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
-    size_t smem = sizeof(double) * (size_t)(max_cols > 0 ? max_cols : 1) + sizeof(int) * (size_t)max_area;
+    size_t smem = sizeof(double) * (det ? 1 : (size_t)(max_cols > 0 ? max_cols : 1)) +
+                  sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, g_s, c_s, lowp);
+    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, g_s, c_s, lowp, det);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1076,15 +1090,16 @@ cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blk
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
                           const float2* w2, const double* c_s, const float2* c2, double* g_s,
-                          const double* c_sb, const float2* c2b, double* g_sb, cudaStream_t s)
+                          const double* c_sb, const float2* c2b, double* g_sb, int det, cudaStream_t s)
 {
     if (nblk <= 0) return cudaSuccess;
-    const size_t acc = (g_sb ? 2 : 1) *
+    if (det && mode == 2) mode = 1;   // no FP32 slot sums in the deterministic mode
+    const size_t acc = det ? 1 : (g_sb ? 2 : 1) *
                        (mode == 2 ? (size_t)kDirSlotFloats / 2 : (size_t)(max_rows > 0 ? max_rows : 1));
     size_t smem = sizeof(double) * acc + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, c_sb, c2b, g_sb, mode);
+    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, c_sb, c2b, g_sb, mode, det);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -188,11 +188,13 @@ __global__ void k_sort_finish(const uint64_t* __restrict__ keys, int64_t n, doub
 }
 
 __global__ void k_gather(const double* __restrict__ c, const int32_t* __restrict__ perm, int64_t n,
-                         int stride, int comp, double* __restrict__ out, float2* __restrict__ out2)
+                         int stride, int comp, const int* __restrict__ nexp, double* __restrict__ out,
+                         float2* __restrict__ out2)
 {
+    const int e = -*nexp;   // inputs scaled by 2^-E (exact)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = c[(int64_t)perm[i] * stride + comp];
+        const double v = scalbn(c[(int64_t)perm[i] * stride + comp], e);
         out[i] = v;
         if (out2) {
             const float h = (float)v;
@@ -213,11 +215,12 @@ __global__ void k_split_f64(const double* __restrict__ x, int64_t n, float2* __r
 }
 
 __global__ void k_scatter(const double* __restrict__ gs, const int32_t* __restrict__ perm, int64_t m,
-                          int stride, int comp, double* __restrict__ g)
+                          int stride, int comp, const int* __restrict__ nexp, double* __restrict__ g)
 {
+    const int e = *nexp;   // back to the input's scale (exact)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
-        g[(int64_t)perm[i] * stride + comp] = gs[i];
+        g[(int64_t)perm[i] * stride + comp] = scalbn(gs[i], e);
 }
 
 // First j in [lo, hi) with wk * r_j > z (hi if none); r ascending.
@@ -424,11 +427,11 @@ cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
+cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp, const int* nexp,
                           double* out, float2* out2, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, out, out2);
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, nexp, out, out2);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -441,11 +444,11 @@ cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
+cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp, const int* nexp,
                            double* g, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    k_scatter<<<grid_for(m, 256), 256, 0, s>>>(gs, perm, m, stride, comp, g);
+    k_scatter<<<grid_for(m, 256), 256, 0, s>>>(gs, perm, m, stride, comp, nexp, g);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "nuht.h"
+#include "det_acc.cuh"
 
 namespace nuht {
 
@@ -36,6 +37,8 @@ struct ProbParams {
     int M, L, Q;   // Q = 2M
     int qs;        // terms q >= qs are small enough to be summed in FP32
     int ntop;      // largest Bessel index used by the local evaluation
+    int fxs;       // accumulation: kFxOff = FP64 atomics; else the deterministic mode's
+                   // fixed-point scale (contributions add round(v 2^fxs) exactly), set per call
     int8_t dcp[kMaxQ / 2];   // per Hankel pair (2p, 2p+1): double-float degrees of the interpolation sums
     double z;      // crossover
     double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
@@ -210,11 +213,17 @@ cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int6
                                 const double* r_s, const double* w_s, double* bl, double4* ba, cudaStream_t s);
 cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
                                   int nprob, int32_t* s_out, cudaStream_t s);
-cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
+// per-call input scaling (k_det.cu): *nexp = the exponent of the largest |x_i|
+// (gather scales the inputs by 2^-nexp, scatter the outputs back), and in the
+// deterministic mode every problem's fixed-point scale fxs; Fx128 sums to FP64
+cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long long* mx, int* nexp, ProbParams* probs,
+                               int nprob, int det, cudaStream_t s);
+cudaError_t launch_fx_decode(const void* src, double* dst, int64_t count, const ProbParams* probs, cudaStream_t s);
+cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp, const int* nexp,
                           double* out, float2* out2, cudaStream_t s);
 cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg, int total, Tile* out,
                                 cudaStream_t s);
-cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
+cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp, const int* nexp,
                            double* g, cudaStream_t s);
 
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
@@ -238,7 +247,7 @@ int direct_sum_mode(double eps, int max_rows, int max_cols);
 cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_rows,
                           int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
                           const float2* w2, const double* c_s, const float2* c2, double* g_s,
-                          const double* c_sb, const float2* c2b, double* g_sb, cudaStream_t s);
+                          const double* c_sb, const float2* c2b, double* g_sb, int det, cudaStream_t s);
 int local_adj_threads(int ntop_max);
 // g_sb / momb (both null, or both set): a second real component's g and
 // moments, summed with the same Bessel values.
@@ -251,7 +260,7 @@ cudaError_t launch_local_adj_eval(const ProbParams* probs, const LocalBlock* blk
                                   cudaStream_t s);
 cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_cols,
                               int max_area, int lowp, const double* r_s, const double* w_s, const float2* r2,
-                              const float2* w2, const double* g_s, double* c_s, cudaStream_t s);
+                              const float2* w2, const double* g_s, double* c_s, int det, cudaStream_t s);
 // x[i] as double-float (hi, lo)
 cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream_t s);
 // Per spreading tile, the path of k_asy_spread (plan time; modes[ntiles]).

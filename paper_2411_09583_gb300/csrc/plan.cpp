@@ -107,6 +107,14 @@ struct nuht_plan_s {
     float2* d_cs2b = nullptr;
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
+    // per-call input scaling: the largest input magnitude (bits) and its exponent
+    unsigned long long* d_mx = nullptr;
+    int* d_nexp = nullptr;
+    // deterministic mode: exact fixed-point (Fx128) accumulators in place of
+    // the FP64 targets of the atomics (same element indices)
+    bool det = false;
+    Fx128 *f_gs = nullptr, *f_gsb = nullptr, *f_cs = nullptr, *f_csb = nullptr;
+    Fx128 *f_mom = nullptr, *f_momb = nullptr, *f_gb = nullptr, *f_tg = nullptr;
 
     int n_loc = 0, n_tmom = 0, n_teval = 0;
     int n_asy = 0, n_tspread = 0, n_tinterp = 0, n_fblock = 0, n_fsmall = 0, n_fa = 0, n_fb = 0;
@@ -790,6 +798,15 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
     size_t a_sm = A.reserve<int32_t>((size_t)ntile[LIST_SPREAD]);
     size_t a_csb = A.reserve<double>(n), a_gsb = A.reserve<double>(m), a_cs2b = A.reserve<float2>(n);
+    const bool det = P->opt.deterministic != 0;
+    const size_t f1 = 1;
+    size_t a_fgs = A.reserve<Fx128>(det ? (size_t)m : f1), a_fgsb = A.reserve<Fx128>(det ? (size_t)m : f1);
+    size_t a_fcs = A.reserve<Fx128>(det ? (size_t)n : f1), a_fcsb = A.reserve<Fx128>(det ? (size_t)n : f1);
+    size_t a_fmom = A.reserve<Fx128>(det ? (size_t)P->mom_len : f1);
+    size_t a_fmomb = A.reserve<Fx128>(det ? (size_t)P->mom_len : f1);
+    size_t a_fgb = A.reserve<Fx128>(det ? 2 * (size_t)P->gb_len : f1);
+    size_t a_ftg = A.reserve<Fx128>(det ? 2 * (size_t)P->gq_len : f1);
+    size_t a_mx = A.reserve<unsigned long long>(1), a_nexp = A.reserve<int>(1);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
@@ -879,6 +896,15 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
     P->d_r2 = (float2*)(D + a_r2); P->d_w2 = (float2*)(D + a_w2); P->d_cs2 = (float2*)(D + a_cs2);
     P->d_csb = (double*)(D + a_csb); P->d_gsb = (double*)(D + a_gsb); P->d_cs2b = (float2*)(D + a_cs2b);
+    P->det = det;
+    if (det) {
+        P->f_gs = (Fx128*)(D + a_fgs); P->f_gsb = (Fx128*)(D + a_fgsb);
+        P->f_cs = (Fx128*)(D + a_fcs); P->f_csb = (Fx128*)(D + a_fcsb);
+        P->f_mom = (Fx128*)(D + a_fmom); P->f_momb = (Fx128*)(D + a_fmomb);
+        P->f_gb = (Fx128*)(D + a_fgb); P->f_tg = (Fx128*)(D + a_ftg);
+    }
+    P->d_mx = (unsigned long long*)(D + a_mx);
+    P->d_nexp = (int*)(D + a_nexp);
     NUHT_CK(launch_split_f64(P->d_r, n, P->d_r2, s));
     NUHT_CK(launch_split_f64(P->d_w, m, P->d_w2, s));
     P->d_tg = (double2*)(D + a_tg); P->d_bq = (float4*)(D + a_bq);
@@ -960,6 +986,7 @@ static int init_problem(ProbParams& pp, int nu, double eps, int m_terms, int64_t
     pp = ProbParams{};
     pp.nu = anu;
     pp.sgn = (nu < 0 && (anu & 1)) ? -1 : 1;
+    pp.fxs = kFxOff;   // the deterministic mode sets its scale per call
     int rc = choose_params(anu, eps, m_terms, &pp.M, &pp.z, &pp.L);
     if (rc != NUHT_OK) return rc;
     pp.Q = 2 * pp.M;
@@ -1007,8 +1034,9 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
     if (o.min_size < 1 || o.min_size > NUHT_MAX_MIN_SIZE || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
+    if (o.deterministic != 0 && o.deterministic != 1) return NUHT_ERR_INVALID_ARG;
     if (o.spread_tile != 0 && (o.spread_tile < 64 || o.spread_tile > 256 || o.spread_tile % 32))
         return NUHT_ERR_INVALID_ARG;
     if (o.timing < NUHT_TIMING_OFF || o.timing > NUHT_TIMING_SERIAL) return NUHT_ERR_INVALID_ARG;
@@ -1103,9 +1131,20 @@ int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, 
 // pair: 0 this component's local and direct blocks; 1 also those of the next
 // component (d_csb, d_cs2b into d_gsb, one Bessel evaluation for both); 2 none
 // (applied with the previous component).
+// Accumulation targets of the kernels: the FP64 array, or in the
+// deterministic mode its exact fixed-point twin (passed under the same
+// pointer type; the kernels index it by element through Accum).
+static double* acc_target(nuht_plan_t P, double* f64, Fx128* fx) { return P->det ? (double*)fx : f64; }
+static size_t acc_bytes(nuht_plan_t P, int64_t count) { return (size_t)count * (P->det ? sizeof(Fx128) : sizeof(double)); }
+
 static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
 {
     const int mask = P->opt.class_mask;
+    double* gs = acc_target(P, P->d_gs, P->f_gs);
+    double* gsb = acc_target(P, P->d_gsb, P->f_gsb);
+    double* mom_acc = acc_target(P, P->d_mom, P->f_mom);
+    double* momb_acc = acc_target(P, P->d_momb, P->f_momb);
+    double2* gb_acc = (double2*)acc_target(P, (double*)P->d_gb, P->f_gb);
     const bool loc = (mask & 1) && P->n_loc && pair != 2, dir = (mask & 4) && P->n_dir && pair != 2;
     const bool asy = (mask & 2) && P->n_asy;
     // The block classes share no scratch and only add into g (FP64 atomics):
@@ -1117,43 +1156,46 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     const cudaStream_t ls = fk.local(s), as = fk.asy(s);
     if (loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
-        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
+        NUHT_CK(cudaMemsetAsync(mom_acc, 0, acc_bytes(P, P->mom_len), ls));
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
-                                     P->d_cs2, P->d_mom, ls));
+                                     P->d_cs2, mom_acc, ls));
+        if (P->det) NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
         double* momb = pair == 1 ? P->d_momb : nullptr;
         if (momb) {
-            NUHT_CK(cudaMemsetAsync(momb, 0, sizeof(double) * P->mom_len, ls));
+            NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
             NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
-                                         P->d_cs2b, momb, ls));
+                                         P->d_cs2b, momb_acc, ls));
+            if (P->det) NUHT_CK(launch_fx_decode(P->f_momb, P->d_momb, P->mom_len, P->d_prob, ls));
         }
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
-        double* gsb = momb ? P->d_gsb : nullptr;
+        double* gsb_l = momb ? gsb : nullptr;
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_local_eval_f32(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                          P->eval_threads, P->d_w2, P->d_mom, P->d_gs, momb, gsb, ls));
+                                          P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb_l, ls));
         else
             NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                      P->eval_threads, P->d_w2, P->d_mom, P->d_gs, momb, gsb, ls));
+                                      P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb_l, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area,
                               direct_sum_mode(P->eps, P->max_dir_rows, P->max_dir_cols), P->d_r, P->d_w,
-                              P->d_r2, P->d_w2, P->d_cs, P->d_cs2, P->d_gs, pair == 1 ? P->d_csb : nullptr,
-                              pair == 1 ? P->d_cs2b : nullptr, pair == 1 ? P->d_gsb : nullptr, ls));
+                              P->d_r2, P->d_w2, P->d_cs, P->d_cs2, gs, pair == 1 ? P->d_csb : nullptr,
+                              pair == 1 ? P->d_cs2b : nullptr, pair == 1 ? gsb : nullptr, P->det ? 1 : 0, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
-        NUHT_CK(cudaMemsetAsync(P->d_gb, 0, sizeof(double2) * P->gb_len, as));
+        NUHT_CK(cudaMemsetAsync(gb_acc, 0, acc_bytes(P, 2 * P->gb_len), as));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                          P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, as));
+                                          P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc, as));
         else
             NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, P->d_gb, as));
+                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc, as));
+        if (P->det) NUHT_CK(launch_fx_decode(P->f_gb, (double*)P->d_gb, 2 * P->gb_len, P->d_prob, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
         const bool lowp = P->opt.precision == NUHT_PREC_MIXED;   // FP32 butterflies
@@ -1168,10 +1210,10 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                          P->d_w, P->d_w2, P->d_gq, P->d_gs, as));
+                                          P->d_w, P->d_w2, P->d_gq, gs, as));
         else
             NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
-                                      P->d_w, P->d_w2, P->d_gq, P->d_gs, as));
+                                      P->d_w, P->d_w2, P->d_gq, gs, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
@@ -1190,6 +1232,12 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         return NUHT_OK;
     }
     NUHT_TRY(ensure_events(P, comps));
+    // c scaled by a power of two from its largest magnitude (and, in the
+    // deterministic mode, the fixed-point scale)
+    NUHT_CK(launch_input_scale(c, P->n * comps, P->d_mx, P->d_nexp, P->d_prob, (int)P->probs.size(), P->det ? 1 : 0,
+                               s));
+    double* gs = acc_target(P, P->d_gs, P->f_gs);
+    double* gsb = acc_target(P, P->d_gsb, P->f_gsb);
     // real components in pairs share the local and direct blocks' Bessel
     // evaluations: the first of a pair applies those blocks to both, the
     // second starts from the second's local and direct sums (d_gsb)
@@ -1199,18 +1247,19 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
         if (pair == 2)
-            NUHT_CK(cudaMemcpyAsync(P->d_gs, P->d_gsb, sizeof(double) * P->m, cudaMemcpyDeviceToDevice, s));
+            NUHT_CK(cudaMemcpyAsync(gs, gsb, acc_bytes(P, P->m), cudaMemcpyDeviceToDevice, s));
         else
-            NUHT_CK(cudaMemsetAsync(P->d_gs, 0, sizeof(double) * P->m, s));
-        NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_cs, P->d_cs2, s));
+            NUHT_CK(cudaMemsetAsync(gs, 0, acc_bytes(P, P->m), s));
+        NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_nexp, P->d_cs, P->d_cs2, s));
         if (pair == 1) {
-            NUHT_CK(cudaMemsetAsync(P->d_gsb, 0, sizeof(double) * P->m, s));
-            NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp + 1, P->d_csb, P->d_cs2b, s));
+            NUHT_CK(cudaMemsetAsync(gsb, 0, acc_bytes(P, P->m), s));
+            NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp + 1, P->d_nexp, P->d_csb, P->d_cs2b, s));
         }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_forward(P, T, s, pair));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
-        NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, g, s));
+        if (P->det) NUHT_CK(launch_fx_decode(P->f_gs, P->d_gs, P->m, P->d_prob, s));
+        NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, P->d_nexp, g, s));
         NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
     }
     return NUHT_OK;
@@ -1224,6 +1273,11 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
 static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
 {
     const int mask = P->opt.class_mask;
+    double* cs = acc_target(P, P->d_cs, P->f_cs);
+    double* csb = acc_target(P, P->d_csb, P->f_csb);
+    double* mom_acc = acc_target(P, P->d_mom, P->f_mom);
+    double* momb_acc = acc_target(P, P->d_momb, P->f_momb);
+    double2* tg_acc = (double2*)acc_target(P, (double*)P->d_tg, P->f_tg);
     const bool loc = (mask & 1) && P->n_loc && pair != 2, dir = (mask & 4) && P->n_dir;
     const bool asy = (mask & 2) && P->n_asy;
     // local and direct blocks beside the asymptotic pipeline, as in apply_forward
@@ -1233,32 +1287,38 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     if (loc) {
         const int thr = local_adj_threads(P->ntop_max);
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
-        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
+        NUHT_CK(cudaMemsetAsync(mom_acc, 0, acc_bytes(P, P->mom_len), ls));
         double* momb = pair == 1 ? P->d_momb : nullptr;
-        if (momb) NUHT_CK(cudaMemsetAsync(momb, 0, sizeof(double) * P->mom_len, ls));
+        if (momb) NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
         NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, thr,
-                                         P->d_w2, P->d_gs, P->d_mom, momb ? P->d_gsb : nullptr, momb, ls));
+                                         P->d_w2, P->d_gs, mom_acc, momb ? P->d_gsb : nullptr,
+                                         momb ? momb_acc : nullptr, ls));
+        if (P->det) {
+            NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
+            if (momb) NUHT_CK(launch_fx_decode(P->f_momb, P->d_momb, P->mom_len, P->d_prob, ls));
+        }
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
         NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, P->d_mom,
-                                      P->d_cs, ls));
+                                      cs, ls));
         if (momb)
             NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, momb,
-                                          P->d_csb, ls));
+                                          csb, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
         NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->max_dir_area,
-                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_r2, P->d_w2, P->d_gs, P->d_cs,
-                                  ls));
+                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_r2, P->d_w2, P->d_gs, cs,
+                                  P->det ? 1 : 0, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
     if (asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
-        NUHT_CK(cudaMemsetAsync(P->d_tg, 0, sizeof(double2) * P->gq_len, as));
+        NUHT_CK(cudaMemsetAsync(tg_acc, 0, acc_bytes(P, 2 * P->gq_len), as));
         NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab, P->d_w,
-                                      P->d_gs, P->d_tg, as));
+                                      P->d_gs, tg_acc, as));
+        if (P->det) NUHT_CK(launch_fx_decode(P->f_tg, (double*)P->d_tg, 2 * P->gq_len, P->d_prob, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->max_fblock_pts, P->tab,
@@ -1271,7 +1331,7 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
         NUHT_CK(launch_asy_adj_interp(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab, P->d_r,
-                                      P->d_bq, P->d_cs, as));
+                                      P->d_bq, cs, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
@@ -1290,6 +1350,12 @@ int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_com
         return NUHT_OK;
     }
     NUHT_TRY(ensure_events(P, comps));
+    // g scaled by a power of two from its largest magnitude (and, in the
+    // deterministic mode, the fixed-point scale)
+    NUHT_CK(launch_input_scale(g, P->m * comps, P->d_mx, P->d_nexp, P->d_prob, (int)P->probs.size(), P->det ? 1 : 0,
+                               s));
+    double* cs = acc_target(P, P->d_cs, P->f_cs);
+    double* csb = acc_target(P, P->d_csb, P->f_csb);
     // real components in pairs share the local blocks' Bessel evaluations: the
     // first of a pair sums both components' moments, the second starts from
     // its local sums (d_csb)
@@ -1299,18 +1365,19 @@ int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_com
         const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
         if (pair == 2)
-            NUHT_CK(cudaMemcpyAsync(P->d_cs, P->d_csb, sizeof(double) * P->n, cudaMemcpyDeviceToDevice, s));
+            NUHT_CK(cudaMemcpyAsync(cs, csb, acc_bytes(P, P->n), cudaMemcpyDeviceToDevice, s));
         else
-            NUHT_CK(cudaMemsetAsync(P->d_cs, 0, sizeof(double) * P->n, s));
-        NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_gs, nullptr, s));
+            NUHT_CK(cudaMemsetAsync(cs, 0, acc_bytes(P, P->n), s));
+        NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_nexp, P->d_gs, nullptr, s));
         if (pair == 1) {
-            NUHT_CK(cudaMemsetAsync(P->d_csb, 0, sizeof(double) * P->n, s));
-            NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp + 1, P->d_gsb, nullptr, s));
+            NUHT_CK(cudaMemsetAsync(csb, 0, acc_bytes(P, P->n), s));
+            NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp + 1, P->d_nexp, P->d_gsb, nullptr, s));
         }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_adjoint(P, T, s, pair));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
-        NUHT_CK(launch_scatter(P->d_cs, P->d_pr, P->n, comps, comp, c, s));
+        if (P->det) NUHT_CK(launch_fx_decode(P->f_cs, P->d_cs, P->n, P->d_prob, s));
+        NUHT_CK(launch_scatter(P->d_cs, P->d_pr, P->n, comps, comp, P->d_nexp, c, s));
         NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
     }
     return NUHT_OK;
