@@ -497,7 +497,7 @@ def run_grad(dev, steps):
                       "err_over_tol": max(err_c, err_r) / 10.0, "rows": 100,
                       "against": "oracle direct sums (orders nu, nu - 1, nu + 1) at 100 sampled points"},
             "ms_per_step": t, "value": 2e6 / (t * 1e-3), "unit": UNIT, "opts": opts,
-            "step": "plan + forward + adjoint (dL/dc) + plans and adjoints of orders nu-1, nu+1 (dL/dr)"}
+            "step": "plan + forward + adjoint (dL/dc) + derivative plan (orders nu-1, nu+1 on the sorted points, no re-sort) and its adjoint (dL/dr)"}
 
 
 def run_stress(dev, steps):

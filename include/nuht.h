@@ -26,7 +26,9 @@
  * contiguous.  The caller owns every array it passes.  Calls are ordered on
  * the given CUDA stream (a cudaStream_t passed as void*; NULL = the legacy
  * default stream) and may return before the GPU work finishes, except
- * nuht_plan, which synchronises the stream once (the subdivision runs on the
+ * nuht_plan, nuht_plan_many and nuht_plan_deriv, which wait once for the
+ * sizes of the block lists (the sort, the subdivision and the list build run
+ * on the device; only lists beyond the device capacity are built on the
  * host), and the *_host entry points, which synchronise before returning.
  *
  * Errors: every int-returning call returns NUHT_OK (0) or one of the
@@ -183,6 +185,39 @@ int nuht_execute(nuht_plan_t p, const double *c, double *g, int nvec, int is_com
  * A is real, so the adjoint is the transpose. */
 int nuht_adjoint(nuht_plan_t p, const double *g, double *c, int nvec, int is_complex,
                  void *stream);
+
+/* Derivative plan of a plan built by nuht_plan (not a batch): the transforms
+ * of orders nu - 1 and nu + 1 on the base plan's points and frequencies, for
+ * the gradients with respect to r and omega.  With J_nu' = (J_{nu-1} -
+ * J_{nu+1}) / 2 (DLMF 10.6.1; J_{-1} = -J_1 as for any negative order):
+ *
+ *   d/dr_j     sum_k e_k g_k = c_j sum_k e_k omega_k J_nu'(omega_k r_j)
+ *   d/domega_k sum_k e_k g_k = e_k sum_j c_j r_j J_nu'(omega_k r_j)
+ *
+ * The two orders run as two problems of one plan whose sums are added with
+ * opposite signs, so each gradient is one pass of the pipeline.  The plan
+ * reuses the base plan's sorted values and permutations (no second sort or
+ * domain check); it needs |nu| + 1 <= 100 (else NUHT_ERR_UNSUPPORTED) and uses
+ * the base plan's eps and options.  The base plan may be destroyed afterwards.
+ * nuht_execute / nuht_adjoint reject a derivative plan (NUHT_ERR_INVALID_ARG);
+ * nuht_info reports its two problems' combined sizes (2n, 2m) and the orders
+ * of nu - 1. */
+int nuht_plan_deriv(nuht_plan_t *out, nuht_plan_t base, void *stream);
+
+/* Gradient with respect to r through a derivative plan d:
+ *   grad_r[j] = sum_v c[j][v] sum_k e[k][v] omega_k J_nu'(omega_k r_j)
+ * for nvec real vectors (c: n x nvec, e: m x nvec, row-major as in
+ * nuht_execute); grad_r has n entries (caller's r order), overwritten.  The
+ * weighting by omega and by c and the half difference of the two orders run
+ * in the gather and scatter kernels.  Accuracy: within 10 eps |c_j| ||omega e||_1
+ * per vector. */
+int nuht_grad_r(nuht_plan_t d, const double *c, const double *e, double *grad_r, int nvec, void *stream);
+
+/* Gradient with respect to omega through a derivative plan d:
+ *   grad_omega[k] = sum_v e[k][v] sum_j c[j][v] r_j J_nu'(omega_k r_j)
+ * (same conventions; grad_omega has m entries, caller's omega order).
+ * Accuracy: within 10 eps |e_k| ||r c||_1 per vector. */
+int nuht_grad_omega(nuht_plan_t d, const double *c, const double *e, double *grad_omega, int nvec, void *stream);
 
 /* Whole transform from HOST arrays: copies r, omega, c to the device, plans,
  * executes, copies g (m x nvec real) back to the host array g, and frees the

@@ -33,7 +33,8 @@ EXPORTED = ["nuht_default_opts", "nuht_choose_params", "nuht_plan", "nuht_execut
             "nuht_get_permutations", "nuht_destroy", "nuht_strerror",
             "nuht_last_cuda_error", "nuht_stage_times", "nuht_stage_name",
             "nuht_kernel_launch_count", "nuht_local_apply_noalloc", "nuht_plan_many",
-            "nuht_probe_alu", "nuht_check_blocks"]
+            "nuht_probe_alu", "nuht_check_blocks", "nuht_plan_deriv", "nuht_grad_r",
+            "nuht_grad_omega"]
 NUM_STAGES = 8
 
 
@@ -129,5 +130,11 @@ def lib():
         L.nuht_probe_alu.restype = i
         L.nuht_check_blocks.argtypes = [i, d, i, p, i64, p, i64, i, p, p, i64]
         L.nuht_check_blocks.restype = i
+        L.nuht_plan_deriv.argtypes = [ctypes.POINTER(p), p, p]
+        L.nuht_plan_deriv.restype = i
+        L.nuht_grad_r.argtypes = [p, p, p, p, i, p]
+        L.nuht_grad_r.restype = i
+        L.nuht_grad_omega.argtypes = [p, p, p, p, i, p]
+        L.nuht_grad_omega.restype = i
         _lib = L
         return _lib

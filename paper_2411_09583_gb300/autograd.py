@@ -3,12 +3,14 @@
     g = A(r, omega) c,   A(k, j) = J_nu(omega_k r_j)
 
 backward, for an upstream gradient e = dL/dg:
-    dL/dc     = A^T e                                      (nuht_adjoint)
-    dL/dr_j   = c_j [A_{nu-1}^T (omega e) - A_{nu+1}^T (omega e)]_j / 2
-    dL/domega = e [A_{nu-1} (r c) - A_{nu+1} (r c)] / 2
-using J_nu' = (J_{nu-1} - J_{nu+1}) / 2 (DLMF 10.6.1) with plans of orders
-nu - 1 and nu + 1 on the same points (J_{-1} = -J_1 is handled by the library).
-Real c for the r / omega gradients; every transform runs in libnuht.so.
+    dL/dc     = A^T e                                            (nuht_adjoint)
+    dL/dr_j   = c_j sum_k e_k omega_k J_nu'(omega_k r_j)         (nuht_grad_r)
+    dL/domega = e_k sum_j c_j r_j J_nu'(omega_k r_j)             (nuht_grad_omega)
+with J_nu' = (J_{nu-1} - J_{nu+1}) / 2 (DLMF 10.6.1), through a derivative
+plan of orders nu - 1 and nu + 1 built from the forward plan's sorted points
+and frequencies (nuht_plan_deriv).  The weightings, the half difference and the
+sum over vectors run in the library's kernels; this module only passes tensors.
+Real c for the r / omega gradients.
 """
 import torch
 
@@ -34,16 +36,11 @@ class _NUHT(torch.autograd.Function):
         if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
             if c.is_complex():
                 raise NotImplementedError("r / omega gradients are for real c")
-            with Plan(ctx.nu - 1, r.detach(), omega.detach(), ctx.eps, **ctx.opts) as pm, \
-                    Plan(ctx.nu + 1, r.detach(), omega.detach(), ctx.eps, **ctx.opts) as pp:
+            with ctx.plan.deriv() as d:
                 if ctx.needs_input_grad[1]:
-                    we = (omega.detach()[:, None] * e if e.dim() > 1 else omega.detach() * e).contiguous()
-                    d = 0.5 * (pm.adjoint(we) - pp.adjoint(we))
-                    grad_r = (c.detach() * d).reshape(c.shape[0], -1).sum(dim=1)
+                    grad_r = d.grad_r(c.detach(), e)
                 if ctx.needs_input_grad[2]:
-                    rc = (r.detach()[:, None] * c.detach() if c.dim() > 1 else r.detach() * c.detach())
-                    d = 0.5 * (pm.execute(rc.contiguous()) - pp.execute(rc.contiguous()))
-                    grad_w = (e * d).reshape(e.shape[0], -1).sum(dim=1)
+                    grad_w = d.grad_omega(c.detach(), e)
         return grad_c, grad_r, grad_w, None, None, None
 
 

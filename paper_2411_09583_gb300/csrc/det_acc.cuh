@@ -8,10 +8,10 @@
 // complement accumulator (two 64-bit words, the carry out of the low word
 // added to the high word).  Integer addition is associative, so the sum, and
 // the double it is converted to at the end, is the same whatever order the
-// additions happen in.  The scale s comes from a bound on the inputs (set per
-// execute on the device): every partial sum stays below 2^126 and one
-// contribution's rounding is at most 2^-(s+1), about 2^-54 of the largest
-// input coefficient.
+// additions happen in.  Every call scales its input vector by a power of two
+// so that its largest magnitude lies in [1, 2) (input_exponent); the scale s is
+// then fixed (kFxScale): every partial sum stays below 2^126 and one
+// contribution's rounding is at most 2^-(s+1), 2^-54 of the largest input.
 #pragma once
 
 #include <climits>
@@ -91,6 +91,24 @@ __device__ __forceinline__ double fx_decode(Fx128 a, int s)
     const double v = scalbn(fma((double)a.hi, 18446744073709551616.0, (double)a.lo), -s);
     return neg ? -v : v;
 }
+
+// E with v in [2^E, 2^(E+1)) for the bit pattern b of a non-negative double v
+// (0 for v = 0): the execute kernels see their inputs scaled by 2^-E of the
+// largest input magnitude, so that it lies in [1, 2).
+__device__ __forceinline__ int input_exponent(unsigned long long b)
+{
+    if (b == 0) return 0;
+    const int ebits = (int)((b >> 52) & 0x7ff);
+    if (ebits) return ebits - 1023;
+    return -1023 - (__clzll((long long)(b & 0xfffffffffffffull)) - 12);   // subnormal: its leading bit
+}
+
+// Deterministic-mode scale of the fixed-point sums: with inputs scaled into
+// [1, 2) in magnitude, a sum of at most 2^31 of them, each carried with a
+// factor of at most 2^40 (every expansion and grid value of the transform
+// stays far below that), is below 2^125 times 2^-53, so round(v 2^53) stays in
+// the signed 128-bit range, and one contribution rounds by at most 2^-54.
+constexpr int kFxScale = 53;
 
 // An accumulation target: an FP64 array (FP64 atomics), or in the
 // deterministic mode an Fx128 array with the same element indices.

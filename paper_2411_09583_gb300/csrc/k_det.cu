@@ -34,30 +34,6 @@ __global__ void __launch_bounds__(kDetThreads) k_absmax_bits(const double* __res
     if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
 }
 
-// *nexp = E with max |x| in [2^E, 2^(E+1)) (0 for an all-zero input); the
-// kernels see x 2^-E, whose largest magnitude is in [1, 2).  Deterministic
-// mode: fxs = 53, so that a sum of at most 2^31 scaled inputs, each carried
-// with a factor of at most 2^40 (every expansion and grid value of the
-// transform stays far below that), is below 2^125, inside the signed 128-bit
-// range, and one contribution rounds by at most 2^-54.
-__global__ void k_set_scale(const unsigned long long* __restrict__ mx, int* __restrict__ nexp,
-                            ProbParams* __restrict__ probs, int nprob, int det)
-{
-    const unsigned long long b = *mx;
-    const int ebits = (int)((b >> 52) & 0x7ff);
-    int e = 0;
-    if (b != 0) {
-        e = (ebits ? ebits : 1) - 1023;
-        if (!ebits) {   // subnormal: the exponent of the leading bit
-            const int lz = __clzll((long long)(b & 0xfffffffffffffull)) - 12;
-            e -= lz + 1;
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nexp = e;
-    if (det)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nprob; i += gridDim.x * blockDim.x) probs[i].fxs = 53;
-}
-
 __global__ void __launch_bounds__(kDetThreads) k_fx_decode(const Fx128* __restrict__ src, double* __restrict__ dst,
                                                            int64_t count, const ProbParams* __restrict__ probs)
 {
@@ -78,8 +54,7 @@ int grid_for(int64_t count)
 
 }  // namespace
 
-cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long long* mx, int* nexp, ProbParams* probs,
-                               int nprob, int det, cudaStream_t s)
+cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long long* mx, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -87,8 +62,6 @@ cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long lon
         k_absmax_bits<<<grid_for(count), kDetThreads, 0, s>>>(x, count, mx);
         count_launches(1);
     }
-    k_set_scale<<<(nprob + 255) / 256, 256, 0, s>>>(mx, nexp, probs, nprob, det);
-    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -188,10 +188,10 @@ __global__ void k_sort_finish(const uint64_t* __restrict__ keys, int64_t n, doub
 }
 
 __global__ void k_gather(const double* __restrict__ c, const int32_t* __restrict__ perm, int64_t n,
-                         int stride, int comp, const int* __restrict__ nexp, double* __restrict__ out,
-                         float2* __restrict__ out2)
+                         int stride, int comp, const unsigned long long* __restrict__ mx,
+                         double* __restrict__ out, float2* __restrict__ out2)
 {
-    const int e = -*nexp;   // inputs scaled by 2^-E (exact)
+    const int e = -input_exponent(*mx);   // inputs scaled by 2^-E (exact)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double v = scalbn(c[(int64_t)perm[i] * stride + comp], e);
@@ -215,12 +215,70 @@ __global__ void k_split_f64(const double* __restrict__ x, int64_t n, float2* __r
 }
 
 __global__ void k_scatter(const double* __restrict__ gs, const int32_t* __restrict__ perm, int64_t m,
-                          int stride, int comp, const int* __restrict__ nexp, double* __restrict__ g)
+                          int stride, int comp, const unsigned long long* __restrict__ mx,
+                          double* __restrict__ g)
 {
-    const int e = *nexp;   // back to the input's scale (exact)
+    const int e = input_exponent(*mx);   // back to the input's scale (exact)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x)
         g[(int64_t)perm[i] * stride + comp] = scalbn(gs[i], e);
+}
+
+// Derivative plans (two problems over two copies of the sorted arrays): the
+// input x (user order) weighted by the sorted values ws (r for the omega
+// gradient, omega for the r gradient), scaled by 2^-E, into both copies.
+__global__ void k_gather_deriv(const double* __restrict__ x, const int32_t* __restrict__ perm,
+                               const double* __restrict__ ws, int64_t nb, int stride, int comp,
+                               const unsigned long long* __restrict__ mx, double* __restrict__ out,
+                               float2* __restrict__ out2)
+{
+    const int e = -input_exponent(*mx);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * nb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = i < nb ? i : i - nb;
+        const double v = scalbn(x[(int64_t)perm[i0] * stride + comp] * ws[i0], e);
+        out[i] = v;
+        if (out2) {
+            const float h = (float)v;
+            out2[i] = make_float2(h, (float)(v - (double)h));
+        }
+    }
+}
+
+// The largest |x_u ws_i| (u = perm[i], every vector), as bits (k_absmax_bits).
+__global__ void k_absmax_weighted(const double* __restrict__ x, const int32_t* __restrict__ perm,
+                                  const double* __restrict__ ws, int64_t nb, int comps,
+                                  unsigned long long* __restrict__ mx)
+{
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb * comps;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = i / comps, v = i - i0 * comps;
+        const double a = x[(int64_t)perm[i0] * comps + v] * ws[i0];
+        const unsigned long long b = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+        m = b > m ? b : m;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
+// out[u] (+)= y_u (gs[k] + gs[mb + k]) / 2 back at the input's scale, u = perm[k]:
+// the two problems' sums (orders nu - 1 and nu + 1, the second negated) give
+// J_nu' = (J_{nu-1} - J_{nu+1}) / 2 (DLMF 10.6.1); vectors after the first add on.
+__global__ void k_scatter_deriv(const double* __restrict__ gs, const int32_t* __restrict__ perm, int64_t mb,
+                                int stride, int comp, const unsigned long long* __restrict__ mx,
+                                const double* __restrict__ y, double* __restrict__ out)
+{
+    const int e = input_exponent(*mx) - 1;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < mb;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = perm[k];
+        const double v = scalbn(gs[k] + gs[mb + k], e) * y[u * stride + comp];
+        out[u] = comp == 0 ? v : out[u] + v;
+    }
 }
 
 // First j in [lo, hi) with wk * r_j > z (hi if none); r ascending.
@@ -427,11 +485,39 @@ cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp, const int* nexp,
-                          double* out, float2* out2, cudaStream_t s)
+cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
+                          const unsigned long long* mx, double* out, float2* out2, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, nexp, out, out2);
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(c, perm, n, stride, comp, mx, out, out2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_deriv(const double* x, const int32_t* perm, const double* ws, int64_t nb, int stride,
+                                int comp, const unsigned long long* mx, double* out, float2* out2, cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_gather_deriv<<<grid_for(2 * nb, 256), 256, 0, s>>>(x, perm, ws, nb, stride, comp, mx, out, out2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax_weighted(const double* x, const int32_t* perm, const double* ws, int64_t nb, int comps,
+                                   unsigned long long* mx, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || nb <= 0) return e;
+    k_absmax_weighted<<<grid_for(nb * comps, 256), 256, 0, s>>>(x, perm, ws, nb, comps, mx);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_deriv(const double* gs, const int32_t* perm, int64_t mb, int stride, int comp,
+                                 const unsigned long long* mx, const double* y, double* out, cudaStream_t s)
+{
+    if (mb <= 0) return cudaSuccess;
+    k_scatter_deriv<<<grid_for(mb, 256), 256, 0, s>>>(gs, perm, mb, stride, comp, mx, y, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -444,11 +530,11 @@ cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp, const int* nexp,
-                           double* g, cudaStream_t s)
+cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
+                           const unsigned long long* mx, double* g, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    k_scatter<<<grid_for(m, 256), 256, 0, s>>>(gs, perm, m, stride, comp, nexp, g);
+    k_scatter<<<grid_for(m, 256), 256, 0, s>>>(gs, perm, m, stride, comp, mx, g);
     count_launches(1);
     return cudaGetLastError();
 }

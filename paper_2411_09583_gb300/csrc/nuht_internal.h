@@ -38,7 +38,7 @@ struct ProbParams {
     int qs;        // terms q >= qs are small enough to be summed in FP32
     int ntop;      // largest Bessel index used by the local evaluation
     int fxs;       // accumulation: kFxOff = FP64 atomics; else the deterministic mode's
-                   // fixed-point scale (contributions add round(v 2^fxs) exactly), set per call
+                   // fixed-point scale kFxScale (contributions add round(v 2^fxs) exactly)
     int8_t dcp[kMaxQ / 2];   // per Hankel pair (2p, 2p+1): double-float degrees of the interpolation sums
     double z;      // crossover
     double cphi, sphi;           // cos, sin of phi = -(2 nu + 1) pi / 4
@@ -213,18 +213,25 @@ cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int6
                                 const double* r_s, const double* w_s, double* bl, double4* ba, cudaStream_t s);
 cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
                                   int nprob, int32_t* s_out, cudaStream_t s);
-// per-call input scaling (k_det.cu): *nexp = the exponent of the largest |x_i|
-// (gather scales the inputs by 2^-nexp, scatter the outputs back), and in the
-// deterministic mode every problem's fixed-point scale fxs; Fx128 sums to FP64
-cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long long* mx, int* nexp, ProbParams* probs,
-                               int nprob, int det, cudaStream_t s);
+// per-call input scaling (k_det.cu): *mx = the bits of the largest |x_i|
+// (gather scales the inputs by 2^-E of it, scatter the outputs back,
+// input_exponent); Fx128 sums to FP64
+cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long long* mx, cudaStream_t s);
 cudaError_t launch_fx_decode(const void* src, double* dst, int64_t count, const ProbParams* probs, cudaStream_t s);
-cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp, const int* nexp,
-                          double* out, float2* out2, cudaStream_t s);
+// derivative plans (k_sort.cu): weighted gather into both problems' copies,
+// the weighted input maximum, and the half difference scattered times y
+cudaError_t launch_gather_deriv(const double* x, const int32_t* perm, const double* ws, int64_t nb, int stride,
+                                int comp, const unsigned long long* mx, double* out, float2* out2, cudaStream_t s);
+cudaError_t launch_absmax_weighted(const double* x, const int32_t* perm, const double* ws, int64_t nb, int comps,
+                                   unsigned long long* mx, cudaStream_t s);
+cudaError_t launch_scatter_deriv(const double* gs, const int32_t* perm, int64_t mb, int stride, int comp,
+                                 const unsigned long long* mx, const double* y, double* out, cudaStream_t s);
+cudaError_t launch_gather(const double* c, const int32_t* perm, int64_t n, int stride, int comp,
+                          const unsigned long long* mx, double* out, float2* out2, cudaStream_t s);
 cudaError_t launch_expand_tiles(const Seg* segs, const int32_t* prefix, int nseg, int total, Tile* out,
                                 cudaStream_t s);
-cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp, const int* nexp,
-                           double* g, cudaStream_t s);
+cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int stride, int comp,
+                           const unsigned long long* mx, double* g, cudaStream_t s);
 
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                  int ntiles, int lmax, const float2* r2, const float2* c2,

@@ -71,6 +71,11 @@ struct SegList {
 
 struct nuht_plan_s {
     int nu_user = 0;
+    // derivative plan (nuht_plan_deriv): problems nu - 1 and nu + 1 (the
+    // second with its sign flipped) over two copies of the base plan's sorted
+    // points and frequencies; n_base, m_base are the base plan's sizes
+    bool deriv = false;
+    int64_t n_base = 0, m_base = 0;
     double eps = 0.0;
     nuht_opts opt{};
     int64_t n = 0, m = 0;
@@ -107,9 +112,8 @@ struct nuht_plan_s {
     float2* d_cs2b = nullptr;
     double *d_es = nullptr, *d_ph = nullptr;
     double2* d_tw = nullptr;
-    // per-call input scaling: the largest input magnitude (bits) and its exponent
+    // per-call input scaling: the bits of the largest input magnitude
     unsigned long long* d_mx = nullptr;
-    int* d_nexp = nullptr;
     // deterministic mode: exact fixed-point (Fx128) accumulators in place of
     // the FP64 targets of the atomics (same element indices)
     bool det = false;
@@ -523,9 +527,13 @@ static int verify_lists(nuht_plan_t P)
         if (rc_ != NUHT_OK) return rc_; \
     } while (0)
 
-static int build_plan(nuht_plan_t P, const double* r, const double* omega)
+// src: build from the sorted arrays and permutations of that plan, repeated
+// once per problem (derivative plans), instead of checking and sorting r and omega.
+static int build_plan(nuht_plan_t P, const double* r, const double* omega, const nuht_plan_s* src = nullptr)
 {
     auto clk = std::chrono::steady_clock::now();
+    if (P->opt.deterministic)
+        for (ProbParams& q : P->probs) q.fxs = kFxScale;
     cudaStream_t s = P->stream;
     const int64_t n = P->n, m = P->m;
     const int nprob = (int)P->probs.size();
@@ -596,13 +604,27 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         NUHT_CK(cudaMemcpyAsync(d_roff, ro, ob, cudaMemcpyHostToDevice, s));
         NUHT_CK(cudaMemcpyAsync(d_woff, wo, ob, cudaMemcpyHostToDevice, s));
     }
-    NUHT_CK(launch_check_domain(r, n, d_flag, s));
-    NUHT_CK(launch_check_domain(omega, m, d_flag + 1, s));
     double* r_s = (double*)(sort_mem + o_r);
     double* w_s = (double*)(sort_mem + o_w);
     int32_t* pr = (int32_t*)(sort_mem + o_pr);
     int32_t* pw = (int32_t*)(sort_mem + o_pw);
     int32_t* stair = (int32_t*)(sort_mem + o_st);
+    if (src) {
+        // already checked and sorted: one copy of the source's arrays per problem
+        for (int ip = 0; ip < nprob; ++ip) {
+            const ProbParams& q = probs[ip];
+            if (q.n) {
+                NUHT_CK(cudaMemcpyAsync(r_s + q.r_off, src->d_r, sizeof(double) * q.n, cudaMemcpyDeviceToDevice, s));
+                NUHT_CK(cudaMemcpyAsync(pr + q.r_off, src->d_pr, sizeof(int32_t) * q.n, cudaMemcpyDeviceToDevice, s));
+            }
+            if (q.m) {
+                NUHT_CK(cudaMemcpyAsync(w_s + q.w_off, src->d_w, sizeof(double) * q.m, cudaMemcpyDeviceToDevice, s));
+                NUHT_CK(cudaMemcpyAsync(pw + q.w_off, src->d_pw, sizeof(int32_t) * q.m, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+    } else {
+    NUHT_CK(launch_check_domain(r, n, d_flag, s));
+    NUHT_CK(launch_check_domain(omega, m, d_flag + 1, s));
     // the two sorts are independent: omega on the auxiliary stream
     {
         Aux* ax = nullptr;
@@ -618,6 +640,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         NUHT_CK(ej);
         NUHT_CK(er);
         NUHT_CK(ek);
+    }
     }
     if (nprob == 1) NUHT_CK(launch_staircase(r_s, n, w_s, m, probs[0].z, stair, s));
     else NUHT_CK(launch_staircase_many(r_s, w_s, m, d_prb, nprob, stair, s));
@@ -806,7 +829,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
     size_t a_fmomb = A.reserve<Fx128>(det ? (size_t)P->mom_len : f1);
     size_t a_fgb = A.reserve<Fx128>(det ? 2 * (size_t)P->gb_len : f1);
     size_t a_ftg = A.reserve<Fx128>(det ? 2 * (size_t)P->gq_len : f1);
-    size_t a_mx = A.reserve<unsigned long long>(1), a_nexp = A.reserve<int>(1);
+    size_t a_mx = A.reserve<unsigned long long>(1);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
@@ -904,7 +927,6 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega)
         P->f_gb = (Fx128*)(D + a_fgb); P->f_tg = (Fx128*)(D + a_ftg);
     }
     P->d_mx = (unsigned long long*)(D + a_mx);
-    P->d_nexp = (int*)(D + a_nexp);
     NUHT_CK(launch_split_f64(P->d_r, n, P->d_r2, s));
     NUHT_CK(launch_split_f64(P->d_w, m, P->d_w2, s));
     P->d_tg = (double2*)(D + a_tg); P->d_bq = (float4*)(D + a_bq);
@@ -986,7 +1008,7 @@ static int init_problem(ProbParams& pp, int nu, double eps, int m_terms, int64_t
     pp = ProbParams{};
     pp.nu = anu;
     pp.sgn = (nu < 0 && (anu & 1)) ? -1 : 1;
-    pp.fxs = kFxOff;   // the deterministic mode sets its scale per call
+    pp.fxs = kFxOff;   // FP64 atomics; build_plan sets kFxScale for the deterministic mode
     int rc = choose_params(anu, eps, m_terms, &pp.M, &pp.z, &pp.L);
     if (rc != NUHT_OK) return rc;
     pp.Q = 2 * pp.M;
@@ -1220,27 +1242,19 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     return NUHT_OK;
 }
 
-int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_complex, void* stream)
+// The component loop of a forward transform: per real component, gather(comp,
+// cs, cs2) writes the sorted, scaled input, apply_forward adds every block
+// class into g (sorted), scatter(comp) writes it out.  Real components in
+// pairs share the local and direct blocks' Bessel evaluations: the first of a
+// pair applies those blocks to both, the second starts from the second's local
+// and direct sums (d_gsb).
+extern "C++" {
+template <class Gather, class Scatter>
+static int drive_forward(nuht_plan_t P, int comps, cudaStream_t s, Gather&& gather, Scatter&& scatter)
 {
-    if (!P || nvec < 1) return NUHT_ERR_INVALID_ARG;
-    if ((P->n > 0 && !c) || (P->m > 0 && !g)) return NUHT_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int comps = nvec * (is_complex ? 2 : 1);
-    if (P->m == 0) return NUHT_OK;
-    if (P->n == 0) {
-        NUHT_CK(cudaMemsetAsync(g, 0, sizeof(double) * P->m * comps, s));
-        return NUHT_OK;
-    }
     NUHT_TRY(ensure_events(P, comps));
-    // c scaled by a power of two from its largest magnitude (and, in the
-    // deterministic mode, the fixed-point scale)
-    NUHT_CK(launch_input_scale(c, P->n * comps, P->d_mx, P->d_nexp, P->d_prob, (int)P->probs.size(), P->det ? 1 : 0,
-                               s));
     double* gs = acc_target(P, P->d_gs, P->f_gs);
     double* gsb = acc_target(P, P->d_gsb, P->f_gsb);
-    // real components in pairs share the local and direct blocks' Bessel
-    // evaluations: the first of a pair applies those blocks to both, the
-    // second starts from the second's local and direct sums (d_gsb)
     const bool pairs = ((P->opt.class_mask & 4) && P->n_dir > 0) || ((P->opt.class_mask & 1) && P->n_loc > 0);
     for (int comp = 0; comp < comps; ++comp) {
         StageTimer T{P, comp};
@@ -1250,19 +1264,39 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
             NUHT_CK(cudaMemcpyAsync(gs, gsb, acc_bytes(P, P->m), cudaMemcpyDeviceToDevice, s));
         else
             NUHT_CK(cudaMemsetAsync(gs, 0, acc_bytes(P, P->m), s));
-        NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp, P->d_nexp, P->d_cs, P->d_cs2, s));
+        NUHT_CK(gather(comp, P->d_cs, P->d_cs2));
         if (pair == 1) {
             NUHT_CK(cudaMemsetAsync(gsb, 0, acc_bytes(P, P->m), s));
-            NUHT_CK(launch_gather(c, P->d_pr, P->n, comps, comp + 1, P->d_nexp, P->d_csb, P->d_cs2b, s));
+            NUHT_CK(gather(comp + 1, P->d_csb, P->d_cs2b));
         }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_forward(P, T, s, pair));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_gs, P->d_gs, P->m, P->d_prob, s));
-        NUHT_CK(launch_scatter(P->d_gs, P->d_pw, P->m, comps, comp, P->d_nexp, g, s));
+        NUHT_CK(scatter(comp));
         NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
     }
     return NUHT_OK;
+}
+}  // extern "C++"
+
+int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_complex, void* stream)
+{
+    if (!P || nvec < 1 || P->deriv) return NUHT_ERR_INVALID_ARG;
+    if ((P->n > 0 && !c) || (P->m > 0 && !g)) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int comps = nvec * (is_complex ? 2 : 1);
+    if (P->m == 0) return NUHT_OK;
+    if (P->n == 0) {
+        NUHT_CK(cudaMemsetAsync(g, 0, sizeof(double) * P->m * comps, s));
+        return NUHT_OK;
+    }
+    // c is scaled by a power of two from its largest magnitude
+    NUHT_CK(launch_input_scale(c, P->n * comps, P->d_mx, s));
+    return drive_forward(
+        P, comps, s,
+        [&](int cp, double* o, float2* o2) { return launch_gather(c, P->d_pr, P->n, comps, cp, P->d_mx, o, o2, s); },
+        [&](int cp) { return launch_scatter(P->d_gs, P->d_pw, P->m, comps, cp, P->d_mx, g, s); });
 }
 
 // Transpose of apply_forward: g (sorted, d_gs) -> c (sorted, d_cs).  Each
@@ -1338,27 +1372,18 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     return NUHT_OK;
 }
 
-int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_complex, void* stream)
+// The component loop of an adjoint transform (drive_forward transposed):
+// gather(comp, gs) writes the sorted, scaled input, apply_adjoint adds every
+// block class into c (sorted), scatter(comp) writes it out.  Pairs share the
+// local blocks' Bessel evaluations: the first sums both components' moments,
+// the second starts from its local sums (d_csb).
+extern "C++" {
+template <class Gather, class Scatter>
+static int drive_adjoint(nuht_plan_t P, int comps, cudaStream_t s, Gather&& gather, Scatter&& scatter)
 {
-    if (!P || nvec < 1) return NUHT_ERR_INVALID_ARG;
-    if ((P->m > 0 && !g) || (P->n > 0 && !c)) return NUHT_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int comps = nvec * (is_complex ? 2 : 1);
-    if (P->n == 0) return NUHT_OK;
-    if (P->m == 0) {
-        NUHT_CK(cudaMemsetAsync(c, 0, sizeof(double) * P->n * comps, s));
-        return NUHT_OK;
-    }
     NUHT_TRY(ensure_events(P, comps));
-    // g scaled by a power of two from its largest magnitude (and, in the
-    // deterministic mode, the fixed-point scale)
-    NUHT_CK(launch_input_scale(g, P->m * comps, P->d_mx, P->d_nexp, P->d_prob, (int)P->probs.size(), P->det ? 1 : 0,
-                               s));
     double* cs = acc_target(P, P->d_cs, P->f_cs);
     double* csb = acc_target(P, P->d_csb, P->f_csb);
-    // real components in pairs share the local blocks' Bessel evaluations: the
-    // first of a pair sums both components' moments, the second starts from
-    // its local sums (d_csb)
     const bool pairs = (P->opt.class_mask & 1) && P->n_loc > 0;
     for (int comp = 0; comp < comps; ++comp) {
         StageTimer T{P, comp};
@@ -1368,19 +1393,110 @@ int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_com
             NUHT_CK(cudaMemcpyAsync(cs, csb, acc_bytes(P, P->n), cudaMemcpyDeviceToDevice, s));
         else
             NUHT_CK(cudaMemsetAsync(cs, 0, acc_bytes(P, P->n), s));
-        NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp, P->d_nexp, P->d_gs, nullptr, s));
+        NUHT_CK(gather(comp, P->d_gs));
         if (pair == 1) {
             NUHT_CK(cudaMemsetAsync(csb, 0, acc_bytes(P, P->n), s));
-            NUHT_CK(launch_gather(g, P->d_pw, P->m, comps, comp + 1, P->d_nexp, P->d_gsb, nullptr, s));
+            NUHT_CK(gather(comp + 1, P->d_gsb));
         }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
         NUHT_TRY(apply_adjoint(P, T, s, pair));
         NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_cs, P->d_cs, P->n, P->d_prob, s));
-        NUHT_CK(launch_scatter(P->d_cs, P->d_pr, P->n, comps, comp, P->d_nexp, c, s));
+        NUHT_CK(scatter(comp));
         NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
     }
     return NUHT_OK;
+}
+}  // extern "C++"
+
+int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_complex, void* stream)
+{
+    if (!P || nvec < 1 || P->deriv) return NUHT_ERR_INVALID_ARG;
+    if ((P->m > 0 && !g) || (P->n > 0 && !c)) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int comps = nvec * (is_complex ? 2 : 1);
+    if (P->n == 0) return NUHT_OK;
+    if (P->m == 0) {
+        NUHT_CK(cudaMemsetAsync(c, 0, sizeof(double) * P->n * comps, s));
+        return NUHT_OK;
+    }
+    // g is scaled by a power of two from its largest magnitude
+    NUHT_CK(launch_input_scale(g, P->m * comps, P->d_mx, s));
+    return drive_adjoint(
+        P, comps, s,
+        [&](int cp, double* o) { return launch_gather(g, P->d_pw, P->m, comps, cp, P->d_mx, o, nullptr, s); },
+        [&](int cp) { return launch_scatter(P->d_cs, P->d_pr, P->n, comps, cp, P->d_mx, c, s); });
+}
+
+int nuht_plan_deriv(nuht_plan_t* out, nuht_plan_t base, void* stream)
+{
+    if (!out) return NUHT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!base || base->deriv || base->probs.size() != 1) return NUHT_ERR_INVALID_ARG;
+    const int nu = base->nu_user;
+    if (nu - 1 < -100 || nu + 1 > 100) return NUHT_ERR_UNSUPPORTED;
+    nuht_plan_t P = new (std::nothrow) nuht_plan_s();
+    if (!P) return NUHT_ERR_NOMEM;
+    P->deriv = true;
+    P->n_base = base->n;
+    P->m_base = base->m;
+    P->nu_user = nu;
+    P->eps = base->eps;
+    P->opt = base->opt;
+    P->n = 2 * base->n;
+    P->m = 2 * base->m;
+    P->stream = (cudaStream_t)stream;
+    P->probs.resize(2);
+    int rc = init_problem(P->probs[0], nu - 1, P->eps, P->opt.m_terms, base->n, base->m, 0, 0);
+    if (rc == NUHT_OK)
+        rc = init_problem(P->probs[1], nu + 1, P->eps, P->opt.m_terms, base->n, base->m, base->n, base->m);
+    if (rc != NUHT_OK) { delete P; return rc; }
+    P->probs[1].sgn = -P->probs[1].sgn;   // its sums enter with -J_{nu+1}
+    P->w = nufft_width(P->eps);
+    rc = build_plan(P, nullptr, nullptr, base);
+    if (rc != NUHT_OK) { nuht_destroy(P); return rc; }
+    *out = P;
+    return NUHT_OK;
+}
+
+int nuht_grad_omega(nuht_plan_t D, const double* c, const double* e, double* grad_omega, int nvec, void* stream)
+{
+    if (!D || !D->deriv || nvec < 1) return NUHT_ERR_INVALID_ARG;
+    const int64_t nb = D->n_base, mb = D->m_base;
+    if ((nb > 0 && !c) || (mb > 0 && (!e || !grad_omega))) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mb == 0) return NUHT_OK;
+    if (nb == 0) {
+        NUHT_CK(cudaMemsetAsync(grad_omega, 0, sizeof(double) * mb, s));
+        return NUHT_OK;
+    }
+    // the forward transform of r c, scaled by a power of two from its largest magnitude
+    NUHT_CK(launch_absmax_weighted(c, D->d_pr, D->d_r, nb, nvec, D->d_mx, s));
+    return drive_forward(
+        D, nvec, s,
+        [&](int cp, double* o, float2* o2) {
+            return launch_gather_deriv(c, D->d_pr, D->d_r, nb, nvec, cp, D->d_mx, o, o2, s);
+        },
+        [&](int cp) { return launch_scatter_deriv(D->d_gs, D->d_pw, mb, nvec, cp, D->d_mx, e, grad_omega, s); });
+}
+
+int nuht_grad_r(nuht_plan_t D, const double* c, const double* e, double* grad_r, int nvec, void* stream)
+{
+    if (!D || !D->deriv || nvec < 1) return NUHT_ERR_INVALID_ARG;
+    const int64_t nb = D->n_base, mb = D->m_base;
+    if ((nb > 0 && (!c || !grad_r)) || (mb > 0 && !e)) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nb == 0) return NUHT_OK;
+    if (mb == 0) {
+        NUHT_CK(cudaMemsetAsync(grad_r, 0, sizeof(double) * nb, s));
+        return NUHT_OK;
+    }
+    // the adjoint transform of omega e, scaled by a power of two from its largest magnitude
+    NUHT_CK(launch_absmax_weighted(e, D->d_pw, D->d_w, mb, nvec, D->d_mx, s));
+    return drive_adjoint(
+        D, nvec, s,
+        [&](int cp, double* o) { return launch_gather_deriv(e, D->d_pw, D->d_w, mb, nvec, cp, D->d_mx, o, nullptr, s); },
+        [&](int cp) { return launch_scatter_deriv(D->d_cs, D->d_pr, nb, nvec, cp, D->d_mx, c, grad_r, s); });
 }
 
 int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega, int64_t m, double eps,

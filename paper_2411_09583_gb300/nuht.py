@@ -165,6 +165,11 @@ class Plan:
         """c = A^T g; g has m rows, c has n rows."""
         return self._apply(N.lib().nuht_adjoint, g, self.m, self.n, out, "nuht_adjoint")
 
+    def deriv(self):
+        """The derivative plan (orders nu - 1 and nu + 1 on the same, already
+        sorted points and frequencies) for gradients in r and omega."""
+        return DerivPlan(self)
+
     def info(self):
         inf = N.NuhtPlanInfo()
         N.check(N.lib().nuht_info(self._h, ctypes.byref(inf)), "nuht_info")
@@ -196,6 +201,57 @@ class Plan:
                                               pw.ctypes.data_as(ctypes.c_void_p)),
                 "nuht_get_permutations")
         return pr, pw
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            N.lib().nuht_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class DerivPlan:
+    """Gradients of sum_k e_k g_k, g = A c, with respect to r and omega
+    (nuht_plan_deriv / nuht_grad_r / nuht_grad_omega); real c and e."""
+
+    def __init__(self, base):
+        self.n, self.m, self.device = base.n, base.m, base.device
+        self._stream = base._stream
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(N.lib().nuht_plan_deriv(ctypes.byref(self._h), base._h, _stream_ptr(self._stream)),
+                    "nuht_plan_deriv")
+
+    def _grad(self, fn, c, e, rows, what):
+        c, e = _dev_f64(c, "c"), _dev_f64(e, "e")
+        if c.dtype != torch.float64 or e.dtype != torch.float64:
+            raise TypeError("%s: real c and e" % what)
+        if c.shape[0] != self.n or e.shape[0] != self.m or c.shape[1:] != e.shape[1:]:
+            raise ValueError("%s: c must have %d rows and e %d, with the same vectors" % (what, self.n, self.m))
+        nvec = 1 if c.dim() == 1 else int(np.prod(c.shape[1:]))
+        out = torch.empty(rows, dtype=torch.float64, device=c.device)
+        with torch.cuda.device(self.device):
+            N.check(fn(self._h, ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+                       ctypes.c_void_p(out.data_ptr()), nvec, _stream_ptr(self._stream)), what)
+        return out
+
+    def grad_r(self, c, e):
+        """sum_v c[j, v] sum_k e[k, v] omega_k J_nu'(omega_k r_j), n entries."""
+        return self._grad(N.lib().nuht_grad_r, c, e, self.n, "nuht_grad_r")
+
+    def grad_omega(self, c, e):
+        """sum_v e[k, v] sum_j c[j, v] r_j J_nu'(omega_k r_j), m entries."""
+        return self._grad(N.lib().nuht_grad_omega, c, e, self.m, "nuht_grad_omega")
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

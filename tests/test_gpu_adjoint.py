@@ -227,3 +227,92 @@ def test_three_vectors_pair_and_single(precision, eps, nu):
         cv, ev = np.ascontiguousarray(c[:, v]), np.ascontiguousarray(e[:, v])
         assert np.max(np.abs(g[rows, v] - oracle.direct_rows(nu, r, omega, cv, rows))) <= tol(eps, cv)
         assert np.max(np.abs(ca[cols, v] - oracle.direct_rows(nu, omega, r, ev, cols))) <= tol(eps, ev)
+
+
+def _deriv_oracle(nu, r, omega, c, e):
+    """(grad_r, grad_omega) of sum_k e_k g_k by the oracle's direct sums of
+    orders nu - 1 and nu + 1 (J_nu' = (J_{nu-1} - J_{nu+1}) / 2); c, e (n, v), (m, v)."""
+    c2, e2 = c.reshape(r.size, -1), e.reshape(omega.size, -1)
+    gr = np.zeros(r.size)
+    gw = np.zeros(omega.size)
+    for v in range(c2.shape[1]):
+        we, rc = omega * e2[:, v], r * c2[:, v]
+        gr += c2[:, v] * 0.5 * (oracle.direct(nu - 1, omega, r, we) - oracle.direct(nu + 1, omega, r, we))
+        gw += e2[:, v] * 0.5 * (oracle.direct(nu - 1, r, omega, rc) - oracle.direct(nu + 1, r, omega, rc))
+    return gr, gw
+
+
+@pytest.mark.parametrize("nu,nvec,det", [(0, 1, False), (1, 1, False), (-3, 1, False), (7, 3, False),
+                                         (20, 1, False), (2, 2, True)])
+def test_derivative_plan_gradients(nu, nvec, det):
+    # nuht_plan_deriv + nuht_grad_r / nuht_grad_omega against the oracle, per
+    # entry within 10 eps |c_j| ||omega e||_1 (r) and 10 eps |e_k| ||r c||_1
+    # (omega), summed over the vectors
+    from paper_2411_09583_gb300 import Plan
+    eps = 1e-10
+    r, omega, _ = uniform_problem(1800, 1600, omega_max=2500.0, seed=820 + abs(nu))
+    rng = np.random.default_rng(821)
+    shape_c = (r.size,) if nvec == 1 else (r.size, nvec)
+    shape_e = (omega.size,) if nvec == 1 else (omega.size, nvec)
+    c, e = rng.standard_normal(shape_c), rng.standard_normal(shape_e)
+    with Plan(nu, to_dev(r), to_dev(omega), eps, deterministic=det) as p:
+        with p.deriv() as d:
+            assert d.n == r.size and d.m == omega.size
+            gr = d.grad_r(to_dev(c), to_dev(e)).cpu().numpy()
+            gw = d.grad_omega(to_dev(c), to_dev(e)).cpu().numpy()
+            if det:
+                assert np.array_equal(gr, d.grad_r(to_dev(c), to_dev(e)).cpu().numpy())
+    ref_r, ref_w = _deriv_oracle(nu, r, omega, c, e)
+    c2, e2 = c.reshape(r.size, -1), e.reshape(omega.size, -1)
+    bound_r = sum(10 * eps * np.abs(c2[:, v]) * np.abs(omega * e2[:, v]).sum() for v in range(nvec))
+    bound_w = sum(10 * eps * np.abs(e2[:, v]) * np.abs(r * c2[:, v]).sum() for v in range(nvec))
+    assert np.all(np.abs(gr - ref_r) <= bound_r + 1e-300)
+    assert np.all(np.abs(gw - ref_w) <= bound_w + 1e-300)
+
+
+def test_derivative_plan_outlives_base_and_rejects_misuse():
+    import ctypes
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300 import _native as N
+    eps = 1e-9
+    r, omega, c = uniform_problem(700, 900, omega_max=1500.0, seed=830)
+    e = np.random.default_rng(831).standard_normal(omega.size)
+    p = Plan(4, to_dev(r), to_dev(omega), eps)
+    d = p.deriv()
+    lib = N.lib()
+    # a derivative plan is not an ordinary plan
+    out = to_dev(np.zeros(omega.size))
+    assert lib.nuht_execute(d._h, ctypes.c_void_p(to_dev(c).data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                            1, 0, None) == N.NUHT_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.nuht_plan_deriv(ctypes.byref(h), d._h, None) == N.NUHT_ERR_INVALID_ARG
+    assert lib.nuht_grad_r(p._h, None, None, None, 1, None) == N.NUHT_ERR_INVALID_ARG
+    p.close()                          # the derivative plan keeps its own copies
+    gr = d.grad_r(to_dev(c), to_dev(e)).cpu().numpy()
+    d.close()
+    ref_r, _ = _deriv_oracle(4, r, omega, c, e)
+    assert np.all(np.abs(gr - ref_r) <= 10 * eps * np.abs(c) * np.abs(omega * e).sum() + 1e-300)
+    with Plan(100, to_dev(r), to_dev(omega), 1e-8) as p100:
+        assert lib.nuht_plan_deriv(ctypes.byref(h), p100._h, None) == N.NUHT_ERR_UNSUPPORTED
+    with Plan.many([0, 1], to_dev(np.concatenate([r, r])), [r.size, r.size],
+                   to_dev(np.concatenate([omega, omega])), [omega.size, omega.size], 1e-8) as bp:
+        assert lib.nuht_plan_deriv(ctypes.byref(h), bp._h, None) == N.NUHT_ERR_INVALID_ARG
+
+
+def test_full_size_gradients_sampled():
+    # n = m = 1e6, nu = 0, eps = 1e-10 (the differentiation workload): both
+    # gradients on 100 sampled entries against the oracle
+    from paper_2411_09583_gb300 import Plan
+    eps = 1e-10
+    r, omega, c = uniform_problem(1_000_000, 1_000_000, omega_max=1e5, seed=6)
+    e = np.random.default_rng(7).standard_normal(omega.size)
+    with Plan(0, to_dev(r), to_dev(omega), eps) as p, p.deriv() as d:
+        gr = d.grad_r(to_dev(c), to_dev(e)).cpu().numpy()
+        gw = d.grad_omega(to_dev(c), to_dev(e)).cpu().numpy()
+    cols = sample_rows(r.size, 100, seed=832)
+    rows = sample_rows(omega.size, 100, seed=833)
+    we, rc = omega * e, r * c
+    ref_r = c[cols] * 0.5 * (oracle.direct_rows(-1, omega, r, we, cols) - oracle.direct_rows(1, omega, r, we, cols))
+    ref_w = e[rows] * 0.5 * (oracle.direct_rows(-1, r, omega, rc, rows) - oracle.direct_rows(1, r, omega, rc, rows))
+    assert np.all(np.abs(gr[cols] - ref_r) <= 10 * eps * np.abs(c[cols]) * np.abs(we).sum())
+    assert np.all(np.abs(gw[rows] - ref_w) <= 10 * eps * np.abs(e[rows]) * np.abs(rc).sum())
