@@ -373,6 +373,30 @@ def run_batched(dev, steps):
         ex_ms.append(s0.elapsed_time(s1))
     info = bp.info()
     bp.close()
+    # the same batch with the local blocks in one persistent launch
+    bpp = Plan.many(nus, dr, n, dw, m, 1e-8, persistent=True, **best)
+    gp = torch.empty(sum(m), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            bpp.execute(dc, out=gp)
+    stream.wait_stream(side)
+    graph_p = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_p):
+        bpp.execute(dc, out=gp)
+    for _ in range(3):
+        graph_p.replay()
+    torch.cuda.synchronize(dev)
+    exp_ms = []
+    for _ in range(steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        graph_p.replay()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        exp_ms.append(s0.elapsed_time(s1))
+    pers_status = bpp.status()
+    bpp.close()
     exe = statistics.median(ex_ms)
     pl = statistics.median(plan_ms)
     # accuracy of the graph's result: 10 sampled rows of every problem
@@ -390,6 +414,8 @@ def run_batched(dev, steps):
             "unit": UNIT, "execute": "one CUDA graph replay (one launch per stage over all problems)",
             "autotuned_opts": best, "autotune_default_execute_ms": default_ms[0] if default_ms else None,
             "autotune_best_execute_ms": table[0][0],
+            "execute_graph_ms_persistent_local": statistics.median(exp_ms),
+            "persistent_status": pers_status,
             "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
             "error": {"err_over_eps_c1": worst, "err_over_tol": worst / 10.0, "rows": 10 * len(probs),
                       "against": "oracle direct sum, 10 sampled rows of every problem (worst problem)"}}
@@ -728,7 +754,7 @@ def run_ours(a):
            "basis": "execute: compulsory bytes (c, sorted r and omega, g) over the execute-only time; "
                     "dominant kernel: ncu DRAM bytes per launch over its live launch time"}
 
-    extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = extra_det = None
+    extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = extra_det = extra_pers = None
     if not a.no_extra and ws == 1:
         # the same workload at the other order of the scaled plain-NUHT
         # configuration (nu = 10), same options and timing as the main line
@@ -783,6 +809,35 @@ def run_ours(a):
                      "error": sampled_error(a.nu, r, omega, c, g_d.cpu().numpy(), a.eps,
                                             sample_rows(a.m, 200, seed=93)),
                      "step": "plan + execute with deterministic=1, same workload and options as the main line"}
+        # the local blocks in one persistent launch (device work queue with
+        # bounded per-block waits) against the two launches: execute time and
+        # the local stage alone (every stage in order on one stream)
+        pers = {}
+        for flag in (False, True):
+            with Plan(a.nu, dr, dw, a.eps, persistent=flag, **opts) as pp_:
+                for _ in range(2):
+                    pp_.execute(dc)
+                ex = []
+                for _ in range(a.steps):
+                    flush.zero_()
+                    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    s0.record(stream)
+                    pp_.execute(dc)
+                    s1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ex.append(s0.elapsed_time(s1))
+                st_ok = pp_.status()
+            loc_alone = []
+            for _ in range(3):
+                flush.zero_()
+                with Plan(a.nu, dr, dw, a.eps, persistent=flag, timing="serial", **opts) as pt:
+                    pt.execute(dc)
+                    stt = pt.stage_times()
+                loc_alone.append(stt["local_moments"] + stt["local_eval"])
+            pers["persistent" if flag else "two_launches"] = {
+                "execute_ms": statistics.median(ex), "local_stage_ms_alone": statistics.median(loc_alone),
+                "status": st_ok}
+        extra_pers = pers
         extra_batched = run_batched(dev, a.steps)
         extra_mixed = run_mixed(dev, a.steps)
         extra_grad = run_grad(dev, a.steps)
@@ -836,6 +891,7 @@ def run_ours(a):
                 "stress": extra_stress,
                 "other_order": extra_order,
                 "deterministic": extra_det,
+                "persistent_local": extra_pers,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],

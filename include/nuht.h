@@ -50,7 +50,7 @@ extern "C" {
 #define NUHT_ERR_DOMAIN      2   /* some r_j or omega_k is negative, NaN or infinite */
 #define NUHT_ERR_NOMEM       3   /* a device or host allocation failed */
 #define NUHT_ERR_CUDA        4   /* a CUDA runtime call failed (see nuht_last_cuda_error) */
-#define NUHT_ERR_TIMEOUT     5   /* a bounded device wait gave up (reserved) */
+#define NUHT_ERR_TIMEOUT     5   /* a bounded device wait gave up (reported by nuht_status) */
 #define NUHT_ERR_UNSUPPORTED 6   /* option combination not built (e.g. order |nu| > 100) */
 #define NUHT_ERR_SCRATCH     7   /* request exceeds the fixed scratch of nuht_local_apply_noalloc */
 #define NUHT_ERR_BAD_BLOCKS  8   /* a block work list failed its check (nuht_check_blocks) */
@@ -98,7 +98,13 @@ typedef struct {
                           does not matter; the same inputs on the same GPU then give the same
                           bits on every run.  Slower (more atomics, no FP32 row sums in the
                           direct blocks, extra device memory).  Default 0 (FP64 atomics). */
-    int reserved[4];   /* must be zero */
+    int persistent;    /* 1 = the local blocks' moments and evaluation in one persistent
+                          launch: resident CTAs take moment tiles, then evaluation tiles,
+                          from a device queue, and an evaluation tile waits (a bounded
+                          poll) until its block's moments are complete.  A wait that gives
+                          up records NUHT_ERR_TIMEOUT for nuht_status.  Not used with
+                          deterministic = 1.  Default 0 (two launches). */
+    int reserved[3];   /* must be zero */
 } nuht_opts;
 
 /* Execute stages, in launch order (nuht_stage_times / nuht_stage_name). */
@@ -271,6 +277,14 @@ int nuht_stage_times(nuht_plan_t p, double *ms, int cap);
 
 /* Static name of stage i ("gather", "local_moments", ...), or NULL. */
 const char *nuht_stage_name(int i);
+
+/* Errors found on the device since the last call for this plan: waits for
+ * the stream, then returns NUHT_OK or the recorded status (NUHT_ERR_TIMEOUT
+ * when a bounded device wait of a persistent launch gave up; that launch
+ * skipped the work behind the wait, so its output is invalid) and clears it.
+ * The execute and adjoint calls return before their kernels run, so a device
+ * error surfaces here. */
+int nuht_status(nuht_plan_t p, void *stream);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter). */

@@ -34,7 +34,7 @@ EXPORTED = ["nuht_default_opts", "nuht_choose_params", "nuht_plan", "nuht_execut
             "nuht_last_cuda_error", "nuht_stage_times", "nuht_stage_name",
             "nuht_kernel_launch_count", "nuht_local_apply_noalloc", "nuht_plan_many",
             "nuht_probe_alu", "nuht_check_blocks", "nuht_plan_deriv", "nuht_grad_r",
-            "nuht_grad_omega"]
+            "nuht_grad_omega", "nuht_status"]
 NUM_STAGES = 8
 
 
@@ -43,7 +43,7 @@ class NuhtOpts(ctypes.Structure):
                 ("n_split_cand", ctypes.c_int), ("m_terms", ctypes.c_int),
                 ("class_mask", ctypes.c_int), ("timing", ctypes.c_int),
                 ("spread_tile", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("persistent", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class NuhtPlanInfo(ctypes.Structure):
@@ -136,5 +136,7 @@ def lib():
         L.nuht_grad_r.restype = i
         L.nuht_grad_omega.argtypes = [p, p, p, p, i, p]
         L.nuht_grad_omega.restype = i
+        L.nuht_status.argtypes = [p, p]
+        L.nuht_status.restype = i
         _lib = L
         return _lib

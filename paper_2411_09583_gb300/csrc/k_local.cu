@@ -89,13 +89,11 @@ __device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int 
 // column of partial moments (compensated double-float accumulators) in shared
 // memory, acc[l * blockDim + tid]; the columns are summed at the end
 // (reduce_columns_add) and added to the block's moments.
-__global__ void __launch_bounds__(kMomThreads)
-k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                const Tile* __restrict__ tiles, const float2* __restrict__ r2,
-                const float2* __restrict__ c2, double* __restrict__ mom)
+__device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict__ probs,
+                                                   const LocalBlock* __restrict__ blks, const Tile t,
+                                                   const float2* __restrict__ r2, const float2* __restrict__ c2,
+                                                   double* __restrict__ mom, acc2* acc)
 {
-    extern __shared__ acc2 acc[];
-    const Tile t = tiles[blockIdx.x];
     const LocalBlock B = blks[t.blk];
     const int L = probs[B.prob].L;
     const int odd = probs[B.prob].nu & 1;
@@ -139,6 +137,15 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
     }
     __syncthreads();
     reduce_columns_add(acc, nt, L, Accum{mom, probs[B.prob].fxs}.at(B.mom_off));
+}
+
+__global__ void __launch_bounds__(kMomThreads)
+k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                const Tile* __restrict__ tiles, const float2* __restrict__ r2,
+                const float2* __restrict__ c2, double* __restrict__ mom)
+{
+    extern __shared__ acc2 acc[];
+    local_moments_tile(probs, blks, tiles[blockIdx.x], r2, c2, mom, acc);
 }
 
 // J_0..J_ntop(y), unnormalised, into this thread's column jb[n * nt + tid]
@@ -231,13 +238,14 @@ __device__ __forceinline__ double series_store_fp64(double y, int ntop, float2* 
 // then sum_l C_l mu_l divided by the square of the normalisation.  With momb
 // (the moments of a second real component) the same C_l also give
 // sum_l C_l mub_l into g_sb.
-__global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
-                             const Tile* __restrict__ tiles, const float2* __restrict__ w2,
-                             const double* __restrict__ mom, double* __restrict__ g_s,
-                             const double* __restrict__ momb, double* __restrict__ g_sb)
+// coherent: read the moments past L1 (they were just written by other CTAs
+// of the same launch, the persistent local kernel)
+__device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ probs,
+                                                const LocalBlock* __restrict__ blks, const Tile t,
+                                                const float2* __restrict__ w2, const double* mom,
+                                                double* __restrict__ g_s, const double* momb,
+                                                double* __restrict__ g_sb, float2* sm2, bool coherent)
 {
-    extern __shared__ float2 sm2[];
-    const Tile t = tiles[blockIdx.x];
     const LocalBlock B = blks[t.blk];
     const ProbParams& P = probs[B.prob];
     const int nt = blockDim.x, tid = threadIdx.x;
@@ -247,11 +255,11 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
     float2* mub = sm2 + (P.ntop + 1); // [L + 1] the second component's (two)
     float2* jb = sm2 + (two ? 2 : 1) * (P.ntop + 1);  // [ntop + 1][nt]
     for (int l = tid; l <= L; l += nt) {
-        const double v = mom[B.mom_off + l];
+        const double v = coherent ? __ldcg(&mom[B.mom_off + l]) : mom[B.mom_off + l];
         const float h = (float)v;
         mu[l] = make_float2(h, (float)(v - (double)h));
         if (two) {
-            const double vb = momb[B.mom_off + l];
+            const double vb = coherent ? __ldcg(&momb[B.mom_off + l]) : momb[B.mom_off + l];
             const float hb = (float)vb;
             mub[l] = make_float2(hb, (float)(vb - (double)hb));
         }
@@ -314,6 +322,72 @@ __global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBl
     }
     Accum{g_s, P.fxs}.add(k, (double)P.sgn * val);
     if (two) Accum{g_sb, P.fxs}.add(k, (double)P.sgn * valb);
+}
+
+__global__ void k_local_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                             const Tile* __restrict__ tiles, const float2* __restrict__ w2,
+                             const double* __restrict__ mom, double* __restrict__ g_s,
+                             const double* __restrict__ momb, double* __restrict__ g_sb)
+{
+    extern __shared__ float2 sm2[];
+    local_eval_tile(probs, blks, tiles[blockIdx.x], w2, mom, g_s, momb, g_sb, sm2, false);
+}
+
+// Persistent local stage: one launch of resident CTAs takes work items from a
+// device queue (q[0], an atomic counter): first every moment tile (of each
+// component), then every evaluation tile.  An evaluation tile of block b
+// waits until all of b's moment tiles are done (q[2 + b] counts them): the
+// items it waits for were taken from the queue before it by CTAs that are
+// running and wait on nothing, so the wait always ends; it is still bounded
+// by wait_limit polls, after which the CTA records NUHT_ERR_TIMEOUT in
+// *status, skips the tile and goes on, so the launch always finishes.
+// stall (testing aid) asks block 0 for one moment tile more than it has.
+__global__ void __launch_bounds__(kMomThreads)
+k_local_persistent(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                   const Tile* __restrict__ tmom, int n_tmom, const Tile* __restrict__ teval, int n_teval,
+                   const int32_t* __restrict__ mom_pre, const float2* __restrict__ r2,
+                   const float2* __restrict__ c2, const float2* __restrict__ c2b, const float2* __restrict__ w2,
+                   double* mom, double* momb, double* __restrict__ g_s, double* __restrict__ g_sb, int* q,
+                   int* status, int wait_limit, int stall)
+{
+    extern __shared__ float4 smq[];
+    __shared__ int item, give_up;
+    const int ncomp = momb ? 2 : 1;
+    const int nmom = ncomp * n_tmom, total = nmom + n_teval;
+    int* done = q + 2;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(&q[0], 1);
+        __syncthreads();
+        const int it = item;
+        if (it >= total) break;
+        if (it < nmom) {
+            const int comp = it >= n_tmom ? 1 : 0;
+            const Tile t = tmom[it - comp * n_tmom];
+            local_moments_tile(probs, blks, t, r2, comp ? c2b : c2, comp ? momb : mom, (acc2*)smq);
+            __threadfence();   // the moments' atomics before the count
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&done[t.blk], 1);
+        } else {
+            const Tile t = teval[it - nmom];
+            if (threadIdx.x == 0) {
+                const int need = ncomp * (mom_pre[t.blk + 1] - mom_pre[t.blk]) + (stall && t.blk == 0 ? 1 : 0);
+                int polls = 0;
+                give_up = 0;
+                while (*(volatile int*)&done[t.blk] < need) {
+                    if (++polls > wait_limit) {
+                        atomicCAS(status, 0, NUHT_ERR_TIMEOUT);
+                        give_up = 1;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                __threadfence();
+            }
+            __syncthreads();
+            if (!give_up) local_eval_tile(probs, blks, t, w2, mom, g_s, momb, g_sb, (float2*)smq, true);
+        }
+        __syncthreads();   // item and the shared buffers are reused by the next item
+    }
 }
 
 // Mixed precision (eps >= 1e-6): k_local_eval in FP32.  J_0..J_ntop(y) by
@@ -1051,6 +1125,37 @@ cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, c
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_local_eval<<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, g_s, momb, g_sb);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_persistent(const ProbParams* probs, const LocalBlock* blks, const Tile* tmom, int n_tmom,
+                                    const Tile* teval, int n_teval, const int32_t* mom_pre, int lmax, int ntop_max,
+                                    int threads, const float2* r2, const float2* c2, const float2* c2b,
+                                    const float2* w2, double* mom, double* momb, double* g_s, double* g_sb, int* q,
+                                    int nloc, int* status, int wait_limit, int stall, cudaStream_t s)
+{
+    if (n_tmom + n_teval <= 0) return cudaSuccess;
+    if (threads < 32 || threads > kMomThreads || (threads & 31)) return cudaErrorInvalidValue;
+    const size_t nmu = momb ? 2 : 1;
+    const size_t sm_mom = sizeof(acc2) * (size_t)(lmax + 1) * threads;
+    const size_t sm_eval = sizeof(float2) * ((size_t)(ntop_max + 1) * threads + nmu * (size_t)(ntop_max + 1));
+    const size_t smem = sm_mom > sm_eval ? sm_mom : sm_eval;
+    cudaError_t e = cudaFuncSetAttribute(k_local_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_persistent, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int items = (momb ? 2 : 1) * n_tmom + n_teval;
+    int grid = sms * per_sm;
+    if (grid > items) grid = items;
+    e = cudaMemsetAsync(q, 0, sizeof(int) * (size_t)(nloc + 2), s);
+    if (e != cudaSuccess) return e;
+    k_local_persistent<<<grid, threads, smem, s>>>(probs, blks, tmom, n_tmom, teval, n_teval, mom_pre, r2, c2, c2b,
+                                                   w2, mom, momb, g_s, g_sb, q, status, wait_limit, stall);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -236,6 +236,11 @@ cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                  int ntiles, int lmax, const float2* r2, const float2* c2,
                                  double* mom, cudaStream_t s);
+cudaError_t launch_local_persistent(const ProbParams* probs, const LocalBlock* blks, const Tile* tmom, int n_tmom,
+                                    const Tile* teval, int n_teval, const int32_t* mom_pre, int lmax, int ntop_max,
+                                    int threads, const float2* r2, const float2* c2, const float2* c2b,
+                                    const float2* w2, double* mom, double* momb, double* g_s, double* g_sb, int* q,
+                                    int nloc, int* status, int wait_limit, int stall, cudaStream_t s);
 int local_moment_threads(int lmax);
 int local_eval_threads(int ntop_max);
 // Mixed precision: k_local_eval with the recurrence and the sum in FP32.

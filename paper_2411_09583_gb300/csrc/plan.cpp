@@ -114,6 +114,11 @@ struct nuht_plan_s {
     double2* d_tw = nullptr;
     // per-call input scaling: the bits of the largest input magnitude
     unsigned long long* d_mx = nullptr;
+    // persistent local stage: queue head, per-block moment-tile counts and the
+    // moment tiles' prefix per block; status word of bounded device waits
+    int* d_q = nullptr;
+    const int32_t* d_pre_mom = nullptr;
+    int* d_status = nullptr;
     // deterministic mode: exact fixed-point (Fx128) accumulators in place of
     // the FP64 targets of the atomics (same element indices)
     bool det = false;
@@ -426,6 +431,18 @@ void nuht_destroy(nuht_plan_t p)
 }
 
 int64_t nuht_kernel_launch_count(void) { return g_launches.load(); }
+
+int nuht_status(nuht_plan_t P, void* stream)
+{
+    if (!P) return NUHT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!P->d_status) return NUHT_OK;
+    int h = 0;
+    NUHT_CK(cudaMemcpyAsync(&h, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NUHT_CK(cudaMemsetAsync(P->d_status, 0, sizeof(int), s));
+    NUHT_CK(cudaStreamSynchronize(s));
+    return h;
+}
 
 const char* nuht_stage_name(int i) { return (i >= 0 && i < NUHT_NUM_STAGES) ? kStageNames[i] : nullptr; }
 
@@ -830,6 +847,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     size_t a_fgb = A.reserve<Fx128>(det ? 2 * (size_t)P->gb_len : f1);
     size_t a_ftg = A.reserve<Fx128>(det ? 2 * (size_t)P->gq_len : f1);
     size_t a_mx = A.reserve<unsigned long long>(1);
+    size_t a_q = A.reserve<int>((size_t)nl + 2), a_status = A.reserve<int>(1);
     NUHT_CK(pool_alloc((void**)&P->dmem, A.size, s));
     P->dbytes = A.size;
     char* D = P->dmem;
@@ -897,6 +915,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     P->d_tspread = tiles[LIST_SPREAD]; P->d_tinterp = tiles[LIST_INTERP];
     P->d_fsmall = tiles[LIST_FSMALL]; P->d_fa = tiles[LIST_FA]; P->d_fb = tiles[LIST_FB];
     P->d_fblock = tiles[LIST_FBLOCK];
+    P->d_pre_mom = bl.pre[LIST_MOM];
     P->d_blk = bl.blk;
     // sorted arrays and permutations stay on the device
     P->d_r = (double*)(D + a_r); P->d_w = (double*)(D + a_w);
@@ -927,6 +946,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
         P->f_gb = (Fx128*)(D + a_fgb); P->f_tg = (Fx128*)(D + a_ftg);
     }
     P->d_mx = (unsigned long long*)(D + a_mx);
+    P->d_q = (int*)(D + a_q);
+    P->d_status = (int*)(D + a_status);
+    NUHT_CK(cudaMemsetAsync(P->d_status, 0, sizeof(int), s));
     NUHT_CK(launch_split_f64(P->d_r, n, P->d_r2, s));
     NUHT_CK(launch_split_f64(P->d_w, m, P->d_w2, s));
     P->d_tg = (double2*)(D + a_tg); P->d_bq = (float4*)(D + a_bq);
@@ -1056,9 +1078,10 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
     if (o.min_size < 1 || o.min_size > NUHT_MAX_MIN_SIZE || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
     if (o.deterministic != 0 && o.deterministic != 1) return NUHT_ERR_INVALID_ARG;
+    if (o.persistent != 0 && o.persistent != 1) return NUHT_ERR_INVALID_ARG;
     if (o.spread_tile != 0 && (o.spread_tile < 64 || o.spread_tile > 256 || o.spread_tile % 32))
         return NUHT_ERR_INVALID_ARG;
     if (o.timing < NUHT_TIMING_OFF || o.timing > NUHT_TIMING_SERIAL) return NUHT_ERR_INVALID_ARG;
@@ -1176,7 +1199,20 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     ClassFork fk;
     if (P->opt.timing != NUHT_TIMING_SERIAL && asy && (loc || dir)) NUHT_CK(fk.open(s));
     const cudaStream_t ls = fk.local(s), as = fk.asy(s);
-    if (loc) {
+    if (loc && P->opt.persistent && !P->det) {
+        // moments and evaluation in one persistent launch (per-block waits)
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        double* momb = pair == 1 ? P->d_momb : nullptr;
+        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
+        if (momb) NUHT_CK(cudaMemsetAsync(momb, 0, sizeof(double) * P->mom_len, ls));
+        const char* st = std::getenv("NUHT_QUEUE_STALL");
+        const bool stall = st && *st && *st != '0';
+        NUHT_CK(launch_local_persistent(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->d_teval, P->n_teval,
+                                        P->d_pre_mom, P->lmax, P->ntop_max, P->eval_threads, P->d_r2, P->d_cs2,
+                                        P->d_cs2b, P->d_w2, P->d_mom, momb, gs, momb ? gsb : nullptr, P->d_q,
+                                        P->n_loc, P->d_status, stall ? 4096 : (1 << 22), stall ? 1 : 0, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
+    } else if (loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(mom_acc, 0, acc_bytes(P, P->mom_len), ls));
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,

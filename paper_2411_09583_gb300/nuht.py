@@ -30,7 +30,7 @@ def _dev_f64(x, name):
 
 
 def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class_mask=7,
-              timing=False, spread_tile=0, deterministic=False):
+              timing=False, spread_tile=0, deterministic=False, persistent=False):
     o = N.NuhtOpts()
     N.lib().nuht_default_opts(ctypes.byref(o))
     o.precision = {"fp64": N.PREC_FP64, "mixed": N.PREC_MIXED}[precision]
@@ -43,6 +43,7 @@ def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class
     o.timing = 2 if timing == "serial" else (1 if timing else 0)
     o.spread_tile = int(spread_tile)
     o.deterministic = 1 if deterministic else 0
+    o.persistent = 1 if persistent else 0
     return o
 
 
@@ -169,6 +170,11 @@ class Plan:
         """The derivative plan (orders nu - 1 and nu + 1 on the same, already
         sorted points and frequencies) for gradients in r and omega."""
         return DerivPlan(self)
+
+    def status(self):
+        """Device errors since the last call (waits for the stream): NUHT_OK or,
+        for instance, NUHT_ERR_TIMEOUT from a bounded wait that gave up."""
+        return int(N.lib().nuht_status(self._h, _stream_ptr(self._stream)))
 
     def info(self):
         inf = N.NuhtPlanInfo()
