@@ -108,6 +108,8 @@ def parse_args(argv=None):
                          "from experiments, Algorithm 2)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the oracle sample")
+    ap.add_argument("--only", choices=["large_grid", "mixed"], default=None,
+                    help="run one side workload alone and print its JSON (for profiling)")
     ap.add_argument("--opts", type=str, default=None,
                     help="plan options as JSON (e.g. '{\"min_size\": 2048}') instead of the autotuner's")
     return ap.parse_args(argv)
@@ -456,8 +458,16 @@ def run_mixed(dev, steps):
         t = statistics.median(ms)
         with Plan(1, dr, dw, 1e-5, precision=prec, **opts) as p:
             gh = p.execute(dc).cpu().numpy()
+        stages = {}
+        for _ in range(3):
+            flush.zero_()
+            with Plan(1, dr, dw, 1e-5, precision=prec, timing="serial", **opts) as pt:
+                pt.execute(dc)
+                for k, v in pt.stage_times().items():
+                    stages.setdefault(k, []).append(v)
         rows = sample_rows(omega.size, 100, seed=98)
         out[prec] = {"ms_per_step": t, "value": 8e6 / (t * 1e-3), "opts": opts,
+                     "stage_ms_alone": {k: statistics.median(v) for k, v in stages.items()},
                      "error": sampled_error(1, r, omega, c, gh, 1e-5, rows)}
     return out
 
@@ -569,6 +579,68 @@ def run_stress(dev, steps):
                                "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                                "error": sampled_error(0, r, omega, c.cpu().numpy(), gh, 1e-8, rows)}
         out[name] = res
+    return out
+
+
+def run_large_grid(dev, steps):
+    """One asymptotic block with grids far larger than L2 (n = m = 4e6, r ~ U[1,2],
+    omega ~ U[1e7,2e7], nu = 0): the spreading, FFT and interpolation kernels
+    move their grids through HBM.  FP64 at eps 1e-12 and mixed at 1e-6: plan +
+    execute, each stage alone, the error on sampled rows, and the stored ncu
+    DRAM bytes per launch of the three kernels as GB/s over their times."""
+    import torch
+
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import large_grid_problem, sample_rows
+    r, omega, c = large_grid_problem()
+    dr, dw, dc = (torch.tensor(x, device=dev) for x in (r, omega, c))
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    hbm_peak, hbm_src = measured_hbm_peak()
+    out = {"workload": "one asymptotic block: n = m = 4e6, nu = 0, r ~ U[1,2], omega ~ U[1e7,2e7], c ~ N(0,1)",
+           "unit": UNIT, "step": "plan + execute", "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
+    for prec, eps in (("fp64", 1e-12), ("mixed", 1e-6)):
+        with Plan(0, dr, dw, eps, precision=prec) as p:
+            p.execute(dc)
+            info = p.info()
+        ms = []
+        for _ in range(max(3, steps // 4)):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            p = Plan(0, dr, dw, eps, precision=prec)
+            g = p.execute(dc)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(s0.elapsed_time(s1))
+            p.close()
+        stages = {}
+        for _ in range(3):
+            flush.zero_()
+            with Plan(0, dr, dw, eps, precision=prec, timing="serial") as pt:
+                pt.execute(dc)
+                for k, v in pt.stage_times().items():
+                    stages.setdefault(k, []).append(v)
+        stages = {k: statistics.median(v) for k, v in stages.items()}
+        t = statistics.median(ms)
+        res = {"eps": eps, "ms_per_step": t, "value": 8e6 / (t * 1e-3), "stage_ms_alone": stages,
+               "grid_cells": info["asy_rows_cols"], "fft_points": info["fft_points"],
+               "error": sampled_error(0, r, omega, c, g.cpu().numpy(), eps, sample_rows(omega.size, 60, seed=92))}
+        wl = "large_grid_%s" % prec
+        sfx = "" if prec == "fp64" else "_f32"
+        hb = {}
+        for stage, kerns in (("asy_spread", ["k_asy_spread" + sfx]), ("asy_interp", ["k_asy_interp" + sfx]),
+                             ("asy_fft", ["k_asy_fft_pass_a", "k_asy_fft_pass_b"])):
+            got = [stored_traffic(k, wl) for k in kerns]
+            if all(tr for tr, _ in got):
+                tr = sum(t for t, _ in got)
+                gbs = tr / (stages[stage] * 1e-3) / 1e9
+                hb[stage] = {"kernels": kerns, "dram_bytes": tr, "stage_ms": stages[stage], "gbs": gbs,
+                             "frac": gbs / hbm_peak}
+            else:
+                hb[stage] = {"kernels": kerns, "dram_bytes": None, "basis": [b for _, b in got]}
+        res["hbm"] = hb
+        out[prec] = res
     return out
 
 
@@ -755,6 +827,7 @@ def run_ours(a):
                     "dominant kernel: ncu DRAM bytes per launch over its live launch time"}
 
     extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = extra_det = extra_pers = None
+    extra_large = None
     if not a.no_extra and ws == 1:
         # the same workload at the other order of the scaled plain-NUHT
         # configuration (nu = 10), same options and timing as the main line
@@ -842,6 +915,7 @@ def run_ours(a):
         extra_mixed = run_mixed(dev, a.steps)
         extra_grad = run_grad(dev, a.steps)
         extra_stress = run_stress(dev, a.steps)
+        extra_large = run_large_grid(dev, a.steps)
 
     line = None
     if rank == 0:
@@ -892,6 +966,7 @@ def run_ours(a):
                 "other_order": extra_order,
                 "deterministic": extra_det,
                 "persistent_local": extra_pers,
+                "large_grid": extra_large,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],
@@ -910,6 +985,13 @@ def main(argv=None):
         if rank != 0:
             return 0
         run_reference(a)
+        return 0
+    if a.only:
+        import torch
+        from paper_2411_09583_gb300 import build_native
+        build_native.build()
+        fn = {"large_grid": run_large_grid, "mixed": run_mixed}[a.only]
+        print(json.dumps(fn(torch.device("cuda", 0), a.steps)))
         return 0
     run_ours(a)
     return 0

@@ -64,7 +64,7 @@ __device__ __forceinline__ void fx_encode(double v, int s, unsigned long long& l
 // carry is exact: the old value returned by the atomic tells whether this
 // addition wrapped, and the wraps of all additions sum to the same count in
 // any order.
-__device__ __forceinline__ void fx_add_words(Fx128* p, unsigned long long lo, unsigned long long hi)
+static __device__ __noinline__ void fx_add_words(Fx128* p, unsigned long long lo, unsigned long long hi)
 {
     if (lo) {
         const unsigned long long old = atomicAdd(&p->lo, lo);
@@ -73,7 +73,9 @@ __device__ __forceinline__ void fx_add_words(Fx128* p, unsigned long long lo, un
     if (hi) atomicAdd(&p->hi, hi);
 }
 
-__device__ __forceinline__ void fx_add(Fx128* p, double v, int s)
+// Not inlined: the hot kernels call it only in the deterministic mode, and
+// keeping it out of line keeps their default (FP64 atomic) path's registers.
+static __device__ __noinline__ void fx_add(Fx128* p, double v, int s)
 {
     unsigned long long lo, hi;
     fx_encode(v, s, lo, hi);

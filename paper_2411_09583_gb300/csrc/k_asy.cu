@@ -852,7 +852,11 @@ __global__ void k_spread_modes(const ProbParams* __restrict__ probs, const AsyBl
     }
 }
 
-__global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+// At most 64 registers: four CTAs of 256 threads fit an SM whenever their
+// shared memory does (the out-of-line deterministic accumulation would
+// otherwise raise the allocation to 80 and cost a CTA per SM at small 2M).
+__global__ void __launch_bounds__(256, 4)
+k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, const int32_t* __restrict__ modes, Tables tab,
                              const double* __restrict__ r_s, const float2* __restrict__ r2,
                              const float2* __restrict__ c2, double2* __restrict__ grid_b)
@@ -958,24 +962,56 @@ __device__ __forceinline__ float4 cdf_from(double2 v)
 // one after the other in shared memory, each in bit-reversed order, sharing
 // every butterfly stage.  tw2[k] = e^{2 pi i k / 2^tw_log2} as double-float.
 // LOWP: the butterflies in FP32 on the values' FP32 parts (mixed precision).
+// The decimation-in-time stages run two at a time (radix 4): a thread loads
+// the four values a group of stages st, st + 1 combines (offsets 0, len,
+// 2 len, 3 len), applies both stages' butterflies in registers and stores them
+// back, so each value crosses shared memory once per two stages and the CTA
+// synchronises half as often.  An odd stage count starts with one radix-2
+// stage (twiddle 1).
+template <bool LOWP>
+__device__ __forceinline__ void fft_bfly(float4& u, float4& v, float4 w)
+{
+    if (LOWP) cf_butterfly(u, v, w);
+    else cdf_butterfly(u, v, w);
+}
+
 template <bool LOWP>
 __device__ void smem_fft_lines(float4* X, int logN, int nlines, const float4* __restrict__ tw2, int tw_log2)
 {
-    const int N = 1 << logN, half = N >> 1;
-    for (int st = 0; st < logN; ++st) {
-        const int len = 1 << st;
-        const int tw_shift = tw_log2 - (st + 1);
+    const int N = 1 << logN;
+    int st = 0;
+    if (logN & 1) {
+        const int half = N >> 1;
+        const float4 one = tw2[0];
         for (int b = threadIdx.x; b < nlines * half; b += blockDim.x) {
-            const int line = b >> (logN - 1);
-            const int bb = b & (half - 1);
-            const int pos = bb & (len - 1);
-            const int i0 = line * N + ((bb >> st) << (st + 1)) + pos;
-            const int i1 = i0 + len;
-            float4 u = X[i0], v = X[i1];
-            if (LOWP) cf_butterfly(u, v, tw2[pos << tw_shift]);
-            else cdf_butterfly(u, v, tw2[pos << tw_shift]);
+            const int i0 = 2 * b;   // stage 0: pairs (2b, 2b + 1), twiddle 1
+            float4 u = X[i0], v = X[i0 + 1];
+            fft_bfly<LOWP>(u, v, one);
             X[i0] = u;
-            X[i1] = v;
+            X[i0 + 1] = v;
+        }
+        __syncthreads();
+        st = 1;
+    }
+    const int quarter = N >> 2;
+    for (; st < logN; st += 2) {
+        const int len = 1 << st;
+        const int sh1 = tw_log2 - (st + 1), sh2 = tw_log2 - (st + 2);
+        for (int b = threadIdx.x; b < nlines * quarter; b += blockDim.x) {
+            const int line = b >> (logN - 2);
+            const int bb = b & (quarter - 1);
+            const int pos = bb & (len - 1);
+            const int i0 = line * N + ((bb >> st) << (st + 2)) + pos;
+            float4 a = X[i0], c1 = X[i0 + len], c2 = X[i0 + 2 * len], c3 = X[i0 + 3 * len];
+            const float4 t1 = tw2[pos << sh1];
+            fft_bfly<LOWP>(a, c1, t1);                       // stage st: (0, len), (2 len, 3 len)
+            fft_bfly<LOWP>(c2, c3, t1);
+            fft_bfly<LOWP>(a, c2, tw2[pos << sh2]);          // stage st + 1: (0, 2 len), (len, 3 len)
+            fft_bfly<LOWP>(c1, c3, tw2[(pos + len) << sh2]);
+            X[i0] = a;
+            X[i0 + len] = c1;
+            X[i0 + 2 * len] = c2;
+            X[i0 + 3 * len] = c3;
         }
         __syncthreads();
     }
@@ -1136,8 +1172,10 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
 // Two-pass (four-step) FFT for nf2 = N1 * N2 > kFftSingleMax.
 // Pass A: for each n1, FFT over n2 of x[n1 + N1 n2], times e^{2 pi i n1 k2 / N},
 // stored at tmp[n1 + N1 k2].  Pass B: for each k2, FFT over n1 of
-// tmp[n1 + N1 k2], which is X[k2 + N2 k1].  Work item ordinal = q * groups + g,
-// g a group of lines handled by one CTA.
+// tmp[n1 + N1 k2], which is X[k2 + N2 k1].  Work item ordinal = g * Q + q,
+// g a group of lines handled by one CTA: the Q CTAs of a group run side by
+// side and read and write the same rows of the [point][Q] grids (one row is
+// all Q values of a point), so a row moves through HBM once, not once per q.
 template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ items, Tables tab,
@@ -1149,8 +1187,8 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
     const int Q = probs[B.prob].Q;
     const int N = B.nf2;
     const FourStep f = four_step(B.log2nf2);
-    const int iq = (int)(it.start / f.groupsA);
-    const int g = (int)(it.start - (int64_t)iq * f.groupsA);
+    const int g = (int)(it.start / Q);
+    const int iq = (int)(it.start - (int64_t)g * Q);
     const int l0 = g * f.lpcA;
     const int nl = (f.N1 - l0) < f.lpcA ? (f.N1 - l0) : f.lpcA;
     for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
@@ -1164,8 +1202,14 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
         const int li = idx >> f.logN2, k2 = idx & (f.N2 - 1);
         const int n1 = l0 + li;
         const long long m = ((long long)n1 * k2) & (N - 1);   // e^{2 pi i n1 k2 / N}
-        const float4 tw = cdf_twiddle(tab, B.log2nf2, m);
-        tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = LOWP ? cf_mul(Xs[idx], tw) : cdf_mul(Xs[idx], tw);
+        if (LOWP) {
+            // FP32 twiddle: m / N is exact in FP32 (N <= 2^24)
+            float sn, cs;
+            sincospif(ldexpf(2.f * (float)m, -B.log2nf2), &sn, &cs);
+            tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = cf_mul(Xs[idx], make_float4(cs, 0.f, sn, 0.f));
+        } else {
+            tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = cdf_mul(Xs[idx], cdf_twiddle(tab, B.log2nf2, m));
+        }
     }
 }
 
@@ -1179,8 +1223,8 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
     const FourStep f = four_step(B.log2nf2);
-    const int iq = (int)(it.start / f.groupsB);
-    const int g = (int)(it.start - (int64_t)iq * f.groupsB);
+    const int g = (int)(it.start / Q);
+    const int iq = (int)(it.start - (int64_t)g * Q);
     const int k20 = g * f.lpcB;
     const int nl = (f.N2 - k20) < f.lpcB ? (f.N2 - k20) : f.lpcB;
     const float4* tq = tmp + B.q_off;

@@ -35,6 +35,18 @@ def loguniform_problem(n, m, r_lo=1e-3, r_hi=1.0, omega_max=4e4, seed=0,
     return r, omega, c
 
 
+def large_grid_problem(n=4_000_000, m=4_000_000, seed=11):
+    """One asymptotic block whose type-3 grids are larger than the L2 cache:
+    r ~ U[1, 2], omega ~ U[1e7, 2e7] (every omega r far above z), c ~ N(0, 1).
+    The half-widths X = 0.5 and S = 5e6 give about 2 X S / pi = 1.6e6 cells on
+    each side of the spreading grid and an FFT of 2^23 points per Hankel term."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(1.0, 2.0, n)
+    omega = rng.uniform(1e7, 2e7, m)
+    c = rng.standard_normal(n)
+    return r, omega, c
+
+
 def exponential_grid(n):
     """omega_j = r_j = 10^(log10 j - log10(n)/2), j = 1..n (Sec. 5.1.1, the
     worst case for the subdivision)."""

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2411_09583_gb300.workloads import batch_problems, uniform_problem
+from paper_2411_09583_gb300.workloads import batch_problems, large_grid_problem, sample_rows, uniform_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -71,3 +71,24 @@ def test_tightest_tolerance_both_directions(nu):
     assert err <= tol(eps, c), (err, tol(eps, c))
     err = np.max(np.abs(ca - oracle.direct(nu, omega, r, e)))
     assert err <= tol(eps, e), (err, tol(eps, e))
+
+
+@pytest.mark.parametrize("precision,eps", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_large_grid_single_block(precision, eps):
+    # one asymptotic block whose spreading grid (~3.2e6 cells x 2M terms) and
+    # FFT (2^23 points x 2M terms) are far larger than the L2 cache: n = m =
+    # 4e6, r ~ U[1,2], omega ~ U[1e7,2e7]; sampled rows and columns against
+    # the oracle, both directions
+    from paper_2411_09583_gb300 import Plan
+    r, omega, c = large_grid_problem()
+    e = np.random.default_rng(12).standard_normal(omega.size)
+    with Plan(0, to_dev(r), to_dev(omega), eps, precision=precision) as p:
+        info = p.info()
+        assert info["n_asy"] == 1 and info["n_local"] == 0 and info["n_direct"] == 0
+        assert info["fft_points"] >= 1 << 23
+        g = p.execute(to_dev(c)).cpu().numpy()
+        ca = p.adjoint(to_dev(e)).cpu().numpy()
+    rows = sample_rows(omega.size, 60, seed=13)
+    cols = sample_rows(r.size, 60, seed=14)
+    assert np.max(np.abs(g[rows] - oracle.direct_rows(0, r, omega, c, rows))) <= tol(eps, c)
+    assert np.max(np.abs(ca[cols] - oracle.direct_rows(0, omega, r, e, cols))) <= tol(eps, e)
