@@ -108,7 +108,7 @@ def parse_args(argv=None):
                          "from experiments, Algorithm 2)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of the oracle sample")
-    ap.add_argument("--only", choices=["large_grid", "mixed"], default=None,
+    ap.add_argument("--only", choices=["large_grid", "mixed", "multi_vector"], default=None,
                     help="run one side workload alone and print its JSON (for profiling)")
     ap.add_argument("--opts", type=str, default=None,
                     help="plan options as JSON (e.g. '{\"min_size\": 2048}') instead of the autotuner's")
@@ -644,6 +644,46 @@ def run_large_grid(dev, steps):
     return out
 
 
+def run_multi_vector(dev, steps, nvec=16):
+    """The n = m = 1e6, nu = 0, eps = 1e-12 workload with nvec coefficient vectors in
+    one execute (plan reused), against one vector: per-vector throughput and the error
+    of every vector on sampled rows."""
+    import numpy as np
+    import torch
+
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300.workloads import sample_rows, uniform_problem
+    r, omega, _ = uniform_problem(1_000_000, 1_000_000, omega_max=1e5, seed=2)
+    C = np.random.default_rng(21).standard_normal((r.size, nvec))
+    dr, dw, dC = (torch.tensor(x, device=dev) for x in (r, omega, C))
+    dc1 = dC[:, 0].contiguous()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "n = m = 1e6, nu = 0, eps 1e-12, r ~ U[0,1], omega ~ U[0,1e5], %d vectors c ~ N(0,1)" % nvec,
+           "unit": UNIT, "step": "execute (plan reused), L2 flushed"}
+    with Plan(0, dr, dw, 1e-12, min_size=2048) as p:
+        for label, x in (("nvec_1", dc1), ("nvec_%d" % nvec, dC)):
+            for _ in range(2):
+                p.execute(x)
+            ms = []
+            for _ in range(max(3, steps // 4)):
+                flush.zero_()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                g = p.execute(x)
+                s1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(s0.elapsed_time(s1))
+            t = statistics.median(ms)
+            k = x.shape[1] if x.dim() > 1 else 1
+            out[label] = {"ms": t, "value_per_vector": 2e6 / (t * 1e-3 / k), "vectors": k}
+        gh = g.cpu().numpy()
+    rows = sample_rows(omega.size, 60, seed=91)
+    out["error"] = sampled_error(0, r, omega, C, gh, 1e-12, rows)
+    out["per_vector_speedup"] = out["nvec_%d" % nvec]["value_per_vector"] / out["nvec_1"]["value_per_vector"]
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -827,7 +867,7 @@ def run_ours(a):
                     "dominant kernel: ncu DRAM bytes per launch over its live launch time"}
 
     extra_batched = extra_mixed = extra_grad = extra_stress = extra_order = extra_det = extra_pers = None
-    extra_large = None
+    extra_large = extra_multi = None
     if not a.no_extra and ws == 1:
         # the same workload at the other order of the scaled plain-NUHT
         # configuration (nu = 10), same options and timing as the main line
@@ -916,6 +956,7 @@ def run_ours(a):
         extra_grad = run_grad(dev, a.steps)
         extra_stress = run_stress(dev, a.steps)
         extra_large = run_large_grid(dev, a.steps)
+        extra_multi = run_multi_vector(dev, a.steps)
 
     line = None
     if rank == 0:
@@ -967,6 +1008,7 @@ def run_ours(a):
                 "deterministic": extra_det,
                 "persistent_local": extra_pers,
                 "large_grid": extra_large,
+                "multi_vector": extra_multi,
                 "plan": {"M": info["M"], "L": info["L"], "z": info["z"], "w": info["nufft_width"],
                          "blocks_local_asy_direct": [info["n_local"], info["n_asy"], info["n_direct"]],
                          "direct_entries": info["direct_entries"],
@@ -990,7 +1032,7 @@ def main(argv=None):
         import torch
         from paper_2411_09583_gb300 import build_native
         build_native.build()
-        fn = {"large_grid": run_large_grid, "mixed": run_mixed}[a.only]
+        fn = {"large_grid": run_large_grid, "mixed": run_mixed, "multi_vector": run_multi_vector}[a.only]
         print(json.dumps(fn(torch.device("cuda", 0), a.steps)))
         return 0
     run_ours(a)

@@ -1017,6 +1017,59 @@ __device__ void smem_fft_lines(float4* X, int logN, int nlines, const float4* __
     }
 }
 
+// The mixed-precision FFT on FP32 complex values (float2: re, im) in shared
+// memory: the stages of smem_fft_lines on half the bytes per value, with the
+// twiddles' FP32 parts.
+__device__ __forceinline__ void cf2_bfly(float2& u, float2& v, float4 w)
+{
+    const float vr = v.x * w.x - v.y * w.z, vi = fmaf(v.x, w.z, v.y * w.x);
+    const float ur = u.x, ui = u.y;
+    u = make_float2(ur + vr, ui + vi);
+    v = make_float2(ur - vr, ui - vi);
+}
+
+__device__ void smem_fft_lines_f32(float2* X, int logN, int nlines, const float4* __restrict__ tw2, int tw_log2)
+{
+    const int N = 1 << logN;
+    int st = 0;
+    if (logN & 1) {
+        const int half = N >> 1;
+        for (int b = threadIdx.x; b < nlines * half; b += blockDim.x) {
+            const int i0 = 2 * b;
+            const float2 u = X[i0], v = X[i0 + 1];
+            X[i0] = make_float2(u.x + v.x, u.y + v.y);
+            X[i0 + 1] = make_float2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+        st = 1;
+    }
+    const int quarter = N >> 2;
+    for (; st < logN; st += 2) {
+        const int len = 1 << st;
+        const int sh1 = tw_log2 - (st + 1), sh2 = tw_log2 - (st + 2);
+        for (int b = threadIdx.x; b < nlines * quarter; b += blockDim.x) {
+            const int line = b >> (logN - 2);
+            const int bb = b & (quarter - 1);
+            const int pos = bb & (len - 1);
+            const int i0 = line * N + ((bb >> st) << (st + 2)) + pos;
+            float2 a = X[i0], c1 = X[i0 + len], c2 = X[i0 + 2 * len], c3 = X[i0 + 3 * len];
+            const float4 t1 = tw2[pos << sh1];
+            cf2_bfly(a, c1, t1);
+            cf2_bfly(c2, c3, t1);
+            cf2_bfly(a, c2, tw2[pos << sh2]);
+            cf2_bfly(c1, c3, tw2[(pos + len) << sh2]);
+            X[i0] = a;
+            X[i0 + len] = c1;
+            X[i0 + 2 * len] = c2;
+            X[i0 + 3 * len] = c3;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ float2 cf2_of(float4 v) { return make_float2(v.x, v.z); }
+__device__ __forceinline__ float4 cf4_of(float2 v) { return make_float4(v.x, 0.f, v.y, 0.f); }
+
 // e^{2 pi i m / N} for 0 <= m < N = 2^logN as double-float: the table entry for
 // the top bits of m / N times the rotation by the rest, an angle below
 // 2 pi / 2^tw_log2, from its Taylor series (five terms, truncation < 1e-19).
@@ -1112,11 +1165,17 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
     const int Q = probs[B.prob].Q;
     const int q = (int)it.start;
     const int N = B.nf2, logN = B.log2nf2;
-    for (int tt = threadIdx.x; tt < N; tt += blockDim.x)
-        Xs[__brev(tt) >> (32 - logN)] = fft_in<ADJ>(B, tab, src, Q, q, tt);
+    float2* Xf = reinterpret_cast<float2*>(Xs);   // LOWP: FP32 values
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) {
+        const float4 v = fft_in<ADJ>(B, tab, src, Q, q, tt);
+        if (LOWP) Xf[__brev(tt) >> (32 - logN)] = cf2_of(v);
+        else Xs[__brev(tt) >> (32 - logN)] = v;
+    }
     __syncthreads();
-    smem_fft_lines<LOWP>(Xs, logN, 1, tab.tw2, tab.tw_log2);
-    for (int tt = threadIdx.x; tt < N; tt += blockDim.x) fft_out<ADJ>(B, tab, dst, Q, q, tt, Xs[tt]);
+    if (LOWP) smem_fft_lines_f32(Xf, logN, 1, tab.tw2, tab.tw_log2);
+    else smem_fft_lines<false>(Xs, logN, 1, tab.tw2, tab.tw_log2);
+    for (int tt = threadIdx.x; tt < N; tt += blockDim.x)
+        fft_out<ADJ>(B, tab, dst, Q, q, tt, LOWP ? cf4_of(Xf[tt]) : Xs[tt]);
 }
 
 // All Q grids of one small block (nf2 * Q <= kFftSmemMax) in one CTA: the
@@ -1136,27 +1195,34 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
     const int pts = B.nf2 * Q;
     if (pts <= pts_lo || pts > pts_hi) return;
     const int N = B.nf2, logN = B.log2nf2, half = N >> 1;
+    float2* Xf = reinterpret_cast<float2*>(Xs);   // LOWP: FP32 values
+    auto put = [&](int i, float4 v) {
+        if (LOWP) Xf[i] = cf2_of(v);
+        else Xs[i] = v;
+    };
     for (int tt = threadIdx.x; tt < N; tt += blockDim.x) {
         const int l = (tt < half) ? tt : tt - N;
         const int dst_i = __brev(tt) >> (32 - logN);
         if (ADJ) {
             const double2* row = src + B.q_off + (int64_t)tt * Q;
-            for (int q = 0; q < Q; ++q) Xs[q * N + dst_i] = cdf_from(row[q]);
+            for (int q = 0; q < Q; ++q) put(q * N + dst_i, cdf_from(row[q]));
         } else if (l < -B.N1 || l > B.N1) {
-            for (int q = 0; q < Q; ++q) Xs[q * N + dst_i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < Q; ++q) put(q * N + dst_i, make_float4(0.f, 0.f, 0.f, 0.f));
         } else {
             const df sc = mode_correction(B, tab, l);
             const double2* row = src + B.b_off + (int64_t)(l + B.N1) * Q;
-            for (int q = 0; q < Q; ++q) Xs[q * N + dst_i] = cdf_scale(cdf_from(row[q]), sc);
+            for (int q = 0; q < Q; ++q) put(q * N + dst_i, cdf_scale(cdf_from(row[q]), sc));
         }
     }
     __syncthreads();
-    smem_fft_lines<LOWP>(Xs, logN, Q, tab.tw2, tab.tw_log2);
+    if (LOWP) smem_fft_lines_f32(Xf, logN, Q, tab.tw2, tab.tw_log2);
+    else smem_fft_lines<false>(Xs, logN, Q, tab.tw2, tab.tw_log2);
+    auto get = [&](int i) { return LOWP ? cf4_of(Xf[i]) : Xs[i]; };
     if (!ADJ) {
         float4* gq = dst + B.q_off;
         for (int idx = threadIdx.x; idx < N * Q; idx += blockDim.x) {
             const int tt = idx / Q, q = idx - tt * Q;
-            gq[idx] = Xs[q * N + tt];
+            gq[idx] = get(q * N + tt);
         }
     } else {
         const int nf1 = 2 * B.N1 + 1;
@@ -1164,7 +1230,7 @@ __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyB
         for (int li = threadIdx.x; li < nf1; li += blockDim.x) {
             const int l = li - B.N1;
             const df sc = mode_correction(B, tab, l);
-            for (int q = 0; q < Q; ++q) gb[(int64_t)li * Q + q] = cdf_scale(Xs[q * N + (l & (N - 1))], sc);
+            for (int q = 0; q < Q; ++q) gb[(int64_t)li * Q + q] = cdf_scale(get(q * N + (l & (N - 1))), sc);
         }
     }
 }
@@ -1191,24 +1257,31 @@ __global__ void k_asy_fft_pass_a(const ProbParams* __restrict__ probs, const Asy
     const int iq = (int)(it.start - (int64_t)g * Q);
     const int l0 = g * f.lpcA;
     const int nl = (f.N1 - l0) < f.lpcA ? (f.N1 - l0) : f.lpcA;
+    float2* Xf = reinterpret_cast<float2*>(Xs);   // LOWP: FP32 values
     for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
         const int li = idx >> f.logN2, n2 = idx & (f.N2 - 1);
-        Xs[li * f.N2 + (__brev(n2) >> (32 - f.logN2))] = fft_in<ADJ>(B, tab, src, Q, iq, (l0 + li) + f.N1 * n2);
+        const int i = li * f.N2 + (__brev(n2) >> (32 - f.logN2));
+        const float4 v = fft_in<ADJ>(B, tab, src, Q, iq, (l0 + li) + f.N1 * n2);
+        if (LOWP) Xf[i] = cf2_of(v);
+        else Xs[i] = v;
     }
     __syncthreads();
-    smem_fft_lines<LOWP>(Xs, f.logN2, nl, tab.tw2, tab.tw_log2);
-    float4* tq = tmp + B.q_off;
+    if (LOWP) smem_fft_lines_f32(Xf, f.logN2, nl, tab.tw2, tab.tw_log2);
+    else smem_fft_lines<false>(Xs, f.logN2, nl, tab.tw2, tab.tw_log2);
     for (int idx = threadIdx.x; idx < nl * f.N2; idx += blockDim.x) {
         const int li = idx >> f.logN2, k2 = idx & (f.N2 - 1);
         const int n1 = l0 + li;
         const long long m = ((long long)n1 * k2) & (N - 1);   // e^{2 pi i n1 k2 / N}
+        const int64_t o = B.q_off + (int64_t)(n1 + f.N1 * k2) * Q + iq;
         if (LOWP) {
-            // FP32 twiddle: m / N is exact in FP32 (N <= 2^24)
+            // FP32 twiddle (m / N is exact in FP32, N <= 2^24); the pass
+            // temporary holds FP32 complex values (float2, half the bytes)
             float sn, cs;
             sincospif(ldexpf(2.f * (float)m, -B.log2nf2), &sn, &cs);
-            tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = cf_mul(Xs[idx], make_float4(cs, 0.f, sn, 0.f));
+            const float2 x = Xf[idx];
+            reinterpret_cast<float2*>(tmp)[o] = make_float2(x.x * cs - x.y * sn, fmaf(x.x, sn, x.y * cs));
         } else {
-            tq[(int64_t)(n1 + f.N1 * k2) * Q + iq] = cdf_mul(Xs[idx], cdf_twiddle(tab, B.log2nf2, m));
+            tmp[o] = cdf_mul(Xs[idx], cdf_twiddle(tab, B.log2nf2, m));
         }
     }
 }
@@ -1227,17 +1300,20 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
     const int iq = (int)(it.start - (int64_t)g * Q);
     const int k20 = g * f.lpcB;
     const int nl = (f.N2 - k20) < f.lpcB ? (f.N2 - k20) : f.lpcB;
-    const float4* tq = tmp + B.q_off;
+    float2* Xf = reinterpret_cast<float2*>(Xs);   // LOWP: FP32 values
     for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
         const int li = idx >> f.logN1, n1 = idx & (f.N1 - 1);
-        Xs[li * f.N1 + (f.logN1 > 0 ? (__brev(n1) >> (32 - f.logN1)) : 0)] =
-            tq[(int64_t)(n1 + f.N1 * (k20 + li)) * Q + iq];
+        const int i = li * f.N1 + (f.logN1 > 0 ? (__brev(n1) >> (32 - f.logN1)) : 0);
+        const int64_t o = B.q_off + (int64_t)(n1 + f.N1 * (k20 + li)) * Q + iq;
+        if (LOWP) Xf[i] = reinterpret_cast<const float2*>(tmp)[o];
+        else Xs[i] = tmp[o];
     }
     __syncthreads();
-    smem_fft_lines<LOWP>(Xs, f.logN1, nl, tab.tw2, tab.tw_log2);
+    if (LOWP) smem_fft_lines_f32(Xf, f.logN1, nl, tab.tw2, tab.tw_log2);
+    else smem_fft_lines<false>(Xs, f.logN1, nl, tab.tw2, tab.tw_log2);
     for (int idx = threadIdx.x; idx < nl * f.N1; idx += blockDim.x) {
         const int li = idx >> f.logN1, k1 = idx & (f.N1 - 1);
-        fft_out<ADJ>(B, tab, dst, Q, iq, (k20 + li) + f.N2 * k1, Xs[idx]);
+        fft_out<ADJ>(B, tab, dst, Q, iq, (k20 + li) + f.N2 * k1, LOWP ? cf4_of(Xf[idx]) : Xs[idx]);
     }
 }
 
@@ -2227,7 +2303,7 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
                                  float4* dst, cudaStream_t s, bool adj, bool lowp)
 {
     if (nitems <= 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * (size_t)max_nf2;
+    size_t smem = (lowp ? sizeof(float2) : sizeof(float4)) * (size_t)max_nf2;
     auto kern = adj ? (lowp ? k_asy_fft_small<true, true> : k_asy_fft_small<true, false>)
                     : (lowp ? k_asy_fft_small<false, true> : k_asy_fft_small<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2257,7 +2333,7 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
     for (int r = 0; r < 2; ++r) {
         const int lo = ranges[r][0], hi = ranges[r][1];
         if (hi <= lo) continue;
-        const size_t smem = sizeof(float4) * (size_t)hi;
+        const size_t smem = (lowp ? sizeof(float2) : sizeof(float4)) * (size_t)hi;
         int nt = ((hi / 2 + 31) / 32) * 32;
         if (r == 0 && nt > 128) nt = 128;
         if (nt > 256) nt = 256;
@@ -2279,7 +2355,7 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
                                  cudaStream_t s, bool adj, bool lowp)
 {
     if (nitems_a <= 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * (size_t)kFftLineBatch;
+    size_t smem = (lowp ? sizeof(float2) : sizeof(float4)) * (size_t)kFftLineBatch;
     auto ka = adj ? (lowp ? k_asy_fft_pass_a<true, true> : k_asy_fft_pass_a<true, false>)
                   : (lowp ? k_asy_fft_pass_a<false, true> : k_asy_fft_pass_a<false, false>);
     auto kb = adj ? (lowp ? k_asy_fft_pass_b<true, true> : k_asy_fft_pass_b<true, false>)

@@ -92,3 +92,22 @@ def test_large_grid_single_block(precision, eps):
     cols = sample_rows(r.size, 60, seed=14)
     assert np.max(np.abs(g[rows] - oracle.direct_rows(0, r, omega, c, rows))) <= tol(eps, c)
     assert np.max(np.abs(ca[cols] - oracle.direct_rows(0, omega, r, e, cols))) <= tol(eps, e)
+
+
+def test_sixteen_vectors_both_directions():
+    # nvec = 16 real vectors in one call (pairs of components share the local
+    # and direct blocks' Bessel values), forward and adjoint, each vector
+    # against the oracle on sampled rows
+    from paper_2411_09583_gb300 import Plan
+    eps = 1e-10
+    r, omega, _ = uniform_problem(6000, 5000, omega_max=8000.0, seed=640)
+    rng = np.random.default_rng(641)
+    C, E = rng.standard_normal((r.size, 16)), rng.standard_normal((omega.size, 16))
+    with Plan(2, to_dev(r), to_dev(omega), eps) as p:
+        G = p.execute(to_dev(C)).cpu().numpy()
+        A = p.adjoint(to_dev(E)).cpu().numpy()
+    rows, cols = sample_rows(omega.size, 80, seed=642), sample_rows(r.size, 80, seed=643)
+    ref_g = oracle.direct_rows(2, r, omega, C, rows)
+    ref_a = oracle.direct_rows(2, omega, r, E, cols)
+    assert np.all(np.max(np.abs(G[rows] - ref_g), axis=0) <= tol(eps, C))
+    assert np.all(np.max(np.abs(A[cols] - ref_a), axis=0) <= tol(eps, E))
