@@ -130,4 +130,36 @@ struct Accum {
     }
 };
 
+// The two modes as compile-time targets with Accum's interface, for kernels
+// instantiated once per mode (the spreading kernel: the out-of-line
+// fixed-point call would otherwise cost the FP64 path registers).
+struct AccumF64 {
+    double* p;
+    int fxs;
+    __device__ __forceinline__ void add(int64_t i, double v) const { atomicAdd(p + i, v); }
+    __device__ __forceinline__ AccumF64 at(int64_t off) const { return AccumF64{p + off, fxs}; }
+};
+
+struct AccumFx {
+    double* p;
+    int fxs;
+    __device__ __forceinline__ void add(int64_t i, double v) const
+    {
+        fx_add(reinterpret_cast<Fx128*>(p) + i, v, fxs);
+    }
+    __device__ __forceinline__ AccumFx at(int64_t off) const
+    {
+        return AccumFx{reinterpret_cast<double*>(reinterpret_cast<Fx128*>(p) + off), fxs};
+    }
+};
+
+template <bool DET>
+struct AccumOf {
+    using type = AccumF64;
+};
+template <>
+struct AccumOf<true> {
+    using type = AccumFx;
+};
+
 }  // namespace nuht

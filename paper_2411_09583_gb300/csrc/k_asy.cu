@@ -196,9 +196,9 @@ __device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
 // target(j, &v, xq) gives target j's cell and kernel coordinate v and writes
 // its 2M weighted values as double-float (re, im) pairs xq[2q], xq[2q + 1];
 // cell(c) is the grid index of cell c, or -1 for a cell outside the grid.
-template <class Target, class Cell>
+template <class Target, class Cell, class Acc>
 __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, const Tables& tab, Target&& target,
-                                               Cell&& cell, Accum gb, float2* sm)
+                                               Cell&& cell, Acc gb, float2* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -472,9 +472,10 @@ __host__ __device__ __forceinline__ size_t spread_fold_smem(int nt, int Q, int w
            sizeof(float) * (size_t)nt * suf + sizeof(int) * (size_t)nt;
 }
 
+template <class Acc>
 __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, const Tables& tab, FoldPlan F,
                             const double* __restrict__ r_s, const float2* __restrict__ r2,
-                            const float2* __restrict__ c2, Accum gb, float4* sm4)
+                            const float2* __restrict__ c2, Acc gb, float4* sm4)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -725,9 +726,10 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
 // (cell, q) output of the tile's window is owned by one thread, which sums
 // over the points whose taps cover that cell and adds the sum to the block's
 // global grid.
+template <class Acc>
 __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                             const double* __restrict__ r_s, const float2* __restrict__ r2,
-                            const float2* __restrict__ c2, Accum gb, float4* smem4)
+                            const float2* __restrict__ c2, Acc gb, float4* smem4)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -852,11 +854,10 @@ __global__ void k_spread_modes(const ProbParams* __restrict__ probs, const AsyBl
     }
 }
 
-// At most 64 registers: four CTAs of 256 threads fit an SM whenever their
-// shared memory does (the out-of-line deterministic accumulation would
-// otherwise raise the allocation to 80 and cost a CTA per SM at small 2M).
-__global__ void __launch_bounds__(256, 4)
-k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
+// One instance per accumulation mode (DET: the deterministic mode's exact
+// fixed-point sums), so that the FP64 path carries no code of the other.
+template <bool DET>
+__global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, const int32_t* __restrict__ modes, Tables tab,
                              const double* __restrict__ r_s, const float2* __restrict__ r2,
                              const float2* __restrict__ c2, double2* __restrict__ grid_b)
@@ -867,7 +868,8 @@ k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ 
     const int mode = modes[blockIdx.x];
     const AsyBlock B = blks[t.blk];
     const int Q = probs[B.prob].Q;
-    const Accum gb = Accum{(double*)grid_b, probs[B.prob].fxs}.at(2 * B.b_off);
+    using Acc = typename AccumOf<DET>::type;
+    const Acc gb = Acc{(double*)grid_b, probs[B.prob].fxs}.at(2 * B.b_off);
     if ((mode & 3) == 2)
         spread_fold(B, Q, probs[B.prob].qs, t, tab, fold_unpack(mode), r_s, r2, c2, gb, smem4);
     else if (mode & 3) {
@@ -2282,7 +2284,7 @@ cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, c
 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                              const float2* r2, const float2* c2, double2* grid_b, cudaStream_t s)
+                              const float2* r2, const float2* c2, double2* grid_b, int det, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
@@ -2291,9 +2293,10 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     if (smem_mom > smem) smem = smem_mom;
     const size_t smem_fold = spread_fold_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
     if (smem_fold > smem) smem = smem_fold;
-    cudaError_t e = cudaFuncSetAttribute(k_asy_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = det ? k_asy_spread<true> : k_asy_spread<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, grid_b);
+    kern<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, grid_b);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -280,7 +280,7 @@ cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, c
                                 Tables tab, const double* r_s, int32_t* modes, cudaStream_t s);
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                              const float2* r2, const float2* c2, double2* grid_b, cudaStream_t s);
+                              const float2* r2, const float2* c2, double2* grid_b, int det, cudaStream_t s);
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
                                   double2* tgrid, cudaStream_t s);

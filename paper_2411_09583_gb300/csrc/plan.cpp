@@ -1252,7 +1252,8 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
                                           P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc, as));
         else
             NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc, as));
+                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc,
+                                      P->det ? 1 : 0, as));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_gb, (double*)P->d_gb, 2 * P->gb_len, P->d_prob, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
