@@ -337,7 +337,7 @@ def run_batched(dev, steps):
     from paper_2411_09583_gb300.autotune import autotune, candidates
     grid = candidates(nus, 1e-8, min_sizes=(512, 1024, 2048), spread_tiles=(0, 128), m_offsets=(0,))
     best, table = autotune(nus, dr, dw, dc, 1e-8, sizes=(n, m), objective="execute", reps=3, grid=grid)
-    default_ms = [t for t, o in table if o == {"min_size": 1024, "spread_tile": 0, "m_terms": 0}]
+    default_ms = [t for t, o in table if o == {"min_size": 1024, "spread_tile": 0, "m_terms": 0, "interp_tile": 0}]
     for _ in range(2):
         Plan.many(nus, dr, n, dw, m, 1e-8, **best).close()
     plan_ms = []
@@ -717,7 +717,7 @@ def run_ours(a):
         grid = candidates([a.nu], a.eps, min_sizes=(1024, 2048, 4096, 8192), spread_tiles=(0, 128),
                           m_offsets=(0, 1))
         opts, table = autotune(a.nu, dr, dw, dc, a.eps, objective="plan+execute", reps=3, grid=grid)
-        dflt = [t for t, o in table if o == {"min_size": 1024, "spread_tile": 0, "m_terms": 0}]
+        dflt = [t for t, o in table if o == {"min_size": 1024, "spread_tile": 0, "m_terms": 0, "interp_tile": 0}]
         tuned = {"opts": opts, "best_ms": table[0][0], "default_opts_ms": dflt[0] if dflt else None,
                  "candidates": len(grid), "objective": "plan+execute"}
 

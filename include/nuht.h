@@ -104,7 +104,10 @@ typedef struct {
                           poll) until its block's moments are complete.  A wait that gives
                           up records NUHT_ERR_TIMEOUT for nuht_status.  Not used with
                           deterministic = 1.  Default 0 (two launches). */
-    int reserved[3];   /* must be zero */
+    int interp_tile;   /* frequencies per interpolation CTA (also the adjoint's spreading of
+                          frequencies): 0 = 256, or 128 (better when the asymptotic blocks
+                          hold few frequencies each) */
+    int reserved[2];   /* must be zero */
 } nuht_opts;
 
 /* Execute stages, in launch order (nuht_stage_times / nuht_stage_name). */

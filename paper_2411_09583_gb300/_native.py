@@ -43,7 +43,8 @@ class NuhtOpts(ctypes.Structure):
                 ("n_split_cand", ctypes.c_int), ("m_terms", ctypes.c_int),
                 ("class_mask", ctypes.c_int), ("timing", ctypes.c_int),
                 ("spread_tile", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("persistent", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("persistent", ctypes.c_int), ("interp_tile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class NuhtPlanInfo(ctypes.Structure):

@@ -8,7 +8,8 @@ a small grid of options and keeps the fastest:
                      crossover z (and with it L), i.e. work between the local
                      and the asymptotic expansions; z and L are re-derived from
                      the error bounds, so every candidate keeps the accuracy;
-  * spread_tile   -- points per spreading CTA.
+  * spread_tile   -- points per spreading CTA;
+  * interp_tile   -- frequencies per interpolation CTA.
 Every candidate runs the same kernels through the C ABI; nothing is skipped.
 """
 import itertools
@@ -32,13 +33,13 @@ def _time(fn, stream, reps):
 
 
 def candidates(nus, eps, min_sizes=(256, 512, 1024, 2048, 4096), spread_tiles=(0, 128),
-               m_offsets=(-1, 0, 1)):
+               m_offsets=(-1, 0, 1), interp_tiles=(0, 128)):
     """Option grid; m_terms offsets apply to the heuristic M of the first order."""
     M0 = choose_params(int(nus[0]), eps)[0]
     ms = sorted({max(1, min(20, M0 + d)) for d in m_offsets})
     out = []
-    for mn, st, M in itertools.product(min_sizes, spread_tiles, ms):
-        out.append({"min_size": mn, "spread_tile": st, "m_terms": 0 if M == M0 else M})
+    for mn, st, M, it in itertools.product(min_sizes, spread_tiles, ms, interp_tiles):
+        out.append({"min_size": mn, "spread_tile": st, "m_terms": 0 if M == M0 else M, "interp_tile": it})
     return out
 
 

@@ -41,7 +41,8 @@ namespace nuht {
 namespace {
 
 constexpr int kWinCells = 64;   // grid cells an interpolation tile stages in shared memory
-constexpr int kInterpTileThreads = 128;   // frequencies per interpolation tile (host: kInterpTile)
+constexpr int kInterpTileThreads = 256;   // most frequencies per interpolation tile (one thread each)
+constexpr int kAdjInterpThreads = 128;    // points per pass of an adjoint interpolation tile
 
 // ------------------------------------------------------------------ spread
 // A point r_j of a block covers the w grid cells l0 + i, i < w, with
@@ -1320,14 +1321,18 @@ __global__ void k_asy_fft_pass_b(const ProbParams* __restrict__ probs, const Asy
 }
 
 // ------------------------------------------------------------ interpolate
-constexpr int kInterpHBytes = 16384;    // shared bytes for the per-bin sums of a dense tile
+// Shared bytes for the per-bin sums of a dense tile, per thread: room for
+// threads / kMomMinPerBin bins (16 bins of a 256-frequency tile, 8 of a 128 one).
+constexpr int kInterpHBytesPerThread = 128;
+constexpr int kAdjInterpHBytes = kInterpHBytesPerThread * kAdjInterpThreads;
 
 // Shared memory (bytes) of k_asy_interp for 2M = qmax.
-__host__ __device__ __forceinline__ size_t interp_smem(int qmax, int w, int deg)
+__host__ __device__ __forceinline__ size_t interp_smem(int qmax, int w, int deg, int threads,
+                                                      int hbytes)
 {
     const int us = (deg + 1 > w ? deg + 1 : w) | 1;
     return sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)((w * (deg + 1) + 1) & ~1) +
-           kInterpHBytes + sizeof(float2) * (size_t)kInterpTileThreads * us + sizeof(int) * kInterpTileThreads;
+           hbytes + sizeof(float2) * (size_t)threads * us + sizeof(int) * threads;
 }
 
 // Per-bin sums of a staged window (dense interpolation tiles):
@@ -1530,8 +1535,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const int hs = nb * Q2 + 2;                                  // bin stride of H (float2)
     float2* coef2 = (float2*)(win + kWinCells * Q);              // [w][deg + 1] taps, or [w][nb] Chebyshev
     float2* H = coef2 + ((w * (deg + 1) + 1) & ~1);              // [bins][hs], 16-byte aligned
-    float2* U = H + kInterpHBytes / sizeof(float2);              // [threads][us]
-    int* t0s = (int*)(U + kInterpTileThreads * us);              // [threads]
+    const int hbytes = kInterpHBytesPerThread * (int)blockDim.x;
+    float2* U = H + hbytes / sizeof(float2);                     // [threads][us]
+    int* t0s = (int*)(U + blockDim.x * us);                      // [threads]
     const bool valid = (int)threadIdx.x < t.count;
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
     long long Om, Sw, svw;
@@ -1547,7 +1553,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const int mask = B.nf2 - 1;
     const float4* gq = grid_q + B.q_off;
     const bool staged = wlen <= kWinCells;
-    const int maxbins = kInterpHBytes / (int)(sizeof(float2) * hs);
+    const int maxbins = hbytes / (int)(sizeof(float2) * hs);
     const bool mom = staged && nbins <= maxbins && t.count >= kMomMinPerBin * nbins;
     if (staged) {
         for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
@@ -1768,7 +1774,7 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
 // l0 + i, i < w (zero outside the 2 N1 + 1 modes).  Dense passes (many points
 // per cell) form the per-bin sums H[d][q'] once per bin and each point sums
 // P_q = sum_d T_d(v) H[d][q]; sparse passes evaluate the w taps of each point.
-__global__ void __launch_bounds__(kInterpTileThreads) k_asy_adj_interp(
+__global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
     Tables tab, const double* __restrict__ r_s, const float4* __restrict__ bgrid, double* __restrict__ c_s)
 {
@@ -1782,11 +1788,11 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_adj_interp(
     const int hs = nb * Q2 + 2;
     float2* coef2 = (float2*)(win + kWinCells * Q);              // [w][deg + 1] taps, or [w][nb] Chebyshev
     float2* H = coef2 + ((w * (deg + 1) + 1) & ~1);              // [bins][hs], 16-byte aligned
-    float2* U = H + kInterpHBytes / sizeof(float2);              // [threads][us]
-    int* l0s = (int*)(U + kInterpTileThreads * us);              // [threads]
+    float2* U = H + kAdjInterpHBytes / sizeof(float2);              // [threads][us]
+    int* l0s = (int*)(U + kAdjInterpThreads * us);              // [threads]
     const float4* gb = bgrid + B.b_off;
     const int nf1 = 2 * B.N1 + 1;
-    const int maxbins = kInterpHBytes / (int)(sizeof(float2) * hs);
+    const int maxbins = kAdjInterpHBytes / (int)(sizeof(float2) * hs);
     for (int base = 0; base < t.count; base += blockDim.x) {
         const int cnt = t.count - base < (int)blockDim.x ? t.count - base : (int)blockDim.x;
         const bool valid = (int)threadIdx.x < cnt;
@@ -2083,11 +2089,11 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
 }
 
 // Shared memory (bytes) of k_asy_interp_f32 for 2M = qmax.
-__host__ __device__ __forceinline__ size_t interp_f32_smem(int qmax, int w, int deg)
+__host__ __device__ __forceinline__ size_t interp_f32_smem(int qmax, int w, int deg, int threads)
 {
     const int us = (deg + 1 > w ? deg + 1 : w) | 1;
     return sizeof(float4) * (size_t)kWinCells * qmax + sizeof(float2) * (size_t)((w * (deg + 1) + 1) & ~1) +
-           kInterpHBytes + sizeof(float) * (size_t)kInterpTileThreads * us + sizeof(int) * kInterpTileThreads;
+           (size_t)kInterpHBytesPerThread * threads + sizeof(float) * (size_t)threads * us + sizeof(int) * threads;
 }
 
 // FP32 interpolation and Hankel combination (coordinates and phase
@@ -2108,8 +2114,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     const int hs = nb * Q2 + 2;                                  // bin stride of H (floats, even)
     float2* coef2 = (float2*)(winf + kWinCells * Q);
     float* H = (float*)(coef2 + ((w * (deg + 1) + 1) & ~1));     // [bins][hs]
-    float* U = H + kInterpHBytes / sizeof(float);                // [threads][us]
-    int* t0s = (int*)(U + kInterpTileThreads * us);
+    const int hbytes = kInterpHBytesPerThread * (int)blockDim.x;
+    float* U = H + hbytes / sizeof(float);                       // [threads][us]
+    int* t0s = (int*)(U + blockDim.x * us);
     const bool valid = (int)threadIdx.x < t.count;
     const int64_t k = t.start + (valid ? threadIdx.x : 0);
     long long Om, Sw, svw;
@@ -2123,7 +2130,7 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     const int mask = B.nf2 - 1;
     const float4* gq = grid_q + B.q_off;
     const bool staged = wlen <= kWinCells;
-    const int maxbins = kInterpHBytes / (int)(sizeof(float) * hs);
+    const int maxbins = hbytes / (int)(sizeof(float) * hs);
     const bool mom = staged && nbins <= maxbins && t.count >= kMomMinPerBin * nbins;
     if (staged)
         for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
@@ -2213,11 +2220,11 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
 }  // namespace
 
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
+                                  int ntiles, int qmax, int nt, Tables tab, const double* w_s, const double* g_s,
                                   double2* tgrid, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const int nt = kInterpTileThreads;
+    if (nt < 32 || nt > kInterpTileThreads || (nt & 31)) return cudaErrorInvalidValue;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     const size_t smem_mom = spread_moments_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
@@ -2234,10 +2241,10 @@ cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks,
                                   double* c_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = interp_smem(qmax, tab.w, tab.deg);
+    const size_t smem = interp_smem(qmax, tab.w, tab.deg, kAdjInterpThreads, kAdjInterpHBytes);
     cudaError_t e = cudaFuncSetAttribute(k_asy_adj_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_adj_interp<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, c_s);
+    k_asy_adj_interp<<<ntiles, kAdjInterpThreads, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, c_s);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -2260,14 +2267,15 @@ cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks,
 }
 
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                                  int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
                                   const float4* grid_q, double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = interp_f32_smem(qmax, tab.w, tab.deg);
+    if (nt < 32 || nt > kInterpTileThreads || (nt & 31)) return cudaErrorInvalidValue;
+    const size_t smem = interp_f32_smem(qmax, tab.w, tab.deg, nt);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp_f32<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
+    k_asy_interp_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -2376,14 +2384,15 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
 }
 
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                              int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
                               const float4* grid_q, double* g_s, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = interp_smem(qmax, tab.w, tab.deg);
+    if (nt < 32 || nt > kInterpTileThreads || (nt & 31)) return cudaErrorInvalidValue;
+    const size_t smem = interp_smem(qmax, tab.w, tab.deg, nt, kInterpHBytesPerThread * nt);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp<<<ntiles, kInterpTileThreads, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
+    k_asy_interp<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
     count_launches(1);
     return cudaGetLastError();
 }

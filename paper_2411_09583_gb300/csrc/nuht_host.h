@@ -61,7 +61,7 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
 void pool_free(void* p, cudaStream_t s);
 
 inline int spread_tile_points(int qmax) { return qmax > 16 ? 128 : 256; }
-constexpr int kInterpTile = 128;
+constexpr int kInterpTileMax = 256;   // frequencies per interpolation tile: 256 (default) or 128
 constexpr int kMomentTile = 2048;
 
 }  // namespace nuht

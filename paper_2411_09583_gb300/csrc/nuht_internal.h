@@ -282,7 +282,7 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
                               const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
                               const float2* r2, const float2* c2, double2* grid_b, int det, cudaStream_t s);
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* w_s, const double* g_s,
+                                  int ntiles, int qmax, int nt, Tables tab, const double* w_s, const double* g_s,
                                   double2* tgrid, cudaStream_t s);
 cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
@@ -292,7 +292,7 @@ cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks,
                                   const double* r_s, const float2* r2, const float2* c2, double2* grid_b,
                                   cudaStream_t s);
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                                  int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                                  int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
                                   const float4* grid_q, double* g_s, cudaStream_t s);
 // lowp: FP32 butterflies on the FP32 parts of the values (mixed precision).
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
@@ -307,7 +307,7 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
                                  const double2* src, float4* tmp, float4* dst,
                                  cudaStream_t s, bool adj = false, bool lowp = false);
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
-                              int ntiles, int qmax, Tables tab, const double* w_s, const float2* w2,
+                              int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
                               const float4* grid_q, double* g_s, cudaStream_t s);
 
 }  // namespace nuht

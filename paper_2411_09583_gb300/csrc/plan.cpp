@@ -132,6 +132,7 @@ struct nuht_plan_s {
     int max_fblock_pts = 0;   // largest nf2 * Q among the blocks FFT'd whole by one CTA
     int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, max_dir_area = 0, ntop_max = 0, eval_threads = 0;
     int spread_threads = 256;
+    int interp_threads = kInterpTileMax;   // frequencies per interpolation tile (one thread each)
     bool has_large_fft = false;
     Tables tab{};
     SubBlk* d_blk = nullptr;          // every block (local, asymptotic, direct), global sorted indices
@@ -683,7 +684,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     bb.mom_tile = kMomentTile;
     bb.eval_tile = P->eval_threads;
     bb.spread_tile = sp_tile;
-    bb.interp_tile = kInterpTile;
+    P->interp_threads = P->opt.interp_tile ? P->opt.interp_tile : kInterpTileMax;
+    bb.interp_tile = P->interp_threads;
     bind_build_temps(bb, sort_mem, bt);
     int64_t* bb_scan = (int64_t*)(sort_mem + bt.scan);
     char* tmp_mem = nullptr;   // temporaries of the host fallback
@@ -1078,10 +1080,11 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
     if (o.min_size < 1 || o.min_size > NUHT_MAX_MIN_SIZE || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
     if (o.deterministic != 0 && o.deterministic != 1) return NUHT_ERR_INVALID_ARG;
     if (o.persistent != 0 && o.persistent != 1) return NUHT_ERR_INVALID_ARG;
+    if (o.interp_tile != 0 && o.interp_tile != 128 && o.interp_tile != 256) return NUHT_ERR_INVALID_ARG;
     if (o.spread_tile != 0 && (o.spread_tile < 64 || o.spread_tile > 256 || o.spread_tile % 32))
         return NUHT_ERR_INVALID_ARG;
     if (o.timing < NUHT_TIMING_OFF || o.timing > NUHT_TIMING_SERIAL) return NUHT_ERR_INVALID_ARG;
@@ -1268,10 +1271,12 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
         if (P->opt.precision == NUHT_PREC_MIXED)
-            NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
+            NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax,
+                                          P->interp_threads, P->tab,
                                           P->d_w, P->d_w2, P->d_gq, gs, as));
         else
-            NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab,
+            NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax,
+                                      P->interp_threads, P->tab,
                                       P->d_w, P->d_w2, P->d_gq, gs, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
     }
@@ -1387,7 +1392,8 @@ static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     if (asy) {
         NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_CK(cudaMemsetAsync(tg_acc, 0, acc_bytes(P, 2 * P->gq_len), as));
-        NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->tab, P->d_w,
+        NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->interp_threads,
+                                      P->tab, P->d_w,
                                       P->d_gs, tg_acc, as));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_tg, (double*)P->d_tg, 2 * P->gq_len, P->d_prob, as));
         NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));

@@ -395,10 +395,29 @@ def test_autotuner_picks_valid_fast_options():
 
 
 @pytest.mark.parametrize("opts", [{"min_size": 64}, {"min_size": 5000}, {"m_terms": 2},
-                                  {"m_terms": 7}, {"spread_tile": 64}, {"n_split_cand": 3}])
+                                  {"m_terms": 7}, {"spread_tile": 64}, {"n_split_cand": 3},
+                                  {"interp_tile": 128}, {"interp_tile": 256}])
 def test_option_variants_keep_accuracy(opts):
     r, omega, c = uniform_problem(1500, 1400, omega_max=2500.0, seed=91)
     _check(1, r, omega, c, 1e-10, **opts)
+
+
+@pytest.mark.parametrize("interp_tile", [128, 256])
+def test_interp_tile_both_directions_dense_and_mixed(interp_tile):
+    # both interpolation tile sizes on dense bins (the per-bin sums, up to 16
+    # bins of a 256-frequency tile) and in mixed precision, forward and adjoint
+    from paper_2411_09583_gb300 import Plan
+    rng = np.random.default_rng(96)
+    r, omega = rng.uniform(1.0, 1.05, 3000), rng.uniform(1000.0, 1200.0, 30000)
+    c, e = rng.standard_normal(r.size), rng.standard_normal(omega.size)
+    for precision, eps in (("fp64", 1e-11), ("mixed", 1e-6)):
+        with Plan(2, to_dev(r), to_dev(omega), eps, precision=precision, interp_tile=interp_tile) as p:
+            g = p.execute(to_dev(c)).cpu().numpy()
+            a = p.adjoint(to_dev(e)).cpu().numpy() if precision == "fp64" else None
+        rows = np.arange(0, omega.size, 37)
+        assert np.max(np.abs(g[rows] - oracle.direct_rows(2, r, omega, c, rows))) <= tol(eps, c)
+        if a is not None:
+            assert np.max(np.abs(a - oracle.direct(2, omega, r, e))) <= tol(eps, e)
 
 
 def test_host_subdivision_fallback_matches(monkeypatch):

@@ -66,7 +66,8 @@ def test_invalid_arguments(lib):
     # option checks run before any device work
     one = (ctypes.c_double * 1)(0.5)
     for field, bad in (("min_size", 0), ("min_size", 16385), ("n_split_cand", 1), ("spread_tile", 96 + 1),
-                       ("precision", 2), ("m_terms", 21), ("deterministic", 2)):
+                       ("precision", 2), ("m_terms", 21), ("deterministic", 2), ("persistent", 3),
+                       ("interp_tile", 64), ("interp_tile", 512)):
         b = N.NuhtOpts()
         lib.nuht_default_opts(ctypes.byref(b))
         setattr(b, field, bad)
