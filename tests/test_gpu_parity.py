@@ -449,3 +449,27 @@ def test_batched_host_subdivision_fallback_matches(monkeypatch):
     with Plan.many(nus, dr, n, dw, m, 1e-8) as p:
         g1 = p.execute(to_dev(cc)).cpu().numpy()
     assert np.max(np.abs(g0 - g1)) <= 1e-12 * np.abs(cc).sum()
+
+
+def test_checked_mode_and_plan_lists_pass_the_work_list_check(monkeypatch):
+    # NUHT_CHECKED: the plan checks its device-built lists on the host before
+    # returning (exact cover, classes, direct areas); a plan's lists, read
+    # back with nuht_get_blocks, also pass nuht_check_blocks directly
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300 import _native as N
+    from paper_2411_09583_gb300.nuht import check_blocks
+    r, omega, c = uniform_problem(20000, 15000, omega_max=2e4, seed=92)
+    monkeypatch.setenv("NUHT_CHECKED", "1")
+    with Plan(3, to_dev(r), to_dev(omega), 1e-9, min_size=512) as p:
+        g = p.execute(to_dev(c)).cpu().numpy()
+        blocks = [p.blocks(k) for k in range(3)]
+    monkeypatch.delenv("NUHT_CHECKED")
+    rows = sample_rows(omega.size, 100, seed=93)
+    assert np.max(np.abs(g[rows] - oracle.direct_rows(3, r, omega, c, rows))) <= tol(1e-9, c)
+    ranges = np.concatenate(blocks)
+    cls = np.concatenate([np.full(len(b), k, np.int32) for k, b in enumerate(blocks)])
+    rs, ws = np.sort(r), np.sort(omega)
+    assert check_blocks(3, 1e-9, rs, ws, ranges, cls, min_size=512) == N.NUHT_OK
+    bad = ranges.copy()
+    bad[0, 3] += 1
+    assert check_blocks(3, 1e-9, rs, ws, bad, cls, min_size=512) == N.NUHT_ERR_BAD_BLOCKS
