@@ -858,11 +858,20 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     auto put = [&](size_t off, const void* src, size_t bytes) {
         if (bytes) std::memcpy(stage + off, src, bytes);
     };
+    // Rounding budget of the FP32 tiers.  Each tier below (the taps'
+    // polynomial degrees, the spreading moments' degrees, the q-fold's
+    // moments, the interpolation's degrees and its per-pair cut) keeps its
+    // rounding bound -- a bound relative to the sum of magnitudes, far above
+    // the typical rounding -- below kRoundBudget eps.  A point or frequency
+    // meets at most four of them, so together they stay below eps / 2, beside
+    // the expansions' truncation of at most eps per entry (Lemma 3.1, Sec. 3.2
+    // eq. asy-error) and inside the 10 eps ||c||_1 contract.
+    constexpr double kRoundBudget = 0.1;
     // Per Hankel pair, the degrees of the interpolation's per-bin and
     // per-frequency sums that need double-float: term q enters g with weight
     // at most |a_q| z^-q, so degree d may round in FP32 once the rounding bound
     // of the degrees from d on (as for tab.dci, whose weight is one) times the
-    // pair's larger weight stays below 1e-2 eps.
+    // pair's larger weight stays below kRoundBudget eps.
     {
         const int nc = T.deg + 1;
         std::vector<double> colsum(nc, 0.0);
@@ -877,7 +886,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
                 double acc = 0.0;
                 while (d > 2) {
                     acc += colsum[d - 1] * (d + 2) * 5.9604644775390625e-08;
-                    if (acc * wmax <= 1e-2 * P->eps) --d; else break;
+                    if (acc * wmax <= kRoundBudget * P->eps) --d; else break;
                 }
                 pp.dcp[pr] = (int8_t)d;
             }
@@ -958,7 +967,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     tb.es = P->d_es; tb.es2 = (const float2*)(D + a_es2);
     tb.w = T.w; tb.deg = T.deg; tb.half_w = 0.5 * T.w;
     // plain FP32 for the degrees whose coefficient tail T_k = max_taps sum_{k' > k} |c_k'|
-    // keeps the FP32 rounding (2^-23 T_k) below 1e-2 eps
+    // keeps the FP32 rounding (2^-23 T_k) below kRoundBudget eps
     tb.deg_comp = T.deg;
     for (int k = T.deg - 1; k >= 0; --k) {
         double tail = 0.0;
@@ -967,12 +976,12 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
             for (int kk = k + 1; kk <= T.deg; ++kk) sum += std::fabs(T.es[(size_t)i * (T.deg + 1) + kk]);
             tail = sum > tail ? sum : tail;
         }
-        if (tail * 1.1920928955078125e-07 <= 1e-2 * P->eps) tb.deg_comp = k; else break;
+        if (tail * 1.1920928955078125e-07 <= kRoundBudget * P->eps) tb.deg_comp = k; else break;
     }
     // Chebyshev form of the taps (moment paths): nb terms, dropping a tail
     // below 1e-3 eps; degrees >= dcs of the spreading moments accumulate in
     // FP32 over at most ceil(tile / 8) points each, degrees >= dci of the
-    // interpolation sum in FP32, both with rounding below 1e-2 eps.
+    // interpolation sum in FP32, both with rounding below kRoundBudget eps.
     tb.ch2 = (const float2*)(D + a_ch2);
     {
         const int nc = T.deg + 1;
@@ -991,21 +1000,21 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
         tb.nb = nb;
         const int nsub = (P->spread_threads + 7) / 8;
         int dcs = nb;
-        while (dcs > 2 && tailmax[dcs - 1] * (nsub + nb) * 1.1920928955078125e-07 <= 1e-2 * P->eps) --dcs;
+        while (dcs > 2 && tailmax[dcs - 1] * (nsub + nb) * 1.1920928955078125e-07 <= kRoundBudget * P->eps) --dcs;
         tb.dcs = dcs;
         int dci = nb;
         double acc = 0.0;
         while (dci > 2) {
             acc += colsum[dci - 1] * (dci + 2) * 5.9604644775390625e-08;
-            if (acc <= 1e-2 * P->eps) --dci; else break;
+            if (acc <= kRoundBudget * P->eps) --dci; else break;
         }
         tb.dci = dci;
         // q-folded spreading: the weights' Chebyshev terms are kept down to
-        // 1e-3 eps; a term above 1e-2 eps / ((kMomFold + 2) 2^-23) multiplies
+        // 1e-3 eps; a term above kRoundBudget eps / ((kMomFold + 2) 2^-23) multiplies
         // moments whose FP32 partial sums (kMomFold points) would show, so
         // those moments stay double-float
         tb.fold_tol = (float)(1e-3 * P->eps);
-        tb.fold_df_tol = (float)(1e-2 * P->eps / ((kMomFold + 2) * 1.1920928955078125e-07));
+        tb.fold_df_tol = (float)(kRoundBudget * P->eps / ((kMomFold + 2) * 1.1920928955078125e-07));
     }
     tb.ph = P->d_ph; tb.ph2 = (const float2*)(D + a_ph2);
     tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
