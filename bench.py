@@ -300,7 +300,7 @@ def stored_traffic(kernel, workload, opts=None, units=None):
         return None, "no capture"
     try:
         db = json.load(open(path))
-        ent = db.get(kernel)
+        ent = db.get(kernel + "@" + workload) or db.get(kernel)
         if not ent or ent.get("workload") != workload:
             return None, "no capture of this kernel and workload"
         if ent.get("source_hash") != source_hash(*ent.get("sources", [])):
