@@ -646,8 +646,10 @@ def run_large_grid(dev, steps):
 
 def run_multi_vector(dev, steps, nvec=16):
     """The n = m = 1e6, nu = 0, eps = 1e-12 workload with nvec coefficient vectors in
-    one execute (plan reused), against one vector: per-vector throughput and the error
-    of every vector on sampled rows."""
+    one execute (plan reused), against one vector: per-vector throughput with the
+    default pairs (vec_group 0) and with all nvec vectors in one group (their local
+    and direct blocks' Bessel work shared), stage times of the grouped call, and
+    the error of every vector on sampled rows."""
     import numpy as np
     import torch
 
@@ -661,26 +663,41 @@ def run_multi_vector(dev, steps, nvec=16):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {"workload": "n = m = 1e6, nu = 0, eps 1e-12, r ~ U[0,1], omega ~ U[0,1e5], %d vectors c ~ N(0,1)" % nvec,
            "unit": UNIT, "step": "execute (plan reused), L2 flushed"}
+
+    def timed(p, x):
+        for _ in range(2):
+            p.execute(x)
+        ms = []
+        for _ in range(max(3, steps // 4)):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            g = p.execute(x)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(s0.elapsed_time(s1))
+        return statistics.median(ms), g
+
+    grouped = "nvec_%d_group_%d" % (nvec, nvec)
     with Plan(0, dr, dw, 1e-12, min_size=2048) as p:
         for label, x in (("nvec_1", dc1), ("nvec_%d" % nvec, dC)):
-            for _ in range(2):
-                p.execute(x)
-            ms = []
-            for _ in range(max(3, steps // 4)):
-                flush.zero_()
-                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s0.record(stream)
-                g = p.execute(x)
-                s1.record(stream)
-                torch.cuda.synchronize(dev)
-                ms.append(s0.elapsed_time(s1))
-            t = statistics.median(ms)
+            t, _ = timed(p, x)
             k = x.shape[1] if x.dim() > 1 else 1
-            out[label] = {"ms": t, "value_per_vector": 2e6 / (t * 1e-3 / k), "vectors": k}
+            out[label] = {"ms": t, "value_per_vector": 2e6 / (t * 1e-3 / k), "vectors": k, "vec_group": "pairs"}
+    with Plan(0, dr, dw, 1e-12, min_size=2048, vec_group=nvec) as p:
+        t, g = timed(p, dC)
+        out[grouped] = {"ms": t, "value_per_vector": 2e6 / (t * 1e-3 / nvec), "vectors": nvec,
+                        "vec_group": nvec}
         gh = g.cpu().numpy()
+    with Plan(0, dr, dw, 1e-12, min_size=2048, vec_group=nvec, timing="serial") as p:
+        p.execute(dC)
+        torch.cuda.synchronize(dev)
+        out[grouped]["stage_ms_serial"] = p.stage_times()
     rows = sample_rows(omega.size, 60, seed=91)
     out["error"] = sampled_error(0, r, omega, C, gh, 1e-12, rows)
-    out["per_vector_speedup"] = out["nvec_%d" % nvec]["value_per_vector"] / out["nvec_1"]["value_per_vector"]
+    base = out["nvec_1"]["value_per_vector"]
+    out["per_vector_speedup"] = {"pairs": out["nvec_%d" % nvec]["value_per_vector"] / base,
+                                 "group": out[grouped]["value_per_vector"] / base}
     return out
 
 

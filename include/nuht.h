@@ -71,6 +71,9 @@ extern "C" {
    and its entry list stay in one CTA's shared memory. */
 #define NUHT_MAX_MIN_SIZE 16384
 
+/* Upper limit of nuht_opts.vec_group. */
+#define NUHT_MAX_VEC_GROUP 16
+
 /* opts.timing: NUHT_TIMING_OFF records nothing; NUHT_TIMING_LIVE records a
  * CUDA event pair around each stage on the stream the stage runs on (the
  * block classes run concurrently as in an untimed execute, so the stage times
@@ -107,7 +110,15 @@ typedef struct {
     int interp_tile;   /* frequencies per interpolation CTA (also the adjoint's spreading of
                           frequencies): 0 = 256, or 128 (better when the asymptotic blocks
                           hold few frequencies each) */
-    int reserved[2];   /* must be zero */
+    int vec_group;     /* real components (vectors, or the parts of complex c) whose local
+                          and direct blocks nuht_execute applies together, sharing their
+                          Bessel work (the moment basis, the Miller sweeps, the direct
+                          entries; the moments become one dense (L+1) x n_b by n_b x G
+                          product per block): 1..NUHT_MAX_VEC_GROUP, 0 = 2.  The plan
+                          holds G copies of the sorted coefficient, moment and output
+                          arrays.  Above 2 not with deterministic = 1 or persistent = 1.
+                          The adjoint shares in pairs whenever this is not 1. */
+    int reserved;      /* must be zero */
 } nuht_opts;
 
 /* Execute stages, in launch order (nuht_stage_times / nuht_stage_name). */

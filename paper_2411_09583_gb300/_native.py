@@ -44,7 +44,7 @@ class NuhtOpts(ctypes.Structure):
                 ("class_mask", ctypes.c_int), ("timing", ctypes.c_int),
                 ("spread_tile", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("interp_tile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("vec_group", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class NuhtPlanInfo(ctypes.Structure):

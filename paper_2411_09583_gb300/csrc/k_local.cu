@@ -1022,6 +1022,241 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
         atomicAdd(&c_s[B.j0 + i], (double)P.sgn * colacc[i]);
 }
 
+// ------------------------------------------------------------ vector groups
+// The G real components of one call (vectors, or the parts of complex c)
+// share the local and direct blocks' Bessel work: the basis T_{2l(+1)}(r_j/R)
+// of a point and the Miller sweep of a row are formed once for all G, and a
+// direct entry is evaluated once.  The moments are then the dense product of
+// Sec. 3.1's factorisation applied to G columns at once,
+//     mu[v][l] = sum_j T_{2l(+1)}(r_j / R) c_v[j]    ((L+1) x n_b by n_b x G per block),
+// and a row's evaluation is sum_l C_l(omega_k R) mu[v][l] for every v.
+// Component v's data sit at v times a stride (c_stride, mom_stride, g_stride)
+// from the first's.
+
+// One CTA per moment tile, in passes of blockDim points.  Each thread forms
+// one point's basis into Tb[l][p] and stages its G coefficients in Cs[v][p]
+// (double-float).  The (L+1) G outputs o = l G + v are then split over the
+// threads: item it = o S + sub sums the pass's points p = sub (mod S) into a
+// compensated accumulator that stays in registers across the passes (S = 1,
+// 2, 4 or 8 lanes per output, so that small products still use the whole
+// CTA); the S partial sums meet by shuffles, one atomic add per output and tile.
+constexpr int kMomGroupOut = 8;   // items per thread
+
+__global__ void __launch_bounds__(kMomThreads)
+k_local_moments_group(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                      const Tile* __restrict__ tiles, const float2* __restrict__ r2,
+                      const float2* __restrict__ c2, int64_t c_stride, int G, double* __restrict__ mom,
+                      int64_t mom_stride)
+{
+    extern __shared__ float2 smg[];
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int L = P.L, odd = P.nu & 1;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int O = (L + 1) * G;
+    int S = 1;
+    while (S < 8 && O * S < 2 * nt) S <<= 1;
+    const int ps = nt + S;                 // row stride of Tb and Cs
+    float2* Tb = smg;                      // [L + 1][ps]
+    float2* Cs = smg + (L + 1) * ps;       // [G][ps]
+    const int items = O * S;
+    const int nout = (items + nt - 1) / nt;   // <= kMomGroupOut (checked by the launcher)
+    const int sub = tid & (S - 1);
+    int toff[kMomGroupOut], coff[kMomGroupOut];
+    acc2 a[kMomGroupOut];
+#pragma unroll
+    for (int i = 0; i < kMomGroupOut; ++i) {
+        const int it = tid + i * nt;
+        const int o = it < items ? it / S : 0;
+        const int l = o / G;
+        toff[i] = l * ps;
+        coff[i] = (o - l * G) * ps;
+        a[i] = acc2{0.f, 0.f};
+    }
+    const df invR{B.iR_h, B.iR_l};
+    const int64_t jend = t.start + t.count;
+    for (int64_t j0 = t.start; j0 < jend; j0 += nt) {
+        const int np = (int)(jend - j0 < nt ? jend - j0 : nt);
+        __syncthreads();   // the previous pass's reads are done
+        if (tid < np) {
+            const int64_t j = j0 + tid;
+            const float2 rj = r2[j];
+            const df y = df_mul(df{rj.x, rj.y}, invR);                          // r_j / R in [0, 1]
+            const df u = df_add(df_mul(df{2.f * y.h, 2.f * y.l}, y), df{-1.f, 0.f});   // T_2(y)
+            const df u2{2.f * u.h, 2.f * u.l};
+            // even: T_{2l}(y) = T_l(u); odd: T_{2l+1}(y) with T_1 = y, T_3 = y (2u - 1)
+            df t0 = odd ? y : df{1.f, 0.f};
+            df t1 = odd ? df_mul(y, df_add(u2, df{-1.f, 0.f})) : u;
+            Tb[tid] = make_float2(t0.h, t0.l);
+            if (L >= 1) Tb[ps + tid] = make_float2(t1.h, t1.l);
+            for (int l = 2; l <= L; ++l) {
+                const df t2 = df_add(df_mul(u2, t1), df_neg(t0));
+                Tb[l * ps + tid] = make_float2(t2.h, t2.l);
+                t0 = t1;
+                t1 = t2;
+            }
+            for (int v = 0; v < G; ++v) Cs[v * ps + tid] = c2[v * c_stride + j];
+        }
+        __syncthreads();
+        for (int p = sub; p < np; p += S) {
+#pragma unroll
+            for (int i = 0; i < kMomGroupOut; ++i) {
+                if (i < nout) {
+                    const float2 tv = Tb[toff[i] + p], cv = Cs[coff[i] + p];
+                    acc_fma(a[i], df{cv.x, cv.y}, df{tv.x, tv.y});
+                }
+            }
+        }
+    }
+    const Accum dst{mom, P.fxs};
+#pragma unroll
+    for (int i = 0; i < kMomGroupOut; ++i) {
+        if (i >= nout) break;   // uniform over the CTA
+        acc2 v = a[i];
+        for (int off = S >> 1; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, v.s, off);
+            const float oc = __shfl_xor_sync(0xffffffffu, v.c, off);
+            float s2, q2;
+            two_sum(v.s, os, s2, q2);
+            v.s = s2;
+            v.c += oc + q2;
+        }
+        const int it = tid + i * nt;
+        if (it < items && sub == 0) {
+            const int o = it / S, l = o / G;
+            dst.add((o - l * G) * mom_stride + B.mom_off + l, acc_value(v));
+        }
+    }
+}
+
+// One thread per row of a local block, as k_local_eval: Miller's recurrence
+// fills this thread's column of jb, then each C_l is formed once and applied
+// to the moments of all G <= GM components (mu[l][v], double-float in shared
+// memory, read by broadcast) with GM compensated sums in registers.
+template <int GM>
+__global__ void k_local_eval_group(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                                   const Tile* __restrict__ tiles, const float2* __restrict__ w2,
+                                   const double* __restrict__ mom, int64_t mom_stride, int G,
+                                   double* __restrict__ g_s, int64_t g_stride)
+{
+    extern __shared__ float2 sme[];
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int nu = P.nu, L = P.L;
+    float2* mu = sme;                          // [L + 1][GM]
+    float2* jb = sme + (P.ntop + 1) * GM;      // [ntop + 1][nt]
+    for (int i = tid; i < (L + 1) * GM; i += nt) {
+        const int l = i / GM, v = i - l * GM;
+        const double x = v < G ? mom[v * mom_stride + B.mom_off + l] : 0.0;
+        const float h = (float)x;
+        mu[i] = make_float2(h, (float)(x - (double)h));
+    }
+    __syncthreads();
+    if (tid >= t.count) return;
+    const int64_t k = t.start + tid;
+    const float2 wk = w2[k];
+    const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});   // y = omega R / 2
+    const Accum dst{g_s, P.fxs};
+    if (!(ydf.h > 0.f)) {
+        // y below the FP32 range: only C_0 survives, and only for nu = 0
+        for (int v = 0; v < G; ++v)
+            dst.add(v * g_stride + k, nu == 0 ? (double)P.sgn * ((double)mu[v].x + (double)mu[v].y) : 0.0);
+        return;
+    }
+    {
+        const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
+        const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
+        const int ntop = hp + L;
+        const int ns = miller_start(ntop, (double)ydf.h);
+        df S;
+        if (ydf.h >= 1.f) S = miller_store_df(ydf, ntop, ns, jb, nt, tid);
+        else S = df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+        const float p2 = exp2f(-(float)ilogbf(S.h));
+        S = df_scale(S, p2);
+        acc2 sum[GM];
+#pragma unroll
+        for (int v = 0; v < GM; ++v) sum[v] = acc2{0.f, 0.f};
+        for (int l = 0; l <= L; ++l) {
+            df cl;
+            if (nu == 0) {
+                // C_l = (2 - delta_l0) (-1)^l J_l^2
+                const float2 v = jb[l * nt + tid];
+                const float xh = v.x * p2, xl = v.y * p2;
+                const float p = xh * xh;
+                float e = fmaf(xh, xh, -p);
+                e = fmaf(2.f * xh, xl, e);
+                const df sq = fast_two_sum(p, e);
+                const float sgn = l == 0 ? 1.f : ((l & 1) ? -2.f : 2.f);
+                cl = df{sgn * sq.h, sgn * sq.l};
+            } else {
+                const int b = hm - l;
+                const float2 va = jb[(hp + l) * nt + tid];
+                const float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
+                float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
+                if (l > 0 || (nu & 1)) sgn *= 2.f;
+                cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
+            }
+            const float2* ml = mu + l * GM;
+#pragma unroll
+            for (int v = 0; v < GM; ++v)
+                if (v < G) acc_fma(sum[v], cl, df{ml[v].x, ml[v].y});
+        }
+        const df iS = df_recip(S);
+        const df iS2 = df_mul(iS, iS);
+#pragma unroll
+        for (int v = 0; v < GM; ++v)
+            if (v < G)
+                dst.add(v * g_stride + k, (double)P.sgn * df_to(df_mul(fast_two_sum(sum[v].s, sum[v].c), iS2)));
+    }
+}
+
+// One CTA per direct block for a group of G components: the entries are
+// evaluated once (after the branch split of k_direct) into shared memory,
+// column-major as double-float values; then each (row, component) pair sums
+// its row against the component's coefficients (compensated double-float),
+// one atomic add per row and component.  Consecutive threads take
+// consecutive rows of one component: conflict-free entry reads, one
+// coefficient address per warp.
+__global__ void k_direct_group(const ProbParams* __restrict__ probs, const DirectBlock* __restrict__ blks,
+                               const double* __restrict__ r_s, const double* __restrict__ w_s,
+                               const float2* __restrict__ r2, const float2* __restrict__ w2,
+                               const float2* __restrict__ c2, int64_t c_stride, int G, double* __restrict__ g_s,
+                               int64_t g_stride, int lowp)
+{
+    extern __shared__ float2 dsm[];
+    __shared__ int cnt[2];
+    const DirectBlock B = blks[blockIdx.x];
+    const ProbParams& P = probs[B.prob];
+    const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
+    const int area = rows * cols;
+    float2* E = dsm;                        // [cols][rows]
+    int* list = (int*)(dsm + area);         // [area]
+    const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt);
+    const DirFx F = direct_frame(r_s, w_s, B);
+    for (int t = threadIdx.x; t < area; t += blockDim.x) {
+        const int e = list[t];
+        const int rr = e / cols, cc = e - rr * cols;
+        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
+        const float h = (float)v;
+        E[cc * rows + rr] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+    const Accum dst{g_s, P.fxs};
+    for (int o = threadIdx.x; o < rows * G; o += blockDim.x) {
+        const int v = o / rows, rr = o - v * rows;
+        const float2* cv = c2 + v * c_stride + B.j0;
+        acc2 s{0.f, 0.f};
+        for (int cc = 0; cc < cols; ++cc) {
+            const float2 ev = E[cc * rows + rr], cf = cv[cc];
+            acc_fma(s, df{ev.x, ev.y}, df{cf.x, cf.y});
+        }
+        dst.add(v * g_stride + B.k0 + rr, (double)P.sgn * acc_value(s));
+    }
+}
+
 }  // namespace
 
 int local_adj_threads(int ntop_max)
@@ -1205,6 +1440,73 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, c_sb, c2b, g_sb, mode, det);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int local_group_fits(int lmax, int G)
+{
+    return G >= 1 && G <= kGroupMax && (lmax + 1) * G <= kMomGroupOut * kMomThreads;
+}
+
+cudaError_t launch_local_moments_group(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                       int ntiles, int lmax, const float2* r2, const float2* c2,
+                                       int64_t c_stride, int G, double* mom, int64_t mom_stride, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (!local_group_fits(lmax, G)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float2) * (size_t)(lmax + 1 + G) * (kMomThreads + 8);
+    cudaError_t e = cudaFuncSetAttribute(k_local_moments_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_moments_group<<<ntiles, kMomThreads, smem, s>>>(probs, blks, tiles, r2, c2, c_stride, G, mom,
+                                                            mom_stride);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int GM>
+static cudaError_t eval_group_as(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles, int ntiles,
+                                 int ntop_max, int threads, const float2* w2, const double* mom,
+                                 int64_t mom_stride, int G, double* g_s, int64_t g_stride, cudaStream_t s)
+{
+    const size_t smem = sizeof(float2) * (size_t)(ntop_max + 1) * (threads + GM);
+    cudaError_t e = cudaFuncSetAttribute(k_local_eval_group<GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_eval_group<GM><<<ntiles, threads, smem, s>>>(probs, blks, tiles, w2, mom, mom_stride, G, g_s,
+                                                          g_stride);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_eval_group(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                    int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
+                                    int64_t mom_stride, int G, double* g_s, int64_t g_stride, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (G < 1 || G > kGroupMax) return cudaErrorInvalidValue;
+    if (G <= 4)
+        return eval_group_as<4>(probs, blks, tiles, ntiles, ntop_max, threads, w2, mom, mom_stride, G, g_s,
+                                g_stride, s);
+    if (G <= 8)
+        return eval_group_as<8>(probs, blks, tiles, ntiles, ntop_max, threads, w2, mom, mom_stride, G, g_s,
+                                g_stride, s);
+    return eval_group_as<16>(probs, blks, tiles, ntiles, ntop_max, threads, w2, mom, mom_stride, G, g_s,
+                             g_stride, s);
+}
+
+cudaError_t launch_direct_group(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_area,
+                                int lowp, const double* r_s, const double* w_s, const float2* r2, const float2* w2,
+                                const float2* c2, int64_t c_stride, int G, double* g_s, int64_t g_stride,
+                                cudaStream_t s)
+{
+    if (nblk <= 0) return cudaSuccess;
+    if (G < 1 || G > kGroupMax) return cudaErrorInvalidValue;
+    const size_t smem = (sizeof(float2) + sizeof(int)) * (size_t)(max_area > 0 ? max_area : 1);
+    cudaError_t e = cudaFuncSetAttribute(k_direct_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_direct_group<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c2, c_stride, G, g_s, g_stride, lowp);
     count_launches(1);
     return cudaGetLastError();
 }

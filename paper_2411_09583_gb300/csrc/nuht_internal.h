@@ -260,6 +260,21 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
                           int max_area, int mode, const double* r_s, const double* w_s, const float2* r2,
                           const float2* w2, const double* c_s, const float2* c2, double* g_s,
                           const double* c_sb, const float2* c2b, double* g_sb, int det, cudaStream_t s);
+// Vector groups: G <= kGroupMax real components applied together (their
+// data at v times c_stride / mom_stride / g_stride from the first's).
+// local_group_fits: the group moment kernel's outputs ((lmax + 1) G) fit its CTA.
+constexpr int kGroupMax = NUHT_MAX_VEC_GROUP;
+int local_group_fits(int lmax, int G);
+cudaError_t launch_local_moments_group(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                       int ntiles, int lmax, const float2* r2, const float2* c2,
+                                       int64_t c_stride, int G, double* mom, int64_t mom_stride, cudaStream_t s);
+cudaError_t launch_local_eval_group(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                    int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
+                                    int64_t mom_stride, int G, double* g_s, int64_t g_stride, cudaStream_t s);
+cudaError_t launch_direct_group(const ProbParams* probs, const DirectBlock* blks, int nblk, int max_area,
+                                int lowp, const double* r_s, const double* w_s, const float2* r2, const float2* w2,
+                                const float2* c2, int64_t c_stride, int G, double* g_s, int64_t g_stride,
+                                cudaStream_t s);
 int local_adj_threads(int ntop_max);
 // g_sb / momb (both null, or both set): a second real component's g and
 // moments, summed with the same Bessel values.

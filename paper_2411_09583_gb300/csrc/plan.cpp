@@ -145,6 +145,11 @@ struct nuht_plan_s {
     int ev_comps = 0;
 };
 
+// Real components applied together by nuht_execute (opts.vec_group; 0 = a
+// pair), and the copies of the per-component arrays the plan holds.
+static int group_size(const nuht_plan_s* P) { return P->opt.vec_group ? P->opt.vec_group : 2; }
+static int group_copies(const nuht_plan_s* P) { return group_size(P) > 2 ? group_size(P) : 2; }
+
 namespace nuht {
 
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -831,15 +836,18 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     }
     size_t a_r = A.reserve<double>(n), a_w = A.reserve<double>(m);
     size_t a_pr = A.reserve<int32_t>(n), a_pw = A.reserve<int32_t>(m);
-    size_t a_mom = A.reserve<double>((size_t)P->mom_len), a_momb = A.reserve<double>((size_t)P->mom_len);
+    // G >= 2 copies (a pair, or a vector group) of the per-component arrays:
+    // sorted coefficients, moments and sorted outputs
+    const size_t gcopies = (size_t)group_copies(P);
+    size_t a_mom = A.reserve<double>(gcopies * (size_t)P->mom_len);
     size_t a_gb = A.reserve<double2>((size_t)P->gb_len);
     size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
     size_t a_gt = A.reserve<float4>(P->has_large_fft ? (size_t)P->gq_len : 1);
-    size_t a_cs = A.reserve<double>(n), a_gs = A.reserve<double>(m);
-    size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m), a_cs2 = A.reserve<float2>(n);
+    size_t a_cs = A.reserve<double>(gcopies * (size_t)n), a_gs = A.reserve<double>(gcopies * (size_t)m);
+    size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m);
+    size_t a_cs2 = A.reserve<float2>(gcopies * (size_t)n);
     size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
     size_t a_sm = A.reserve<int32_t>((size_t)ntile[LIST_SPREAD]);
-    size_t a_csb = A.reserve<double>(n), a_gsb = A.reserve<double>(m), a_cs2b = A.reserve<float2>(n);
     const bool det = P->opt.deterministic != 0;
     const size_t f1 = 1;
     size_t a_fgs = A.reserve<Fx128>(det ? (size_t)m : f1), a_fgsb = A.reserve<Fx128>(det ? (size_t)m : f1);
@@ -944,11 +952,11 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     P->d_asy = bl.asy;
     P->d_dir = bl.dir;
     P->d_es = (double*)(D + a_es); P->d_ph = (double*)(D + a_ph); P->d_tw = (double2*)(D + a_tw);
-    P->d_mom = (double*)(D + a_mom); P->d_momb = (double*)(D + a_momb);
+    P->d_mom = (double*)(D + a_mom); P->d_momb = P->d_mom + P->mom_len;
     P->d_gb = (double2*)(D + a_gb); P->d_gq = (float4*)(D + a_gq); P->d_gtmp = (float4*)(D + a_gt);
     P->d_cs = (double*)(D + a_cs); P->d_gs = (double*)(D + a_gs);
     P->d_r2 = (float2*)(D + a_r2); P->d_w2 = (float2*)(D + a_w2); P->d_cs2 = (float2*)(D + a_cs2);
-    P->d_csb = (double*)(D + a_csb); P->d_gsb = (double*)(D + a_gsb); P->d_cs2b = (float2*)(D + a_cs2b);
+    P->d_csb = P->d_cs + n; P->d_gsb = P->d_gs + m; P->d_cs2b = P->d_cs2 + n;
     P->det = det;
     if (det) {
         P->f_gs = (Fx128*)(D + a_fgs); P->f_gsb = (Fx128*)(D + a_fgsb);
@@ -1089,8 +1097,9 @@ static int check_opts(const nuht_opts* opt, nuht_opts& o)
     if (o.min_size < 1 || o.min_size > NUHT_MAX_MIN_SIZE || o.n_split_cand < 2 || o.m_terms < 0 || o.m_terms > kMaxM ||
         (o.precision != NUHT_PREC_FP64 && o.precision != NUHT_PREC_MIXED))
         return NUHT_ERR_INVALID_ARG;
-    for (int i = 0; i < 2; ++i)
-        if (o.reserved[i]) return NUHT_ERR_INVALID_ARG;
+    if (o.reserved) return NUHT_ERR_INVALID_ARG;
+    if (o.vec_group < 0 || o.vec_group > NUHT_MAX_VEC_GROUP) return NUHT_ERR_INVALID_ARG;
+    if (o.vec_group > 2 && (o.deterministic || o.persistent)) return NUHT_ERR_INVALID_ARG;
     if (o.deterministic != 0 && o.deterministic != 1) return NUHT_ERR_INVALID_ARG;
     if (o.persistent != 0 && o.persistent != 1) return NUHT_ERR_INVALID_ARG;
     if (o.interp_tile != 0 && o.interp_tile != 128 && o.interp_tile != 256) return NUHT_ERR_INVALID_ARG;
@@ -1180,30 +1189,42 @@ int nuht_plan_many(nuht_plan_t* out, int nprob, const int* nu, const double* r, 
         if (rc_ != NUHT_OK) return rc_; \
     } while (0)
 
-// Algorithm 2 on the device for one vector component: local moments and
-// evaluation, direct blocks, and the asymptotic type-3 pipeline, all
-// accumulating into g in sorted order (FP64 atomics).  They run one after the
-// other on the caller's stream: each kernel fills the GPU, and running them
-// concurrently only makes them compete for shared memory.
-// pair: 0 this component's local and direct blocks; 1 also those of the next
-// component (d_csb, d_cs2b into d_gsb, one Bessel evaluation for both); 2 none
-// (applied with the previous component).
 // Accumulation targets of the kernels: the FP64 array, or in the
 // deterministic mode its exact fixed-point twin (passed under the same
 // pointer type; the kernels index it by element through Accum).
 static double* acc_target(nuht_plan_t P, double* f64, Fx128* fx) { return P->det ? (double*)fx : f64; }
 static size_t acc_bytes(nuht_plan_t P, int64_t count) { return (size_t)count * (P->det ? sizeof(Fx128) : sizeof(double)); }
 
-static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
+// Sorted coefficients and sums of member v of a group (the accumulation
+// target of the sums: d_gs + v m, or in the deterministic mode, where groups
+// are pairs, f_gs / f_gsb).
+static float2* member_c2(nuht_plan_t P, int v) { return P->d_cs2 + (int64_t)v * P->n; }
+static double* member_c(nuht_plan_t P, int v) { return P->d_cs + (int64_t)v * P->n; }
+static double* member_g(nuht_plan_t P, int v) { return P->d_gs + (int64_t)v * P->m; }
+static double* member_g_acc(nuht_plan_t P, int v)
+{
+    if (P->det) return (double*)(v == 0 ? P->f_gs : P->f_gsb);
+    return member_g(P, v);
+}
+
+// Algorithm 2 on the device for the ng real components c0 .. c0 + ng - 1 of a
+// group (sorted, scaled coefficients in member_c / member_c2): every block
+// class adds into the members' sums (sorted order, FP64 atomics).  The local
+// and direct blocks are applied to the whole group at once, with one Bessel
+// evaluation for all members (the pair kernels for ng <= 2, the group
+// kernels above); the asymptotic type-3 pipeline runs per member.
+static int apply_forward(nuht_plan_t P, int c0, int ng, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
-    double* gs = acc_target(P, P->d_gs, P->f_gs);
-    double* gsb = acc_target(P, P->d_gsb, P->f_gsb);
+    StageTimer T{P, c0};
+    double* gs = member_g_acc(P, 0);
+    double* gsb = ng == 2 ? member_g_acc(P, 1) : nullptr;
     double* mom_acc = acc_target(P, P->d_mom, P->f_mom);
     double* momb_acc = acc_target(P, P->d_momb, P->f_momb);
     double2* gb_acc = (double2*)acc_target(P, (double*)P->d_gb, P->f_gb);
-    const bool loc = (mask & 1) && P->n_loc && pair != 2, dir = (mask & 4) && P->n_dir && pair != 2;
+    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir;
     const bool asy = (mask & 2) && P->n_asy;
+    const bool group = ng > 2;
     // The block classes share no scratch and only add into g (FP64 atomics):
     // the local and direct blocks run beside the asymptotic pipeline (ClassFork),
     // each stage's events on its own stream.  NUHT_TIMING_SERIAL keeps every
@@ -1211,17 +1232,27 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
     ClassFork fk;
     if (P->opt.timing != NUHT_TIMING_SERIAL && asy && (loc || dir)) NUHT_CK(fk.open(s));
     const cudaStream_t ls = fk.local(s), as = fk.asy(s);
-    if (loc && P->opt.persistent && !P->det) {
+    if (loc && group) {
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len * ng, ls));
+        NUHT_CK(launch_local_moments_group(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
+                                           P->d_cs2, P->n, ng, P->d_mom, P->mom_len, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
+        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
+        NUHT_CK(launch_local_eval_group(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
+                                        P->eval_threads, P->d_w2, P->d_mom, P->mom_len, ng, P->d_gs, P->m, ls));
+        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
+    } else if (loc && P->opt.persistent && !P->det) {
         // moments and evaluation in one persistent launch (per-block waits)
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
-        double* momb = pair == 1 ? P->d_momb : nullptr;
+        double* momb = ng == 2 ? P->d_momb : nullptr;
         NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len, ls));
         if (momb) NUHT_CK(cudaMemsetAsync(momb, 0, sizeof(double) * P->mom_len, ls));
         const char* st = std::getenv("NUHT_QUEUE_STALL");
         const bool stall = st && *st && *st != '0';
         NUHT_CK(launch_local_persistent(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->d_teval, P->n_teval,
                                         P->d_pre_mom, P->lmax, P->ntop_max, P->eval_threads, P->d_r2, P->d_cs2,
-                                        P->d_cs2b, P->d_w2, P->d_mom, momb, gs, momb ? gsb : nullptr, P->d_q,
+                                        P->d_cs2b, P->d_w2, P->d_mom, momb, gs, gsb, P->d_q,
                                         P->n_loc, P->d_status, stall ? 4096 : (1 << 22), stall ? 1 : 0, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
     } else if (loc) {
@@ -1230,7 +1261,7 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
                                      P->d_cs2, mom_acc, ls));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
-        double* momb = pair == 1 ? P->d_momb : nullptr;
+        double* momb = ng == 2 ? P->d_momb : nullptr;
         if (momb) {
             NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
             NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
@@ -1239,36 +1270,42 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         }
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
-        double* gsb_l = momb ? gsb : nullptr;
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_local_eval_f32(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                          P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb_l, ls));
+                                          P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb, ls));
         else
             NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                      P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb_l, ls));
+                                      P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
-        NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area,
-                              direct_sum_mode(P->eps, P->max_dir_rows, P->max_dir_cols), P->d_r, P->d_w,
-                              P->d_r2, P->d_w2, P->d_cs, P->d_cs2, gs, pair == 1 ? P->d_csb : nullptr,
-                              pair == 1 ? P->d_cs2b : nullptr, pair == 1 ? gsb : nullptr, P->det ? 1 : 0, ls));
+        const int mode = direct_sum_mode(P->eps, P->max_dir_rows, P->max_dir_cols);
+        if (group)
+            NUHT_CK(launch_direct_group(P->d_prob, P->d_dir, P->n_dir, P->max_dir_area, mode >= 1 ? 1 : 0, P->d_r,
+                                        P->d_w, P->d_r2, P->d_w2, P->d_cs2, P->n, ng, P->d_gs, P->m, ls));
+        else
+            NUHT_CK(launch_direct(P->d_prob, P->d_dir, P->n_dir, P->max_dir_rows, P->max_dir_area, mode, P->d_r,
+                                  P->d_w, P->d_r2, P->d_w2, P->d_cs, P->d_cs2, gs, gsb ? P->d_csb : nullptr,
+                                  gsb ? P->d_cs2b : nullptr, gsb, P->det ? 1 : 0, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
-    if (asy) {
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
+    for (int v = 0; asy && v < ng; ++v) {
+        StageTimer Tv{P, c0 + v};
+        const float2* c2 = member_c2(P, v);
+        double* gv = member_g_acc(P, v);
+        NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_CK(cudaMemsetAsync(gb_acc, 0, acc_bytes(P, 2 * P->gb_len), as));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                          P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc, as));
+                                          P->spread_threads, P->tab, P->d_r, P->d_r2, c2, gb_acc, as));
         else
             NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                      P->spread_threads, P->tab, P->d_r, P->d_r2, P->d_cs2, gb_acc,
+                                      P->spread_threads, P->tab, P->d_r, P->d_r2, c2, gb_acc,
                                       P->det ? 1 : 0, as));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_gb, (double*)P->d_gb, 2 * P->gb_len, P->d_prob, as));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
+        NUHT_TRY(Tv.end(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_FFT, as));
         const bool lowp = P->opt.precision == NUHT_PREC_MIXED;   // FP32 butterflies
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->max_fblock_pts, P->tab,
                                      P->d_gb, P->d_gq, as, false, lowp));
@@ -1277,55 +1314,50 @@ static int apply_forward(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
         if (P->has_large_fft)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
                                          P->d_gb, P->d_gtmp, P->d_gq, as, false, lowp));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
+        NUHT_TRY(Tv.end(NUHT_STAGE_ASY_FFT, as));
+        NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_INTERP, as));
         if (P->opt.precision == NUHT_PREC_MIXED)
             NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax,
-                                          P->interp_threads, P->tab,
-                                          P->d_w, P->d_w2, P->d_gq, gs, as));
+                                          P->interp_threads, P->tab, P->d_w, P->d_w2, P->d_gq, gv, as));
         else
             NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax,
-                                      P->interp_threads, P->tab,
-                                      P->d_w, P->d_w2, P->d_gq, gs, as));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
+                                      P->interp_threads, P->tab, P->d_w, P->d_w2, P->d_gq, gv, as));
+        NUHT_TRY(Tv.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
     return NUHT_OK;
 }
 
-// The component loop of a forward transform: per real component, gather(comp,
-// cs, cs2) writes the sorted, scaled input, apply_forward adds every block
-// class into g (sorted), scatter(comp) writes it out.  Real components in
-// pairs share the local and direct blocks' Bessel evaluations: the first of a
-// pair applies those blocks to both, the second starts from the second's local
-// and direct sums (d_gsb).
+// The component loop of a forward transform, in groups of G real components
+// (opts.vec_group; 1 when the plan has no local or direct blocks to share):
+// gather(comp, c, c2) writes a component's sorted, scaled input into its
+// member's arrays, apply_forward adds every block class into the members'
+// sums, scatter(comp, g) writes a member's sums out.
 extern "C++" {
 template <class Gather, class Scatter>
 static int drive_forward(nuht_plan_t P, int comps, cudaStream_t s, Gather&& gather, Scatter&& scatter)
 {
     NUHT_TRY(ensure_events(P, comps));
-    double* gs = acc_target(P, P->d_gs, P->f_gs);
-    double* gsb = acc_target(P, P->d_gsb, P->f_gsb);
-    const bool pairs = ((P->opt.class_mask & 4) && P->n_dir > 0) || ((P->opt.class_mask & 1) && P->n_loc > 0);
-    for (int comp = 0; comp < comps; ++comp) {
-        StageTimer T{P, comp};
-        const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
+    const bool share = ((P->opt.class_mask & 4) && P->n_dir > 0) || ((P->opt.class_mask & 1) && P->n_loc > 0);
+    int G = share ? group_size(P) : 1;
+    if (G > 2 && !local_group_fits(P->lmax, G)) G = 2;   // the moments' outputs would not fit one CTA
+    for (int c0 = 0; c0 < comps; c0 += G) {
+        const int ng = comps - c0 < G ? comps - c0 : G;
+        StageTimer T{P, c0};
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
-        if (pair == 2)
-            NUHT_CK(cudaMemcpyAsync(gs, gsb, acc_bytes(P, P->m), cudaMemcpyDeviceToDevice, s));
-        else
-            NUHT_CK(cudaMemsetAsync(gs, 0, acc_bytes(P, P->m), s));
-        NUHT_CK(gather(comp, P->d_cs, P->d_cs2));
-        if (pair == 1) {
-            NUHT_CK(cudaMemsetAsync(gsb, 0, acc_bytes(P, P->m), s));
-            NUHT_CK(gather(comp + 1, P->d_csb, P->d_cs2b));
+        for (int v = 0; v < ng; ++v) {
+            NUHT_CK(cudaMemsetAsync(member_g_acc(P, v), 0, acc_bytes(P, P->m), s));
+            NUHT_CK(gather(c0 + v, member_c(P, v), member_c2(P, v)));
         }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
-        NUHT_TRY(apply_forward(P, T, s, pair));
-        NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
-        if (P->det) NUHT_CK(launch_fx_decode(P->f_gs, P->d_gs, P->m, P->d_prob, s));
-        NUHT_CK(scatter(comp));
-        NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
+        NUHT_TRY(apply_forward(P, c0, ng, s));
+        for (int v = 0; v < ng; ++v) {
+            StageTimer Tv{P, c0 + v};
+            NUHT_TRY(Tv.begin(NUHT_STAGE_SCATTER, s));
+            if (P->det) NUHT_CK(launch_fx_decode(member_g_acc(P, v), member_g(P, v), P->m, P->d_prob, s));
+            NUHT_CK(scatter(c0 + v, member_g(P, v)));
+            NUHT_TRY(Tv.end(NUHT_STAGE_SCATTER, s));
+        }
     }
     return NUHT_OK;
 }
@@ -1347,7 +1379,7 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
     return drive_forward(
         P, comps, s,
         [&](int cp, double* o, float2* o2) { return launch_gather(c, P->d_pr, P->n, comps, cp, P->d_mx, o, o2, s); },
-        [&](int cp) { return launch_scatter(P->d_gs, P->d_pw, P->m, comps, cp, P->d_mx, g, s); });
+        [&](int cp, const double* src) { return launch_scatter(src, P->d_pw, P->m, comps, cp, P->d_mx, g, s); });
 }
 
 // Transpose of apply_forward: g (sorted, d_gs) -> c (sorted, d_cs).  Each
@@ -1436,7 +1468,7 @@ static int drive_adjoint(nuht_plan_t P, int comps, cudaStream_t s, Gather&& gath
     NUHT_TRY(ensure_events(P, comps));
     double* cs = acc_target(P, P->d_cs, P->f_cs);
     double* csb = acc_target(P, P->d_csb, P->f_csb);
-    const bool pairs = (P->opt.class_mask & 1) && P->n_loc > 0;
+    const bool pairs = (P->opt.class_mask & 1) && P->n_loc > 0 && group_size(P) != 1;
     for (int comp = 0; comp < comps; ++comp) {
         StageTimer T{P, comp};
         const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
@@ -1529,7 +1561,9 @@ int nuht_grad_omega(nuht_plan_t D, const double* c, const double* e, double* gra
         [&](int cp, double* o, float2* o2) {
             return launch_gather_deriv(c, D->d_pr, D->d_r, nb, nvec, cp, D->d_mx, o, o2, s);
         },
-        [&](int cp) { return launch_scatter_deriv(D->d_gs, D->d_pw, mb, nvec, cp, D->d_mx, e, grad_omega, s); });
+        [&](int cp, const double* src) {
+            return launch_scatter_deriv(src, D->d_pw, mb, nvec, cp, D->d_mx, e, grad_omega, s);
+        });
 }
 
 int nuht_grad_r(nuht_plan_t D, const double* c, const double* e, double* grad_r, int nvec, void* stream)

@@ -30,7 +30,8 @@ def _dev_f64(x, name):
 
 
 def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class_mask=7,
-              timing=False, spread_tile=0, deterministic=False, persistent=False, interp_tile=0):
+              timing=False, spread_tile=0, deterministic=False, persistent=False, interp_tile=0,
+              vec_group=0):
     o = N.NuhtOpts()
     N.lib().nuht_default_opts(ctypes.byref(o))
     o.precision = {"fp64": N.PREC_FP64, "mixed": N.PREC_MIXED}[precision]
@@ -45,6 +46,7 @@ def make_opts(precision="fp64", min_size=1024, n_split_cand=16, m_terms=0, class
     o.deterministic = 1 if deterministic else 0
     o.persistent = 1 if persistent else 0
     o.interp_tile = int(interp_tile)
+    o.vec_group = int(vec_group)
     return o
 
 

@@ -67,9 +67,18 @@ def test_invalid_arguments(lib):
     one = (ctypes.c_double * 1)(0.5)
     for field, bad in (("min_size", 0), ("min_size", 16385), ("n_split_cand", 1), ("spread_tile", 96 + 1),
                        ("precision", 2), ("m_terms", 21), ("deterministic", 2), ("persistent", 3),
-                       ("interp_tile", 64), ("interp_tile", 512)):
+                       ("interp_tile", 64), ("interp_tile", 512), ("vec_group", -1), ("vec_group", 17),
+                       ("reserved", 1)):
         b = N.NuhtOpts()
         lib.nuht_default_opts(ctypes.byref(b))
         setattr(b, field, bad)
+        assert lib.nuht_plan(ctypes.byref(h), 0, one, 1, one, 1, 1e-8, ctypes.byref(b), None) == \
+            N.NUHT_ERR_INVALID_ARG, field
+    # vector groups above a pair exclude the deterministic and persistent modes
+    for field in ("deterministic", "persistent"):
+        b = N.NuhtOpts()
+        lib.nuht_default_opts(ctypes.byref(b))
+        b.vec_group = 3
+        setattr(b, field, 1)
         assert lib.nuht_plan(ctypes.byref(h), 0, one, 1, one, 1, 1e-8, ctypes.byref(b), None) == \
             N.NUHT_ERR_INVALID_ARG, field
