@@ -458,6 +458,16 @@ def run_mixed(dev, steps):
         t = statistics.median(ms)
         with Plan(1, dr, dw, 1e-5, precision=prec, **opts) as p:
             gh = p.execute(dc).cpu().numpy()
+            asy_members = p.info()["asy_members"]
+            ex = []
+            for _ in range(max(3, steps // 4)):
+                flush.zero_()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                p.execute(dc)
+                s1.record(stream)
+                torch.cuda.synchronize(dev)
+                ex.append(s0.elapsed_time(s1))
         stages = {}
         for _ in range(3):
             flush.zero_()
@@ -467,6 +477,7 @@ def run_mixed(dev, steps):
                     stages.setdefault(k, []).append(v)
         rows = sample_rows(omega.size, 100, seed=98)
         out[prec] = {"ms_per_step": t, "value": 8e6 / (t * 1e-3), "opts": opts,
+                     "execute_ms": statistics.median(ex), "asy_members": asy_members,
                      "stage_ms_alone": {k: statistics.median(v) for k, v in stages.items()},
                      "error": sampled_error(1, r, omega, c, gh, 1e-5, rows)}
     return out

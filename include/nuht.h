@@ -138,7 +138,7 @@ typedef struct {
     int     L;             /* Wimp order (terms l = 0..L), Lemma 3.1 */
     int     nufft_width;   /* ES kernel width w of the type-3 NUFFTs */
     int     nufft_degree;  /* degree of the kernel's piecewise polynomials */
-    int     pad_;
+    int     asy_members;   /* real components per asymptotic spreading / interpolation launch */
     double  z;             /* crossover point, B^asy_{nu,M}(z) = eps */
     double  eps;
     int64_t n, m;

@@ -49,7 +49,7 @@ class NuhtOpts(ctypes.Structure):
 
 class NuhtPlanInfo(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_int), ("M", ctypes.c_int), ("L", ctypes.c_int),
-                ("nufft_width", ctypes.c_int), ("nufft_degree", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("nufft_width", ctypes.c_int), ("nufft_degree", ctypes.c_int), ("asy_members", ctypes.c_int),
                 ("z", ctypes.c_double), ("eps", ctypes.c_double),
                 ("n", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("n_local", ctypes.c_int64), ("n_asy", ctypes.c_int64),

@@ -197,9 +197,14 @@ __device__ __forceinline__ int mom_degree(int e, int ndf, int dcs, int nb)
 // target(j, &v, xq) gives target j's cell and kernel coordinate v and writes
 // its 2M weighted values as double-float (re, im) pairs xq[2q], xq[2q + 1];
 // cell(c) is the grid index of cell c, or -1 for a cell outside the grid.
-template <class Target, class Cell, class Acc>
+// Members (forward spreading of V real components): target writes member 0's
+// values; values(vm, xq) rewrites this thread's point's values for member vm,
+// whose grid sits moff accumulator elements after member 0's.  The basis,
+// the cells and the bins are formed once for all members.
+template <class Target, class Values, class Cell, class Acc>
 __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, const Tables& tab, Target&& target,
-                                               Cell&& cell, Acc gb, float2* sm)
+                                               Values&& values, int V, int64_t moff, Cell&& cell, Acc gb,
+                                               float2* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -262,6 +267,12 @@ __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, con
     const int nqA = min(nq, (qs + 1) >> 1);        // quads holding a term q < qs
     const int nA = L.ndf * nqA, nB = L.ndf * (nq - nqA);
     const int nitems_pad = (nitems + 31) & ~31;
+    for (int vm = 0; vm < V; ++vm) {
+    if (vm > 0) {
+        if (tid < cnt) values(vm, X + tid * L.sx);
+        __syncthreads();
+    }
+    const Acc gv = gb.at(vm * moff);
     for (int b = 0; b < nbins; ++b) {
         const int p0 = bstart[b], p1 = bstart[b + 1];
         if (p0 == p1) continue;
@@ -375,9 +386,10 @@ __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, con
             }
             for (; e < L.dpad; ++e) sf = fmaf(ar[e].x, Mb[e * Q2 + qv].x, sf);
             const double val = acc_value(s) + (double)sf;
-            if (val != 0.0) gb.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
+            if (val != 0.0) gv.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
         }
         __syncthreads();
+    }
     }
 }
 
@@ -473,10 +485,14 @@ __host__ __device__ __forceinline__ size_t spread_fold_smem(int nt, int Q, int w
            sizeof(float) * (size_t)nt * suf + sizeof(int) * (size_t)nt;
 }
 
-template <class Acc>
+// Members (MULTI): V real components with coefficients c2 + vm c_stride,
+// grids moff accumulator elements apart; the points' cells, bases and phase
+// factors and the bins are formed once for all members.
+template <bool MULTI, class Acc>
 __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, const Tables& tab, FoldPlan F,
                             const double* __restrict__ r_s, const float2* __restrict__ r2,
-                            const float2* __restrict__ c2, Acc gb, float4* sm4)
+                            const float2* __restrict__ c2, int64_t c_stride, int V, int64_t moff, Acc gb,
+                            float4* sm4)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb, dcs = tab.dcs;
@@ -498,8 +514,10 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
         const int d = mom_degree(e, L.ndf, dcs, nb);
         Ach[i] = d >= 0 ? tab.ch2[r * (tab.deg + 1) + d] : make_float2(0.f, 0.f);
     }
+    // this thread's point: (r_j/rho)^(-1/2) e^{i w_c x_j} (the weight without c_j)
+    df yr{0.f, 0.f}, yi{0.f, 0.f};
+    const int64_t j = t.start + tid;
     if (tid < cnt) {
-        const int64_t j = t.start + tid;
         long long X;
         df vd;
         l0s[tid] = spread_cell_fx(B, w, r_s[j], &X, &vd);
@@ -524,9 +542,9 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             fm = fc;
             fc = fn;
         }
-        df wr, wi, rat;
-        spread_weight_fx(B, X, r2[j], c2[j], &wr, &wi, &rat);
-        Y[tid] = make_float4(wr.h, wr.l, wi.h, wi.l);
+        df rat;
+        spread_weight_fx(B, X, r2[j], MULTI ? make_float2(1.f, 0.f) : c2[j], &yr, &yi, &rat);
+        if (!MULTI) Y[tid] = make_float4(yr.h, yr.l, yi.h, yi.l);
     }
     __syncthreads();
     const int lfirst = l0s[0];
@@ -541,6 +559,16 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
     const int nf1 = 2 * B.N1 + 1;
     const int npd = Edf >> 1, npf = (E - Edf) >> 1;
     const df rho{B.rho_h, B.rho_l};
+    for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
+    if (MULTI) {
+        if (tid < cnt) {
+            const float2 cv = c2[vm * c_stride + j];
+            const df wr = df_mul(df{cv.x, cv.y}, yr), wi = df_mul(df{cv.x, cv.y}, yi);
+            Y[tid] = make_float4(wr.h, wr.l, wi.h, wi.l);
+        }
+        __syncthreads();
+    }
+    const Acc gv = gb.at(vm * moff);
     for (int g0 = 0; g0 < nbins; g0 += G) {
         const int gn = nbins - g0 < G ? nbins - g0 : G;
         // (a) N of the group's bins: items (bin, degree pair) split over
@@ -716,9 +744,10 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
                 sacc.c += e2;
             }
             const double val = acc_value(sacc);
-            if (val != 0.0) gb.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
+            if (val != 0.0) gv.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
         }
         __syncthreads();
+    }
     }
 }
 
@@ -726,11 +755,13 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
 // (cell l0, w kernel taps, the 2M weighted, pre-phased values), then each
 // (cell, q) output of the tile's window is owned by one thread, which sums
 // over the points whose taps cover that cell and adds the sum to the block's
-// global grid.
-template <class Acc>
+// global grid.  Members as in spread_fold: the taps and phase factors are
+// formed once, the weighted values and the sums per member.
+template <bool MULTI, class Acc>
 __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                             const double* __restrict__ r_s, const float2* __restrict__ r2,
-                            const float2* __restrict__ c2, Acc gb, float4* smem4)
+                            const float2* __restrict__ c2, int64_t c_stride, int V, int64_t moff, Acc gb,
+                            float4* smem4)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -741,8 +772,9 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
     for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
     __syncthreads();
     const int cnt = t.count;
+    const int64_t j = t.start + tid;
+    df yr{0.f, 0.f}, yi{0.f, 0.f}, rat{0.f, 0.f};   // this point's weight without c_j, and its ratio
     if (tid < cnt) {
-        const int64_t j = t.start + tid;
         long long X;
         df vd;
         l0s[tid] = spread_cell_fx(B, w, r_s[j], &X, &vd);
@@ -751,12 +783,13 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
             const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
-        df wr, wi, rat;
-        spread_weight_fx(B, X, r2[j], c2[j], &wr, &wi, &rat);
-        for (int q = 0; q < Q; ++q) {
-            aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
-            wr = df_mul(wr, rat);
-            wi = df_mul(wi, rat);
+        spread_weight_fx(B, X, r2[j], MULTI ? make_float2(1.f, 0.f) : c2[j], &yr, &yi, &rat);
+        if (!MULTI) {
+            for (int q = 0; q < Q; ++q) {
+                aval[tid * Q + q] = make_float4(yr.h, yr.l, yi.h, yi.l);
+                yr = df_mul(yr, rat);
+                yi = df_mul(yi, rat);
+            }
         }
     }
     __syncthreads();
@@ -777,6 +810,20 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
     const int sub = lane & (kSub - 1);
     const unsigned gmask = 0x3u << (lane & ~(kSub - 1));
     const int half = (cnt + 1) >> 1;
+    for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
+    if (MULTI) {
+        if (tid < cnt) {
+            const float2 cv = c2[vm * c_stride + j];
+            df wr = df_mul(df{cv.x, cv.y}, yr), wi = df_mul(df{cv.x, cv.y}, yi);
+            for (int q = 0; q < Q; ++q) {
+                aval[tid * Q + q] = make_float4(wr.h, wr.l, wi.h, wi.l);
+                wr = df_mul(wr, rat);
+                wi = df_mul(wi, rat);
+            }
+        }
+        __syncthreads();
+    }
+    const Acc gv = gb.at(vm * moff);
     for (int base = tid - sub; base < nout * kSub; base += nt) {
         const int item = (base + sub) / kSub;   // same item for both lanes of a pair
         const bool live = item < nout;
@@ -814,9 +861,11 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
         vi += __shfl_down_sync(gmask, vi, 1, kSub);
         const int idx = cell + B.N1;
         if (live && sub == 0 && idx >= 0 && idx < nf1 && (vr != 0.0 || vi != 0.0)) {
-            gb.add(2 * ((int64_t)idx * Q + q), vr);
-            gb.add(2 * ((int64_t)idx * Q + q) + 1, vi);
+            gv.add(2 * ((int64_t)idx * Q + q), vr);
+            gv.add(2 * ((int64_t)idx * Q + q) + 1, vi);
         }
+    }
+    if (MULTI) __syncthreads();   // aval is rewritten for the next member
     }
 }
 
@@ -857,11 +906,16 @@ __global__ void k_spread_modes(const ProbParams* __restrict__ probs, const AsyBl
 
 // One instance per accumulation mode (DET: the deterministic mode's exact
 // fixed-point sums), so that the FP64 path carries no code of the other.
-template <bool DET>
+// Members: V real components (coefficients c2 + vm c_stride, grids grid_b +
+// vm gb_stride) spread by the same CTAs, which form each point's cell, basis
+// or taps and phase factor once.  MULTI: the instance for V > 1 (V = 1 runs
+// the instance without the member loop's registers and barriers).
+template <bool DET, bool MULTI>
 __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                              const Tile* __restrict__ tiles, const int32_t* __restrict__ modes, Tables tab,
                              const double* __restrict__ r_s, const float2* __restrict__ r2,
-                             const float2* __restrict__ c2, double2* __restrict__ grid_b)
+                             const float2* __restrict__ c2, int64_t c_stride, int V,
+                             double2* __restrict__ grid_b, int64_t gb_stride)
 {
     extern __shared__ float4 smem4[];
     const Tile t = tiles[blockIdx.x];
@@ -871,30 +925,39 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
     const int Q = probs[B.prob].Q;
     using Acc = typename AccumOf<DET>::type;
     const Acc gb = Acc{(double*)grid_b, probs[B.prob].fxs}.at(2 * B.b_off);
+    const int64_t moff = 2 * gb_stride;
     if ((mode & 3) == 2)
-        spread_fold(B, Q, probs[B.prob].qs, t, tab, fold_unpack(mode), r_s, r2, c2, gb, smem4);
+        spread_fold<MULTI>(B, Q, probs[B.prob].qs, t, tab, fold_unpack(mode), r_s, r2, c2, c_stride, V, moff, gb,
+                           smem4);
     else if (mode & 3) {
         // c_j (r_j/rho)^(-q-1/2) e^{i w_c x_j} onto the 2 N1 + 1 modes
         const int nf1 = 2 * B.N1 + 1;
+        df yr{0.f, 0.f}, yi{0.f, 0.f}, rat{0.f, 0.f};   // this thread's point's weight without c_j
+        int64_t jt = 0;
+        auto put = [&](float2* xq, float2 cv) {
+            df wr = df_mul(df{cv.x, cv.y}, yr), wi = df_mul(df{cv.x, cv.y}, yi);
+            for (int q = 0; q < Q; ++q) {
+                xq[2 * q] = make_float2(wr.h, wr.l);
+                xq[2 * q + 1] = make_float2(wi.h, wi.l);
+                wr = df_mul(wr, rat);
+                wi = df_mul(wi, rat);
+            }
+        };
         spread_moments(Q, probs[B.prob].qs, t, tab,
             [&](int64_t j, df* v, float2* xq) {
                 long long Xp;
                 const int l0 = spread_cell_fx(B, tab.w, r_s[j], &Xp, v);
-                df wr, wi, rat;
-                spread_weight_fx(B, Xp, r2[j], c2[j], &wr, &wi, &rat);
-                for (int q = 0; q < Q; ++q) {
-                    xq[2 * q] = make_float2(wr.h, wr.l);
-                    xq[2 * q + 1] = make_float2(wi.h, wi.l);
-                    wr = df_mul(wr, rat);
-                    wi = df_mul(wi, rat);
-                }
+                spread_weight_fx(B, Xp, r2[j], make_float2(1.f, 0.f), &yr, &yi, &rat);
+                jt = j;
+                put(xq, c2[j]);
                 return l0;
             },
+            [&](int vm, float2* xq) { put(xq, c2[vm * c_stride + jt]); }, MULTI ? V : 1, moff,
             [&](int c) -> int64_t { const int x = c + B.N1; return (x >= 0 && x < nf1) ? x : -1; },
             gb, (float2*)smem4);
     }
     else
-        spread_taps(B, Q, t, tab, r_s, r2, c2, gb, smem4);
+        spread_taps<MULTI>(B, Q, t, tab, r_s, r2, c2, c_stride, V, moff, gb, smem4);
 }
 
 // -------------------------------------------------------------------- FFT
@@ -1160,9 +1223,12 @@ __device__ __forceinline__ void fft_out(const AsyBlock& B, const Tables& tab, fl
 template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
-                                const double2* __restrict__ src, float4* __restrict__ dst)
+                                const double2* __restrict__ src, float4* __restrict__ dst, int64_t src_stride,
+                                int64_t dst_stride)
 {
     extern __shared__ float4 Xs[];
+    src += blockIdx.y * src_stride;   // member blockIdx.y of a batch of real components
+    dst += blockIdx.y * dst_stride;
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
@@ -1189,9 +1255,12 @@ __global__ void k_asy_fft_small(const ProbParams* __restrict__ probs, const AsyB
 template <bool ADJ, bool LOWP>
 __global__ void k_asy_fft_block(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                 const Tile* __restrict__ items, Tables tab,
-                                const double2* __restrict__ src, float4* __restrict__ dst, int pts_lo, int pts_hi)
+                                const double2* __restrict__ src, float4* __restrict__ dst, int pts_lo, int pts_hi,
+                                int64_t src_stride, int64_t dst_stride)
 {
     extern __shared__ float4 Xs[];   // [Q][N], each grid bit-reversed
+    src += blockIdx.y * src_stride;   // member blockIdx.y of a batch of real components
+    dst += blockIdx.y * dst_stride;
     const Tile it = items[blockIdx.x];
     const AsyBlock B = blks[it.blk];
     const int Q = probs[B.prob].Q;
@@ -1520,10 +1589,14 @@ __device__ __forceinline__ void tap_sums_eval(const float2* u, int w, int Q, int
 // basis, A[i][d]), and each frequency sums P_q' = sum_d T_d(v) H[d][q'];
 // sparse tiles evaluate the w taps of each frequency.  Each thread keeps its
 // basis (or taps) in a row of shared memory.
-__global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
+// Members: V real components (FFT outputs grid_q + vm gq_stride, sums into
+// g_s + vm g_stride) interpolated by the same CTAs: a frequency's cell, basis
+// or taps, phase and deconvolution factor are formed once; the window, the
+// per-bin sums and the frequency's sums per member.
+__global__ void __launch_bounds__(kInterpTileThreads, 3) k_asy_interp(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
     Tables tab, const double* __restrict__ w_s, const float2* __restrict__ w2, const float4* __restrict__ grid_q,
-    double* __restrict__ g_s)
+    int64_t gq_stride, int V, double* __restrict__ g_s, int64_t g_stride)
 {
     extern __shared__ float4 win[];          // [kWinCells][Q] grid cells of this tile
     const Tile t = tiles[blockIdx.x];
@@ -1551,16 +1624,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
     const int nbins = t0s[t.count - 1] - wstart + 1;
     const int wlen = nbins - 1 + w;
     const int mask = B.nf2 - 1;
-    const float4* gq = grid_q + B.q_off;
     const bool staged = wlen <= kWinCells;
     const int maxbins = hbytes / (int)(sizeof(float2) * hs);
     const bool mom = staged && nbins <= maxbins && t.count >= kMomMinPerBin * nbins;
-    if (staged) {
-        for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
-            const int cc = idx / Q;
-            win[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
-        }
-    }
     if (mom) {
         for (int i = threadIdx.x; i < w * nb; i += blockDim.x) {
             const int r = i / nb, d = i - r * nb;
@@ -1570,59 +1636,72 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
         for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
     }
     __syncthreads();
-    if (mom) {
-        bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, P.qs, P.dcp);
-        __syncthreads();
-    }
-    if (!valid) return;
-    // this thread's Chebyshev basis T_d(v) (dense tile) or taps psi_i(v)
+    // this thread's Chebyshev basis T_d(v) (dense tile) or taps psi_i(v), and
+    // the member-independent factors of its output
     float2* u = U + threadIdx.x * us;
-    if (mom) {
-        cheb_basis_row(u, vh, vl, dci, nb);
-    } else {
-        for (int i = 0; i < w; ++i) {
-            const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
-            u[i] = make_float2(tp.h, tp.l);
+    df mz{0.f, 0.f}, sn{0.f, 0.f}, cs{0.f, 0.f}, scale{0.f, 0.f};
+    if (valid) {
+        if (mom) {
+            cheb_basis_row(u, vh, vl, dci, nb);
+        } else {
+            for (int i = 0; i < w; ++i) {
+                const df tp = horner_comp(coef2 + i * (deg + 1), deg, vh, vl, tab.deg_comp);
+                u[i] = make_float2(tp.h, tp.l);
+            }
         }
+        const float2 wk2 = w2[k];
+        const df m1d = df_recip(df_mul(df{wk2.x, wk2.y}, df{B.rho_h, B.rho_l}));   // 1/(omega rho) < 1/z
+        mz = df_mul(m1d, df{P.z2.x, P.z2.y});                                       // z/(omega rho) < 1
+        df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+        // sqrt(2/pi) (omega rho)^(-1/2) (4 / w^2) / psi^(alpha s)
+        scale = df_mul(df_mul(df_sqrt(m1d), df_recip(psihat_fx(tab, B, Sw))), df{tab.ic2.x, tab.ic2.y});
+        if (P.sgn < 0) scale = df_negate(scale);
     }
     const float2* Hb = H + (t0 - wstart) * hs;
-    const float2 wk2 = w2[k];
-    const df m1d = df_recip(df_mul(df{wk2.x, wk2.y}, df{B.rho_h, B.rho_l}));   // 1/(omega rho) < 1/z
-    const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});                               // z/(omega rho) < 1
-    // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
-    acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
-    df mq{1.f, 0.f};
     const int qs = P.qs;
-    auto combine = [&](int q, df prd, df pid) {
-        const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
-        // multiply by i^q: (pr + i pi) i^q
-        switch (q & 3) {
-            case 0: acc_fma(tr, cq, prd); acc_fma(ti, cq, pid); break;
-            case 1: acc_fma(tr, df{-cq.h, -cq.l}, pid); acc_fma(ti, cq, prd); break;
-            case 2: acc_fma(tr, df{-cq.h, -cq.l}, prd); acc_fma(ti, df{-cq.h, -cq.l}, pid); break;
-            default: acc_fma(tr, cq, pid); acc_fma(ti, df{-cq.h, -cq.l}, prd); break;
-        }
-        mq = df_mul(mq, mz);
-    };
-    if (mom)
-        bin_sums_eval(Hb, u, nb, dci, Q, qs, P.dcp, combine);
-    else
-        tap_sums_eval(u, w, Q, qs, [&](int i, int q) {
-            return staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
-        }, combine);
-    df sn, cs;
-    df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
-    // Re(e^{i (omega r_c + phi)} T) = Re(e^{i omega r_c} (e^{i phi} T))
-    const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
     const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
-    const df ur = df_add(df_mul(cph, tre), df_negate(df_mul(sph, tim)));
-    const df ui = df_add(df_mul(sph, tre), df_mul(cph, tim));
-    const df re = df_add(df_mul(cs, ur), df_negate(df_mul(sn, ui)));
-    // sqrt(2/pi) (omega rho)^(-1/2) (4 / w^2) / psi^(alpha s)
-    const df scale = df_mul(df_sqrt(m1d), df_recip(psihat_fx(tab, B, Sw)));
-    df outv = df_mul(df_mul(scale, re), df{tab.ic2.x, tab.ic2.y});
-    if (P.sgn < 0) outv = df_negate(outv);
-    Accum{g_s, P.fxs}.add(k, df_to(outv));
+    for (int vm = 0; vm < V; ++vm) {
+        const float4* gq = grid_q + vm * gq_stride + B.q_off;
+        if (vm > 0) __syncthreads();   // the previous member's reads of the window and H are done
+        if (staged) {
+            for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
+                const int cc = idx / Q;
+                win[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
+            }
+        }
+        __syncthreads();
+        if (mom) {
+            bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, qs, P.dcp);
+            __syncthreads();
+        }
+        if (!valid) continue;
+        // T = sum_q a_q i^q (omega rho)^(-q) P_q, accumulated in double-float
+        acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
+        df mq{1.f, 0.f};
+        auto combine = [&](int q, df prd, df pid) {
+            const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
+            // multiply by i^q: (pr + i pi) i^q
+            switch (q & 3) {
+                case 0: acc_fma(tr, cq, prd); acc_fma(ti, cq, pid); break;
+                case 1: acc_fma(tr, df{-cq.h, -cq.l}, pid); acc_fma(ti, cq, prd); break;
+                case 2: acc_fma(tr, df{-cq.h, -cq.l}, prd); acc_fma(ti, df{-cq.h, -cq.l}, pid); break;
+                default: acc_fma(tr, cq, pid); acc_fma(ti, df{-cq.h, -cq.l}, prd); break;
+            }
+            mq = df_mul(mq, mz);
+        };
+        if (mom)
+            bin_sums_eval(Hb, u, nb, dci, Q, qs, P.dcp, combine);
+        else
+            tap_sums_eval(u, w, Q, qs, [&](int i, int q) {
+                return staged ? win[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
+            }, combine);
+        // Re(e^{i (omega r_c + phi)} T) = Re(e^{i omega r_c} (e^{i phi} T))
+        const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
+        const df ur = df_add(df_mul(cph, tre), df_negate(df_mul(sph, tim)));
+        const df ui = df_add(df_mul(sph, tre), df_mul(cph, tim));
+        const df re = df_add(df_mul(cs, ur), df_negate(df_mul(sn, ui)));
+        Accum{g_s + vm * g_stride, P.fxs}.add(k, df_to(df_mul(scale, re)));
+    }
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1643,22 +1722,38 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp(
 //         e^{i (omega r_c + phi)} i^q a_q z^-q (z/(omega rho))^q,
 // as double-float (re, im) pairs xq[2q], xq[2q + 1]; returns the FFT-grid cell
 // t0 of omega_k and its kernel coordinate v.
-__device__ __forceinline__ int adj_spread_values(const AsyBlock& B, const ProbParams& P, const Tables& tab,
-                                                 double wk, double gk, df* v, float2* xq)
+// The factor of g_k in those values, split as f = fr + i fi (q = 0, without
+// g_k) and the ratio mz = z/(omega rho) of consecutive terms: one frequency's
+// part that the real components of a group share.
+struct AdjFactor {
+    df fr, fi, mz;
+};
+
+__device__ __forceinline__ int adj_spread_factor(const AsyBlock& B, const ProbParams& P, const Tables& tab,
+                                                 double wk, df* v, AdjFactor* F)
 {
     long long Om, Sw, svw;
     const int t0 = interp_cell_sv(B, tab.w, wk, &Om, &Sw, &svw);
     *v = df_from_sv(svw);
     const df m1d = df_recip(df_from(wk * B.rho));
-    const df mz = df_mul(m1d, df{P.z2.x, P.z2.y});
+    F->mz = df_mul(m1d, df{P.z2.x, P.z2.y});
     df sn, cs;
     df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
     const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
     const df er = df_add(df_mul(cs, cph), df_negate(df_mul(sn, sph)));
     const df ei = df_add(df_mul(sn, cph), df_mul(cs, sph));
-    const df amp = df_mul(df_mul(df_from((double)P.sgn * gk * tab.interp_const), df_sqrt(m1d)),
+    const df amp = df_mul(df_mul(df_from((double)P.sgn * tab.interp_const), df_sqrt(m1d)),
                           df_recip(psihat_fx(tab, B, Sw)));
-    const df fr = df_mul(amp, er), fi = df_mul(amp, ei);
+    F->fr = df_mul(amp, er);
+    F->fi = df_mul(amp, ei);
+    return t0;
+}
+
+// The 2M values x_q for g_k from the frequency's factor.
+__device__ __forceinline__ void adj_values(const ProbParams& P, const AdjFactor& F, double gk, float2* xq)
+{
+    const df g = df_from(gk);
+    const df fr = df_mul(F.fr, g), fi = df_mul(F.fi, g), mz = F.mz;
     df mq{1.f, 0.f};
     for (int q = 0; q < P.Q; ++q) {
         const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
@@ -1676,17 +1771,19 @@ __device__ __forceinline__ int adj_spread_values(const AsyBlock& B, const ProbPa
         xq[2 * q + 1] = make_float2(ui.h, ui.l);
         mq = df_mul(mq, mz);
     }
-    return t0;
 }
 
 // Frequencies of a tile -> FFT grid (periodic, atomics into tgrid).  Dense
 // tiles (many frequencies per cell) take the per-bin moment path of the
 // forward spreading; sparse tiles evaluate each frequency's w taps and sum,
-// per grid cell, the frequencies that reach it.
+// per grid cell, the frequencies that reach it.  Members: V real components
+// (g_s + vm g_stride into tgrid + vm tg_stride) share each frequency's cell,
+// basis or taps and factor (MULTI: the instance for V > 1).
+template <bool MULTI>
 __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ tiles, Tables tab,
                                  const double* __restrict__ w_s, const double* __restrict__ g_s,
-                                 double2* __restrict__ tgrid)
+                                 int64_t g_stride, int V, double2* __restrict__ tgrid, int64_t tg_stride)
 {
     extern __shared__ float4 sma[];
     __shared__ int use_mom;
@@ -1707,8 +1804,17 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
     }
     __syncthreads();
     if (use_mom) {
+        AdjFactor F{};
+        int64_t kt = 0;
         spread_moments(Q, P.qs, t, tab,
-            [&](int64_t k, df* v, float2* xq) { return adj_spread_values(B, P, tab, w_s[k], g_s[k], v, xq); },
+            [&](int64_t k, df* v, float2* xq) {
+                const int t0 = adj_spread_factor(B, P, tab, w_s[k], v, &F);
+                kt = k;
+                adj_values(P, F, g_s[k], xq);
+                return t0;
+            },
+            [&](int vm, float2* xq) { adj_values(P, F, g_s[vm * g_stride + kt], xq); }, MULTI ? V : 1,
+            2 * tg_stride,
             [&](int c) -> int64_t { return c & mask; }, tg, (float2*)sma);
         return;
     }
@@ -1719,10 +1825,12 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
     int* t0s = (int*)(taps + nt * w);                   // [nt]
     for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
     __syncthreads();
+    AdjFactor F{};
+    const int64_t k = t.start + tid;
     if (tid < cnt) {
-        const int64_t k = t.start + tid;
         df vdf;
-        const int t0 = adj_spread_values(B, P, tab, w_s[k], g_s[k], &vdf, (float2*)(uval + tid * Q));
+        const int t0 = adj_spread_factor(B, P, tab, w_s[k], &vdf, &F);
+        adj_values(P, F, g_s[k], (float2*)(uval + tid * Q));
         for (int i = 0; i < w; ++i) {
             const df tp = horner_comp(coef + i * (deg + 1), deg, vdf.h, vdf.l, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
@@ -1733,6 +1841,13 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
     const int tfirst = t0s[0];
     const int span = t0s[cnt - 1] - tfirst + w;
     const bool dense = span <= 2 * w;
+    for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
+    if (MULTI && vm > 0) {
+        __syncthreads();   // the previous member's reads of uval are done
+        if (tid < cnt) adj_values(P, F, g_s[vm * g_stride + k], (float2*)(uval + tid * Q));
+        __syncthreads();
+    }
+    const Accum tgv = tg.at(2 * vm * tg_stride);
     for (int item = tid; item < span * Q; item += nt) {
         const int c = item / Q, q = item - c * Q;
         const int cell = tfirst + c;
@@ -1761,9 +1876,10 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
         }
         if (any) {
             const int64_t o = (int64_t)(cell & mask) * Q + q;
-            tg.add(2 * o, acc_value(ar));
-            tg.add(2 * o + 1, acc_value(ai));
+            tgv.add(2 * o, acc_value(ar));
+            tgv.add(2 * o + 1, acc_value(ai));
         }
+    }
     }
 }
 
@@ -1774,9 +1890,14 @@ __global__ void k_asy_adj_spread(const ProbParams* __restrict__ probs, const Asy
 // l0 + i, i < w (zero outside the 2 N1 + 1 modes).  Dense passes (many points
 // per cell) form the per-bin sums H[d][q'] once per bin and each point sums
 // P_q = sum_d T_d(v) H[d][q]; sparse passes evaluate the w taps of each point.
+// Members: V real components (modes bgrid + vm bg_stride, sums into c_s + vm
+// c_stride) share each point's cell, basis or taps and factors (MULTI: the
+// instance for V > 1, which also forms the phase before the member loop).
+template <bool MULTI>
 __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
-    Tables tab, const double* __restrict__ r_s, const float4* __restrict__ bgrid, double* __restrict__ c_s)
+    Tables tab, const double* __restrict__ r_s, const float4* __restrict__ bgrid, int64_t bg_stride, int V,
+    double* __restrict__ c_s, int64_t c_stride)
 {
     extern __shared__ float4 win[];          // [kWinCells][Q] modes of this pass
     const Tile t = tiles[blockIdx.x];
@@ -1790,7 +1911,6 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
     float2* H = coef2 + ((w * (deg + 1) + 1) & ~1);              // [bins][hs], 16-byte aligned
     float2* U = H + kAdjInterpHBytes / sizeof(float2);              // [threads][us]
     int* l0s = (int*)(U + kAdjInterpThreads * us);              // [threads]
-    const float4* gb = bgrid + B.b_off;
     const int nf1 = 2 * B.N1 + 1;
     const int maxbins = kAdjInterpHBytes / (int)(sizeof(float2) * hs);
     for (int base = 0; base < t.count; base += blockDim.x) {
@@ -1809,13 +1929,6 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
         const int wlen = nbins - 1 + w;
         const bool staged = wlen <= kWinCells;
         const bool mom = staged && nbins <= maxbins && cnt >= kMomMinPerBin * nbins;
-        if (staged)
-            for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
-                const int cc = idx / Q;
-                const int li = wstart + cc + B.N1;
-                win[idx] = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + (idx - cc * Q)]
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
         if (mom) {
             for (int i = threadIdx.x; i < w * nb; i += blockDim.x) {
                 const int r = i / nb, d = i - r * nb;
@@ -1825,13 +1938,11 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
             for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
         }
         __syncthreads();
-        if (mom) {
-            bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, qs, P.dcp);
-            __syncthreads();
-        }
+        // this point's basis or taps, (r/rho)^(-1) and the phase e^{i w_c x}
+        float2* u = U + threadIdx.x * us;
+        df rat{0.f, 0.f}, sn{0.f, 0.f}, cs{0.f, 0.f};
         if (valid) {
             const float vh = vd.h, vl = vd.l;
-            float2* u = U + threadIdx.x * us;
             if (mom) {
                 cheb_basis_row(u, vh, vl, dci, nb);
             } else {
@@ -1840,8 +1951,26 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
                     u[i] = make_float2(tp.h, tp.l);
                 }
             }
+            rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1) <= 1
+            if (MULTI) df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+        }
+        for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
+            const float4* gb = bgrid + vm * bg_stride + B.b_off;
+            if (vm > 0) __syncthreads();   // the previous member's reads of the window and H are done
+            if (staged)
+                for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
+                    const int cc = idx / Q;
+                    const int li = wstart + cc + B.N1;
+                    win[idx] = (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + (idx - cc * Q)]
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            __syncthreads();
+            if (mom) {
+                bin_sums_build(win, coef2, H, nbins, w, nb, dci, Q, qs, P.dcp);
+                __syncthreads();
+            }
+            if (!valid) continue;
             // T = sum_q (r/rho)^(-q) P_q, P_q = sum_i psi_i(v) b'_{l0 + i, q}
-            const df rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1) <= 1
             acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
             df mq{1.f, 0.f};
             auto combine = [&](int, df prd, df pid) {
@@ -1858,11 +1987,10 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
                     return (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }, combine);
             // c_j += Re( e^{i w_c x} (r/rho)^(-1/2) T )
-            df sn, cs;
-            df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+            if (!MULTI) df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
             const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
             const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
-            Accum{c_s, P.fxs}.add(j, df_to(df_mul(df_sqrt(rat), re)));
+            Accum{c_s + vm * c_stride, P.fxs}.add(j, df_to(df_mul(df_sqrt(rat), re)));
         }
         __syncthreads();   // l0s, the window and H are rewritten by the next pass
     }
@@ -1885,10 +2013,12 @@ __host__ __device__ __forceinline__ int f32_stride4(int n)
 
 // FP32 spreading, dense tile: the moment form of spread_moments in single
 // precision (each of the 8 partial sums of a moment covers at most
-// ceil(tile / 8) points).
+// ceil(tile / 8) points).  Members (MULTI) as in spread_fold.
+template <bool MULTI>
 __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                                    const double* __restrict__ r_s, const float2* __restrict__ r2,
-                                   const float2* __restrict__ c2, Accum gb, float* sm)
+                                   const float2* __restrict__ c2, int64_t c_stride, int V, int64_t moff,
+                                   Accum gb, float* sm)
 {
     const int nt = blockDim.x, tid = threadIdx.x, cnt = t.count;
     const int w = tab.w, nb = tab.nb;
@@ -1905,8 +2035,9 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
         const int r = i / dpad, d = i - r * dpad;
         Ach[i] = d < nb ? tab.ch2[r * (tab.deg + 1) + d].x : 0.f;
     }
+    const int64_t j = t.start + tid;
+    float yr = 0.f, yi = 0.f, ratio = 0.f;   // this point's weight without c_j, and its ratio
     if (tid < cnt) {
-        const int64_t j = t.start + tid;
         long long Xp;
         df vdf;
         l0s[tid] = spread_cell_fx(B, tab.w, r_s[j], &Xp, &vdf);
@@ -1924,9 +2055,14 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
         for (int d = nb; d < su; ++d) u[d] = 0.f;
         float sn, cs;
         f32_sincos_turns(mul128_bits(Xp, B.KW, B.sW), &sn, &cs);
-        const float ratio = B.rho_h / r2[j].x;
-        const float w0 = c2[j].x * sqrtf(ratio);
-        float wr = w0 * cs, wi = w0 * sn;
+        ratio = B.rho_h / r2[j].x;
+        const float w0 = sqrtf(ratio);
+        yr = w0 * cs;
+        yi = w0 * sn;
+    }
+    auto put = [&](int vm) {
+        const float cv = c2[vm * c_stride + j].x;
+        float wr = cv * yr, wi = cv * yi;
         float* xq = X + tid * sx;
         for (int q = 0; q < Q; ++q) {
             xq[2 * q] = wr;
@@ -1934,7 +2070,8 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
             wr *= ratio;
             wi *= ratio;
         }
-    }
+    };
+    if (tid < cnt) put(0);
     __syncthreads();
     const int lfirst = l0s[0];
     const int nbins = l0s[cnt - 1] - lfirst + 1;
@@ -1948,6 +2085,12 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
     const int nf1 = 2 * B.N1 + 1;
     const int nitems = ndp * nq * kSpreadSub;
     const int nitems_pad = (nitems + 31) & ~31;
+    for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
+    if (MULTI && vm > 0) {
+        if (tid < cnt) put(vm);
+        __syncthreads();
+    }
+    const Accum gv = gb.at(vm * moff);
     for (int b = 0; b < nbins; ++b) {
         const int p0 = bstart[b], p1 = bstart[b + 1];
         if (p0 == p1) continue;
@@ -1987,9 +2130,10 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
             if (idx < 0 || idx >= nf1) continue;
             float sacc = 0.f;
             for (int d = 0; d < nb; ++d) sacc = fmaf(Ach[i * dpad + d], Mb[d * Q2 + qv], sacc);
-            if (sacc != 0.f) gb.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), (double)sacc);
+            if (sacc != 0.f) gv.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), (double)sacc);
         }
         __syncthreads();
+    }
     }
 }
 
@@ -2002,9 +2146,12 @@ __host__ __device__ __forceinline__ size_t spread_moments_f32_smem(int nt, int Q
 }
 
 // FP32 spreading, sparse tile: taps per point, one thread per (cell, q).
+// Members (MULTI) as in spread_taps.
+template <bool MULTI>
 __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                                 const double* __restrict__ r_s, const float2* __restrict__ r2,
-                                const float2* __restrict__ c2, Accum gb, float2* smf)
+                                const float2* __restrict__ c2, int64_t c_stride, int V, int64_t moff,
+                                Accum gb, float2* smf)
 {
     const int w = tab.w, deg = tab.deg, nt = blockDim.x, tid = threadIdx.x;
     const int ncoef = w * (deg + 1);
@@ -2015,8 +2162,9 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
     for (int i = tid; i < ncoef; i += nt) coef[i] = tab.es2[i];
     __syncthreads();
     const int cnt = t.count;
+    const int64_t j = t.start + tid;
+    float yr = 0.f, yi = 0.f, ratio = 0.f;   // this point's weight without c_j, and its ratio
     if (tid < cnt) {
-        const int64_t j = t.start + tid;
         long long Xp;
         df vdf;
         l0s[tid] = spread_cell_fx(B, tab.w, r_s[j], &Xp, &vdf);
@@ -2024,20 +2172,33 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
         for (int i = 0; i < w; ++i) taps[tid * w + i] = horner_f32(coef + i * (deg + 1), deg, v);
         float sn, cs;
         f32_sincos_turns(mul128_bits(Xp, B.KW, B.sW), &sn, &cs);
-        const float ratio = B.rho_h / r2[j].x;
-        const float w0 = c2[j].x * sqrtf(ratio);
-        float wr = w0 * cs, wi = w0 * sn;
+        ratio = B.rho_h / r2[j].x;
+        const float w0 = sqrtf(ratio);
+        yr = w0 * cs;
+        yi = w0 * sn;
+    }
+    auto put = [&](int vm) {
+        const float cv = c2[vm * c_stride + j].x;
+        float wr = cv * yr, wi = cv * yi;
         for (int q = 0; q < Q; ++q) {
             aval[tid * Q + q] = make_float2(wr, wi);
             wr *= ratio;
             wi *= ratio;
         }
-    }
+    };
+    if (tid < cnt) put(0);
     __syncthreads();
     const int lfirst = l0s[0];
     const int span = l0s[cnt - 1] - lfirst + w;
     const int nf1 = 2 * B.N1 + 1;
     const bool dense = span <= 2 * w;
+    for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
+    if (MULTI && vm > 0) {
+        __syncthreads();   // the previous member's reads of aval are done
+        if (tid < cnt) put(vm);
+        __syncthreads();
+    }
+    const Accum gv = gb.at(vm * moff);
     for (int item = tid; item < span * Q; item += nt) {
         const int c = item / Q, q = item - c * Q;
         const int cell = lfirst + c;
@@ -2063,18 +2224,22 @@ __device__ void spread_taps_f32(const AsyBlock& B, int Q, const Tile& t, const T
         }
         const int idx = cell + B.N1;
         if (idx >= 0 && idx < nf1 && (sr != 0.f || si != 0.f)) {
-            gb.add(2 * ((int64_t)idx * Q + q), (double)sr);
-            gb.add(2 * ((int64_t)idx * Q + q) + 1, (double)si);
+            gv.add(2 * ((int64_t)idx * Q + q), (double)sr);
+            gv.add(2 * ((int64_t)idx * Q + q) + 1, (double)si);
         }
+    }
     }
 }
 
 // FP32 spreading (coordinates and phase reduction in FP64).
 // Mixed precision: the plain moment path for every dense tile (mode != 0).
+// Members as in k_asy_spread.
+template <bool MULTI>
 __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks,
                                  const Tile* __restrict__ tiles, const int32_t* __restrict__ modes, Tables tab,
                                  const double* __restrict__ r_s, const float2* __restrict__ r2,
-                                 const float2* __restrict__ c2, double2* __restrict__ grid_b)
+                                 const float2* __restrict__ c2, int64_t c_stride, int V,
+                                 double2* __restrict__ grid_b, int64_t gb_stride)
 {
     extern __shared__ float2 smf[];
     const Tile t = tiles[blockIdx.x];
@@ -2083,9 +2248,9 @@ __global__ void k_asy_spread_f32(const ProbParams* __restrict__ probs, const Asy
     const int Q = probs[B.prob].Q;
     const Accum gb = Accum{(double*)grid_b, probs[B.prob].fxs}.at(2 * B.b_off);
     if (modes[blockIdx.x] & 3)
-        spread_moments_f32(B, Q, t, tab, r_s, r2, c2, gb, (float*)smf);
+        spread_moments_f32<MULTI>(B, Q, t, tab, r_s, r2, c2, c_stride, V, 2 * gb_stride, gb, (float*)smf);
     else
-        spread_taps_f32(B, Q, t, tab, r_s, r2, c2, gb, smf);
+        spread_taps_f32<MULTI>(B, Q, t, tab, r_s, r2, c2, c_stride, V, 2 * gb_stride, gb, smf);
 }
 
 // Shared memory (bytes) of k_asy_interp_f32 for 2M = qmax.
@@ -2098,11 +2263,11 @@ __host__ __device__ __forceinline__ size_t interp_f32_smem(int qmax, int w, int 
 
 // FP32 interpolation and Hankel combination (coordinates and phase
 // reduction in FP64); dense tiles by per-bin Chebyshev sums as in
-// k_asy_interp, sparse tiles by taps.
-__global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
+// k_asy_interp, sparse tiles by taps.  Members as in k_asy_interp.
+__global__ void __launch_bounds__(kInterpTileThreads, 4) k_asy_interp_f32(
     const ProbParams* __restrict__ probs, const AsyBlock* __restrict__ blks, const Tile* __restrict__ tiles,
     Tables tab, const double* __restrict__ w_s, const float2* __restrict__ w2, const float4* __restrict__ grid_q,
-    double* __restrict__ g_s)
+    int64_t gq_stride, int V, double* __restrict__ g_s, int64_t g_stride)
 {
     extern __shared__ float4 winf[];
     const Tile t = tiles[blockIdx.x];
@@ -2128,15 +2293,9 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
     const int nbins = t0s[t.count - 1] - wstart + 1;
     const int wlen = nbins - 1 + w;
     const int mask = B.nf2 - 1;
-    const float4* gq = grid_q + B.q_off;
     const bool staged = wlen <= kWinCells;
     const int maxbins = hbytes / (int)(sizeof(float) * hs);
     const bool mom = staged && nbins <= maxbins && t.count >= kMomMinPerBin * nbins;
-    if (staged)
-        for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
-            const int cc = idx / Q;
-            winf[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
-        }
     if (mom) {
         for (int i = threadIdx.x; i < w * nb; i += blockDim.x) {
             const int r = i / nb, d = i - r * nb;
@@ -2146,82 +2305,98 @@ __global__ void __launch_bounds__(kInterpTileThreads) k_asy_interp_f32(
         for (int i = threadIdx.x; i < w * (deg + 1); i += blockDim.x) coef2[i] = tab.es2[i];
     }
     __syncthreads();
-    if (mom) {
-        for (int o = threadIdx.x; o < nbins * nb * Q2; o += blockDim.x) {
-            const int b = o / (nb * Q2), rem = o - b * nb * Q2;
-            const int d = rem / Q2, qv = rem - d * Q2;
-            const int q = qv >> 1, im = qv & 1;
-            float acc = 0.f;
-            for (int i = 0; i < w; ++i) {
-                const float4 gv = winf[(b + i) * Q + q];
-                acc = fmaf(coef2[i * nb + d].x, im ? gv.z : gv.x, acc);
-            }
-            H[b * hs + rem] = acc;
-        }
-        __syncthreads();
-    }
-    if (!valid) return;
+    // this thread's basis or taps, and the member-independent factors of its output
     float* u = U + threadIdx.x * us;
-    if (mom) {
-        float tm = 1.f, tc = v;
-        u[0] = 1.f;
-        u[1] = v;
-        for (int d = 2; d < nb; ++d) {
-            const float tn = fmaf(2.f * v, tc, -tm);
-            u[d] = tn;
-            tm = tc;
-            tc = tn;
-        }
-    } else {
-        for (int i = 0; i < w; ++i) u[i] = horner_f32(coef2 + i * (deg + 1), deg, v);
-    }
-    const float* Hb = H + (t0 - wstart) * hs;
-    const float m1 = 1.f / (w2[k].x * B.rho_h);
-    float tr = 0.f, ti = 0.f, mq = 1.f;
-    for (int q = 0; q < Q; ++q) {
-        float pr = 0.f, pi = 0.f;
+    float m1 = 0.f, outs = 0.f, sn = 0.f, cs = 0.f;
+    if (valid) {
         if (mom) {
-            for (int d = 0; d < nb; ++d) {
-                const float2 hv = *(const float2*)(Hb + d * Q2 + 2 * q);
-                pr = fmaf(u[d], hv.x, pr);
-                pi = fmaf(u[d], hv.y, pi);
+            float tm = 1.f, tc = v;
+            u[0] = 1.f;
+            u[1] = v;
+            for (int d = 2; d < nb; ++d) {
+                const float tn = fmaf(2.f * v, tc, -tm);
+                u[d] = tn;
+                tm = tc;
+                tc = tn;
             }
         } else {
-            for (int i = 0; i < w; ++i) {
-                const float4 gv = staged ? winf[(t0 + i - wstart) * Q + q] : gq[(int64_t)((t0 + i) & mask) * Q + q];
-                pr = fmaf(u[i], gv.x, pr);
-                pi = fmaf(u[i], gv.z, pi);
-            }
+            for (int i = 0; i < w; ++i) u[i] = horner_f32(coef2 + i * (deg + 1), deg, v);
         }
-        const float cq = P.a2[q].x * mq;
-        switch (q & 3) {
-            case 0: tr = fmaf(cq, pr, tr); ti = fmaf(cq, pi, ti); break;
-            case 1: tr = fmaf(-cq, pi, tr); ti = fmaf(cq, pr, ti); break;
-            case 2: tr = fmaf(-cq, pr, tr); ti = fmaf(-cq, pi, ti); break;
-            default: tr = fmaf(cq, pi, tr); ti = fmaf(-cq, pr, ti); break;
-        }
-        mq *= m1 * P.z2.x;
+        m1 = 1.f / (w2[k].x * B.rho_h);
+        f32_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+        // psi^(alpha s) in FP32 from the table's high parts
+        const float sf = df_from_i64(Sw < 0 ? -Sw : Sw).h * ldexpf(1.f, -B.fw);
+        const float xi = B.alpha_h * sf * tab.ph_scale2.x;
+        int piece = (int)xi;
+        if (piece > tab.ph_pieces - 1) piece = tab.ph_pieces - 1;
+        const float ph = horner_f32(tab.ph2 + piece * (tab.ph_deg + 1), tab.ph_deg, 2.f * (xi - (float)piece) - 1.f);
+        outs = tab.ic2.x * sqrtf(m1) / ph;
+        if (P.sgn < 0) outs = -outs;
     }
-    float sn, cs;
-    f32_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+    const float* Hb = H + (t0 - wstart) * hs;
     const float cph = P.cphi2.x, sph = P.sphi2.x;
-    const float ur = cph * tr - sph * ti, ui = sph * tr + cph * ti;
-    const float re = cs * ur - sn * ui;
-    // psi^(alpha s) in FP32 from the table's high parts
-    const float sf = df_from_i64(Sw < 0 ? -Sw : Sw).h * ldexpf(1.f, -B.fw);
-    const float xi = B.alpha_h * sf * tab.ph_scale2.x;
-    int piece = (int)xi;
-    if (piece > tab.ph_pieces - 1) piece = tab.ph_pieces - 1;
-    const float ph = horner_f32(tab.ph2 + piece * (tab.ph_deg + 1), tab.ph_deg, 2.f * (xi - (float)piece) - 1.f);
-    const float val = tab.ic2.x * sqrtf(m1) / ph * re;
-    Accum{g_s, P.fxs}.add(k, (double)(P.sgn < 0 ? -val : val));
+    for (int vm = 0; vm < V; ++vm) {
+        const float4* gq = grid_q + vm * gq_stride + B.q_off;
+        if (vm > 0) __syncthreads();   // the previous member's reads of the window and H are done
+        if (staged)
+            for (int idx = threadIdx.x; idx < wlen * Q; idx += blockDim.x) {
+                const int cc = idx / Q;
+                winf[idx] = gq[(int64_t)((wstart + cc) & mask) * Q + (idx - cc * Q)];
+            }
+        __syncthreads();
+        if (mom) {
+            for (int o = threadIdx.x; o < nbins * nb * Q2; o += blockDim.x) {
+                const int b = o / (nb * Q2), rem = o - b * nb * Q2;
+                const int d = rem / Q2, qv = rem - d * Q2;
+                const int q = qv >> 1, im = qv & 1;
+                float acc = 0.f;
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = winf[(b + i) * Q + q];
+                    acc = fmaf(coef2[i * nb + d].x, im ? gv.z : gv.x, acc);
+                }
+                H[b * hs + rem] = acc;
+            }
+            __syncthreads();
+        }
+        if (!valid) continue;
+        float tr = 0.f, ti = 0.f, mq = 1.f;
+        for (int q = 0; q < Q; ++q) {
+            float pr = 0.f, pi = 0.f;
+            if (mom) {
+                for (int d = 0; d < nb; ++d) {
+                    const float2 hv = *(const float2*)(Hb + d * Q2 + 2 * q);
+                    pr = fmaf(u[d], hv.x, pr);
+                    pi = fmaf(u[d], hv.y, pi);
+                }
+            } else {
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = staged ? winf[(t0 + i - wstart) * Q + q]
+                                             : gq[(int64_t)((t0 + i) & mask) * Q + q];
+                    pr = fmaf(u[i], gv.x, pr);
+                    pi = fmaf(u[i], gv.z, pi);
+                }
+            }
+            const float cq = P.a2[q].x * mq;
+            switch (q & 3) {
+                case 0: tr = fmaf(cq, pr, tr); ti = fmaf(cq, pi, ti); break;
+                case 1: tr = fmaf(-cq, pi, tr); ti = fmaf(cq, pr, ti); break;
+                case 2: tr = fmaf(-cq, pr, tr); ti = fmaf(-cq, pi, ti); break;
+                default: tr = fmaf(cq, pi, tr); ti = fmaf(-cq, pr, ti); break;
+            }
+            mq *= m1 * P.z2.x;
+        }
+        const float ur = cph * tr - sph * ti, ui = sph * tr + cph * ti;
+        const float re = cs * ur - sn * ui;
+        Accum{g_s + vm * g_stride, P.fxs}.add(k, (double)(outs * re));
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, int nt, Tables tab, const double* w_s, const double* g_s,
-                                  double2* tgrid, cudaStream_t s)
+                                  int64_t g_stride, int members, double2* tgrid, int64_t tg_stride,
+                                  cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (nt < 32 || nt > kInterpTileThreads || (nt & 31)) return cudaErrorInvalidValue;
@@ -2229,53 +2404,64 @@ cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks,
                   sizeof(float2) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     const size_t smem_mom = spread_moments_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
     if (smem_mom > smem) smem = smem_mom;
-    cudaError_t e = cudaFuncSetAttribute(k_asy_adj_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (members < 1) return cudaErrorInvalidValue;
+    auto kern = members > 1 ? k_asy_adj_spread<true> : k_asy_adj_spread<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_adj_spread<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, g_s, tgrid);
+    kern<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, g_s, g_stride, members, tgrid, tg_stride);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
-                                  double* c_s, cudaStream_t s)
+                                  int64_t bg_stride, int members, double* c_s, int64_t c_stride, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     const size_t smem = interp_smem(qmax, tab.w, tab.deg, kAdjInterpThreads, kAdjInterpHBytes);
-    cudaError_t e = cudaFuncSetAttribute(k_asy_adj_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (members < 1) return cudaErrorInvalidValue;
+    auto kern = members > 1 ? k_asy_adj_interp<true> : k_asy_adj_interp<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_adj_interp<<<ntiles, kAdjInterpThreads, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, c_s);
+    kern<<<ntiles, kAdjInterpThreads, smem, s>>>(probs, blks, tiles, tab, r_s, bgrid, bg_stride, members, c_s,
+                                                 c_stride);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   const int32_t* modes, int ntiles, int qmax, int nt, Tables tab,
-                                  const double* r_s, const float2* r2, const float2* c2, double2* grid_b,
-                                  cudaStream_t s)
+                                  const double* r_s, const float2* r2, const float2* c2, int64_t c_stride,
+                                  int members, double2* grid_b, int64_t gb_stride, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float2) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
                   sizeof(float) * (size_t)nt * tab.w + sizeof(int) * (size_t)nt;
     const size_t smem_mom = spread_moments_f32_smem(nt, qmax, tab.w, tab.nb);
     if (smem_mom > smem) smem = smem_mom;
-    cudaError_t e = cudaFuncSetAttribute(k_asy_spread_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (members < 1) return cudaErrorInvalidValue;
+    auto kern = members > 1 ? k_asy_spread_f32<true> : k_asy_spread_f32<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_spread_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, grid_b);
+    kern<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, c_stride, members, grid_b,
+                                  gb_stride);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
-                                  const float4* grid_q, double* g_s, cudaStream_t s)
+                                  const float4* grid_q, int64_t gq_stride, int members, double* g_s,
+                                  int64_t g_stride, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (nt < 32 || nt > kInterpTileThreads || (nt & 31)) return cudaErrorInvalidValue;
     const size_t smem = interp_f32_smem(qmax, tab.w, tab.deg, nt);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
+    if (members < 1) return cudaErrorInvalidValue;
+    k_asy_interp_f32<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, gq_stride, members, g_s,
+                                              g_stride);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -2292,7 +2478,8 @@ cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, c
 
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                              const float2* r2, const float2* c2, double2* grid_b, int det, cudaStream_t s)
+                              const float2* r2, const float2* c2, int64_t c_stride, int members,
+                              double2* grid_b, int64_t gb_stride, int det, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float4) * (size_t)nt * qmax + sizeof(float2) * (size_t)tab.w * (tab.deg + 1) +
@@ -2301,19 +2488,24 @@ cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, con
     if (smem_mom > smem) smem = smem_mom;
     const size_t smem_fold = spread_fold_smem(nt, qmax, tab.w, tab.nb, tab.dcs);
     if (smem_fold > smem) smem = smem_fold;
-    auto kern = det ? k_asy_spread<true> : k_asy_spread<false>;
+    auto kern = det ? k_asy_spread<true, false>
+                    : (members > 1 ? k_asy_spread<false, true> : k_asy_spread<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, grid_b);
+    if (members < 1 || (det && members != 1)) return cudaErrorInvalidValue;
+    kern<<<ntiles, nt, smem, s>>>(probs, blks, tiles, modes, tab, r_s, r2, c2, c_stride, members, grid_b,
+                                  gb_stride);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* src,
-                                 float4* dst, cudaStream_t s, bool adj, bool lowp)
+                                 float4* dst, cudaStream_t s, bool adj, bool lowp, int members,
+                                 int64_t src_stride, int64_t dst_stride)
 {
     if (nitems <= 0) return cudaSuccess;
+    if (members < 1 || members > 65535) return cudaErrorInvalidValue;
     size_t smem = (lowp ? sizeof(float2) : sizeof(float4)) * (size_t)max_nf2;
     auto kern = adj ? (lowp ? k_asy_fft_small<true, true> : k_asy_fft_small<true, false>)
                     : (lowp ? k_asy_fft_small<false, true> : k_asy_fft_small<false, false>);
@@ -2322,16 +2514,18 @@ cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, 
     int nt = max_nf2 / 2;
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;
-    kern<<<nitems, nt, smem, s>>>(probs, blks, items, tab, src, dst);
+    kern<<<dim3(nitems, members), nt, smem, s>>>(probs, blks, items, tab, src, dst, src_stride, dst_stride);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_pts, Tables tab, const double2* src, float4* dst,
-                                 cudaStream_t s, bool adj, bool lowp)
+                                 cudaStream_t s, bool adj, bool lowp, int members, int64_t src_stride,
+                                 int64_t dst_stride)
 {
     if (nitems <= 0) return cudaSuccess;
+    if (members < 1 || members > 65535) return cudaErrorInvalidValue;
     if (max_pts < 1 || max_pts > kFftSmemMax) max_pts = kFftSmemMax;
     auto kern = adj ? (lowp ? k_asy_fft_block<true, true> : k_asy_fft_block<true, false>)
                     : (lowp ? k_asy_fft_block<false, true> : k_asy_fft_block<false, false>);
@@ -2351,7 +2545,8 @@ cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, 
         if (nt < 32) nt = 32;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<nitems, nt, smem, s>>>(probs, blks, items, tab, src, dst, lo, hi);
+        kern<<<dim3(nitems, members), nt, smem, s>>>(probs, blks, items, tab, src, dst, lo, hi, src_stride,
+                                                     dst_stride);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ++launched;
@@ -2385,14 +2580,17 @@ cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, 
 
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
-                              const float4* grid_q, double* g_s, cudaStream_t s)
+                              const float4* grid_q, int64_t gq_stride, int members, double* g_s,
+                              int64_t g_stride, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (nt < 32 || nt > kInterpTileThreads || (nt & 31)) return cudaErrorInvalidValue;
     const size_t smem = interp_smem(qmax, tab.w, tab.deg, nt, kInterpHBytesPerThread * nt);
     cudaError_t e = cudaFuncSetAttribute(k_asy_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_asy_interp<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, g_s);
+    if (members < 1) return cudaErrorInvalidValue;
+    k_asy_interp<<<ntiles, nt, smem, s>>>(probs, blks, tiles, tab, w_s, w2, grid_q, gq_stride, members, g_s,
+                                          g_stride);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1257,6 +1257,145 @@ __global__ void k_direct_group(const ProbParams* __restrict__ probs, const Direc
     }
 }
 
+// Adjoint local blocks for a group of G <= GM components: each row's Miller
+// sweep (phase 1) and each C_l(row) (phase 2) are formed once for all members;
+// the adjoint moments are the dense product nu[v][l] = sum_rows C_l(row)
+// g_v(row) / S(row)^2, G compensated sums per warp and l.
+template <int GM>
+__global__ void __launch_bounds__(kMomThreads)
+k_local_adj_moments_group(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                          const Tile* __restrict__ tiles, const float2* __restrict__ w2,
+                          const double* __restrict__ g_s, int64_t g_stride, int G, double* __restrict__ mom,
+                          int64_t mom_stride)
+{
+    extern __shared__ float2 sm2[];
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const ProbParams& P = probs[B.prob];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int nu = P.nu, L = P.L;
+    const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
+    const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
+    const int ntop = hp + L;
+    float2* jb = sm2;                                  // [ntop + 1][nt]
+    float2* gsm = sm2 + (size_t)(P.ntop + 1) * nt;     // [GM][nt] g_v,k / S^2 per row
+    float* p2m = (float*)(gsm + GM * nt);              // [nt] scale per row
+    for (int base = 0; base < t.count; base += nt) {
+        const int cnt = t.count - base < nt ? t.count - base : nt;
+        if (tid < cnt) {
+            const int64_t k = t.start + base + tid;
+            const float2 wk = w2[k];
+            const df ydf = df_mul(df{wk.x, wk.y}, df{0.5f * B.R_h, 0.5f * B.R_l});   // y = omega R / 2
+            df iS2{1.f, 0.f};
+            float p2 = 1.f;
+            if (!(ydf.h > 0.f)) {
+                // y below the FP32 range: J_n(y) = delta_n0 to far below rounding
+                for (int q = 0; q <= ntop; ++q) jb[q * nt + tid] = make_float2(q == 0 ? 1.f : 0.f, 0.f);
+            } else {
+                const int ns = miller_start(ntop, (double)ydf.h);
+                df S = (ydf.h >= 1.f) ? miller_store_df(ydf, ntop, ns, jb, nt, tid)
+                                      : df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+                p2 = exp2f(-(float)ilogbf(S.h));
+                S = df_scale(S, p2);
+                const df iS = df_recip(S);
+                iS2 = df_mul(iS, iS);
+            }
+            p2m[tid] = p2;
+            for (int v = 0; v < GM; ++v) {
+                const df gs = v < G ? df_mul(df_from((double)P.sgn * g_s[v * g_stride + k]), iS2) : df{0.f, 0.f};
+                gsm[v * nt + tid] = make_float2(gs.h, gs.l);
+            }
+        }
+        __syncthreads();
+        for (int l = warp; l <= L; l += nw) {
+            const int b = hm - l, bi = b >= 0 ? b : -b;
+            float sgn = (b < 0 && (bi & 1)) ? -1.f : 1.f;
+            if (l > 0 || (nu & 1)) sgn *= 2.f;
+            acc2 a[GM];
+#pragma unroll
+            for (int v = 0; v < GM; ++v) a[v] = acc2{0.f, 0.f};
+            for (int kk = lane; kk < cnt; kk += 32) {
+                const float2 va = jb[(hp + l) * nt + kk];
+                const float2 vb = jb[bi * nt + kk];
+                const float p = p2m[kk], ps = p * sgn;
+                const df cl = df_mul(df{va.x * p, va.y * p}, df{vb.x * ps, vb.y * ps});
+#pragma unroll
+                for (int v = 0; v < GM; ++v) {
+                    if (v < G) {
+                        const float2 g = gsm[v * nt + kk];
+                        acc_fma(a[v], cl, df{g.x, g.y});
+                    }
+                }
+            }
+            const Accum dst{mom, P.fxs};
+#pragma unroll
+            for (int v = 0; v < GM; ++v) {
+                if (v < G) {
+                    const acc2 sv = warp_sum_acc(a[v]);
+                    if (lane == 0) dst.add(v * mom_stride + B.mom_off + l, acc_value(sv));
+                }
+            }
+        }
+        __syncthreads();   // jb and gsm are rewritten by the next pass
+    }
+}
+
+// Adjoint local evaluation for a group: each point's basis T_{2l(+1)}(r_j/R)
+// once, applied to the G members' adjoint moments (mu[l][v] in shared
+// memory), G compensated sums per point.
+template <int GM>
+__global__ void __launch_bounds__(kMomThreads)
+k_local_adj_eval_group(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                       const Tile* __restrict__ tiles, const float2* __restrict__ r2,
+                       const double* __restrict__ mom, int64_t mom_stride, int G, double* __restrict__ c_s,
+                       int64_t c_stride)
+{
+    extern __shared__ float2 mu2[];   // [L + 1][GM]
+    const Tile t = tiles[blockIdx.x];
+    const LocalBlock B = blks[t.blk];
+    const int L = probs[B.prob].L;
+    const int odd = probs[B.prob].nu & 1;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    for (int i = tid; i < (L + 1) * GM; i += nt) {
+        const int l = i / GM, v = i - l * GM;
+        const double x = v < G ? mom[v * mom_stride + B.mom_off + l] : 0.0;
+        const float h = (float)x;
+        mu2[i] = make_float2(h, (float)(x - (double)h));
+    }
+    __syncthreads();
+    const df invR{B.iR_h, B.iR_l};
+    const Accum dst{c_s, probs[B.prob].fxs};
+    for (int64_t j = t.start + tid; j < t.start + t.count; j += nt) {
+        const float2 rj = r2[j];
+        const df y = df_mul(df{rj.x, rj.y}, invR);
+        const df u = df_add(df_mul(df{2.f * y.h, 2.f * y.l}, y), df{-1.f, 0.f});
+        const df u2{2.f * u.h, 2.f * u.l};
+        df t0 = odd ? y : df{1.f, 0.f};
+        df t1 = odd ? df_mul(y, df_add(u2, df{-1.f, 0.f})) : u;
+        acc2 sum[GM];
+#pragma unroll
+        for (int v = 0; v < GM; ++v) sum[v] = acc2{0.f, 0.f};
+        for (int l = 0; l <= L; ++l) {
+            df tl;
+            if (l == 0) tl = t0;
+            else if (l == 1) tl = t1;
+            else {
+                tl = df_add(df_mul(u2, t1), df_neg(t0));
+                t0 = t1;
+                t1 = tl;
+            }
+            const float2* ml = mu2 + l * GM;
+#pragma unroll
+            for (int v = 0; v < GM; ++v)
+                if (v < G) acc_fma(sum[v], tl, df{ml[v].x, ml[v].y});
+        }
+#pragma unroll
+        for (int v = 0; v < GM; ++v)
+            if (v < G) dst.add(v * c_stride + j, acc_value(sum[v]));
+    }
+}
+
 }  // namespace
 
 int local_adj_threads(int ntop_max)
@@ -1444,9 +1583,13 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
     return cudaGetLastError();
 }
 
-int local_group_fits(int lmax, int G)
+int local_group_fits(int lmax, int ntop_max, int eval_threads, int G)
 {
-    return G >= 1 && G <= kGroupMax && (lmax + 1) * G <= kMomGroupOut * kMomThreads;
+    constexpr size_t kSmemMax = 200 * 1024;
+    const size_t mom_smem = sizeof(float2) * (size_t)(lmax + 1 + G) * (kMomThreads + 8);
+    const size_t eval_smem = sizeof(float2) * (size_t)(ntop_max + 1) * (eval_threads + kGroupMax);
+    return G >= 1 && G <= kGroupMax && (lmax + 1) * G <= kMomGroupOut * kMomThreads && mom_smem <= kSmemMax &&
+           eval_smem <= kSmemMax;
 }
 
 cudaError_t launch_local_moments_group(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
@@ -1454,7 +1597,7 @@ cudaError_t launch_local_moments_group(const ProbParams* probs, const LocalBlock
                                        int64_t c_stride, int G, double* mom, int64_t mom_stride, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    if (!local_group_fits(lmax, G)) return cudaErrorInvalidValue;
+    if (G < 1 || G > kGroupMax || (lmax + 1) * G > kMomGroupOut * kMomThreads) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float2) * (size_t)(lmax + 1 + G) * (kMomThreads + 8);
     cudaError_t e = cudaFuncSetAttribute(k_local_moments_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -1509,6 +1652,60 @@ cudaError_t launch_direct_group(const ProbParams* probs, const DirectBlock* blks
     k_direct_group<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c2, c_stride, G, g_s, g_stride, lowp);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int GM>
+static cudaError_t adj_group_as(const ProbParams* probs, const LocalBlock* blks, const Tile* teval, int n_teval,
+                                const Tile* tmom, int n_tmom, int lmax, int ntop_max, int threads, const float2* w2,
+                                const float2* r2, const double* g_s, int64_t g_stride, int G, double* mom,
+                                int64_t mom_stride, double* c_s, int64_t c_stride, bool moments, cudaStream_t s)
+{
+    if (moments) {
+        if (n_teval <= 0) return cudaSuccess;
+        const size_t smem = sizeof(float2) * (size_t)(ntop_max + 1 + GM) * threads + sizeof(float) * threads;
+        cudaError_t e = cudaFuncSetAttribute(k_local_adj_moments_group<GM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_local_adj_moments_group<GM><<<n_teval, threads, smem, s>>>(probs, blks, teval, w2, g_s, g_stride, G, mom,
+                                                                     mom_stride);
+    } else {
+        if (n_tmom <= 0) return cudaSuccess;
+        const size_t smem = sizeof(float2) * (size_t)(lmax + 1) * GM;
+        cudaError_t e = cudaFuncSetAttribute(k_local_adj_eval_group<GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_local_adj_eval_group<GM><<<n_tmom, kMomThreads, smem, s>>>(probs, blks, tmom, r2, mom, mom_stride, G, c_s,
+                                                                     c_stride);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int local_adj_group_threads(int ntop_max)
+{
+    // (ntop + 1 + 16) double-float values plus a scale per thread within ~200 KB
+    int t = (int)(200 * 1024 / (8 * (ntop_max + 1 + kGroupMax) + 4));
+    t = (t / 32) * 32;
+    if (t > kMomThreads) t = kMomThreads;
+    if (t < 32) t = 32;
+    return t;
+}
+
+cudaError_t launch_local_adj_group(const ProbParams* probs, const LocalBlock* blks, const Tile* teval, int n_teval,
+                                   const Tile* tmom, int n_tmom, int lmax, int ntop_max, int threads,
+                                   const float2* w2, const float2* r2, const double* g_s, int64_t g_stride, int G,
+                                   double* mom, int64_t mom_stride, double* c_s, int64_t c_stride, bool moments,
+                                   cudaStream_t s)
+{
+    if (G < 1 || G > kGroupMax) return cudaErrorInvalidValue;
+    if (G <= 4)
+        return adj_group_as<4>(probs, blks, teval, n_teval, tmom, n_tmom, lmax, ntop_max, threads, w2, r2, g_s,
+                               g_stride, G, mom, mom_stride, c_s, c_stride, moments, s);
+    if (G <= 8)
+        return adj_group_as<8>(probs, blks, teval, n_teval, tmom, n_tmom, lmax, ntop_max, threads, w2, r2, g_s,
+                               g_stride, G, mom, mom_stride, c_s, c_stride, moments, s);
+    return adj_group_as<16>(probs, blks, teval, n_teval, tmom, n_tmom, lmax, ntop_max, threads, w2, r2, g_s,
+                            g_stride, G, mom, mom_stride, c_s, c_stride, moments, s);
 }
 
 }  // namespace nuht

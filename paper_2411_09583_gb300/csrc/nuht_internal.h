@@ -203,12 +203,18 @@ size_t radix_sort_scratch_bytes(int64_t n);
 
 cudaError_t launch_staircase(const double* r, int64_t n, const double* w, int64_t m, double z,
                              int32_t* s_out, cudaStream_t s);
-// Algorithm 1 on the device (one CTA): lists out[0..ocap) local,
-// out[ocap..2 ocap) asymptotic, out[2 ocap..3 ocap) direct; res = {counts, overflow}.
+// Algorithm 1 on the device: lists out[0..ocap) local, out[ocap..2 ocap)
+// asymptotic, out[2 ocap..3 ocap) direct; res = {counts, overflow}.  With
+// grid_ctas > 1 (subdivide_grid_ctas(): one per SM where cooperative launches
+// work, else 0) a cooperative launch of that many CTAs (scratch ctot[grid_ctas],
+// gst[8]); otherwise, or if that launch is refused, one CTA.  The lists are the
+// same either way.
+constexpr int kSubGridMax = 1024;
+int subdivide_grid_ctas();
 cudaError_t launch_subdivide(const int32_t* stair, const double* r_s, const double* w_s, const ProbParams* probs,
                              int nprob, int64_t min_size,
                              int n_cand, SubBlk* qa, SubBlk* qb, int64_t qcap, SubBlk* out, int64_t ocap,
-                             int64_t* res, cudaStream_t s);
+                             int64_t* res, int4* ctot, int64_t* gst, int grid_ctas, cudaStream_t s);
 cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int64_t* res, const ProbParams* probs,
                                 const double* r_s, const double* w_s, double* bl, double4* ba, cudaStream_t s);
 cudaError_t launch_staircase_many(const double* r, const double* w, int64_t m, const ProbParams* probs,
@@ -262,9 +268,10 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
                           const double* c_sb, const float2* c2b, double* g_sb, int det, cudaStream_t s);
 // Vector groups: G <= kGroupMax real components applied together (their
 // data at v times c_stride / mom_stride / g_stride from the first's).
-// local_group_fits: the group moment kernel's outputs ((lmax + 1) G) fit its CTA.
+// local_group_fits: the group moment kernel's outputs ((lmax + 1) G) fit its
+// CTA, and both group kernels' shared memory stays within 200 KB.
 constexpr int kGroupMax = NUHT_MAX_VEC_GROUP;
-int local_group_fits(int lmax, int G);
+int local_group_fits(int lmax, int ntop_max, int eval_threads, int G);
 cudaError_t launch_local_moments_group(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                        int ntiles, int lmax, const float2* r2, const float2* c2,
                                        int64_t c_stride, int G, double* mom, int64_t mom_stride, cudaStream_t s);
@@ -276,6 +283,15 @@ cudaError_t launch_direct_group(const ProbParams* probs, const DirectBlock* blks
                                 const float2* c2, int64_t c_stride, int G, double* g_s, int64_t g_stride,
                                 cudaStream_t s);
 int local_adj_threads(int ntop_max);
+// Adjoint local blocks for a group of G components (g_s + v g_stride, moments
+// mom + v mom_stride, sums into c_s + v c_stride): moments (row tiles teval,
+// threads from local_adj_group_threads) or evaluation (column tiles tmom).
+int local_adj_group_threads(int ntop_max);
+cudaError_t launch_local_adj_group(const ProbParams* probs, const LocalBlock* blks, const Tile* teval, int n_teval,
+                                   const Tile* tmom, int n_tmom, int lmax, int ntop_max, int threads,
+                                   const float2* w2, const float2* r2, const double* g_s, int64_t g_stride, int G,
+                                   double* mom, int64_t mom_stride, double* c_s, int64_t c_stride, bool moments,
+                                   cudaStream_t s);
 // g_sb / momb (both null, or both set): a second real component's g and
 // moments, summed with the same Bessel values.
 cudaError_t launch_local_adj_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
@@ -293,36 +309,50 @@ cudaError_t launch_split_f64(const double* x, int64_t n, float2* out, cudaStream
 // Per spreading tile, the path of k_asy_spread (plan time; modes[ntiles]).
 cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles, int ntiles,
                                 Tables tab, const double* r_s, int32_t* modes, cudaStream_t s);
+// members: real components spread by one launch (coefficients c2 + v c_stride,
+// grids grid_b + v gb_stride); 1 in the deterministic mode.
 cudaError_t launch_asy_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               const int32_t* modes, int ntiles, int qmax, int nt, Tables tab, const double* r_s,
-                              const float2* r2, const float2* c2, double2* grid_b, int det, cudaStream_t s);
+                              const float2* r2, const float2* c2, int64_t c_stride, int members,
+                              double2* grid_b, int64_t gb_stride, int det, cudaStream_t s);
+// members as in launch_asy_spread (inputs g_s + v g_stride, grids tgrid + v tg_stride)
 cudaError_t launch_asy_adj_spread(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, int nt, Tables tab, const double* w_s, const double* g_s,
-                                  double2* tgrid, cudaStream_t s);
+                                  int64_t g_stride, int members, double2* tgrid, int64_t tg_stride,
+                                  cudaStream_t s);
+// members as in launch_asy_interp (modes bgrid + v bg_stride, sums into c_s + v c_stride)
 cudaError_t launch_asy_adj_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, Tables tab, const double* r_s, const float4* bgrid,
-                                  double* c_s, cudaStream_t s);
+                                  int64_t bg_stride, int members, double* c_s, int64_t c_stride, cudaStream_t s);
 cudaError_t launch_asy_spread_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   const int32_t* modes, int ntiles, int qmax, int nt, Tables tab,
-                                  const double* r_s, const float2* r2, const float2* c2, double2* grid_b,
-                                  cudaStream_t s);
+                                  const double* r_s, const float2* r2, const float2* c2, int64_t c_stride,
+                                  int members, double2* grid_b, int64_t gb_stride, cudaStream_t s);
 cudaError_t launch_asy_interp_f32(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                                   int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
-                                  const float4* grid_q, double* g_s, cudaStream_t s);
+                                  const float4* grid_q, int64_t gq_stride, int members, double* g_s,
+                                  int64_t g_stride, cudaStream_t s);
 // lowp: FP32 butterflies on the FP32 parts of the values (mixed precision).
+// members: a batch of real components (grids src + v src_stride -> dst + v
+// dst_stride) in one launch.
 cudaError_t launch_asy_fft_small(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_nf2, Tables tab, const double2* src,
-                                 float4* dst, cudaStream_t s, bool adj = false, bool lowp = false);
+                                 float4* dst, cudaStream_t s, bool adj = false, bool lowp = false,
+                                 int members = 1, int64_t src_stride = 0, int64_t dst_stride = 0);
 // max_pts: the largest nf2 * Q among the blocks of the list (sizes the CTA).
 cudaError_t launch_asy_fft_block(const ProbParams* probs, const AsyBlock* blks, const Tile* items,
                                  int nitems, int max_pts, Tables tab, const double2* src, float4* dst,
-                                 cudaStream_t s, bool adj = false, bool lowp = false);
+                                 cudaStream_t s, bool adj = false, bool lowp = false, int members = 1,
+                                 int64_t src_stride = 0, int64_t dst_stride = 0);
 cudaError_t launch_asy_fft_large(const ProbParams* probs, const AsyBlock* blks, const Tile* items_a,
                                  int nitems_a, const Tile* items_b, int nitems_b, Tables tab,
                                  const double2* src, float4* tmp, float4* dst,
                                  cudaStream_t s, bool adj = false, bool lowp = false);
+// members: real components interpolated by one launch (FFT outputs grid_q + v
+// gq_stride, sums into g_s + v g_stride).
 cudaError_t launch_asy_interp(const ProbParams* probs, const AsyBlock* blks, const Tile* tiles,
                               int ntiles, int qmax, int nt, Tables tab, const double* w_s, const float2* w2,
-                              const float4* grid_q, double* g_s, cudaStream_t s);
+                              const float4* grid_q, int64_t gq_stride, int members, double* g_s,
+                              int64_t g_stride, cudaStream_t s);
 
 }  // namespace nuht

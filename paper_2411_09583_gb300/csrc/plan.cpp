@@ -132,6 +132,9 @@ struct nuht_plan_s {
     int max_fblock_pts = 0;   // largest nf2 * Q among the blocks FFT'd whole by one CTA
     int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, max_dir_area = 0, ntop_max = 0, eval_threads = 0;
     int spread_threads = 256;
+    // real components per asymptotic launch (forward spreading and
+    // interpolation, FP64 path): grids for that many are allocated
+    int asy_members = 1;
     int interp_threads = kInterpTileMax;   // frequencies per interpolation tile (one thread each)
     bool has_large_fft = false;
     Tables tab{};
@@ -149,6 +152,8 @@ struct nuht_plan_s {
 // pair), and the copies of the per-component arrays the plan holds.
 static int group_size(const nuht_plan_s* P) { return P->opt.vec_group ? P->opt.vec_group : 2; }
 static int group_copies(const nuht_plan_s* P) { return group_size(P) > 2 ? group_size(P) : 2; }
+// Device memory the grids of the extra members of an asymptotic launch may take.
+constexpr size_t kAsyMemberBytes = (size_t)1 << 30;
 
 namespace nuht {
 
@@ -593,6 +598,8 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     size_t o_out = sa.reserve<SubBlk>(3 * ocap);
     size_t o_bl = sa.reserve<double>(ocap), o_ba = sa.reserve<double4>(ocap);
     size_t o_res = sa.reserve<int64_t>(4);
+    const int sub_ctas = subdivide_grid_ctas();
+    size_t o_ctot = sa.reserve<int4>(sub_ctas > 0 ? (size_t)sub_ctas : 1), o_gst = sa.reserve<int64_t>(8);
     BuildTemps bt = reserve_build_temps(sa, ocap);
     size_t o_scr = sa.size;
     const size_t scr = radix_sort_scratch_bytes(n), scr_w = radix_sort_scratch_bytes(m);
@@ -672,8 +679,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     int64_t* d_res = (int64_t*)(sort_mem + o_res);
     double* d_bl = (double*)(sort_mem + o_bl);
     double4* d_ba = (double4*)(sort_mem + o_ba);
-    NUHT_CK(launch_subdivide(stair, r_s, w_s, d_prb, nprob, P->opt.min_size, P->opt.n_split_cand, (SubBlk*)(sort_mem + o_qa),
-                             (SubBlk*)(sort_mem + o_qb), qcap, d_out, ocap, d_res, s));
+    NUHT_CK(launch_subdivide(stair, r_s, w_s, d_prb, nprob, P->opt.min_size, P->opt.n_split_cand,
+                             (SubBlk*)(sort_mem + o_qa), (SubBlk*)(sort_mem + o_qb), qcap, d_out, ocap, d_res,
+                             (int4*)(sort_mem + o_ctot), (int64_t*)(sort_mem + o_gst), sub_ctas, s));
     NUHT_CK(launch_block_bounds(d_out, d_out + ocap, d_res, d_prb, r_s, w_s, d_bl, d_ba, s));
     P->eval_threads = local_eval_threads(P->ntop_max);
     const int sp_tile = P->opt.spread_tile ? P->opt.spread_tile : spread_tile_points(P->qmax);
@@ -840,13 +848,24 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     // sorted coefficients, moments and sorted outputs
     const size_t gcopies = (size_t)group_copies(P);
     size_t a_mom = A.reserve<double>(gcopies * (size_t)P->mom_len);
-    size_t a_gb = A.reserve<double2>((size_t)P->gb_len);
-    size_t a_gq = A.reserve<float4>((size_t)P->gq_len);
+    // Members of one asymptotic launch: up to a group's components share each
+    // point's and frequency's cell, basis and phase in the FP64 spreading and
+    // interpolation kernels, given their own spreading grid and FFT output,
+    // as long as the extra grids stay within kAsyMemberBytes.
+    {
+        const size_t per = sizeof(double2) * (size_t)P->gb_len + sizeof(float4) * (size_t)P->gq_len;
+        int am = P->opt.deterministic ? 1 : group_size(P);
+        while (am > 1 && (size_t)(am - 1) * per > kAsyMemberBytes) --am;
+        P->asy_members = am;
+    }
+    size_t a_gb = A.reserve<double2>((size_t)P->asy_members * (size_t)P->gb_len);
+    size_t a_gq = A.reserve<float4>((size_t)P->asy_members * (size_t)P->gq_len);
     size_t a_gt = A.reserve<float4>(P->has_large_fft ? (size_t)P->gq_len : 1);
     size_t a_cs = A.reserve<double>(gcopies * (size_t)n), a_gs = A.reserve<double>(gcopies * (size_t)m);
     size_t a_r2 = A.reserve<float2>(n), a_w2 = A.reserve<float2>(m);
     size_t a_cs2 = A.reserve<float2>(gcopies * (size_t)n);
-    size_t a_tg = A.reserve<double2>((size_t)P->gq_len), a_bq = A.reserve<float4>((size_t)P->gb_len);
+    size_t a_tg = A.reserve<double2>((size_t)P->asy_members * (size_t)P->gq_len);
+    size_t a_bq = A.reserve<float4>((size_t)P->asy_members * (size_t)P->gb_len);
     size_t a_sm = A.reserve<int32_t>((size_t)ntile[LIST_SPREAD]);
     const bool det = P->opt.deterministic != 0;
     const size_t f1 = 1;
@@ -1261,6 +1280,9 @@ static int apply_forward(nuht_plan_t P, int c0, int ng, cudaStream_t s)
         NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
                                      P->d_cs2, mom_acc, ls));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
+        // a pair's second moments by a second launch: the group kernel at G = 2
+        // was measured slower on the complex n = m = 4e6 workload (5.68 against
+        // 5.38 ms per execute)
         double* momb = ng == 2 ? P->d_momb : nullptr;
         if (momb) {
             NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
@@ -1290,38 +1312,48 @@ static int apply_forward(nuht_plan_t P, int c0, int ng, cudaStream_t s)
                                   gsb ? P->d_cs2b : nullptr, gsb, P->det ? 1 : 0, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
-    for (int v = 0; asy && v < ng; ++v) {
-        StageTimer Tv{P, c0 + v};
-        const float2* c2 = member_c2(P, v);
-        double* gv = member_g_acc(P, v);
+    // the asymptotic pipeline, asy_members components per spreading and
+    // interpolation launch (their FFTs one after the other)
+    const bool lowp = P->opt.precision == NUHT_PREC_MIXED;   // FP32 kernels and butterflies
+    const int am = P->asy_members;
+    for (int v0 = 0; asy && v0 < ng; v0 += am) {
+        const int nv = ng - v0 < am ? ng - v0 : am;
+        StageTimer Tv{P, c0 + v0};
+        const float2* c2 = member_c2(P, v0);
+        double* gv = member_g_acc(P, v0);
         NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_SPREAD, as));
-        NUHT_CK(cudaMemsetAsync(gb_acc, 0, acc_bytes(P, 2 * P->gb_len), as));
-        if (P->opt.precision == NUHT_PREC_MIXED)
+        NUHT_CK(cudaMemsetAsync(gb_acc, 0, acc_bytes(P, 2 * P->gb_len * nv), as));
+        if (lowp)
             NUHT_CK(launch_asy_spread_f32(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                          P->spread_threads, P->tab, P->d_r, P->d_r2, c2, gb_acc, as));
+                                          P->spread_threads, P->tab, P->d_r, P->d_r2, c2, P->n, nv, gb_acc,
+                                          P->gb_len, as));
         else
             NUHT_CK(launch_asy_spread(P->d_prob, P->d_asy, P->d_tspread, P->d_smode, P->n_tspread, P->qmax,
-                                      P->spread_threads, P->tab, P->d_r, P->d_r2, c2, gb_acc,
-                                      P->det ? 1 : 0, as));
+                                      P->spread_threads, P->tab, P->d_r, P->d_r2, c2, P->n, nv, gb_acc,
+                                      P->gb_len, P->det ? 1 : 0, as));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_gb, (double*)P->d_gb, 2 * P->gb_len, P->d_prob, as));
         NUHT_TRY(Tv.end(NUHT_STAGE_ASY_SPREAD, as));
         NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_FFT, as));
-        const bool lowp = P->opt.precision == NUHT_PREC_MIXED;   // FP32 butterflies
+        // the members' FFTs of whole blocks in one launch each; the two-pass
+        // FFTs of large blocks per member (one temporary)
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->max_fblock_pts, P->tab,
-                                     P->d_gb, P->d_gq, as, false, lowp));
+                                     P->d_gb, P->d_gq, as, false, lowp, nv, P->gb_len, P->gq_len));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small,
-                                     P->tab, P->d_gb, P->d_gq, as, false, lowp));
-        if (P->has_large_fft)
+                                     P->tab, P->d_gb, P->d_gq, as, false, lowp, nv, P->gb_len, P->gq_len));
+        for (int u = 0; P->has_large_fft && u < nv; ++u)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
-                                         P->d_gb, P->d_gtmp, P->d_gq, as, false, lowp));
+                                         P->d_gb + (int64_t)u * P->gb_len, P->d_gtmp,
+                                         P->d_gq + (int64_t)u * P->gq_len, as, false, lowp));
         NUHT_TRY(Tv.end(NUHT_STAGE_ASY_FFT, as));
         NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_INTERP, as));
-        if (P->opt.precision == NUHT_PREC_MIXED)
+        if (lowp)
             NUHT_CK(launch_asy_interp_f32(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax,
-                                          P->interp_threads, P->tab, P->d_w, P->d_w2, P->d_gq, gv, as));
+                                          P->interp_threads, P->tab, P->d_w, P->d_w2, P->d_gq, P->gq_len, nv,
+                                          gv, P->m, as));
         else
             NUHT_CK(launch_asy_interp(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax,
-                                      P->interp_threads, P->tab, P->d_w, P->d_w2, P->d_gq, gv, as));
+                                      P->interp_threads, P->tab, P->d_w, P->d_w2, P->d_gq, P->gq_len, nv, gv,
+                                      P->m, as));
         NUHT_TRY(Tv.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
@@ -1340,7 +1372,8 @@ static int drive_forward(nuht_plan_t P, int comps, cudaStream_t s, Gather&& gath
     NUHT_TRY(ensure_events(P, comps));
     const bool share = ((P->opt.class_mask & 4) && P->n_dir > 0) || ((P->opt.class_mask & 1) && P->n_loc > 0);
     int G = share ? group_size(P) : 1;
-    if (G > 2 && !local_group_fits(P->lmax, G)) G = 2;   // the moments' outputs would not fit one CTA
+    // groups whose moment outputs or shared memory would not fit one CTA: pairs
+    if (G > 2 && !local_group_fits(P->lmax, P->ntop_max, P->eval_threads, G)) G = 2;
     for (int c0 = 0; c0 < comps; c0 += G) {
         const int ng = comps - c0 < G ? comps - c0 : G;
         StageTimer T{P, c0};
@@ -1382,112 +1415,146 @@ int nuht_execute(nuht_plan_t P, const double* c, double* g, int nvec, int is_com
         [&](int cp, const double* src) { return launch_scatter(src, P->d_pw, P->m, comps, cp, P->d_mx, g, s); });
 }
 
-// Transpose of apply_forward: g (sorted, d_gs) -> c (sorted, d_cs).  Each
+// The accumulation target of member v's adjoint sums (d_cs + v n, or f_cs /
+// f_csb in the deterministic mode, where groups are pairs).
+static double* member_c_acc(nuht_plan_t P, int v)
+{
+    if (P->det) return (double*)(v == 0 ? P->f_cs : P->f_csb);
+    return member_c(P, v);
+}
+
+// Transpose of apply_forward for the ng real components c0 .. c0 + ng - 1 of
+// a group: sorted g of member v in member_g -> sorted c in member_c.  Each
 // block class runs its transposed pipeline; column contributions of blocks at
-// different levels meet in c with FP64 atomics.  pair as in apply_forward,
-// for the local blocks only (d_gsb into d_csb); the direct blocks run per
-// component.
-static int apply_adjoint(nuht_plan_t P, StageTimer& T, cudaStream_t s, int pair)
+// different levels meet in c with FP64 atomics.  The local blocks take a
+// group of more than two members in the group kernels (one Miller sweep per
+// row and one basis per point for all), else pairs (one Miller sweep per row
+// for both); the direct blocks run per member; the asymptotic pipeline takes
+// asy_members members per spreading and interpolation launch.
+static int apply_adjoint(nuht_plan_t P, int c0, int ng, bool pairs, cudaStream_t s)
 {
     const int mask = P->opt.class_mask;
-    double* cs = acc_target(P, P->d_cs, P->f_cs);
-    double* csb = acc_target(P, P->d_csb, P->f_csb);
-    double* mom_acc = acc_target(P, P->d_mom, P->f_mom);
-    double* momb_acc = acc_target(P, P->d_momb, P->f_momb);
-    double2* tg_acc = (double2*)acc_target(P, (double*)P->d_tg, P->f_tg);
-    const bool loc = (mask & 1) && P->n_loc && pair != 2, dir = (mask & 4) && P->n_dir;
+    StageTimer T{P, c0};
+    const bool loc = (mask & 1) && P->n_loc, dir = (mask & 4) && P->n_dir;
     const bool asy = (mask & 2) && P->n_asy;
     // local and direct blocks beside the asymptotic pipeline, as in apply_forward
     ClassFork fk;
     if (P->opt.timing != NUHT_TIMING_SERIAL && asy && (loc || dir)) NUHT_CK(fk.open(s));
     const cudaStream_t ls = fk.local(s), as = fk.asy(s);
     if (loc) {
+        // member v's adjoint moments in d_mom + v mom_len (f_mom / f_momb in the
+        // deterministic mode, decoded there)
         const int thr = local_adj_threads(P->ntop_max);
+        auto mom_of = [&](int v) { return P->d_mom + (int64_t)v * P->mom_len; };
+        auto mom_acc = [&](int v) { return P->det ? (double*)(v == 0 ? P->f_mom : P->f_momb) : mom_of(v); };
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
-        NUHT_CK(cudaMemsetAsync(mom_acc, 0, acc_bytes(P, P->mom_len), ls));
-        double* momb = pair == 1 ? P->d_momb : nullptr;
-        if (momb) NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
-        NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, thr,
-                                         P->d_w2, P->d_gs, mom_acc, momb ? P->d_gsb : nullptr,
-                                         momb ? momb_acc : nullptr, ls));
-        if (P->det) {
-            NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
-            if (momb) NUHT_CK(launch_fx_decode(P->f_momb, P->d_momb, P->mom_len, P->d_prob, ls));
+        if (ng > 2) {
+            // a group: one Miller sweep per row and one basis per point for all members
+            NUHT_CK(cudaMemsetAsync(P->d_mom, 0, sizeof(double) * P->mom_len * ng, ls));
+            NUHT_CK(launch_local_adj_group(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->d_tmom, P->n_tmom,
+                                           P->lmax, P->ntop_max, local_adj_group_threads(P->ntop_max), P->d_w2,
+                                           P->d_r2, P->d_gs, P->m, ng, P->d_mom, P->mom_len, P->d_cs, P->n, true,
+                                           ls));
+            NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
+            NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
+            NUHT_CK(launch_local_adj_group(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->d_tmom, P->n_tmom,
+                                           P->lmax, P->ntop_max, 0, P->d_w2, P->d_r2, P->d_gs, P->m, ng, P->d_mom,
+                                           P->mom_len, P->d_cs, P->n, false, ls));
+            NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
         }
-        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
-        NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
-        NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, P->d_mom,
-                                      cs, ls));
-        if (momb)
-            NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2, momb,
-                                          csb, ls));
-        NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
+        for (int v = 0; ng <= 2 && v < ng; v += pairs ? 2 : 1) {
+            const bool two = pairs && v + 1 < ng;
+            NUHT_CK(cudaMemsetAsync(mom_acc(v), 0, acc_bytes(P, P->mom_len * (two && !P->det ? 2 : 1)), ls));
+            if (two && P->det) NUHT_CK(cudaMemsetAsync(mom_acc(v + 1), 0, acc_bytes(P, P->mom_len), ls));
+            NUHT_CK(launch_local_adj_moments(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max, thr,
+                                             P->d_w2, member_g(P, v), mom_acc(v),
+                                             two ? member_g(P, v + 1) : nullptr, two ? mom_acc(v + 1) : nullptr,
+                                             ls));
+            if (P->det) {
+                NUHT_CK(launch_fx_decode(P->f_mom, mom_of(0), P->mom_len, P->d_prob, ls));
+                if (two) NUHT_CK(launch_fx_decode(P->f_momb, mom_of(1), P->mom_len, P->d_prob, ls));
+            }
+        }
+        if (ng <= 2) {
+            NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
+            NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
+            for (int v = 0; v < ng; ++v)
+                NUHT_CK(launch_local_adj_eval(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
+                                              mom_of(v), member_c_acc(P, v), ls));
+            NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
+        }
     }
     if (dir) {
         NUHT_TRY(T.begin(NUHT_STAGE_DIRECT, ls));
-        NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->max_dir_area,
-                                  P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_r2, P->d_w2, P->d_gs, cs,
-                                  P->det ? 1 : 0, ls));
+        for (int v = 0; v < ng; ++v)
+            NUHT_CK(launch_direct_adj(P->d_prob, P->d_dir, P->n_dir, P->max_dir_cols, P->max_dir_area,
+                                      P->eps >= 1e-6 ? 1 : 0, P->d_r, P->d_w, P->d_r2, P->d_w2, member_g(P, v),
+                                      member_c_acc(P, v), P->det ? 1 : 0, ls));
         NUHT_TRY(T.end(NUHT_STAGE_DIRECT, ls));
     }
-    if (asy) {
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_SPREAD, as));
-        NUHT_CK(cudaMemsetAsync(tg_acc, 0, acc_bytes(P, 2 * P->gq_len), as));
+    double2* tg_acc = (double2*)acc_target(P, (double*)P->d_tg, P->f_tg);
+    const int am = P->asy_members;
+    for (int v0 = 0; asy && v0 < ng; v0 += am) {
+        const int nv = ng - v0 < am ? ng - v0 : am;
+        StageTimer Tv{P, c0 + v0};
+        NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_CK(cudaMemsetAsync(tg_acc, 0, acc_bytes(P, 2 * P->gq_len * nv), as));
         NUHT_CK(launch_asy_adj_spread(P->d_prob, P->d_asy, P->d_tinterp, P->n_tinterp, P->qmax, P->interp_threads,
-                                      P->tab, P->d_w,
-                                      P->d_gs, tg_acc, as));
+                                      P->tab, P->d_w, member_g(P, v0), P->m, nv, tg_acc, P->gq_len, as));
         if (P->det) NUHT_CK(launch_fx_decode(P->f_tg, (double*)P->d_tg, 2 * P->gq_len, P->d_prob, as));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_SPREAD, as));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_FFT, as));
+        NUHT_TRY(Tv.end(NUHT_STAGE_ASY_SPREAD, as));
+        NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_FFT, as));
         NUHT_CK(launch_asy_fft_block(P->d_prob, P->d_asy, P->d_fblock, P->n_fblock, P->max_fblock_pts, P->tab,
-                                     P->d_tg, P->d_bq, as, true));
+                                     P->d_tg, P->d_bq, as, true, false, nv, P->gq_len, P->gb_len));
         NUHT_CK(launch_asy_fft_small(P->d_prob, P->d_asy, P->d_fsmall, P->n_fsmall, P->max_nf2_small, P->tab,
-                                     P->d_tg, P->d_bq, as, true));
-        if (P->has_large_fft)
+                                     P->d_tg, P->d_bq, as, true, false, nv, P->gq_len, P->gb_len));
+        for (int u = 0; P->has_large_fft && u < nv; ++u)
             NUHT_CK(launch_asy_fft_large(P->d_prob, P->d_asy, P->d_fa, P->n_fa, P->d_fb, P->n_fb, P->tab,
-                                         P->d_tg, P->d_gtmp, P->d_bq, as, true));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_FFT, as));
-        NUHT_TRY(T.begin(NUHT_STAGE_ASY_INTERP, as));
+                                         P->d_tg + (int64_t)u * P->gq_len, P->d_gtmp,
+                                         P->d_bq + (int64_t)u * P->gb_len, as, true));
+        NUHT_TRY(Tv.end(NUHT_STAGE_ASY_FFT, as));
+        NUHT_TRY(Tv.begin(NUHT_STAGE_ASY_INTERP, as));
         NUHT_CK(launch_asy_adj_interp(P->d_prob, P->d_asy, P->d_tspread, P->n_tspread, P->qmax, P->tab, P->d_r,
-                                      P->d_bq, cs, as));
-        NUHT_TRY(T.end(NUHT_STAGE_ASY_INTERP, as));
+                                      P->d_bq, P->gb_len, nv, member_c_acc(P, v0), P->n, as));
+        NUHT_TRY(Tv.end(NUHT_STAGE_ASY_INTERP, as));
     }
     NUHT_CK(fk.close());
     return NUHT_OK;
 }
 
-// The component loop of an adjoint transform (drive_forward transposed):
-// gather(comp, gs) writes the sorted, scaled input, apply_adjoint adds every
-// block class into c (sorted), scatter(comp) writes it out.  Pairs share the
-// local blocks' Bessel evaluations: the first sums both components' moments,
-// the second starts from its local sums (d_csb).
+// The component loop of an adjoint transform (drive_forward transposed), in
+// groups as in drive_forward: gather(comp, g) writes a component's sorted,
+// scaled input into its member's array, apply_adjoint adds every block class
+// into the members' sums, scatter(comp, c) writes a member's sums out.
 extern "C++" {
 template <class Gather, class Scatter>
 static int drive_adjoint(nuht_plan_t P, int comps, cudaStream_t s, Gather&& gather, Scatter&& scatter)
 {
     NUHT_TRY(ensure_events(P, comps));
-    double* cs = acc_target(P, P->d_cs, P->f_cs);
-    double* csb = acc_target(P, P->d_csb, P->f_csb);
-    const bool pairs = (P->opt.class_mask & 1) && P->n_loc > 0 && group_size(P) != 1;
-    for (int comp = 0; comp < comps; ++comp) {
-        StageTimer T{P, comp};
-        const int pair = !pairs ? 0 : (comp & 1) ? 2 : (comp + 1 < comps ? 1 : 0);
+    const bool share = (P->opt.class_mask & 1) && P->n_loc > 0;
+    const bool pairs = share && group_size(P) != 1;
+    // members per group: the group size when there are asymptotic launches to
+    // share, else a pair of the local blocks
+    int G = group_size(P);
+    if (G > 2 && !local_group_fits(P->lmax, P->ntop_max, P->eval_threads, G)) G = 2;
+    if (!pairs && !(P->n_asy && (P->opt.class_mask & 2))) G = 1;
+    for (int c0 = 0; c0 < comps; c0 += G) {
+        const int ng = comps - c0 < G ? comps - c0 : G;
+        StageTimer T{P, c0};
         NUHT_TRY(T.begin(NUHT_STAGE_GATHER, s));
-        if (pair == 2)
-            NUHT_CK(cudaMemcpyAsync(cs, csb, acc_bytes(P, P->n), cudaMemcpyDeviceToDevice, s));
-        else
-            NUHT_CK(cudaMemsetAsync(cs, 0, acc_bytes(P, P->n), s));
-        NUHT_CK(gather(comp, P->d_gs));
-        if (pair == 1) {
-            NUHT_CK(cudaMemsetAsync(csb, 0, acc_bytes(P, P->n), s));
-            NUHT_CK(gather(comp + 1, P->d_gsb));
+        for (int v = 0; v < ng; ++v) {
+            NUHT_CK(cudaMemsetAsync(member_c_acc(P, v), 0, acc_bytes(P, P->n), s));
+            NUHT_CK(gather(c0 + v, member_g(P, v)));
         }
         NUHT_TRY(T.end(NUHT_STAGE_GATHER, s));
-        NUHT_TRY(apply_adjoint(P, T, s, pair));
-        NUHT_TRY(T.begin(NUHT_STAGE_SCATTER, s));
-        if (P->det) NUHT_CK(launch_fx_decode(P->f_cs, P->d_cs, P->n, P->d_prob, s));
-        NUHT_CK(scatter(comp));
-        NUHT_TRY(T.end(NUHT_STAGE_SCATTER, s));
+        NUHT_TRY(apply_adjoint(P, c0, ng, pairs, s));
+        for (int v = 0; v < ng; ++v) {
+            StageTimer Tv{P, c0 + v};
+            NUHT_TRY(Tv.begin(NUHT_STAGE_SCATTER, s));
+            if (P->det) NUHT_CK(launch_fx_decode(member_c_acc(P, v), member_c(P, v), P->n, P->d_prob, s));
+            NUHT_CK(scatter(c0 + v, member_c(P, v)));
+            NUHT_TRY(Tv.end(NUHT_STAGE_SCATTER, s));
+        }
     }
     return NUHT_OK;
 }
@@ -1509,7 +1576,7 @@ int nuht_adjoint(nuht_plan_t P, const double* g, double* c, int nvec, int is_com
     return drive_adjoint(
         P, comps, s,
         [&](int cp, double* o) { return launch_gather(g, P->d_pw, P->m, comps, cp, P->d_mx, o, nullptr, s); },
-        [&](int cp) { return launch_scatter(P->d_cs, P->d_pr, P->n, comps, cp, P->d_mx, c, s); });
+        [&](int cp, const double* src) { return launch_scatter(src, P->d_pr, P->n, comps, cp, P->d_mx, c, s); });
 }
 
 int nuht_plan_deriv(nuht_plan_t* out, nuht_plan_t base, void* stream)
@@ -1582,7 +1649,9 @@ int nuht_grad_r(nuht_plan_t D, const double* c, const double* e, double* grad_r,
     return drive_adjoint(
         D, nvec, s,
         [&](int cp, double* o) { return launch_gather_deriv(e, D->d_pw, D->d_w, mb, nvec, cp, D->d_mx, o, nullptr, s); },
-        [&](int cp) { return launch_scatter_deriv(D->d_cs, D->d_pr, nb, nvec, cp, D->d_mx, c, grad_r, s); });
+        [&](int cp, const double* src) {
+            return launch_scatter_deriv(src, D->d_pr, nb, nvec, cp, D->d_mx, c, grad_r, s);
+        });
 }
 
 int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega, int64_t m, double eps,
@@ -1627,6 +1696,7 @@ int nuht_info(nuht_plan_t P, nuht_plan_info* out)
     out->L = P->probs[0].L;
     out->nufft_width = P->w;
     out->nufft_degree = P->tab.deg;
+    out->asy_members = P->asy_members;
     out->z = P->probs[0].z;
     out->eps = P->eps;
     out->n = P->n;

@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 from gpu_helpers import to_dev, tol  # noqa: E402
 
 
-@pytest.mark.parametrize("nu,nvec,group", [(0, 3, 0), (0, 5, 4), (1, 16, 16), (3, 7, 3), (2, 9, 8), (0, 2, 1)])
+@pytest.mark.parametrize("nu,nvec,group", [(0, 3, 0), (0, 5, 4), (1, 16, 16), (3, 7, 3), (2, 9, 8), (0, 2, 1),
+                                            (100, 6, 6)])
 def test_groups_forward_match_oracle(nu, nvec, group):
     # every row of a problem with all three block classes, each vector
     # against the oracle; groups of `group` with a ragged last group
@@ -27,7 +28,7 @@ def test_groups_forward_match_oracle(nu, nvec, group):
     C = np.random.default_rng(701 + nvec).standard_normal((r.size, nvec))
     with Plan(nu, to_dev(r), to_dev(omega), eps, vec_group=group) as p:
         info = p.info()
-        assert info["n_local"] > 0 and info["n_asy"] > 0 and info["n_direct"] > 0
+        assert info["n_local"] > 0 and (nu == 100 or (info["n_asy"] > 0 and info["n_direct"] > 0))
         G = p.execute(to_dev(C)).cpu().numpy()
     ref = oracle.direct(nu, r, omega, C)
     assert np.all(np.max(np.abs(G - ref), axis=0) <= tol(eps, C))
@@ -86,3 +87,31 @@ def test_group_batched_plan():
         Ci = C[ro[i]:ro[i + 1]]
         ref = oracle.direct(nu, rr, ww, Ci)
         assert np.all(np.max(np.abs(G[wo[i]:wo[i + 1]] - ref), axis=0) <= tol(eps, Ci)), i
+
+
+@pytest.mark.parametrize("nu,nvec,group,precision", [(0, 5, 4, "fp64"), (1, 16, 16, "fp64"), (3, 3, 0, "fp64"),
+                                                     (0, 6, 8, "mixed"), (2, 3, 1, "fp64")])
+def test_groups_adjoint_match_oracle(nu, nvec, group, precision):
+    # the adjoint with the same groups: asymptotic members share each
+    # frequency's and point's cell, basis and factors, the local blocks run
+    # in pairs; every column of every vector against the oracle's transposed sum
+    from paper_2411_09583_gb300 import Plan
+    eps = 1e-10 if precision == "fp64" else 1e-6
+    r, omega, _ = uniform_problem(2400, 2600, omega_max=3000.0, seed=740 + nu)
+    E = np.random.default_rng(741 + nvec).standard_normal((omega.size, nvec))
+    with Plan(nu, to_dev(r), to_dev(omega), eps, vec_group=group, precision=precision) as p:
+        info = p.info()
+        assert info["asy_members"] >= 1
+        A = p.adjoint(to_dev(E)).cpu().numpy()
+    ref = oracle.direct(nu, omega, r, E)
+    assert np.all(np.max(np.abs(A - ref), axis=0) <= tol(eps, E))
+
+
+def test_asy_members_from_group_size():
+    # a plan takes as many members per asymptotic launch as its group (grids
+    # permitting), one with groups of one or in the deterministic mode
+    from paper_2411_09583_gb300 import Plan
+    r, omega, _ = uniform_problem(3000, 3000, omega_max=4000.0, seed=750)
+    for opts, want in (({"vec_group": 8}, 8), ({}, 2), ({"vec_group": 1}, 1), ({"deterministic": True}, 1)):
+        with Plan(0, to_dev(r), to_dev(omega), 1e-9, **opts) as p:
+            assert p.info()["asy_members"] == want, opts

@@ -473,3 +473,28 @@ def test_checked_mode_and_plan_lists_pass_the_work_list_check(monkeypatch):
     bad = ranges.copy()
     bad[0, 3] += 1
     assert check_blocks(3, 1e-9, rs, ws, bad, cls, min_size=512) == N.NUHT_ERR_BAD_BLOCKS
+
+
+@pytest.mark.parametrize("nu,min_size", [(0, 256), (7, 1024)])
+def test_multi_cta_subdivision_matches_host_walk(monkeypatch, nu, min_size):
+    # n = m = 1e6: levels of the subdivision with thousands of mixed blocks,
+    # which the device splits over all SMs (cooperative launch); its lists must
+    # equal, entry for entry, the host walk's (forced by a tiny device list
+    # capacity), and pass the host check
+    from paper_2411_09583_gb300 import Plan
+    from paper_2411_09583_gb300 import _native as N
+    from paper_2411_09583_gb300.nuht import check_blocks
+    r, omega, _ = uniform_problem(1_000_000, 1_000_000, omega_max=1e5, seed=94 + nu)
+    dr, dw = to_dev(r), to_dev(omega)
+    with Plan(nu, dr, dw, 1e-10, min_size=min_size) as p:
+        dev_blocks = [p.blocks(k) for k in range(3)]
+    monkeypatch.setenv("NUHT_SUBDIVIDE_CAPACITY", "64")
+    with Plan(nu, dr, dw, 1e-10, min_size=min_size) as p:
+        host_blocks = [p.blocks(k) for k in range(3)]
+    monkeypatch.delenv("NUHT_SUBDIVIDE_CAPACITY")
+    assert sum(len(b) for b in dev_blocks) > 8000
+    for a, b in zip(dev_blocks, host_blocks):
+        assert np.array_equal(a, b)
+    ranges = np.concatenate(dev_blocks)
+    cls = np.concatenate([np.full(len(b), k, np.int32) for k, b in enumerate(dev_blocks)])
+    assert check_blocks(nu, 1e-10, np.sort(r), np.sort(omega), ranges, cls, min_size=min_size) == N.NUHT_OK
