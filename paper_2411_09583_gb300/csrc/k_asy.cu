@@ -2013,7 +2013,21 @@ __host__ __device__ __forceinline__ int f32_stride4(int n)
 
 // FP32 spreading, dense tile: the moment form of spread_moments in single
 // precision (each of the 8 partial sums of a moment covers at most
-// ceil(tile / 8) points).  Members (MULTI) as in spread_fold.
+// ceil(tile / 8) points).  The bins go in groups of up to kF32GroupBins: the
+// moment items of all the group's bins share one pass (and one barrier), and
+// each cell of the group's window then sums A[c - b] M_b over the group's bins
+// b that reach it (each bin's sum in FP32 as before, the bins' sums combined
+// with compensated additions) and adds it with one FP64 atomic.  Members
+// (MULTI) as in spread_fold.
+constexpr int kF32GroupBytes = 16384;
+
+__host__ __device__ __forceinline__ int f32_group_bins(int dpad, int Q2)
+{
+    int g = kF32GroupBytes / (int)(sizeof(float) * dpad * Q2);
+    if (g < 1) g = 1;
+    return g < kMaxTileBins ? g : kMaxTileBins;
+}
+
 template <bool MULTI>
 __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, const Tables& tab,
                                    const double* __restrict__ r_s, const float2* __restrict__ r2,
@@ -2025,10 +2039,11 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
     const int Q2 = 2 * Q;
     const int ndp = (nb + 1) >> 1, dpad = 2 * ndp, nq = Q2 >> 2;
     const int su = mom_stride(nb), sx = f32_stride4(Q2);
+    const int GB = f32_group_bins(dpad, Q2);
     float* U = sm;                               // [nt][su]
     float* X = U + nt * su;                      // [nt][sx]
-    float* Mb = X + nt * sx;                     // [dpad][Q2]
-    float* Ach = Mb + dpad * Q2;                 // [w][dpad]
+    float* Mb = X + nt * sx;                     // [GB][dpad][Q2]
+    float* Ach = Mb + GB * dpad * Q2;            // [w][dpad]
     int* l0s = (int*)(Ach + w * dpad);           // [nt]
     __shared__ int bstart[kMaxTileBins + 3];
     for (int i = tid; i < w * dpad; i += nt) {
@@ -2084,21 +2099,24 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
     __syncthreads();
     const int nf1 = 2 * B.N1 + 1;
     const int nitems = ndp * nq * kSpreadSub;
-    const int nitems_pad = (nitems + 31) & ~31;
     for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
     if (MULTI && vm > 0) {
         if (tid < cnt) put(vm);
         __syncthreads();
     }
     const Accum gv = gb.at(vm * moff);
-    for (int b = 0; b < nbins; ++b) {
-        const int p0 = bstart[b], p1 = bstart[b + 1];
-        if (p0 == p1) continue;
-        for (int it = tid; it < nitems_pad; it += nt) {
-            const bool live = it < nitems;
+    for (int g0 = 0; g0 < nbins; g0 += GB) {
+        const int gn = nbins - g0 < GB ? nbins - g0 : GB;
+        // (a) the moments of the group's bins: items (bin, degree pair, value quad, sub-range)
+        const int gitems = gn * nitems;
+        const int gitems_pad = (gitems + 31) & ~31;
+        for (int it = tid; it < gitems_pad; it += nt) {
+            const bool live = it < gitems;
             const int sub = it & (kSpreadSub - 1);
-            const int o = live ? it / kSpreadSub : 0;
+            const int ob = live ? it / kSpreadSub : 0;
+            const int bb = ob / (ndp * nq), o = ob - bb * (ndp * nq);
             const int dp = o / nq, qq = o - dp * nq;
+            const int p0 = bstart[g0 + bb], p1 = bstart[g0 + bb + 1];
             float A[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
             if (live) {
                 for (int p = p0 + sub; p < p1; p += kSpreadSub) {
@@ -2112,25 +2130,39 @@ __device__ void spread_moments_f32(const AsyBlock& B, int Q, const Tile& t, cons
                     }
                 }
             }
+            float* mb = Mb + bb * dpad * Q2;
 #pragma unroll
             for (int e = 0; e < 2; ++e)
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
-                    float a = A[e][f];
+                    float av = A[e][f];
 #pragma unroll
-                    for (int off = kSpreadSub >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-                    if (live && sub == 0) Mb[(2 * dp + e) * Q2 + 4 * qq + f] = a;
+                    for (int off = kSpreadSub >> 1; off > 0; off >>= 1) av += __shfl_xor_sync(0xffffffffu, av, off);
+                    if (live && sub == 0) mb[(2 * dp + e) * Q2 + 4 * qq + f] = av;
                 }
         }
         __syncthreads();
-        const int l0 = lfirst + b;
-        for (int o = tid; o < w * Q2; o += nt) {
-            const int i = o / Q2, qv = o - i * Q2;
-            const int idx = l0 + i + B.N1;
+        // (c) cell lfirst + g0 + c: sum over the group's bins b with 0 <= c - b < w
+        const int ncell = gn + w - 1;
+        for (int o = tid; o < ncell * Q2; o += nt) {
+            const int c = o / Q2, qv = o - c * Q2;
+            const int idx = lfirst + g0 + c + B.N1;
             if (idx < 0 || idx >= nf1) continue;
-            float sacc = 0.f;
-            for (int d = 0; d < nb; ++d) sacc = fmaf(Ach[i * dpad + d], Mb[d * Q2 + qv], sacc);
-            if (sacc != 0.f) gv.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), (double)sacc);
+            const int b_lo = c - w + 1 > 0 ? c - w + 1 : 0;
+            const int b_hi = c < gn - 1 ? c : gn - 1;
+            float ss = 0.f, sc = 0.f;
+            for (int bb = b_lo; bb <= b_hi; ++bb) {
+                const float* ar = Ach + (c - bb) * dpad;
+                const float* mb = Mb + bb * dpad * Q2 + qv;
+                float part = 0.f;
+                for (int d = 0; d < nb; ++d) part = fmaf(ar[d], mb[d * Q2], part);
+                float t, e;
+                two_sum(ss, part, t, e);
+                ss = t;
+                sc += e;
+            }
+            const float sacc = ss + sc;
+            if (sacc != 0.f) gv.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), (double)ss + (double)sc);
         }
         __syncthreads();
     }
@@ -2141,7 +2173,7 @@ __host__ __device__ __forceinline__ size_t spread_moments_f32_smem(int nt, int Q
 {
     const int dpad = 2 * ((nb + 1) >> 1);
     return sizeof(float) * ((size_t)nt * mom_stride(nb) + (size_t)nt * f32_stride4(2 * Q) +
-                            (size_t)dpad * 2 * Q + (size_t)w * dpad) +
+                            (size_t)f32_group_bins(dpad, 2 * Q) * dpad * 2 * Q + (size_t)w * dpad) +
            sizeof(int) * (size_t)nt;
 }
 

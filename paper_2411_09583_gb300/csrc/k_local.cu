@@ -214,23 +214,63 @@ __device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb
     return df_add(S, df_neg(jc));   // J_0 was added with weight 2; it counts once
 }
 
-// Small arguments (y < 1): J_0..J_ntop(y) directly from the power series
-// (DLMF 10.2.2) in FP64, stored as double-float; already normalised (returns 1).
-__device__ __forceinline__ double series_store_fp64(double y, int ntop, float2* jb, int nt, int tid)
+// 1 / k as double-float (k < 2^24, exact in FP32)
+__device__ __forceinline__ df df_inv_int(int k) { return df_recip(df{(float)k, 0.f}); }
+
+// J_n(x) for 0 <= x < 1 from the power series (DLMF 10.2.2) in double-float:
+// (x/2)^n / n! times sum_k (-x^2/4)^k n! / (k! (n+k)!), summed until a term
+// falls below 2^-53 of the sum (at most 9 terms: the ratio of consecutive
+// terms is at most 1/(4 k (n+k))).  FP32-pipe arithmetic only (FP64 runs at
+// 1/64 of the FP32 rate here); an (x/2)^n / n! below FP32's range gives 0,
+// far below any tolerance.
+// lead (x/2)^n / n! times the sum, q = -x^2/4
+__device__ __forceinline__ df jn_series_sum(int n, df lead, df q)
 {
-    const double h = 0.5 * y, q = -h * h;
-    double lead = 1.0;   // (y/2)^n / n!
-    for (int n = 0; n <= ntop; ++n) {
-        if (n > 0) lead *= h / (double)n;
-        double term = lead, sum = lead;
-        for (int k = 1; k <= 12; ++k) {
-            term *= q / ((double)k * (double)(n + k));
-            sum += term;
-        }
-        const float fh = (float)sum;
-        jb[n * nt + tid] = make_float2(fh, (float)(sum - (double)fh));
+    df term = lead, sum = lead;
+    for (int k = 1; k <= 9; ++k) {
+        term = df_mul(df_mul(term, q), df_inv_int(k * (n + k)));
+        sum = df_add(sum, term);
+        if (fabsf(term.h) <= 1.1102230246251565e-16f * fabsf(sum.h)) break;
     }
-    return 1.0;
+    return sum;
+}
+
+__device__ __forceinline__ df jn_series_df(int n, df x)
+{
+    const df h{0.5f * x.h, 0.5f * x.l};
+    df lead{1.f, 0.f};
+    for (int i = 1; i <= n && lead.h != 0.f; ++i) lead = df_mul(df_mul(lead, h), df_inv_int(i));
+    return jn_series_sum(n, lead, df_neg(df_mul(h, h)));
+}
+
+// The same series in FP32 (mixed precision): six terms reach 1e-9 relative.
+__device__ __forceinline__ float jn_series_f32(int n, float x)
+{
+    const float h = 0.5f * x;
+    float lead = 1.f;
+    for (int i = 1; i <= n && lead != 0.f; ++i) lead *= h / (float)i;
+    const float q = -h * h;
+    float term = lead, sum = lead;
+    for (int k = 1; k <= 6; ++k) {
+        term *= q / (float)(k * (n + k));
+        sum += term;
+    }
+    return sum;
+}
+
+// Small arguments (y < 1): J_0..J_ntop(y) directly from the power series, in
+// double-float; already normalised (returns 1).
+__device__ __forceinline__ df series_store_df(df y, int ntop, float2* jb, int nt, int tid)
+{
+    const df h{0.5f * y.h, 0.5f * y.l};
+    const df q = df_neg(df_mul(h, h));
+    df lead{1.f, 0.f};   // (y/2)^n / n!
+    for (int n = 0; n <= ntop; ++n) {
+        if (n > 0 && lead.h != 0.f) lead = df_mul(df_mul(lead, h), df_inv_int(n));
+        const df v = lead.h != 0.f ? jn_series_sum(n, lead, q) : df{0.f, 0.f};
+        jb[n * nt + tid] = make_float2(v.h, v.l);
+    }
+    return df{1.f, 0.f};
 }
 
 // One thread per row of a local block.  J_0..J_ntop(x/2) by Miller's backward
@@ -284,7 +324,7 @@ __device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ p
         if (ydf.h >= 1.f) {
             S = miller_store_df(ydf, ntop, ns, jb, nt, tid);
         } else {
-            S = df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+            S = series_store_df(ydf, ntop, jb, nt, tid);
         }
         // scale by a power of two near 1/S so that products of two values stay in FP32 range
         const float p2 = exp2f(-(float)ilogbf(S.h));
@@ -616,7 +656,7 @@ __device__ __forceinline__ double direct_entry(const ProbParams& P, double w, do
 {
     if (asy) return lowp ? (double)jn_hankel_f32(P, w, r) : jn_hankel_df(P, w, r);
     const double x = w * r;
-    if (x < 1.0) return jn_series(P.nu, x);
+    if (x < 1.0) return lowp ? (double)jn_series_f32(P.nu, (float)x) : df_to(jn_series_df(P.nu, df_from(x)));
     return lowp ? (double)jn_miller_f32(P.nu, (float)x) : jn_miller_df(P.nu, x);
 }
 
@@ -670,14 +710,15 @@ __device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, 
                                                   bool lowp)
 {
     const int s = F.fr + F.fw;
-    if (s < 64 || s > 127) return direct_entry(P, w, r, asy, lowp);
+    // the phase in turns needs s <= 127; x alone (local side) any s >= 64
+    if (s < 64 || (asy && s > 127)) return direct_entry(P, w, r, asy, lowp);
     const unsigned long long Om = (unsigned long long)fx_from_double(w, F.fw);
     const unsigned long long R = (unsigned long long)fx_from_double(r, F.fr);
     const unsigned long long Pl = Om * R, Ph = __umul64hi(Om, R);
     const df x = df_from_u128(Ph, Pl, s);
     if (asy) return lowp ? (double)jn_hankel_f32x(P, x.h, turns_u128(Ph, Pl, s))
                          : jn_hankel_dfx(P, x, turns_u128(Ph, Pl, s));
-    if (x.h < 1.f) return jn_series(P.nu, w * r);
+    if (x.h < 1.f) return lowp ? (double)jn_series_f32(P.nu, x.h) : df_to(jn_series_df(P.nu, x));
     return lowp ? (double)jn_miller_f32x(P.nu, x.h) : jn_miller_dfx(P.nu, x);
 }
 
@@ -685,13 +726,13 @@ __device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, 
 __device__ __forceinline__ float direct_entry_f32x(const ProbParams& P, DirFx F, double w, double r, bool asy)
 {
     const int s = F.fr + F.fw;
-    if (s < 64 || s > 127) return (float)direct_entry(P, w, r, asy, true);
+    if (s < 64 || (asy && s > 127)) return (float)direct_entry(P, w, r, asy, true);
     const unsigned long long Om = (unsigned long long)fx_from_double(w, F.fw);
     const unsigned long long R = (unsigned long long)fx_from_double(r, F.fr);
     const unsigned long long Pl = Om * R, Ph = __umul64hi(Om, R);
     const df x = df_from_u128(Ph, Pl, s);
     if (asy) return jn_hankel_f32x(P, x.h, turns_u128(Ph, Pl, s));
-    if (x.h < 1.f) return (float)jn_series(P.nu, w * r);
+    if (x.h < 1.f) return jn_series_f32(P.nu, x.h);
     return jn_miller_f32x(P.nu, x.h);
 }
 
@@ -752,8 +793,8 @@ __device__ __forceinline__ int direct_partition(const ProbParams& P, const Direc
 // entries, FP64 row sums.  mode 2: FP32 entries whose products with the FP32
 // parts of c accumulate in FP32 atomics, each row spread over S = kDirSlots
 // slots (fewer when S rows > kDirSlotFloats) by list position, the slots of a
-// row then added in FP64 (direct_sum_mode picks it when its rounding bound
-// fits the tolerance).  With g_sb set, every entry is also applied to a second
+// row then summed by a warp in compensated FP32 (direct_sum_mode picks it when
+// its rounding bound fits the tolerance).  With g_sb set, every entry is also applied to a second
 // coefficient vector (c_sb, c2b) into g_sb: the entries are evaluated once for
 // both (the two real components of complex c, or two vectors).
 constexpr int kDirSlots = 32;
@@ -806,14 +847,16 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
             if (two) atomicAdd(&rowfb[slot], v * c2b[B.j0 + cc].x);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-            double sum = 0.0, sumb = 0.0;
-            for (int k = 0; k < S; ++k) {
-                sum += (double)rowf[i * S + k];
-                if (two) sumb += (double)rowfb[i * S + k];
+        // a row's S <= 32 slots summed by one warp, compensated FP32 sums
+        // through the shuffles (no FP64 adds: FP64 runs at 1/64 of the rate)
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = threadIdx.x >> 5; i < rows; i += nw) {
+            const acc2 a = warp_sum_acc(acc2{lane < S ? rowf[i * S + lane] : 0.f, 0.f});
+            if (lane == 0) atomicAdd(&g_s[B.k0 + i], (double)P.sgn * acc_value(a));
+            if (two) {
+                const acc2 ab = warp_sum_acc(acc2{lane < S ? rowfb[i * S + lane] : 0.f, 0.f});
+                if (lane == 0) atomicAdd(&g_sb[B.k0 + i], (double)P.sgn * acc_value(ab));
             }
-            atomicAdd(&g_s[B.k0 + i], (double)P.sgn * sum);
-            if (two) atomicAdd(&g_sb[B.k0 + i], (double)P.sgn * sumb);
         }
         return;
     }
@@ -894,7 +937,7 @@ k_local_adj_moments(const ProbParams* __restrict__ probs, const LocalBlock* __re
             } else {
                 const int ns = miller_start(ntop, (double)ydf.h);
                 df S = (ydf.h >= 1.f) ? miller_store_df(ydf, ntop, ns, jb, nt, tid)
-                                      : df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+                                      : series_store_df(ydf, ntop, jb, nt, tid);
                 // a power of two near 1/S keeps products of two values in FP32 range
                 const float p2 = exp2f(-(float)ilogbf(S.h));
                 S = df_scale(S, p2);
@@ -1173,7 +1216,7 @@ __global__ void k_local_eval_group(const ProbParams* __restrict__ probs, const L
         const int ns = miller_start(ntop, (double)ydf.h);
         df S;
         if (ydf.h >= 1.f) S = miller_store_df(ydf, ntop, ns, jb, nt, tid);
-        else S = df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+        else S = series_store_df(ydf, ntop, jb, nt, tid);
         const float p2 = exp2f(-(float)ilogbf(S.h));
         S = df_scale(S, p2);
         acc2 sum[GM];
@@ -1295,7 +1338,7 @@ k_local_adj_moments_group(const ProbParams* __restrict__ probs, const LocalBlock
             } else {
                 const int ns = miller_start(ntop, (double)ydf.h);
                 df S = (ydf.h >= 1.f) ? miller_store_df(ydf, ntop, ns, jb, nt, tid)
-                                      : df_from(series_store_fp64(df_to(ydf), ntop, jb, nt, tid));
+                                      : series_store_df(ydf, ntop, jb, nt, tid);
                 p2 = exp2f(-(float)ilogbf(S.h));
                 S = df_scale(S, p2);
                 const df iS = df_recip(S);
