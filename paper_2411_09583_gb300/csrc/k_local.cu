@@ -185,25 +185,50 @@ __device__ __forceinline__ int miller_fp32_head(int ns, int lo, float ih, float*
     return i;
 }
 
+// The double-float steps start from the FP32 head's state scaled near 1 (an
+// exact power of two) and rescale by 2^-20 whenever a value passes 2^20 (the
+// check runs every second step, whose growth is below 2^16, so values stay
+// below 2^36): products of two stored values times a moment (below 2^33)
+// then stay far inside the FP32 range without per-term scaling.  Each step J_{i-1} = (2i/y) J_i - J_{i+1} is one compensated
+// multiply-subtract: the factor 2i/y and the product are kept as unevaluated
+// (hi, lo) pairs and only the result is renormalised.  S, the normalisation,
+// is a compensated FP32 sum.
 __device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb, int nt, int tid)
 {
     const df iy = df_recip(y);
     const float ih = 2.f * iy.h, il = 2.f * iy.l;   // 2 / y
     float f1, f0, fS;
     const int i0 = miller_fp32_head(ns, miller_fp32_floor(ntop, y.h), ih, &f1, &f0, &fS);
-    df jp1{f1, 0.f}, jc{f0, 0.f}, S{fS, 0.f};
-    if (i0 <= ntop) jb[i0 * nt + tid] = make_float2(jc.h, jc.l);
+    const float s0 = ldexpf(1.f, -ilogbf(f0));
+    float jh = f0 * s0, jl = 0.f, ph = f1 * s0, pl = 0.f;
+    acc2 S{fS * s0, 0.f};
+    if (i0 <= ntop) jb[i0 * nt + tid] = make_float2(jh, jl);
+    auto step = [&](int i) {
+        const float fi = (float)i;
+        const float th = fi * ih;
+        const float tl = fmaf(fi, il, fmaf(fi, ih, -th));
+        const float P = th * jh;
+        const float Pe = fmaf(tl, jh, fmaf(th, jl, fmaf(th, jh, -P)));
+        float sm, e;
+        two_sum(P, -ph, sm, e);
+        const df nj = fast_two_sum(sm, e + (Pe - pl));
+        ph = jh;
+        pl = jl;
+        jh = nj.h;
+        jl = nj.l;
+    };
     for (int i = i0; i >= 2; i -= 2) {
-        const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
-        const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
-        if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = make_float2(jm.h, jm.l);
-        if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = make_float2(jmm.h, jmm.l);
-        S = df_add(S, df{2.f * jmm.h, 2.f * jmm.l});
-        jp1 = jm;
-        jc = jmm;
-        if (df_big(jc)) {
-            const float sc = 8.673617379884035e-19f;   // 2^-60
-            jc = df_scale(jc, sc); jp1 = df_scale(jp1, sc); S = df_scale(S, sc);
+        step(i);
+        if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = make_float2(jh, jl);
+        step(i - 1);
+        if (i - 2 <= ntop) jb[(i - 2) * nt + tid] = make_float2(jh, jl);
+        float s2, e2;
+        two_sum(S.s, 2.f * jh, s2, e2);
+        S.s = s2;
+        S.c += e2 + 2.f * jl;
+        if (fabsf(jh) > 1048576.f) {
+            const float sc = 9.5367431640625e-07f;   // 2^-20
+            jh *= sc; jl *= sc; ph *= sc; pl *= sc; S.s *= sc; S.c *= sc;
             const int top = ntop < i0 ? ntop : i0;
             for (int q = i - 2; q <= top; ++q) {
                 const float2 v = jb[q * nt + tid];
@@ -211,7 +236,10 @@ __device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb
             }
         }
     }
-    return df_add(S, df_neg(jc));   // J_0 was added with weight 2; it counts once
+    // J_0 was added with weight 2; it counts once
+    float s2, e2;
+    two_sum(S.s, -jh, s2, e2);
+    return fast_two_sum(s2, S.c + e2 - jl);
 }
 
 // 1 / k as double-float (k < 2^24, exact in FP32)
@@ -294,14 +322,21 @@ __device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ p
     float2* mu = sm2;                 // [L + 1] moments of this block, double-float
     float2* mub = sm2 + (P.ntop + 1); // [L + 1] the second component's (two)
     float2* jb = sm2 + (two ? 2 : 1) * (P.ntop + 1);  // [ntop + 1][nt]
+    const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
+    const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
+    // the moments times the sign and weight of their term: C_l = sgn_l J_{hp+l} J_{|hm-l|},
+    // sgn_l = (-1 for an odd negative index hm - l) (2 unless l = 0 and nu is even)
     for (int l = tid; l <= L; l += nt) {
+        const int b = hm - l;
+        float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
+        if (l > 0 || (nu & 1)) sgn *= 2.f;
         const double v = coherent ? __ldcg(&mom[B.mom_off + l]) : mom[B.mom_off + l];
         const float h = (float)v;
-        mu[l] = make_float2(h, (float)(v - (double)h));
+        mu[l] = make_float2(sgn * h, sgn * (float)(v - (double)h));
         if (two) {
             const double vb = coherent ? __ldcg(&momb[B.mom_off + l]) : momb[B.mom_off + l];
             const float hb = (float)vb;
-            mub[l] = make_float2(hb, (float)(vb - (double)hb));
+            mub[l] = make_float2(sgn * hb, sgn * (float)(vb - (double)hb));
         }
     }
     __syncthreads();
@@ -316,8 +351,6 @@ __device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ p
         val = (nu == 0) ? (double)mu[0].x + (double)mu[0].y : 0.0;
         if (two) valb = (nu == 0) ? (double)mub[0].x + (double)mub[0].y : 0.0;
     } else {
-        const int hp = (nu & 1) ? (nu + 1) / 2 : nu / 2;   // index paired with +l
-        const int hm = (nu & 1) ? (nu - 1) / 2 : nu / 2;   // index paired with -l
         const int ntop = hp + L;
         const int ns = miller_start(ntop, (double)ydf.h);
         df S;
@@ -326,34 +359,29 @@ __device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ p
         } else {
             S = series_store_df(ydf, ntop, jb, nt, tid);
         }
-        // scale by a power of two near 1/S so that products of two values stay in FP32 range
-        const float p2 = exp2f(-(float)ilogbf(S.h));
-        S = df_scale(S, p2);
+        // The stored values stay below 2^36 and the signed moments below 2^33
+        // (inputs scaled below 2, at most 2^31 points), so the products
+        // J_a J_b mu_l (each an unevaluated (hi, lo) pair) and their sums stay
+        // inside the FP32 range; S^2 is divided out at the end.
         acc2 sum{0.f, 0.f}, sumb{0.f, 0.f};
         if (nu == 0) {
-            // C_l = (2 - delta_l0) (-1)^l J_l^2: one stored value per term, squared
+            // C_l = sgn_l J_l^2: one stored value per term, squared
             for (int l = 0; l <= L; ++l) {
                 const float2 v = jb[l * nt + tid];
-                const float xh = v.x * p2, xl = v.y * p2;
-                const float p = xh * xh;
-                float e = fmaf(xh, xh, -p);
-                e = fmaf(2.f * xh, xl, e);
-                const df sq = fast_two_sum(p, e);
-                const float sgn = l == 0 ? 1.f : ((l & 1) ? -2.f : 2.f);
-                const df cl{sgn * sq.h, sgn * sq.l};
-                acc_fma(sum, cl, df{mu[l].x, mu[l].y});
-                if (two) acc_fma(sumb, cl, df{mub[l].x, mub[l].y});
+                const float p = v.x * v.x;
+                const float e = fmaf(2.f * v.x, v.y, fmaf(v.x, v.x, -p));
+                acc_fma(sum, df{p, e}, df{mu[l].x, mu[l].y});
+                if (two) acc_fma(sumb, df{p, e}, df{mub[l].x, mub[l].y});
             }
         } else {
             for (int l = 0; l <= L; ++l) {
                 const int b = hm - l;
                 const float2 va = jb[(hp + l) * nt + tid];
-                float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
-                float sgn = (b < 0 && ((-b) & 1)) ? -1.f : 1.f;
-                if (l > 0 || (nu & 1)) sgn *= 2.f;
-                const df cl = df_mul(df{va.x * p2, va.y * p2}, df{vb.x * p2 * sgn, vb.y * p2 * sgn});
-                acc_fma(sum, cl, df{mu[l].x, mu[l].y});
-                if (two) acc_fma(sumb, cl, df{mub[l].x, mub[l].y});
+                const float2 vb = jb[(b >= 0 ? b : -b) * nt + tid];
+                const float p = va.x * vb.x;
+                const float e = fmaf(va.y, vb.x, fmaf(va.x, vb.y, fmaf(va.x, vb.x, -p)));
+                acc_fma(sum, df{p, e}, df{mu[l].x, mu[l].y});
+                if (two) acc_fma(sumb, df{p, e}, df{mub[l].x, mub[l].y});
             }
         }
         const df iS = df_recip(S);
