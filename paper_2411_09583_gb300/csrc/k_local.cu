@@ -301,6 +301,89 @@ __device__ __forceinline__ df series_store_df(df y, int ntop, float2* jb, int nt
     return df{1.f, 0.f};
 }
 
+// nu = 0: sum_l sgn_l J_l(y)^2 mu_l (and the same with mub) accumulated while
+// Miller's backward recurrence produces J_l, l <= L, without storing them:
+// the steps, the start and the rescaling of miller_store_df; a rescale by
+// 2^-20 scales the sums of squares by 2^-40.  Returns S (unnormalised
+// values, as miller_store_df).
+__device__ __forceinline__ df miller_sum_nu0(df y, int L, int ns, const float2* mu, const float2* mub, bool two,
+                                            acc2* sum, acc2* sumb)
+{
+    const df iy = df_recip(y);
+    const float ih = 2.f * iy.h, il = 2.f * iy.l;   // 2 / y
+    float f1, f0, fS;
+    const int i0 = miller_fp32_head(ns, miller_fp32_floor(L, y.h), ih, &f1, &f0, &fS);
+    const float s0 = ldexpf(1.f, -ilogbf(f0));
+    float jh = f0 * s0, jl = 0.f, ph = f1 * s0, pl = 0.f;
+    acc2 S{fS * s0, 0.f};
+    acc2 A{0.f, 0.f}, Ab{0.f, 0.f};
+    auto take = [&](int l) {
+        if (l <= L) {
+            const float p = jh * jh;
+            const float e = fmaf(2.f * jh, jl, fmaf(jh, jh, -p));
+            acc_fma(A, df{p, e}, df{mu[l].x, mu[l].y});
+            if (two) acc_fma(Ab, df{p, e}, df{mub[l].x, mub[l].y});
+        }
+    };
+    auto step = [&](int i) {
+        const float fi = (float)i;
+        const float th = fi * ih;
+        const float tl = fmaf(fi, il, fmaf(fi, ih, -th));
+        const float P = th * jh;
+        const float Pe = fmaf(tl, jh, fmaf(th, jl, fmaf(th, jh, -P)));
+        float sm, e;
+        two_sum(P, -ph, sm, e);
+        const df nj = fast_two_sum(sm, e + (Pe - pl));
+        ph = jh;
+        pl = jl;
+        jh = nj.h;
+        jl = nj.l;
+    };
+    take(i0);
+    for (int i = i0; i >= 2; i -= 2) {
+        step(i);
+        take(i - 1);
+        step(i - 1);
+        take(i - 2);
+        float s2, e2;
+        two_sum(S.s, 2.f * jh, s2, e2);
+        S.s = s2;
+        S.c += e2 + 2.f * jl;
+        if (fabsf(jh) > 1048576.f) {
+            const float sc = 9.5367431640625e-07f;    // 2^-20
+            const float sc2 = 9.094947017729282e-13f; // 2^-40
+            jh *= sc; jl *= sc; ph *= sc; pl *= sc; S.s *= sc; S.c *= sc;
+            A.s *= sc2; A.c *= sc2; Ab.s *= sc2; Ab.c *= sc2;
+        }
+    }
+    *sum = A;
+    *sumb = Ab;
+    float s2, e2;
+    two_sum(S.s, -jh, s2, e2);
+    return fast_two_sum(s2, S.c + e2 - jl);
+}
+
+// nu = 0, y < 1: the same sums from the power series values (normalised).
+__device__ __forceinline__ void series_sum_nu0(df y, int L, const float2* mu, const float2* mub, bool two,
+                                               acc2* sum, acc2* sumb)
+{
+    const df h{0.5f * y.h, 0.5f * y.l};
+    const df q = df_neg(df_mul(h, h));
+    df lead{1.f, 0.f};   // (y/2)^n / n!
+    acc2 A{0.f, 0.f}, Ab{0.f, 0.f};
+    for (int n = 0; n <= L && lead.h != 0.f; ++n) {
+        if (n > 0) lead = df_mul(df_mul(lead, h), df_inv_int(n));
+        if (lead.h == 0.f) break;
+        const df v = jn_series_sum(n, lead, q);
+        const float p = v.h * v.h;
+        const float e = fmaf(2.f * v.h, v.l, fmaf(v.h, v.h, -p));
+        acc_fma(A, df{p, e}, df{mu[n].x, mu[n].y});
+        if (two) acc_fma(Ab, df{p, e}, df{mub[n].x, mub[n].y});
+    }
+    *sum = A;
+    *sumb = Ab;
+}
+
 // One thread per row of a local block.  J_0..J_ntop(x/2) by Miller's backward
 // recurrence, kept (unnormalised) in this thread's column of shared memory,
 // then sum_l C_l mu_l divided by the square of the normalisation.  With momb
@@ -353,8 +436,15 @@ __device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ p
     } else {
         const int ntop = hp + L;
         const int ns = miller_start(ntop, (double)ydf.h);
-        df S;
-        if (ydf.h >= 1.f) {
+        df S{1.f, 0.f};
+        acc2 sum{0.f, 0.f}, sumb{0.f, 0.f};
+        if (nu == 0) {
+            // C_l = sgn_l J_l^2, summed as the values are made (no column)
+            if (ydf.h >= 1.f)
+                S = miller_sum_nu0(ydf, L, ns, mu, mub, two, &sum, &sumb);
+            else
+                series_sum_nu0(ydf, L, mu, mub, two, &sum, &sumb);
+        } else if (ydf.h >= 1.f) {
             S = miller_store_df(ydf, ntop, ns, jb, nt, tid);
         } else {
             S = series_store_df(ydf, ntop, jb, nt, tid);
@@ -363,17 +453,7 @@ __device__ __forceinline__ void local_eval_tile(const ProbParams* __restrict__ p
         // (inputs scaled below 2, at most 2^31 points), so the products
         // J_a J_b mu_l (each an unevaluated (hi, lo) pair) and their sums stay
         // inside the FP32 range; S^2 is divided out at the end.
-        acc2 sum{0.f, 0.f}, sumb{0.f, 0.f};
-        if (nu == 0) {
-            // C_l = sgn_l J_l^2: one stored value per term, squared
-            for (int l = 0; l <= L; ++l) {
-                const float2 v = jb[l * nt + tid];
-                const float p = v.x * v.x;
-                const float e = fmaf(2.f * v.x, v.y, fmaf(v.x, v.x, -p));
-                acc_fma(sum, df{p, e}, df{mu[l].x, mu[l].y});
-                if (two) acc_fma(sumb, df{p, e}, df{mub[l].x, mub[l].y});
-            }
-        } else {
+        if (nu != 0) {
             for (int l = 0; l <= L; ++l) {
                 const int b = hm - l;
                 const float2 va = jb[(hp + l) * nt + tid];
@@ -1559,13 +1639,15 @@ int local_eval_threads(int ntop_max)
 }
 
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                                   int ntiles, int ntop_max, int threads, const float2* w2,
+                                   int ntiles, int ntop_max, bool column, int threads, const float2* w2,
                                    const double* mom, double* g_s, const double* momb, double* g_sb,
                                    cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     const size_t nmu = momb ? 2 : 1;
-    size_t smem = sizeof(float2) * ((size_t)(ntop_max + 1) * threads + nmu * (size_t)(ntop_max + 1));
+    // rows of order 0 keep no Bessel column (their sums are formed during the sweep)
+    const size_t col = column ? (size_t)(ntop_max + 1) * threads : 0;
+    size_t smem = sizeof(float2) * (col + nmu * (size_t)(ntop_max + 1));
     cudaError_t e = cudaFuncSetAttribute(k_local_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -256,7 +256,7 @@ cudaError_t launch_local_eval_f32(const ProbParams* probs, const LocalBlock* blk
                                   int ntiles, int ntop_max, int threads, const float2* w2, const double* mom,
                                   double* g_s, const double* momb, double* g_sb, cudaStream_t s);
 cudaError_t launch_local_eval(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
-                              int ntiles, int ntop_max, int threads, const float2* w2,
+                              int ntiles, int ntop_max, bool column, int threads, const float2* w2,
                               const double* mom, double* g_s, const double* momb, double* g_sb,
                               cudaStream_t s);
 // Mode of the direct kernel (0 double-float; 1 FP32 entries, FP64 sums; 2 FP32

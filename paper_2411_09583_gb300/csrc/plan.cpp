@@ -130,7 +130,7 @@ struct nuht_plan_s {
     int n_dir = 0;
     int64_t mom_len = 0, gb_len = 0, gq_len = 0;
     int max_fblock_pts = 0;   // largest nf2 * Q among the blocks FFT'd whole by one CTA
-    int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, max_dir_area = 0, ntop_max = 0, eval_threads = 0;
+    int max_nf2_small = 0, max_dir_rows = 0, max_dir_cols = 0, max_dir_area = 0, ntop_max = 0, nu_max = 0, eval_threads = 0;
     int spread_threads = 256;
     // real components per asymptotic launch (forward spreading and
     // interpolation, FP64 path): grids for that many are allocated
@@ -569,7 +569,9 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
     P->lmax = 0;
     P->qmax = 0;
     P->ntop_max = 0;
+    P->nu_max = 0;
     for (const ProbParams& q : probs) {
+        P->nu_max = q.nu > P->nu_max ? q.nu : P->nu_max;
         P->lmax = q.L > P->lmax ? q.L : P->lmax;
         P->qmax = q.Q > P->qmax ? q.Q : P->qmax;
         P->ntop_max = q.ntop > P->ntop_max ? q.ntop : P->ntop_max;
@@ -1297,7 +1299,7 @@ static int apply_forward(nuht_plan_t P, int c0, int ng, cudaStream_t s)
                                           P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb, ls));
         else
             NUHT_CK(launch_local_eval(P->d_prob, P->d_loc, P->d_teval, P->n_teval, P->ntop_max,
-                                      P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb, ls));
+                                      P->nu_max > 0, P->eval_threads, P->d_w2, P->d_mom, gs, momb, gsb, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_EVAL, ls));
     }
     if (dir) {
