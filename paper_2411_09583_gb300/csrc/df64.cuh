@@ -201,6 +201,47 @@ __device__ __forceinline__ void df_sincos_turns(unsigned long long F, df* sn, df
     df_sincos_quadrant(x, quad, sn, cs);
 }
 
+// sin and cos of 2 pi F / 2^64 (F a fraction of a turn in 64-bit fixed
+// point) from a table tw[k] = e^{2 pi i k / 8192}, k < 4096, as double-float
+// (cos h, cos l, sin h, sin l): table-driven argument reduction.  The
+// quadrant is the top two bits (rounded); of the remainder x (|x| <= pi/4)
+// the nearest table angle theta_k = 2 pi k / 8192 (k <= 1024) is taken and
+// the residual delta = x - theta_k (|delta| <= pi / 8192, from 48 exact bits
+// of the fixed-point remainder) enters through its Taylor series:
+// sin delta = delta - delta^3/6 and 1 - cos delta = delta^2/2 - delta^4/24,
+// whose next terms are below 1e-19.  Then sin(theta + delta) =
+// sin theta + (cos theta sin delta - sin theta (1 - cos delta)) and
+// cos(theta + delta) = cos theta - (sin theta sin delta + cos theta (1 - cos
+// delta)) in double-float; odd symmetry gives negative x.
+__device__ __forceinline__ void df_sincos_turns_tab(unsigned long long F, const float4* __restrict__ tw, df* sn,
+                                                    df* cs)
+{
+    const unsigned long long Fq = F + (1ULL << 61);
+    const int quad = (int)(Fq >> 62);
+    const long long rem = (long long)(Fq & ((1ULL << 62) - 1)) - (1LL << 61);   // [-2^61, 2^61)
+    const long long ar = rem < 0 ? -rem : rem;                                      // [0, 2^61]
+    const int k = (int)((ar + (1LL << 50)) >> 51);                                 // nearest k / 8192 turn
+    const long long r = (ar - ((long long)k << 51)) >> 3;                          // [-2^47, 2^47], 2^-61 turns
+    float th, tl;
+    two_sum((float)(int)(r >> 24) * 16777216.f, (float)(int)(r & 0xFFFFFF), th, tl);
+    const float s61 = 4.336808689942018e-19f;                                      // 2^-61
+    const df dl = df_mul(df{th * s61, tl * s61}, df{6.2831854820251465f, -1.7484555314695172e-07f});
+    const df d2 = df_mul(dl, dl);
+    const df sd = fast_two_sum(dl.h, dl.l - dl.h * d2.h * (1.f / 6.f));          // sin delta
+    const df u{0.5f * d2.h, 0.5f * d2.l - d2.h * d2.h * (1.f / 24.f)};            // 1 - cos delta
+    const float4 t = tw[k];
+    const df ck{t.x, t.y}, sk{t.z, t.w};
+    df s0 = df_add(sk, df_add(df_mul(ck, sd), df_negate(df_mul(sk, u))));
+    const df c0 = df_add(ck, df_negate(df_add(df_mul(sk, sd), df_mul(ck, u))));
+    if (rem < 0) s0 = df_negate(s0);
+    switch (quad & 3) {
+        case 0: *sn = s0; *cs = c0; break;
+        case 1: *sn = c0; *cs = df_negate(s0); break;
+        case 2: *sn = df_negate(s0); *cs = df_negate(c0); break;
+        default: *sn = df_negate(c0); *cs = s0; break;
+    }
+}
+
 // sin, cos of 2 pi F / 2^64 (a fraction of a turn in 64-bit fixed point) in
 // FP32: the quadrant from the top bits, sincosf of the remainder.
 __device__ __forceinline__ void f32_sincos_turns(unsigned long long F, float* sn, float* cs)

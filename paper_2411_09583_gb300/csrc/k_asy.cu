@@ -85,11 +85,11 @@ __device__ __forceinline__ int spread_cell_fx(const AsyBlock& B, int w, double r
 // and the ratio (r_j/rho)^(-1) that steps the weight from q to q + 1; r_j and
 // c_j come as double-float pairs, the phase w_c x_j / (2 pi) from the
 // fixed-point offset.
-__device__ __forceinline__ void spread_weight_fx(const AsyBlock& B, long long X, float2 r2, float2 c2, df* wr,
-                                                 df* wi, df* rat)
+__device__ __forceinline__ void spread_weight_fx(const AsyBlock& B, const float4* __restrict__ tw, long long X,
+                                                 float2 r2, float2 c2, df* wr, df* wi, df* rat)
 {
     df sn, cs;
-    df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+    df_sincos_turns_tab(mul128_bits(X, B.KW, B.sW), tw, &sn, &cs);
     *rat = df_mul(df{B.rho_h, B.rho_l}, df_recip(df{r2.x, r2.y}));
     const df w0 = df_mul(df{c2.x, c2.y}, df_sqrt(*rat));
     *wr = df_mul(w0, cs);
@@ -543,7 +543,7 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             fc = fn;
         }
         df rat;
-        spread_weight_fx(B, X, r2[j], MULTI ? make_float2(1.f, 0.f) : c2[j], &yr, &yi, &rat);
+        spread_weight_fx(B, tab.tw2, X, r2[j], MULTI ? make_float2(1.f, 0.f) : c2[j], &yr, &yi, &rat);
         if (!MULTI) Y[tid] = make_float4(yr.h, yr.l, yi.h, yi.l);
     }
     __syncthreads();
@@ -783,7 +783,7 @@ __device__ void spread_taps(const AsyBlock& B, int Q, const Tile& t, const Table
             const df tp = horner_comp(coef + i * (deg + 1), deg, vh, vl, tab.deg_comp);
             taps[tid * w + i] = make_float2(tp.h, tp.l);
         }
-        spread_weight_fx(B, X, r2[j], MULTI ? make_float2(1.f, 0.f) : c2[j], &yr, &yi, &rat);
+        spread_weight_fx(B, tab.tw2, X, r2[j], MULTI ? make_float2(1.f, 0.f) : c2[j], &yr, &yi, &rat);
         if (!MULTI) {
             for (int q = 0; q < Q; ++q) {
                 aval[tid * Q + q] = make_float4(yr.h, yr.l, yi.h, yi.l);
@@ -947,7 +947,7 @@ __global__ void k_asy_spread(const ProbParams* __restrict__ probs, const AsyBloc
             [&](int64_t j, df* v, float2* xq) {
                 long long Xp;
                 const int l0 = spread_cell_fx(B, tab.w, r_s[j], &Xp, v);
-                spread_weight_fx(B, Xp, r2[j], make_float2(1.f, 0.f), &yr, &yi, &rat);
+                spread_weight_fx(B, tab.tw2, Xp, r2[j], make_float2(1.f, 0.f), &yr, &yi, &rat);
                 jt = j;
                 put(xq, c2[j]);
                 return l0;
@@ -1652,7 +1652,7 @@ __global__ void __launch_bounds__(kInterpTileThreads, 3) k_asy_interp(
         const float2 wk2 = w2[k];
         const df m1d = df_recip(df_mul(df{wk2.x, wk2.y}, df{B.rho_h, B.rho_l}));   // 1/(omega rho) < 1/z
         mz = df_mul(m1d, df{P.z2.x, P.z2.y});                                       // z/(omega rho) < 1
-        df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+        df_sincos_turns_tab(mul128_bits(Om, B.KRc, B.sR), tab.tw2, &sn, &cs);
         // sqrt(2/pi) (omega rho)^(-1/2) (4 / w^2) / psi^(alpha s)
         scale = df_mul(df_mul(df_sqrt(m1d), df_recip(psihat_fx(tab, B, Sw))), df{tab.ic2.x, tab.ic2.y});
         if (P.sgn < 0) scale = df_negate(scale);
@@ -1738,7 +1738,7 @@ __device__ __forceinline__ int adj_spread_factor(const AsyBlock& B, const ProbPa
     const df m1d = df_recip(df_from(wk * B.rho));
     F->mz = df_mul(m1d, df{P.z2.x, P.z2.y});
     df sn, cs;
-    df_sincos_turns(mul128_bits(Om, B.KRc, B.sR), &sn, &cs);
+    df_sincos_turns_tab(mul128_bits(Om, B.KRc, B.sR), tab.tw2, &sn, &cs);
     const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
     const df er = df_add(df_mul(cs, cph), df_negate(df_mul(sn, sph)));
     const df ei = df_add(df_mul(sn, cph), df_mul(cs, sph));
@@ -1952,7 +1952,7 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
                 }
             }
             rat = df_mul(df_from(B.rho), df_recip(df_from(rj)));   // (r/rho)^(-1) <= 1
-            if (MULTI) df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+            if (MULTI) df_sincos_turns_tab(mul128_bits(X, B.KW, B.sW), tab.tw2, &sn, &cs);
         }
         for (int vm = 0; vm < (MULTI ? V : 1); ++vm) {
             const float4* gb = bgrid + vm * bg_stride + B.b_off;
@@ -1987,7 +1987,7 @@ __global__ void __launch_bounds__(kAdjInterpThreads) k_asy_adj_interp(
                     return (li >= 0 && li < nf1) ? gb[(int64_t)li * Q + q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }, combine);
             // c_j += Re( e^{i w_c x} (r/rho)^(-1/2) T )
-            if (!MULTI) df_sincos_turns(mul128_bits(X, B.KW, B.sW), &sn, &cs);
+            if (!MULTI) df_sincos_turns_tab(mul128_bits(X, B.KW, B.sW), tab.tw2, &sn, &cs);
             const df tre = fast_two_sum(tr.s, tr.c), tim = fast_two_sum(ti.s, ti.c);
             const df re = df_add(df_mul(cs, tre), df_negate(df_mul(sn, tim)));
             Accum{c_s + vm * c_stride, P.fxs}.add(j, df_to(df_mul(df_sqrt(rat), re)));
