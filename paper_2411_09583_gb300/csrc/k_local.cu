@@ -185,6 +185,27 @@ __device__ __forceinline__ int miller_fp32_head(int ns, int lo, float ih, float*
     return i;
 }
 
+// One step J_{i-1} = (2i/y) J_i - J_{i+1} of Miller's recurrence in
+// double-float, (ih, il) = 2/y: on entry (jh, jl) = J_i and (ph, pl) =
+// J_{i+1}, on exit J_{i-1} and J_i.  A compensated multiply-subtract: the
+// factor 2i/y and the product stay unevaluated (hi, lo) pairs and only the
+// result is renormalised.
+__device__ __forceinline__ void miller_step(int i, float ih, float il, float& jh, float& jl, float& ph, float& pl)
+{
+    const float fi = (float)i;
+    const float th = fi * ih;
+    const float tl = fmaf(fi, il, fmaf(fi, ih, -th));
+    const float P = th * jh;
+    const float Pe = fmaf(tl, jh, fmaf(th, jl, fmaf(th, jh, -P)));
+    float sm, e;
+    two_sum(P, -ph, sm, e);
+    const df nj = fast_two_sum(sm, e + (Pe - pl));
+    ph = jh;
+    pl = jl;
+    jh = nj.h;
+    jl = nj.l;
+}
+
 // The double-float steps start from the FP32 head's state scaled near 1 (an
 // exact power of two) and rescale by 2^-20 whenever a value passes 2^20 (the
 // check runs every second step, whose growth is below 2^16, so values stay
@@ -203,20 +224,7 @@ __device__ __forceinline__ df miller_store_df(df y, int ntop, int ns, float2* jb
     float jh = f0 * s0, jl = 0.f, ph = f1 * s0, pl = 0.f;
     acc2 S{fS * s0, 0.f};
     if (i0 <= ntop) jb[i0 * nt + tid] = make_float2(jh, jl);
-    auto step = [&](int i) {
-        const float fi = (float)i;
-        const float th = fi * ih;
-        const float tl = fmaf(fi, il, fmaf(fi, ih, -th));
-        const float P = th * jh;
-        const float Pe = fmaf(tl, jh, fmaf(th, jl, fmaf(th, jh, -P)));
-        float sm, e;
-        two_sum(P, -ph, sm, e);
-        const df nj = fast_two_sum(sm, e + (Pe - pl));
-        ph = jh;
-        pl = jl;
-        jh = nj.h;
-        jl = nj.l;
-    };
+    auto step = [&](int i) { miller_step(i, ih, il, jh, jl, ph, pl); };
     for (int i = i0; i >= 2; i -= 2) {
         step(i);
         if (i - 1 <= ntop) jb[(i - 1) * nt + tid] = make_float2(jh, jl);
@@ -325,20 +333,7 @@ __device__ __forceinline__ df miller_sum_nu0(df y, int L, int ns, const float2* 
             if (two) acc_fma(Ab, df{p, e}, df{mub[l].x, mub[l].y});
         }
     };
-    auto step = [&](int i) {
-        const float fi = (float)i;
-        const float th = fi * ih;
-        const float tl = fmaf(fi, il, fmaf(fi, ih, -th));
-        const float P = th * jh;
-        const float Pe = fmaf(tl, jh, fmaf(th, jl, fmaf(th, jh, -P)));
-        float sm, e;
-        two_sum(P, -ph, sm, e);
-        const df nj = fast_two_sum(sm, e + (Pe - pl));
-        ph = jh;
-        pl = jl;
-        jh = nj.h;
-        jl = nj.l;
-    };
+    auto step = [&](int i) { miller_step(i, ih, il, jh, jl, ph, pl); };
     take(i0);
     for (int i = i0; i >= 2; i -= 2) {
         step(i);
@@ -720,7 +715,7 @@ __device__ __forceinline__ double jn_hankel_dfx(const ProbParams& P, df x, unsig
     }
     qq = df_mul(qq, u);
     df sx, cx;
-    df_sincos_turns(turns, &sx, &cx);
+    df_sincos_turns_tab(turns, P.tw2, &sx, &cx);
     const df cph{P.cphi2.x, P.cphi2.y}, sph{P.sphi2.x, P.sphi2.y};
     const df cchi = df_add(df_mul(cx, cph), df_negate(df_mul(sx, sph)));   // cos(x + phi)
     const df schi = df_add(df_mul(sx, cph), df_mul(cx, sph));              // sin(x + phi)
@@ -740,22 +735,27 @@ __device__ __forceinline__ double jn_miller_dfx(int n, df x)
     const float ih = i2.h, il = i2.l;
     float f1, f0, fS;
     const int i0 = miller_fp32_head(ns, miller_fp32_floor(n, xf), ih, &f1, &f0, &fS);
-    df jp1{f1, 0.f}, jc{f0, 0.f}, S{fS, 0.f}, res{0.f, 0.f};
+    // compensated steps from the head's state (as miller_store_df), keeping J_n
+    float jh = f0, jl = 0.f, ph = f1, pl = 0.f;
+    acc2 S{fS, 0.f};
+    df res{0.f, 0.f};
     for (int i = i0; i >= 2; i -= 2) {
-        const df jm = df_add(df_mul(df_imul((float)i, ih, il), jc), df_neg(jp1));
-        const df jmm = df_add(df_mul(df_imul((float)(i - 1), ih, il), jm), df_neg(jc));
-        if (i - 1 == n) res = jm;
-        if (i - 2 == n) res = jmm;
-        S = df_add(S, df{2.f * jmm.h, 2.f * jmm.l});
-        jp1 = jm;
-        jc = jmm;
-        if (df_big(jc)) {
+        miller_step(i, ih, il, jh, jl, ph, pl);
+        if (i - 1 == n) res = df{jh, jl};
+        miller_step(i - 1, ih, il, jh, jl, ph, pl);
+        if (i - 2 == n) res = df{jh, jl};
+        float s2, e2;
+        two_sum(S.s, 2.f * jh, s2, e2);
+        S.s = s2;
+        S.c += e2 + 2.f * jl;
+        if (fabsf(jh) > 1.152921504606847e18f) {
             const float sc = 8.673617379884035e-19f;   // 2^-60
-            jc = df_scale(jc, sc); jp1 = df_scale(jp1, sc); S = df_scale(S, sc); res = df_scale(res, sc);
+            jh *= sc; jl *= sc; ph *= sc; pl *= sc; S.s *= sc; S.c *= sc; res = df_scale(res, sc);
         }
     }
-    S = df_add(S, df_neg(jc));
-    return df_to(df_mul(res, df_recip(S)));
+    float s2, e2;
+    two_sum(S.s, -jh, s2, e2);   // J_0 was added with weight 2; it counts once
+    return df_to(df_mul(res, df_recip(fast_two_sum(s2, S.c + e2 - jl))));
 }
 
 // J_nu at the exact product w*r: asymptotic side (Hankel in double-float, or

@@ -49,6 +49,8 @@ struct ProbParams {
     int64_t r_off, w_off;        // offsets of this problem in the sorted arrays
     int64_t n, m;
     int64_t c_off, g_off;        // offsets of this problem's c and g (batched)
+    const float4* tw2;           // the plan's table e^{2 pi i k / 8192}, k < 4096, as double-float
+                                 // (cos h, cos l, sin h, sin l): phases of the direct entries
 };
 
 // Local block: rows k0..k1 (omega), columns j0..j1 (r), absolute indices into

@@ -920,6 +920,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
                 pp.dcp[pr] = (int8_t)d;
             }
     }
+    for (ProbParams& q : probs) q.tw2 = (const float4*)(D + a_tw2);
     put(a_prob, probs.data(), sizeof(ProbParams) * probs.size());
     put(a_es, T.es.data(), sizeof(double) * T.es.size());
     put(a_es2, T.es2.data(), sizeof(float2) * T.es2.size());
