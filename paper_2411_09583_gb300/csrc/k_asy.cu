@@ -137,7 +137,7 @@ __device__ __forceinline__ df psihat_of(const Tables& T, df xi)
     if (piece > T.ph_pieces - 1) piece = T.ph_pieces - 1;
     const df u = df_add(t, df{-(float)piece, 0.f});
     const df v = df_add(df{2.f * u.h, 2.f * u.l}, df{-1.f, 0.f});
-    return horner_comp(T.ph2 + piece * (T.ph_deg + 1), T.ph_deg, v.h, v.l);
+    return horner_comp(T.ph2 + piece * (T.ph_deg + 1), T.ph_deg, v.h, v.l, T.ph_comp);
 }
 
 // psi^(xi) for xi = alpha s (s from the fixed-point offset S).
@@ -1679,6 +1679,19 @@ __global__ void __launch_bounds__(kInterpTileThreads, 3) k_asy_interp(
         acc2 tr{0.f, 0.f}, ti{0.f, 0.f};
         df mq{1.f, 0.f};
         auto combine = [&](int q, df prd, df pid) {
+            if (q >= qs) {
+                // small terms (FP32 sums, weights below 1e-8 of the first):
+                // products and sums in FP32, into the compensation parts
+                const float cq = P.a2[q].x * mq.h;
+                switch (q & 3) {
+                    case 0: tr.c = fmaf(cq, prd.h, tr.c); ti.c = fmaf(cq, pid.h, ti.c); break;
+                    case 1: tr.c = fmaf(-cq, pid.h, tr.c); ti.c = fmaf(cq, prd.h, ti.c); break;
+                    case 2: tr.c = fmaf(-cq, prd.h, tr.c); ti.c = fmaf(-cq, pid.h, ti.c); break;
+                    default: tr.c = fmaf(cq, pid.h, tr.c); ti.c = fmaf(-cq, prd.h, ti.c); break;
+                }
+                mq.h *= mz.h;
+                return;
+            }
             const df cq = df_mul(df{P.a2[q].x, P.a2[q].y}, mq);
             // multiply by i^q: (pr + i pi) i^q
             switch (q & 3) {

@@ -26,6 +26,7 @@ struct HostTables {
     std::vector<double> ch;     // [w][deg + 1] the same pieces as coefficients of T_0..T_deg(v)
     std::vector<float2> ch2;    // the same split into (hi, lo) floats
     int ph_pieces = 0, ph_deg = 0;
+    int ph_comp = 0;            // psi-hat degrees above this one may be summed in plain FP32
     double ph_scale = 0.0, ph_xmax = 0.0;
     std::vector<double> ph;     // [ph_pieces][ph_deg + 1]
     std::vector<float2> ph2;    // the same split into (hi, lo) floats

@@ -186,6 +186,7 @@ struct Tables {
     float2 ic2;            // the same as double-float
     float2 ph_scale2;      // ph_scale as double-float
     int ph_pieces, ph_deg;
+    int ph_comp;           // psi-hat degrees above this one are evaluated in plain FP32
     double ph_scale;       // pieces per unit of xi
     double ph_xmax;        // table covers xi in [0, ph_xmax]
     const double2* tw;     // e^{2 pi i k / 2^tw_log2}, k < 2^(tw_log2 - 1)

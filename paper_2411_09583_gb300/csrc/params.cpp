@@ -227,6 +227,33 @@ const HostTables& kernel_tables(int w)
         const float hi = (float)T.ph[i];
         T.ph2[i] = make_float2(hi, (float)(T.ph[i] - (double)hi));
     }
+    // Degrees whose coefficient tail, rounded in FP32 (2^-23 relative), stays
+    // below 1e-3 eps_w of the smallest psi^ on the piece, for the smallest
+    // tolerance of this width, eps_w = 10^-(w - 1): the deconvolution factor's
+    // relative error stays below 1e-3 eps.  The largest such degree over the
+    // pieces bounds the compensated part of the Horner sums.
+    {
+        const int nc = T.ph_deg + 1;
+        const double eps_w = std::pow(10.0, -(double)(w - 1));
+        T.ph_comp = 0;
+        for (int p = 0; p < T.ph_pieces; ++p) {
+            const double* c = &T.ph[(size_t)p * nc];
+            double mn = 1e300;
+            for (int t = 0; t <= 64; ++t) {
+                const double v = -1.0 + 2.0 * t / 64.0;
+                double y = 0.0;
+                for (int k = nc - 1; k >= 0; --k) y = y * v + c[k];
+                mn = std::fmin(mn, std::fabs(y));
+            }
+            double tail = 0.0;
+            int kc = -1;
+            for (int k = nc - 1; k >= 0; --k) {
+                tail += std::fabs(c[k]);
+                if (tail * 1.1920928955078125e-07 > 1e-3 * eps_w * mn) { kc = k; break; }
+            }
+            T.ph_comp = kc > T.ph_comp ? kc : T.ph_comp;
+        }
+    }
     // twiddles e^{2 pi i k / 8192}, k < 4096 (single-CTA FFTs up to 8192 points)
     T.tw_log2 = 13;
     T.tw.assign((size_t)1 << (T.tw_log2 - 1), make_double2(0.0, 0.0));

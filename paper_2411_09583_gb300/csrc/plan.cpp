@@ -1047,7 +1047,7 @@ static int build_plan(nuht_plan_t P, const double* r, const double* omega, const
         tb.fold_df_tol = (float)(kRoundBudget * P->eps / ((kMomFold + 2) * 1.1920928955078125e-07));
     }
     tb.ph = P->d_ph; tb.ph2 = (const float2*)(D + a_ph2);
-    tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg;
+    tb.ph_pieces = T.ph_pieces; tb.ph_deg = T.ph_deg; tb.ph_comp = T.ph_comp;
     tb.interp_const = std::sqrt(2.0 / M_PI) * 4.0 / ((double)T.w * (double)T.w);
     tb.ic2 = make_float2((float)tb.interp_const, (float)(tb.interp_const - (double)(float)tb.interp_const));
     tb.ph_scale = T.ph_scale; tb.ph_xmax = T.ph_xmax;
