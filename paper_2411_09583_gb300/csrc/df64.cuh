@@ -111,6 +111,19 @@ namespace nuht {
 
 __device__ __forceinline__ df df_negate(df a) { return df{-a.h, -a.l}; }
 
+// Three-term step a t1 - t0 in double-float (a Chebyshev recurrence with
+// a = 2x), as one
+// compensated multiply-subtract: the product's rounding error and the low
+// parts enter the correction, only the result is renormalised.
+__device__ __forceinline__ df cheb_step(df a, df t1, df t0)
+{
+    const float P = a.h * t1.h;
+    const float Pe = fmaf(a.l, t1.h, fmaf(a.h, t1.l, fmaf(a.h, t1.h, -P)));
+    float sm, e;
+    two_sum(P, -t0.h, sm, e);
+    return fast_two_sum(sm, e + (Pe - t0.l));
+}
+
 // 1/a by one Newton step from the FP32 reciprocal (error ~ 2^-47).
 __device__ __forceinline__ df df_recip(df a)
 {

@@ -236,7 +236,7 @@ __device__ __forceinline__ void spread_moments(int Q, int qs, const Tile& t, con
         const df v2{2.f * vh, 2.f * vl};
         int d = 2;
         for (; d < dcs; ++d) {
-            const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+            const df tn = cheb_step(v2, tc, tm);
             ud[d] = make_float2(tn.h, tn.l);
             tm = tc;
             tc = tn;
@@ -530,7 +530,7 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
         const df v2{2.f * vh, 2.f * vl};
         int d = 2;
         for (; d < Edf; ++d) {
-            const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+            const df tn = cheb_step(v2, tc, tm);
             ud[d] = make_float2(tn.h, tn.l);
             tm = tc;
             tc = tn;
@@ -1478,7 +1478,7 @@ __device__ __forceinline__ void cheb_basis_row(float2* u, float vh, float vl, in
     const df v2{2.f * vh, 2.f * vl};
     int d = 2;
     for (; d < dci; ++d) {
-        const df tn = df_add(df_mul(v2, tc), df_negate(tm));
+        const df tn = cheb_step(v2, tc, tm);
         u[d] = make_float2(tn.h, tn.l);
         tm = tc;
         tc = tn;

@@ -123,8 +123,8 @@ __device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict_
             acc_fma(acc[nt + tid], cjb, t1b);
         }
         for (int l = 2; l <= L; ++l) {
-            const df t2a = df_add(df_mul(u2a, t1a), df_neg(t0a));
-            const df t2b = df_add(df_mul(u2b, t1b), df_neg(t0b));
+            const df t2a = cheb_step(u2a, t1a, t0a);
+            const df t2b = cheb_step(u2b, t1b, t0b);
             acc2 a = acc[l * nt + tid];
             acc_fma(a, cja, t2a);
             acc_fma(a, cjb, t2b);
@@ -1131,7 +1131,7 @@ k_local_adj_eval(const ProbParams* __restrict__ probs, const LocalBlock* __restr
         acc_fma(sum, t0, df{mu2[0].x, mu2[0].y});
         if (L >= 1) acc_fma(sum, t1, df{mu2[1].x, mu2[1].y});
         for (int l = 2; l <= L; ++l) {
-            const df t2 = df_add(df_mul(u2, t1), df_neg(t0));
+            const df t2 = cheb_step(u2, t1, t0);
             acc_fma(sum, t2, df{mu2[l].x, mu2[l].y});
             t0 = t1;
             t1 = t2;
@@ -1242,7 +1242,7 @@ k_local_moments_group(const ProbParams* __restrict__ probs, const LocalBlock* __
             Tb[tid] = make_float2(t0.h, t0.l);
             if (L >= 1) Tb[ps + tid] = make_float2(t1.h, t1.l);
             for (int l = 2; l <= L; ++l) {
-                const df t2 = df_add(df_mul(u2, t1), df_neg(t0));
+                const df t2 = cheb_step(u2, t1, t0);
                 Tb[l * ps + tid] = make_float2(t2.h, t2.l);
                 t0 = t1;
                 t1 = t2;
@@ -1532,7 +1532,7 @@ k_local_adj_eval_group(const ProbParams* __restrict__ probs, const LocalBlock* _
             if (l == 0) tl = t0;
             else if (l == 1) tl = t1;
             else {
-                tl = df_add(df_mul(u2, t1), df_neg(t0));
+                tl = cheb_step(u2, t1, t0);
                 t0 = t1;
                 t1 = tl;
             }
