@@ -419,6 +419,44 @@ constexpr int kFoldMax = 8;          // Chebyshev terms of the weights' dependen
 constexpr int kFoldDfMax = 4;        // extra double-float degrees of N the fold may need
 constexpr int kFoldGroupBytes = 8192;
 
+// Constants of the fold's weight expansion: 1/(j + 1) as double-float and
+// MC(j, k) = 2^(1-j) C(j, (j-k)/2) (halved for k = 0; zero unless j >= k and
+// j - k is even), the Chebyshev coefficients of v^j -- exact small floats.
+struct FoldConsts {
+    float2 inv[kFoldMax];
+    float mc[kFoldMax][kFoldMax];
+};
+constexpr FoldConsts make_fold_consts()
+{
+    FoldConsts c{};
+    for (int j = 0; j < kFoldMax; ++j) {
+        const double v = 1.0 / (j + 1);
+        const float h = (float)v;
+        c.inv[j] = float2{h, (float)(v - (double)h)};
+        for (int k = 0; k < kFoldMax; ++k) {
+            double m = 0.0;
+            if (k <= j && ((j - k) & 1) == 0) {
+                const int i = (j - k) / 2;
+                double binom = 1.0;
+                for (int t = 0; t < i; ++t) binom = binom * (j - t) / (t + 1);
+                m = binom * 2.0;
+                for (int t = 0; t < j; ++t) m *= 0.5;
+                if (k == 0) m *= 0.5;
+            }
+            c.mc[j][k] = (float)m;
+        }
+    }
+    return c;
+}
+__constant__ FoldConsts kFoldC = make_fold_consts();
+
+// a f for a double-float a and a float f
+__device__ __forceinline__ df df_mul_f(df a, float f)
+{
+    const float p = a.h * f;
+    return fast_two_sum(p, fmaf(a.l, f, fmaf(a.h, f, -p)));
+}
+
 struct FoldPlan {
     int K;      // terms k < K of the weights' Chebyshev form
     int E;      // moments N[e], e < E (even)
@@ -651,22 +689,20 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             df tj[kFoldMax];
             tj[0] = df{1.f, 0.f};
             for (int j = 0; j + 1 < K; ++j) {
-                const df f = df_mul(df{(float)(q + j), 0.f}, df_recip(df{(float)(j + 1), 0.f}));
-                tj[j + 1] = df_mul(df_mul(tj[j], eta), f);
+                // t_{j+1} = t_j eta (q + j) / (j + 1)
+                const float2 iv = kFoldC.inv[j];
+                tj[j + 1] = df_mul(df_mul(tj[j], eta), df_mul_f(df{iv.x, iv.y}, (float)(q + j)));
             }
-            df sq{1.f, 0.f};
-            for (int i = 0; i < q; ++i) sq = df_mul(sq, s);
+            // s^q by repeated squaring
+            df sq{1.f, 0.f}, sp = s;
+            for (int e = q; e > 0; e >>= 1) {
+                if (e & 1) sq = df_mul(sq, sp);
+                if (e > 1) sp = df_mul(sp, sp);
+            }
             float2* bt = beta + (b * Q + q) * kFoldMax;
             for (int k = 0; k < K; ++k) {
                 df acc{0.f, 0.f};
-                float cjk = 1.f;                     // C(j, (j - k)/2) for j = k
-                for (int j = k; j < K; j += 2) {
-                    const float mc = ldexpf(cjk, 1 - j) * (k == 0 ? 0.5f : 1.f);
-                    acc = df_add(acc, df_mul(tj[j], df{mc, 0.f}));
-                    // C(j+2, i+1) = C(j, i) (j+1)(j+2) / ((i+1)(j+2-i-1)), i = (j-k)/2
-                    const int i = (j - k) >> 1;
-                    cjk = cjk * (float)((j + 1) * (j + 2)) / (float)((i + 1) * (j + 1 - i));
-                }
+                for (int j = k; j < K; j += 2) acc = df_add(acc, df_mul_f(tj[j], kFoldC.mc[j][k]));
                 const df bk = df_mul(sq, acc);
                 bt[k] = make_float2(bk.h, bk.l);
             }
