@@ -708,47 +708,86 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             }
         }
         __syncthreads();
-        // (b) M[d][q] = sum_k beta_qk (N[d+k] + N[|d-k|]) / 2 into the row order of Mb
-        for (int o = tid; o < gn * L.dpad * Q; o += nt) {
-            const int b = o / (L.dpad * Q), rem = o - b * (L.dpad * Q);
-            const int e = rem / Q, q = rem - e * Q;
+        // (b) M[d][q] = sum_k beta_qk (N[d+k] + N[|d-k|]) / 2 into the row order of Mb;
+        // each item forms two consecutive q, so one sum N[d+k] + N[|d-k|]
+        // (an unevaluated (hi, lo) pair) serves both
+        for (int o = tid; o < gn * L.dpad * (Q >> 1); o += nt) {
+            const int b = o / (L.dpad * (Q >> 1)), rem = o - b * (L.dpad * (Q >> 1));
+            const int e = rem / (Q >> 1), q0 = 2 * (rem - e * (Q >> 1));
             const int d = mom_degree(e, L.ndf, dcs, nb);
-            float2 mr = make_float2(0.f, 0.f), mi = make_float2(0.f, 0.f);
+            float2 mr0 = make_float2(0.f, 0.f), mi0 = mr0, mr1 = mr0, mi1 = mr0;
             if (d >= 0) {
-                const float2* bt = beta + (b * Q + q) * kFoldMax;
+                const float2* bt0 = beta + (b * Q + q0) * kFoldMax;
+                const float2* bt1 = bt0 + kFoldMax;
                 const float4* Nb = N + b * E;
-                const float2 b0 = bt[0];
                 const float4 n0 = Nb[d];
-                if (e < 2 * L.ndf && q < qs) {
-                    acc2 ar{0.f, 0.f}, ai{0.f, 0.f};
-                    acc_fma(ar, df{b0.x, b0.y}, df{n0.x, n0.y});
-                    acc_fma(ai, df{b0.x, b0.y}, df{n0.z, n0.w});
+                const bool dfe = e < 2 * L.ndf;
+                if (dfe && q0 < qs) {
+                    const bool df1 = q0 + 1 < qs;
+                    acc2 ar0{0.f, 0.f}, ai0{0.f, 0.f}, ar1{0.f, 0.f}, ai1{0.f, 0.f};
+                    const float2 b00 = bt0[0], b10 = bt1[0];
+                    acc_fma(ar0, df{b00.x, b00.y}, df{n0.x, n0.y});
+                    acc_fma(ai0, df{b00.x, b00.y}, df{n0.z, n0.w});
+                    if (df1) {
+                        acc_fma(ar1, df{b10.x, b10.y}, df{n0.x, n0.y});
+                        acc_fma(ai1, df{b10.x, b10.y}, df{n0.z, n0.w});
+                    } else {
+                        ar1.s = b10.x * n0.x;
+                        ai1.s = b10.x * n0.z;
+                    }
                     for (int k = 1; k < K; ++k) {
                         const float4 n1 = Nb[d + k], n2 = Nb[d >= k ? d - k : k - d];
-                        const df sr = df_add(df{n1.x, n1.y}, df{n2.x, n2.y});
-                        const df si = df_add(df{n1.z, n1.w}, df{n2.z, n2.w});
-                        const float2 bk = bt[k];
-                        const df hb{0.5f * bk.x, 0.5f * bk.y};
-                        acc_fma(ar, hb, sr);
-                        acc_fma(ai, hb, si);
+                        float sr, er, si, ei;
+                        two_sum(n1.x, n2.x, sr, er);
+                        two_sum(n1.z, n2.z, si, ei);
+                        const df Sr{sr, er + (n1.y + n2.y)}, Si{si, ei + (n1.w + n2.w)};
+                        const float2 bk0 = bt0[k], bk1 = bt1[k];
+                        acc_fma(ar0, df{0.5f * bk0.x, 0.5f * bk0.y}, Sr);
+                        acc_fma(ai0, df{0.5f * bk0.x, 0.5f * bk0.y}, Si);
+                        if (df1) {
+                            acc_fma(ar1, df{0.5f * bk1.x, 0.5f * bk1.y}, Sr);
+                            acc_fma(ai1, df{0.5f * bk1.x, 0.5f * bk1.y}, Si);
+                        } else {
+                            ar1.s = fmaf(0.5f * bk1.x, sr, ar1.s);
+                            ai1.s = fmaf(0.5f * bk1.x, si, ai1.s);
+                        }
                     }
-                    const df vr = fast_two_sum(ar.s, ar.c), vi = fast_two_sum(ai.s, ai.c);
-                    mr = make_float2(vr.h, vr.l);
-                    mi = make_float2(vi.h, vi.l);
+                    df v = fast_two_sum(ar0.s, ar0.c);
+                    mr0 = make_float2(v.h, v.l);
+                    v = fast_two_sum(ai0.s, ai0.c);
+                    mi0 = make_float2(v.h, v.l);
+                    if (df1) {
+                        v = fast_two_sum(ar1.s, ar1.c);
+                        mr1 = make_float2(v.h, v.l);
+                        v = fast_two_sum(ai1.s, ai1.c);
+                        mi1 = make_float2(v.h, v.l);
+                    } else {
+                        mr1 = make_float2(ar1.s, 0.f);
+                        mi1 = make_float2(ai1.s, 0.f);
+                    }
                 } else {
-                    float fr = b0.x * n0.x, fi = b0.x * n0.z;
+                    const float b00 = bt0[0].x, b10 = bt1[0].x;
+                    float fr0 = b00 * n0.x, fi0 = b00 * n0.z, fr1 = b10 * n0.x, fi1 = b10 * n0.z;
                     for (int k = 1; k < K; ++k) {
                         const float4 n1 = Nb[d + k], n2 = Nb[d >= k ? d - k : k - d];
-                        const float hb = 0.5f * bt[k].x;
-                        fr = fmaf(hb, n1.x + n2.x, fr);
-                        fi = fmaf(hb, n1.z + n2.z, fi);
+                        const float sr = n1.x + n2.x, si = n1.z + n2.z;
+                        const float h0 = 0.5f * bt0[k].x, h1 = 0.5f * bt1[k].x;
+                        fr0 = fmaf(h0, sr, fr0);
+                        fi0 = fmaf(h0, si, fi0);
+                        fr1 = fmaf(h1, sr, fr1);
+                        fi1 = fmaf(h1, si, fi1);
                     }
-                    mr = make_float2(fr, 0.f);
-                    mi = make_float2(fi, 0.f);
+                    mr0 = make_float2(fr0, 0.f);
+                    mi0 = make_float2(fi0, 0.f);
+                    mr1 = make_float2(fr1, 0.f);
+                    mi1 = make_float2(fi1, 0.f);
                 }
             }
-            Mb[(b * L.dpad + e) * Q2 + 2 * q] = mr;
-            Mb[(b * L.dpad + e) * Q2 + 2 * q + 1] = mi;
+            float2* mo = Mb + (b * L.dpad + e) * Q2 + 2 * q0;
+            mo[0] = mr0;
+            mo[1] = mi0;
+            mo[2] = mr1;
+            mo[3] = mi1;
         }
         __syncthreads();
         // (c) grid[lfirst + g0 + c][q'] += sum_b sum_d A[c - b][d] M_b[d][q'] over
