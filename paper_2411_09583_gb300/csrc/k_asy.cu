@@ -1491,26 +1491,40 @@ __device__ __forceinline__ void bin_sums_build(const float4* win, const float2* 
 {
     const int Q2 = 2 * Q, hs = nb * Q2 + 2;
     const int npr = (nb + 1) >> 1;
+    // a tile of one or two bins has few items: one degree per item then, so
+    // that twice as many threads share the work
+    const int g2 = (nbins * npr * Q * 2 <= (int)blockDim.x) ? 1 : 2;   // degrees per item
+    const int nper = g2 == 2 ? npr : nb;
     // q is the slowest index, so that a warp's items mostly share q (and with
     // it the double-float / FP32 branch)
-    for (int o = threadIdx.x; o < nbins * npr * Q; o += blockDim.x) {
-        const int q = o / (nbins * npr), rem = o - q * (nbins * npr);
-        const int b = rem / npr, dp = rem - b * npr;
-        const int d0 = 2 * dp, d1 = d0 + 1;
-        const bool has1 = d1 < nb;
+    for (int o = threadIdx.x; o < nbins * nper * Q; o += blockDim.x) {
+        const int q = o / (nbins * nper), rem = o - q * (nbins * nper);
+        const int b = rem / nper, dp = rem - b * nper;
+        const int d0 = g2 * dp, d1 = d0 + 1;
+        const bool has1 = g2 == 2 && d1 < nb;
         float2* h0 = H + b * hs + d0 * Q2 + 2 * q;
         if (d0 < min(dci, (int)dcp[q >> 1]) && q < qs) {
             acc2 a0r{0.f, 0.f}, a0i{0.f, 0.f}, a1r{0.f, 0.f}, a1i{0.f, 0.f};
+            if (has1) {
 #pragma unroll 4
-            for (int i = 0; i < w; ++i) {
-                const float4 gv = win[(b + i) * Q + q];
-                const float2 c0 = coef2[i * nb + d0];
-                const float2 c1 = has1 ? coef2[i * nb + d1] : make_float2(0.f, 0.f);
-                const df gr{gv.x, gv.y}, gi{gv.z, gv.w};
-                acc_fma(a0r, df{c0.x, c0.y}, gr);
-                acc_fma(a0i, df{c0.x, c0.y}, gi);
-                acc_fma(a1r, df{c1.x, c1.y}, gr);
-                acc_fma(a1i, df{c1.x, c1.y}, gi);
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = win[(b + i) * Q + q];
+                    const float2 c0 = coef2[i * nb + d0];
+                    const float2 c1 = coef2[i * nb + d1];
+                    const df gr{gv.x, gv.y}, gi{gv.z, gv.w};
+                    acc_fma(a0r, df{c0.x, c0.y}, gr);
+                    acc_fma(a0i, df{c0.x, c0.y}, gi);
+                    acc_fma(a1r, df{c1.x, c1.y}, gr);
+                    acc_fma(a1i, df{c1.x, c1.y}, gi);
+                }
+            } else {
+#pragma unroll 4
+                for (int i = 0; i < w; ++i) {
+                    const float4 gv = win[(b + i) * Q + q];
+                    const float2 c0 = coef2[i * nb + d0];
+                    acc_fma(a0r, df{c0.x, c0.y}, df{gv.x, gv.y});
+                    acc_fma(a0i, df{c0.x, c0.y}, df{gv.z, gv.w});
+                }
             }
             df v = fast_two_sum(a0r.s, a0r.c);
             h0[0] = make_float2(v.h, v.l);
