@@ -12,6 +12,9 @@
 
 namespace nuht {
 
+// streaming multiprocessors of the current device, cached per device (k_det.cu)
+int device_sm_count();
+
 namespace {
 
 __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -365,7 +368,7 @@ int64_t block_scan_scratch(int64_t cap) { return 3 * ((cap + kScanTile - 1) / kS
 
 cudaError_t launch_block_build(const BlockBuild& bb, int64_t* scratch, cudaStream_t s)
 {
-    k_block_sizes<<<152 * 8, 256, 0, s>>>(bb);
+    k_block_sizes<<<device_sm_count() * 8, 256, 0, s>>>(bb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t ptiles = (bb.ocap + kScanTile - 1) / kScanTile;
@@ -381,7 +384,7 @@ cudaError_t launch_block_build(const BlockBuild& bb, int64_t* scratch, cudaStrea
 
 cudaError_t launch_block_fill(const BlockBuild& bb, const BuildLists& L, cudaStream_t s)
 {
-    k_block_fill<<<152 * 8, 256, 0, s>>>(bb, L);
+    k_block_fill<<<device_sm_count() * 8, 256, 0, s>>>(bb, L);
     count_launches(1);
     return cudaGetLastError();
 }

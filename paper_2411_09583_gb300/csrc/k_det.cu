@@ -12,6 +12,8 @@
 
 namespace nuht {
 
+int device_sm_count();
+
 namespace {
 
 constexpr int kDetThreads = 256;
@@ -44,15 +46,24 @@ __global__ void __launch_bounds__(kDetThreads) k_fx_decode(const Fx128* __restri
 
 int grid_for(int64_t count)
 {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        sms = 1;
     const int64_t need = (count + kDetThreads - 1) / kDetThreads;
-    const int64_t cap = (int64_t)sms * 8;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
     return (int)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
 }  // namespace
+
+int device_sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    return sms;
+}
 
 cudaError_t launch_input_scale(const double* x, int64_t count, unsigned long long* mx, cudaStream_t s)
 {

@@ -18,6 +18,9 @@
 
 namespace nuht {
 
+// streaming multiprocessors of the current device, cached per device (k_det.cu)
+int device_sm_count();
+
 namespace {
 
 constexpr int kSortThreads = 256;
@@ -341,7 +344,8 @@ __global__ void k_expand_tiles(const Seg* __restrict__ segs, const int32_t* __re
 inline int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
-    if (b > 152 * 32) b = 152 * 32;
+    const int64_t cap = (int64_t)device_sm_count() * 32;
+    if (b > cap) b = cap;
     return b < 1 ? 1 : (int)b;
 }
 

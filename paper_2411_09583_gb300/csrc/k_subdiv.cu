@@ -21,6 +21,9 @@
 
 namespace nuht {
 
+// streaming multiprocessors of the current device, cached per device (k_det.cu)
+int device_sm_count();
+
 namespace {
 
 constexpr int kSubThreads = 1024;
@@ -503,7 +506,7 @@ cudaError_t launch_subdivide(const int32_t* stair, const double* r_s, const doub
 cudaError_t launch_block_bounds(const SubBlk* loc, const SubBlk* asy, const int64_t* res, const ProbParams* probs,
                                 const double* r_s, const double* w_s, double* bl, double4* ba, cudaStream_t s)
 {
-    k_block_bounds<<<152 * 8, 256, 0, s>>>(loc, asy, res, probs, r_s, w_s, bl, ba);
+    k_block_bounds<<<device_sm_count() * 8, 256, 0, s>>>(loc, asy, res, probs, r_s, w_s, bl, ba);
     count_launches(1);
     return cudaGetLastError();
 }
