@@ -33,17 +33,28 @@ if ROOT not in sys.path:
 
 METRIC = "NUHT (n+m)/s at ε=1e-8 fp64 vs fp32-mixed; batched; % HBM roofline"
 UNIT = "(n+m)/s"
-# FP64 FMA pipe of GB300: 2 FMA (4 FLOP) per clock per SM, 152 SMs, 2070 MHz max clock.
-FP64_PEAK_TFLOPS = 4 * 152 * 2070e6 / 1e12
-# FP32 pipes: 128 instructions per clock per SM.  A compensated double-float
-# multiply-add (TwoProduct + TwoSum + corrections) costs 12 FP32 instructions,
-# so the FP64-equivalent peak of the double-float loops is 2 * 40.3e12 / 12.
-FP32_ISSUE_PER_S = 128 * 152 * 2070e6
-DF_PEAK_TFLOPS = 2 * FP32_ISSUE_PER_S / 12 / 1e12
 L2_FLUSH_BYTES = 512 << 20
 HBM_FALLBACK_GBS = 6800.0
 DTYPE = ("df64: double-float (pairs of FP32, ~48-bit) tap, moment and Bessel arithmetic; "
          "64-bit fixed-point positions and phases; FP64 set-up and FP64 atomic accumulation")
+
+
+def df_model_peak(dev):
+    """Unit-count model of the double-float peak (context beside the measured
+    one): the FP32 pipes issue 128 instructions per clock per SM and a
+    compensated double-float multiply-add (TwoProduct + TwoSum + corrections)
+    costs 12 of them, so FP64-equivalent FLOP/s = 2 x 128 x SMs x clock / 12.
+    SMs from the device, the clock from MEASURED_PEAKS.json (sm_max_mhz).
+    Returns (TFLOP/s, description)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        pass
+    tf = 2 * 128 * sms * mhz * 1e6 / 12 / 1e12
+    return tf, "128 FP32 instr/clk/SM x %d SMs x %.0f MHz / 12 instr x 2 FLOP" % (sms, mhz)
 
 
 def measured_hbm_peak():
@@ -871,8 +882,7 @@ def run_ours(a):
                 "peak_source": "measured in this run (nuht_probe_alu, burst): FP64-equivalent FLOP/s of "
                                "the double-float compensated multiply-add acc_fma on the FP32 pipes; "
                                "FP32 FMA %.1f, FP64 FMA %.3f TFLOP/s measured beside it; unit-count model "
-                               "%.3f (128 FP32 instr/clk/SM x 152 SMs x 2070 MHz / 12 instr x 2 FLOP)"
-                               % (alu["ffma_tflops"], alu["dfma_tflops"], DF_PEAK_TFLOPS),
+                               "%.3f (%s)" % ((alu["ffma_tflops"], alu["dfma_tflops"]) + df_model_peak(dev)),
                 "algorithmic_flops_per_launch": flops, "units_per_launch": units,
                 "launch_ms": mean_stage[dom], "launch_ms_alone": mean_serial[dom]}
         tr, basis = stored_traffic(kernel_of.get(dom, dom), workload_config(a)["workload"], opts, units)
