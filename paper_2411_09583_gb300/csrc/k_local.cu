@@ -88,17 +88,26 @@ __device__ __forceinline__ void reduce_columns_add(const acc2* acc, int nt, int 
 // One CTA per tile of columns of one local block.  Each thread keeps its own
 // column of partial moments (compensated double-float accumulators) in shared
 // memory, acc[l * blockDim + tid]; the columns are summed at the end
-// (reduce_columns_add) and added to the block's moments.
+// (reduce_columns_add) and added to the block's moments.  TWO: a second real
+// component (coefficients c2b, moments momb, accumulators after the first
+// component's) shares each point's Chebyshev recurrence.
+template <bool TWO>
 __device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict__ probs,
                                                    const LocalBlock* __restrict__ blks, const Tile t,
                                                    const float2* __restrict__ r2, const float2* __restrict__ c2,
-                                                   double* __restrict__ mom, acc2* acc)
+                                                   double* __restrict__ mom, acc2* acc,
+                                                   const float2* __restrict__ c2b = nullptr,
+                                                   double* __restrict__ momb = nullptr)
 {
     const LocalBlock B = blks[t.blk];
     const int L = probs[B.prob].L;
     const int odd = probs[B.prob].nu & 1;
     const int nt = blockDim.x, tid = threadIdx.x;
-    for (int l = 0; l <= L; ++l) acc[l * nt + tid] = acc2{0.f, 0.f};
+    acc2* accb = acc + (L + 1) * nt;
+    for (int l = 0; l <= L; ++l) {
+        acc[l * nt + tid] = acc2{0.f, 0.f};
+        if (TWO) accb[l * nt + tid] = acc2{0.f, 0.f};
+    }
     const df invR{B.iR_h, B.iR_l};
     // two points per step: two independent recurrences (a point beyond the
     // tile enters with c = 0)
@@ -107,8 +116,13 @@ __device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict_
         const int64_t jb = j + nt < jend ? j + nt : j;
         const float2 ra = r2[j], ca = c2[j], rb = r2[jb];
         const float2 cb = j + nt < jend ? c2[jb] : make_float2(0.f, 0.f);
+        float2 da = make_float2(0.f, 0.f), db = da;
+        if (TWO) {
+            da = c2b[j];
+            db = j + nt < jend ? c2b[jb] : make_float2(0.f, 0.f);
+        }
         const df ya = df_mul(df{ra.x, ra.y}, invR), yb = df_mul(df{rb.x, rb.y}, invR);   // r_j / R in [0, 1]
-        const df cja{ca.x, ca.y}, cjb{cb.x, cb.y};
+        const df cja{ca.x, ca.y}, cjb{cb.x, cb.y}, dja{da.x, da.y}, djb{db.x, db.y};
         const df ua = df_add(df_mul(df{2.f * ya.h, 2.f * ya.l}, ya), df{-1.f, 0.f});   // T_2(y)
         const df ub = df_add(df_mul(df{2.f * yb.h, 2.f * yb.l}, yb), df{-1.f, 0.f});
         const df u2a{2.f * ua.h, 2.f * ua.l}, u2b{2.f * ub.h, 2.f * ub.l};
@@ -118,9 +132,17 @@ __device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict_
         df t1b = odd ? df_mul(yb, df_add(u2b, df{-1.f, 0.f})) : ub;
         acc_fma(acc[tid], cja, t0a);
         acc_fma(acc[tid], cjb, t0b);
+        if (TWO) {
+            acc_fma(accb[tid], dja, t0a);
+            acc_fma(accb[tid], djb, t0b);
+        }
         if (L >= 1) {
             acc_fma(acc[nt + tid], cja, t1a);
             acc_fma(acc[nt + tid], cjb, t1b);
+            if (TWO) {
+                acc_fma(accb[nt + tid], dja, t1a);
+                acc_fma(accb[nt + tid], djb, t1b);
+            }
         }
         for (int l = 2; l <= L; ++l) {
             const df t2a = cheb_step(u2a, t1a, t0a);
@@ -129,6 +151,12 @@ __device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict_
             acc_fma(a, cja, t2a);
             acc_fma(a, cjb, t2b);
             acc[l * nt + tid] = a;
+            if (TWO) {
+                acc2 a2 = accb[l * nt + tid];
+                acc_fma(a2, dja, t2a);
+                acc_fma(a2, djb, t2b);
+                accb[l * nt + tid] = a2;
+            }
             t0a = t1a;
             t1a = t2a;
             t0b = t1b;
@@ -137,6 +165,7 @@ __device__ __forceinline__ void local_moments_tile(const ProbParams* __restrict_
     }
     __syncthreads();
     reduce_columns_add(acc, nt, L, Accum{mom, probs[B.prob].fxs}.at(B.mom_off));
+    if (TWO) reduce_columns_add(accb, nt, L, Accum{momb, probs[B.prob].fxs}.at(B.mom_off));
 }
 
 __global__ void __launch_bounds__(kMomThreads)
@@ -145,7 +174,17 @@ k_local_moments(const ProbParams* __restrict__ probs, const LocalBlock* __restri
                 const float2* __restrict__ c2, double* __restrict__ mom)
 {
     extern __shared__ acc2 acc[];
-    local_moments_tile(probs, blks, tiles[blockIdx.x], r2, c2, mom, acc);
+    local_moments_tile<false>(probs, blks, tiles[blockIdx.x], r2, c2, mom, acc);
+}
+
+// A pair of real components in one pass (one recurrence per point for both).
+__global__ void __launch_bounds__(kMomThreads)
+k_local_moments2(const ProbParams* __restrict__ probs, const LocalBlock* __restrict__ blks,
+                 const Tile* __restrict__ tiles, const float2* __restrict__ r2, const float2* __restrict__ c2,
+                 const float2* __restrict__ c2b, double* __restrict__ mom, double* __restrict__ momb)
+{
+    extern __shared__ acc2 acc[];
+    local_moments_tile<true>(probs, blks, tiles[blockIdx.x], r2, c2, mom, acc, c2b, momb);
 }
 
 // J_0..J_ntop(y), unnormalised, into this thread's column jb[n * nt + tid]
@@ -506,7 +545,7 @@ k_local_persistent(const ProbParams* __restrict__ probs, const LocalBlock* __res
         if (it < nmom) {
             const int comp = it >= n_tmom ? 1 : 0;
             const Tile t = tmom[it - comp * n_tmom];
-            local_moments_tile(probs, blks, t, r2, comp ? c2b : c2, comp ? momb : mom, (acc2*)smq);
+            local_moments_tile<false>(probs, blks, t, r2, comp ? c2b : c2, comp ? momb : mom, (acc2*)smq);
             __threadfence();   // the moments' atomics before the count
             __syncthreads();
             if (threadIdx.x == 0) atomicAdd(&done[t.blk], 1);
@@ -1616,6 +1655,30 @@ cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks
     k_local_moments<<<ntiles, threads, smem, s>>>(probs, blks, tiles, r2, c2, mom);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// The pair kernel when its 2 (lmax + 1) accumulators per thread fit the
+// one-component kernel's threads in ~200 KB of shared memory; else
+// cudaErrorInvalidValue (the caller runs two one-component launches).
+cudaError_t launch_local_moments2(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                  int ntiles, int lmax, const float2* r2, const float2* c2, const float2* c2b,
+                                  double* mom, double* momb, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    const int threads = local_moment_threads(lmax);
+    const size_t smem = 2 * sizeof(acc2) * (size_t)(lmax + 1) * threads;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_local_moments2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_moments2<<<ntiles, threads, smem, s>>>(probs, blks, tiles, r2, c2, c2b, mom, momb);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+bool local_moments2_fits(int lmax)
+{
+    return 2 * sizeof(acc2) * (size_t)(lmax + 1) * local_moment_threads(lmax) <= 200 * 1024;
 }
 
 int local_moment_threads(int lmax)

@@ -245,6 +245,10 @@ cudaError_t launch_scatter(const double* gs, const int32_t* perm, int64_t m, int
 cudaError_t launch_local_moments(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
                                  int ntiles, int lmax, const float2* r2, const float2* c2,
                                  double* mom, cudaStream_t s);
+cudaError_t launch_local_moments2(const ProbParams* probs, const LocalBlock* blks, const Tile* tiles,
+                                  int ntiles, int lmax, const float2* r2, const float2* c2, const float2* c2b,
+                                  double* mom, double* momb, cudaStream_t s);
+bool local_moments2_fits(int lmax);
 cudaError_t launch_local_persistent(const ProbParams* probs, const LocalBlock* blks, const Tile* tmom, int n_tmom,
                                     const Tile* teval, int n_teval, const int32_t* mom_pre, int lmax, int ntop_max,
                                     int threads, const float2* r2, const float2* c2, const float2* c2b,

@@ -1280,19 +1280,24 @@ static int apply_forward(nuht_plan_t P, int c0, int ng, cudaStream_t s)
     } else if (loc) {
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_CK(cudaMemsetAsync(mom_acc, 0, acc_bytes(P, P->mom_len), ls));
-        NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
-                                     P->d_cs2, mom_acc, ls));
-        if (P->det) NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
-        // a pair's second moments by a second launch: the group kernel at G = 2
-        // was measured slower on the complex n = m = 4e6 workload (5.68 against
-        // 5.38 ms per execute)
+        // a pair's moments in one pass (one Chebyshev recurrence per point for
+        // both components) when its accumulators fit, else a second launch (the
+        // group kernel at G = 2 was measured slower on the complex n = m = 4e6
+        // workload: 5.68 against 5.38 ms per execute)
         double* momb = ng == 2 ? P->d_momb : nullptr;
-        if (momb) {
-            NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
+        if (momb) NUHT_CK(cudaMemsetAsync(momb_acc, 0, acc_bytes(P, P->mom_len), ls));
+        if (momb && local_moments2_fits(P->lmax)) {
+            NUHT_CK(launch_local_moments2(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
+                                          P->d_cs2, P->d_cs2b, mom_acc, momb_acc, ls));
+        } else {
             NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
-                                         P->d_cs2b, momb_acc, ls));
-            if (P->det) NUHT_CK(launch_fx_decode(P->f_momb, P->d_momb, P->mom_len, P->d_prob, ls));
+                                         P->d_cs2, mom_acc, ls));
+            if (momb)
+                NUHT_CK(launch_local_moments(P->d_prob, P->d_loc, P->d_tmom, P->n_tmom, P->lmax, P->d_r2,
+                                             P->d_cs2b, momb_acc, ls));
         }
+        if (P->det) NUHT_CK(launch_fx_decode(P->f_mom, P->d_mom, P->mom_len, P->d_prob, ls));
+        if (momb && P->det) NUHT_CK(launch_fx_decode(P->f_momb, P->d_momb, P->mom_len, P->d_prob, ls));
         NUHT_TRY(T.end(NUHT_STAGE_LOCAL_MOMENTS, ls));
         NUHT_TRY(T.begin(NUHT_STAGE_LOCAL_EVAL, ls));
         if (P->opt.precision == NUHT_PREC_MIXED)
