@@ -1007,19 +1007,52 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         }
         return;
     }
-    for (int t = threadIdx.x; t < area; t += blockDim.x) {
-        const int e = list[t];
-        const int rr = e / cols, cc = e - rr * cols;
-        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
-        if (det) {
+    if (det) {
+        for (int t = threadIdx.x; t < area; t += blockDim.x) {
+            const int e = list[t];
+            const int rr = e / cols, cc = e - rr * cols;
+            const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
             fx_add(reinterpret_cast<Fx128*>(g_s) + B.k0 + rr, (double)P.sgn * (v * c_s[B.j0 + cc]), P.fxs);
             if (two) fx_add(reinterpret_cast<Fx128*>(g_sb) + B.k0 + rr, (double)P.sgn * (v * c_sb[B.j0 + cc]), P.fxs);
-        } else {
-            atomicAdd(&rowacc[rr], v * c_s[B.j0 + cc]);
-            if (two) atomicAdd(&rowaccb[rr], v * c_sb[B.j0 + cc]);
+        }
+        return;
+    }
+    // A warp's 32 list positions hold runs of entries of one row (the list keeps
+    // each warp's chunk of the partition in row order): the products are summed
+    // over each run by a segmented scan through the shuffles, and one lane per
+    // run adds the run's sum to the row, instead of one shared-memory FP64
+    // atomic (a compare-and-swap loop, serialised within a run) per entry.
+    const int lane = threadIdx.x & 31;
+    const int area_pad = (area + 31) & ~31;
+    for (int t = threadIdx.x; t < area_pad; t += blockDim.x) {
+        int rr = -1;
+        double p = 0.0, pb = 0.0;
+        if (t < area) {
+            const int e = list[t];
+            rr = e / cols;
+            const int cc = e - rr * cols;
+            const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
+            p = v * c_s[B.j0 + cc];
+            if (two) pb = v * c_sb[B.j0 + cc];
+        }
+        const int rprev = __shfl_up_sync(0xffffffffu, rr, 1);
+        const int rnext = __shfl_down_sync(0xffffffffu, rr, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || rprev != rr);
+        const int seg0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // first lane of this run
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double q = __shfl_up_sync(0xffffffffu, p, off);
+            const double qb = two ? __shfl_up_sync(0xffffffffu, pb, off) : 0.0;
+            if (lane - off >= seg0) {
+                p += q;
+                if (two) pb += qb;
+            }
+        }
+        if (rr >= 0 && (lane == 31 || rnext != rr)) {
+            atomicAdd(&rowacc[rr], p);
+            if (two) atomicAdd(&rowaccb[rr], pb);
         }
     }
-    if (det) return;
     __syncthreads();
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
         atomicAdd(&g_s[B.k0 + i], (double)P.sgn * rowacc[i]);
