@@ -740,7 +740,7 @@ __device__ __forceinline__ unsigned long long turns_u128(unsigned long long Ph, 
 }
 
 // jn_hankel_df with x = omega r given as double-float and its phase in turns.
-__device__ __forceinline__ double jn_hankel_dfx(const ProbParams& P, df x, unsigned long long turns)
+__device__ __forceinline__ df jn_hankel_dfx(const ProbParams& P, df x, unsigned long long turns)
 {
     const df y = df_recip(x);
     const df u = df_mul(y, df{P.z2.x, P.z2.y});
@@ -759,11 +759,11 @@ __device__ __forceinline__ double jn_hankel_dfx(const ProbParams& P, df x, unsig
     const df cchi = df_add(df_mul(cx, cph), df_negate(df_mul(sx, sph)));   // cos(x + phi)
     const df schi = df_add(df_mul(sx, cph), df_mul(cx, sph));              // sin(x + phi)
     const df amp = df_sqrt(df_mul(df{0.6366197466850281f, 2.5682552973194106e-08f}, y));   // sqrt(2 / (pi x))
-    return df_to(df_mul(amp, df_add(df_mul(pp, cchi), df_negate(df_mul(qq, schi)))));
+    return df_mul(amp, df_add(df_mul(pp, cchi), df_negate(df_mul(qq, schi))));
 }
 
 // jn_miller_df with x >= 1 given as double-float (no FP64 divisions).
-__device__ __forceinline__ double jn_miller_dfx(int n, df x)
+__device__ __forceinline__ df jn_miller_dfx(int n, df x)
 {
     const float xf = x.h;
     const float a = xf + 20.f + 4.f * sqrtf(xf);
@@ -794,7 +794,7 @@ __device__ __forceinline__ double jn_miller_dfx(int n, df x)
     }
     float s2, e2;
     two_sum(S.s, -jh, s2, e2);   // J_0 was added with weight 2; it counts once
-    return df_to(df_mul(res, df_recip(fast_two_sum(s2, S.c + e2 - jl))));
+    return df_mul(res, df_recip(fast_two_sum(s2, S.c + e2 - jl)));
 }
 
 // J_nu at the exact product w*r: asymptotic side (Hankel in double-float, or
@@ -853,20 +853,26 @@ __device__ __forceinline__ float jn_miller_f32x(int n, float x)
 
 // direct_entry in the block's fixed-point frame; the series for x < 1 as in
 // direct_entry.
-__device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, double w, double r, bool asy,
-                                                  bool lowp)
+__device__ __forceinline__ df direct_entry_df(const ProbParams& P, DirFx F, double w, double r, bool asy,
+                                              bool lowp)
 {
     const int s = F.fr + F.fw;
     // the phase in turns needs s <= 127; x alone (local side) any s >= 64
-    if (s < 64 || (asy && s > 127)) return direct_entry(P, w, r, asy, lowp);
+    if (s < 64 || (asy && s > 127)) return df_from(direct_entry(P, w, r, asy, lowp));
     const unsigned long long Om = (unsigned long long)fx_from_double(w, F.fw);
     const unsigned long long R = (unsigned long long)fx_from_double(r, F.fr);
     const unsigned long long Pl = Om * R, Ph = __umul64hi(Om, R);
     const df x = df_from_u128(Ph, Pl, s);
-    if (asy) return lowp ? (double)jn_hankel_f32x(P, x.h, turns_u128(Ph, Pl, s))
+    if (asy) return lowp ? df{jn_hankel_f32x(P, x.h, turns_u128(Ph, Pl, s)), 0.f}
                          : jn_hankel_dfx(P, x, turns_u128(Ph, Pl, s));
-    if (x.h < 1.f) return lowp ? (double)jn_series_f32(P.nu, x.h) : df_to(jn_series_df(P.nu, x));
-    return lowp ? (double)jn_miller_f32x(P.nu, x.h) : jn_miller_dfx(P.nu, x);
+    if (x.h < 1.f) return lowp ? df{jn_series_f32(P.nu, x.h), 0.f} : jn_series_df(P.nu, x);
+    return lowp ? df{jn_miller_f32x(P.nu, x.h), 0.f} : jn_miller_dfx(P.nu, x);
+}
+
+__device__ __forceinline__ double direct_entry_fx(const ProbParams& P, DirFx F, double w, double r, bool asy,
+                                                  bool lowp)
+{
+    return df_to(direct_entry_df(P, F, w, r, asy, lowp));
 }
 
 // direct_entry_fx for lowp as an FP32 value (no FP64 beyond the rare series).
@@ -1024,16 +1030,22 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
     // atomic (a compare-and-swap loop, serialised within a run) per entry.
     const int lane = threadIdx.x & 31;
     const int area_pad = (area + 31) & ~31;
+    // Entries and products in double-float (the FP32 pipes), the run sums too;
+    // one conversion to FP64 per run.
     for (int t = threadIdx.x; t < area_pad; t += blockDim.x) {
         int rr = -1;
-        double p = 0.0, pb = 0.0;
+        df p{0.f, 0.f}, pb{0.f, 0.f};
         if (t < area) {
             const int e = list[t];
             rr = e / cols;
             const int cc = e - rr * cols;
-            const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
-            p = v * c_s[B.j0 + cc];
-            if (two) pb = v * c_sb[B.j0 + cc];
+            const df v = direct_entry_df(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
+            const float2 cv = c2[B.j0 + cc];
+            p = df_mul(v, df{cv.x, cv.y});
+            if (two) {
+                const float2 cvb = c2b[B.j0 + cc];
+                pb = df_mul(v, df{cvb.x, cvb.y});
+            }
         }
         const int rprev = __shfl_up_sync(0xffffffffu, rr, 1);
         const int rnext = __shfl_down_sync(0xffffffffu, rr, 1);
@@ -1041,16 +1053,17 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         const int seg0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // first lane of this run
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double q = __shfl_up_sync(0xffffffffu, p, off);
-            const double qb = two ? __shfl_up_sync(0xffffffffu, pb, off) : 0.0;
+            const df q{__shfl_up_sync(0xffffffffu, p.h, off), __shfl_up_sync(0xffffffffu, p.l, off)};
+            df qb{0.f, 0.f};
+            if (two) qb = df{__shfl_up_sync(0xffffffffu, pb.h, off), __shfl_up_sync(0xffffffffu, pb.l, off)};
             if (lane - off >= seg0) {
-                p += q;
-                if (two) pb += qb;
+                p = df_add(p, q);
+                if (two) pb = df_add(pb, qb);
             }
         }
         if (rr >= 0 && (lane == 31 || rnext != rr)) {
-            atomicAdd(&rowacc[rr], p);
-            if (two) atomicAdd(&rowaccb[rr], pb);
+            atomicAdd(&rowacc[rr], df_to(p));
+            if (two) atomicAdd(&rowaccb[rr], df_to(pb));
         }
     }
     __syncthreads();
