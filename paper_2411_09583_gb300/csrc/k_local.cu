@@ -899,6 +899,15 @@ __device__ __forceinline__ DirFx direct_frame(const double* __restrict__ r_s, co
     return DirFx{62 - er, 62 - ew};
 }
 
+// Division of an entry index by the block's column count with one wide
+// multiply: m = ceil(2^32 / d) gives floor(e m / 2^32) = floor(e / d) exactly
+// whenever e d < 2^32 (direct blocks hold at most a few thousand entries).
+struct ColDiv {
+    unsigned long long m;
+    __device__ __forceinline__ explicit ColDiv(int d) : m(((1ull << 32) + (unsigned)d - 1) / (unsigned)d) {}
+    __device__ __forceinline__ int operator()(int e) const { return (int)(((unsigned long long)(unsigned)e * m) >> 32); }
+};
+
 // Splits the entries of a direct block into a local list (omega r <= z, from
 // the front) and an asymptotic list (from the back) in shared memory, so that
 // warps run one branch each.  The split uses the FP32 parts of omega and r
@@ -915,11 +924,12 @@ __device__ __forceinline__ int direct_partition(const ProbParams& P, const Direc
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int area_pad = (area + 31) & ~31;
+    const ColDiv div(cols);
     for (int e = threadIdx.x; e < area_pad; e += blockDim.x) {
         const bool valid = e < area;
         bool asy = false;
         if (valid) {
-            const int rr = e / cols, cc = e - rr * cols;
+            const int rr = div(e), cc = e - rr * cols;
             asy = w2[B.k0 + rr].x * r2[B.j0 + cc].x > zf;
         }
         const unsigned ma = __ballot_sync(0xffffffffu, valid && asy);
@@ -969,6 +979,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
+    const ColDiv cdiv(cols);
     const int area = rows * cols;
     int S = kDirSlots;
     while (S > 1 && S * rows > kDirSlotFloats) S >>= 1;
@@ -993,7 +1004,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
     if (mode == 2) {
         for (int t = threadIdx.x; t < area; t += blockDim.x) {
             const int e = list[t];
-            const int rr = e / cols, cc = e - rr * cols;
+            const int rr = cdiv(e), cc = e - rr * cols;
             const float v = direct_entry_f32x(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc);
             const int slot = rr * S + (t & (S - 1));
             atomicAdd(&rowf[slot], v * c2[B.j0 + cc].x);
@@ -1016,7 +1027,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
     if (det) {
         for (int t = threadIdx.x; t < area; t += blockDim.x) {
             const int e = list[t];
-            const int rr = e / cols, cc = e - rr * cols;
+            const int rr = cdiv(e), cc = e - rr * cols;
             const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
             fx_add(reinterpret_cast<Fx128*>(g_s) + B.k0 + rr, (double)P.sgn * (v * c_s[B.j0 + cc]), P.fxs);
             if (two) fx_add(reinterpret_cast<Fx128*>(g_sb) + B.k0 + rr, (double)P.sgn * (v * c_sb[B.j0 + cc]), P.fxs);
@@ -1037,7 +1048,7 @@ __global__ void k_direct(const ProbParams* __restrict__ probs, const DirectBlock
         df p{0.f, 0.f}, pb{0.f, 0.f};
         if (t < area) {
             const int e = list[t];
-            rr = e / cols;
+            rr = cdiv(e);
             const int cc = e - rr * cols;
             const df v = direct_entry_df(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, mode == 1);
             const float2 cv = c2[B.j0 + cc];
@@ -1239,6 +1250,7 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
+    const ColDiv cdiv(cols);
     const int area = rows * cols;
     const int accd = det ? 0 : cols;
     int* list = (int*)(colacc + accd);
@@ -1247,7 +1259,7 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
     const DirFx F = direct_frame(r_s, w_s, B);
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
-        const int rr = e / cols, cc = e - rr * cols;
+        const int rr = cdiv(e), cc = e - rr * cols;
         const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
         if (det) fx_add(reinterpret_cast<Fx128*>(c_s) + B.j0 + cc, (double)P.sgn * (v * g_s[B.k0 + rr]), P.fxs);
         else atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
@@ -1467,6 +1479,7 @@ __global__ void k_direct_group(const ProbParams* __restrict__ probs, const Direc
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
+    const ColDiv cdiv(cols);
     const int area = rows * cols;
     float2* E = dsm;                        // [cols][rows]
     int* list = (int*)(dsm + area);         // [area]
@@ -1474,7 +1487,7 @@ __global__ void k_direct_group(const ProbParams* __restrict__ probs, const Direc
     const DirFx F = direct_frame(r_s, w_s, B);
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
         const int e = list[t];
-        const int rr = e / cols, cc = e - rr * cols;
+        const int rr = cdiv(e), cc = e - rr * cols;
         const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
         const float h = (float)v;
         E[cc * rows + rr] = make_float2(h, (float)(v - (double)h));
