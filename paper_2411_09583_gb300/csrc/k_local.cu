@@ -916,20 +916,30 @@ struct ColDiv {
 // multiple of 32.
 __device__ __forceinline__ int direct_partition(const ProbParams& P, const DirectBlock& B, int cols, int area,
                                                 const float2* __restrict__ r2, const float2* __restrict__ w2,
-                                                int* list, int* cnt)
+                                                int* list, int* cnt, bool colmajor = false)
 {
+    // entry e is (row e / cols, column e % cols), or with colmajor (row e % rows,
+    // column e / rows)
+    const int rows = area / cols;
     if (threadIdx.x == 0) { cnt[0] = 0; cnt[1] = 0; }
     __syncthreads();
     const float zf = (float)P.z;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int area_pad = (area + 31) & ~31;
-    const ColDiv div(cols);
+    const ColDiv div(colmajor ? rows : cols);
     for (int e = threadIdx.x; e < area_pad; e += blockDim.x) {
         const bool valid = e < area;
         bool asy = false;
         if (valid) {
-            const int rr = div(e), cc = e - rr * cols;
+            int rr, cc;
+            if (colmajor) {
+                cc = div(e);
+                rr = e - cc * rows;
+            } else {
+                rr = div(e);
+                cc = e - rr * cols;
+            }
             asy = w2[B.k0 + rr].x * r2[B.j0 + cc].x > zf;
         }
         const unsigned ma = __ballot_sync(0xffffffffu, valid && asy);
@@ -1250,21 +1260,48 @@ __global__ void k_direct_adj(const ProbParams* __restrict__ probs, const DirectB
     const DirectBlock B = blks[blockIdx.x];
     const ProbParams& P = probs[B.prob];
     const int rows = B.k1 - B.k0 + 1, cols = B.j1 - B.j0 + 1;
-    const ColDiv cdiv(cols);
+    const ColDiv rdiv(rows);
     const int area = rows * cols;
     const int accd = det ? 0 : cols;
     int* list = (int*)(colacc + accd);
     for (int i = threadIdx.x; i < accd; i += blockDim.x) colacc[i] = 0.0;
-    const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt);
+    // entries in column-major order, so that a warp's list positions hold runs
+    // of one column (as the forward's hold runs of one row)
+    const int nloc = direct_partition(P, B, cols, area, r2, w2, list, cnt, true);
     const DirFx F = direct_frame(r_s, w_s, B);
-    for (int t = threadIdx.x; t < area; t += blockDim.x) {
-        const int e = list[t];
-        const int rr = cdiv(e), cc = e - rr * cols;
-        const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
-        if (det) fx_add(reinterpret_cast<Fx128*>(c_s) + B.j0 + cc, (double)P.sgn * (v * g_s[B.k0 + rr]), P.fxs);
-        else atomicAdd(&colacc[cc], v * g_s[B.k0 + rr]);
+    if (det) {
+        for (int t = threadIdx.x; t < area; t += blockDim.x) {
+            const int e = list[t];
+            const int cc = rdiv(e), rr = e - cc * rows;
+            const double v = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0);
+            fx_add(reinterpret_cast<Fx128*>(c_s) + B.j0 + cc, (double)P.sgn * (v * g_s[B.k0 + rr]), P.fxs);
+        }
+        return;
     }
-    if (det) return;
+    // run sums by a segmented scan through the shuffles, one shared-memory
+    // atomic per run (see k_direct)
+    const int lane = threadIdx.x & 31;
+    const int area_pad = (area + 31) & ~31;
+    for (int t = threadIdx.x; t < area_pad; t += blockDim.x) {
+        int cc = -1;
+        double p = 0.0;
+        if (t < area) {
+            const int e = list[t];
+            cc = rdiv(e);
+            const int rr = e - cc * rows;
+            p = direct_entry_fx(P, F, w_s[B.k0 + rr], r_s[B.j0 + cc], t >= nloc, lowp != 0) * g_s[B.k0 + rr];
+        }
+        const int cprev = __shfl_up_sync(0xffffffffu, cc, 1);
+        const int cnext = __shfl_down_sync(0xffffffffu, cc, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || cprev != cc);
+        const int seg0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double q = __shfl_up_sync(0xffffffffu, p, off);
+            if (lane - off >= seg0) p += q;
+        }
+        if (cc >= 0 && (lane == 31 || cnext != cc)) atomicAdd(&colacc[cc], p);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < cols; i += blockDim.x)
         atomicAdd(&c_s[B.j0 + i], (double)P.sgn * colacc[i]);
