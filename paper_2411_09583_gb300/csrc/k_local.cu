@@ -1733,7 +1733,7 @@ cudaError_t launch_direct_adj(const ProbParams* probs, const DirectBlock* blks, 
                   sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_adj<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, g_s, c_s, lowp, det);
+    k_direct_adj<<<nblk, 256, smem, s>>>(probs, blks, r_s, w_s, r2, w2, g_s, c_s, lowp, det);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1890,7 +1890,7 @@ cudaError_t launch_direct(const ProbParams* probs, const DirectBlock* blks, int 
     size_t smem = sizeof(double) * acc + sizeof(int) * (size_t)max_area;
     cudaError_t e = cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct<<<nblk, 128, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, c_sb, c2b, g_sb, mode, det);
+    k_direct<<<nblk, 256, smem, s>>>(probs, blks, r_s, w_s, r2, w2, c_s, c2, g_s, c_sb, c2b, g_sb, mode, det);
     count_launches(1);
     return cudaGetLastError();
 }
