@@ -99,9 +99,42 @@ int local_order(int nu, double z, double eps)
 int choose_params(int nu, double eps, int m_terms, int* M, double* z, int* L)
 {
     nu = nu < 0 ? -nu : nu;
+    // a pure function of (nu, eps, m_terms) whose bisections take microseconds:
+    // remembered, so that a batch of many problems of few orders pays once per order
+    struct Key {
+        int nu, m_terms;
+        double eps;
+        bool operator<(const Key& o) const
+        {
+            if (nu != o.nu) return nu < o.nu;
+            if (m_terms != o.m_terms) return m_terms < o.m_terms;
+            return eps < o.eps;
+        }
+    };
+    struct Val {
+        int M, L;
+        double z;
+    };
+    static std::mutex mu;
+    static std::map<Key, Val> cache;
+    const Key key{nu, m_terms, eps};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *M = it->second.M;
+            *z = it->second.z;
+            *L = it->second.L;
+            return *L < 0 ? NUHT_ERR_UNSUPPORTED : NUHT_OK;
+        }
+    }
     *M = m_terms > 0 ? m_terms : heuristic_m(nu, eps);
     *z = crossover(nu, *M, eps);
     *L = local_order(nu, *z, eps);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (cache.size() < 4096) cache.emplace(key, Val{*M, *L, *z});
+    }
     return *L < 0 ? NUHT_ERR_UNSUPPORTED : NUHT_OK;
 }
 
