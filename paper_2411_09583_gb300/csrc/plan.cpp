@@ -275,6 +275,31 @@ cudaError_t aux_stream(Aux** out)
     return cudaSuccess;
 }
 
+// Per host thread and device: the stream on which the host-buffer entry point
+// uploads the coefficients while the plan runs, with its fork and done events.
+struct CopyAux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+};
+
+cudaError_t copy_aux(CopyAux** out)
+{
+    thread_local CopyAux a[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    CopyAux& x = a[dev];
+    if (!x.s) {
+        e = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    *out = &x;
+    return cudaSuccess;
+}
+
 // Per host thread and device: the two streams (and fork / join events) on
 // which an execute runs its block classes: the asymptotic pipeline on a
 // stream of the greatest priority, the local and direct blocks on one of the
@@ -1671,18 +1696,36 @@ int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega,
     Arena A;
     size_t o_r = A.reserve<double>(n), o_w = A.reserve<double>(m);
     size_t o_c = A.reserve<double>((size_t)n * nvec), o_g = A.reserve<double>((size_t)m * nvec);
+    // the coefficients' upload runs on a stream of its own beside the plan's
+    // device work (the plan never reads c); execute waits for it
     char* D = nullptr;
     NUHT_CK(pool_alloc((void**)&D, A.size, s));
     int rc = NUHT_OK;
     nuht_plan_t P = nullptr;
+    CopyAux* cx = nullptr;
+    bool c_issued = false;
     do {
         cudaError_t e = cudaSuccess;
         if (n) e = cudaMemcpyAsync(D + o_r, r, sizeof(double) * n, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && m) e = cudaMemcpyAsync(D + o_w, omega, sizeof(double) * m, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && n) e = cudaMemcpyAsync(D + o_c, c, sizeof(double) * n * nvec, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && n) {
+            // forked after the point uploads so that it does not share the
+            // link with them: the plan starts as early as before
+            e = copy_aux(&cx);
+            if (e == cudaSuccess) e = cudaEventRecord(cx->fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cx->s, cx->fork, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(D + o_c, c, sizeof(double) * n * nvec, cudaMemcpyHostToDevice, cx->s);
+            if (e == cudaSuccess) e = cudaEventRecord(cx->done, cx->s);
+            c_issued = e == cudaSuccess;
+        }
         if (e != cudaSuccess) { g_cuda_msg = cudaGetErrorString(e); rc = NUHT_ERR_CUDA; break; }
         rc = nuht_plan(&P, nu, (const double*)(D + o_r), n, (const double*)(D + o_w), m, eps, opt, stream);
         if (rc != NUHT_OK) break;
+        if (c_issued) {
+            e = cudaStreamWaitEvent(s, cx->done, 0);
+            if (e != cudaSuccess) { g_cuda_msg = cudaGetErrorString(e); rc = NUHT_ERR_CUDA; break; }
+        }
         rc = nuht_execute(P, (const double*)(D + o_c), (double*)(D + o_g), nvec, 0, stream);
         if (rc != NUHT_OK) break;
         if (m) e = cudaMemcpyAsync(g, D + o_g, sizeof(double) * m * nvec, cudaMemcpyDeviceToHost, s);
@@ -1690,6 +1733,9 @@ int nuht_transform_host(int nu, const double* r, int64_t n, const double* omega,
         if (e != cudaSuccess) { g_cuda_msg = cudaGetErrorString(e); rc = NUHT_ERR_CUDA; break; }
     } while (0);
     nuht_destroy(P);
+    // the upload finishes before the arena goes back to the pool (also on the
+    // paths that left the loop early)
+    if (cx) cudaStreamSynchronize(cx->s);
     pool_free(D, s);
     cudaStreamSynchronize(s);
     return rc;
