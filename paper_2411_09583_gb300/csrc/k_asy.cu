@@ -679,8 +679,9 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             }
         }
         // beta_qk = s^q sum_{j >= k, j = k mod 2} t_j MC(j, k), t_j = C(q+j-1, j) eta^j,
-        // MC(j, k) = 2^(1-j) C(j, (j-k)/2) (halved for k = 0)
-        for (int sl = tid; sl < gn * Q; sl += nt) {
+        // MC(j, k) = 2^(1-j) C(j, (j-k)/2) (halved for k = 0); on the last
+        // threads, which have the fewest items of (a)
+        for (int sl = nt - 1 - tid; sl < gn * Q; sl += nt) {
             const int b = sl / Q, q = sl - b * Q;
             const double R = B.rc + B.h * ((lfirst + g0 + b) + 0.5 * (w - 1));
             const df iR = df_recip(df_from(R));
@@ -821,7 +822,8 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             const double val = acc_value(sacc);
             if (val != 0.0) gv.add(2 * ((int64_t)idx * Q + (qv >> 1)) + (qv & 1), val);
         }
-        __syncthreads();
+        // no barrier here: (c) reads Ach and Mb only, the next group's (a)
+        // and beta write N and beta, and its (b) writes Mb after a barrier
     }
     }
 }
