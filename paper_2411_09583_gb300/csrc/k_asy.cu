@@ -38,6 +38,8 @@
 
 namespace nuht {
 
+int device_sm_count();
+
 namespace {
 
 constexpr int kWinCells = 64;   // grid cells an interpolation tile stages in shared memory
@@ -2606,8 +2608,8 @@ cudaError_t launch_spread_modes(const ProbParams* probs, const AsyBlock* blks, c
                                 Tables tab, const double* r_s, int32_t* modes, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    const int nb = (ntiles + 255) / 256;
-    k_spread_modes<<<nb < 152 * 16 ? nb : 152 * 16, 256, 0, s>>>(probs, blks, tiles, ntiles, tab, r_s, modes);
+    const int nb = (ntiles + 255) / 256, cap = device_sm_count() * 16;
+    k_spread_modes<<<nb < cap ? nb : cap, 256, 0, s>>>(probs, blks, tiles, ntiles, tab, r_s, modes);
     count_launches(1);
     return cudaGetLastError();
 }
