@@ -418,6 +418,8 @@ __host__ __device__ __forceinline__ size_t spread_moments_smem(int nt, int Q, in
 // the plain moment path.  Tiles whose bins are too wide for their radius
 // (eta too large for kFoldMax terms) take the plain moment path.
 constexpr int kFoldMax = 8;          // Chebyshev terms of the weights' dependence on v within a bin
+constexpr int kBetaStride = kFoldMax + 1;   // row stride of beta (float2): odd, so the q rows an
+                                            // M item's half-warp reads fall in distinct banks
 constexpr int kFoldDfMax = 4;        // extra double-float degrees of N the fold may need
 constexpr int kFoldGroupBytes = 8192;
 
@@ -520,7 +522,7 @@ __host__ __device__ __forceinline__ size_t spread_fold_smem(int nt, int Q, int w
     const int em = fold_emax(nb), edm = fold_edf_max(nb, dcs);
     const int sud = mom_stride(edm), suf = mom_stride(em - 2);
     return sizeof(float4) * ((size_t)nt + (size_t)G * em) +
-           sizeof(float2) * ((size_t)nt * sud + (size_t)G * L.dpad * 2 * Q + (size_t)G * Q * kFoldMax +
+           sizeof(float2) * ((size_t)nt * sud + (size_t)G * L.dpad * (2 * Q + 1) + (size_t)G * Q * kBetaStride +
                              (size_t)w * L.dpad) +
            sizeof(float) * (size_t)nt * suf + sizeof(int) * (size_t)nt;
 }
@@ -543,9 +545,12 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
     float4* Y = sm4;                                  // [nt] y_p as (re.h, re.l, im.h, im.l)
     float4* N = Y + nt;                               // [G][E] N[e] of a group of bins
     float2* Ud = (float2*)(N + G * E);                // [nt][sud] T_e(v_p), e < Edf
-    float2* Mb = Ud + nt * sud;                       // [G][dpad][Q2] M of a group of bins
-    float2* beta = Mb + G * L.dpad * Q2;              // [G][Q][kFoldMax] beta_qk
-    float2* Ach = beta + G * Q * kFoldMax;            // [w][dpad] Chebyshev coefficients of the taps
+    // M rows padded to Q2 + 1 (odd) float2: the items of a half-warp (4 degrees
+    // x 4 q pairs) store to distinct banks
+    const int Q2s = Q2 + 1;
+    float2* Mb = Ud + nt * sud;                       // [G][dpad][Q2s] M of a group of bins
+    float2* beta = Mb + G * L.dpad * Q2s;             // [G][Q][kBetaStride] beta_qk
+    float2* Ach = beta + G * Q * kBetaStride;         // [w][dpad] Chebyshev coefficients of the taps
     float* Uf = (float*)(Ach + w * L.dpad);           // [nt][suf] T_e(v_p), Edf <= e < E
     int* l0s = (int*)(Uf + nt * suf);                 // [nt]
     __shared__ int bstart[kMaxTileBins + 3];
@@ -702,7 +707,7 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
                 if (e & 1) sq = df_mul(sq, sp);
                 if (e > 1) sp = df_mul(sp, sp);
             }
-            float2* bt = beta + (b * Q + q) * kFoldMax;
+            float2* bt = beta + (b * Q + q) * kBetaStride;
             for (int k = 0; k < K; ++k) {
                 df acc{0.f, 0.f};
                 for (int j = k; j < K; j += 2) acc = df_add(acc, df_mul_f(tj[j], kFoldC.mc[j][k]));
@@ -720,8 +725,8 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             const int d = mom_degree(e, L.ndf, dcs, nb);
             float2 mr0 = make_float2(0.f, 0.f), mi0 = mr0, mr1 = mr0, mi1 = mr0;
             if (d >= 0) {
-                const float2* bt0 = beta + (b * Q + q0) * kFoldMax;
-                const float2* bt1 = bt0 + kFoldMax;
+                const float2* bt0 = beta + (b * Q + q0) * kBetaStride;
+                const float2* bt1 = bt0 + kBetaStride;
                 const float4* Nb = N + b * E;
                 const float4 n0 = Nb[d];
                 const bool dfe = e < 2 * L.ndf;
@@ -786,7 +791,7 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
                     mi1 = make_float2(fi1, 0.f);
                 }
             }
-            float2* mo = Mb + (b * L.dpad + e) * Q2 + 2 * q0;
+            float2* mo = Mb + (b * L.dpad + e) * Q2s + 2 * q0;
             mo[0] = mr0;
             mo[1] = mi0;
             mo[2] = mr1;
@@ -806,16 +811,16 @@ __device__ void spread_fold(const AsyBlock& B, int Q, int qs, const Tile& t, con
             acc2 sacc{0.f, 0.f};
             for (int b = b_lo; b <= b_hi; ++b) {
                 const float2* ar = Ach + (c - b) * L.dpad;
-                const float2* mb = Mb + b * L.dpad * Q2 + qv;
+                const float2* mb = Mb + b * L.dpad * Q2s + qv;
                 float sf = 0.f;
                 int e = 0;
                 if (dq) {
                     for (; e < 2 * L.ndf; ++e) {
-                        const float2 a2 = ar[e], m2 = mb[e * Q2];
+                        const float2 a2 = ar[e], m2 = mb[e * Q2s];
                         acc_fma(sacc, df{a2.x, a2.y}, df{m2.x, m2.y});
                     }
                 }
-                for (; e < L.dpad; ++e) sf = fmaf(ar[e].x, mb[e * Q2].x, sf);
+                for (; e < L.dpad; ++e) sf = fmaf(ar[e].x, mb[e * Q2s].x, sf);
                 float s2, e2;
                 two_sum(sacc.s, sf, s2, e2);
                 sacc.s = s2;
