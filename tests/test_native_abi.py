@@ -38,6 +38,29 @@ def test_params_match_oracle(lib, nu, eps):
     assert abs(z - zo) <= 1e-12 * zo
 
 
+def test_params_cached_and_concurrent_calls_agree(lib):
+    # the parameter choice is remembered per (order, tolerance, forced M): a
+    # repeated call (answered from memory) and calls from several host threads
+    # return the first call's values, which are the oracle's
+    import concurrent.futures as cf
+    from paper_2411_09583_gb300 import choose_params
+    cases = [(nu, eps, mt) for nu in (0, 1, 4, 13) for eps in (1e-6, 1e-9, 1e-13) for mt in (0, 6)]
+    first = {c: choose_params(c[0], c[1], m_terms=c[2]) for c in cases}
+    with cf.ThreadPoolExecutor(8) as ex:
+        again = list(ex.map(lambda c: (c, choose_params(c[0], c[1], m_terms=c[2])), cases * 4))
+    for c, v in again:
+        assert v == first[c], c
+    for (nu, eps, mt), (M, z, L) in first.items():
+        if mt == 0:
+            Mo, zo, Lo = OP.choose_params(nu, eps)
+            assert (M, L) == (Mo, Lo)
+            assert abs(z - zo) <= 1e-12 * zo
+        else:
+            assert M == mt
+            assert abs(z - OP.crossover_z(nu, mt, eps)) <= 1e-12 * z
+            assert L == OP.choose_l(nu, z, eps)
+
+
 def test_params_negative_order_and_forced_m(lib):
     from paper_2411_09583_gb300 import choose_params
     assert choose_params(-3, 1e-8) == choose_params(3, 1e-8)
